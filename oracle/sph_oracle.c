@@ -1,0 +1,697 @@
+/*
+ * sph_oracle.c -- plain, slow, obviously correct FP64 CPU oracle of one SPH
+ * time step (paper Section 2, Algorithm 1: build tree, find neighbours and
+ * smoothing length, SPH kernels, new time step, update).
+ *
+ * TEST INFRASTRUCTURE. Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library. It shares no code, header
+ * or constant with the CUDA path, and the CUDA path never calls it.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no FMA contraction:
+ * every +, -, * and / below is rounded on its own, in the order written).
+ *
+ * The paper prints none of the SPH equations; each function states the
+ * textbook definition it follows (Monaghan 1992 forms, M4 cubic spline of
+ * Table 1) and the reading taken where the paper is silent.
+ *
+ * Parallel loops are in gather form (each i writes only its own outputs), so
+ * results do not depend on the number of OpenMP threads.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int32_t eos;         /* 0 = Tait, 1 = ideal gas */
+    int32_t n_target;    /* target neighbour count (100) */
+    int32_t n_tol;       /* accepted |n - n_target| (5) */
+    int32_t max_h_iter;  /* h iterations before giving up */
+    int32_t periodic_z;  /* 1: minimum image along z with period lz */
+    int32_t pad_;
+    double rho0, c0, gamma, alpha, beta, eta2, cfl, lz;
+} orc_params;
+
+static const double ORC_PI = 3.14159265358979323846;
+
+void orc_set_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------------
+ * M4 cubic spline in 3D (Table 1, "M4 spline"), support 2h, q = r/h,
+ * sigma = 1/(pi h^3):
+ *   W = sigma (1 - 1.5 q^2 + 0.75 q^3)   0 <= q < 1
+ *   W = sigma 0.25 (2 - q)^3             1 <= q < 2
+ *   W = 0                                otherwise
+ * and its radial derivative dW/dr = (1/(pi h^4)) f(q) with
+ *   f = -3 q + 2.25 q^2 (q < 1),  f = -0.75 (2 - q)^2 (1 <= q < 2).
+ * ------------------------------------------------------------------------- */
+double orc_W(double r, double h)
+{
+    double q = r / h;
+    double sigma = 1.0 / (ORC_PI * h * h * h);
+    if (q < 1.0) return sigma * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+    if (q < 2.0) {
+        double t = 2.0 - q;
+        return sigma * (0.25 * t * t * t);
+    }
+    return 0.0;
+}
+
+double orc_dWdr(double r, double h)
+{
+    double q = r / h;
+    double k = 1.0 / (ORC_PI * h * h * h * h);
+    if (q < 1.0) return k * (-3.0 * q + 2.25 * q * q);
+    if (q < 2.0) {
+        double t = 2.0 - q;
+        return k * (-0.75 * t * t);
+    }
+    return 0.0;
+}
+
+/* Pair vector r_ij = r_i - r_j; along z the minimum image with period lz when
+ * periodic_z is set (Section 4.1.1: the patch is periodic in Z). */
+static inline void orc_pair(const orc_params *P, const double *x, const double *y,
+                            const double *z, int64_t i, int64_t j, double *d)
+{
+    d[0] = x[i] - x[j];
+    d[1] = y[i] - y[j];
+    double dz = z[i] - z[j];
+    if (P->periodic_z) {
+        double half = 0.5 * P->lz;
+        if (dz > half) dz = dz - P->lz;
+        else if (dz < -half) dz = dz + P->lz;
+    }
+    d[2] = dz;
+}
+
+/* r^2 = (dx dx + dy dy) + dz dz, left to right, each operation rounded. */
+static inline double orc_r2(const double *d)
+{
+    return (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+}
+
+/* Gather radius test r_ij^2 < (2 h)^2 with a strict "<". */
+static inline double orc_support2(double h)
+{
+    double s = 2.0 * h;
+    return s * s;
+}
+
+/* ---------------------------------------------------------------------------
+ * Uniform cell grid (Algorithm 1 step 1 replaced by a cell list): particles
+ * binned by floor((x - lo) / w); a query of radius R visits every cell whose
+ * index range overlaps [x - R, x + R] (one extra cell each side, so the
+ * candidate set is a superset), then applies the exact pair test.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double lo[3], w[3];
+    int n[3];
+    int periodic_z;
+    double lz;
+    int64_t *start; /* ncells + 1 */
+    int64_t *order; /* particle ids grouped by cell, ascending id within a cell */
+} orc_grid;
+
+static int orc_cell1(double v, double lo, double w, int n)
+{
+    double f = floor((v - lo) / w);
+    if (f < 0.0) return 0;
+    if (f > (double)(n - 1)) return n - 1;
+    return (int)f;
+}
+
+static int orc_grid_build(orc_grid *g, const orc_params *P, int64_t n, const double *x,
+                          const double *y, const double *z, double cell_w)
+{
+    const double *c[3] = {x, y, z};
+    for (int d = 0; d < 3; ++d) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int64_t i = 0; i < n; ++i) {
+            if (c[d][i] < mn) mn = c[d][i];
+            if (c[d][i] > mx) mx = c[d][i];
+        }
+        if (n == 0) { mn = 0.0; mx = 0.0; }
+        double ext = mx - mn;
+        double w = cell_w > 0.0 ? cell_w : 1.0;
+        int cnt = (int)fmin(256.0, floor(ext / w) + 1.0);
+        if (cnt < 1) cnt = 1;
+        if ((double)cnt * w <= ext) w = ext / ((double)cnt - 0.5);
+        g->lo[d] = mn;
+        g->w[d] = w;
+        g->n[d] = cnt;
+    }
+    g->periodic_z = P->periodic_z;
+    g->lz = P->lz;
+    if (P->periodic_z) {
+        double w = cell_w > 0.0 ? cell_w : P->lz;
+        int cnt = (int)floor(P->lz / w);
+        if (cnt < 1) cnt = 1;
+        if (cnt > 256) cnt = 256;
+        g->lo[2] = -0.5 * P->lz;
+        g->w[2] = P->lz / (double)cnt;
+        g->n[2] = cnt;
+    }
+    int64_t ncell = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    g->start = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
+    g->order = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *cell = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!g->start || !g->order || !cell) {
+        free(g->start); free(g->order); free(cell);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int kx = orc_cell1(x[i], g->lo[0], g->w[0], g->n[0]);
+        int ky = orc_cell1(y[i], g->lo[1], g->w[1], g->n[1]);
+        int kz = orc_cell1(z[i], g->lo[2], g->w[2], g->n[2]);
+        cell[i] = ((int64_t)kz * g->n[1] + ky) * g->n[0] + kx;
+        g->start[cell[i] + 1] += 1;
+    }
+    for (int64_t k = 0; k < ncell; ++k) g->start[k + 1] += g->start[k];
+    int64_t *fill = (int64_t *)malloc((size_t)ncell * sizeof(int64_t) + 8);
+    if (!fill) { free(g->start); free(g->order); free(cell); return -1; }
+    memcpy(fill, g->start, (size_t)ncell * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) g->order[fill[cell[i]]++] = i;
+    free(fill);
+    free(cell);
+    return 0;
+}
+
+static void orc_grid_free(orc_grid *g)
+{
+    free(g->start);
+    free(g->order);
+}
+
+/* Index range of cells to visit along axis d for a query interval [v-R, v+R]. */
+static void orc_range(const orc_grid *g, int d, double v, double R, int *k0, int *k1)
+{
+    double a = floor((v - R - g->lo[d]) / g->w[d]) - 1.0;
+    double b = floor((v + R - g->lo[d]) / g->w[d]) + 1.0;
+    if (d == 2 && g->periodic_z) {
+        if (b - a + 1.0 >= (double)g->n[2]) { *k0 = 0; *k1 = g->n[2] - 1; return; }
+        *k0 = (int)a;  /* may be negative or >= n: wrapped by the caller */
+        *k1 = (int)b;
+        return;
+    }
+    if (a < 0.0) a = 0.0;
+    if (b > (double)(g->n[d] - 1)) b = (double)(g->n[d] - 1);
+    *k0 = (int)a;
+    *k1 = (int)b;
+}
+
+static inline int orc_wrap(int k, int n)
+{
+    int r = k % n;
+    return r < 0 ? r + n : r;
+}
+
+/* Visit every candidate j of the query (cells overlapping radius R) and call
+ * visit(ctx, j). Each particle is visited at most once. */
+typedef void (*orc_visit_fn)(void *ctx, int64_t j);
+
+static void orc_grid_query(const orc_grid *g, double px, double py, double pz, double R,
+                           orc_visit_fn visit, void *ctx)
+{
+    int x0, x1, y0, y1, z0, z1;
+    orc_range(g, 0, px, R, &x0, &x1);
+    orc_range(g, 1, py, R, &y0, &y1);
+    orc_range(g, 2, pz, R, &z0, &z1);
+    for (int kz = z0; kz <= z1; ++kz) {
+        int cz = g->periodic_z ? orc_wrap(kz, g->n[2]) : kz;
+        for (int ky = y0; ky <= y1; ++ky)
+            for (int kx = x0; kx <= x1; ++kx) {
+                int64_t c = ((int64_t)cz * g->n[1] + ky) * g->n[0] + kx;
+                for (int64_t e = g->start[c]; e < g->start[c + 1]; ++e) visit(ctx, g->order[e]);
+            }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Neighbour counting (Algorithm 1 step 2; footnote of Section 2: the run aims
+ * at a target neighbour count which sets h). Gather set of i at radius 2h:
+ *   N_i(h) = { j != i : r_ij^2 < (2h)^2 },  n_i = |N_i|.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    const orc_params *P;
+    const double *x, *y, *z;
+    int64_t i;
+    double s2;
+    int64_t count;
+} orc_count_ctx;
+
+static void orc_count_visit(void *vctx, int64_t j)
+{
+    orc_count_ctx *c = (orc_count_ctx *)vctx;
+    if (j == c->i) return;
+    double d[3];
+    orc_pair(c->P, c->x, c->y, c->z, c->i, j, d);
+    if (orc_r2(d) < c->s2) c->count += 1;
+}
+
+int64_t orc_count_brute(const orc_params *P, int64_t n, const double *x, const double *y,
+                        const double *z, int64_t i, double h)
+{
+    orc_count_ctx c = {P, x, y, z, i, orc_support2(h), 0};
+    for (int64_t j = 0; j < n; ++j) orc_count_visit(&c, j);
+    return c.count;
+}
+
+static int64_t orc_count_grid(const orc_grid *g, const orc_params *P, const double *x,
+                              const double *y, const double *z, int64_t i, double h)
+{
+    orc_count_ctx c = {P, x, y, z, i, orc_support2(h), 0};
+    orc_grid_query(g, x[i], y[i], z[i], 2.0 * h, orc_count_visit, &c);
+    return c.count;
+}
+
+/* ---------------------------------------------------------------------------
+ * Smoothing-length iteration (reading of the Section 2 footnote; the paper
+ * gives no update rule). Bracketing search that uses only correctly rounded
+ * + - * and compares, so every conforming implementation reaches the same
+ * bits:
+ *   lo = 0, hi = +inf, h = h_in
+ *   repeat up to max_h_iter counts:
+ *     n = |N_i(h)|;  if |n - n_target| <= n_tol: converged
+ *     if n < n_target - n_tol: lo = h, h = (hi == inf) ? 1.25 h : (lo + hi) / 2
+ *     else:                    hi = h, h = (lo == 0)   ? 0.8 h  : (lo + hi) / 2
+ * The returned h is the last one counted; nnb is its count. A particle that
+ * never lands in the band keeps that h and conv = 0.
+ * ------------------------------------------------------------------------- */
+static double orc_h_search(const orc_params *P, int64_t i, double h0,
+                           int64_t (*count)(const void *, int64_t, double), const void *cctx,
+                           int32_t *nnb, uint8_t *conv)
+{
+    double h = h0, lo = 0.0, hi = INFINITY;
+    int64_t lowb = (int64_t)P->n_target - P->n_tol;
+    int64_t highb = (int64_t)P->n_target + P->n_tol;
+    *conv = 0;
+    for (int it = 0; it < P->max_h_iter; ++it) {
+        int64_t k = count(cctx, i, h);
+        *nnb = (int32_t)k;
+        if (k >= lowb && k <= highb) { *conv = 1; return h; }
+        if (it == P->max_h_iter - 1) break;
+        if (k < lowb) {
+            lo = h;
+            h = isinf(hi) ? h * 1.25 : 0.5 * (lo + hi);
+        } else {
+            hi = h;
+            h = (lo == 0.0) ? h * 0.8 : 0.5 * (lo + hi);
+        }
+    }
+    return h;
+}
+
+typedef struct {
+    const orc_grid *g;
+    const orc_params *P;
+    const double *x, *y, *z;
+    int64_t n;
+} orc_hctx;
+
+static int64_t orc_hcount_grid(const void *v, int64_t i, double h)
+{
+    const orc_hctx *c = (const orc_hctx *)v;
+    return orc_count_grid(c->g, c->P, c->x, c->y, c->z, i, h);
+}
+
+static int64_t orc_hcount_brute(const void *v, int64_t i, double h)
+{
+    const orc_hctx *c = (const orc_hctx *)v;
+    return orc_count_brute(c->P, c->n, c->x, c->y, c->z, i, h);
+}
+
+static double orc_max(int64_t n, const double *a)
+{
+    double m = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        if (a[i] > m) m = a[i];
+    return m;
+}
+
+/* Returns the number of particles that did not converge, or -1 on allocation
+ * failure. brute != 0 counts over all pairs instead of the cell grid. */
+int64_t orc_h_iterate(const orc_params *P, int64_t n, const double *x, const double *y,
+                      const double *z, const double *h_in, double *h_out, int32_t *nnb,
+                      uint8_t *conv, int brute)
+{
+    orc_grid g;
+    memset(&g, 0, sizeof g);
+    if (!brute && orc_grid_build(&g, P, n, x, y, z, 2.0 * orc_max(n, h_in)) != 0) return -1;
+    orc_hctx c = {&g, P, x, y, z, n};
+    int64_t bad = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : bad)
+    for (int64_t i = 0; i < n; ++i) {
+        h_out[i] = orc_h_search(P, i, h_in[i], brute ? orc_hcount_brute : orc_hcount_grid, &c,
+                                &nnb[i], &conv[i]);
+        if (!conv[i]) bad += 1;
+    }
+    if (!brute) orc_grid_free(&g);
+    return bad;
+}
+
+/* ---------------------------------------------------------------------------
+ * Symmetric interaction set (reading; the paper is silent): the forces sum
+ * over S_i = { j != i : r_ij^2 < (2h_i)^2  or  r_ij^2 < (2h_j)^2 }, which is
+ * symmetric in (i, j) as antisymmetric pair forces need. The density sums
+ * over the gather subset N_i (first condition).
+ *
+ * CSR layout: row i holds first the entries of N_i in ascending j, then those
+ * of S_i \ N_i in ascending j; ngather[i] = |N_i|.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    const orc_params *P;
+    const double *x, *y, *z, *h;
+    int64_t i;
+    double si2;
+    int64_t *buf;   /* candidate list: j, tagged by (j << 1) | outer */
+    int64_t len, cap;
+    int oom;
+} orc_sym_ctx;
+
+static void orc_sym_visit(void *vctx, int64_t j)
+{
+    orc_sym_ctx *c = (orc_sym_ctx *)vctx;
+    if (j == c->i) return;
+    double d[3];
+    orc_pair(c->P, c->x, c->y, c->z, c->i, j, d);
+    double r2 = orc_r2(d);
+    int in_i = r2 < c->si2;
+    int in_j = r2 < orc_support2(c->h[j]);
+    if (!(in_i || in_j)) return;
+    if (c->len == c->cap) {
+        int64_t nc = c->cap ? 2 * c->cap : 256;
+        int64_t *nb = (int64_t *)realloc(c->buf, (size_t)nc * sizeof(int64_t));
+        if (!nb) { c->oom = 1; return; }
+        c->buf = nb;
+        c->cap = nc;
+    }
+    c->buf[c->len++] = (j << 1) | (in_i ? 0 : 1);
+}
+
+static int orc_cmp_i64(const void *a, const void *b)
+{
+    int64_t u = *(const int64_t *)a, v = *(const int64_t *)b;
+    return (u > v) - (u < v);
+}
+
+/* Gather row i of S_i into c->buf, sorted so that N_i comes first. */
+static void orc_sym_row(const orc_grid *g, orc_sym_ctx *c, int brute, int64_t n, double hmax)
+{
+    c->len = 0;
+    if (brute) {
+        for (int64_t j = 0; j < n; ++j) orc_sym_visit(c, j);
+    } else {
+        double hi = c->h[c->i];
+        double R = 2.0 * (hi > hmax ? hi : hmax);
+        orc_grid_query(g, c->x[c->i], c->y[c->i], c->z[c->i], R, orc_sym_visit, c);
+    }
+    /* key: outer flag first, then j: sort (outer, j) lexicographically */
+    for (int64_t k = 0; k < c->len; ++k) {
+        int64_t v = c->buf[k];
+        c->buf[k] = ((v & 1) << 62) | (v >> 1);
+    }
+    qsort(c->buf, (size_t)c->len, sizeof(int64_t), orc_cmp_i64);
+}
+
+/* Pass 1: counts[i] = |S_i|. Returns 0, or -1 on allocation failure. */
+int orc_csr_count(const orc_params *P, int64_t n, const double *x, const double *y,
+                  const double *z, const double *h, int64_t *counts, int brute)
+{
+    orc_grid g;
+    memset(&g, 0, sizeof g);
+    double hmax = orc_max(n, h);
+    if (!brute && orc_grid_build(&g, P, n, x, y, z, 2.0 * hmax) != 0) return -1;
+    int fail = 0;
+#pragma omp parallel reduction(| : fail)
+    {
+        orc_sym_ctx c = {P, x, y, z, h, 0, 0.0, NULL, 0, 0, 0};
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) {
+            c.i = i;
+            c.si2 = orc_support2(h[i]);
+            orc_sym_row(&g, &c, brute, n, hmax);
+            counts[i] = c.len;
+        }
+        fail |= c.oom;
+        free(c.buf);
+    }
+    if (!brute) orc_grid_free(&g);
+    return fail ? -1 : 0;
+}
+
+/* Pass 2: offsets[n+1] (given, exclusive prefix of counts), idx[nnz],
+ * ngather[n]. */
+int orc_csr_fill(const orc_params *P, int64_t n, const double *x, const double *y,
+                 const double *z, const double *h, const int64_t *offsets, int32_t *idx,
+                 int32_t *ngather, int brute)
+{
+    orc_grid g;
+    memset(&g, 0, sizeof g);
+    double hmax = orc_max(n, h);
+    if (!brute && orc_grid_build(&g, P, n, x, y, z, 2.0 * hmax) != 0) return -1;
+    int fail = 0;
+#pragma omp parallel reduction(| : fail)
+    {
+        orc_sym_ctx c = {P, x, y, z, h, 0, 0.0, NULL, 0, 0, 0};
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) {
+            c.i = i;
+            c.si2 = orc_support2(h[i]);
+            orc_sym_row(&g, &c, brute, n, hmax);
+            if (c.len != offsets[i + 1] - offsets[i]) { fail = 1; continue; }
+            int32_t ng = 0;
+            for (int64_t k = 0; k < c.len; ++k) {
+                int64_t v = c.buf[k];
+                if (!(v >> 62)) ng += 1;
+                idx[offsets[i] + k] = (int32_t)(v & ((INT64_C(1) << 62) - 1));
+            }
+            ngather[i] = ng;
+        }
+        fail |= c.oom;
+        free(c.buf);
+    }
+    if (!brute) orc_grid_free(&g);
+    return fail ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Density summation (Section 2, step 3 "density"): standard volume elements,
+ *   rho_i = m_i W(0, h_i) + sum_{j in N_i} m_j W(r_ij, h_i).
+ * ------------------------------------------------------------------------- */
+void orc_density(const orc_params *P, int64_t n, const double *x, const double *y,
+                 const double *z, const double *m, const double *h, const int64_t *offsets,
+                 const int32_t *idx, const int32_t *ngather, double *rho)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = m[i] * orc_W(0.0, h[i]);
+        for (int64_t e = offsets[i]; e < offsets[i] + ngather[i]; ++e) {
+            int64_t j = idx[e];
+            double d[3];
+            orc_pair(P, x, y, z, i, j, d);
+            s = s + m[j] * orc_W(sqrt(orc_r2(d)), h[i]);
+        }
+        rho[i] = s;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Equation of state.
+ *  Tait (square patch): p = (c0^2 rho0 / 7) (x^7 - 1), x = rho/rho0, with
+ *    x^7 = ((x^2)^2 x^2) x; sound speed c = sqrt(dp/drho) = c0 x^3.
+ *  Ideal gas (Evrard, Section 4.1.2, gamma = 5/3): p = (gamma - 1) rho u,
+ *    c = sqrt(gamma (gamma - 1) u).
+ * ------------------------------------------------------------------------- */
+void orc_eos(const orc_params *P, int64_t n, const double *rho, const double *u, double *p,
+             double *c)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        if (P->eos == 0) {
+            double xr = rho[i] / P->rho0;
+            double x2 = xr * xr;
+            double x4 = x2 * x2;
+            double x7 = (x4 * x2) * xr;
+            p[i] = (P->c0 * P->c0 * P->rho0 / 7.0) * (x7 - 1.0);
+            c[i] = P->c0 * (x2 * xr);
+        } else {
+            p[i] = (P->gamma - 1.0) * rho[i] * u[i];
+            c[i] = sqrt(P->gamma * (P->gamma - 1.0) * u[i]);
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Momentum and energy with Monaghan artificial viscosity (Section 2, step 3
+ * "acceleration, rate of change of internal energy"; Table 1 "standard"
+ * volume elements and "kernel derivatives" gradients). For j in S_i:
+ *   r_ij = r_i - r_j, v_ij = v_i - v_j, r = |r_ij|
+ *   Fbar_ij = (dW/dr(r, h_i) + dW/dr(r, h_j)) / 2 / r  (each zero outside its
+ *             own support), so grad_i Wbar_ij = Fbar_ij r_ij
+ *   A_i = p_i / rho_i^2
+ *   if v_ij . r_ij < 0:
+ *      hb = (h_i + h_j)/2, cb = (c_i + c_j)/2, rhob = (rho_i + rho_j)/2
+ *      mu_ij = hb (v_ij . r_ij) / (r^2 + eta2 hb^2)
+ *      Pi_ij = (-alpha cb mu_ij + beta mu_ij^2) / rhob
+ *   else mu_ij = Pi_ij = 0
+ *   a_i   = - sum_j m_j (A_i + A_j + Pi_ij) Fbar_ij r_ij
+ *   du_i  = A_i sum_j m_j Fbar_ij (v_ij . r_ij)
+ *           + 1/2 sum_j m_j Pi_ij Fbar_ij (v_ij . r_ij)
+ *   mumax_i = max_j |mu_ij|
+ * A pair at zero separation contributes nothing.
+ * ------------------------------------------------------------------------- */
+void orc_forces(const orc_params *P, int64_t n, const double *x, const double *y,
+                const double *z, const double *vx, const double *vy, const double *vz,
+                const double *m, const double *h, const double *rho, const double *p,
+                const double *c, const int64_t *offsets, const int32_t *idx, double *ax,
+                double *ay, double *az, double *du, double *mumax)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double Ai = p[i] / (rho[i] * rho[i]);
+        double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0, sv = 0.0, mum = 0.0;
+        for (int64_t e = offsets[i]; e < offsets[i + 1]; ++e) {
+            int64_t j = idx[e];
+            double d[3];
+            orc_pair(P, x, y, z, i, j, d);
+            double r2 = orc_r2(d);
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2);
+            double Fb = 0.5 * (orc_dWdr(r, h[i]) + orc_dWdr(r, h[j])) / r;
+            double wx = vx[i] - vx[j], wy = vy[i] - vy[j], wz = vz[i] - vz[j];
+            double vr = (wx * d[0] + wy * d[1]) + wz * d[2];
+            double Pi = 0.0, mu = 0.0;
+            if (vr < 0.0) {
+                double hb = 0.5 * (h[i] + h[j]);
+                double cb = 0.5 * (c[i] + c[j]);
+                double rb = 0.5 * (rho[i] + rho[j]);
+                mu = hb * vr / (r2 + P->eta2 * hb * hb);
+                Pi = (-P->alpha * cb * mu + P->beta * mu * mu) / rb;
+            }
+            double Aj = p[j] / (rho[j] * rho[j]);
+            double g = m[j] * (Ai + Aj + Pi) * Fb;
+            sx = sx + g * d[0];
+            sy = sy + g * d[1];
+            sz = sz + g * d[2];
+            sp = sp + m[j] * Fb * vr;
+            sv = sv + m[j] * Pi * Fb * vr;
+            double amu = fabs(mu);
+            if (amu > mum) mum = amu;
+        }
+        ax[i] = -sx;
+        ay[i] = -sy;
+        az[i] = -sz;
+        du[i] = Ai * sp + 0.5 * sv;
+        mumax[i] = mum;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * New time step (Algorithm 1 step 5; reading: Monaghan's Courant form with
+ * the viscous signal term, CFL factor from the workload):
+ *   dt = cfl * min_i h_i / (c_i + 1.2 (alpha c_i + beta mumax_i)).
+ * Returns +inf for n == 0.
+ * ------------------------------------------------------------------------- */
+double orc_dt(const orc_params *P, int64_t n, const double *h, const double *c,
+              const double *mumax)
+{
+    double best = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        double v = h[i] / (c[i] + 1.2 * (P->alpha * c[i] + P->beta * mumax[i]));
+        if (v < best) best = v;
+    }
+    return P->cfl * best;
+}
+
+/* ---------------------------------------------------------------------------
+ * Update velocity and position (Algorithm 1 step 6; leapfrog read as
+ * kick-drift): v += dt a; u += dt du; x += dt v (new v); then z is wrapped
+ * back into [-lz/2, lz/2) when periodic.
+ * ------------------------------------------------------------------------- */
+void orc_leapfrog(const orc_params *P, int64_t n, double dt, double *x, double *y, double *z,
+                  double *vx, double *vy, double *vz, double *u, const double *ax,
+                  const double *ay, const double *az, const double *du)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        vx[i] = vx[i] + dt * ax[i];
+        vy[i] = vy[i] + dt * ay[i];
+        vz[i] = vz[i] + dt * az[i];
+        u[i] = u[i] + dt * du[i];
+        x[i] = x[i] + dt * vx[i];
+        y[i] = y[i] + dt * vy[i];
+        z[i] = z[i] + dt * vz[i];
+        if (P->periodic_z) {
+            double half = 0.5 * P->lz;
+            if (z[i] >= half) z[i] = z[i] - P->lz;
+            else if (z[i] < -half) z[i] = z[i] + P->lz;
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Whole time step, Algorithm 1 order: neighbours and h, density, EOS,
+ * forces, dt, update. State arrays are updated in place; rho, p, c, a, du,
+ * mumax receive the values of the last step's force evaluation. stats (may be
+ * NULL) receives { nnz of the last step, non-converged particles summed over
+ * the steps }. Returns 0, or -1 on allocation failure.
+ * ------------------------------------------------------------------------- */
+int orc_step(const orc_params *P, int64_t n, int nsteps, double *x, double *y, double *z,
+             double *vx, double *vy, double *vz, const double *m, double *h, double *u,
+             double *rho, double *p, double *c, double *ax, double *ay, double *az, double *du,
+             double *mumax, double *time, double *dt_out, int64_t *stats)
+{
+    int32_t *nnb = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t *ng = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    uint8_t *conv = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    int64_t *off = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    double *hn = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    int rc = 0;
+    int64_t bad_total = 0, nnz = 0;
+    if (!nnb || !ng || !conv || !off || !hn) { rc = -1; goto done; }
+    for (int s = 0; s < nsteps; ++s) {
+        int64_t bad = orc_h_iterate(P, n, x, y, z, h, hn, nnb, conv, 0);
+        if (bad < 0) { rc = -1; goto done; }
+        bad_total += bad;
+        memcpy(h, hn, (size_t)n * sizeof(double));
+        if (orc_csr_count(P, n, x, y, z, h, off + 1, 0) != 0) { rc = -1; goto done; }
+        off[0] = 0;
+        for (int64_t i = 0; i < n; ++i) off[i + 1] += off[i];
+        nnz = off[n];
+        int32_t *idx = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+        if (!idx) { rc = -1; goto done; }
+        if (orc_csr_fill(P, n, x, y, z, h, off, idx, ng, 0) != 0) { free(idx); rc = -1; goto done; }
+        orc_density(P, n, x, y, z, m, h, off, idx, ng, rho);
+        orc_eos(P, n, rho, u, p, c);
+        orc_forces(P, n, x, y, z, vx, vy, vz, m, h, rho, p, c, off, idx, ax, ay, az, du, mumax);
+        free(idx);
+        double dt = orc_dt(P, n, h, c, mumax);
+        orc_leapfrog(P, n, dt, x, y, z, vx, vy, vz, u, ax, ay, az, du);
+        *time = *time + dt;
+        *dt_out = dt;
+    }
+done:
+    if (stats) { stats[0] = nnz; stats[1] = bad_total; }
+    free(nnb); free(ng); free(conv); free(off); free(hn);
+    return rc;
+}
