@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""SPH time-step benchmark (arXiv 1809.08013, Algorithm 1) on one GB300.
+
+Default workload: rotating square patch, 100^3 = 1,000,000 particles, FP64,
+20 leapfrog steps from the initial conditions (neighbour lists rebuilt and h
+iterated to 100 +- 5 every step). One benchmark "step" is one full SPH time
+step through the C ABI (sph_step). Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 runs under torchrun as independent replicas (one instance per GPU, no
+collective on the data path; the barrier and max-over-ranks timing only).
+--impl reference times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SPH particle-updates/s at 1M on 1 GB300 (% roofline); ensemble p50/p99 latency"
+UNIT = "particle-updates/s"
+
+# Counted FP64 work of one pair term of the force kernel, from the operations
+# the definition writes out (each +, -, *, / and sqrt = 1): pair vector 3,
+# r^2 5, r 1, q_i and q_j 2, two cubic-spline derivatives 2 x 5 plus their
+# 1/(pi h^4) factors 2, Fbar 3, v_ij 3, v.r 5, (A_i + A_j + Pi) m_j Fbar 4,
+# acceleration 6, energy sums 7  -> 51; the viscosity branch (v.r < 0) adds
+# hb, cb, rhob 6, mu 5, Pi 6 -> 17 more.
+FLOPS_PAIR_BASE = 51
+FLOPS_PAIR_AV = 17
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--side", type=int, default=100, help="lattice side (100 -> 1M particles)")
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_name(side):
+    n = side ** 3
+    return (f"rotating square patch {side}^3 = {n:,} particles (Section 4.1.1: lattice dx=1/{side}, "
+            f"jitter 0.01 dx, omega=5, rho0=1000, Tait c0=50, periodic z), FP64, cubic spline, "
+            f"h iterated to 100+-5 neighbours every step, Monaghan AV alpha=1 beta=2, CFL 0.3, "
+            f"kick-drift leapfrog from the initial conditions")
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (read-only)."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.proc = None
+        self.lines = []
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self, t0, t1):
+        import datetime
+        rows = []
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        if not inside:  # region shorter than the sampling period: nearest samples
+            inside = sorted(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + t1)))[:3]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[3][k].lower() == "active"})
+        mhz = sorted(r[1] for r in inside)
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+# --------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1809_08013_gb300 import ics
+    oracle.build()
+    side = 37  # bounded sample of the workload: same recipe at 37^3 = 50,653 particles
+    s, prm = ics.square_patch(side, seed=args.seed)
+    n = side ** 3
+    for _ in range(args.warmup):
+        oracle.step(prm, s, nsteps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(prm, s, nsteps=1)  # every step starts from the initial conditions
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    sample = (f"oracle (plain C FP64, OpenMP) step of the same patch recipe at {side}^3 = {n:,} "
+              f"particles from its initial conditions, {args.steps} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.side), "sample_particles": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- native arm
+def av_fraction(B, ctx, arr, sample_rows=4000):
+    """Share of interaction pairs with v_ij . r_ij < 0 (viscosity branch) on a
+    sample of rows of the last step's neighbour list (host-side estimate used
+    only for the counted-flop figure)."""
+    import numpy as np
+    off, idx, ng, order = ctx.neighbors_to_host()
+    n = len(order)
+    if n == 0 or off[-1] == 0:
+        return 0.0, 0
+    rng = np.random.Generator(np.random.PCG64(0))
+    rows = rng.choice(n, size=min(sample_rows, n), replace=False)
+    x = {k: arr[k].cpu().numpy() for k in ("x", "y", "z", "vx", "vy", "vz")}
+    tot = neg = 0
+    for k in rows:
+        js = order[idx[off[k]:off[k + 1]]]
+        i = order[k]
+        d = np.stack([x["x"][i] - x["x"][js], x["y"][i] - x["y"][js], x["z"][i] - x["z"][js]])
+        d[2] -= np.round(d[2])
+        w = np.stack([x["vx"][i] - x["vx"][js], x["vy"][i] - x["vy"][js], x["vz"][i] - x["vz"][js]])
+        vr = (w * d).sum(0)
+        neg += int(np.count_nonzero(vr < 0))
+        tot += len(js)
+    return neg / max(tot, 1), int(off[-1])
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1809_08013_gb300 import binding as B
+    from paper_1809_08013_gb300 import ics
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                init_method="env://")
+    if not torch.cuda.is_available():
+        raise RuntimeError("the native arm needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.load()
+
+    s, prm = ics.square_patch(args.side, seed=args.seed)
+    n = len(s["x"])
+    ctx = B.Context(n, device=local)
+    arr = B.alloc_arrays(s, device=dev)
+    ic = {k: arr[k].clone() for k in B.STATE_FIELDS}
+    stream = torch.cuda.current_stream(dev)
+
+    def reset():
+        for k in B.STATE_FIELDS:
+            arr[k].copy_(ic[k])
+        arr["time"].zero_()
+
+    fp64_peak = B.probe_fma_peak(local, fp64=True, stream=stream)
+    fp32_peak = B.probe_fma_peak(local, fp64=False, stream=stream)
+
+    # warm-up (untimed), then back to the initial conditions
+    ctx.step(prm, arr, nsteps=args.warmup, stream=stream)
+    st = ctx.sync(stream)
+    if st not in (B.SPH_OK, B.SPH_E_HNOCONV):
+        raise RuntimeError(f"warm-up status {B.STATUS_NAMES.get(st)}: {ctx.error()}")
+    reset()
+    torch.cuda.synchronize(dev)
+
+    uuid = None
+    try:
+        u = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+        if u is not None:
+            us = str(u)
+            uuid = us if us.startswith("GPU-") else "GPU-" + us
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    time.sleep(1.0 if sampler else 0.0)
+
+    ctx.timing_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = ctx.launch_count()
+    w0 = time.time()
+    e0.record(stream)
+    ctx.step(prm, arr, nsteps=args.steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    w1 = time.time()
+    if world > 1:
+        dist.barrier()
+    launches = ctx.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    phase_ms, phase_launches, tsteps = ctx.timing_read()
+    ctx.timing_enable(False)
+    status = ctx.sync(stream)
+    if sampler:
+        time.sleep(0.3)
+        sampler.stop()
+    if status not in (B.SPH_OK, B.SPH_E_HNOCONV):
+        raise RuntimeError(f"timed status {B.STATUS_NAMES.get(status)}: {ctx.error()}")
+
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * n * args.steps / (ms_max * 1e-3)
+
+    # end to end through the public API: pinned host state in, one step, state out
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(s[k])).pin_memory()
+                for k in B.STATE_FIELDS}
+        hdt = torch.zeros(1, dtype=torch.float64).pin_memory()
+        reset()
+        torch.cuda.synchronize(dev)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        f0.record(stream)
+        for _ in range(args.steps):
+            for k in B.STATE_FIELDS:
+                arr[k].copy_(host[k], non_blocking=True)
+            ctx.step(prm, arr, nsteps=1, stream=stream)
+            for k in B.STATE_FIELDS:
+                host[k].copy_(arr[k], non_blocking=True)
+            hdt.copy_(arr["dt"], non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = f0.elapsed_time(f1)
+        if world > 1:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        ctx.sync(stream)
+        e2e = {"value": world * n * args.steps / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * len(B.STATE_FIELDS) * n,
+               "d2h_bytes_per_step": 8 * len(B.STATE_FIELDS) * n + 8}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (forces): counted FP64 flops per launch
+    f_av, nnz = av_fraction(B, ctx, arr)
+    flops_launch = nnz * (FLOPS_PAIR_BASE + FLOPS_PAIR_AV * f_av)
+    forces_s = phase_ms["forces"] * 1e-3 / max(tsteps, 1)
+    achieved = flops_launch / forces_s / 1e12
+    peak = fp64_peak / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_forces (+ k_dt_finish)",
+                "peak_source": "FP64 FMA-chain probe on this GPU in this run (sph_probe_fma_peak), "
+                               "2 flops per FMA",
+                "fp32_probe_tflops": fp32_peak / 1e12,
+                "flops_per_launch": flops_launch, "pairs_per_launch": nnz,
+                "av_pair_fraction": f_av}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.step(prm, s, nsteps=1)
+        tc = time.perf_counter() - t0
+        cpu = {"value": n / tc, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+               "sample": f"one oracle step (plain C FP64, OpenMP) of the same {n:,}-particle "
+                         f"patch from its initial conditions: {tc:.1f} s"}
+
+    clocks = sampler.summary(w0, w1) if sampler else None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.side), "n_particles": n,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (state ~0.2 GB + neighbour list ~0.4 GB)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "status": B.STATUS_NAMES.get(status),
+            "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
+            "launches_per_phase": phase_launches}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

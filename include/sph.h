@@ -1,0 +1,201 @@
+/*
+ * sph.h -- C ABI of libsph, the GB300 (sm_103a) implementation of the SPH
+ * time-step hot path of "Towards a Mini-App for Smoothed Particle
+ * Hydrodynamics at Exascale" (arXiv 1809.08013), Section 2, Algorithm 1:
+ *
+ *   1. build tree            -> Morton-sorted uniform cell lists
+ *   2. find neighbours and h -> sph_build_neighbors
+ *   3. SPH kernels           -> sph_density, sph_eos, sph_forces
+ *   5. new time step         -> sph_forces (writes dt)
+ *   6. update v, x           -> sph_step (steps 1-6, nsteps times)
+ *
+ * Step 4 (self-gravity) is not part of this library.
+ *
+ * Conventions for every call:
+ *  - Pointers in sph_particles are DEVICE pointers to float64 (or int32)
+ *    arrays of length n, owned by the caller (e.g. torch CUDA tensors), in
+ *    the caller's particle order. Scalars time and dt are device pointers to
+ *    one double each.
+ *  - `stream` is a cudaStream_t passed as a plain pointer (NULL = the legacy
+ *    default stream). All work is enqueued asynchronously on it; no call
+ *    synchronises the host except sph_sync and sph_ctx_create/destroy.
+ *  - Arguments are validated on the host before any launch: a null context
+ *    or params, n < 0, n > the context's capacity, or a null required array
+ *    returns SPH_E_INVAL and launches nothing.
+ *  - Conditions found on the device (CSR capacity exceeded, h iteration not
+ *    converged) are recorded in a device status word; sph_sync returns them.
+ *    Calls never abort or throw across the ABI.
+ *  - A context is not thread-safe; use one context per host thread/stream.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_E_INVAL = 1,     /* bad argument; nothing was launched */
+    SPH_E_NOMEM = 2,     /* device allocation failed in sph_ctx_create */
+    SPH_E_CUDA = 3,      /* a CUDA runtime call or launch failed; see sph_last_error */
+    SPH_E_CAPACITY = 4,  /* neighbour list longer than nnz_capacity: outputs of the
+                            affected step are not valid; recreate with more capacity */
+    SPH_E_HNOCONV = 5,   /* some particle's h search ended outside n_target +- n_tol;
+                            results are still computed with its last h */
+    SPH_E_TIMEOUT = 6    /* reserved for bounded device waits */
+} sph_status;
+
+/* Physical and numerical parameters (Section 4.1 workloads). */
+typedef struct {
+    int32_t eos;         /* 0 = Tait (square patch), 1 = ideal gas (Evrard) */
+    int32_t n_target;    /* target neighbour count, e.g. 100 */
+    int32_t n_tol;       /* accepted |n - n_target|, e.g. 5 */
+    int32_t max_h_iter;  /* h-search counts per particle, >= 1 */
+    int32_t periodic_z;  /* 1: minimum image along z with period lz, z kept in [-lz/2, lz/2) */
+    int32_t precision;   /* 0 = FP64 (the only value accepted by this version) */
+    double rho0, c0;     /* Tait: p = c0^2 rho0 / 7 ((rho/rho0)^7 - 1), c = c0 (rho/rho0)^3 */
+    double gamma;        /* ideal gas: p = (gamma - 1) rho u, c = sqrt(gamma (gamma - 1) u) */
+    double alpha, beta;  /* Monaghan artificial viscosity */
+    double eta2;         /* eta^2 in mu_ij = hb v.r / (r^2 + eta^2 hb^2), e.g. 0.01 */
+    double cfl;          /* dt = cfl * min h / (c + 1.2 (alpha c + beta mumax)) */
+    double lz;           /* period along z when periodic_z = 1 */
+} sph_params;
+
+/* Caller-owned particle arrays (device pointers, caller order, length n). */
+typedef struct {
+    int64_t n;
+    double *x, *y, *z;       /* position */
+    double *vx, *vy, *vz;    /* velocity */
+    double *m;               /* mass */
+    double *h;               /* smoothing length: input guess, output converged value */
+    double *u;               /* specific internal energy */
+    double *rho, *p, *c;     /* density, pressure, sound speed */
+    double *ax, *ay, *az;    /* acceleration */
+    double *du;              /* du/dt */
+    double *mumax;           /* optional (may be NULL): max_j |mu_ij| */
+    int32_t *nnb;            /* optional (may be NULL): gather neighbour count n_i */
+    double *time;            /* device scalar: simulated time, advanced by sph_step */
+    double *dt;              /* device scalar: last time step */
+} sph_particles;
+
+/* View of the context-owned neighbour list, valid until the next call that
+ * rebuilds it. Rows are in the library's internal (Morton cell) order:
+ * internal row k belongs to caller particle order[k], and every idx entry is
+ * an internal row number. Row k lists first its gather set
+ * N_k = { j : r_kj < 2 h_k } (ngather[k] entries), then the rest of the
+ * symmetric set S_k = { j : r_kj < 2 max(h_k, h_j) }. Entry order within each
+ * part is unspecified. All pointers are device pointers; *nnz_dev is the
+ * number of entries (offsets[n]). */
+typedef struct {
+    int64_t n;
+    const int64_t *offsets;  /* n + 1 */
+    const int32_t *idx;      /* offsets[n] */
+    const int32_t *ngather;  /* n */
+    const int32_t *order;    /* n: caller index of internal row k */
+    const int64_t *nnz_dev;  /* = offsets + n */
+} sph_neighbors;
+
+/* Create a context on CUDA device `device` for up to n_capacity particles and
+ * nnz_capacity neighbour-list entries (about 1.1 x 105 per particle for the
+ * 100-neighbour workloads). Allocates all scratch once; later calls allocate
+ * nothing. On failure *out is NULL. */
+sph_status sph_ctx_create(sph_ctx **out, int64_t n_capacity, int64_t nnz_capacity, int device);
+
+/* Free the context and its device memory (synchronises the device). NULL is a no-op. */
+void sph_ctx_destroy(sph_ctx *ctx);
+
+/* Algorithm 1 steps 1-2 (Section 2 and its footnote: h follows a target
+ * neighbour count). Reads x, y, z, h (and m, v, u, which it also copies into
+ * the context); sorts the particles by the Morton code of their cell; runs
+ * the bracketing h search per particle (count of N_i(h) must reach
+ * n_target +- n_tol); writes the final h (and nnb if given) back to the
+ * caller arrays and builds the symmetric neighbour list. `out` may be NULL. */
+sph_status sph_build_neighbors(sph_ctx *ctx, const sph_params *prm, sph_particles *P,
+                               sph_neighbors *out, void *stream);
+
+/* Algorithm 1 step 3, density: rho_i = m_i W(0, h_i) + sum_{j in N_i} m_j W(r_ij, h_i)
+ * with the M4 cubic spline (Table 1). Uses the neighbour list of the last
+ * sph_build_neighbors and the caller's current x, y, z, m, h; writes rho. */
+sph_status sph_density(sph_ctx *ctx, const sph_params *prm, sph_particles *P, void *stream);
+
+/* Algorithm 1 step 3, equation of state: reads rho, u; writes p, c. Elementwise. */
+sph_status sph_eos(sph_ctx *ctx, const sph_params *prm, sph_particles *P, void *stream);
+
+/* Algorithm 1 steps 3 and 5: momentum and energy equations with Monaghan
+ * artificial viscosity over S_i, and the new time step. Reads x, y, z, vx,
+ * vy, vz, m, h, rho, p, c; writes ax, ay, az, du, mumax (if given) and *dt. */
+sph_status sph_forces(sph_ctx *ctx, const sph_params *prm, sph_particles *P, void *stream);
+
+/* Algorithm 1, nsteps full iterations: neighbours and h, density, EOS,
+ * forces, dt, then the kick-drift update v += dt a, u += dt du, x += dt v
+ * (z wrapped when periodic), time += dt. State is kept in the context's
+ * sorted order between steps and written back to the caller arrays at the
+ * end, together with h, rho, p, c, a, du, mumax, nnb of the last step. */
+sph_status sph_step(sph_ctx *ctx, const sph_params *prm, sph_particles *P, int nsteps,
+                    void *stream);
+
+/* Copy the neighbour list of the last sph_build_neighbors (or last step of
+ * sph_step) into caller HOST buffers, synchronously after the stream's work:
+ * offsets (n + 1), ngather (n), order (n) and, if idx is not NULL, idx (up to
+ * idx_capacity entries; SPH_E_INVAL if offsets[n] > idx_capacity). Any of the
+ * pointers may be NULL to skip that array. Layout as in sph_neighbors. */
+sph_status sph_neighbors_to_host(sph_ctx *ctx, int64_t *offsets, int32_t *idx,
+                                 int64_t idx_capacity, int32_t *ngather, int32_t *order,
+                                 void *stream);
+
+/* Phases of sph_step timed by sph_timing_read. */
+enum {
+    SPH_PHASE_CELLS = 0,    /* load, bounding box, Morton keys, radix sort, permute, cell ranges */
+    SPH_PHASE_HSEARCH = 1,  /* h search, FP32 thresholds, per-cell max h */
+    SPH_PHASE_CSR = 2,      /* neighbour-list count, scan, fill */
+    SPH_PHASE_DENSITY = 3,  /* density with the equation of state fused */
+    SPH_PHASE_FORCES = 4,   /* momentum, energy, viscosity, dt partials and dt */
+    SPH_PHASE_UPDATE = 5,   /* kick-drift update and the final write-back */
+    SPH_NPHASES = 6
+};
+
+/* Enable (1) or disable (0) per-phase timing of sph_step with CUDA events
+ * recorded on the call's stream; enabling clears the accumulators and
+ * creates the event pool (host-side objects, up to 1024 steps per read). */
+sph_status sph_timing_enable(sph_ctx *ctx, int enable);
+
+/* Wait for the recorded events and return, per phase, the accumulated device
+ * milliseconds (ms[SPH_NPHASES]) and kernel launches (launches[SPH_NPHASES])
+ * since the last read or enable; *steps receives the number of timed steps.
+ * Any output pointer may be NULL. Clears the accumulators. */
+sph_status sph_timing_read(sph_ctx *ctx, double *ms, int64_t *launches, int64_t *steps);
+
+/* Total kernel launches issued by this context since creation. */
+int64_t sph_launch_count(const sph_ctx *ctx);
+
+/* Wait for the stream, then return and clear the device status: SPH_OK, or
+ * the most severe of SPH_E_CAPACITY and SPH_E_HNOCONV raised since the last
+ * sph_sync. */
+sph_status sph_sync(sph_ctx *ctx, void *stream);
+
+/* Number of particles whose h search did not converge since the last
+ * sph_sync (valid after sph_sync returned; reset by the next sph_sync). */
+int64_t sph_last_hnoconv(const sph_ctx *ctx);
+
+/* Text of the last error on this context ("" if none). Never NULL. */
+const char *sph_last_error(const sph_ctx *ctx);
+
+/* Measurement utility, not part of the SPH path: run a register-resident
+ * FMA-chain kernel on `stream` of `device` and return the achieved rate as
+ * *flops_per_s = 2 x FMAs per second, FP64 when fp64 != 0, else FP32. This is
+ * the denominator of the FP64 pair kernels' roofline. Synchronous. */
+sph_status sph_probe_fma_peak(int device, int fp64, void *stream, double *flops_per_s);
+
+/* Version string of the library. */
+const char *sph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

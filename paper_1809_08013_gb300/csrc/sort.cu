@@ -1,0 +1,364 @@
+// sort.cu -- Algorithm 1 step 1 ("build tree"), done as Morton-sorted cell
+// lists: bounding box and cell grid on the device, 24-bit Morton key of each
+// particle's cell, a stable LSD radix sort (3 passes of 8 bits), the
+// permutation of the particle state into sorted order, and the [start, end)
+// range of every occupied cell.
+#include <math_constants.h>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ------------------------------------------------------------------ state I/O
+__global__ void __launch_bounds__(kThreads)
+k_load_state(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+             const double* __restrict__ z, const double* __restrict__ h,
+             const double* __restrict__ vx, const double* __restrict__ vy,
+             const double* __restrict__ vz, const double* __restrict__ m,
+             const double* __restrict__ u, double4_32a* __restrict__ posh,
+             double4_32a* __restrict__ velm, double* __restrict__ ue, int32_t* __restrict__ order) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    posh[k] = make_double4_32a(x[k], y[k], z[k], h[k]);
+    velm[k] = make_double4_32a(vx ? vx[k] : 0.0, vy ? vy[k] : 0.0, vz ? vz[k] : 0.0, m ? m[k] : 0.0);
+    ue[k] = u ? u[k] : 0.0;
+    order[k] = (int32_t)k;
+}
+
+void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s) {
+    const int64_t n = P->n;
+    c->n = n;
+    if (n == 0) return;
+    const int b = c->cur;
+    c->launches += 1;
+    k_load_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        n, P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m, P->u, c->posh[b], c->velm[b],
+        c->ue[b], c->order[b]);
+}
+
+// Re-read the caller's arrays into the sorted order of the last build.
+__global__ void __launch_bounds__(kThreads)
+k_gather_state(int64_t n, int what, const int32_t* __restrict__ order,
+               const double* __restrict__ x, const double* __restrict__ y,
+               const double* __restrict__ z, const double* __restrict__ h,
+               const double* __restrict__ vx, const double* __restrict__ vy,
+               const double* __restrict__ vz, const double* __restrict__ m,
+               const double* __restrict__ rho, const double* __restrict__ p,
+               const double* __restrict__ cs, double4_32a* __restrict__ posh,
+               double4_32a* __restrict__ velm, double4_32a* __restrict__ therm) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t o = order[k];
+    posh[k] = make_double4_32a(x[o], y[o], z[o], h[o]);
+    if (what == GATHER_DENSITY) {
+        velm[k] = make_double4_32a(0.0, 0.0, 0.0, m[o]);
+    } else {
+        velm[k] = make_double4_32a(vx[o], vy[o], vz[o], m[o]);
+        const double r = rho[o];
+        therm[k] = make_double4_32a(r, p[o] / (r * r), cs[o], 1.0 / h[o]);
+    }
+}
+
+void launch_gather_state(sph_ctx* c, const sph_particles* P, int what, cudaStream_t s) {
+    const int64_t n = c->n;
+    if (n == 0) return;
+    const int b = c->cur;
+    c->launches += 1;
+    k_gather_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        n, what, c->order[b], P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m, P->rho, P->p,
+        P->c, c->posh[b], c->velm[b], c->therm);
+}
+
+// ------------------------------------------------------------ bbox and grid
+__global__ void __launch_bounds__(kThreads)
+k_bbox(int64_t n, const double4_32a* __restrict__ posh, double* __restrict__ part) {
+    double mn0 = CUDART_INF, mn1 = CUDART_INF, mn2 = CUDART_INF;
+    double mx0 = -CUDART_INF, mx1 = -CUDART_INF, mx2 = -CUDART_INF;
+    double hmx = 0.0, hs = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double4_32a p = posh[k];
+        mn0 = fmin(mn0, p.x); mx0 = fmax(mx0, p.x);
+        mn1 = fmin(mn1, p.y); mx1 = fmax(mx1, p.y);
+        mn2 = fmin(mn2, p.z); mx2 = fmax(mx2, p.z);
+        hmx = fmax(hmx, p.w);
+        hs += p.w;
+    }
+    double v[8] = {mn0, mn1, mn2, -mx0, -mx1, -mx2, -hmx, hs};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) v[q] = fmin(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+        v[7] += __shfl_xor_sync(0xffffffffu, v[7], o);
+    }
+    __shared__ double sh[kThreads / 32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < 8; ++q) sh[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int q = threadIdx.x;
+        double r = sh[0][q];
+        for (int w = 1; w < kThreads / 32; ++w) r = (q == 7) ? r + sh[w][q] : fmin(r, sh[w][q]);
+        part[blockIdx.x * 8 + q] = r;
+    }
+}
+
+__device__ __forceinline__ int grid_count(double ext, double w, double* wout) {
+    double c = floor(ext / w) + 1.0;
+    if (c > (double)kMaxCellsPerAxis) c = (double)kMaxCellsPerAxis;
+    if (c < 1.0) c = 1.0;
+    double ww = w;
+    if (c * ww <= ext) ww = ext / (c - 0.5);
+    *wout = ww;
+    return (int)c;
+}
+
+// One block: reduce the bbox partials and derive the cell grid. The cell width
+// is 2 <h> (mean smoothing length), so a typical particle's 2h sphere spans
+// 2-3 cells per axis; wider or narrower searches visit more or fewer cells.
+__global__ void __launch_bounds__(32)
+k_grid_setup(const double* __restrict__ part, int nb, int64_t n, KParams kp, int64_t cellcap,
+             Grid* __restrict__ g) {
+    __shared__ double r[8];
+    if (threadIdx.x < 8) {
+        const int q = threadIdx.x;
+        double a = (q == 7) ? 0.0 : CUDART_INF;
+        for (int b = 0; b < nb; ++b) a = (q == 7) ? a + part[b * 8 + q] : fmin(a, part[b * 8 + q]);
+        r[q] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double mn[3] = {r[0], r[1], r[2]};
+    double mx[3] = {-r[3], -r[4], -r[5]};
+    if (n == 0) {
+        for (int d = 0; d < 3; ++d) { mn[d] = 0.0; mx[d] = 0.0; }
+    }
+    const double hmean = n > 0 ? r[7] / (double)n : 1.0;
+    double w = 2.0 * hmean;
+    if (!(w > 0.0) || !isfinite(w)) w = 1.0;
+    const bool per = kp.periodic_z != 0;
+    int cnt[3];
+    double ww[3], lo[3];
+    for (int tries = 0; tries < 200; ++tries) {
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = mn[d];
+            cnt[d] = grid_count(mx[d] - mn[d], w, &ww[d]);
+        }
+        if (per) {
+            double c = floor(kp.lz / w);
+            if (c < 1.0) c = 1.0;
+            if (c > (double)kMaxCellsPerAxis) c = (double)kMaxCellsPerAxis;
+            cnt[2] = (int)c;
+            lo[2] = -0.5 * kp.lz;
+            ww[2] = kp.lz / c;
+        }
+        if ((long long)cnt[0] * cnt[1] * cnt[2] <= cellcap) break;
+        w *= 1.25;
+    }
+    double X = 0.0;
+    for (int d = 0; d < 3; ++d) X = fmax(X, fmax(fabs(mn[d]), fabs(mx[d])));
+    if (per) X = fmax(X, 0.5 * kp.lz);
+    for (int d = 0; d < 3; ++d) {
+        g->lo[d] = lo[d];
+        g->w[d] = ww[d];
+        g->inv_w[d] = 1.0 / ww[d];
+        g->n[d] = cnt[d];
+        g->lof[d] = (float)lo[d];
+        g->wf[d] = (float)ww[d];
+        g->invwf[d] = (float)(1.0 / ww[d]);
+        g->slop[d] = (float)(1e-3 * ww[d] + 1.2e-7 * X);
+    }
+    g->periodic_z = per ? 1 : 0;
+    g->lz = kp.lz;
+    g->lzf = (float)kp.lz;
+    g->halflzf = (float)(0.5 * kp.lz);
+    g->X = X;
+    g->hmean = hmean;
+    g->hmax_bits = 0ull;
+    g->ncells = (long long)cnt[0] * cnt[1] * cnt[2];
+}
+
+// ----------------------------------------------------------- Morton keys
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t compact3(uint32_t v) {
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030c30c3u;
+    v = (v | (v >> 4)) & 0x0300f00fu;
+    v = (v | (v >> 8)) & 0x030000ffu;
+    v = (v | (v >> 16)) & 0x000003ffu;
+    return v;
+}
+
+__device__ __forceinline__ int cell_coord(double v, double lo, double inv, int n) {
+    double f = floor((v - lo) * inv);
+    if (!(f >= 0.0)) return 0;  // also catches NaN
+    if (f > (double)(n - 1)) return n - 1;
+    return (int)f;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_keys(int64_t n, const double4_32a* __restrict__ posh, const Grid* __restrict__ g,
+       uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double4_32a p = posh[k];
+    const int kx = cell_coord(p.x, g->lo[0], g->inv_w[0], g->n[0]);
+    const int ky = cell_coord(p.y, g->lo[1], g->inv_w[1], g->n[1]);
+    const int kz = cell_coord(p.z, g->lo[2], g->inv_w[2], g->n[2]);
+    keys[k] = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+    vals[k] = (int32_t)k;
+}
+
+// --------------------------------------------------------- stable radix sort
+__global__ void __launch_bounds__(kThreads)
+k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
+             int nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll
+    for (int k = 0; k < kRadixItems; ++k) {
+        const int64_t i = base + k * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Each warp ranks a contiguous run of 256 keys in (iteration, lane) order, so
+// the rank of a key among equal digits follows its input position: stable.
+__global__ void __launch_bounds__(kThreads)
+k_radix_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t n,
+                int shift, const uint32_t* __restrict__ hist, int nblocks,
+                uint32_t* __restrict__ kout, int32_t* __restrict__ vout) {
+    __shared__ uint32_t cnt[kThreads / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < (kThreads / 32) * 256; q += kThreads) (&cnt[0][0])[q] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile + warp * (32 * kRadixItems);
+    uint32_t key[kRadixItems];
+    int32_t val[kRadixItems];
+    uint32_t rank[kRadixItems];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+        const int64_t i = base + it * 32 + lane;
+        const bool ok = i < n;
+        key[it] = ok ? kin[i] : 0u;
+        val[it] = ok ? vin[i] : 0;
+        const uint32_t d = ok ? ((key[it] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t b = ok ? cnt[warp][d] : 0u;
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) cnt[warp][d] = b + __popc(peers);
+        __syncwarp();
+        rank[it] = b + __popc(peers & lt);
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // one digit per thread
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const uint32_t c = cnt[w][d];
+            cnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+        const int64_t i = base + it * 32 + lane;
+        if (i < n) {
+            const uint32_t d = (key[it] >> shift) & 255u;
+            const uint32_t pos = hist[(int64_t)d * nblocks + blockIdx.x] + cnt[warp][d] + rank[it];
+            kout[pos] = key[it];
+            vout[pos] = val[it];
+        }
+    }
+}
+
+// ------------------------------------------------------ permute and cells
+__global__ void __launch_bounds__(kThreads)
+k_permute(int64_t n, const int32_t* __restrict__ perm, const double4_32a* __restrict__ posh_in,
+          const double4_32a* __restrict__ velm_in, const double* __restrict__ u_in,
+          const int32_t* __restrict__ order_in, double4_32a* __restrict__ posh_out,
+          double4_32a* __restrict__ velm_out, double* __restrict__ u_out,
+          int32_t* __restrict__ order_out, float4* __restrict__ fpos) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t o = perm[k];
+    const double4_32a p = posh_in[o];
+    posh_out[k] = p;
+    velm_out[k] = velm_in[o];
+    u_out[k] = u_in[o];
+    order_out[k] = order_in[o];
+    fpos[k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_cells_clear(const Grid* __restrict__ g, int2* __restrict__ cells,
+              unsigned long long* __restrict__ cell_hmax) {
+    const long long nc = g->ncells;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+         c += (long long)gridDim.x * blockDim.x) {
+        cells[c] = make_int2(0, 0);
+        cell_hmax[c] = 0ull;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_cells_mark(int64_t n, const uint32_t* __restrict__ keys, const Grid* __restrict__ g,
+             int2* __restrict__ cells) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t key = keys[k];
+    const bool first = (k == 0) || keys[k - 1] != key;
+    const bool last = (k == n - 1) || keys[k + 1] != key;
+    if (!(first || last)) return;
+    const int kx = compact3(key), ky = compact3(key >> 1), kz = compact3(key >> 2);
+    const long long lin = ((long long)kz * g->n[1] + ky) * g->n[0] + kx;
+    if (first) cells[lin].x = (int)k;
+    if (last) cells[lin].y = (int)(k + 1);
+}
+
+void launch_build_cells(sph_ctx* c, const KParams& kp, cudaStream_t s) {
+    const int64_t n = c->n;
+    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    c->launches += 2;
+    k_bbox<<<kReduceBlocks, kThreads, 0, s>>>(n, c->posh[c->cur], c->red_part);
+    k_grid_setup<<<1, 32, 0, s>>>(c->red_part, kReduceBlocks, n, kp, c->cellcap, c->grid);
+    if (n == 0) return;
+    c->launches += 1 + 3 * 5 + 3;
+    k_keys<<<nb, kThreads, 0, s>>>(n, c->posh[c->cur], c->grid, c->keys[0], c->vals[0]);
+    const int nsb = (int)((n + kRadixTile - 1) / kRadixTile);
+    int src = 0;
+    for (int pass = 0; pass < 3; ++pass) {
+        const int shift = 8 * pass;
+        k_radix_hist<<<nsb, kThreads, 0, s>>>(c->keys[src], n, shift, c->hist, nsb);
+        launch_scan_u32(c->hist, (int64_t)256 * nsb, c->hist_part, s);
+        k_radix_scatter<<<nsb, kThreads, 0, s>>>(c->keys[src], c->vals[src], n, shift, c->hist,
+                                                  nsb, c->keys[1 - src], c->vals[1 - src]);
+        src = 1 - src;
+    }
+    // sorted keys / permutation now in keys[src], vals[src]
+    const int a = c->cur, b = 1 - c->cur;
+    k_permute<<<nb, kThreads, 0, s>>>(n, c->vals[src], c->posh[a], c->velm[a], c->ue[a],
+                                       c->order[a], c->posh[b], c->velm[b], c->ue[b], c->order[b],
+                                       c->fpos);
+    c->cur = b;
+    k_cells_clear<<<kReduceBlocks, kThreads, 0, s>>>(c->grid, c->cells, c->cell_hmax);
+    k_cells_mark<<<nb, kThreads, 0, s>>>(n, c->keys[src], c->grid, c->cells);
+}
+
+}  // namespace sph

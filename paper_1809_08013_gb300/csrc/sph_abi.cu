@@ -1,0 +1,445 @@
+// sph_abi.cu -- the extern "C" entry points declared in include/sph.h:
+// argument checks, context allocation, and the launch sequence of each call.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "sph_internal.cuh"
+
+using namespace sph;
+
+namespace {
+
+void set_err(sph_ctx* c, const char* fmt, ...) {
+    if (!c) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+}
+
+// Switch to the context's device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+sph_status check_launch(sph_ctx* c, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_err(c, "%s: %s", where, cudaGetErrorString(e));
+        return SPH_E_CUDA;
+    }
+    return SPH_OK;
+}
+
+sph_status check_params(sph_ctx* c, const sph_params* p) {
+    if (!p) { set_err(c, "params is NULL"); return SPH_E_INVAL; }
+    if (p->eos != 0 && p->eos != 1) { set_err(c, "eos must be 0 or 1"); return SPH_E_INVAL; }
+    if (p->precision != 0) { set_err(c, "only precision 0 (FP64) is available"); return SPH_E_INVAL; }
+    if (p->max_h_iter < 1 || p->n_target < 1 || p->n_tol < 0) {
+        set_err(c, "bad h-search parameters");
+        return SPH_E_INVAL;
+    }
+    if (p->periodic_z && !(p->lz > 0.0)) { set_err(c, "periodic_z needs lz > 0"); return SPH_E_INVAL; }
+    if (!(p->cfl > 0.0)) { set_err(c, "cfl must be > 0"); return SPH_E_INVAL; }
+    return SPH_OK;
+}
+
+sph_status check_particles(sph_ctx* c, const sph_particles* P) {
+    if (!P) { set_err(c, "particles is NULL"); return SPH_E_INVAL; }
+    if (P->n < 0 || P->n > c->ncap) {
+        set_err(c, "n = %lld outside [0, capacity %lld]", (long long)P->n, (long long)c->ncap);
+        return SPH_E_INVAL;
+    }
+    return SPH_OK;
+}
+
+#define NEED(ptr)                                              \
+    do {                                                       \
+        if (!(ptr)) {                                          \
+            set_err(c, "required array " #ptr " is NULL");     \
+            return SPH_E_INVAL;                                \
+        }                                                      \
+    } while (0)
+
+template <class T>
+bool dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T)) == cudaSuccess;
+}
+
+void free_all(sph_ctx* c) {
+    void* ptrs[] = {c->posh[0], c->posh[1], c->velm[0], c->velm[1], c->ue[0], c->ue[1],
+                    c->therm, c->acc, c->pint, c->mumax, c->fpos, c->tin, c->order[0],
+                    c->order[1], c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist,
+                    c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
+                    c->offsets, c->row_part, c->idx, c->red_part, c->dt_part, c->grid,
+                    c->status, c->scratch_scalar};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->status_host) cudaFreeHost(c->status_host);
+}
+
+// Record a timing marker closing `phase` (or opening a call when phase < 0).
+void mark(sph_ctx* c, int phase, cudaStream_t s) {
+    if (!c->timing) return;
+    if (phase >= 0) c->phase_launches[phase] += c->launches - c->mark_launches;
+    c->mark_launches = c->launches;
+    if (c->ev_used >= c->ev_cap) return;  // pool full: later markers are dropped
+    if (cudaEventRecord(c->ev[c->ev_used], s) != cudaSuccess) return;
+    c->ev_phase[c->ev_used++] = phase;
+}
+
+void free_events(sph_ctx* c) {
+    if (c->ev) {
+        for (int k = 0; k < c->ev_cap; ++k) cudaEventDestroy(c->ev[k]);
+        delete[] c->ev;
+        delete[] c->ev_phase;
+    }
+    c->ev = nullptr;
+    c->ev_phase = nullptr;
+    c->ev_cap = c->ev_used = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t sph_launch_count(const sph_ctx* c) { return c ? c->launches : 0; }
+
+sph_status sph_timing_enable(sph_ctx* c, int enable) {
+    if (!c) return SPH_E_INVAL;
+    DeviceGuard dg(c->device);
+    free_events(c);
+    c->timing = 0;
+    memset(c->phase_launches, 0, sizeof(c->phase_launches));
+    c->timed_steps = 0;
+    c->mark_launches = c->launches;
+    if (!enable) return SPH_OK;
+    const int cap = 8 * 1024;
+    c->ev = new (std::nothrow) cudaEvent_t[cap];
+    c->ev_phase = new (std::nothrow) int[cap];
+    if (!c->ev || !c->ev_phase) {
+        delete[] c->ev;
+        delete[] c->ev_phase;
+        c->ev = nullptr;
+        c->ev_phase = nullptr;
+        return SPH_E_NOMEM;
+    }
+    for (int k = 0; k < cap; ++k) {
+        if (cudaEventCreate(&c->ev[k]) != cudaSuccess) {
+            c->ev_cap = k;
+            free_events(c);
+            cudaGetLastError();
+            set_err(c, "cudaEventCreate failed");
+            return SPH_E_CUDA;
+        }
+    }
+    c->ev_cap = cap;
+    c->timing = 1;
+    return SPH_OK;
+}
+
+sph_status sph_timing_read(sph_ctx* c, double* ms, int64_t* launches, int64_t* steps) {
+    if (!c) return SPH_E_INVAL;
+    DeviceGuard dg(c->device);
+    double acc[SPH_NPHASES] = {0};
+    if (c->ev_used > 0 && cudaEventSynchronize(c->ev[c->ev_used - 1]) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, "sph_timing_read: event wait failed");
+        return SPH_E_CUDA;
+    }
+    for (int k = 1; k < c->ev_used; ++k) {
+        const int ph = c->ev_phase[k];
+        if (ph < 0) continue;
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, c->ev[k - 1], c->ev[k]) == cudaSuccess) acc[ph] += t;
+        else cudaGetLastError();
+    }
+    for (int p = 0; p < SPH_NPHASES; ++p) {
+        if (ms) ms[p] = acc[p];
+        if (launches) launches[p] = c->phase_launches[p];
+    }
+    if (steps) *steps = c->timed_steps;
+    c->ev_used = 0;
+    memset(c->phase_launches, 0, sizeof(c->phase_launches));
+    c->timed_steps = 0;
+    c->mark_launches = c->launches;
+    return SPH_OK;
+}
+
+const char* sph_version(void) { return "libsph 0.1 (sm_103a, FP64)"; }
+
+const char* sph_last_error(const sph_ctx* c) { return c ? c->err : "context is NULL"; }
+
+int64_t sph_last_hnoconv(const sph_ctx* c) { return c ? c->last_hnoconv : 0; }
+
+sph_status sph_ctx_create(sph_ctx** out, int64_t ncap, int64_t nnzcap, int device) {
+    if (!out) return SPH_E_INVAL;
+    *out = nullptr;
+    if (ncap < 0 || nnzcap < 0 || ncap > (int64_t)INT32_MAX - 1 || nnzcap > ((int64_t)1 << 40))
+        return SPH_E_INVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return SPH_E_CUDA;
+    }
+    DeviceGuard dg(device);
+    if (!dg.ok) return SPH_E_CUDA;
+    sph_ctx* c = new (std::nothrow) sph_ctx;
+    if (!c) return SPH_E_NOMEM;
+    memset(c, 0, sizeof(*c));
+    c->device = device;
+    c->ncap = ncap;
+    c->nnzcap = nnzcap;
+    c->cellcap = std::min<int64_t>(std::max<int64_t>(2 * ncap, 32768),
+                                   (int64_t)kMaxCellsPerAxis * kMaxCellsPerAxis * kMaxCellsPerAxis);
+    const size_t N = (size_t)std::max<int64_t>(ncap, 1);
+    const size_t nsb = (N + kRadixTile - 1) / kRadixTile;
+    const size_t nfb = (N + kThreads - 1) / kThreads;
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+        ok = ok && dalloc(&c->posh[b], N) && dalloc(&c->velm[b], N) && dalloc(&c->ue[b], N) &&
+             dalloc(&c->order[b], N) && dalloc(&c->keys[b], N) && dalloc(&c->vals[b], N);
+    }
+    ok = ok && dalloc(&c->therm, N) && dalloc(&c->acc, N) && dalloc(&c->pint, N) &&
+         dalloc(&c->mumax, N) && dalloc(&c->fpos, N) && dalloc(&c->tin, N) &&
+         dalloc(&c->hist, 256 * nsb) && dalloc(&c->hist_part, (size_t)scan_parts(256 * nsb) + 1) &&
+         dalloc(&c->cells, (size_t)c->cellcap) && dalloc(&c->cell_hmax, (size_t)c->cellcap) &&
+         dalloc(&c->nnb, N) && dalloc(&c->ngather, N) && dalloc(&c->rowlen, N) &&
+         dalloc(&c->offsets, N + 1) && dalloc(&c->row_part, (size_t)scan_parts(N) + 1) &&
+         dalloc(&c->idx, (size_t)nnzcap) && dalloc(&c->red_part, (size_t)kReduceBlocks * 8) &&
+         dalloc(&c->dt_part, nfb) && dalloc(&c->grid, 1) && dalloc(&c->status, 2) &&
+         dalloc(&c->scratch_scalar, 2);
+    ok = ok && cudaMallocHost((void**)&c->status_host, 2 * sizeof(unsigned)) == cudaSuccess;
+    ok = ok && cudaMemset(c->status, 0, 2 * sizeof(unsigned)) == cudaSuccess &&
+         cudaMemset(c->offsets, 0, sizeof(int64_t)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return SPH_E_NOMEM;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return SPH_E_CUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+void sph_ctx_destroy(sph_ctx* c) {
+    if (!c) return;
+    DeviceGuard dg(c->device);
+    cudaDeviceSynchronize();
+    free_events(c);
+    free_all(c);
+    delete c;
+}
+
+sph_status sph_build_neighbors(sph_ctx* c, const sph_params* prm, sph_particles* P,
+                               sph_neighbors* out, void* stream) {
+    if (!c) return SPH_E_INVAL;
+    sph_status st;
+    if ((st = check_params(c, prm)) != SPH_OK || (st = check_particles(c, P)) != SPH_OK) return st;
+    if (P->n > 0) { NEED(P->x); NEED(P->y); NEED(P->z); NEED(P->h); }
+    DeviceGuard dg(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const KParams kp = kparams(prm);
+    launch_load_state(c, P, s);
+    launch_build_cells(c, kp, s);
+    launch_h_search(c, kp, s);
+    launch_csr(c, s);
+    launch_scatter(c, P, SC_H | SC_NNB, s);
+    if ((st = check_launch(c, "sph_build_neighbors")) != SPH_OK) return st;
+    if (out) {
+        out->n = c->n;
+        out->offsets = c->offsets;
+        out->idx = c->idx;
+        out->ngather = c->ngather;
+        out->order = c->order[c->cur];
+        out->nnz_dev = c->offsets + c->n;
+    }
+    return SPH_OK;
+}
+
+static sph_status need_build(sph_ctx* c, const sph_particles* P) {
+    if (P->n != c->n) {
+        set_err(c, "n = %lld differs from the last sph_build_neighbors (n = %lld)",
+                (long long)P->n, (long long)c->n);
+        return SPH_E_INVAL;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_density(sph_ctx* c, const sph_params* prm, sph_particles* P, void* stream) {
+    if (!c) return SPH_E_INVAL;
+    sph_status st;
+    if ((st = check_params(c, prm)) != SPH_OK || (st = check_particles(c, P)) != SPH_OK ||
+        (st = need_build(c, P)) != SPH_OK)
+        return st;
+    if (P->n > 0) { NEED(P->x); NEED(P->y); NEED(P->z); NEED(P->h); NEED(P->m); NEED(P->rho); }
+    DeviceGuard dg(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const KParams kp = kparams(prm);
+    launch_gather_state(c, P, GATHER_DENSITY, s);
+    launch_density(c, kp, false, s);
+    launch_scatter(c, P, SC_RHO, s);
+    return check_launch(c, "sph_density");
+}
+
+sph_status sph_eos(sph_ctx* c, const sph_params* prm, sph_particles* P, void* stream) {
+    if (!c) return SPH_E_INVAL;
+    sph_status st;
+    if ((st = check_params(c, prm)) != SPH_OK || (st = check_particles(c, P)) != SPH_OK) return st;
+    if (P->n > 0) {
+        NEED(P->rho); NEED(P->p); NEED(P->c);
+        if (prm->eos == 1) NEED(P->u);
+    }
+    DeviceGuard dg(c->device);
+    launch_eos_caller(kparams(prm), P, (cudaStream_t)stream);
+    return check_launch(c, "sph_eos");
+}
+
+sph_status sph_forces(sph_ctx* c, const sph_params* prm, sph_particles* P, void* stream) {
+    if (!c) return SPH_E_INVAL;
+    sph_status st;
+    if ((st = check_params(c, prm)) != SPH_OK || (st = check_particles(c, P)) != SPH_OK ||
+        (st = need_build(c, P)) != SPH_OK)
+        return st;
+    NEED(P->dt);
+    if (P->n > 0) {
+        NEED(P->x); NEED(P->y); NEED(P->z); NEED(P->vx); NEED(P->vy); NEED(P->vz);
+        NEED(P->m); NEED(P->h); NEED(P->rho); NEED(P->p); NEED(P->c);
+        NEED(P->ax); NEED(P->ay); NEED(P->az); NEED(P->du);
+    }
+    DeviceGuard dg(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const KParams kp = kparams(prm);
+    launch_gather_state(c, P, GATHER_FORCES, s);
+    launch_forces(c, kp, P->dt, nullptr, s);
+    launch_scatter(c, P, SC_ACC | SC_MUMAX, s);
+    return check_launch(c, "sph_forces");
+}
+
+sph_status sph_step(sph_ctx* c, const sph_params* prm, sph_particles* P, int nsteps,
+                    void* stream) {
+    if (!c) return SPH_E_INVAL;
+    sph_status st;
+    if ((st = check_params(c, prm)) != SPH_OK || (st = check_particles(c, P)) != SPH_OK) return st;
+    if (nsteps < 0) { set_err(c, "nsteps < 0"); return SPH_E_INVAL; }
+    NEED(P->dt); NEED(P->time);
+    if (P->n > 0) {
+        NEED(P->x); NEED(P->y); NEED(P->z); NEED(P->vx); NEED(P->vy); NEED(P->vz);
+        NEED(P->m); NEED(P->h); NEED(P->u); NEED(P->rho); NEED(P->p); NEED(P->c);
+        NEED(P->ax); NEED(P->ay); NEED(P->az); NEED(P->du);
+    }
+    DeviceGuard dg(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const KParams kp = kparams(prm);
+    mark(c, -1, s);
+    launch_load_state(c, P, s);
+    for (int k = 0; k < nsteps; ++k) {
+        launch_build_cells(c, kp, s);
+        mark(c, SPH_PHASE_CELLS, s);
+        launch_h_search(c, kp, s);
+        mark(c, SPH_PHASE_HSEARCH, s);
+        launch_csr(c, s);
+        mark(c, SPH_PHASE_CSR, s);
+        launch_density(c, kp, true, s);
+        mark(c, SPH_PHASE_DENSITY, s);
+        launch_forces(c, kp, P->dt, P->time, s);
+        mark(c, SPH_PHASE_FORCES, s);
+        launch_leapfrog(c, kp, P->dt, s);
+        if (k == nsteps - 1)
+            launch_scatter(c, P, SC_POS | SC_VEL | SC_H | SC_U | SC_RHO | SC_PC | SC_ACC |
+                                     SC_MUMAX | SC_NNB, s);
+        mark(c, SPH_PHASE_UPDATE, s);
+        if (c->timing) c->timed_steps += 1;
+    }
+    return check_launch(c, "sph_step");
+}
+
+sph_status sph_neighbors_to_host(sph_ctx* c, int64_t* offsets, int32_t* idx,
+                                 int64_t idx_capacity, int32_t* ngather, int32_t* order,
+                                 void* stream) {
+    if (!c) return SPH_E_INVAL;
+    DeviceGuard dg(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->n;
+    int64_t nnz = 0;
+    cudaError_t e = cudaMemcpyAsync(&nnz, c->offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && offsets)
+        e = cudaMemcpy(offsets, c->offsets, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ngather && n > 0)
+        e = cudaMemcpy(ngather, c->ngather, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && order && n > 0)
+        e = cudaMemcpy(order, c->order[c->cur], (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_err(c, "sph_neighbors_to_host: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        return SPH_E_CUDA;
+    }
+    if (idx) {
+        if (nnz > idx_capacity || nnz > c->nnzcap) {
+            set_err(c, "neighbour list has %lld entries; buffer holds %lld (context capacity %lld)",
+                    (long long)nnz, (long long)idx_capacity, (long long)c->nnzcap);
+            return SPH_E_INVAL;
+        }
+        if (nnz > 0) {
+            e = cudaMemcpy(idx, c->idx, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                set_err(c, "sph_neighbors_to_host: %s", cudaGetErrorString(e));
+                cudaGetLastError();
+                return SPH_E_CUDA;
+            }
+        }
+    }
+    return SPH_OK;
+}
+
+sph_status sph_sync(sph_ctx* c, void* stream) {
+    if (!c) return SPH_E_INVAL;
+    DeviceGuard dg(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(c->status_host, c->status, 2 * sizeof(unsigned),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_err(c, "sph_sync: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        return SPH_E_CUDA;
+    }
+    const unsigned bits = c->status_host[0];
+    c->last_hnoconv = (int64_t)c->status_host[1];
+    if (bits & ST_CAPACITY) {
+        set_err(c, "neighbour list exceeded nnz capacity %lld", (long long)c->nnzcap);
+        return SPH_E_CAPACITY;
+    }
+    if (bits & ST_HNOCONV) {
+        set_err(c, "%lld particle(s) did not reach the target neighbour count",
+                (long long)c->last_hnoconv);
+        return SPH_E_HNOCONV;
+    }
+    return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// sph_internal.cuh -- internal types and launchers of libsph (not part of the ABI).
+//
+// Data layout in HBM (internal, Morton-cell order, one entry per particle):
+//   posh[k]   = (x, y, z, h)        double4_32a, 32 B
+//   velm[k]   = (vx, vy, vz, m)     double4_32a, 32 B
+//   therm[k]  = (rho, A, c, 1/h)    double4_32a, 32 B, A = p / rho^2
+//   acc[k]    = (ax, ay, az, du)    double4_32a, 32 B
+//   ue[k], pint[k], mumax[k]        u, p and max_j |mu_ij| (double)
+//   fpos[k]   = (xf, yf, zf, Tout)  float4, 16 B: FP32 copy of the position and
+//               the upper FP32 threshold of the (2h)^2 test (see neighbors.cu)
+//   tin[k]    = Tin                 float: lower FP32 threshold
+// The j-side loads of the pair kernels therefore touch one or three 32-byte
+// sectors per neighbour instead of up to eleven scattered arrays.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+constexpr int kMortonBits = 8;                      // bits per axis -> 24-bit keys
+constexpr int kMaxCellsPerAxis = 1 << kMortonBits;  // 256
+constexpr int kThreads = 256;
+constexpr int kRadixItems = 8;                      // keys per thread in the sort
+constexpr int kRadixTile = kThreads * kRadixItems;  // 2048 keys per block
+constexpr int kScanTile = kThreads * 8;             // elements per block in scans
+constexpr int kReduceBlocks = 304;                  // 2 x 152 SMs
+
+// device status word
+enum : unsigned {
+    ST_CAPACITY = 1u,   // neighbour list exceeded nnz capacity
+    ST_HNOCONV = 2u,    // some h search did not converge
+};
+
+// Cell grid, computed on the device from the particle bounding box each build.
+struct Grid {
+    double lo[3];
+    double w[3];
+    double inv_w[3];
+    int n[3];
+    int periodic_z;
+    double lz;
+    double X;        // max |coordinate| (bounds the FP32 rounding error)
+    double hmean;
+    unsigned long long hmax_bits;  // bits of max h after the h search
+    long long ncells;
+    float lof[3], wf[3], invwf[3];
+    float lzf, halflzf;
+    float slop[3];   // absolute slack added to query boxes (FP32 rounding cover)
+};
+
+// Parameters copied by value into kernels.
+struct KParams {
+    int eos, n_target, n_tol, max_h_iter, periodic_z;
+    double rho0, c0, gamma, alpha, beta, eta2, cfl, lz;
+};
+
+inline KParams kparams(const sph_params* p) {
+    KParams k;
+    k.eos = p->eos; k.n_target = p->n_target; k.n_tol = p->n_tol;
+    k.max_h_iter = p->max_h_iter; k.periodic_z = p->periodic_z;
+    k.rho0 = p->rho0; k.c0 = p->c0; k.gamma = p->gamma; k.alpha = p->alpha;
+    k.beta = p->beta; k.eta2 = p->eta2; k.cfl = p->cfl; k.lz = p->lz;
+    return k;
+}
+
+}  // namespace sph
+
+struct sph_ctx {
+    int device;
+    int64_t ncap, nnzcap, cellcap;
+    int64_t n;              // particles of the last build
+    int cur;                // current buffer of the double-buffered state
+    double4_32a *posh[2], *velm[2];     // permuted with the particles (double-buffered)
+    double* ue[2];                  // specific internal energy u
+    double4_32a* therm;                 // recomputed every step after the sort
+    double4_32a* acc;
+    double* pint;
+    double* mumax;
+    float4* fpos;
+    float* tin;
+    int32_t* order[2];
+    uint32_t* keys[2];
+    int32_t* vals[2];
+    uint32_t* hist;         // 256 x sort blocks
+    uint32_t* hist_part;    // scan partials of hist
+    int2* cells;            // (start, end) per linear cell id
+    unsigned long long* cell_hmax;  // per cell, bits of max h (h > 0)
+    int32_t *nnb, *ngather, *rowlen;
+    int64_t* offsets;
+    int64_t* row_part;      // scan partials of the row lengths
+    int32_t* idx;
+    double* red_part;       // bbox partials: kReduceBlocks x 8
+    double* dt_part;        // per force block
+    sph::Grid* grid;
+    unsigned* status;       // [0] bits, [1] non-converged count
+    unsigned* status_host;  // pinned mirror
+    double* scratch_scalar; // [0] internal dt, [1] internal time
+    int64_t last_hnoconv;
+    // launch accounting and optional per-phase event timing
+    int64_t launches;
+    int timing;
+    cudaEvent_t* ev;        // event pool (ev_cap entries) when timing is on
+    int* ev_phase;          // phase of each recorded marker (-1 = start of a call)
+    int ev_cap, ev_used;
+    int64_t mark_launches;  // launches at the previous marker
+    int64_t phase_launches[SPH_NPHASES];
+    int64_t timed_steps;
+    char err[512];
+};
+
+namespace sph {
+
+// ---- sort.cu
+void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s);
+void launch_gather_state(sph_ctx* c, const sph_particles* P, int what, cudaStream_t s);
+void launch_build_cells(sph_ctx* c, const KParams& kp, cudaStream_t s);
+
+// ---- neighbors.cu
+void launch_h_search(sph_ctx* c, const KParams& kp, cudaStream_t s);
+void launch_csr(sph_ctx* c, cudaStream_t s);
+
+// ---- physics.cu
+enum { GATHER_DENSITY = 1, GATHER_FORCES = 2 };
+void launch_density(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s);
+void launch_eos_caller(const KParams& kp, const sph_particles* P, cudaStream_t s);
+void launch_forces(sph_ctx* c, const KParams& kp, double* dt_out, double* time_inout,
+                   cudaStream_t s);
+void launch_leapfrog(sph_ctx* c, const KParams& kp, const double* dt, cudaStream_t s);
+void launch_scatter(sph_ctx* c, const sph_particles* P, unsigned fields, cudaStream_t s);
+
+enum : unsigned {
+    SC_POS = 1u, SC_VEL = 2u, SC_H = 4u, SC_U = 8u, SC_RHO = 16u, SC_PC = 32u,
+    SC_ACC = 64u, SC_MUMAX = 128u, SC_NNB = 256u,
+};
+
+// ---- scan.cu
+// exclusive scan of n int32 into n+1 int64 (out[n] = total)
+void launch_scan_i32_i64(const int32_t* in, int64_t n, int64_t* out, int64_t* part,
+                         cudaStream_t s);
+// exclusive scan in place over n uint32
+void launch_scan_u32(uint32_t* data, int64_t n, uint32_t* part, cudaStream_t s);
+int64_t scan_parts(int64_t n);
+
+}  // namespace sph

@@ -1,0 +1,256 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same
+seeded inputs: bit-exact h and neighbour sets, FP64 fields within 1e-12
+normwise, per call and per step from identical inputs; plus edge cases.
+
+Workloads (Section 4.1): the rotating square patch at 30^3 (27,000 particles,
+one step) and 100^3 (1,000,000, the benchmark size), a ragged 17^3 patch with
+random velocities (viscosity active), a variable-h patch, and an Evrard
+sphere of 20,000 particles.
+"""
+import numpy as np
+import pytest
+
+from paper_1809_08013_gb300 import ics
+from parity_util import TOL_FP64, canon_gpu, canon_oracle, normwise, same_sets
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_08013_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _case(name):
+    if name == "patch27k":
+        return ics.square_patch(30, seed=1)
+    if name == "patch_ragged_av":
+        s, p = ics.square_patch(17, seed=5)
+        return ics.random_velocities(s, seed=6, scale=2.0), p
+    if name == "patch_varh":
+        s, p = ics.square_patch(20, seed=7)
+        s = ics.perturb_h(s, seed=8, rel=0.3)
+        return ics.random_velocities(s, seed=9, scale=1.0), p
+    if name == "evrard20k":
+        return ics.evrard(20000, seed=3)
+    raise KeyError(name)
+
+
+CASES = ["patch27k", "patch_ragged_av", "patch_varh", "evrard20k"]
+_ORC = {}
+
+
+def oracle_of(orc, name):
+    if name not in _ORC:
+        s, prm = _case(name)
+        _ORC[name] = (s, prm, orc.pipeline(prm, s), orc.h_iterate(prm, s["x"], s["y"], s["z"], s["h"])[3])
+    return _ORC[name]
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def gpu_build(B, prm, s, ctx=None):
+    ctx = ctx or B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.build_neighbors(prm, arr)
+    st = ctx.sync()
+    return ctx, arr, st
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_neighbors_bit_exact(B, orc, name):
+    s, prm, o, bad = oracle_of(orc, name)
+    ctx, arr, st = gpu_build(B, prm, s)
+    assert st == (B.SPH_E_HNOCONV if bad else B.SPH_OK)
+    assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
+    assert np.array_equal(host(arr["nnb"]), o["nnb"])
+    off, idx, ng, order = ctx.neighbors_to_host()
+    assert np.array_equal(np.sort(order), np.arange(len(order)))
+    assert off[-1] == o["off"][-1]
+    assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_density_eos_forces_from_identical_inputs(B, orc, name):
+    s, prm, o, _ = oracle_of(orc, name)
+    ctx, arr, st = gpu_build(B, prm, s)
+    ctx.density(prm, arr)
+    assert normwise(host(arr["rho"]), o["rho"]) <= TOL_FP64
+    # EOS and forces from the oracle's density, pressure and sound speed
+    arr["rho"].copy_(torch.from_numpy(o["rho"]))
+    ctx.eos(prm, arr)
+    assert normwise(host(arr["p"]), o["p"]) <= TOL_FP64
+    assert normwise(host(arr["c"]), o["c"]) <= TOL_FP64
+    arr["p"].copy_(torch.from_numpy(o["p"]))
+    arr["c"].copy_(torch.from_numpy(o["c"]))
+    ctx.forces(prm, arr)
+    assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
+    for k in ("ax", "ay", "az", "du", "mumax"):
+        ref = o[k]
+        got = host(arr[k])
+        if np.max(np.abs(ref)) == 0.0:
+            assert np.max(np.abs(got)) == 0.0, k
+        else:
+            assert normwise(got, ref) <= TOL_FP64, k
+    assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_one_step_matches_oracle(B, orc, name):
+    s, prm = _case(name)
+    st_o, ex = orc.step(prm, s, nsteps=1)
+    ctx = B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=1)
+    ctx.sync()
+    for k in ("x", "y", "z", "vx", "vy", "vz", "u"):
+        assert normwise(host(arr[k]), st_o[k]) <= TOL_FP64, k
+    assert np.array_equal(host(arr["h"]).view(np.int64), st_o["h"].view(np.int64))
+    for k in ("rho", "p", "c", "ax", "ay", "az", "du", "mumax"):
+        if np.max(np.abs(ex[k])) == 0.0:
+            assert np.max(np.abs(host(arr[k]))) == 0.0, k
+        else:
+            assert normwise(host(arr[k]), ex[k]) <= TOL_FP64, k
+    assert abs(host(arr["dt"])[0] - ex["dt"]) <= TOL_FP64 * ex["dt"]
+    assert abs(host(arr["time"])[0] - ex["time"]) <= TOL_FP64 * ex["time"]
+
+
+def test_three_steps_drift_is_small(B, orc):
+    # trajectories are reported as drift: an ulp-level position difference can
+    # flip a count at a bisection boundary, so only a loose bound is held
+    s, prm = _case("patch_ragged_av")
+    st_o, ex = orc.step(prm, s, nsteps=3)
+    ctx = B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=3)
+    ctx.sync()
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert normwise(host(arr[k]), st_o[k]) <= 1e-9, k
+    flips = int(np.count_nonzero(host(arr["h"]) != st_o["h"]))
+    assert flips <= len(s["x"]) // 100
+
+
+def test_deterministic(B):
+    s, prm = _case("patch_ragged_av")
+    outs = []
+    for _ in range(2):
+        ctx = B.Context(len(s["x"]))
+        arr = B.alloc_arrays(s)
+        ctx.step(prm, arr, nsteps=2)
+        ctx.sync()
+        outs.append({k: host(v).copy() for k, v in arr.items()})
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k].view(np.uint8), outs[1][k].view(np.uint8)), k
+
+
+def test_full_size_one_step_1m(B, orc):
+    # the benchmark workload: 100^3 rotating patch, one full step through
+    # sph_step, element by element against the oracle
+    s, prm = ics.square_patch(100, seed=2)
+    o = orc.pipeline(prm, s)
+    s1 = dict(s)
+    s1["h"] = o["h"]
+    st_o = orc.leapfrog(prm, s1, o["dt"], o["ax"], o["ay"], o["az"], o["du"])
+    ctx = B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=1)
+    assert ctx.sync() == B.SPH_OK
+    assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
+    assert np.array_equal(host(arr["nnb"]), o["nnb"])
+    off, idx, ng, order = ctx.neighbors_to_host()
+    assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
+    for k in ("rho", "p", "c", "ax", "ay", "az", "du", "mumax"):
+        assert normwise(host(arr[k]), o[k]) <= TOL_FP64, k
+    for k in ("x", "y", "z", "vx", "vy", "vz", "u"):
+        assert normwise(host(arr[k]), st_o[k]) <= TOL_FP64, k
+    assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
+
+
+# ---------------------------------------------------------------- edge cases
+def test_empty_input(B):
+    s = {k: np.zeros(0) for k in ics.FIELDS}
+    prm = ics.SphParams()
+    ctx = B.Context(16)
+    arr = B.alloc_arrays(s)
+    ctx.build_neighbors(prm, arr)
+    ctx.step(prm, arr, nsteps=1)
+    assert ctx.sync() == B.SPH_OK
+    assert np.isinf(host(arr["dt"])[0])
+    off, idx, ng, order = ctx.neighbors_to_host()
+    assert off.tolist() == [0] and len(idx) == 0
+
+
+def test_single_particle(B, orc):
+    s = {k: np.zeros(1) for k in ics.FIELDS}
+    s["m"][:] = 2.0
+    s["h"][:] = 0.1
+    prm = ics.SphParams(periodic_z=0, max_h_iter=6)
+    ctx = B.Context(1)
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=1)
+    assert ctx.sync() == B.SPH_E_HNOCONV and ctx.last_hnoconv() == 1
+    st_o, ex = orc.step(prm, s, nsteps=1)
+    assert host(arr["h"])[0] == st_o["h"][0]
+    assert host(arr["rho"])[0] == pytest.approx(ex["rho"][0], rel=1e-14)
+    assert host(arr["ax"])[0] == 0.0 and host(arr["du"])[0] == 0.0
+    assert host(arr["dt"])[0] == pytest.approx(ex["dt"], rel=1e-14)
+
+
+def test_small_target_nonperiodic(B, orc):
+    s, prm = ics.square_patch(4, seed=12)
+    prm.periodic_z = 0
+    prm.n_target, prm.n_tol = 10, 2
+    o = orc.pipeline(prm, s)
+    ctx, arr, st = gpu_build(B, prm, s)
+    assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
+    off, idx, ng, order = ctx.neighbors_to_host()
+    assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
+
+
+def test_perfect_lattice_reports_non_convergence(B, orc):
+    s, prm = ics.square_patch(12, seed=0, jitter=0.0)
+    prm.max_h_iter = 12
+    h, nnb, conv, bad = orc.h_iterate(prm, s["x"], s["y"], s["z"], s["h"])
+    ctx, arr, st = gpu_build(B, prm, s)
+    assert st == B.SPH_E_HNOCONV
+    assert ctx.last_hnoconv() == bad
+    assert np.array_equal(host(arr["h"]).view(np.int64), h.view(np.int64))
+    assert np.array_equal(host(arr["nnb"]), nnb)
+    assert ctx.sync() == B.SPH_OK  # status cleared by the previous sync
+
+
+def test_capacity_overflow_is_reported_not_fatal(B):
+    s, prm = _case("patch27k")
+    ctx = B.Context(len(s["x"]), nnz_capacity=1000)
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=1)
+    assert ctx.sync() == B.SPH_E_CAPACITY
+    # a context with room works afterwards on the same device
+    ctx2 = B.Context(len(s["x"]))
+    arr2 = B.alloc_arrays(s)
+    ctx2.step(prm, arr2, nsteps=1)
+    assert ctx2.sync() == B.SPH_OK
+
+
+def test_invalid_arguments_rejected(B):
+    s, prm = ics.square_patch(5, seed=1)
+    ctx = B.Context(10)
+    arr = B.alloc_arrays(s)  # 125 > capacity 10
+    with pytest.raises(B.SphError) as e:
+        ctx.build_neighbors(prm, arr)
+    assert e.value.status == B.SPH_E_INVAL
+    ctx = B.Context(200)
+    bad = ics.SphParams(eos=7)
+    with pytest.raises(B.SphError):
+        ctx.build_neighbors(bad, arr)
+    # density before any build of this size
+    with pytest.raises(B.SphError):
+        ctx.density(prm, arr)
