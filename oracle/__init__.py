@@ -72,6 +72,7 @@ def lib():
         L.orc_density.argtypes = [_P, C.c_int64, _D, _D, _D, _D, _D, _I64, _I32, _I32, _D]
         L.orc_eos.argtypes = [_P, C.c_int64, _D, _D, _D, _D]
         L.orc_forces.argtypes = [_P, C.c_int64] + [_D] * 11 + [_I64, _I32] + [_D] * 5
+        L.orc_forces_scale.argtypes = [_P, C.c_int64] + [_D] * 11 + [_I64, _I32] + [_D] * 3
         L.orc_dt.restype = C.c_double
         L.orc_dt.argtypes = [_P, C.c_int64, _D, _D, _D]
         L.orc_leapfrog.argtypes = [_P, C.c_int64, C.c_double] + [_D] * 11
@@ -194,6 +195,24 @@ def forces(prm, s: dict, rho, p, c, off, idx):
     return tuple(out)
 
 
+def forces_scale(prm, s: dict, rho, p, c, off, idx):
+    """Per-particle magnitudes of the summed force terms (sa, sdu, smu); see
+    orc_forces_scale."""
+    arrs = [_c64(s[k]) for k in ("x", "y", "z", "vx", "vy", "vz", "m", "h")]
+    rho, p, c = _c64(rho), _c64(p), _c64(c)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    if len(idx) == 0:
+        idx = np.zeros(1, dtype=np.int32)
+    n = len(arrs[0])
+    out = [np.empty(n) for _ in range(3)]
+    P = params(prm)
+    lib().orc_forces_scale(C.byref(P), n, *[_d(a) for a in arrs], _d(rho), _d(p), _d(c),
+                           off.ctypes.data_as(_I64), idx.ctypes.data_as(_I32),
+                           *[_d(a) for a in out])
+    return tuple(out)
+
+
 def dt(prm, h, c, mumax) -> float:
     h, c, mumax = _c64(h), _c64(c), _c64(mumax)
     P = params(prm)
@@ -242,5 +261,7 @@ def pipeline(prm, s: dict):
     rho = density(prm, s["x"], s["y"], s["z"], s["m"], h, off, idx, ng)
     p, c = eos(prm, rho, s["u"])
     ax, ay, az, du, mumax = forces(prm, s2, rho, p, c, off, idx)
+    sa, sdu, smu = forces_scale(prm, s2, rho, p, c, off, idx)
     return dict(h=h, nnb=nnb, conv=conv, off=off, idx=idx, ng=ng, rho=rho, p=p, c=c, ax=ax,
-                ay=ay, az=az, du=du, mumax=mumax, dt=dt(prm, h, c, mumax))
+                ay=ay, az=az, du=du, mumax=mumax, dt=dt(prm, h, c, mumax),
+                scale_a=sa, scale_du=sdu, scale_mu=smu)

@@ -606,6 +606,57 @@ void orc_forces(const orc_params *P, int64_t n, const double *x, const double *y
     }
 }
 
+/* Conditioning scales of the force sums, for comparing two implementations
+ * whose sums round differently: per particle the sums of the magnitudes of
+ * the terms that the definitions above add up,
+ *   sa_i  = sum_j m_j |A_i + A_j + Pi_ij| |Fbar_ij| |r_ij|
+ *   sdu_i = |A_i| sum_j m_j |Fbar_ij| |v_ij| |r_ij| + 1/2 sum_j m_j |Pi_ij Fbar_ij| |v_ij| |r_ij|
+ *   smu_i = max_j hb |v_ij| |r_ij| / (r^2 + eta2 hb^2)
+ * Rounding in v_ij . r_ij alone is bounded by a few ulps of |v_ij| |r_ij|, so
+ * a field whose exact value is zero (du and mu under rigid rotation) carries
+ * noise of order 1e-16 of these scales in any implementation. */
+void orc_forces_scale(const orc_params *P, int64_t n, const double *x, const double *y,
+                      const double *z, const double *vx, const double *vy, const double *vz,
+                      const double *m, const double *h, const double *rho, const double *p,
+                      const double *c, const int64_t *offsets, const int32_t *idx, double *sa,
+                      double *sdu, double *smu)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double Ai = p[i] / (rho[i] * rho[i]);
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+        for (int64_t e = offsets[i]; e < offsets[i + 1]; ++e) {
+            int64_t j = idx[e];
+            double d[3];
+            orc_pair(P, x, y, z, i, j, d);
+            double r2 = orc_r2(d);
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2);
+            double Fb = 0.5 * (orc_dWdr(r, h[i]) + orc_dWdr(r, h[j])) / r;
+            double wx = vx[i] - vx[j], wy = vy[i] - vy[j], wz = vz[i] - vz[j];
+            double vr = (wx * d[0] + wy * d[1]) + wz * d[2];
+            double vabs = sqrt((wx * wx + wy * wy) + wz * wz);
+            double hb = 0.5 * (h[i] + h[j]);
+            double Pi = 0.0;
+            if (vr < 0.0) {
+                double cb = 0.5 * (c[i] + c[j]);
+                double rb = 0.5 * (rho[i] + rho[j]);
+                double mu = hb * vr / (r2 + P->eta2 * hb * hb);
+                Pi = (-P->alpha * cb * mu + P->beta * mu * mu) / rb;
+            }
+            double Aj = p[j] / (rho[j] * rho[j]);
+            s1 = s1 + m[j] * fabs(Ai + Aj + Pi) * fabs(Fb) * r;
+            s2 = s2 + m[j] * fabs(Fb) * vabs * r;
+            s3 = s3 + m[j] * fabs(Pi * Fb) * vabs * r;
+            double mus = hb * vabs * r / (r2 + P->eta2 * hb * hb);
+            if (mus > s4) s4 = mus;
+        }
+        sa[i] = s1;
+        sdu[i] = fabs(Ai) * s2 + 0.5 * s3;
+        smu[i] = s4;
+    }
+}
+
 /* ---------------------------------------------------------------------------
  * New time step (Algorithm 1 step 5; reading: Monaghan's Courant form with
  * the viscous signal term, CFL factor from the workload):

@@ -19,6 +19,20 @@ def normwise(a, ref) -> float:
     return float(err / scale)
 
 
+def scaled(a, ref, scale) -> float:
+    """Normwise error against the larger of the result's magnitude and the
+    magnitude of the terms it sums (scale from the oracle's orc_forces_scale).
+    For a field whose exact value cancels to zero (du and mu under rigid
+    rotation, where v_ij . r_ij = 0 for every pair) both sides hold rounding
+    noise, and only the summed-term magnitude is a meaningful yardstick."""
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = max(float(np.max(np.abs(ref))) if ref.size else 0.0,
+              float(np.max(np.abs(scale))) if np.size(scale) else 0.0)
+    err = float(np.max(np.abs(a - ref))) if ref.size else 0.0
+    return err / den if den > 0.0 else err
+
+
 def canon_oracle(off, idx, ng):
     """Sorted (row, col, gather-flag) triples of the oracle CSR (caller ids)."""
     n = len(off) - 1

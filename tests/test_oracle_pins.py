@@ -469,3 +469,16 @@ def test_square_patch_initial_rotation():
     assert abs(np.sum(m * s["vx"])) < 1e-3 * np.sum(m * np.abs(s["vx"]))
     assert abs(m.sum() - 1000.0) < 1e-9
     assert s["x"].min() > -0.5 and s["z"].max() < 0.5
+
+
+def test_force_scales_bound_the_sums(orc):
+    # triangle inequality: each scale bounds its field; rigid rotation leaves
+    # du and mu at rounding level relative to the scale
+    s, prm, o = _conservation_case(orc, 111)
+    a = np.sqrt(o["ax"] ** 2 + o["ay"] ** 2 + o["az"] ** 2)
+    assert np.all(a <= o["scale_a"] * (1 + 1e-12))
+    assert np.all(np.abs(o["du"]) <= o["scale_du"] * (1 + 1e-12))
+    assert np.all(o["mumax"] <= o["scale_mu"] * (1 + 1e-12))
+    s2, prm2 = ics.square_patch(10, seed=112)
+    o2 = orc.pipeline(prm2, s2)
+    assert np.max(np.abs(o2["du"])) <= 1e-14 * np.max(o2["scale_du"])
