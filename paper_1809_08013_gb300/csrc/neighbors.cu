@@ -78,35 +78,38 @@ __device__ __forceinline__ double exact_r2(const double4_32a& a, const double4_3
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// Cell index range overlapping [v - R, v + R] along one axis (clamped), or,
-// for the periodic z axis, a possibly wrapped range.
-__device__ __forceinline__ void axis_range(float v, float R, const Grid* __restrict__ g, int d,
-                                           int& k0, int& k1) {
-    const float lo = g->lof[d], inv = g->invwf[d], s = g->slop[d];
-    const int n = g->n[d];
-    float a = floorf((v - R - s - lo) * inv);
-    float b = floorf((v + R + s - lo) * inv);
-    if (d == 2 && g->periodic_z) {
-        a = floorf((v - R - s + g->halflzf) * inv);
-        b = floorf((v + R + s + g->halflzf) * inv);
-        if (!(b - a + 1.0f < (float)n)) {
-            k0 = 0;
-            k1 = n - 1;
-            return;
-        }
-        k0 = (int)a;
-        k1 = (int)b;
-        return;
-    }
-    a = fminf(fmaxf(a, 0.0f), (float)n);
-    b = fmaxf(fminf(b, (float)(n - 1)), -1.0f);
-    k0 = (int)a;
-    k1 = (int)b;
-}
-
 __device__ __forceinline__ int wrapi(int k, int n) {
     int r = k % n;
     return r < 0 ? r + n : r;
+}
+
+// Cell index range overlapping [a, b] along axis d (clamped); along the
+// periodic z axis the range may be unclamped (wrapped by the caller) or the
+// whole axis (*all = true).
+__device__ __forceinline__ void box_range(float a, float b, const Grid* __restrict__ g, int d,
+                                          int& k0, int& k1, bool& all) {
+    const float lo = g->lof[d], inv = g->invwf[d], s = g->slop[d];
+    const int n = g->n[d];
+    all = false;
+    if (d == 2 && g->periodic_z) {
+        const float fa = floorf((a - s + g->halflzf) * inv);
+        const float fb = floorf((b + s + g->halflzf) * inv);
+        if (!(fb - fa + 1.0f < (float)n)) {
+            k0 = 0;
+            k1 = n - 1;
+            all = true;
+            return;
+        }
+        k0 = (int)fa;
+        k1 = (int)fb;
+        return;
+    }
+    float fa = floorf((a - s - lo) * inv);
+    float fb = floorf((b + s - lo) * inv);
+    fa = fminf(fmaxf(fa, 0.0f), (float)n);
+    fb = fmaxf(fminf(fb, (float)(n - 1)), -1.0f);
+    k0 = (int)fa;
+    k1 = (int)fb;
 }
 
 // Distance from v to the slab of cell k along axis d (0 inside), inflated by slop.
@@ -116,15 +119,41 @@ __device__ __forceinline__ float axis_gap(float v, int k, const Grid* __restrict
     return fmaxf(0.0f, fmaxf(a - v, v - b));
 }
 
-// Visit every non-empty cell overlapping the box of half-width R around fi.
-// f(cell, kx, ky, kz_unwrapped, start, end); return value ignored.
-template <class F>
-__device__ __forceinline__ void for_cells(const Grid* __restrict__ g, const int2* __restrict__ cells,
-                                          const float4& fi, float R, F&& f) {
+__device__ __forceinline__ float wmin(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float wmax(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Warp-cooperative candidate walk. The 32 lanes of a warp query the union of
+// their boxes [q - R, q + R] (inactive lanes contribute nothing); cells are
+// visited in warp-uniform loops, each cell's particles are staged 32 at a
+// time in shared memory, and every lane sees every staged candidate:
+//   keep(cell, kx, ky, kz) -> bool  per-lane wish to visit a cell (any lane
+//                                    wanting it makes the warp visit it)
+//   visit(j, fj, tinj)               per lane, per staged candidate
+// All 32 lanes must call this together.
+template <class Keep, class Visit>
+__device__ __forceinline__ void warp_walk(const Grid* __restrict__ g, const int2* __restrict__ cells,
+                                          const float4* __restrict__ fpos,
+                                          const float* __restrict__ tin, float4* s_f, float* s_t,
+                                          const float4& q, float R, bool active, Keep&& keep,
+                                          Visit&& visit) {
+    const int lane = threadIdx.x & 31;
+    const float lx = wmin(active ? q.x - R : CUDART_INF_F), hx = wmax(active ? q.x + R : -CUDART_INF_F);
+    if (!(lx <= hx)) return;  // no active lane
+    const float ly = wmin(active ? q.y - R : CUDART_INF_F), hy = wmax(active ? q.y + R : -CUDART_INF_F);
+    const float lz = wmin(active ? q.z - R : CUDART_INF_F), hz = wmax(active ? q.z + R : -CUDART_INF_F);
     int x0, x1, y0, y1, z0, z1;
-    axis_range(fi.x, R, g, 0, x0, x1);
-    axis_range(fi.y, R, g, 1, y0, y1);
-    axis_range(fi.z, R, g, 2, z0, z1);
+    bool ax, ay, az;
+    box_range(lx, hx, g, 0, x0, x1, ax);
+    box_range(ly, hy, g, 1, y0, y1, ay);
+    box_range(lz, hz, g, 2, z0, z1, az);
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
     const bool per = g->periodic_z != 0;
     for (int kz = z0; kz <= z1; ++kz) {
@@ -133,53 +162,78 @@ __device__ __forceinline__ void for_cells(const Grid* __restrict__ g, const int2
             const long long row = ((long long)cz * ny + ky) * nx;
             for (int kx = x0; kx <= x1; ++kx) {
                 const int2 se = __ldg(&cells[row + kx]);
-                if (se.y > se.x) f(row + kx, kx, ky, kz, se.x, se.y);
+                if (se.y <= se.x) continue;
+                if (!__any_sync(0xffffffffu, active && keep(row + kx, kx, ky, kz))) continue;
+                for (int base = se.x; base < se.y; base += 32) {
+                    const int j = base + lane;
+                    if (j < se.y) {
+                        s_f[lane] = __ldg(&fpos[j]);
+                        if (tin) s_t[lane] = __ldg(&tin[j]);
+                    }
+                    __syncwarp();
+                    const int cnt = min(32, se.y - base);
+                    for (int k = 0; k < cnt; ++k) visit(base + k, s_f[k], tin ? s_t[k] : 0.0f);
+                    __syncwarp();
+                }
             }
         }
     }
 }
 
 // ------------------------------------------------------------ h search
+// One warp per 32 consecutive particles. Each pass counts |N_i(h)| for every
+// still-searching lane; the warp repeats passes until all lanes are done.
 __global__ void __launch_bounds__(kThreads)
 k_h_iterate(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
             const float4* __restrict__ fpos, const int2* __restrict__ cells,
             int32_t* __restrict__ nnb, unsigned* __restrict__ status) {
+    __shared__ float4 s_f[kThreads / 32][32];
+    const int warp = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double4_32a pi = posh[i];
-    const float4 fi = fpos[i];
+    const bool valid = i < n;
+    double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
+    float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        pi = posh[i];
+        fi = fpos[i];
+    }
     double h = pi.w, lo = 0.0, hi = CUDART_INF;
     const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
-    int cnt = 0;
-    bool conv = false;
-    for (int it = 0; it < kp.max_h_iter; ++it) {
+    int cnt = 0, it = 0;
+    bool active = valid && kp.max_h_iter > 0, conv = false;
+    while (__any_sync(0xffffffffu, active)) {
         const Thr t = thresholds(h, g);
         const float R = (float)(2.0 * h) * 1.0001f;
-        cnt = 0;
-        for_cells(g, cells, fi, R, [&](long long, int, int, int, int s, int e) {
-            for (int j = s; j < e; ++j) {
-                const float4 fj = __ldg(&fpos[j]);
+        int c = 0;
+        warp_walk(
+            g, cells, fpos, nullptr, s_f[warp], nullptr, fi, R, active,
+            [&](long long, int, int, int) { return true; },
+            [&](int j, const float4& fj, float) {
                 const float r2f = f_r2(fi, fj, g);
                 if (r2f < t.tin) {
-                    cnt += (j != i);
-                } else if (r2f <= t.tout && j != i) {
-                    cnt += exact_r2(pi, posh[j], g) < t.r2;
+                    c += (j != i);
+                } else if (r2f <= t.tout && j != i && active) {
+                    c += exact_r2(pi, posh[j], g) < t.r2;
                 }
+            });
+        if (active) {
+            cnt = c;
+            ++it;
+            if (cnt >= lowb && cnt <= highb) {
+                conv = true;
+                active = false;
+            } else if (it >= kp.max_h_iter) {
+                active = false;
+            } else if (cnt < lowb) {
+                lo = h;
+                h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+            } else {
+                hi = h;
+                h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
             }
-        });
-        if (cnt >= lowb && cnt <= highb) {
-            conv = true;
-            break;
-        }
-        if (it == kp.max_h_iter - 1) break;
-        if (cnt < lowb) {
-            lo = h;
-            h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
-        } else {
-            hi = h;
-            h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
         }
     }
+    if (!valid) return;
     posh[i].w = h;
     nnb[i] = cnt;
     if (!conv) {
@@ -229,6 +283,8 @@ k_cell_hmax(const Grid* __restrict__ gc, Grid* gw, const int2* __restrict__ cell
 // FILL = false: rowlen[i] = |S_i|, ngather[i] = |N_i|.
 // FILL = true : write row i at offsets[i] (N_i first); rows are skipped when
 //               the total exceeds the capacity (status bit raised).
+// One warp per 32 consecutive particles; a cell is visited when some lane
+// can reach it: its box lies within 2 max(h_i, max h of the cell).
 template <bool FILL>
 __global__ void __launch_bounds__(kThreads)
 k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ posh,
@@ -237,40 +293,50 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
       int32_t* __restrict__ rowlen, int32_t* __restrict__ ngather,
       const int64_t* __restrict__ offsets, int32_t* __restrict__ idx, int64_t nnzcap,
       unsigned* __restrict__ status) {
+    __shared__ float4 s_f[kThreads / 32][32];
+    __shared__ float s_t[kThreads / 32][32];
+    const int warp = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (FILL) {
         const int64_t tot = offsets[n];
         if (tot > nnzcap) {
             if (i == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
-            return;
+            return;  // whole grid returns: no warp-collective call is left waiting
         }
     }
-    if (i >= n) return;
-    const double4_32a pi = posh[i];
-    const float4 fi = fpos[i];
-    const float tin_i = tin[i];
+    const bool valid = i < n;
+    double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
+    float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
+    float tin_i = -1.0f;
+    if (valid) {
+        pi = posh[i];
+        fi = fpos[i];
+        tin_i = tin[i];
+    }
     const double r2i = thresholds(pi.w, g).r2;
     const double hmaxg = __longlong_as_double((long long)g->hmax_bits);
     const float Rbig = (float)(2.0 * fmax(pi.w, hmaxg)) * 1.0001f;
     int64_t pg = 0, po = 0, pg_end = 0, po_end = 0;
-    if (FILL) {
+    if (FILL && valid) {
         pg = offsets[i];
         pg_end = po = pg + ngather[i];
         po_end = offsets[i + 1];
     }
     int cg = 0, co = 0;
     const bool per = g->periodic_z != 0;
-    for_cells(g, cells, fi, Rbig, [&](long long cell, int kx, int ky, int kz, int s, int e) {
-        const double hc = __longlong_as_double((long long)__ldg(&cell_hmax[cell]));
-        const float reach = (float)(2.0 * fmax(pi.w, hc)) * 1.0001f;
-        const float gx = axis_gap(fi.x, kx, g, 0), gy = axis_gap(fi.y, ky, g, 1);
-        const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
-        if (fmaf(gz, gz, fmaf(gy, gy, gx * gx)) >= reach * reach) return;
-        for (int j = s; j < e; ++j) {
-            if (j == i) continue;
-            const float4 fj = __ldg(&fpos[j]);
+    warp_walk(
+        g, cells, fpos, tin, s_f[warp], s_t[warp], fi, Rbig, valid,
+        [&](long long cell, int kx, int ky, int kz) {
+            const double hc = __longlong_as_double((long long)__ldg(&cell_hmax[cell]));
+            const float reach = (float)(2.0 * fmax(pi.w, hc)) * 1.0001f;
+            const float gx = axis_gap(fi.x, kx, g, 0), gy = axis_gap(fi.y, ky, g, 1);
+            const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
+            return fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < reach * reach;
+        },
+        [&](int j, const float4& fj, float tinj) {
+            if (!valid || j == i) return;
             const float r2f = f_r2(fi, fj, g);
-            bool in_i, in_j = false, have = false;
+            bool in_i, have = false;
             double er2 = 0.0;
             if (r2f < tin_i) {
                 in_i = true;
@@ -281,28 +347,27 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
                 have = true;
                 in_i = er2 < r2i;
             }
-            if (!in_i) {
-                if (r2f > fj.w) continue;
-                if (r2f < __ldg(&tin[j])) {
-                    in_j = true;
-                } else {
-                    const double4_32a pj = posh[j];
-                    if (!have) er2 = exact_r2(pi, pj, g);
-                    const double Rj = 2.0 * pj.w;
-                    in_j = er2 < __dmul_rn(Rj, Rj);
-                }
-                if (!in_j) continue;
-            }
             if (in_i) {
                 if (FILL && pg < pg_end) idx[pg++] = j;
                 ++cg;
+                return;
+            }
+            if (r2f > fj.w) return;
+            bool in_j;
+            if (r2f < tinj) {
+                in_j = true;
             } else {
+                const double4_32a pj = posh[j];
+                if (!have) er2 = exact_r2(pi, pj, g);
+                const double Rj = 2.0 * pj.w;
+                in_j = er2 < __dmul_rn(Rj, Rj);
+            }
+            if (in_j) {
                 if (FILL && po < po_end) idx[po++] = j;
                 ++co;
             }
-        }
-    });
-    if (!FILL) {
+        });
+    if (!FILL && valid) {
         rowlen[i] = cg + co;
         ngather[i] = cg;
     }

@@ -15,16 +15,65 @@ namespace sph {
 
 constexpr double kInvPi = 0.31830988618379067154;
 
-__device__ __forceinline__ void pair_vec(const double4_32a& a, const double4_32a& b, const KParams& kp,
-                                         double& dx, double& dy, double& dz) {
-    dx = a.x - b.x;
-    dy = a.y - b.y;
-    dz = a.z - b.z;
-    if (kp.periodic_z) {
-        const double half = 0.5 * kp.lz;
-        if (dz > half) dz -= kp.lz;
-        else if (dz < -half) dz += kp.lz;
-    }
+// ---- FP64-pipe economy helpers. GB300 issues FP64 arithmetic at 1/64 of
+// the FP32 rate, so compares, selects, sign tests and clamps are done with
+// integer operations on the IEEE bit patterns (which order non-negative
+// doubles like their values), and divisions / square roots start from the
+// hardware approximations refined by Newton-Raphson.
+__device__ __forceinline__ long long bits(double v) { return __double_as_longlong(v); }
+
+// 1/sqrt(x), x > 0 normal: rsqrt.approx.f64 seed, two Newton-Raphson steps
+// y <- y (3/2 - x/2 y^2) (quadratic convergence; a few ulp in the end).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double hx = 0.5 * x;
+    y = y * fma(-hx, y * y, 1.5);
+    y = y * fma(-hx, y * y, 1.5);
+    return y;
+}
+
+// 1/d, d > 0 normal: rcp.approx.ftz.f64 seed, two Newton-Raphson steps
+// y <- y + y (1 - d y).
+__device__ __forceinline__ double rcp_nr(double d) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+    double e = fma(-d, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-d, y, 1.0);
+    y = fma(y, e, y);
+    return y;
+}
+
+// Minimum image along z: |dz| > lz/2 (integer compare of |dz|'s bits) shifts
+// dz by -sign(dz) lz, the same two-sided rule as the definition.
+__device__ __forceinline__ double wrap_z(double dz, long long half_bits, double lz) {
+    if ((bits(dz) & 0x7fffffffffffffffLL) > half_bits) dz -= copysign(lz, dz);
+    return dz;
+}
+
+constexpr long long kOneBits = 0x3ff0000000000000LL;  // bits of 1.0
+constexpr long long kTwoBits = 0x4000000000000000LL;  // bits of 2.0
+
+// Cubic-spline shape g(q) = pi h^3 W: 1 - 1.5 q^2 + 0.75 q^3 (q < 1),
+// (2 - q)^3 / 4 (1 <= q < 2), 0 beyond; q >= 0.
+__device__ __forceinline__ double w_shape(double q) {
+    const double q2 = q * q;
+    const double win = fma(q2, fma(0.75, q, -1.5), 1.0);
+    const double t = 2.0 - q;
+    const double wout = (0.25 * t) * (t * t);
+    const long long qb = bits(q);
+    return qb < kOneBits ? win : (qb < kTwoBits ? wout : 0.0);
+}
+
+// Derivative shape f(q) = pi h^4 dW/dr: q (2.25 q - 3) (q < 1),
+// -0.75 (2 - q)^2 (1 <= q < 2), 0 beyond; q >= 0.
+__device__ __forceinline__ double dw_shape(double q) {
+    const double fin = q * fma(2.25, q, -3.0);
+    const double t = 2.0 - q;
+    const double fout = (-0.75 * t) * t;
+    const long long qb = bits(q);
+    return qb < kOneBits ? fin : (qb < kTwoBits ? fout : 0.0);
 }
 
 __device__ __forceinline__ void eos(const KParams& kp, double rho, double u, double& p, double& c) {
@@ -43,39 +92,46 @@ __device__ __forceinline__ void eos(const KParams& kp, double rho, double u, dou
 
 // ------------------------------------------------------------ density
 // rho_i = m_i W(0, h_i) + sum_{j in N_i} m_j W(r_ij, h_i). With FUSE the EOS
-// follows in the same thread and therm[i] = (rho, p/rho^2, c, 1/h) is written.
+// follows in the same thread and the pair kernels' per-particle packs are
+// written: therm = (rho/2, p/rho^2, alpha c/2, h/2), kern = (1/h, 1/h^4).
 template <bool FUSE>
 __global__ void __launch_bounds__(kThreads)
 k_density(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
           const double4_32a* __restrict__ velm, const double* __restrict__ ue,
           const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
           const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
-          double* __restrict__ pint) {
+          double2* __restrict__ kern, double* __restrict__ pint, double* __restrict__ cint) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || offsets[n] > nnzcap) return;
     const double4_32a pi = posh[i];
     const double hinv = 1.0 / pi.w;
+    const long long half_bits = bits(0.5 * kp.lz);
     double acc = 0.0;
     const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
     for (int64_t e = e0; e < e1; ++e) {
         const int j = __ldg(&idx[e]);
         const double4_32a pj = posh[j];
         const double mj = velm[j].w;
-        double dx, dy, dz;
-        pair_vec(pi, pj, kp, dx, dy, dz);
-        const double q = sqrt(dx * dx + dy * dy + dz * dz) * hinv;
-        const double t = fmax(2.0 - q, 0.0), s = fmax(1.0 - q, 0.0);
-        acc += mj * (0.25 * t * t * t - s * s * s);
+        const double dx = pi.x - pj.x, dy = pi.y - pj.y;
+        double dz = pi.z - pj.z;
+        if (kp.periodic_z) dz = wrap_z(dz, half_bits, kp.lz);
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        // r2 > 0 for j != i unless two particles coincide; r = r2 / sqrt(r2)
+        const double q = bits(r2) > 0 ? r2 * rsqrt_nr(r2) * hinv : 0.0;
+        acc = fma(mj, w_shape(q), acc);
     }
     const double sigma = hinv * hinv * hinv * kInvPi;
     const double rho = (velm[i].w + acc) * sigma;
     if (FUSE) {
         double p, c;
         eos(kp, rho, ue[i], p, c);
-        therm[i] = make_double4_32a(rho, p / (rho * rho), c, hinv);
+        therm[i] = make_double4_32a(0.5 * rho, p / (rho * rho), 0.5 * kp.alpha * c, 0.5 * pi.w);
+        const double h2 = hinv * hinv;
+        kern[i] = make_double2(hinv, h2 * h2);
         pint[i] = p;
+        cint[i] = c;
     } else {
-        therm[i].x = rho;
+        therm[i].x = 0.5 * rho;
     }
 }
 
@@ -88,11 +144,11 @@ void launch_density(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s
     if (fuse_eos)
         k_density<true><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->ue[b],
                                                 c->offsets, c->ngather, c->idx, c->nnzcap,
-                                                c->therm, c->pint);
+                                                c->therm, c->kern, c->pint, c->cint);
     else
         k_density<false><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->ue[b],
                                                  c->offsets, c->ngather, c->idx, c->nnzcap,
-                                                 c->therm, c->pint);
+                                                 c->therm, c->kern, c->pint, c->cint);
 }
 
 // ------------------------------------------------------------ EOS (caller arrays)
@@ -120,61 +176,70 @@ void launch_eos_caller(const KParams& kp, const sph_particles* P, cudaStream_t s
 //   a_i  = -sum m_j (A_i + A_j + Pi) Fbar r_ij
 //   du_i = A_i sum m_j Fbar v.r + 1/2 sum m_j Pi Fbar v.r
 // and the time-step candidate h_i / (c_i + 1.2 (alpha c_i + beta mumax_i)).
+// Algebra used: Fbar = (0.5/pi) (f(q_i)/h_i^4 + f(q_j)/h_j^4) / r with the
+// shape f above; both divisions of the viscosity share one reciprocal,
+// R = 1 / ((r^2 + eta2 hb^2) rhob): mu = hb v.r rhob R and 1/rhob = (r^2 +
+// eta2 hb^2) R; Pi = mu (beta mu - alpha cb) / rhob.
 __global__ void __launch_bounds__(kThreads)
-k_forces(int64_t n, KParams kp, const double4_32a* __restrict__ posh, const double4_32a* __restrict__ velm,
-         const double4_32a* __restrict__ therm, const int64_t* __restrict__ offsets,
-         const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ acc,
-         double* __restrict__ mumax, double* __restrict__ dt_part) {
+k_forces(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+         const double4_32a* __restrict__ velm, const double4_32a* __restrict__ therm,
+         const double2* __restrict__ kern, const double* __restrict__ cint,
+         const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
+         double4_32a* __restrict__ acc, double* __restrict__ mumax, double* __restrict__ dt_part) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dtc = CUDART_INF;
     if (i < n && offsets[n] <= nnzcap) {
         const double4_32a pi = posh[i];
         const double4_32a vi = velm[i];
         const double4_32a ti = therm[i];
-        const double hi2 = ti.w * ti.w;
-        const double Ki = hi2 * hi2;
-        double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0, sv = 0.0, mum = 0.0;
+        const double2 ki = kern[i];
+        const long long half_bits = bits(0.5 * kp.lz);
+        const double eta2 = kp.eta2, beta = kp.beta;
+        double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0, sv = 0.0;
+        long long mum = 0;  // bits of max |mu| (non-negative doubles order as integers)
         const int64_t e0 = offsets[i], e1 = offsets[i + 1];
         for (int64_t e = e0; e < e1; ++e) {
             const int j = __ldg(&idx[e]);
             const double4_32a pj = posh[j];
             const double4_32a vj = velm[j];
             const double4_32a tj = therm[j];
-            double dx, dy, dz;
-            pair_vec(pi, pj, kp, dx, dy, dz);
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 == 0.0) continue;
-            const double rinv = rsqrt(r2);
+            const double2 kj = __ldg(&kern[j]);
+            const double dx = pi.x - pj.x, dy = pi.y - pj.y;
+            double dz = pi.z - pj.z;
+            if (kp.periodic_z) dz = wrap_z(dz, half_bits, kp.lz);
+            const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            if (bits(r2) == 0) continue;  // coincident particles exert no force
+            const double rinv = rsqrt_nr(r2);
             const double r = r2 * rinv;
-            const double qi = r * ti.w, qj = r * tj.w;
-            const double ta = fmax(2.0 - qi, 0.0), sa = fmax(1.0 - qi, 0.0);
-            const double tb = fmax(2.0 - qj, 0.0), sb = fmax(1.0 - qj, 0.0);
-            const double fa = 3.0 * sa * sa - 0.75 * ta * ta;
-            const double fb = 3.0 * sb * sb - 0.75 * tb * tb;
-            const double hj2 = tj.w * tj.w;
-            const double Fb = (Ki * fa + (hj2 * hj2) * fb) * (0.5 * kInvPi) * rinv;
+            const double fa = dw_shape(r * ki.x), fb = dw_shape(r * kj.x);
+            const double Fb = fma(ki.y, fa, kj.y * fb) * ((0.5 * kInvPi) * rinv);
             const double wx = vi.x - vj.x, wy = vi.y - vj.y, wz = vi.z - vj.z;
-            const double vr = wx * dx + wy * dy + wz * dz;
-            double Pi = 0.0, mu = 0.0;
-            if (vr < 0.0) {
-                const double hb = 0.5 * (pi.w + pj.w);
-                const double cb = 0.5 * (ti.z + tj.z);
-                const double rb = 0.5 * (ti.x + tj.x);
-                mu = hb * vr / (r2 + kp.eta2 * hb * hb);
-                Pi = (-kp.alpha * cb * mu + kp.beta * mu * mu) / rb;
+            const double vr = fma(wz, dz, fma(wy, dy, wx * dx));
+            double Pi = 0.0;
+            if (__double2hiint(vr) < 0) {  // v.r < 0 (a -0 gives mu = Pi = 0 as well)
+                const double hb = ti.w + tj.w;
+                const double d1 = fma(eta2 * hb, hb, r2);
+                const double rb = ti.x + tj.x;
+                const double R = rcp_nr(d1 * rb);
+                const double mu = ((hb * vr) * rb) * R;
+                Pi = (mu * fma(beta, mu, -(ti.z + tj.z))) * (d1 * R);
+                const long long ab = bits(mu) & 0x7fffffffffffffffLL;
+                mum = ab > mum ? ab : mum;
             }
-            const double g = vj.w * (ti.y + tj.y + Pi) * Fb;
-            sx += g * dx;
-            sy += g * dy;
-            sz += g * dz;
-            const double mFv = vj.w * Fb * vr;
+            const double mF = vj.w * Fb;
+            const double g = mF * ((ti.y + tj.y) + Pi);
+            sx = fma(g, dx, sx);
+            sy = fma(g, dy, sy);
+            sz = fma(g, dz, sz);
+            const double mFv = mF * vr;
             sp += mFv;
-            sv += mFv * Pi;
-            mum = fmax(mum, fabs(mu));
+            sv = fma(mFv, Pi, sv);
         }
-        acc[i] = make_double4_32a(-sx, -sy, -sz, ti.y * sp + 0.5 * sv);
-        mumax[i] = mum;
-        dtc = pi.w / (ti.z + 1.2 * (kp.alpha * ti.z + kp.beta * mum));
+        const double mu_max = __longlong_as_double(mum);
+        acc[i] = make_double4_32a(-sx, -sy, -sz, fma(ti.y, sp, 0.5 * sv));
+        mumax[i] = mu_max;
+        const double ci = cint[i];
+        dtc = pi.w / (ci + 1.2 * (kp.alpha * ci + kp.beta * mu_max));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
@@ -215,8 +280,9 @@ void launch_forces(sph_ctx* c, const KParams& kp, double* dt_out, double* time_i
     const int b = c->cur;
     c->launches += (n > 0) ? 2 : 1;
     if (n > 0)
-        k_forces<<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->therm, c->offsets,
-                                         c->idx, c->nnzcap, c->acc, c->mumax, c->dt_part);
+        k_forces<<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->therm, c->kern,
+                                         c->cint, c->offsets, c->idx, c->nnzcap, c->acc,
+                                         c->mumax, c->dt_part);
     k_dt_finish<<<1, kThreads, 0, s>>>(c->dt_part, n > 0 ? (int)nb : 0, kp.cfl, dt_out,
                                        time_inout);
 }
@@ -262,7 +328,7 @@ void launch_leapfrog(sph_ctx* c, const KParams& kp, const double* dt, cudaStream
 struct ScatterSrc {
     const int32_t* order;
     const double4_32a *posh, *velm, *therm, *acc;
-    const double *ue, *pint, *mumax;
+    const double *ue, *pint, *cint, *mumax;
     const int32_t* nnb;
 };
 
@@ -281,10 +347,10 @@ k_scatter(int64_t n, unsigned f, ScatterSrc S, sph_particles P) {
         P.vx[o] = v.x; P.vy[o] = v.y; P.vz[o] = v.z;
     }
     if (f & SC_U) P.u[o] = S.ue[k];
-    if (f & (SC_RHO | SC_PC)) {
-        const double4_32a t = S.therm[k];
-        if (f & SC_RHO) P.rho[o] = t.x;
-        if (f & SC_PC) { P.p[o] = S.pint[k]; P.c[o] = t.z; }
+    if (f & SC_RHO) P.rho[o] = 2.0 * S.therm[k].x;
+    if (f & SC_PC) {
+        P.p[o] = S.pint[k];
+        P.c[o] = S.cint[k];
     }
     if (f & SC_ACC) {
         const double4_32a a = S.acc[k];
@@ -300,7 +366,7 @@ void launch_scatter(sph_ctx* c, const sph_particles* P, unsigned fields, cudaStr
     const int b = c->cur;
     c->launches += 1;
     ScatterSrc S{c->order[b], c->posh[b], c->velm[b], c->therm, c->acc, c->ue[b], c->pint,
-                 c->mumax, c->nnb};
+                 c->cint, c->mumax, c->nnb};
     k_scatter<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(n, fields, S, *P);
 }
 

@@ -36,37 +36,45 @@ void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s) {
         c->ue[b], c->order[b]);
 }
 
-// Re-read the caller's arrays into the sorted order of the last build.
+// Re-read the caller's arrays into the sorted order of the last build and
+// derive the per-particle quantities the pair kernels load for j.
 __global__ void __launch_bounds__(kThreads)
-k_gather_state(int64_t n, int what, const int32_t* __restrict__ order,
+k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ order,
                const double* __restrict__ x, const double* __restrict__ y,
                const double* __restrict__ z, const double* __restrict__ h,
                const double* __restrict__ vx, const double* __restrict__ vy,
                const double* __restrict__ vz, const double* __restrict__ m,
                const double* __restrict__ rho, const double* __restrict__ p,
                const double* __restrict__ cs, double4_32a* __restrict__ posh,
-               double4_32a* __restrict__ velm, double4_32a* __restrict__ therm) {
+               double4_32a* __restrict__ velm, double4_32a* __restrict__ therm,
+               double2* __restrict__ kern, double* __restrict__ cint) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t o = order[k];
-    posh[k] = make_double4_32a(x[o], y[o], z[o], h[o]);
+    const double hh = h[o];
+    posh[k] = make_double4_32a(x[o], y[o], z[o], hh);
     if (what == GATHER_DENSITY) {
         velm[k] = make_double4_32a(0.0, 0.0, 0.0, m[o]);
     } else {
         velm[k] = make_double4_32a(vx[o], vy[o], vz[o], m[o]);
-        const double r = rho[o];
-        therm[k] = make_double4_32a(r, p[o] / (r * r), cs[o], 1.0 / h[o]);
+        const double r = rho[o], c = cs[o];
+        const double hinv = 1.0 / hh;
+        const double h2 = hinv * hinv;
+        therm[k] = make_double4_32a(0.5 * r, p[o] / (r * r), 0.5 * alpha * c, 0.5 * hh);
+        kern[k] = make_double2(hinv, h2 * h2);
+        cint[k] = c;
     }
 }
 
-void launch_gather_state(sph_ctx* c, const sph_particles* P, int what, cudaStream_t s) {
+void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, int what,
+                         cudaStream_t s) {
     const int64_t n = c->n;
     if (n == 0) return;
     const int b = c->cur;
     c->launches += 1;
     k_gather_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-        n, what, c->order[b], P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m, P->rho, P->p,
-        P->c, c->posh[b], c->velm[b], c->therm);
+        n, what, kp.alpha, c->order[b], P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m,
+        P->rho, P->p, P->c, c->posh[b], c->velm[b], c->therm, c->kern, c->cint);
 }
 
 // ------------------------------------------------------------ bbox and grid

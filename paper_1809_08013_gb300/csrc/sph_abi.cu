@@ -83,7 +83,7 @@ bool dalloc(T** p, size_t count) {
 
 void free_all(sph_ctx* c) {
     void* ptrs[] = {c->posh[0], c->posh[1], c->velm[0], c->velm[1], c->ue[0], c->ue[1],
-                    c->therm, c->acc, c->pint, c->mumax, c->fpos, c->tin, c->order[0],
+                    c->therm, c->kern, c->acc, c->pint, c->cint, c->mumax, c->fpos, c->tin, c->order[0],
                     c->order[1], c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist,
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->red_part, c->dt_part, c->grid,
@@ -215,7 +215,8 @@ sph_status sph_ctx_create(sph_ctx** out, int64_t ncap, int64_t nnzcap, int devic
         ok = ok && dalloc(&c->posh[b], N) && dalloc(&c->velm[b], N) && dalloc(&c->ue[b], N) &&
              dalloc(&c->order[b], N) && dalloc(&c->keys[b], N) && dalloc(&c->vals[b], N);
     }
-    ok = ok && dalloc(&c->therm, N) && dalloc(&c->acc, N) && dalloc(&c->pint, N) &&
+    ok = ok && dalloc(&c->therm, N) && dalloc(&c->kern, N) && dalloc(&c->acc, N) &&
+         dalloc(&c->pint, N) && dalloc(&c->cint, N) &&
          dalloc(&c->mumax, N) && dalloc(&c->fpos, N) && dalloc(&c->tin, N) &&
          dalloc(&c->hist, 256 * nsb) && dalloc(&c->hist_part, (size_t)scan_parts(256 * nsb) + 1) &&
          dalloc(&c->cells, (size_t)c->cellcap) && dalloc(&c->cell_hmax, (size_t)c->cellcap) &&
@@ -297,7 +298,7 @@ sph_status sph_density(sph_ctx* c, const sph_params* prm, sph_particles* P, void
     DeviceGuard dg(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const KParams kp = kparams(prm);
-    launch_gather_state(c, P, GATHER_DENSITY, s);
+    launch_gather_state(c, P, kp, GATHER_DENSITY, s);
     launch_density(c, kp, false, s);
     launch_scatter(c, P, SC_RHO, s);
     return check_launch(c, "sph_density");
@@ -331,7 +332,7 @@ sph_status sph_forces(sph_ctx* c, const sph_params* prm, sph_particles* P, void*
     DeviceGuard dg(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const KParams kp = kparams(prm);
-    launch_gather_state(c, P, GATHER_FORCES, s);
+    launch_gather_state(c, P, kp, GATHER_FORCES, s);
     launch_forces(c, kp, P->dt, nullptr, s);
     launch_scatter(c, P, SC_ACC | SC_MUMAX, s);
     return check_launch(c, "sph_forces");

@@ -1,11 +1,12 @@
 // sph_internal.cuh -- internal types and launchers of libsph (not part of the ABI).
 //
 // Data layout in HBM (internal, Morton-cell order, one entry per particle):
-//   posh[k]   = (x, y, z, h)        double4_32a, 32 B
-//   velm[k]   = (vx, vy, vz, m)     double4_32a, 32 B
-//   therm[k]  = (rho, A, c, 1/h)    double4_32a, 32 B, A = p / rho^2
-//   acc[k]    = (ax, ay, az, du)    double4_32a, 32 B
-//   ue[k], pint[k], mumax[k]        u, p and max_j |mu_ij| (double)
+//   posh[k]   = (x, y, z, h)              32 B (double4, 32-byte aligned)
+//   velm[k]   = (vx, vy, vz, m)           32 B
+//   therm[k]  = (rho/2, A, alpha c/2, h/2) 32 B, A = p / rho^2
+//   kern[k]   = (1/h, 1/h^4)              16 B
+//   acc[k]    = (ax, ay, az, du)          32 B
+//   ue[k], pint[k], cint[k], mumax[k]     u, p, c and max_j |mu_ij| (double)
 //   fpos[k]   = (xf, yf, zf, Tout)  float4, 16 B: FP32 copy of the position and
 //               the upper FP32 threshold of the (2h)^2 test (see neighbors.cu)
 //   tin[k]    = Tin                 float: lower FP32 threshold
@@ -76,8 +77,10 @@ struct sph_ctx {
     double4_32a *posh[2], *velm[2];     // permuted with the particles (double-buffered)
     double* ue[2];                  // specific internal energy u
     double4_32a* therm;                 // recomputed every step after the sort
+    double2* kern;
     double4_32a* acc;
     double* pint;
+    double* cint;
     double* mumax;
     float4* fpos;
     float* tin;
@@ -115,7 +118,8 @@ namespace sph {
 
 // ---- sort.cu
 void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s);
-void launch_gather_state(sph_ctx* c, const sph_particles* P, int what, cudaStream_t s);
+void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, int what,
+                         cudaStream_t s);
 void launch_build_cells(sph_ctx* c, const KParams& kp, cudaStream_t s);
 
 // ---- neighbors.cu
