@@ -2,13 +2,13 @@
 //
 // Pair test. The definition is the FP64 test r_ij^2 < (2h)^2 with
 // r^2 = (dx dx + dy dy) + dz dz, each operation rounded on its own (minimum
-// image along z when periodic). GB300's FP64 pipe is narrow, so candidates are
-// first classified in FP32 from float copies of the positions:
+// image along z when periodic). GB300 issues FP64 at 1/64 of the FP32 rate,
+// so candidates are classified in FP32 from float copies of the positions:
 //   r2f < Tin   -> certainly inside,   r2f > Tout -> certainly outside,
 //   otherwise   -> the exact FP64 test above decides.
-// Tin/Tout are derived per particle from a rigorous bound on the FP32 error
-// (see thresholds()), so every decision equals the FP64 one bit for bit and
-// the neighbour sets are exact.
+// Tin/Tout come from a rigorous bound on the FP32 error evaluated with
+// directed-rounding FP32 operations (thresholds()), so every decision equals
+// the FP64 one and the neighbour sets are exact.
 //
 // h search (reading of the Section 2 footnote: h follows a target neighbour
 // count): bracketing search using only correctly rounded * and +,
@@ -18,37 +18,57 @@
 //
 // Symmetric set S_i = { j != i : r_ij < 2h_i or r_ij < 2h_j } as CSR: row i
 // holds N_i (r_ij < 2h_i) first, then the rest.
+//
+// Work decomposition: one warp per particle. The lanes take 32 candidates of
+// a cell at a time (coalesced loads), counts come from ballots and row
+// entries are compacted with ballot prefix counts, so the particle's own
+// iteration count never stalls other particles.
 #include <math_constants.h>
 
 #include "sph_internal.cuh"
 
 namespace sph {
 
+constexpr unsigned kFull = 0xffffffffu;
+
+// Lower and upper FP32 bounds of a positive double from its bit pattern
+// (truncation is rounding toward zero; integer operations only).
+__device__ __forceinline__ void f32_bounds(double x, float& lo, float& hi) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)(b >> 52) - 1023 + 127;
+    if (e <= 0) {
+        lo = 0.0f;
+        hi = 1.17549435e-38f;
+    } else if (e >= 255) {
+        lo = 3.40282347e+38f;
+        hi = CUDART_INF_F;
+    } else {
+        const unsigned lb = ((unsigned)e << 23) | ((unsigned)(b >> 29) & 0x7fffffu);
+        lo = __int_as_float((int)lb);
+        hi = (b & 0x1fffffffull) ? __int_as_float((int)(lb + 1)) : lo;
+    }
+}
+
 struct Thr {
     float tin, tout;
-    double r2;  // (2h)^2 in FP64, the exact threshold
 };
 
-// FP32 classification thresholds for radius R = 2h.
-// |xf - x| <= 2^-24 X for each coordinate (X = max |coordinate|); the FP32
-// difference, the periodic shift by lzf and the rounding of r2f add at most
-// 2^-24 (2X + 2.02 R + 2 lz) per component and 3 * 2^-24 relative on the sum
-// of squares, so the FP32 norm is within d = sqrt(3) e of the norm of the FP64
-// difference vector, whose rounded square differs from it by < 2^-50 relative.
-__device__ __forceinline__ Thr thresholds(double h, const Grid* __restrict__ g) {
-    const double R = 2.0 * h;
+// FP32 classification thresholds for radius R = 2h (R > 0).
+// The FP32 norm of a pair differs from the norm of the FP64 difference vector
+// by at most d = sqrt(3) e, e = eC + eR R (see k_grid_setup); the FP32 sum of
+// squares adds at most 3 * 2^-24 relative; the FP64 square differs from the
+// FP64 norm squared by < 2^-50 relative. All operations round outward.
+__device__ __forceinline__ Thr thresholds(double R, const Grid* __restrict__ g) {
+    float Rl, Rh;
+    f32_bounds(R, Rl, Rh);
+    const float e = __fmaf_ru(g->eR, Rh, g->eC);
+    const float d = __fmul_ru(1.7320525f, e);
     Thr t;
-    t.r2 = __dmul_rn(R, R);
-    const double u24 = 5.9604644775390625e-08;  // 2^-24
-    const double per = g->periodic_z ? 2.0 * g->lz : 0.0;
-    const double e = u24 * (4.0 * g->X + 2.02 * R + per) * 1.0001 + 1e-37;
-    const double d = 1.7320508075688772 * e * 1.000001;
-    const double a = R * (1.0 - 8.8817841970012523e-16) - d;
-    const double b = R * (1.0 + 8.8817841970012523e-16) + d;
-    t.tin = a > 0.0 ? __double2float_rd(a * a * (1.0 - 3.0 * u24) * (1.0 - 9.094947017729282e-13))
-                    : -1.0f;
-    t.tout = __double2float_ru(b * b * (1.0 + 3.0 * u24) * (1.0 + 9.094947017729282e-13));
-    if (g->periodic_z && R > 0.25 * g->lz) {  // wrap decisions may differ: exact path only
+    const float a = __fsub_rd(__fmul_rd(Rl, 0.99999905f), d);  // Rl (1 - 2^-20) - d
+    t.tin = a > 0.0f ? __fmul_rd(__fmul_rd(a, a), 0.9999997f) : -1.0f;
+    const float b = __fadd_ru(__fmul_ru(Rh, 1.00000096f), d);   // Rh (1 + 2^-20) + d
+    t.tout = __fmul_ru(__fmul_ru(b, b), 1.0000003f);
+    if (g->periodic_z && Rh > 0.25f * g->lzf) {  // wrap decisions may differ: exact path only
         t.tin = -1.0f;
         t.tout = CUDART_INF_F;
     }
@@ -83,29 +103,27 @@ __device__ __forceinline__ int wrapi(int k, int n) {
     return r < 0 ? r + n : r;
 }
 
-// Cell index range overlapping [a, b] along axis d (clamped); along the
-// periodic z axis the range may be unclamped (wrapped by the caller) or the
-// whole axis (*all = true).
-__device__ __forceinline__ void box_range(float a, float b, const Grid* __restrict__ g, int d,
-                                          int& k0, int& k1, bool& all) {
-    const float lo = g->lof[d], inv = g->invwf[d], s = g->slop[d];
+// Cell index range overlapping [v - R, v + R] along axis d (clamped); along the
+// periodic z axis an unclamped range (wrapped by the caller) or the whole axis.
+__device__ __forceinline__ void axis_range(float v, float R, const Grid* __restrict__ g, int d,
+                                           int& k0, int& k1) {
+    const float inv = g->invwf[d], s = g->slop[d];
     const int n = g->n[d];
-    all = false;
     if (d == 2 && g->periodic_z) {
-        const float fa = floorf((a - s + g->halflzf) * inv);
-        const float fb = floorf((b + s + g->halflzf) * inv);
+        const float fa = floorf((v - R - s + g->halflzf) * inv);
+        const float fb = floorf((v + R + s + g->halflzf) * inv);
         if (!(fb - fa + 1.0f < (float)n)) {
             k0 = 0;
             k1 = n - 1;
-            all = true;
             return;
         }
         k0 = (int)fa;
         k1 = (int)fb;
         return;
     }
-    float fa = floorf((a - s - lo) * inv);
-    float fb = floorf((b + s - lo) * inv);
+    const float lo = g->lof[d];
+    float fa = floorf((v - R - s - lo) * inv);
+    float fb = floorf((v + R + s - lo) * inv);
     fa = fminf(fmaxf(fa, 0.0f), (float)n);
     fb = fmaxf(fminf(fb, (float)(n - 1)), -1.0f);
     k0 = (int)fa;
@@ -119,126 +137,84 @@ __device__ __forceinline__ float axis_gap(float v, int k, const Grid* __restrict
     return fmaxf(0.0f, fmaxf(a - v, v - b));
 }
 
-__device__ __forceinline__ float wmin(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ float wmax(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Warp-cooperative candidate walk. The 32 lanes of a warp query the union of
-// their boxes [q - R, q + R] (inactive lanes contribute nothing); cells are
-// visited in warp-uniform loops, each cell's particles are staged 32 at a
-// time in shared memory, and every lane sees every staged candidate:
-//   keep(cell, kx, ky, kz) -> bool  per-lane wish to visit a cell (any lane
-//                                    wanting it makes the warp visit it)
-//   visit(j, fj, tinj)               per lane, per staged candidate
-// All 32 lanes must call this together.
-template <class Keep, class Visit>
-__device__ __forceinline__ void warp_walk(const Grid* __restrict__ g, const int2* __restrict__ cells,
-                                          const float4* __restrict__ fpos,
-                                          const float* __restrict__ tin, float4* s_f, float* s_t,
-                                          const float4& q, float R, bool active, Keep&& keep,
-                                          Visit&& visit) {
-    const int lane = threadIdx.x & 31;
-    const float lx = wmin(active ? q.x - R : CUDART_INF_F), hx = wmax(active ? q.x + R : -CUDART_INF_F);
-    if (!(lx <= hx)) return;  // no active lane
-    const float ly = wmin(active ? q.y - R : CUDART_INF_F), hy = wmax(active ? q.y + R : -CUDART_INF_F);
-    const float lz = wmin(active ? q.z - R : CUDART_INF_F), hz = wmax(active ? q.z + R : -CUDART_INF_F);
-    int x0, x1, y0, y1, z0, z1;
-    bool ax, ay, az;
-    box_range(lx, hx, g, 0, x0, x1, ax);
-    box_range(ly, hy, g, 1, y0, y1, ay);
-    box_range(lz, hz, g, 2, z0, z1, az);
-    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-    const bool per = g->periodic_z != 0;
-    for (int kz = z0; kz <= z1; ++kz) {
-        const int cz = per ? wrapi(kz, nz) : kz;
-        for (int ky = y0; ky <= y1; ++ky) {
-            const long long row = ((long long)cz * ny + ky) * nx;
-            for (int kx = x0; kx <= x1; ++kx) {
-                const int2 se = __ldg(&cells[row + kx]);
-                if (se.y <= se.x) continue;
-                if (!__any_sync(0xffffffffu, active && keep(row + kx, kx, ky, kz))) continue;
-                for (int base = se.x; base < se.y; base += 32) {
-                    const int j = base + lane;
-                    if (j < se.y) {
-                        s_f[lane] = __ldg(&fpos[j]);
-                        if (tin) s_t[lane] = __ldg(&tin[j]);
-                    }
-                    __syncwarp();
-                    const int cnt = min(32, se.y - base);
-                    for (int k = 0; k < cnt; ++k) visit(base + k, s_f[k], tin ? s_t[k] : 0.0f);
-                    __syncwarp();
-                }
-            }
-        }
-    }
+// Upper FP32 bound of 2 x (a positive double), widened by 1e-4 relative.
+__device__ __forceinline__ float reach_f32(double h) {
+    float lo, hi;
+    f32_bounds(h, lo, hi);
+    return 2.0f * hi * 1.0001f;
 }
 
 // ------------------------------------------------------------ h search
-// One warp per 32 consecutive particles. Each pass counts |N_i(h)| for every
-// still-searching lane; the warp repeats passes until all lanes are done.
 __global__ void __launch_bounds__(kThreads)
 k_h_iterate(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
             const float4* __restrict__ fpos, const int2* __restrict__ cells,
             int32_t* __restrict__ nnb, unsigned* __restrict__ status) {
-    __shared__ float4 s_f[kThreads / 32][32];
-    const int warp = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < n;
-    double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
-    float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) {
-        pi = posh[i];
-        fi = fpos[i];
-    }
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;  // warp-uniform
+    const double4_32a pi = posh[i];
+    const float4 fi = fpos[i];
     double h = pi.w, lo = 0.0, hi = CUDART_INF;
     const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
-    int cnt = 0, it = 0;
-    bool active = valid && kp.max_h_iter > 0, conv = false;
-    while (__any_sync(0xffffffffu, active)) {
-        const Thr t = thresholds(h, g);
-        const float R = (float)(2.0 * h) * 1.0001f;
+    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    const bool per = g->periodic_z != 0;
+    int cnt = 0;
+    bool conv = false;
+    for (int it = 0; it < kp.max_h_iter; ++it) {
+        const double R = 2.0 * h;
+        const Thr t = thresholds(R, g);
+        const float Rq = reach_f32(h);
+        double R2 = -1.0;  // (2h)^2 in FP64, formed on first use
+        int x0, x1, y0, y1, z0, z1;
+        axis_range(fi.x, Rq, g, 0, x0, x1);
+        axis_range(fi.y, Rq, g, 1, y0, y1);
+        axis_range(fi.z, Rq, g, 2, z0, z1);
         int c = 0;
-        warp_walk(
-            g, cells, fpos, nullptr, s_f[warp], nullptr, fi, R, active,
-            [&](long long, int, int, int) { return true; },
-            [&](int j, const float4& fj, float) {
-                const float r2f = f_r2(fi, fj, g);
-                if (r2f < t.tin) {
-                    c += (j != i);
-                } else if (r2f <= t.tout && j != i && active) {
-                    c += exact_r2(pi, posh[j], g) < t.r2;
+        for (int kz = z0; kz <= z1; ++kz) {
+            const int cz = per ? wrapi(kz, nz) : kz;
+            for (int ky = y0; ky <= y1; ++ky) {
+                const long long row = ((long long)cz * ny + ky) * nx;
+                for (int kx = x0; kx <= x1; ++kx) {
+                    const int2 se = __ldg(&cells[row + kx]);
+                    for (int base = se.x; base < se.y; base += 32) {
+                        const int j = base + lane;
+                        const bool ok = j < se.y && j != i;
+                        bool in = false, bd = false;
+                        if (ok) {
+                            const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
+                            in = r2f < t.tin;
+                            bd = !in && r2f <= t.tout;
+                        }
+                        if (__any_sync(kFull, bd) && bd) {
+                            if (R2 < 0.0) R2 = __dmul_rn(R, R);
+                            in = exact_r2(pi, posh[j], g) < R2;
+                        }
+                        c += __popc(__ballot_sync(kFull, in));
+                    }
                 }
-            });
-        if (active) {
-            cnt = c;
-            ++it;
-            if (cnt >= lowb && cnt <= highb) {
-                conv = true;
-                active = false;
-            } else if (it >= kp.max_h_iter) {
-                active = false;
-            } else if (cnt < lowb) {
-                lo = h;
-                h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
-            } else {
-                hi = h;
-                h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
             }
         }
+        cnt = c;
+        if (cnt >= lowb && cnt <= highb) {
+            conv = true;
+            break;
+        }
+        if (it == kp.max_h_iter - 1) break;
+        if (cnt < lowb) {
+            lo = h;
+            h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+        } else {
+            hi = h;
+            h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+        }
     }
-    if (!valid) return;
-    posh[i].w = h;
-    nnb[i] = cnt;
-    if (!conv) {
-        atomicOr(&status[0], (unsigned)ST_HNOCONV);
-        atomicAdd(&status[1], 1u);
+    if (lane == 0) {
+        posh[i].w = h;
+        nnb[i] = cnt;
+        if (!conv) {
+            atomicOr(&status[0], (unsigned)ST_HNOCONV);
+            atomicAdd(&status[1], 1u);
+        }
     }
 }
 
@@ -248,7 +224,7 @@ k_finalize_h(int64_t n, const Grid* __restrict__ g, const double4_32a* __restric
              float4* __restrict__ fpos, float* __restrict__ tin) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const Thr t = thresholds(posh[i].w, g);
+    const Thr t = thresholds(2.0 * posh[i].w, g);
     fpos[i].w = t.tout;
     tin[i] = t.tin;
 }
@@ -258,33 +234,39 @@ __global__ void __launch_bounds__(kThreads)
 k_cell_hmax(const Grid* __restrict__ gc, Grid* gw, const int2* __restrict__ cells,
             const double4_32a* __restrict__ posh, unsigned long long* __restrict__ cell_hmax) {
     const long long nc = gc->ncells;
-    double bmax = 0.0;
+    long long bmax = 0;  // bits of positive doubles order like their values
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
          c += (long long)gridDim.x * blockDim.x) {
         const int2 se = cells[c];
-        double m = 0.0;
-        for (int k = se.x; k < se.y; ++k) m = fmax(m, posh[k].w);
-        cell_hmax[c] = (unsigned long long)__double_as_longlong(m);
-        bmax = fmax(bmax, m);
+        long long m = 0;
+        for (int k = se.x; k < se.y; ++k) {
+            const long long b = __double_as_longlong(posh[k].w);
+            m = b > m ? b : m;
+        }
+        cell_hmax[c] = (unsigned long long)m;
+        bmax = m > bmax ? m : bmax;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-    __shared__ double sh[kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long v = __shfl_xor_sync(kFull, bmax, o);
+        bmax = v > bmax ? v : bmax;
+    }
+    __shared__ long long sh[kThreads / 32];
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = bmax;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = sh[0];
-        for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, sh[w]);
-        atomicMax(&gw->hmax_bits, (unsigned long long)__double_as_longlong(m));
+        long long m = sh[0];
+        for (int w = 1; w < kThreads / 32; ++w) m = sh[w] > m ? sh[w] : m;
+        atomicMax(&gw->hmax_bits, (unsigned long long)m);
     }
 }
 
 // ------------------------------------------------------------ CSR
 // FILL = false: rowlen[i] = |S_i|, ngather[i] = |N_i|.
-// FILL = true : write row i at offsets[i] (N_i first); rows are skipped when
-//               the total exceeds the capacity (status bit raised).
-// One warp per 32 consecutive particles; a cell is visited when some lane
-// can reach it: its box lies within 2 max(h_i, max h of the cell).
+// FILL = true : write row i at offsets[i] (N_i first) with ballot-compacted,
+//               coalesced stores; nothing is written when the total exceeds
+//               the capacity (status bit raised).
+// A cell is visited when its box lies within 2 max(h_i, max h of the cell).
 template <bool FILL>
 __global__ void __launch_bounds__(kThreads)
 k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ posh,
@@ -293,81 +275,92 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
       int32_t* __restrict__ rowlen, int32_t* __restrict__ ngather,
       const int64_t* __restrict__ offsets, int32_t* __restrict__ idx, int64_t nnzcap,
       unsigned* __restrict__ status) {
-    __shared__ float4 s_f[kThreads / 32][32];
-    __shared__ float s_t[kThreads / 32][32];
-    const int warp = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (FILL) {
-        const int64_t tot = offsets[n];
-        if (tot > nnzcap) {
-            if (i == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
-            return;  // whole grid returns: no warp-collective call is left waiting
-        }
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (FILL && offsets[n] > nnzcap) {
+        if (i == 0 && lane == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
+        return;
     }
-    const bool valid = i < n;
-    double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
-    float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
-    float tin_i = -1.0f;
-    if (valid) {
-        pi = posh[i];
-        fi = fpos[i];
-        tin_i = tin[i];
-    }
-    const double r2i = thresholds(pi.w, g).r2;
-    const double hmaxg = __longlong_as_double((long long)g->hmax_bits);
-    const float Rbig = (float)(2.0 * fmax(pi.w, hmaxg)) * 1.0001f;
+    if (i >= n) return;  // warp-uniform
+    const double4_32a pi = posh[i];
+    const float4 fi = fpos[i];
+    const float tin_i = tin[i];
+    const long long hib = __double_as_longlong(pi.w);
+    const long long hgb = (long long)g->hmax_bits;
+    const float Rbig = reach_f32(__longlong_as_double(hgb > hib ? hgb : hib));
+    double R2i = -1.0;
+    const unsigned lt = (1u << lane) - 1u;
     int64_t pg = 0, po = 0, pg_end = 0, po_end = 0;
-    if (FILL && valid) {
+    if (FILL) {
         pg = offsets[i];
         pg_end = po = pg + ngather[i];
         po_end = offsets[i + 1];
     }
     int cg = 0, co = 0;
+    int x0, x1, y0, y1, z0, z1;
+    axis_range(fi.x, Rbig, g, 0, x0, x1);
+    axis_range(fi.y, Rbig, g, 1, y0, y1);
+    axis_range(fi.z, Rbig, g, 2, z0, z1);
+    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
     const bool per = g->periodic_z != 0;
-    warp_walk(
-        g, cells, fpos, tin, s_f[warp], s_t[warp], fi, Rbig, valid,
-        [&](long long cell, int kx, int ky, int kz) {
-            const double hc = __longlong_as_double((long long)__ldg(&cell_hmax[cell]));
-            const float reach = (float)(2.0 * fmax(pi.w, hc)) * 1.0001f;
-            const float gx = axis_gap(fi.x, kx, g, 0), gy = axis_gap(fi.y, ky, g, 1);
-            const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
-            return fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < reach * reach;
-        },
-        [&](int j, const float4& fj, float tinj) {
-            if (!valid || j == i) return;
-            const float r2f = f_r2(fi, fj, g);
-            bool in_i, have = false;
-            double er2 = 0.0;
-            if (r2f < tin_i) {
-                in_i = true;
-            } else if (r2f > fi.w) {
-                in_i = false;
-            } else {
-                er2 = exact_r2(pi, posh[j], g);
-                have = true;
-                in_i = er2 < r2i;
+    for (int kz = z0; kz <= z1; ++kz) {
+        const int cz = per ? wrapi(kz, nz) : kz;
+        const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
+        for (int ky = y0; ky <= y1; ++ky) {
+            const long long row = ((long long)cz * ny + ky) * nx;
+            const float gy = axis_gap(fi.y, ky, g, 1);
+            for (int kx = x0; kx <= x1; ++kx) {
+                const int2 se = __ldg(&cells[row + kx]);
+                if (se.y <= se.x) continue;
+                const long long hcb = (long long)__ldg(&cell_hmax[row + kx]);
+                const float reach = reach_f32(__longlong_as_double(hcb > hib ? hcb : hib));
+                const float gx = axis_gap(fi.x, kx, g, 0);
+                if (fmaf(gz, gz, fmaf(gy, gy, gx * gx)) >= reach * reach) continue;
+                for (int base = se.x; base < se.y; base += 32) {
+                    const int j = base + lane;
+                    const bool ok = j < se.y && j != i;
+                    bool in_i = false, in_j = false;
+                    if (ok) {
+                        const float4 fj = __ldg(&fpos[j]);
+                        const float r2f = f_r2(fi, fj, g);
+                        bool bd_i = false;
+                        if (r2f < tin_i) in_i = true;
+                        else if (r2f <= fi.w) bd_i = true;
+                        double er2 = -1.0;
+                        if (bd_i) {
+                            if (R2i < 0.0) R2i = __dmul_rn(2.0 * pi.w, 2.0 * pi.w);
+                            er2 = exact_r2(pi, posh[j], g);
+                            in_i = er2 < R2i;
+                        }
+                        if (!in_i && r2f <= fj.w) {
+                            if (r2f < __ldg(&tin[j])) {
+                                in_j = true;
+                            } else {
+                                const double4_32a pj = posh[j];
+                                if (er2 < 0.0) er2 = exact_r2(pi, pj, g);
+                                const double Rj = 2.0 * pj.w;
+                                in_j = er2 < __dmul_rn(Rj, Rj);
+                            }
+                        }
+                    }
+                    const unsigned gm = __ballot_sync(kFull, in_i);
+                    const unsigned om = __ballot_sync(kFull, in_j);
+                    if (FILL) {
+                        if (in_i) {
+                            const int64_t q = pg + cg + __popc(gm & lt);
+                            if (q < pg_end) idx[q] = j;
+                        } else if (in_j) {
+                            const int64_t q = po + co + __popc(om & lt);
+                            if (q < po_end) idx[q] = j;
+                        }
+                    }
+                    cg += __popc(gm);
+                    co += __popc(om);
+                }
             }
-            if (in_i) {
-                if (FILL && pg < pg_end) idx[pg++] = j;
-                ++cg;
-                return;
-            }
-            if (r2f > fj.w) return;
-            bool in_j;
-            if (r2f < tinj) {
-                in_j = true;
-            } else {
-                const double4_32a pj = posh[j];
-                if (!have) er2 = exact_r2(pi, pj, g);
-                const double Rj = 2.0 * pj.w;
-                in_j = er2 < __dmul_rn(Rj, Rj);
-            }
-            if (in_j) {
-                if (FILL && po < po_end) idx[po++] = j;
-                ++co;
-            }
-        });
-    if (!FILL && valid) {
+        }
+    }
+    if (!FILL && lane == 0) {
         rowlen[i] = cg + co;
         ngather[i] = cg;
     }
@@ -377,10 +370,11 @@ void launch_h_search(sph_ctx* c, const KParams& kp, cudaStream_t s) {
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const unsigned nbw = (unsigned)((n * 32 + kThreads - 1) / kThreads);  // one warp per particle
     double4_32a* posh = c->posh[c->cur];
     c->launches += 3;
-    k_h_iterate<<<nb, kThreads, 0, s>>>(n, c->grid, kp, posh, c->fpos, c->cells, c->nnb,
-                                        c->status);
+    k_h_iterate<<<nbw, kThreads, 0, s>>>(n, c->grid, kp, posh, c->fpos, c->cells, c->nnb,
+                                         c->status);
     k_finalize_h<<<nb, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin);
     k_cell_hmax<<<kReduceBlocks, kThreads, 0, s>>>(c->grid, c->grid, c->cells, posh, c->cell_hmax);
 }
@@ -392,16 +386,16 @@ void launch_csr(sph_ctx* c, cudaStream_t s) {
         cudaMemsetAsync(c->offsets, 0, sizeof(int64_t), s);
         return;
     }
-    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const unsigned nbw = (unsigned)((n * 32 + kThreads - 1) / kThreads);
     double4_32a* posh = c->posh[c->cur];
     c->launches += 5;
-    k_csr<false><<<nb, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
-                                         c->cell_hmax, c->rowlen, c->ngather, nullptr, nullptr,
-                                         c->nnzcap, c->status);
+    k_csr<false><<<nbw, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
+                                          c->cell_hmax, c->rowlen, c->ngather, nullptr, nullptr,
+                                          c->nnzcap, c->status);
     launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s);
-    k_csr<true><<<nb, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
-                                        c->cell_hmax, c->rowlen, c->ngather, c->offsets, c->idx,
-                                        c->nnzcap, c->status);
+    k_csr<true><<<nbw, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
+                                         c->cell_hmax, c->rowlen, c->ngather, c->offsets, c->idx,
+                                         c->nnzcap, c->status);
 }
 
 }  // namespace sph

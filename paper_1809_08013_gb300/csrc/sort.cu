@@ -182,6 +182,12 @@ k_grid_setup(const double* __restrict__ part, int nb, int64_t n, KParams kp, int
     g->lzf = (float)kp.lz;
     g->halflzf = (float)(0.5 * kp.lz);
     g->X = X;
+    // |fl32 difference - FP64 difference| <= 2^-24 (4X + 2.02R + 2 lz) per
+    // component (conversions of both coordinates, the FP32 subtraction, the
+    // periodic shift); 1.0001 and the upward rounding keep it an upper bound
+    const double u24 = 5.9604644775390625e-08;
+    g->eC = __double2float_ru(u24 * (4.0 * X + (per ? 2.0 * kp.lz : 0.0)) * 1.0001 + 1e-37);
+    g->eR = __double2float_ru(u24 * 2.02 * 1.0001);
     g->hmean = hmean;
     g->hmax_bits = 0ull;
     g->ncells = (long long)cnt[0] * cnt[1] * cnt[2];

@@ -50,6 +50,7 @@ struct Grid {
     float lof[3], wf[3], invwf[3];
     float lzf, halflzf;
     float slop[3];   // absolute slack added to query boxes (FP32 rounding cover)
+    float eC, eR;    // FP32-error bound of a coordinate difference: e(R) <= eC + eR * R
 };
 
 // Parameters copied by value into kernels.
