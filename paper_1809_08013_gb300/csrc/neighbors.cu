@@ -144,11 +144,84 @@ __device__ __forceinline__ float reach_f32(double h) {
     return 2.0f * hi * 1.0001f;
 }
 
+// One warp, one particle: enumerate the candidates of every cell overlapping
+// the box [q - R, q + R] as one flat list. Up to 32 cells are fetched at once
+// (one per lane), a warp scan of their sizes gives each cell's offset, and the
+// list is handed out 32 candidates at a time: chunk(valid, j) is called by
+// all lanes together, lane l receiving candidate j (valid = false past the
+// end). With PRUNE a cell is dropped unless its box lies within
+// 2 max(h_i, max h of the cell) of the particle (hib = bits of h_i).
+template <bool PRUNE, class Chunk>
+__device__ __forceinline__ void particle_pass(const Grid* __restrict__ g,
+                                              const int2* __restrict__ cells,
+                                              const unsigned long long* __restrict__ cell_hmax,
+                                              const float4& q, float R, long long hib,
+                                              int* s_start, int* s_pref, Chunk&& chunk) {
+    const int lane = threadIdx.x & 31;
+    int x0, x1, y0, y1, z0, z1;
+    axis_range(q.x, R, g, 0, x0, x1);
+    axis_range(q.y, R, g, 1, y0, y1);
+    axis_range(q.z, R, g, 2, z0, z1);
+    const int nxr = x1 - x0 + 1, nyr = y1 - y0 + 1, nzr = z1 - z0 + 1;
+    if (nxr <= 0 || nyr <= 0 || nzr <= 0) return;
+    const int C = nxr * nyr * nzr;
+    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    const bool per = g->periodic_z != 0;
+    for (int c0 = 0; c0 < C; c0 += 32) {
+        const int c = c0 + lane;
+        int start = 0, cnt = 0;
+        if (c < C) {
+            const int kx = x0 + c % nxr;
+            const int rr = c / nxr;
+            const int ky = y0 + rr % nyr;
+            const int kz = z0 + rr / nyr;
+            const int cz = per ? wrapi(kz, nz) : kz;
+            const long long lin = ((long long)cz * ny + ky) * nx + kx;
+            const int2 se = __ldg(&cells[lin]);
+            start = se.x;
+            cnt = se.y - se.x;
+            if (PRUNE && cnt > 0) {
+                const long long hcb = (long long)__ldg(&cell_hmax[lin]);
+                const float reach = reach_f32(__longlong_as_double(hcb > hib ? hcb : hib));
+                const float gx = axis_gap(q.x, kx, g, 0), gy = axis_gap(q.y, ky, g, 1);
+                const float gz = per ? 0.0f : axis_gap(q.z, kz, g, 2);
+                if (fmaf(gz, gz, fmaf(gy, gy, gx * gx)) >= reach * reach) cnt = 0;
+            }
+        }
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int total = __shfl_sync(kFull, inc, 31);
+        s_start[lane] = start;
+        s_pref[lane] = inc - cnt;  // exclusive offset; lanes past C hold total
+        __syncwarp();
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            const bool valid = t < total;
+            int j = -1;
+            if (valid) {
+                int k = 0;  // last cell whose offset is <= t
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (s_pref[k + step] <= t) k += step;
+                j = s_start[k] + (t - s_pref[k]);
+            }
+            chunk(valid, j);
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------ h search
 __global__ void __launch_bounds__(kThreads)
 k_h_iterate(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
             const float4* __restrict__ fpos, const int2* __restrict__ cells,
             int32_t* __restrict__ nnb, unsigned* __restrict__ status) {
+    __shared__ int s_start[kThreads / 32][32], s_pref[kThreads / 32][32];
+    const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;  // warp-uniform
@@ -156,44 +229,27 @@ k_h_iterate(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh
     const float4 fi = fpos[i];
     double h = pi.w, lo = 0.0, hi = CUDART_INF;
     const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
-    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-    const bool per = g->periodic_z != 0;
     int cnt = 0;
     bool conv = false;
     for (int it = 0; it < kp.max_h_iter; ++it) {
         const double R = 2.0 * h;
         const Thr t = thresholds(R, g);
-        const float Rq = reach_f32(h);
         double R2 = -1.0;  // (2h)^2 in FP64, formed on first use
-        int x0, x1, y0, y1, z0, z1;
-        axis_range(fi.x, Rq, g, 0, x0, x1);
-        axis_range(fi.y, Rq, g, 1, y0, y1);
-        axis_range(fi.z, Rq, g, 2, z0, z1);
         int c = 0;
-        for (int kz = z0; kz <= z1; ++kz) {
-            const int cz = per ? wrapi(kz, nz) : kz;
-            for (int ky = y0; ky <= y1; ++ky) {
-                const long long row = ((long long)cz * ny + ky) * nx;
-                for (int kx = x0; kx <= x1; ++kx) {
-                    const int2 se = __ldg(&cells[row + kx]);
-                    for (int base = se.x; base < se.y; base += 32) {
-                        const int j = base + lane;
-                        const bool ok = j < se.y && j != i;
-                        bool in = false, bd = false;
-                        if (ok) {
-                            const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
-                            in = r2f < t.tin;
-                            bd = !in && r2f <= t.tout;
-                        }
-                        if (__any_sync(kFull, bd) && bd) {
-                            if (R2 < 0.0) R2 = __dmul_rn(R, R);
-                            in = exact_r2(pi, posh[j], g) < R2;
-                        }
-                        c += __popc(__ballot_sync(kFull, in));
-                    }
-                }
-            }
-        }
+        particle_pass<false>(g, cells, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
+                             [&](bool valid, int j) {
+                                 bool in = false, bd = false;
+                                 if (valid && j != i) {
+                                     const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
+                                     in = r2f < t.tin;
+                                     bd = !in && r2f <= t.tout;
+                                 }
+                                 if (__any_sync(kFull, bd) && bd) {
+                                     if (R2 < 0.0) R2 = __dmul_rn(R, R);
+                                     in = exact_r2(pi, posh[j], g) < R2;
+                                 }
+                                 c += __popc(__ballot_sync(kFull, in));
+                             });
         cnt = c;
         if (cnt >= lowb && cnt <= highb) {
             conv = true;
@@ -275,6 +331,8 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
       int32_t* __restrict__ rowlen, int32_t* __restrict__ ngather,
       const int64_t* __restrict__ offsets, int32_t* __restrict__ idx, int64_t nnzcap,
       unsigned* __restrict__ status) {
+    __shared__ int s_start[kThreads / 32][32], s_pref[kThreads / 32][32];
+    const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (FILL && offsets[n] > nnzcap) {
@@ -297,69 +355,46 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
         po_end = offsets[i + 1];
     }
     int cg = 0, co = 0;
-    int x0, x1, y0, y1, z0, z1;
-    axis_range(fi.x, Rbig, g, 0, x0, x1);
-    axis_range(fi.y, Rbig, g, 1, y0, y1);
-    axis_range(fi.z, Rbig, g, 2, z0, z1);
-    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-    const bool per = g->periodic_z != 0;
-    for (int kz = z0; kz <= z1; ++kz) {
-        const int cz = per ? wrapi(kz, nz) : kz;
-        const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
-        for (int ky = y0; ky <= y1; ++ky) {
-            const long long row = ((long long)cz * ny + ky) * nx;
-            const float gy = axis_gap(fi.y, ky, g, 1);
-            for (int kx = x0; kx <= x1; ++kx) {
-                const int2 se = __ldg(&cells[row + kx]);
-                if (se.y <= se.x) continue;
-                const long long hcb = (long long)__ldg(&cell_hmax[row + kx]);
-                const float reach = reach_f32(__longlong_as_double(hcb > hib ? hcb : hib));
-                const float gx = axis_gap(fi.x, kx, g, 0);
-                if (fmaf(gz, gz, fmaf(gy, gy, gx * gx)) >= reach * reach) continue;
-                for (int base = se.x; base < se.y; base += 32) {
-                    const int j = base + lane;
-                    const bool ok = j < se.y && j != i;
-                    bool in_i = false, in_j = false;
-                    if (ok) {
-                        const float4 fj = __ldg(&fpos[j]);
-                        const float r2f = f_r2(fi, fj, g);
-                        bool bd_i = false;
-                        if (r2f < tin_i) in_i = true;
-                        else if (r2f <= fi.w) bd_i = true;
-                        double er2 = -1.0;
-                        if (bd_i) {
-                            if (R2i < 0.0) R2i = __dmul_rn(2.0 * pi.w, 2.0 * pi.w);
-                            er2 = exact_r2(pi, posh[j], g);
-                            in_i = er2 < R2i;
-                        }
-                        if (!in_i && r2f <= fj.w) {
-                            if (r2f < __ldg(&tin[j])) {
-                                in_j = true;
-                            } else {
-                                const double4_32a pj = posh[j];
-                                if (er2 < 0.0) er2 = exact_r2(pi, pj, g);
-                                const double Rj = 2.0 * pj.w;
-                                in_j = er2 < __dmul_rn(Rj, Rj);
-                            }
-                        }
-                    }
-                    const unsigned gm = __ballot_sync(kFull, in_i);
-                    const unsigned om = __ballot_sync(kFull, in_j);
-                    if (FILL) {
-                        if (in_i) {
-                            const int64_t q = pg + cg + __popc(gm & lt);
-                            if (q < pg_end) idx[q] = j;
-                        } else if (in_j) {
-                            const int64_t q = po + co + __popc(om & lt);
-                            if (q < po_end) idx[q] = j;
-                        }
-                    }
-                    cg += __popc(gm);
-                    co += __popc(om);
+    particle_pass<true>(g, cells, cell_hmax, fi, Rbig, hib, s_start[warp], s_pref[warp],
+                        [&](bool valid, int j) {
+        bool in_i = false, in_j = false;
+        if (valid && j != i) {
+            const float4 fj = __ldg(&fpos[j]);
+            const float r2f = f_r2(fi, fj, g);
+            bool bd_i = false;
+            if (r2f < tin_i) in_i = true;
+            else if (r2f <= fi.w) bd_i = true;
+            double er2 = -1.0;
+            if (bd_i) {
+                if (R2i < 0.0) R2i = __dmul_rn(2.0 * pi.w, 2.0 * pi.w);
+                er2 = exact_r2(pi, posh[j], g);
+                in_i = er2 < R2i;
+            }
+            if (!in_i && r2f <= fj.w) {
+                if (r2f < __ldg(&tin[j])) {
+                    in_j = true;
+                } else {
+                    const double4_32a pj = posh[j];
+                    if (er2 < 0.0) er2 = exact_r2(pi, pj, g);
+                    const double Rj = 2.0 * pj.w;
+                    in_j = er2 < __dmul_rn(Rj, Rj);
                 }
             }
         }
-    }
+        const unsigned gm = __ballot_sync(kFull, in_i);
+        const unsigned om = __ballot_sync(kFull, in_j);
+        if (FILL) {
+            if (in_i) {
+                const int64_t q = pg + cg + __popc(gm & lt);
+                if (q < pg_end) idx[q] = j;
+            } else if (in_j) {
+                const int64_t q = po + co + __popc(om & lt);
+                if (q < po_end) idx[q] = j;
+            }
+        }
+        cg += __popc(gm);
+        co += __popc(om);
+    });
     if (!FILL && lane == 0) {
         rowlen[i] = cg + co;
         ngather[i] = cg;
