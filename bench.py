@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--side", type=int, default=100, help="lattice side (100 -> 1M particles)")
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--cell-scale", type=float, default=0.0,
+                    help="neighbour-search cell width / (2 <h>); 0 = library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -199,6 +201,7 @@ def run_native(args):
     B.load()
 
     s, prm = ics.square_patch(args.side, seed=args.seed)
+    prm.cell_scale = args.cell_scale
     n = len(s["x"])
     ctx = B.Context(n, device=local)
     arr = B.alloc_arrays(s, device=dev)

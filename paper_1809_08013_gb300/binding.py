@@ -27,7 +27,7 @@ class SphParams(C.Structure):
         ("max_h_iter", C.c_int32), ("periodic_z", C.c_int32), ("precision", C.c_int32),
         ("rho0", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
         ("alpha", C.c_double), ("beta", C.c_double), ("eta2", C.c_double),
-        ("cfl", C.c_double), ("lz", C.c_double),
+        ("cfl", C.c_double), ("lz", C.c_double), ("cell_scale", C.c_double),
     ]
 
 
@@ -118,7 +118,8 @@ def params(p) -> SphParams:
     """Marshal an object with the SphParams attributes (see ics.SphParams)."""
     return SphParams(int(p.eos), int(p.n_target), int(p.n_tol), int(p.max_h_iter),
                      int(p.periodic_z), 0, float(p.rho0), float(p.c0), float(p.gamma),
-                     float(p.alpha), float(p.beta), float(p.eta2), float(p.cfl), float(p.lz))
+                     float(p.alpha), float(p.beta), float(p.eta2), float(p.cfl), float(p.lz),
+                     float(getattr(p, "cell_scale", 0.0)))
 
 
 def _ptr(t):

@@ -149,9 +149,10 @@ __device__ __forceinline__ float reach_f32(double h) {
 // (one per lane), a warp scan of their sizes gives each cell's offset, and the
 // list is handed out 32 candidates at a time: chunk(valid, j) is called by
 // all lanes together, lane l receiving candidate j (valid = false past the
-// end). With PRUNE a cell is dropped unless its box lies within
+// end). PRUNE = 1 drops a cell whose box lies farther than R from the
+// particle; PRUNE = 2 drops it unless its box lies within
 // 2 max(h_i, max h of the cell) of the particle (hib = bits of h_i).
-template <bool PRUNE, class Chunk>
+template <int PRUNE, class Chunk>
 __device__ __forceinline__ void particle_pass(const Grid* __restrict__ g,
                                               const int2* __restrict__ cells,
                                               const unsigned long long* __restrict__ cell_hmax,
@@ -181,8 +182,11 @@ __device__ __forceinline__ void particle_pass(const Grid* __restrict__ g,
             start = se.x;
             cnt = se.y - se.x;
             if (PRUNE && cnt > 0) {
-                const long long hcb = (long long)__ldg(&cell_hmax[lin]);
-                const float reach = reach_f32(__longlong_as_double(hcb > hib ? hcb : hib));
+                float reach = R;
+                if (PRUNE == 2) {
+                    const long long hcb = (long long)__ldg(&cell_hmax[lin]);
+                    reach = reach_f32(__longlong_as_double(hcb > hib ? hcb : hib));
+                }
                 const float gx = axis_gap(q.x, kx, g, 0), gy = axis_gap(q.y, ky, g, 1);
                 const float gz = per ? 0.0f : axis_gap(q.z, kz, g, 2);
                 if (fmaf(gz, gz, fmaf(gy, gy, gx * gx)) >= reach * reach) cnt = 0;
@@ -219,7 +223,8 @@ __device__ __forceinline__ void particle_pass(const Grid* __restrict__ g,
 __global__ void __launch_bounds__(kThreads)
 k_h_iterate(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
             const float4* __restrict__ fpos, const int2* __restrict__ cells,
-            int32_t* __restrict__ nnb, unsigned* __restrict__ status) {
+            int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
+            int32_t* __restrict__ gslab, unsigned* __restrict__ status) {
     __shared__ int s_start[kThreads / 32][32], s_pref[kThreads / 32][32];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -231,25 +236,34 @@ k_h_iterate(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh
     const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
     int cnt = 0;
     bool conv = false;
+    const unsigned lt = (1u << lane) - 1u;
+    int32_t* slab = gslab + i * kGSlab;
     for (int it = 0; it < kp.max_h_iter; ++it) {
         const double R = 2.0 * h;
         const Thr t = thresholds(R, g);
         double R2 = -1.0;  // (2h)^2 in FP64, formed on first use
         int c = 0;
-        particle_pass<false>(g, cells, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
-                             [&](bool valid, int j) {
-                                 bool in = false, bd = false;
-                                 if (valid && j != i) {
-                                     const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
-                                     in = r2f < t.tin;
-                                     bd = !in && r2f <= t.tout;
-                                 }
-                                 if (__any_sync(kFull, bd) && bd) {
-                                     if (R2 < 0.0) R2 = __dmul_rn(R, R);
-                                     in = exact_r2(pi, posh[j], g) < R2;
-                                 }
-                                 c += __popc(__ballot_sync(kFull, in));
-                             });
+        // every count also records the gather set in the slab; the last count
+        // (the converged one, or the last allowed) leaves N_i(h_final) there
+        particle_pass<1>(g, cells, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
+                         [&](bool valid, int j) {
+                             bool in = false, bd = false;
+                             if (valid && j != i) {
+                                 const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
+                                 in = r2f < t.tin;
+                                 bd = !in && r2f <= t.tout;
+                             }
+                             if (__any_sync(kFull, bd) && bd) {
+                                 if (R2 < 0.0) R2 = __dmul_rn(R, R);
+                                 in = exact_r2(pi, posh[j], g) < R2;
+                             }
+                             const unsigned m = __ballot_sync(kFull, in);
+                             if (in) {
+                                 const int q = c + __popc(m & lt);
+                                 if (q < kGSlab) slab[q] = j;
+                             }
+                             c += __popc(m);
+                         });
         cnt = c;
         if (cnt >= lowb && cnt <= highb) {
             conv = true;
@@ -267,6 +281,8 @@ k_h_iterate(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh
     if (lane == 0) {
         posh[i].w = h;
         nnb[i] = cnt;
+        ngather[i] = cnt;
+        if (cnt > kGSlab) atomicOr(&status[2], (unsigned)IF_SLAB_OVF);
         if (!conv) {
             atomicOr(&status[0], (unsigned)ST_HNOCONV);
             atomicAdd(&status[1], 1u);
@@ -277,12 +293,13 @@ k_h_iterate(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh
 // Per-particle FP32 thresholds at the final h.
 __global__ void __launch_bounds__(kThreads)
 k_finalize_h(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ posh,
-             float4* __restrict__ fpos, float* __restrict__ tin) {
+             float4* __restrict__ fpos, float* __restrict__ tin, int32_t* __restrict__ ocnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const Thr t = thresholds(2.0 * posh[i].w, g);
     fpos[i].w = t.tout;
     tin[i] = t.tin;
+    ocnt[i] = 0;
 }
 
 // Per-cell max h, and the global max (one atomic per block).
@@ -318,6 +335,76 @@ k_cell_hmax(const Grid* __restrict__ gc, Grid* gw, const int2* __restrict__ cell
 }
 
 // ------------------------------------------------------------ CSR
+// Slab path (normal case). The h search left N_i in the gather slab. The
+// rest of S_i is the transpose of the non-mutual gather pairs:
+// S_j \ N_j = { i : j in N_i and i not in N_j }. k_outer scans the gather
+// slabs, appends such i to j's outer slab (atomic slot, so unordered),
+// k_rowlen forms |S_i|, and k_compose writes each CSR row: the gather slab,
+// then the outer slab sorted by index (deterministic rows).
+__global__ void __launch_bounds__(kThreads)
+k_outer(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ posh,
+        const float4* __restrict__ fpos, const float* __restrict__ tin,
+        const int32_t* __restrict__ ngather, const int32_t* __restrict__ gslab,
+        int32_t* __restrict__ ocnt, int32_t* __restrict__ oslab, unsigned* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n || (status[2] & IF_SLAB_OVF)) return;
+    const int ng = ngather[i];
+    const float4 fi = fpos[i];
+    for (int s = lane; s < ng; s += 32) {
+        const int j = __ldg(&gslab[i * kGSlab + s]);
+        const float4 fj = __ldg(&fpos[j]);
+        const float r2f = f_r2(fi, fj, g);
+        bool in_j;
+        if (r2f < __ldg(&tin[j])) {
+            in_j = true;
+        } else if (r2f > fj.w) {
+            in_j = false;
+        } else {
+            const double4_32a pj = posh[j];
+            const double Rj = 2.0 * pj.w;
+            in_j = exact_r2(posh[i], pj, g) < __dmul_rn(Rj, Rj);
+        }
+        if (!in_j) {
+            const int q = atomicAdd(&ocnt[j], 1);
+            if (q < kOSlab) oslab[(int64_t)j * kOSlab + q] = (int32_t)i;
+            else atomicOr(&status[2], (unsigned)IF_SLAB_OVF);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_rowlen(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __restrict__ ocnt,
+         int32_t* __restrict__ rowlen, const unsigned* __restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (status[2] & IF_SLAB_OVF)) return;
+    rowlen[i] = ngather[i] + ocnt[i];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_compose(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __restrict__ gslab,
+          const int32_t* __restrict__ ocnt, const int32_t* __restrict__ oslab,
+          const int64_t* __restrict__ offsets, int32_t* __restrict__ idx, int64_t nnzcap,
+          unsigned* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (status[2] & IF_SLAB_OVF) return;
+    if (offsets[n] > nnzcap) {
+        if (i == 0 && lane == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
+        return;
+    }
+    if (i >= n) return;
+    const int64_t off = offsets[i];
+    const int ng = ngather[i], no = ocnt[i];
+    for (int s = lane; s < ng; s += 32) idx[off + s] = __ldg(&gslab[i * kGSlab + s]);
+    const int v = lane < no ? __ldg(&oslab[i * kOSlab + lane]) : 0x7fffffff;
+    int rank = 0;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) rank += __shfl_sync(kFull, v, t) < v;
+    if (lane < no) idx[off + ng + rank] = v;
+}
+
+// Fallback (a row overflowed a slab): the full two-pass build below.
 // FILL = false: rowlen[i] = |S_i|, ngather[i] = |N_i|.
 // FILL = true : write row i at offsets[i] (N_i first) with ballot-compacted,
 //               coalesced stores; nothing is written when the total exceeds
@@ -335,6 +422,7 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (!(status[2] & IF_SLAB_OVF)) return;  // the slab path built the list
     if (FILL && offsets[n] > nnzcap) {
         if (i == 0 && lane == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
         return;
@@ -355,7 +443,7 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
         po_end = offsets[i + 1];
     }
     int cg = 0, co = 0;
-    particle_pass<true>(g, cells, cell_hmax, fi, Rbig, hib, s_start[warp], s_pref[warp],
+    particle_pass<2>(g, cells, cell_hmax, fi, Rbig, hib, s_start[warp], s_pref[warp],
                         [&](bool valid, int j) {
         bool in_i = false, in_j = false;
         if (valid && j != i) {
@@ -409,8 +497,8 @@ void launch_h_search(sph_ctx* c, const KParams& kp, cudaStream_t s) {
     double4_32a* posh = c->posh[c->cur];
     c->launches += 3;
     k_h_iterate<<<nbw, kThreads, 0, s>>>(n, c->grid, kp, posh, c->fpos, c->cells, c->nnb,
-                                         c->status);
-    k_finalize_h<<<nb, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin);
+                                         c->ngather, c->gslab, c->status);
+    k_finalize_h<<<nb, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->ocnt);
     k_cell_hmax<<<kReduceBlocks, kThreads, 0, s>>>(c->grid, c->grid, c->cells, posh, c->cell_hmax);
 }
 
@@ -421,13 +509,19 @@ void launch_csr(sph_ctx* c, cudaStream_t s) {
         cudaMemsetAsync(c->offsets, 0, sizeof(int64_t), s);
         return;
     }
+    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const unsigned nbw = (unsigned)((n * 32 + kThreads - 1) / kThreads);
     double4_32a* posh = c->posh[c->cur];
-    c->launches += 5;
+    c->launches += 8;
+    k_outer<<<nbw, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->ngather, c->gslab,
+                                     c->ocnt, c->oslab, c->status);
+    k_rowlen<<<nb, kThreads, 0, s>>>(n, c->ngather, c->ocnt, c->rowlen, c->status);
     k_csr<false><<<nbw, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
                                           c->cell_hmax, c->rowlen, c->ngather, nullptr, nullptr,
                                           c->nnzcap, c->status);
     launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s);
+    k_compose<<<nbw, kThreads, 0, s>>>(n, c->ngather, c->gslab, c->ocnt, c->oslab, c->offsets,
+                                       c->idx, c->nnzcap, c->status);
     k_csr<true><<<nbw, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
                                          c->cell_hmax, c->rowlen, c->ngather, c->offsets, c->idx,
                                          c->nnzcap, c->status);

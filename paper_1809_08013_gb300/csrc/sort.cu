@@ -123,11 +123,11 @@ __device__ __forceinline__ int grid_count(double ext, double w, double* wout) {
 }
 
 // One block: reduce the bbox partials and derive the cell grid. The cell width
-// is 2 <h> (mean smoothing length), so a typical particle's 2h sphere spans
-// 2-3 cells per axis; wider or narrower searches visit more or fewer cells.
+// is 2 <h> cell_scale (<h> the mean smoothing length); the neighbour sets do
+// not depend on it, only the number of candidates and cells visited do.
 __global__ void __launch_bounds__(32)
 k_grid_setup(const double* __restrict__ part, int nb, int64_t n, KParams kp, int64_t cellcap,
-             Grid* __restrict__ g) {
+             Grid* __restrict__ g, unsigned* __restrict__ status) {
     __shared__ double r[8];
     if (threadIdx.x < 8) {
         const int q = threadIdx.x;
@@ -142,8 +142,9 @@ k_grid_setup(const double* __restrict__ part, int nb, int64_t n, KParams kp, int
     if (n == 0) {
         for (int d = 0; d < 3; ++d) { mn[d] = 0.0; mx[d] = 0.0; }
     }
+    status[2] = 0u;
     const double hmean = n > 0 ? r[7] / (double)n : 1.0;
-    double w = 2.0 * hmean;
+    double w = 2.0 * hmean * kp.cell_scale;
     if (!(w > 0.0) || !isfinite(w)) w = 1.0;
     const bool per = kp.periodic_z != 0;
     int cnt[3];
@@ -351,7 +352,8 @@ void launch_build_cells(sph_ctx* c, const KParams& kp, cudaStream_t s) {
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     c->launches += 2;
     k_bbox<<<kReduceBlocks, kThreads, 0, s>>>(n, c->posh[c->cur], c->red_part);
-    k_grid_setup<<<1, 32, 0, s>>>(c->red_part, kReduceBlocks, n, kp, c->cellcap, c->grid);
+    k_grid_setup<<<1, 32, 0, s>>>(c->red_part, kReduceBlocks, n, kp, c->cellcap, c->grid,
+                                  c->status);
     if (n == 0) return;
     c->launches += 1 + 3 * 5 + 3;
     k_keys<<<nb, kThreads, 0, s>>>(n, c->posh[c->cur], c->grid, c->keys[0], c->vals[0]);

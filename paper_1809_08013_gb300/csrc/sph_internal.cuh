@@ -34,6 +34,12 @@ enum : unsigned {
     ST_CAPACITY = 1u,   // neighbour list exceeded nnz capacity
     ST_HNOCONV = 2u,    // some h search did not converge
 };
+// internal flags (status[2], cleared at every build)
+enum : unsigned {
+    IF_SLAB_OVF = 1u,   // a row did not fit the gather/outer slabs: full CSR kernels run
+};
+constexpr int kGSlab = 128;  // gather-set slots per particle (>= n_target + n_tol)
+constexpr int kOSlab = 32;   // outer-set slots per particle
 
 // Cell grid, computed on the device from the particle bounding box each build.
 struct Grid {
@@ -56,7 +62,7 @@ struct Grid {
 // Parameters copied by value into kernels.
 struct KParams {
     int eos, n_target, n_tol, max_h_iter, periodic_z;
-    double rho0, c0, gamma, alpha, beta, eta2, cfl, lz;
+    double rho0, c0, gamma, alpha, beta, eta2, cfl, lz, cell_scale;
 };
 
 inline KParams kparams(const sph_params* p) {
@@ -65,6 +71,7 @@ inline KParams kparams(const sph_params* p) {
     k.max_h_iter = p->max_h_iter; k.periodic_z = p->periodic_z;
     k.rho0 = p->rho0; k.c0 = p->c0; k.gamma = p->gamma; k.alpha = p->alpha;
     k.beta = p->beta; k.eta2 = p->eta2; k.cfl = p->cfl; k.lz = p->lz;
+    k.cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 1.0;
     return k;
 }
 
@@ -96,10 +103,13 @@ struct sph_ctx {
     int64_t* offsets;
     int64_t* row_part;      // scan partials of the row lengths
     int32_t* idx;
+    int32_t* gslab;         // kGSlab per particle: gather set of the last h-search count
+    int32_t* oslab;         // kOSlab per particle: outer set (r < 2 h_j only), unordered
+    int32_t* ocnt;          // outer-set sizes
     double* red_part;       // bbox partials: kReduceBlocks x 8
     double* dt_part;        // per force block
     sph::Grid* grid;
-    unsigned* status;       // [0] bits, [1] non-converged count
+    unsigned* status;       // [0] bits, [1] non-converged count, [2] internal flags
     unsigned* status_host;  // pinned mirror
     double* scratch_scalar; // [0] internal dt, [1] internal time
     int64_t last_hnoconv;

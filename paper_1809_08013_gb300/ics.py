@@ -64,6 +64,7 @@ class SphParams:
     max_h_iter: int = 64         # smoothing-length iterations before giving up
     periodic_z: int = 1          # 1: minimum-image periodicity along z
     lz: float = 1.0              # period along z
+    cell_scale: float = 0.0      # neighbour-search cell width / (2 <h>); 0 = library default
 
     def as_dict(self) -> dict:
         return dataclasses.asdict(self)

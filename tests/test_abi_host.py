@@ -51,8 +51,8 @@ def test_ctx_create_rejects_bad_sizes(lib):
 
 
 def test_param_struct_layout_matches_header():
-    # offsets of the C struct (int32 x 6, then 8 doubles)
-    assert C.sizeof(binding.SphParams) == 6 * 4 + 8 * 8
+    # offsets of the C struct (int32 x 6, then 9 doubles)
+    assert C.sizeof(binding.SphParams) == 6 * 4 + 9 * 8
     assert binding.SphParams.rho0.offset == 24
     assert C.sizeof(binding.SphParticles) == 8 + 20 * 8
     assert C.sizeof(binding.SphNeighbors) == 8 + 5 * 8

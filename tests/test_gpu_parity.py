@@ -264,3 +264,28 @@ def test_invalid_arguments_rejected(B):
     # density before any build of this size
     with pytest.raises(B.SphError):
         ctx.density(prm, arr)
+
+
+def test_slab_overflow_uses_full_build(B, orc):
+    # 150 neighbours per particle exceed the 128-entry gather slab, so the
+    # library takes its two-pass CSR build; results must not change
+    s, prm = ics.square_patch(17, seed=21)
+    prm.n_target = 150
+    o = orc.pipeline(prm, s)
+    ctx, arr, st = gpu_build(B, prm, s)
+    assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
+    off, idx, ng, order = ctx.neighbors_to_host()
+    assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
+    ctx.density(prm, arr)
+    assert normwise(host(arr["rho"]), o["rho"]) <= TOL_FP64
+
+
+@pytest.mark.parametrize("cell_scale", [0.5, 0.75, 1.5])
+def test_neighbours_do_not_depend_on_cell_width(B, orc, cell_scale):
+    s, prm, o, _ = oracle_of(orc, "patch_varh")
+    prm2 = ics.SphParams(**prm.as_dict())
+    prm2.cell_scale = cell_scale
+    ctx, arr, st = gpu_build(B, prm2, s)
+    assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
+    off, idx, ng, order = ctx.neighbors_to_host()
+    assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
