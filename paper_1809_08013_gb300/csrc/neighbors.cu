@@ -397,11 +397,27 @@ k_compose(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __restr
     const int64_t off = offsets[i];
     const int ng = ngather[i], no = ocnt[i];
     for (int s = lane; s < ng; s += 32) idx[off + s] = __ldg(&gslab[i * kGSlab + s]);
-    const int v = lane < no ? __ldg(&oslab[i * kOSlab + lane]) : 0x7fffffff;
-    int rank = 0;
+    // outer part sorted by index: rank of each entry among the row's entries
+    constexpr int kPer = kOSlab / 32;
+    int v[kPer];
 #pragma unroll
-    for (int t = 0; t < 32; ++t) rank += __shfl_sync(kFull, v, t) < v;
-    if (lane < no) idx[off + ng + rank] = v;
+    for (int k = 0; k < kPer; ++k) {
+        const int s = k * 32 + lane;
+        v[k] = s < no ? __ldg(&oslab[i * kOSlab + s]) : 0x7fffffff;
+    }
+    int rank[kPer] = {};
+#pragma unroll
+    for (int k2 = 0; k2 < kPer; ++k2) {
+        if (k2 * 32 >= no) break;
+        for (int t = 0; t < 32; ++t) {
+            const int w = __shfl_sync(kFull, v[k2], t);
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) rank[k] += w < v[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+        if (k * 32 + lane < no) idx[off + ng + rank[k]] = v[k];
 }
 
 // Fallback (a row overflowed a slab): the full two-pass build below.

@@ -39,7 +39,7 @@ enum : unsigned {
     IF_SLAB_OVF = 1u,   // a row did not fit the gather/outer slabs: full CSR kernels run
 };
 constexpr int kGSlab = 128;  // gather-set slots per particle (>= n_target + n_tol)
-constexpr int kOSlab = 32;   // outer-set slots per particle
+constexpr int kOSlab = 96;   // outer-set slots per particle (patch max ~40, Evrard ~64)
 
 // Cell grid, computed on the device from the particle bounding box each build.
 struct Grid {

@@ -272,7 +272,8 @@ def test_slab_overflow_uses_full_build(B, orc):
     s, prm = ics.square_patch(17, seed=21)
     prm.n_target = 150
     o = orc.pipeline(prm, s)
-    ctx, arr, st = gpu_build(B, prm, s)
+    ctx, arr, st = gpu_build(B, prm, s, ctx=B.Context(len(s["x"]), nnz_capacity=260 * len(s["x"])))
+    assert st == B.SPH_OK
     assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
     off, idx, ng, order = ctx.neighbors_to_host()
     assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
