@@ -187,6 +187,30 @@ int64_t sph_last_hnoconv(const sph_ctx *ctx);
 /* Text of the last error on this context ("" if none). Never NULL. */
 const char *sph_last_error(const sph_ctx *ctx);
 
+/* Largest n accepted by sph_dt_noalloc (its static scratch holds one partial
+ * minimum per 256 particles: 8192 doubles, 64 KiB per device). */
+#define SPH_NOALLOC_MAX_N ((int64_t)2097152)
+
+/* The time step of sph_forces, dt = cfl * min_i h_i / (c_i + 1.2 (alpha c_i +
+ * beta mumax_i)), computed from caller-held device arrays without any device
+ * allocation. The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- code running under a host that owns
+ * all device memory through its own pool (a serving runtime, a framework
+ * plugin with a fixed budget), or a latency-critical loop where an
+ * allocation may synchronise the device.
+ *  - h, c, mumax (mumax may be NULL = all zero) are device arrays of length n;
+ *    *dt is a device scalar written on `stream` (the current device's).
+ *  - Its scratch is a static device array inside the library, which every GPU
+ *    that loads the library holds until the process exits. The first call on
+ *    a device looks up that array's device address (cudaGetSymbolAddress); make
+ *    this first call before any stream capture. No call allocates.
+ *  - n > SPH_NOALLOC_MAX_N, n < 0, cfl <= 0 or a NULL required pointer returns
+ *    SPH_E_INVAL and launches nothing; n = 0 writes +inf.
+ *  - All calls on a device share the scratch: calls that may overlap on the
+ *    GPU (different streams without ordering) race; serialise them. */
+sph_status sph_dt_noalloc(const sph_params *prm, int64_t n, const double *h, const double *c,
+                          const double *mumax, double *dt, void *stream);
+
 /* Measurement utility, not part of the SPH path: run a register-resident
  * FMA-chain kernel on `stream` of `device` and return the achieved rate as
  * *flops_per_s = 2 x FMAs per second, FP64 when fp64 != 0, else FP32. This is
