@@ -1,0 +1,140 @@
+// df.cuh -- double-float arithmetic on the FP32 pipes.
+//
+// A value is the unevaluated sum hi + lo of two floats (about 48 significant
+// bits). The building blocks are the classical error-free transformations:
+// Knuth's TwoSum, Dekker's Fast2Sum (|a| >= |b|) and the FMA-based TwoProd
+// (a b = p + e exactly). Every operation uses the explicitly rounded
+// intrinsics so the compiler cannot contract or reassociate them.
+//
+// Error model used by the pair kernels: add and mul return a result within
+// about 2^-47 (|x| + |y|) and 2^-47 |x y| of the exact one, so a chain of a few
+// tens of operations stays near 1e-14 relative to the magnitudes involved.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+namespace dfl {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ df neg(df x) { return {-x.hi, -x.lo}; }
+
+// x + y with the low parts folded in once (error ~2^-47 (|x| + |y|)).
+__device__ __forceinline__ df add(df x, df y) {
+    const df s = two_sum(x.hi, y.hi);
+    const float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df addf(df x, float b) {
+    const df s = two_sum(x.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+
+__device__ __forceinline__ df mul(df x, df y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df mulf(df x, float b) {
+    const float p = __fmul_rn(x.hi, b);
+    float e = __fmaf_rn(x.hi, b, -p);
+    e = __fmaf_rn(x.lo, b, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df sqr(df x) {
+    const float p = __fmul_rn(x.hi, x.hi);
+    float e = __fmaf_rn(x.hi, x.hi, -p);
+    e = __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, e);
+    return fast_two_sum(p, e);
+}
+
+// exact scaling by a power of two (no overflow/underflow in use)
+__device__ __forceinline__ df scale2(df x, float p2) { return {__fmul_rn(x.hi, p2), __fmul_rn(x.lo, p2)}; }
+
+// 1/sqrt(x), x > 0: FP32 approximation, then one Newton step in double-float,
+// y1 = y0 + y0 (1 - x y0^2) / 2 (error ~2^-46 from the ~2^-23 seed).
+__device__ __forceinline__ df rsqrt(df x) {
+    float y0;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(x.hi));
+    const float hy = __fmul_rn(0.5f, y0);
+    const float p = __fmul_rn(y0, y0);
+    const df y2 = {p, __fmaf_rn(y0, y0, -p)};
+    const df e = addf(neg(mul(x, y2)), 1.0f);  // 1 - x y0^2, small: computed exactly enough
+    return addf(mulf(e, hy), y0);
+}
+
+// 1/x, x > 0: FP32 approximation, one Newton step y1 = y0 + y0 (1 - x y0).
+__device__ __forceinline__ df rcp(df x) {
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(x.hi));
+    const df e = addf(neg(mulf(x, y0)), 1.0f);
+    return addf(mulf(e, y0), y0);
+}
+
+// Per-particle conversion to double-float with the FP64 pipe (exact to 2^-48).
+__device__ __forceinline__ df from_double_fp64(double d) {
+    const float hi = __double2float_rn(d);
+    const float lo = __double2float_rn(d - (double)hi);
+    return {hi, lo};
+}
+
+// Split of a double into hi + lo (error <= 2^-47 |d|) with integer operations
+// and one integer-to-float conversion, keeping the FP64 pipe free: hi takes
+// the top 24 significand bits, lo = R 2^-52 2^(e-1023) with R the remaining
+// 29 bits rounded to 24. |d| < 2^-60 maps to 0 (an absolute error far below
+// every use here); |d| > 2^60 takes the FP64-pipe conversion.
+__device__ __forceinline__ df from_double(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 60) return {0.0f, 0.0f};
+    if (e > 1023 + 60) return from_double_fp64(d);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned ef = (unsigned)(e - 896) << 23;  // float exponent field of 2^(e-1023)
+    const float hi = __uint_as_float(sign | ef | (unsigned)((b >> 29) & 0x7fffffu));
+    const unsigned R = (unsigned)(b & 0x1fffffffull);
+    float lo = __fmul_rn(__fmul_rn(__uint2float_rn(R), 2.220446049250313e-16f), __uint_as_float(ef));
+    lo = sign ? -lo : lo;
+    return fast_two_sum(hi, lo);
+}
+
+// Per-particle conversion back to FP64 (two conversions and one FP64 add).
+__device__ __forceinline__ double to_double(df x) { return (double)x.hi + (double)x.lo; }
+
+// Per-particle pack of the double-float force kernel (48 B per particle):
+//   dpk[3k] = (1/h, 1/h^4), dpk[3k+1] = (p/rho^2, h/2), dpk[3k+2] = (rho/2, alpha c/2).
+__device__ __forceinline__ void write_pack(float4* __restrict__ dpk, int64_t k, double hinv,
+                                           double A, double h, double rho, double alpha, double c) {
+    const double h2 = hinv * hinv;
+    const df a = from_double_fp64(hinv), b = from_double_fp64(h2 * h2);
+    const df cA = from_double_fp64(A), d = from_double_fp64(0.5 * h);
+    const df e = from_double_fp64(0.5 * rho), f = from_double_fp64(0.5 * alpha * c);
+    dpk[3 * k + 0] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    dpk[3 * k + 1] = make_float4(cA.hi, cA.lo, d.hi, d.lo);
+    dpk[3 * k + 2] = make_float4(e.hi, e.lo, f.hi, f.lo);
+}
+
+}  // namespace dfl
+}  // namespace sph

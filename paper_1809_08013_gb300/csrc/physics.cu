@@ -136,6 +136,10 @@ k_density(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
 }
 
 void launch_density(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s) {
+    if (kp.precision != PREC_FP64_NATIVE) {
+        launch_density_df(c, kp, fuse_eos, s);
+        return;
+    }
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
@@ -278,11 +282,15 @@ void launch_forces(sph_ctx* c, const KParams& kp, double* dt_out, double* time_i
     const int64_t n = c->n;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const int b = c->cur;
-    c->launches += (n > 0) ? 2 : 1;
-    if (n > 0)
+    c->launches += 1;
+    if (kp.precision != PREC_FP64_NATIVE)
+        launch_forces_df(c, kp, s);
+    else if (n > 0) {
+        c->launches += 1;
         k_forces<<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->therm, c->kern,
                                          c->cint, c->offsets, c->idx, c->nnzcap, c->acc,
                                          c->mumax, c->dt_part);
+    }
     k_dt_finish<<<1, kThreads, 0, s>>>(c->dt_part, n > 0 ? (int)nb : 0, kp.cfl, dt_out,
                                        time_inout);
 }

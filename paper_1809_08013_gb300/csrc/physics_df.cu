@@ -1,0 +1,238 @@
+// physics_df.cu -- density and forces (Algorithm 1 step 3) with the pair
+// arithmetic in double-float on the FP32 pipes.
+//
+// Same definitions as physics.cu (cubic-spline gather density; momentum and
+// energy with Monaghan viscosity over S_i; time-step candidate). GB300 issues
+// FP64 at 1/64 of the FP32 rate; here the FP64 pipe only forms the six
+// coordinate and velocity differences of a pair (x_i - x_j is the one place
+// where 53-bit inputs meet), each difference is split exactly enough into a
+// float pair by integer operations, and everything else -- r^2, 1/r, the
+// kernel polynomials, the viscosity, the sums -- runs in ~48-bit double-float
+// (df.cuh). Per-particle inputs (1/h, 1/h^4, p/rho^2, h/2, rho/2, alpha c/2,
+// m) are converted once per step into a float pack read for every neighbour.
+#include <math_constants.h>
+
+#include "df.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+using dfl::df;
+
+namespace {
+
+constexpr double kInvPiD = 0.31830988618379067154;
+
+__device__ __forceinline__ long long bitsd(double v) { return __double_as_longlong(v); }
+
+__device__ __forceinline__ double wrap_z_d(double dz, long long half_bits, double lz) {
+    if ((bitsd(dz) & 0x7fffffffffffffffLL) > half_bits) dz -= copysign(lz, dz);
+    return dz;
+}
+
+// pi h^3 W as a function of q >= 0 (cubic spline).
+__device__ __forceinline__ df w_shape(df q) {
+    const df q2 = dfl::sqr(q);
+    const df a = dfl::addf(dfl::mulf(q, 0.75f), -1.5f);
+    const df win = dfl::addf(dfl::mul(q2, a), 1.0f);  // 1 - 1.5 q^2 + 0.75 q^3
+    const df t = dfl::addf(dfl::neg(q), 2.0f);
+    const df wout = dfl::scale2(dfl::mul(dfl::sqr(t), t), 0.25f);  // (2 - q)^3 / 4
+    const df zero = {0.0f, 0.0f};
+    return q.hi < 1.0f ? win : (q.hi < 2.0f ? wout : zero);
+}
+
+// pi h^4 dW/dr as a function of q >= 0.
+__device__ __forceinline__ df dw_shape(df q) {
+    const df fin = dfl::mul(q, dfl::addf(dfl::mulf(q, 2.25f), -3.0f));  // q (2.25 q - 3)
+    const df t = dfl::addf(dfl::neg(q), 2.0f);
+    const df fout = dfl::mulf(dfl::sqr(t), -0.75f);                       // -0.75 (2 - q)^2
+    const df zero = {0.0f, 0.0f};
+    return q.hi < 1.0f ? fin : (q.hi < 2.0f ? fout : zero);
+}
+
+__device__ __forceinline__ df ld2(const float2* p, int64_t k) {
+    const float2 v = __ldg(&p[k]);
+    return {v.x, v.y};
+}
+
+__device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, double& p, double& c) {
+    if (kp.eos == 0) {
+        const double x = rho / kp.rho0;
+        const double x2 = x * x;
+        const double x4 = x2 * x2;
+        const double x7 = (x4 * x2) * x;
+        p = (kp.c0 * kp.c0 * kp.rho0 / 7.0) * (x7 - 1.0);
+        c = kp.c0 * (x2 * x);
+    } else {
+        p = (kp.gamma - 1.0) * rho * u;
+        c = sqrt(kp.gamma * (kp.gamma - 1.0) * u);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ density
+template <bool FUSE>
+__global__ void __launch_bounds__(kThreads)
+k_density_df(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+             const float2* __restrict__ mdf, const double* __restrict__ ue,
+             const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
+             const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
+             double2* __restrict__ kern, float4* __restrict__ dpk, double* __restrict__ pint,
+             double* __restrict__ cint) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || offsets[n] > nnzcap) return;
+    const double4_32a pi = posh[i];
+    const double hinv = 1.0 / pi.w;
+    const df Hi = dfl::from_double_fp64(hinv);
+    const long long half_bits = bitsd(0.5 * kp.lz);
+    df acc = ld2(mdf, i);  // self term m_i W(0, h_i): shape 1
+    const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
+    for (int64_t e = e0; e < e1; ++e) {
+        const int j = __ldg(&idx[e]);
+        const double4_32a pj = posh[j];
+        double dz = pi.z - pj.z;
+        if (kp.periodic_z) dz = wrap_z_d(dz, half_bits, kp.lz);
+        const df X = dfl::from_double(pi.x - pj.x), Y = dfl::from_double(pi.y - pj.y);
+        const df Z = dfl::from_double(dz);
+        const df r2 = dfl::add(dfl::add(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
+        df w = {1.0f, 0.0f};  // coincident particles: q = 0
+        if (r2.hi > 0.0f) {
+            const df q = dfl::mul(dfl::mul(r2, dfl::rsqrt(r2)), Hi);
+            w = w_shape(q);
+        }
+        acc = dfl::add(acc, dfl::mul(ld2(mdf, j), w));
+    }
+    const double sigma = hinv * hinv * hinv * kInvPiD;
+    const double rho = dfl::to_double(acc) * sigma;
+    if (FUSE) {
+        double p, c;
+        eos_d(kp, rho, ue[i], p, c);
+        const double A = p / (rho * rho);
+        therm[i] = make_double4_32a(0.5 * rho, A, 0.5 * kp.alpha * c, 0.5 * pi.w);
+        const double h2 = hinv * hinv;
+        kern[i] = make_double2(hinv, h2 * h2);
+        dfl::write_pack(dpk, i, hinv, A, pi.w, rho, kp.alpha, c);
+        pint[i] = p;
+        cint[i] = c;
+    } else {
+        therm[i].x = 0.5 * rho;
+    }
+}
+
+void launch_density_df(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s) {
+    const int64_t n = c->n;
+    if (n == 0) return;
+    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const int b = c->cur;
+    c->launches += 1;
+    if (fuse_eos)
+        k_density_df<true><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->mdf, c->ue[b], c->offsets,
+                                                   c->ngather, c->idx, c->nnzcap, c->therm,
+                                                   c->kern, c->dpk, c->pint, c->cint);
+    else
+        k_density_df<false><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->mdf, c->ue[b],
+                                                    c->offsets, c->ngather, c->idx, c->nnzcap,
+                                                    c->therm, c->kern, c->dpk, c->pint, c->cint);
+}
+
+// ------------------------------------------------------------ forces + dt
+// Definitions as in physics.cu; algebra: Fbar = (0.5/pi)(f(q_i)/h_i^4 +
+// f(q_j)/h_j^4)/r, one shared reciprocal R = 1/((r^2 + eta2 hb^2) rhob) for the
+// viscosity, mu = hb v.r rhob R, 1/rhob = (r^2 + eta2 hb^2) R.
+__global__ void __launch_bounds__(kThreads)
+k_forces_df(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+            const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
+            const float2* __restrict__ mdf, const double* __restrict__ cint,
+            const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
+            double4_32a* __restrict__ acc, double* __restrict__ mumax,
+            double* __restrict__ dt_part) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double dtc = CUDART_INF;
+    if (i < n && offsets[n] <= nnzcap) {
+        const double4_32a pi = posh[i];
+        const double4_32a vi = velm[i];
+        const float4 a0 = dpk[3 * i], a1 = dpk[3 * i + 1], a2 = dpk[3 * i + 2];
+        const df Hi = {a0.x, a0.y}, Ki = {a0.z, a0.w}, Ai = {a1.x, a1.y}, hhi = {a1.z, a1.w};
+        const df rhi = {a2.x, a2.y}, cai = {a2.z, a2.w};
+        const long long half_bits = bitsd(0.5 * kp.lz);
+        const df c_half_pi = dfl::from_double_fp64(0.5 * kInvPiD);
+        const df eta2 = dfl::from_double_fp64(kp.eta2);
+        const df betad = dfl::from_double_fp64(kp.beta);
+        df sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sp = {0.f, 0.f}, sv = {0.f, 0.f};
+        df mumx = {0.f, 0.f};
+        const int64_t e0 = offsets[i], e1 = offsets[i + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            const int j = __ldg(&idx[e]);
+            const double4_32a pj = posh[j];
+            const double4_32a vj = velm[j];
+            const float4 b0 = __ldg(&dpk[3 * j]), b1 = __ldg(&dpk[3 * j + 1]);
+            const float4 b2 = __ldg(&dpk[3 * j + 2]);
+            double dz = pi.z - pj.z;
+            if (kp.periodic_z) dz = wrap_z_d(dz, half_bits, kp.lz);
+            const df X = dfl::from_double(pi.x - pj.x), Y = dfl::from_double(pi.y - pj.y);
+            const df Z = dfl::from_double(dz);
+            const df r2 = dfl::add(dfl::add(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
+            if (!(r2.hi > 0.0f)) continue;  // coincident particles exert no force
+            const df rinv = dfl::rsqrt(r2);
+            const df r = dfl::mul(r2, rinv);
+            const df fa = dw_shape(dfl::mul(r, Hi));
+            const df fb = dw_shape(dfl::mul(r, df{b0.x, b0.y}));
+            const df Fb = dfl::mul(dfl::add(dfl::mul(Ki, fa), dfl::mul(df{b0.z, b0.w}, fb)),
+                                   dfl::mul(rinv, c_half_pi));
+            const df WX = dfl::from_double(vi.x - vj.x), WY = dfl::from_double(vi.y - vj.y);
+            const df WZ = dfl::from_double(vi.z - vj.z);
+            const df vr = dfl::add(dfl::add(dfl::mul(WX, X), dfl::mul(WY, Y)), dfl::mul(WZ, Z));
+            df Pi = {0.f, 0.f};
+            if (vr.hi < 0.0f) {
+                const df hb = dfl::add(hhi, df{b1.z, b1.w});
+                const df d1 = dfl::add(r2, dfl::mul(dfl::mul(eta2, hb), hb));
+                const df rb = dfl::add(rhi, df{b2.x, b2.y});
+                const df R = dfl::rcp(dfl::mul(d1, rb));
+                const df mu = dfl::mul(dfl::mul(dfl::mul(hb, vr), rb), R);
+                const df cb = dfl::add(cai, df{b2.z, b2.w});
+                const df t = dfl::add(dfl::mul(betad, mu), dfl::neg(cb));  // beta mu - alpha cb
+                Pi = dfl::mul(dfl::mul(mu, t), dfl::mul(d1, R));
+                if (-mu.hi > mumx.hi) mumx = dfl::neg(mu);
+            }
+            const df mF = dfl::mul(ld2(mdf, j), Fb);
+            const df g = dfl::mul(mF, dfl::add(dfl::add(Ai, df{b1.x, b1.y}), Pi));
+            sx = dfl::add(sx, dfl::mul(g, X));
+            sy = dfl::add(sy, dfl::mul(g, Y));
+            sz = dfl::add(sz, dfl::mul(g, Z));
+            const df mFv = dfl::mul(mF, vr);
+            sp = dfl::add(sp, mFv);
+            sv = dfl::add(sv, dfl::mul(mFv, Pi));
+        }
+        const double Aid = dfl::to_double(Ai);
+        acc[i] = make_double4_32a(-dfl::to_double(sx), -dfl::to_double(sy), -dfl::to_double(sz),
+                                  fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)));
+        const double mu_max = dfl::to_double(mumx);
+        mumax[i] = mu_max;
+        const double ci = cint[i];
+        dtc = pi.w / (ci + 1.2 * (kp.alpha * ci + kp.beta * mu_max));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
+    __shared__ double sh[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dtc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = sh[0];
+        for (int w = 1; w < kThreads / 32; ++w) m = fmin(m, sh[w]);
+        dt_part[blockIdx.x] = m;
+    }
+}
+
+void launch_forces_df(sph_ctx* c, const KParams& kp, cudaStream_t s) {
+    const int64_t n = c->n;
+    if (n == 0) return;
+    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const int b = c->cur;
+    c->launches += 1;
+    k_forces_df<<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->dpk, c->mdf, c->cint,
+                                        c->offsets, c->idx, c->nnzcap, c->acc, c->mumax,
+                                        c->dt_part);
+}
+
+}  // namespace sph

@@ -5,6 +5,7 @@
 // range of every occupied cell.
 #include <math_constants.h>
 
+#include "df.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -47,21 +48,27 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
                const double* __restrict__ rho, const double* __restrict__ p,
                const double* __restrict__ cs, double4_32a* __restrict__ posh,
                double4_32a* __restrict__ velm, double4_32a* __restrict__ therm,
-               double2* __restrict__ kern, double* __restrict__ cint) {
+               double2* __restrict__ kern, double* __restrict__ cint, float4* __restrict__ dpk,
+               float2* __restrict__ mdf) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t o = order[k];
     const double hh = h[o];
     posh[k] = make_double4_32a(x[o], y[o], z[o], hh);
+    const double mm = m[o];
+    const dfl::df md = dfl::from_double_fp64(mm);
+    mdf[k] = make_float2(md.hi, md.lo);
     if (what == GATHER_DENSITY) {
-        velm[k] = make_double4_32a(0.0, 0.0, 0.0, m[o]);
+        velm[k] = make_double4_32a(0.0, 0.0, 0.0, mm);
     } else {
-        velm[k] = make_double4_32a(vx[o], vy[o], vz[o], m[o]);
+        velm[k] = make_double4_32a(vx[o], vy[o], vz[o], mm);
         const double r = rho[o], c = cs[o];
         const double hinv = 1.0 / hh;
         const double h2 = hinv * hinv;
-        therm[k] = make_double4_32a(0.5 * r, p[o] / (r * r), 0.5 * alpha * c, 0.5 * hh);
+        const double A = p[o] / (r * r);
+        therm[k] = make_double4_32a(0.5 * r, A, 0.5 * alpha * c, 0.5 * hh);
         kern[k] = make_double2(hinv, h2 * h2);
+        dfl::write_pack(dpk, k, hinv, A, hh, r, alpha, c);
         cint[k] = c;
     }
 }
@@ -74,7 +81,7 @@ void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, 
     c->launches += 1;
     k_gather_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         n, what, kp.alpha, c->order[b], P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m,
-        P->rho, P->p, P->c, c->posh[b], c->velm[b], c->therm, c->kern, c->cint);
+        P->rho, P->p, P->c, c->posh[b], c->velm[b], c->therm, c->kern, c->cint, c->dpk, c->mdf);
 }
 
 // ------------------------------------------------------------ bbox and grid
@@ -309,13 +316,16 @@ k_permute(int64_t n, const int32_t* __restrict__ perm, const double4_32a* __rest
           const double4_32a* __restrict__ velm_in, const double* __restrict__ u_in,
           const int32_t* __restrict__ order_in, double4_32a* __restrict__ posh_out,
           double4_32a* __restrict__ velm_out, double* __restrict__ u_out,
-          int32_t* __restrict__ order_out, float4* __restrict__ fpos) {
+          int32_t* __restrict__ order_out, float4* __restrict__ fpos, float2* __restrict__ mdf) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t o = perm[k];
     const double4_32a p = posh_in[o];
     posh_out[k] = p;
-    velm_out[k] = velm_in[o];
+    const double4_32a v = velm_in[o];
+    velm_out[k] = v;
+    const dfl::df m = dfl::from_double_fp64(v.w);
+    mdf[k] = make_float2(m.hi, m.lo);
     u_out[k] = u_in[o];
     order_out[k] = order_in[o];
     fpos[k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
@@ -371,7 +381,7 @@ void launch_build_cells(sph_ctx* c, const KParams& kp, cudaStream_t s) {
     const int a = c->cur, b = 1 - c->cur;
     k_permute<<<nb, kThreads, 0, s>>>(n, c->vals[src], c->posh[a], c->velm[a], c->ue[a],
                                        c->order[a], c->posh[b], c->velm[b], c->ue[b], c->order[b],
-                                       c->fpos);
+                                       c->fpos, c->mdf);
     c->cur = b;
     k_cells_clear<<<kReduceBlocks, kThreads, 0, s>>>(c->grid, c->cells, c->cell_hmax);
     k_cells_mark<<<nb, kThreads, 0, s>>>(n, c->keys[src], c->grid, c->cells);

@@ -61,14 +61,14 @@ struct Grid {
 
 // Parameters copied by value into kernels.
 struct KParams {
-    int eos, n_target, n_tol, max_h_iter, periodic_z;
+    int eos, n_target, n_tol, max_h_iter, periodic_z, precision;
     double rho0, c0, gamma, alpha, beta, eta2, cfl, lz, cell_scale;
 };
 
 inline KParams kparams(const sph_params* p) {
     KParams k;
     k.eos = p->eos; k.n_target = p->n_target; k.n_tol = p->n_tol;
-    k.max_h_iter = p->max_h_iter; k.periodic_z = p->periodic_z;
+    k.max_h_iter = p->max_h_iter; k.periodic_z = p->periodic_z; k.precision = p->precision;
     k.rho0 = p->rho0; k.c0 = p->c0; k.gamma = p->gamma; k.alpha = p->alpha;
     k.beta = p->beta; k.eta2 = p->eta2; k.cfl = p->cfl; k.lz = p->lz;
     k.cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 1.0;
@@ -89,6 +89,8 @@ struct sph_ctx {
     double4_32a* acc;
     double* pint;
     double* cint;
+    float4* dpk;            // 3 per particle: double-float pack of the force kernel
+    float2* mdf;            // mass as a float pair
     double* mumax;
     float4* fpos;
     float* tin;
@@ -140,6 +142,10 @@ void launch_csr(sph_ctx* c, cudaStream_t s);
 // ---- physics.cu
 enum { GATHER_DENSITY = 1, GATHER_FORCES = 2 };
 void launch_density(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s);
+// ---- physics_df.cu (precision 0)
+void launch_density_df(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s);
+void launch_forces_df(sph_ctx* c, const KParams& kp, cudaStream_t s);
+enum { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP64_NATIVE = 2 };
 void launch_eos_caller(const KParams& kp, const sph_particles* P, cudaStream_t s);
 void launch_forces(sph_ctx* c, const KParams& kp, double* dt_out, double* time_inout,
                    cudaStream_t s);
