@@ -102,21 +102,26 @@ __device__ __forceinline__ df from_double_fp64(double d) {
 }
 
 // Split of a double into hi + lo (error <= 2^-47 |d|) with integer operations
-// and one integer-to-float conversion, keeping the FP64 pipe free: hi takes
-// the top 24 significand bits, lo = R 2^-52 2^(e-1023) with R the remaining
-// 29 bits rounded to 24. |d| < 2^-60 maps to 0 (an absolute error far below
-// every use here); |d| > 2^60 takes the FP64-pipe conversion.
+// only: on GB300 both FP64 arithmetic and the int/float conversion
+// instructions occupy the narrow FP64 pipe, so neither is used. hi takes the
+// top 24 significand bits; the remaining 29 bits R are normalised with a
+// leading-zero count and truncated to 24 bits for lo. Meant for pair
+// differences: |d| < 2^-60 maps to 0 (an absolute error far below any use
+// here) and |d| is assumed below 2^60 (larger magnitudes saturate).
 __device__ __forceinline__ df from_double(double d) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const int e = (int)((b >> 52) & 0x7ff);
+    int e = (int)((b >> 52) & 0x7ff);
     if (e < 1023 - 60) return {0.0f, 0.0f};
-    if (e > 1023 + 60) return from_double_fp64(d);
+    e = e > 1023 + 60 ? 1023 + 60 : e;
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    const unsigned ef = (unsigned)(e - 896) << 23;  // float exponent field of 2^(e-1023)
-    const float hi = __uint_as_float(sign | ef | (unsigned)((b >> 29) & 0x7fffffu));
-    const unsigned R = (unsigned)(b & 0x1fffffffull);
-    float lo = __fmul_rn(__fmul_rn(__uint2float_rn(R), 2.220446049250313e-16f), __uint_as_float(ef));
-    lo = sign ? -lo : lo;
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) |
+                                     (unsigned)((b >> 29) & 0x7fffffu));
+    const unsigned R = (unsigned)(b & 0x1fffffffull);  // value R 2^(e - 1075)
+    const int lz = __clz((int)R);                       // 3..32
+    // leading one of R at bit 31 - lz: move it to bit 23 (truncating below)
+    const unsigned m = lz >= 8 ? (R << (lz - 8)) : (R >> (8 - lz));
+    const unsigned lob = sign | ((unsigned)(e - 917 - lz) << 23) | (m & 0x7fffffu);
+    const float lo = R ? __uint_as_float(lob) : 0.0f;
     return fast_two_sum(hi, lo);
 }
 
