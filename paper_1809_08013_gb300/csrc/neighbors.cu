@@ -144,6 +144,86 @@ __device__ __forceinline__ float reach_f32(double h) {
     return 2.0f * hi * 1.0001f;
 }
 
+// Cell index range overlapping [a, b] along axis d (clamped); along the
+// periodic z axis an unclamped range (wrapped by the caller) or the whole axis.
+__device__ __forceinline__ void box_range(float a, float b, const Grid* __restrict__ g, int d,
+                                          int& k0, int& k1) {
+    const float inv = g->invwf[d], s = g->slop[d];
+    const int n = g->n[d];
+    if (d == 2 && g->periodic_z) {
+        const float fa = floorf((a - s + g->halflzf) * inv);
+        const float fb = floorf((b + s + g->halflzf) * inv);
+        if (!(fb - fa + 1.0f < (float)n)) {
+            k0 = 0;
+            k1 = n - 1;
+            return;
+        }
+        k0 = (int)fa;
+        k1 = (int)fb;
+        return;
+    }
+    const float lo = g->lof[d];
+    float fa = floorf((a - s - lo) * inv);
+    float fb = floorf((b + s - lo) * inv);
+    fa = fminf(fmaxf(fa, 0.0f), (float)n);
+    fb = fmaxf(fminf(fb, (float)(n - 1)), -1.0f);
+    k0 = (int)fa;
+    k1 = (int)fb;
+}
+
+__device__ __forceinline__ float wmin(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ float wmax(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// One warp, 32 particles (one per lane): walk the cells of the union of the
+// active lanes' boxes [q - R, q + R] in warp-uniform loops, skipping a cell
+// no active lane wants (keep), staging each cell's particles 32 at a time in
+// shared memory; every lane then sees every staged candidate (visit). All
+// lanes must call this together.
+template <class Keep, class Visit>
+__device__ __forceinline__ void warp_walk(const Grid* __restrict__ g, const int2* __restrict__ cells,
+                                          const float4* __restrict__ fpos, float4* s_f,
+                                          const float4& q, float R, bool active, Keep&& keep,
+                                          Visit&& visit) {
+    const int lane = threadIdx.x & 31;
+    const float lx = wmin(active ? q.x - R : CUDART_INF_F), hx = wmax(active ? q.x + R : -CUDART_INF_F);
+    if (!(lx <= hx)) return;  // no active lane
+    const float ly = wmin(active ? q.y - R : CUDART_INF_F), hy = wmax(active ? q.y + R : -CUDART_INF_F);
+    const float lz = wmin(active ? q.z - R : CUDART_INF_F), hz = wmax(active ? q.z + R : -CUDART_INF_F);
+    int x0, x1, y0, y1, z0, z1;
+    box_range(lx, hx, g, 0, x0, x1);
+    box_range(ly, hy, g, 1, y0, y1);
+    box_range(lz, hz, g, 2, z0, z1);
+    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    const bool per = g->periodic_z != 0;
+    for (int kz = z0; kz <= z1; ++kz) {
+        const int cz = per ? wrapi(kz, nz) : kz;
+        for (int ky = y0; ky <= y1; ++ky) {
+            const long long row = ((long long)cz * ny + ky) * nx;
+            for (int kx = x0; kx <= x1; ++kx) {
+                const int2 se = __ldg(&cells[row + kx]);
+                if (se.y <= se.x) continue;
+                if (!__any_sync(kFull, active && keep(kx, ky, kz))) continue;
+                for (int base = se.x; base < se.y; base += 32) {
+                    const int j = base + lane;
+                    if (j < se.y) s_f[lane] = __ldg(&fpos[j]);
+                    __syncwarp();
+                    const int cnt = min(32, se.y - base);
+                    for (int k = 0; k < cnt; ++k) visit(base + k, s_f[k]);
+                    __syncwarp();
+                }
+            }
+        }
+    }
+}
+
 // One warp, one particle: enumerate the candidates of every cell overlapping
 // the box [q - R, q + R] as one flat list. Up to 32 cells are fetched at once
 // (one per lane), a warp scan of their sizes gives each cell's offset, and the
@@ -220,72 +300,174 @@ __device__ __forceinline__ void particle_pass(const Grid* __restrict__ g,
 }
 
 // ------------------------------------------------------------ h search
+// Phase 1: one warp per 32 consecutive (Morton-sorted) particles, one lane
+// per particle. Each pass counts N_i(h) for every still-searching lane over
+// the union of their query boxes (candidates staged once for the warp) and
+// records the gather set in the slab. While more than kDeferLanes lanes are
+// still searching the warp keeps going; the stragglers are then handed, with
+// their bisection state, to the per-particle kernel below through a worklist.
+constexpr int kDeferLanes = 8;
+
+__global__ void __launch_bounds__(kThreads, 2)
+k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
+          const float4* __restrict__ fpos, const int2* __restrict__ cells,
+          int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ gslab,
+          double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
+          int32_t* __restrict__ wl, unsigned* __restrict__ status) {
+    __shared__ float4 s_f[kThreads / 32][32];
+    const int warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
+    float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        pi = posh[i];
+        fi = fpos[i];
+    }
+    double h = pi.w, lo = 0.0, hi = CUDART_INF;
+    const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
+    int cnt = 0, it = 0;
+    bool active = valid && kp.max_h_iter > 0, conv = false, deferred = false;
+    int32_t* slab = gslab + (valid ? i : 0) * kGSlab;
+    for (int pass = 0;; ++pass) {  // pass is warp-uniform; it (per lane) stops at convergence
+        const unsigned am = __ballot_sync(kFull, active);
+        if (!am) break;
+        if (pass > 0 && __popc(am) <= kDeferLanes) {
+            if (active) {
+                deferred = true;
+                active = false;
+                posh[i].w = h;
+                hs_lo[i] = lo;
+                hs_hi[i] = hi;
+                hs_it[i] = it;
+                wl[atomicAdd(&status[3], 1u)] = (int32_t)i;
+            }
+            break;
+        }
+        const double R = 2.0 * h;
+        const Thr t = thresholds(R, g);
+        const float Rq = reach_f32(h);
+        double R2 = -1.0;
+        int c = 0;
+        warp_walk(
+            g, cells, fpos, s_f[warp], fi, Rq, active,
+            [&](int kx, int ky, int kz) {
+                const float gx = axis_gap(fi.x, kx, g, 0), gy = axis_gap(fi.y, ky, g, 1);
+                const float gz = g->periodic_z ? 0.0f : axis_gap(fi.z, kz, g, 2);
+                return fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < Rq * Rq;
+            },
+            [&](int j, const float4& fj) {
+                if (!active || j == i) return;
+                const float r2f = f_r2(fi, fj, g);
+                bool in = r2f < t.tin;
+                if (!in && r2f <= t.tout) {
+                    if (R2 < 0.0) R2 = __dmul_rn(R, R);
+                    in = exact_r2(pi, posh[j], g) < R2;
+                }
+                if (in) {
+                    if (c < kGSlab) slab[c] = j;
+                    ++c;
+                }
+            });
+        if (active) {
+            cnt = c;
+            ++it;
+            if (cnt >= lowb && cnt <= highb) {
+                conv = true;
+                active = false;
+            } else if (it >= kp.max_h_iter) {
+                active = false;
+            } else if (cnt < lowb) {
+                lo = h;
+                h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+            } else {
+                hi = h;
+                h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+            }
+        }
+    }
+    if (!valid || deferred) return;
+    posh[i].w = h;
+    nnb[i] = cnt;
+    ngather[i] = cnt;
+    if (cnt > kGSlab) atomicOr(&status[2], (unsigned)IF_SLAB_OVF);
+    if (!conv) {
+        atomicOr(&status[0], (unsigned)ST_HNOCONV);
+        atomicAdd(&status[1], 1u);
+    }
+}
+
+// Phase 2: one warp per handed-over particle (persistent grid over the
+// worklist), continuing its bisection where phase 1 stopped.
 __global__ void __launch_bounds__(kThreads)
-k_h_iterate(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
+k_h_iterate(const Grid* __restrict__ g, KParams kp, double4_32a* posh,
             const float4* __restrict__ fpos, const int2* __restrict__ cells,
             int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
-            int32_t* __restrict__ gslab, unsigned* __restrict__ status) {
+            int32_t* __restrict__ gslab, const double* __restrict__ hs_lo,
+            const double* __restrict__ hs_hi, const int32_t* __restrict__ hs_it,
+            const int32_t* __restrict__ wl, unsigned* __restrict__ status) {
     __shared__ int s_start[kThreads / 32][32], s_pref[kThreads / 32][32];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;  // warp-uniform
-    const double4_32a pi = posh[i];
-    const float4 fi = fpos[i];
-    double h = pi.w, lo = 0.0, hi = CUDART_INF;
-    const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
-    int cnt = 0;
-    bool conv = false;
+    const unsigned count = *(volatile unsigned*)&status[3];
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const unsigned lt = (1u << lane) - 1u;
-    int32_t* slab = gslab + i * kGSlab;
-    for (int it = 0; it < kp.max_h_iter; ++it) {
-        const double R = 2.0 * h;
-        const Thr t = thresholds(R, g);
-        double R2 = -1.0;  // (2h)^2 in FP64, formed on first use
-        int c = 0;
-        // every count also records the gather set in the slab; the last count
-        // (the converged one, or the last allowed) leaves N_i(h_final) there
-        particle_pass<1>(g, cells, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
-                         [&](bool valid, int j) {
-                             bool in = false, bd = false;
-                             if (valid && j != i) {
-                                 const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
-                                 in = r2f < t.tin;
-                                 bd = !in && r2f <= t.tout;
-                             }
-                             if (__any_sync(kFull, bd) && bd) {
-                                 if (R2 < 0.0) R2 = __dmul_rn(R, R);
-                                 in = exact_r2(pi, posh[j], g) < R2;
-                             }
-                             const unsigned m = __ballot_sync(kFull, in);
-                             if (in) {
-                                 const int q = c + __popc(m & lt);
-                                 if (q < kGSlab) slab[q] = j;
-                             }
-                             c += __popc(m);
-                         });
-        cnt = c;
-        if (cnt >= lowb && cnt <= highb) {
-            conv = true;
-            break;
+    const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nwarps) {
+        const int64_t i = wl[w];
+        const double4_32a pi = posh[i];
+        const float4 fi = fpos[i];
+        double h = pi.w, lo = hs_lo[i], hi = hs_hi[i];
+        int cnt = 0;
+        bool conv = false;
+        int32_t* slab = gslab + i * kGSlab;
+        for (int it = hs_it[i]; it < kp.max_h_iter; ++it) {
+            const double R = 2.0 * h;
+            const Thr t = thresholds(R, g);
+            double R2 = -1.0;  // (2h)^2 in FP64, formed on first use
+            int c = 0;
+            particle_pass<1>(g, cells, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
+                             [&](bool valid, int j) {
+                                 bool in = false, bd = false;
+                                 if (valid && j != i) {
+                                     const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
+                                     in = r2f < t.tin;
+                                     bd = !in && r2f <= t.tout;
+                                 }
+                                 if (__any_sync(kFull, bd) && bd) {
+                                     if (R2 < 0.0) R2 = __dmul_rn(R, R);
+                                     in = exact_r2(pi, posh[j], g) < R2;
+                                 }
+                                 const unsigned m = __ballot_sync(kFull, in);
+                                 if (in) {
+                                     const int q = c + __popc(m & lt);
+                                     if (q < kGSlab) slab[q] = j;
+                                 }
+                                 c += __popc(m);
+                             });
+            cnt = c;
+            if (cnt >= lowb && cnt <= highb) {
+                conv = true;
+                break;
+            }
+            if (it == kp.max_h_iter - 1) break;
+            if (cnt < lowb) {
+                lo = h;
+                h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+            } else {
+                hi = h;
+                h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+            }
         }
-        if (it == kp.max_h_iter - 1) break;
-        if (cnt < lowb) {
-            lo = h;
-            h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
-        } else {
-            hi = h;
-            h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
-        }
-    }
-    if (lane == 0) {
-        posh[i].w = h;
-        nnb[i] = cnt;
-        ngather[i] = cnt;
-        if (cnt > kGSlab) atomicOr(&status[2], (unsigned)IF_SLAB_OVF);
-        if (!conv) {
-            atomicOr(&status[0], (unsigned)ST_HNOCONV);
-            atomicAdd(&status[1], 1u);
+        if (lane == 0) {
+            posh[i].w = h;
+            nnb[i] = cnt;
+            ngather[i] = cnt;
+            if (cnt > kGSlab) atomicOr(&status[2], (unsigned)IF_SLAB_OVF);
+            if (!conv) {
+                atomicOr(&status[0], (unsigned)ST_HNOCONV);
+                atomicAdd(&status[1], 1u);
+            }
         }
     }
 }
@@ -509,11 +691,13 @@ void launch_h_search(sph_ctx* c, const KParams& kp, cudaStream_t s) {
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
-    const unsigned nbw = (unsigned)((n * 32 + kThreads - 1) / kThreads);  // one warp per particle
     double4_32a* posh = c->posh[c->cur];
-    c->launches += 3;
-    k_h_iterate<<<nbw, kThreads, 0, s>>>(n, c->grid, kp, posh, c->fpos, c->cells, c->nnb,
-                                         c->ngather, c->gslab, c->status);
+    c->launches += 4;
+    k_h_union<<<nb, kThreads, 0, s>>>(n, c->grid, kp, posh, c->fpos, c->cells, c->nnb, c->ngather,
+                                      c->gslab, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->status);
+    k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(c->grid, kp, posh, c->fpos, c->cells,
+                                                       c->nnb, c->ngather, c->gslab, c->hs_lo,
+                                                       c->hs_hi, c->hs_it, c->wl, c->status);
     k_finalize_h<<<nb, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->ocnt);
     k_cell_hmax<<<kReduceBlocks, kThreads, 0, s>>>(c->grid, c->grid, c->cells, posh, c->cell_hmax);
 }

@@ -150,6 +150,7 @@ k_grid_setup(const double* __restrict__ part, int nb, int64_t n, KParams kp, int
         for (int d = 0; d < 3; ++d) { mn[d] = 0.0; mx[d] = 0.0; }
     }
     status[2] = 0u;
+    status[3] = 0u;
     const double hmean = n > 0 ? r[7] / (double)n : 1.0;
     double w = 2.0 * hmean * kp.cell_scale;
     if (!(w > 0.0) || !isfinite(w)) w = 1.0;

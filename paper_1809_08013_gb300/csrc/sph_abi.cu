@@ -89,7 +89,7 @@ void free_all(sph_ctx* c) {
                     c->therm, c->kern, c->acc, c->pint, c->cint, c->dpk, c->mdf, c->mumax, c->fpos, c->tin, c->order[0],
                     c->order[1], c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist,
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
-                    c->offsets, c->row_part, c->idx, c->gslab, c->oslab, c->ocnt, c->red_part, c->dt_part, c->grid,
+                    c->offsets, c->row_part, c->idx, c->gslab, c->oslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -229,6 +229,7 @@ sph_status sph_ctx_create(sph_ctx** out, int64_t ncap, int64_t nnzcap, int devic
          dalloc(&c->idx, (size_t)nnzcap) && dalloc(&c->red_part, (size_t)kReduceBlocks * 8) &&
          dalloc(&c->dt_part, nfb) && dalloc(&c->grid, 1) && dalloc(&c->status, 4) &&
          dalloc(&c->gslab, N * kGSlab) && dalloc(&c->oslab, N * kOSlab) && dalloc(&c->ocnt, N) &&
+         dalloc(&c->hs_lo, N) && dalloc(&c->hs_hi, N) && dalloc(&c->hs_it, N) && dalloc(&c->wl, N) &&
          dalloc(&c->scratch_scalar, 2);
     ok = ok && cudaMallocHost((void**)&c->status_host, 2 * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemset(c->status, 0, 4 * sizeof(unsigned)) == cudaSuccess &&

@@ -108,10 +108,14 @@ struct sph_ctx {
     int32_t* gslab;         // kGSlab per particle: gather set of the last h-search count
     int32_t* oslab;         // kOSlab per particle: outer set (r < 2 h_j only), unordered
     int32_t* ocnt;          // outer-set sizes
+    double *hs_lo, *hs_hi;  // bisection bracket of particles handed to the per-particle search
+    int32_t* hs_it;         // counts already done for them
+    int32_t* wl;            // their indices (count in status[3])
     double* red_part;       // bbox partials: kReduceBlocks x 8
     double* dt_part;        // per force block
     sph::Grid* grid;
-    unsigned* status;       // [0] bits, [1] non-converged count, [2] internal flags
+    unsigned* status;       // [0] bits, [1] non-converged count, [2] internal flags,
+                            // [3] h-search worklist length
     unsigned* status_host;  // pinned mirror
     double* scratch_scalar; // [0] internal dt, [1] internal time
     int64_t last_hnoconv;
