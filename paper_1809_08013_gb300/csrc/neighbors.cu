@@ -316,6 +316,7 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
           int32_t* __restrict__ wl, unsigned* __restrict__ status) {
     __shared__ float4 s_f[kThreads / 32][32];
     const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < n;
     double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
@@ -329,10 +330,22 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
     int cnt = 0, it = 0;
     bool active = valid && kp.max_h_iter > 0, conv = false, deferred = false;
     int32_t* slab = gslab + (valid ? i : 0) * kGSlab;
+    const bool per = g->periodic_z != 0;
+    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
     for (int pass = 0;; ++pass) {  // pass is warp-uniform; it (per lane) stops at convergence
         const unsigned am = __ballot_sync(kFull, active);
         if (!am) break;
-        if (pass > 0 && __popc(am) <= kDeferLanes) {
+        const double R = 2.0 * h;
+        const Thr t = thresholds(R, g);
+        const float Rq = reach_f32(h);
+        const float lx = wmin(active ? fi.x - Rq : CUDART_INF_F), hx = wmax(active ? fi.x + Rq : -CUDART_INF_F);
+        const float ly = wmin(active ? fi.y - Rq : CUDART_INF_F), hy = wmax(active ? fi.y + Rq : -CUDART_INF_F);
+        const float lzz = wmin(active ? fi.z - Rq : CUDART_INF_F), hzz = wmax(active ? fi.z + Rq : -CUDART_INF_F);
+        // Periodic z: candidates are moved to the image nearest the warp's reference
+        // z, which is each lane's minimum image while the warp spans < lz/4.
+        const float zc = __shfl_sync(kFull, fi.z, __ffs(am) - 1);
+        const bool wide = per && (hzz - lzz > 0.25f * g->lzf);
+        if ((pass > 0 && __popc(am) <= kDeferLanes) || wide) {
             if (active) {
                 deferred = true;
                 active = false;
@@ -344,31 +357,71 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
             }
             break;
         }
-        const double R = 2.0 * h;
-        const Thr t = thresholds(R, g);
-        const float Rq = reach_f32(h);
+        int x0, x1, y0, y1, z0, z1;
+        box_range(lx, hx, g, 0, x0, x1);
+        box_range(ly, hy, g, 1, y0, y1);
+        box_range(lzz, hzz, g, 2, z0, z1);
         double R2 = -1.0;
         int c = 0;
-        warp_walk(
-            g, cells, fpos, s_f[warp], fi, Rq, active,
-            [&](int kx, int ky, int kz) {
-                const float gx = axis_gap(fi.x, kx, g, 0), gy = axis_gap(fi.y, ky, g, 1);
-                const float gz = g->periodic_z ? 0.0f : axis_gap(fi.z, kz, g, 2);
-                return fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < Rq * Rq;
-            },
-            [&](int j, const float4& fj) {
-                if (!active || j == i) return;
-                const float r2f = f_r2(fi, fj, g);
-                bool in = r2f < t.tin;
-                if (!in && r2f <= t.tout) {
-                    if (R2 < 0.0) R2 = __dmul_rn(R, R);
-                    in = exact_r2(pi, posh[j], g) < R2;
+        const float Rq2 = Rq * Rq;
+        for (int kz = z0; kz <= z1; ++kz) {
+            const int cz = per ? wrapi(kz, nz) : kz;
+            const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
+            for (int ky = y0; ky <= y1; ++ky) {
+                const long long row = ((long long)cz * ny + ky) * nx;
+                const float gy = axis_gap(fi.y, ky, g, 1);
+                for (int kx = x0; kx <= x1; ++kx) {
+                    const int2 se = __ldg(&cells[row + kx]);
+                    if (se.y <= se.x) continue;
+                    const float gx = axis_gap(fi.x, kx, g, 0);
+                    if (!__any_sync(kFull, active && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < Rq2))
+                        continue;
+                    for (int base = se.x; base < se.y; base += 32) {
+                        const int j = base + lane;
+                        float4 f = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);  // far away
+                        if (j < se.y) {
+                            f = __ldg(&fpos[j]);
+                            if (per) {
+                                const float d = f.z - zc;
+                                if (d > g->halflzf) f.z -= g->lzf;
+                                else if (d < -g->halflzf) f.z += g->lzf;
+                            }
+                        }
+                        s_f[warp][lane] = f;
+                        __syncwarp();
+                        unsigned in = 0u, bd = 0u;
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
+                            const float4 q = s_f[warp][k];
+                            const float dx = fi.x - q.x, dy = fi.y - q.y, dz = fi.z - q.z;
+                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            if (r2 < t.tin) in |= 1u << k;
+                            if (r2 <= t.tout) bd |= 1u << k;
+                        }
+                        __syncwarp();
+                        if (!active) in = bd = 0u;
+                        const int64_t selfk = i - base;
+                        if (selfk >= 0 && selfk < 32) {
+                            in &= ~(1u << selfk);
+                            bd &= ~(1u << selfk);
+                        }
+                        bd &= ~in;
+                        while (bd) {  // the ~1e-5-wide border band: exact FP64 test
+                            const int k = __ffs(bd) - 1;
+                            bd &= bd - 1u;
+                            if (R2 < 0.0) R2 = __dmul_rn(R, R);
+                            if (exact_r2(pi, posh[base + k], g) < R2) in |= 1u << k;
+                        }
+                        while (in) {
+                            const int k = __ffs(in) - 1;
+                            in &= in - 1u;
+                            if (c < kGSlab) slab[c] = base + k;
+                            ++c;
+                        }
+                    }
                 }
-                if (in) {
-                    if (c < kGSlab) slab[c] = j;
-                    ++c;
-                }
-            });
+            }
+        }
         if (active) {
             cnt = c;
             ++it;
