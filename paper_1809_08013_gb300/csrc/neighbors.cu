@@ -308,13 +308,52 @@ __device__ __forceinline__ void particle_pass(const Grid* __restrict__ g,
 // their bisection state, to the per-particle kernel below through a worklist.
 constexpr int kDeferLanes = 8;
 
-__global__ void __launch_bounds__(kThreads, 2)
+// Test the 32 staged candidates of a warp against every lane's particle and
+// fold the outcome into that lane's count and gather slab. Candidates are
+// (float x, y, z) already moved to the lane's periodic image; sidx holds
+// their particle indices. Padding slots sit far away.
+__device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const int* __restrict__ sidx,
+                                            const float4& fi, const Thr& t, bool active, int64_t i,
+                                            const double4_32a& pi, double R, double& R2,
+                                            const double4_32a* posh, const Grid* __restrict__ g,
+                                            int32_t* slab, int& c) {
+    unsigned in = 0u, bd = 0u;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const float4 q = st[k];
+        const float dx = fi.x - q.x, dy = fi.y - q.y, dz = fi.z - q.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (r2 < t.tin) in |= 1u << k;
+        if (r2 <= t.tout) bd |= 1u << k;
+    }
+    if (!active) return;
+    bd &= ~in;
+    while (bd) {  // the ~1e-5-wide border band: exact FP64 test
+        const int k = __ffs(bd) - 1;
+        bd &= bd - 1u;
+        const int j = sidx[k];
+        if (j == i) continue;
+        if (R2 < 0.0) R2 = __dmul_rn(R, R);
+        if (exact_r2(pi, posh[j], g) < R2) in |= 1u << k;
+    }
+    while (in) {
+        const int k = __ffs(in) - 1;
+        in &= in - 1u;
+        const int j = sidx[k];
+        if (j == i) continue;
+        if (c < kGSlab) slab[c] = j;
+        ++c;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 3)
 k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
           const float4* __restrict__ fpos, const int2* __restrict__ cells,
           int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ gslab,
           double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
           int32_t* __restrict__ wl, unsigned* __restrict__ status) {
     __shared__ float4 s_f[kThreads / 32][32];
+    __shared__ int s_i[kThreads / 32][32];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -332,6 +371,8 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
     int32_t* slab = gslab + (valid ? i : 0) * kGSlab;
     const bool per = g->periodic_z != 0;
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    float4* st = s_f[warp];
+    int* sidx = s_i[warp];
     for (int pass = 0;; ++pass) {  // pass is warp-uniform; it (per lane) stops at convergence
         const unsigned am = __ballot_sync(kFull, active);
         if (!am) break;
@@ -362,7 +403,7 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
         box_range(ly, hy, g, 1, y0, y1);
         box_range(lzz, hzz, g, 2, z0, z1);
         double R2 = -1.0;
-        int c = 0;
+        int c = 0, fill = 0;  // fill: staged candidates (warp-uniform)
         const float Rq2 = Rq * Rq;
         for (int kz = z0; kz <= z1; ++kz) {
             const int cz = per ? wrapi(kz, nz) : kz;
@@ -376,51 +417,39 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
                     const float gx = axis_gap(fi.x, kx, g, 0);
                     if (!__any_sync(kFull, active && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < Rq2))
                         continue;
-                    for (int base = se.x; base < se.y; base += 32) {
-                        const int j = base + lane;
-                        float4 f = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);  // far away
-                        if (j < se.y) {
-                            f = __ldg(&fpos[j]);
+                    // append the cell's particles to the staging buffer; run full chunks
+                    for (int s0 = se.x; s0 < se.y;) {
+                        const int take = min(32 - fill, se.y - s0);
+                        if (lane < take) {
+                            float4 f = __ldg(&fpos[s0 + lane]);
                             if (per) {
                                 const float d = f.z - zc;
                                 if (d > g->halflzf) f.z -= g->lzf;
                                 else if (d < -g->halflzf) f.z += g->lzf;
                             }
+                            st[fill + lane] = f;
+                            sidx[fill + lane] = s0 + lane;
                         }
-                        s_f[warp][lane] = f;
-                        __syncwarp();
-                        unsigned in = 0u, bd = 0u;
-#pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            const float4 q = s_f[warp][k];
-                            const float dx = fi.x - q.x, dy = fi.y - q.y, dz = fi.z - q.z;
-                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            if (r2 < t.tin) in |= 1u << k;
-                            if (r2 <= t.tout) bd |= 1u << k;
-                        }
-                        __syncwarp();
-                        if (!active) in = bd = 0u;
-                        const int64_t selfk = i - base;
-                        if (selfk >= 0 && selfk < 32) {
-                            in &= ~(1u << selfk);
-                            bd &= ~(1u << selfk);
-                        }
-                        bd &= ~in;
-                        while (bd) {  // the ~1e-5-wide border band: exact FP64 test
-                            const int k = __ffs(bd) - 1;
-                            bd &= bd - 1u;
-                            if (R2 < 0.0) R2 = __dmul_rn(R, R);
-                            if (exact_r2(pi, posh[base + k], g) < R2) in |= 1u << k;
-                        }
-                        while (in) {
-                            const int k = __ffs(in) - 1;
-                            in &= in - 1u;
-                            if (c < kGSlab) slab[c] = base + k;
-                            ++c;
+                        fill += take;
+                        s0 += take;
+                        if (fill == 32) {
+                            __syncwarp();
+                            union_chunk(st, sidx, fi, t, active, i, pi, R, R2, posh, g, slab, c);
+                            __syncwarp();
+                            fill = 0;
                         }
                     }
                 }
             }
+        }
+        if (fill > 0) {  // last partial chunk: pad with far-away slots
+            if (lane >= fill) {
+                st[lane] = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
+                sidx[lane] = -1;
+            }
+            __syncwarp();
+            union_chunk(st, sidx, fi, t, active, i, pi, R, R2, posh, g, slab, c);
+            __syncwarp();
         }
         if (active) {
             cnt = c;
