@@ -64,7 +64,7 @@ typedef struct {
     double eta2;         /* eta^2 in mu_ij = hb v.r / (r^2 + eta^2 hb^2), e.g. 0.01 */
     double cfl;          /* dt = cfl * min h / (c + 1.2 (alpha c + beta mumax)) */
     double lz;           /* period along z when periodic_z = 1 */
-    double cell_scale;   /* cell width = 2 <h> cell_scale (0 selects the default 1); a tuning
+    double cell_scale;   /* cell width = 2 <h> cell_scale (0 selects the default 1.25); a tuning
                             knob of the neighbour search, results do not depend on it */
 } sph_params;
 

@@ -49,26 +49,30 @@ __device__ __forceinline__ df addf(df x, float b) {
     return fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
 }
 
+// Products return (p, e) without the final Fast2Sum: that step is exact (it
+// does not change hi + lo), and every consumer here -- another product, a
+// sum, a sign or range test of hi, the conversion to double -- accepts a low
+// part of a few ulps of hi at ~2^-46 relative error.
 __device__ __forceinline__ df mul(df x, df y) {
     const float p = __fmul_rn(x.hi, y.hi);
     float e = __fmaf_rn(x.hi, y.hi, -p);
     e = __fmaf_rn(x.hi, y.lo, e);
     e = __fmaf_rn(x.lo, y.hi, e);
-    return fast_two_sum(p, e);
+    return {p, e};
 }
 
 __device__ __forceinline__ df mulf(df x, float b) {
     const float p = __fmul_rn(x.hi, b);
     float e = __fmaf_rn(x.hi, b, -p);
     e = __fmaf_rn(x.lo, b, e);
-    return fast_two_sum(p, e);
+    return {p, e};
 }
 
 __device__ __forceinline__ df sqr(df x) {
     const float p = __fmul_rn(x.hi, x.hi);
     float e = __fmaf_rn(x.hi, x.hi, -p);
     e = __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, e);
-    return fast_two_sum(p, e);
+    return {p, e};
 }
 
 // exact scaling by a power of two (no overflow/underflow in use)

@@ -615,8 +615,18 @@ k_outer(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ p
     if (i >= n || (status[2] & IF_SLAB_OVF)) return;
     const int ng = ngather[i];
     const float4 fi = fpos[i];
-    for (int s = lane; s < ng; s += 32) {
-        const int j = __ldg(&gslab[i * kGSlab + s]);
+    // the slab row is read up front so the dependent loads of the entries overlap
+    constexpr int kPer = kGSlab / 32;
+    int jj[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int s = k * 32 + lane;
+        jj[k] = s < ng ? __ldg(&gslab[i * kGSlab + s]) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int j = jj[k];
+        if (j < 0) continue;
         const float4 fj = __ldg(&fpos[j]);
         const float r2f = f_r2(fi, fj, g);
         bool in_j;
@@ -670,14 +680,15 @@ k_compose(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __restr
         v[k] = s < no ? __ldg(&oslab[i * kOSlab + s]) : 0x7fffffff;
     }
     int rank[kPer] = {};
+    for (int t = 0; t < no; ++t) {  // no is warp-uniform; rows hold a few outer entries
+        int w = __shfl_sync(kFull, v[0], t & 31);
 #pragma unroll
-    for (int k2 = 0; k2 < kPer; ++k2) {
-        if (k2 * 32 >= no) break;
-        for (int t = 0; t < 32; ++t) {
-            const int w = __shfl_sync(kFull, v[k2], t);
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) rank[k] += w < v[k];
+        for (int k2 = 1; k2 < kPer; ++k2) {
+            const int w2 = __shfl_sync(kFull, v[k2], t & 31);
+            w = (t >> 5) == k2 ? w2 : w;
         }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) rank[k] += w < v[k];
     }
 #pragma unroll
     for (int k = 0; k < kPer; ++k)

@@ -71,7 +71,7 @@ inline KParams kparams(const sph_params* p) {
     k.max_h_iter = p->max_h_iter; k.periodic_z = p->periodic_z; k.precision = p->precision;
     k.rho0 = p->rho0; k.c0 = p->c0; k.gamma = p->gamma; k.alpha = p->alpha;
     k.beta = p->beta; k.eta2 = p->eta2; k.cfl = p->cfl; k.lz = p->lz;
-    k.cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 1.0;
+    k.cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 1.25;
     return k;
 }
 
