@@ -105,13 +105,16 @@ __device__ __forceinline__ df from_double_fp64(double d) {
     return {hi, lo};
 }
 
-// Split of a double into hi + lo (error <= 2^-47 |d|) with integer operations
-// only: on GB300 both FP64 arithmetic and the int/float conversion
-// instructions occupy the narrow FP64 pipe, so neither is used. hi takes the
-// top 24 significand bits; the remaining 29 bits R are normalised with a
-// leading-zero count and truncated to 24 bits for lo. Meant for pair
-// differences: |d| < 2^-60 maps to 0 (an absolute error far below any use
-// here) and |d| is assumed below 2^60 (larger magnitudes saturate).
+// Split of a double into hi + lo (error <= 2^-47 |d|) using integer and FP32
+// operations only: on GB300 FP64 arithmetic, int/float conversions and the
+// leading-zero count all issue on the narrow FP64 pipe, so none is used.
+// hi takes the top 24 significand bits. The remaining 29 bits R = Rh 2^23 + Rl
+// become floats exactly by the 2^23 trick (the bits of an integer m < 2^23
+// ORed into 2^23's mantissa give 2^23 + m; subtracting 2^23 is exact), then
+// lo = (Rh 2^23 + Rl) 2^(e-1075) rounded once. lo may exceed half an ulp of
+// hi, which the double-float operations accept. Meant for pair differences:
+// |d| < 2^-60 maps to 0 (an absolute error far below any use here) and |d|
+// is assumed below 2^60 (larger magnitudes saturate).
 __device__ __forceinline__ df from_double(double d) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     int e = (int)((b >> 52) & 0x7ff);
@@ -120,13 +123,12 @@ __device__ __forceinline__ df from_double(double d) {
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
     const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) |
                                      (unsigned)((b >> 29) & 0x7fffffu));
-    const unsigned R = (unsigned)(b & 0x1fffffffull);  // value R 2^(e - 1075)
-    const int lz = __clz((int)R);                       // 3..32
-    // leading one of R at bit 31 - lz: move it to bit 23 (truncating below)
-    const unsigned m = lz >= 8 ? (R << (lz - 8)) : (R >> (8 - lz));
-    const unsigned lob = sign | ((unsigned)(e - 917 - lz) << 23) | (m & 0x7fffffu);
-    const float lo = R ? __uint_as_float(lob) : 0.0f;
-    return fast_two_sum(hi, lo);
+    const unsigned R = (unsigned)(b & 0x1fffffffull);
+    const float fl = __fsub_rn(__uint_as_float(0x4b000000u | (R & 0x7fffffu)), 8388608.0f);
+    const float fh = __fsub_rn(__uint_as_float(0x4b000000u | (R >> 23)), 8388608.0f);
+    const float r = __fmaf_rn(fh, 8388608.0f, fl);                     // R rounded to float
+    const float lo = __fmul_rn(r, __uint_as_float((unsigned)(e - 948) << 23));  // R 2^(e-1075)
+    return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
 }
 
 // Per-particle conversion back to FP64 (two conversions and one FP64 add).

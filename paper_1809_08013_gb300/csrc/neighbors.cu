@@ -712,13 +712,14 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
     __shared__ int s_start[kThreads / 32][32], s_pref[kThreads / 32][32];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (!(status[2] & IF_SLAB_OVF)) return;  // the slab path built the list
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (FILL && offsets[n] > nnzcap) {
-        if (i == 0 && lane == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
+        if (gw == 0 && lane == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
         return;
     }
-    if (i >= n) return;  // warp-uniform
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = gw; i < n; i += nwarps) {  // persistent: one warp per particle in turn
     const double4_32a pi = posh[i];
     const float4 fi = fpos[i];
     const float tin_i = tin[i];
@@ -778,6 +779,7 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
         rowlen[i] = cg + co;
         ngather[i] = cg;
     }
+    }
 }
 
 void launch_h_search(sph_ctx* c, const KParams& kp, cudaStream_t s) {
@@ -809,13 +811,13 @@ void launch_csr(sph_ctx* c, cudaStream_t s) {
     k_outer<<<nbw, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->ngather, c->gslab,
                                      c->ocnt, c->oslab, c->status);
     k_rowlen<<<nb, kThreads, 0, s>>>(n, c->ngather, c->ocnt, c->rowlen, c->status);
-    k_csr<false><<<nbw, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
+    k_csr<false><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
                                           c->cell_hmax, c->rowlen, c->ngather, nullptr, nullptr,
                                           c->nnzcap, c->status);
     launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s);
     k_compose<<<nbw, kThreads, 0, s>>>(n, c->ngather, c->gslab, c->ocnt, c->oslab, c->offsets,
                                        c->idx, c->nnzcap, c->status);
-    k_csr<true><<<nbw, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
+    k_csr<true><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
                                          c->cell_hmax, c->rowlen, c->ngather, c->offsets, c->idx,
                                          c->nnzcap, c->status);
 }
