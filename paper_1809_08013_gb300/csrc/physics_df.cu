@@ -140,7 +140,7 @@ void launch_density_df(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_
 // Definitions as in physics.cu; algebra: Fbar = (0.5/pi)(f(q_i)/h_i^4 +
 // f(q_j)/h_j^4)/r, one shared reciprocal R = 1/((r^2 + eta2 hb^2) rhob) for the
 // viscosity, mu = hb v.r rhob R, 1/rhob = (r^2 + eta2 hb^2) R.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 k_forces_df(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
             const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
             const float2* __restrict__ mdf, const double* __restrict__ cint,
