@@ -37,6 +37,26 @@ UNIT = "particle-updates/s"
 FLOPS_PAIR_BASE = 51
 FLOPS_PAIR_AV = 17
 
+# DRAM traffic of one k_forces_df launch from an ncu capture (dram__bytes_read.sum
+# + dram__bytes_write.sum) on the 70^3 patch, scaled to a launch here by the
+# number of pairs it processes (profiles/k_forces_df_patch343k.md). It is
+# reported only while the kernel sources hash to the version that was captured.
+FORCES_TRAFFIC = {"sources": ("physics_df.cu", "df.cuh", "sph_internal.cuh"),
+                  "sha1": "c1ceb5aa5b5fff5a222bc19cbd251d88a64787e7",
+                  "bytes": 197.3e6 + 14.21e6, "pairs": 34642666}
+
+
+def forces_traffic(pairs):
+    import hashlib
+    h = hashlib.sha1()
+    src = os.path.join(ROOT, "paper_1809_08013_gb300", "csrc")
+    for f in FORCES_TRAFFIC["sources"]:
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != FORCES_TRAFFIC["sha1"] or pairs <= 0:
+        return None
+    return FORCES_TRAFFIC["bytes"] * pairs / FORCES_TRAFFIC["pairs"]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -312,8 +332,8 @@ def run_native(args):
     achieved = flops_launch / forces_s / 1e12
     peak = fp64_peak / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_forces (+ k_dt_finish)",
+                "frac": achieved / peak, "traffic": forces_traffic(nnz),
+                "kernel": "k_forces_df (+ k_dt_finish)",
                 "peak_source": "FP64 FMA-chain probe on this GPU in this run (sph_probe_fma_peak), "
                                "2 flops per FMA",
                 "fp32_probe_tflops": fp32_peak / 1e12,
