@@ -7,6 +7,10 @@ iterated to 100 +- 5 every step). One benchmark "step" is one full SPH time
 step through the C ABI (sph_step). Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--workload patch|evrard] [--precision fp64|mixed]
+
+--workload evrard --precision mixed is the Evrard collapse (Section 4.1.2,
+hydrodynamics only) of 10^6 particles with the mixed-precision pair kernels.
 
 N > 1 runs under torchrun as independent replicas (one instance per GPU, no
 collective on the data path; the barrier and max-over-ranks timing only).
@@ -37,25 +41,30 @@ UNIT = "particle-updates/s"
 FLOPS_PAIR_BASE = 51
 FLOPS_PAIR_AV = 17
 
-# DRAM traffic of one k_forces_df launch from an ncu capture (dram__bytes_read.sum
-# + dram__bytes_write.sum) on the 70^3 patch, scaled to a launch here by the
-# number of pairs it processes (profiles/k_forces_df_patch343k.md). It is
-# reported only while the kernel sources hash to the version that was captured.
-FORCES_TRAFFIC = {"sources": ("physics_df.cu", "df.cuh", "sph_internal.cuh"),
-                  "sha1": "c1ceb5aa5b5fff5a222bc19cbd251d88a64787e7",
-                  "bytes": 197.3e6 + 14.21e6, "pairs": 34642666}
+# DRAM traffic of one force-kernel launch from an ncu capture (dram__bytes_read.sum
+# + dram__bytes_write.sum), scaled to a launch here by the number of pairs it
+# processes (profiles/k_forces_df_patch343k.md for FP64). It is reported only
+# while the kernel sources hash to the version that was captured.
+FORCES_TRAFFIC = {
+    "fp64": {"sources": ("physics_df.cu", "df.cuh", "sph_internal.cuh"),
+             "sha1": "c1ceb5aa5b5fff5a222bc19cbd251d88a64787e7",
+             "bytes": 197.3e6 + 14.21e6, "pairs": 34642666},
+}
 
 
-def forces_traffic(pairs):
+def forces_traffic(kind, pairs):
     import hashlib
+    ref = FORCES_TRAFFIC.get(kind)
+    if ref is None or pairs <= 0:
+        return None
     h = hashlib.sha1()
     src = os.path.join(ROOT, "paper_1809_08013_gb300", "csrc")
-    for f in FORCES_TRAFFIC["sources"]:
+    for f in ref["sources"]:
         with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != FORCES_TRAFFIC["sha1"] or pairs <= 0:
+    if h.hexdigest() != ref["sha1"]:
         return None
-    return FORCES_TRAFFIC["bytes"] * pairs / FORCES_TRAFFIC["pairs"]
+    return ref["bytes"] * pairs / ref["pairs"]
 
 
 def parse():
@@ -65,7 +74,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--side", type=int, default=100, help="lattice side (100 -> 1M particles)")
-    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=None, help="default 2 (patch), 3 (evrard)")
+    ap.add_argument("--workload", choices=("patch", "evrard"), default="patch")
+    ap.add_argument("--n", type=int, default=1_000_000, help="Evrard particle count")
+    ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64")
     ap.add_argument("--cell-scale", type=float, default=0.0,
                     help="neighbour-search cell width / (2 <h>); 0 = library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -80,12 +92,41 @@ def dist_env():
     return rank, world, local
 
 
-def workload_name(side):
+PRECISION = {"fp64": 0, "mixed": 1}
+DTYPE = {"fp64": "f64", "mixed": "f32 pair terms + f64 state"}
+
+
+def workload_name(args, n=None):
+    prec = ("FP64" if args.precision == "fp64" else
+            "mixed precision (FP32 relative-coordinate pair terms, double-float sums, FP64 "
+            "positions, h, neighbour sets and integration)")
+    if args.workload == "evrard":
+        n = n or args.n
+        return (f"Evrard collapse, hydrodynamics only, {n:,} particles (Section 4.1.2: R=M=1, "
+                f"rho ~ 1/r sampled r=R sqrt(U), u=0.05, ideal gas gamma=5/3, v=0), {prec}, "
+                f"cubic spline, h iterated to 100+-5 neighbours every step, Monaghan AV alpha=1 "
+                f"beta=2, CFL 0.3, kick-drift leapfrog from the initial conditions")
+    side = args.side if n is None else round(n ** (1 / 3))
     n = side ** 3
     return (f"rotating square patch {side}^3 = {n:,} particles (Section 4.1.1: lattice dx=1/{side}, "
-            f"jitter 0.01 dx, omega=5, rho0=1000, Tait c0=50, periodic z), FP64, cubic spline, "
+            f"jitter 0.01 dx, omega=5, rho0=1000, Tait c0=50, periodic z), {prec}, cubic spline, "
             f"h iterated to 100+-5 neighbours every step, Monaghan AV alpha=1 beta=2, CFL 0.3, "
             f"kick-drift leapfrog from the initial conditions")
+
+
+def make_workload(args, n=None):
+    """Seeded initial conditions of the selected workload (n overrides the size)."""
+    from paper_1809_08013_gb300 import ics
+    if args.workload == "evrard":
+        seed = 3 if args.seed is None else args.seed
+        s, prm = ics.evrard(n or args.n, seed=seed)
+    else:
+        seed = 2 if args.seed is None else args.seed
+        side = args.side if n is None else round(n ** (1 / 3))
+        s, prm = ics.square_patch(side, seed=seed)
+    prm.precision = PRECISION[args.precision]
+    prm.cell_scale = args.cell_scale
+    return s, prm
 
 
 # --------------------------------------------------------------- clocks
@@ -150,11 +191,10 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    from paper_1809_08013_gb300 import ics
     oracle.build()
-    side = 37  # bounded sample of the workload: same recipe at 37^3 = 50,653 particles
-    s, prm = ics.square_patch(side, seed=args.seed)
-    n = side ** 3
+    # bounded sample of the workload: the same recipe at about 50k particles
+    s, prm = make_workload(args, n=50_653)
+    n = len(s["x"])
     for _ in range(args.warmup):
         oracle.step(prm, s, nsteps=1)
     t0 = time.perf_counter()
@@ -162,13 +202,13 @@ def run_reference(args):
         oracle.step(prm, s, nsteps=1)  # every step starts from the initial conditions
     dt = time.perf_counter() - t0
     value = n * args.steps / dt
-    sample = (f"oracle (plain C FP64, OpenMP) step of the same patch recipe at {side}^3 = {n:,} "
+    sample = (f"oracle (plain C FP64, OpenMP) step of the same {args.workload} recipe at {n:,} "
               f"particles from its initial conditions, {args.steps} steps")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.side), "sample_particles": n},
+            "config": {"workload": workload_name(args), "sample_particles": n},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -177,7 +217,7 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- native arm
-def av_fraction(B, ctx, arr, sample_rows=4000):
+def av_fraction(B, ctx, arr, periodic_z, sample_rows=4000):
     """Share of interaction pairs with v_ij . r_ij < 0 (viscosity branch) on a
     sample of rows of the last step's neighbour list (host-side estimate used
     only for the counted-flop figure)."""
@@ -194,7 +234,8 @@ def av_fraction(B, ctx, arr, sample_rows=4000):
         js = order[idx[off[k]:off[k + 1]]]
         i = order[k]
         d = np.stack([x["x"][i] - x["x"][js], x["y"][i] - x["y"][js], x["z"][i] - x["z"][js]])
-        d[2] -= np.round(d[2])
+        if periodic_z:
+            d[2] -= np.round(d[2])
         w = np.stack([x["vx"][i] - x["vx"][js], x["vy"][i] - x["vy"][js], x["vz"][i] - x["vz"][js]])
         vr = (w * d).sum(0)
         neg += int(np.count_nonzero(vr < 0))
@@ -208,7 +249,6 @@ def run_native(args):
     import torch.distributed as dist
 
     from paper_1809_08013_gb300 import binding as B
-    from paper_1809_08013_gb300 import ics
 
     rank, world, local = dist_env()
     if world > 1:
@@ -220,8 +260,7 @@ def run_native(args):
     dev = torch.device("cuda", local)
     B.load()
 
-    s, prm = ics.square_patch(args.side, seed=args.seed)
-    prm.cell_scale = args.cell_scale
+    s, prm = make_workload(args)
     n = len(s["x"])
     ctx = B.Context(n, device=local)
     arr = B.alloc_arrays(s, device=dev)
@@ -326,16 +365,20 @@ def run_native(args):
         return
 
     # roofline of the dominant kernel (forces): counted FP64 flops per launch
-    f_av, nnz = av_fraction(B, ctx, arr)
+    f_av, nnz = av_fraction(B, ctx, arr, prm.periodic_z)
     flops_launch = nnz * (FLOPS_PAIR_BASE + FLOPS_PAIR_AV * f_av)
     forces_s = phase_ms["forces"] * 1e-3 / max(tsteps, 1)
     achieved = flops_launch / forces_s / 1e12
-    peak = fp64_peak / 1e12
+    mixed = args.precision == "mixed"
+    peak = (fp32_peak if mixed else fp64_peak) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": forces_traffic(nnz),
-                "kernel": "k_forces_df (+ k_dt_finish)",
-                "peak_source": "FP64 FMA-chain probe on this GPU in this run (sph_probe_fma_peak), "
+                "frac": achieved / peak,
+                "traffic": forces_traffic("mixed" if mixed else "fp64", nnz),
+                "kernel": "k_forces_mx (+ k_dt_finish)" if mixed else "k_forces_df (+ k_dt_finish)",
+                "peak_source": ("FP32" if mixed else "FP64") +
+                               " FMA-chain probe on this GPU in this run (sph_probe_fma_peak), "
                                "2 flops per FMA",
+                "fp64_probe_tflops": fp64_peak / 1e12,
                 "fp32_probe_tflops": fp32_peak / 1e12,
                 "flops_per_launch": flops_launch, "pairs_per_launch": nnz,
                 "av_pair_fraction": f_av}
@@ -349,14 +392,14 @@ def run_native(args):
         tc = time.perf_counter() - t0
         cpu = {"value": n / tc, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                "sample": f"one oracle step (plain C FP64, OpenMP) of the same {n:,}-particle "
-                         f"patch from its initial conditions: {tc:.1f} s"}
+                         f"{args.workload} from its initial conditions: {tc:.1f} s"}
 
     clocks = sampler.summary(w0, w1) if sampler else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": workload_name(args.side), "n_particles": n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": workload_name(args), "n_particles": n,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (state ~0.2 GB + neighbour list ~0.4 GB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

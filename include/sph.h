@@ -57,7 +57,13 @@ typedef struct {
     int32_t n_tol;       /* accepted |n - n_target|, e.g. 5 */
     int32_t max_h_iter;  /* h-search counts per particle, >= 1 */
     int32_t periodic_z;  /* 1: minimum image along z with period lz, z kept in [-lz/2, lz/2) */
-    int32_t precision;   /* 0 = FP64 (the only value accepted by this version) */
+    int32_t precision;   /* arithmetic of the pair sums (density, forces); positions, h,
+                            neighbour sets, dt and the integration are FP64 in all three:
+                            0 = FP64-accurate (double-float pair arithmetic, ~1e-14),
+                            1 = mixed: FP32 relative coordinates, kernel, gradient and
+                                viscosity terms, sums kept in double-float (~1e-7),
+                            2 = the same sums with native FP64 arithmetic.
+                            Other values: SPH_E_INVAL. */
     double rho0, c0;     /* Tait: p = c0^2 rho0 / 7 ((rho/rho0)^7 - 1), c = c0 (rho/rho0)^3 */
     double gamma;        /* ideal gas: p = (gamma - 1) rho u, c = sqrt(gamma (gamma - 1) u) */
     double alpha, beta;  /* Monaghan artificial viscosity */

@@ -117,7 +117,7 @@ def probe_fma_peak(device: int = 0, fp64: bool = True, stream=None) -> float:
 def params(p) -> SphParams:
     """Marshal an object with the SphParams attributes (see ics.SphParams)."""
     return SphParams(int(p.eos), int(p.n_target), int(p.n_tol), int(p.max_h_iter),
-                     int(p.periodic_z), 0, float(p.rho0), float(p.c0), float(p.gamma),
+                     int(p.periodic_z), int(getattr(p, "precision", 0)), float(p.rho0), float(p.c0), float(p.gamma),
                      float(p.alpha), float(p.beta), float(p.eta2), float(p.cfl), float(p.lz),
                      float(getattr(p, "cell_scale", 0.0)))
 

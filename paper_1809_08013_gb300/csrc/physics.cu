@@ -136,6 +136,11 @@ k_density(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
 }
 
 void launch_density(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s) {
+    if (kp.precision == PREC_MIXED) {
+        launch_pack_mx(c, false, s);
+        launch_density_mx(c, kp, fuse_eos, s);
+        return;
+    }
     if (kp.precision != PREC_FP64_NATIVE) {
         launch_density_df(c, kp, fuse_eos, s);
         return;
@@ -283,7 +288,9 @@ void launch_forces(sph_ctx* c, const KParams& kp, double* dt_out, double* time_i
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const int b = c->cur;
     c->launches += 1;
-    if (kp.precision != PREC_FP64_NATIVE)
+    if (kp.precision == PREC_MIXED)
+        launch_forces_mx(c, kp, s);
+    else if (kp.precision != PREC_FP64_NATIVE)
         launch_forces_df(c, kp, s);
     else if (n > 0) {
         c->launches += 1;

@@ -1,0 +1,308 @@
+// physics_mixed.cu -- density and forces (Algorithm 1 step 3) in mixed
+// precision: FP32 pair arithmetic on relative coordinates, FP32 kernel and
+// gradient terms, sums accumulated in double-float (about 48 bits). Positions,
+// the h / neighbour-count iteration, the time step and the integration stay
+// FP64 (the neighbour sets are the exact FP64 ones). Definitions as in
+// physics.cu; results are within ~1e-6 of the FP64 evaluation.
+//
+// Relative coordinates without the FP64 pipe: each FP64 position (and
+// velocity) is split once per step into a float pair hi + lo; for a pair,
+// (hi_i - hi_j) is exact when the two highs are within a factor of two (and
+// within 2^-24 |dx| otherwise), so dx = (hi_i - hi_j) + (lo_i - lo_j) carries
+// a relative error of a few 2^-24. Along the periodic z axis the wrap is
+// applied to the exact high difference (see rel_z).
+//
+// Per-particle pack, five float4 (80 B):
+//   mpk[5k]   = (x_hi, y_hi, z_hi, m)      mpk[5k+1] = (x_lo, y_lo, z_lo, 1/h)
+//   mpk[5k+2] = (vx_hi, vy_hi, vz_hi, 1/h^4)  mpk[5k+3] = (vx_lo, vy_lo, vz_lo, p/rho^2)
+//   mpk[5k+4] = (h/2, rho/2, alpha c/2, 0)
+#include <math_constants.h>
+
+#include "df.cuh"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+using dfl::df;
+
+namespace {
+
+constexpr float kInvPiF = 0.318309886f;
+
+__device__ __forceinline__ void split2(double d, float& hi, float& lo) {
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
+}
+
+// relative coordinate a_i - a_j from float pairs
+__device__ __forceinline__ float rel(float hi_i, float lo_i, float hi_j, float lo_j) {
+    return __fsub_rn(hi_i, hi_j) + __fsub_rn(lo_i, lo_j);
+}
+
+// Periodic z: the high difference is formed exactly (TwoSum) and wrapped by
+// the high part of lz, which is exact for |dz_hi| in [lz/2, lz] (Sterbenz);
+// the rounding error, the low parts and lz's low part go into the correction.
+struct ZWrap {
+    bool per;
+    float half, lzh, lzl;
+};
+
+__device__ __forceinline__ ZWrap make_zwrap(const KParams& kp) {
+    ZWrap w;
+    w.per = kp.periodic_z != 0;
+    w.lzh = __double2float_rn(kp.lz);
+    w.lzl = __double2float_rn(kp.lz - (double)w.lzh);
+    w.half = 0.5f * w.lzh;
+    return w;
+}
+
+__device__ __forceinline__ float rel_z(float hi_i, float lo_i, float hi_j, float lo_j,
+                                       const ZWrap& w) {
+    if (!w.per) return rel(hi_i, lo_i, hi_j, lo_j);
+    const df t = dfl::two_sum(hi_i, -hi_j);
+    float d = t.hi, corr = __fadd_rn(t.lo, __fsub_rn(lo_i, lo_j));
+    if (d > w.half) {
+        d = __fsub_rn(d, w.lzh);
+        corr = __fsub_rn(corr, w.lzl);
+    } else if (d < -w.half) {
+        d = __fadd_rn(d, w.lzh);
+        corr = __fadd_rn(corr, w.lzl);
+    }
+    return __fadd_rn(d, corr);
+}
+
+__device__ __forceinline__ float rsqrt_f(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y * fmaf(-0.5f * x * y, y, 1.5f);  // one Newton step
+}
+
+__device__ __forceinline__ float rcp_f(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y * fmaf(-x, y, 2.0f);
+}
+
+// pi h^3 W(q) and pi h^4 dW/dr (q) for q >= 0
+__device__ __forceinline__ float w_shape_f(float q) {
+    const float win = fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
+    const float t = 2.0f - q;
+    const float wout = 0.25f * t * t * t;
+    return q < 1.0f ? win : (q < 2.0f ? wout : 0.0f);
+}
+
+__device__ __forceinline__ float dw_shape_f(float q) {
+    const float fin = q * fmaf(2.25f, q, -3.0f);
+    const float t = 2.0f - q;
+    const float fout = -0.75f * t * t;
+    return q < 1.0f ? fin : (q < 2.0f ? fout : 0.0f);
+}
+
+__device__ __forceinline__ void eos_m(const KParams& kp, double rho, double u, double& p, double& c) {
+    if (kp.eos == 0) {
+        const double x = rho / kp.rho0;
+        const double x2 = x * x;
+        const double x4 = x2 * x2;
+        const double x7 = (x4 * x2) * x;
+        p = (kp.c0 * kp.c0 * kp.rho0 / 7.0) * (x7 - 1.0);
+        c = kp.c0 * (x2 * x);
+    } else {
+        p = (kp.gamma - 1.0) * rho * u;
+        c = sqrt(kp.gamma * (kp.gamma - 1.0) * u);
+    }
+}
+
+}  // namespace
+
+// Thermodynamic part of the pack (1/h^4, p/rho^2, h/2, rho/2, alpha c/2).
+__device__ __forceinline__ void pack_thermo(float4* __restrict__ mpk, int64_t k, double h,
+                                            double rho, double A, double alpha, double c) {
+    const double hinv = 1.0 / h;
+    const double h2 = hinv * hinv;
+    mpk[5 * k + 2].w = (float)(h2 * h2);
+    mpk[5 * k + 3].w = (float)A;
+    mpk[5 * k + 4] = make_float4((float)(0.5 * h), (float)(0.5 * rho), (float)(0.5 * alpha * c), 0.0f);
+}
+
+// Position / velocity / mass / 1/h part of the pack from the sorted state;
+// with THERMO also the thermodynamic part from therm = (rho/2, p/rho^2,
+// alpha c/2, h/2) (a standalone force call, where density ran elsewhere).
+template <bool THERMO>
+__global__ void __launch_bounds__(kThreads)
+k_pack_mx(int64_t n, const double4_32a* __restrict__ posh, const double4_32a* __restrict__ velm,
+          const double4_32a* __restrict__ therm, float4* __restrict__ mpk) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double4_32a p = posh[k];
+    const double4_32a v = velm[k];
+    float xh, xl, yh, yl, zh, zl, ah, al, bh, bl, ch, cl;
+    split2(p.x, xh, xl);
+    split2(p.y, yh, yl);
+    split2(p.z, zh, zl);
+    split2(v.x, ah, al);
+    split2(v.y, bh, bl);
+    split2(v.z, ch, cl);
+    const double hinv = 1.0 / p.w;
+    mpk[5 * k + 0] = make_float4(xh, yh, zh, (float)v.w);
+    mpk[5 * k + 1] = make_float4(xl, yl, zl, (float)hinv);
+    if (THERMO) {
+        const double4_32a t = therm[k];
+        const double h2 = hinv * hinv;
+        mpk[5 * k + 2] = make_float4(ah, bh, ch, (float)(h2 * h2));
+        mpk[5 * k + 3] = make_float4(al, bl, cl, (float)t.y);
+        mpk[5 * k + 4] = make_float4((float)t.w, (float)t.x, (float)t.z, 0.0f);
+    } else {
+        mpk[5 * k + 2] = make_float4(ah, bh, ch, 0.0f);
+        mpk[5 * k + 3] = make_float4(al, bl, cl, 0.0f);
+    }
+}
+
+template <bool FUSE>
+__global__ void __launch_bounds__(kThreads)
+k_density_mx(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+             const double* __restrict__ ue, float4* __restrict__ mpk,
+             const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
+             const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
+             double* __restrict__ pint, double* __restrict__ cint) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || offsets[n] > nnzcap) return;
+    const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1];
+    const float hinv = a1.w;
+    const ZWrap zw = make_zwrap(kp);
+    df acc = {a0.w, 0.0f};  // self term m_i W(0, h_i): shape 1
+    const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
+    for (int64_t e = e0; e < e1; ++e) {
+        const int j = __ldg(&idx[e]);
+        const float4 b0 = __ldg(&mpk[5 * j]), b1 = __ldg(&mpk[5 * j + 1]);
+        const float dx = rel(a0.x, a1.x, b0.x, b1.x), dy = rel(a0.y, a1.y, b0.y, b1.y);
+        const float dz = rel_z(a0.z, a1.z, b0.z, b1.z, zw);
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float q = r2 > 0.0f ? r2 * rsqrt_f(r2) * hinv : 0.0f;
+        acc = dfl::addf(acc, b0.w * w_shape_f(q));
+    }
+    const double hd = posh[i].w;
+    const double hid = 1.0 / hd;
+    const double rho = dfl::to_double(acc) * (hid * hid * hid * 0.31830988618379067154);
+    if (FUSE) {
+        double p, c;
+        eos_m(kp, rho, ue[i], p, c);
+        const double A = p / (rho * rho);
+        therm[i] = make_double4_32a(0.5 * rho, A, 0.5 * kp.alpha * c, 0.5 * hd);
+        pack_thermo(mpk, i, hd, rho, A, kp.alpha, c);
+        pint[i] = p;
+        cint[i] = c;
+    } else {
+        therm[i].x = 0.5 * rho;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_forces_mx(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+            const float4* __restrict__ mpk, const double* __restrict__ cint,
+            const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
+            double4_32a* __restrict__ acc, double* __restrict__ mumax,
+            double* __restrict__ dt_part) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double dtc = CUDART_INF;
+    if (i < n && offsets[n] <= nnzcap) {
+        const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1], a2 = mpk[5 * i + 2];
+        const float4 a3 = mpk[5 * i + 3], a4 = mpk[5 * i + 4];
+        const ZWrap zw = make_zwrap(kp);
+        const float eta2 = (float)kp.eta2, beta = (float)kp.beta;
+        const float cpi = 0.5f * kInvPiF;
+        df sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sp = {0.f, 0.f}, sv = {0.f, 0.f};
+        float mum = 0.0f;
+        const int64_t e0 = offsets[i], e1 = offsets[i + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            const int j = __ldg(&idx[e]);
+            const float4 b0 = __ldg(&mpk[5 * j]), b1 = __ldg(&mpk[5 * j + 1]);
+            const float4 b2 = __ldg(&mpk[5 * j + 2]), b3 = __ldg(&mpk[5 * j + 3]);
+            const float4 b4 = __ldg(&mpk[5 * j + 4]);
+            const float dx = rel(a0.x, a1.x, b0.x, b1.x), dy = rel(a0.y, a1.y, b0.y, b1.y);
+            const float dz = rel_z(a0.z, a1.z, b0.z, b1.z, zw);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (!(r2 > 0.0f)) continue;  // coincident particles exert no force
+            const float rinv = rsqrt_f(r2);
+            const float r = r2 * rinv;
+            const float fa = dw_shape_f(r * a1.w), fb = dw_shape_f(r * b1.w);
+            const float Fb = fmaf(a2.w, fa, b2.w * fb) * (cpi * rinv);
+            const float wx = rel(a2.x, a3.x, b2.x, b3.x), wy = rel(a2.y, a3.y, b2.y, b3.y);
+            const float wz = rel(a2.z, a3.z, b2.z, b3.z);
+            const float vr = fmaf(wz, dz, fmaf(wy, dy, wx * dx));
+            float Pi = 0.0f;
+            if (vr < 0.0f) {
+                const float hb = a4.x + b4.x;
+                const float d1 = fmaf(eta2 * hb, hb, r2);
+                const float rb = a4.y + b4.y;
+                const float R = rcp_f(d1 * rb);
+                const float mu = hb * vr * rb * R;
+                Pi = mu * fmaf(beta, mu, -(a4.z + b4.z)) * (d1 * R);
+                mum = fmaxf(mum, -mu);
+            }
+            const float mF = b0.w * Fb;
+            const float g = mF * ((a3.w + b3.w) + Pi);
+            sx = dfl::addf(sx, g * dx);
+            sy = dfl::addf(sy, g * dy);
+            sz = dfl::addf(sz, g * dz);
+            const float mFv = mF * vr;
+            sp = dfl::addf(sp, mFv);
+            sv = dfl::addf(sv, mFv * Pi);
+        }
+        const double Aid = (double)a3.w;
+        acc[i] = make_double4_32a(-dfl::to_double(sx), -dfl::to_double(sy), -dfl::to_double(sz),
+                                  fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)));
+        mumax[i] = (double)mum;
+        const double ci = cint[i];
+        dtc = posh[i].w / (ci + 1.2 * (kp.alpha * ci + kp.beta * (double)mum));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
+    __shared__ double sh[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dtc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = sh[0];
+        for (int w = 1; w < kThreads / 32; ++w) m = fmin(m, sh[w]);
+        dt_part[blockIdx.x] = m;
+    }
+}
+
+void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s) {
+    const int64_t n = c->n;
+    if (n == 0) return;
+    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const int b = c->cur;
+    c->launches += 1;
+    if (thermo)
+        k_pack_mx<true><<<nb, kThreads, 0, s>>>(n, c->posh[b], c->velm[b], c->therm, c->mpk);
+    else
+        k_pack_mx<false><<<nb, kThreads, 0, s>>>(n, c->posh[b], c->velm[b], c->therm, c->mpk);
+}
+
+void launch_density_mx(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s) {
+    const int64_t n = c->n;
+    if (n == 0) return;
+    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const int b = c->cur;
+    c->launches += 1;
+    if (fuse_eos)
+        k_density_mx<true><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->ue[b], c->mpk, c->offsets,
+                                                   c->ngather, c->idx, c->nnzcap, c->therm,
+                                                   c->pint, c->cint);
+    else
+        k_density_mx<false><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->ue[b], c->mpk,
+                                                    c->offsets, c->ngather, c->idx, c->nnzcap,
+                                                    c->therm, c->pint, c->cint);
+}
+
+void launch_forces_mx(sph_ctx* c, const KParams& kp, cudaStream_t s) {
+    const int64_t n = c->n;
+    if (n == 0) return;
+    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const int b = c->cur;
+    c->launches += 1;
+    k_forces_mx<<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->mpk, c->cint, c->offsets, c->idx,
+                                        c->nnzcap, c->acc, c->mumax, c->dt_part);
+}
+
+}  // namespace sph

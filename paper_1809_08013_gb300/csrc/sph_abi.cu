@@ -47,8 +47,8 @@ sph_status check_launch(sph_ctx* c, const char* where) {
 sph_status check_params(sph_ctx* c, const sph_params* p) {
     if (!p) { set_err(c, "params is NULL"); return SPH_E_INVAL; }
     if (p->eos != 0 && p->eos != 1) { set_err(c, "eos must be 0 or 1"); return SPH_E_INVAL; }
-    if (p->precision != 0 && p->precision != 2) {
-        set_err(c, "precision must be 0 (FP64-accurate) or 2 (FP64 pipe)");
+    if (p->precision < 0 || p->precision > 2) {
+        set_err(c, "precision must be 0 (FP64-accurate), 1 (mixed) or 2 (FP64 pipe)");
         return SPH_E_INVAL;
     }
     if (p->max_h_iter < 1 || p->n_target < 1 || p->n_tol < 0) {
@@ -86,7 +86,7 @@ bool dalloc(T** p, size_t count) {
 
 void free_all(sph_ctx* c) {
     void* ptrs[] = {c->posh[0], c->posh[1], c->velm[0], c->velm[1], c->ue[0], c->ue[1],
-                    c->therm, c->kern, c->acc, c->pint, c->cint, c->dpk, c->mdf, c->mumax, c->fpos, c->tin, c->order[0],
+                    c->therm, c->kern, c->acc, c->pint, c->cint, c->dpk, c->mdf, c->mpk, c->mumax, c->fpos, c->tin, c->order[0],
                     c->order[1], c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist,
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->gslab, c->oslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
@@ -220,7 +220,7 @@ sph_status sph_ctx_create(sph_ctx** out, int64_t ncap, int64_t nnzcap, int devic
     }
     ok = ok && dalloc(&c->therm, N) && dalloc(&c->kern, N) && dalloc(&c->acc, N) &&
          dalloc(&c->pint, N) && dalloc(&c->cint, N) && dalloc(&c->dpk, 3 * N) &&
-         dalloc(&c->mdf, N) &&
+         dalloc(&c->mdf, N) && dalloc(&c->mpk, 5 * N) &&
          dalloc(&c->mumax, N) && dalloc(&c->fpos, N) && dalloc(&c->tin, N) &&
          dalloc(&c->hist, 256 * nsb) && dalloc(&c->hist_part, (size_t)scan_parts(256 * nsb) + 1) &&
          dalloc(&c->cells, (size_t)c->cellcap) && dalloc(&c->cell_hmax, (size_t)c->cellcap) &&
@@ -339,6 +339,7 @@ sph_status sph_forces(sph_ctx* c, const sph_params* prm, sph_particles* P, void*
     cudaStream_t s = (cudaStream_t)stream;
     const KParams kp = kparams(prm);
     launch_gather_state(c, P, kp, GATHER_FORCES, s);
+    if (kp.precision == PREC_MIXED) launch_pack_mx(c, true, s);
     launch_forces(c, kp, P->dt, nullptr, s);
     launch_scatter(c, P, SC_ACC | SC_MUMAX, s);
     return check_launch(c, "sph_forces");

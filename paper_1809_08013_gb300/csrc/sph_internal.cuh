@@ -91,6 +91,7 @@ struct sph_ctx {
     double* cint;
     float4* dpk;            // 3 per particle: double-float pack of the force kernel
     float2* mdf;            // mass as a float pair
+    float4* mpk;            // 5 per particle: pack of the mixed-precision pair kernels
     double* mumax;
     float4* fpos;
     float* tin;
@@ -150,6 +151,10 @@ void launch_density(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s
 void launch_density_df(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s);
 void launch_forces_df(sph_ctx* c, const KParams& kp, cudaStream_t s);
 enum { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP64_NATIVE = 2 };
+// ---- physics_mixed.cu (precision 1)
+void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s);
+void launch_density_mx(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s);
+void launch_forces_mx(sph_ctx* c, const KParams& kp, cudaStream_t s);
 void launch_eos_caller(const KParams& kp, const sph_particles* P, cudaStream_t s);
 void launch_forces(sph_ctx* c, const KParams& kp, double* dt_out, double* time_inout,
                    cudaStream_t s);

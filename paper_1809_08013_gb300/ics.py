@@ -65,6 +65,8 @@ class SphParams:
     periodic_z: int = 1          # 1: minimum-image periodicity along z
     lz: float = 1.0              # period along z
     cell_scale: float = 0.0      # neighbour-search cell width / (2 <h>); 0 = library default
+    precision: int = 0           # pair arithmetic: 0 FP64-accurate, 1 mixed FP32/double-float,
+                                 # 2 native FP64 (the oracle is FP64 throughout)
 
     def as_dict(self) -> dict:
         return dataclasses.asdict(self)
