@@ -327,6 +327,24 @@ def run_native(args):
         ms_max = float(t.item())
     value = world * n * args.steps / (ms_max * 1e-3)
 
+    # step 0 alone from the initial conditions (the longest h search): the timed
+    # run's first step is this same work, so the rest gives the steady state
+    reset()
+    torch.cuda.synchronize(dev)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    ctx.step(prm, arr, nsteps=1, stream=stream)
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    step0_ms = g0.elapsed_time(g1)
+    ctx.sync(stream)
+    steady = None
+    if args.steps > 1 and ms > step0_ms:
+        sms = (ms - step0_ms) / (args.steps - 1)
+        steady = {"ms_per_step": sms, "value": world * n / (sms * 1e-3), "step0_ms": step0_ms,
+                  "steps": f"2-{args.steps} of the timed run (total minus a separate step 0)"}
+
     # end to end through the public API: pinned host state in, one step, state out
     e2e = None
     if not args.no_e2e:
@@ -403,6 +421,7 @@ def run_native(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (state ~0.2 GB + neighbour list ~0.4 GB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "steady_state": steady,
             "clocks": clocks, "status": B.STATUS_NAMES.get(status),
             "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
             "launches_per_phase": phase_launches}
