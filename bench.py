@@ -81,6 +81,10 @@ def parse():
     ap.add_argument("--cell-scale", type=float, default=0.0,
                     help="neighbour-search cell width / (2 <h>); 0 = library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the batched-ensemble measurement")
+    ap.add_argument("--ensemble-steps", type=int, default=50)
+    ap.add_argument("--ensemble-count", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -241,6 +245,115 @@ def av_fraction(B, ctx, arr, periodic_z, sample_rows=4000):
         neg += int(np.count_nonzero(vr < 0))
         tot += len(js)
     return neg / max(tot, 1), int(off[-1])
+
+
+def ensemble_instances(count, precision, seed=1000):
+    """Configuration 4: `count` rotating patches, N log-uniform in [4096,
+    262144] rounded to cubes, omega ~ U[2, 8], seeds seed + k."""
+    from paper_1809_08013_gb300 import ics
+    out = []
+    for k, (side, omega) in enumerate(ics.ensemble_sizes(count, seed)):
+        s, p = ics.square_patch(side, seed=seed + k, omega=omega)
+        p.precision = PRECISION[precision]
+        out.append((s, p))
+    return out
+
+
+def run_ensemble(args, B, dev):
+    """Batched ensemble (one CUDA graph of sph_batch_step over all instances)
+    against the single-instance path run one instance after another.
+    Latency of an instance = time from submission to its result: in the
+    batch every instance is submitted together and completes with the graph;
+    one at a time, instance k completes after all earlier ones."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.Stream(device=dev)  # graphs are captured on a non-default stream
+    with torch.cuda.stream(stream):
+        return _run_ensemble(args, B, dev, stream)
+
+
+def _run_ensemble(args, B, dev, stream):
+    import numpy as np
+    import torch
+    K = args.ensemble_steps
+    insts = ensemble_instances(args.ensemble_count, args.precision)
+    counts = [len(s["x"]) for s, _ in insts]
+    ntot = sum(counts)
+    state = {k: np.concatenate([s[k] for s, _ in insts]) for k in B.STATE_FIELDS}
+    ctx = B.Context(ntot, max_instances=len(insts), device=dev.index)
+    ctx.batch_set(counts, [p for _, p in insts], stream=stream)
+    arr = B.alloc_arrays(state, device=dev, ninst=len(insts))
+    ic = {k: arr[k].clone() for k in B.STATE_FIELDS}
+
+    def reset():
+        for k in B.STATE_FIELDS:
+            arr[k].copy_(ic[k])
+        arr["time"].zero_()
+
+    ctx.batch_step(arr, nsteps=1, stream=stream)  # warm-up
+    ctx.sync(stream)
+    reset()
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    l0 = ctx.launch_count()
+    with torch.cuda.graph(g, stream=stream):
+        ctx.batch_step(arr, nsteps=K, stream=stream)
+    graph_kernels = ctx.launch_count() - l0
+    g.replay()  # warm replay
+    torch.cuda.synchronize(dev)
+    reset()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_batch = e0.elapsed_time(e1)
+    st = ctx.sync(stream)
+    batched = {k: arr[k].cpu().numpy() for k in ("x", "y", "z", "vx", "vy", "vz", "h", "u")}
+    del g
+
+    # the plain single-instance path, one instance after another on one context
+    one = B.Context(max(counts), device=dev.index)
+    t_alone = []
+    same = True
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for k, (s, p) in enumerate(insts):
+        a = B.alloc_arrays(s, device=dev)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        one.step(p, a, nsteps=K, stream=stream)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_alone.append(f0.elapsed_time(f1))
+        for f in batched:
+            same = same and np.array_equal(a[f].cpu().numpy().view(np.uint8),
+                                           batched[f][off[k]:off[k + 1]].view(np.uint8))
+    one.sync(stream)
+    t_alone = np.array(t_alone)
+    done_seq = np.cumsum(t_alone)
+    upd = ntot * K
+    return {
+        "workload": f"{len(insts)} rotating patches, N log-uniform in [4096, 262144] rounded to "
+                    f"cubes (sum {ntot:,}), omega ~ U[2,8], seeds 1000+k, {K} steps each, "
+                    f"{args.precision}",
+        "instances": len(insts), "particles": ntot, "steps": K,
+        "batched": {"ms": t_batch, "updates_per_s": upd / (t_batch * 1e-3),
+                    "latency_ms_p50": t_batch, "latency_ms_p99": t_batch,
+                    "launch": "one CUDA graph of sph_batch_step",
+                    "kernels_in_graph": graph_kernels,
+                    "status": B.STATUS_NAMES.get(st)},
+        "single_instance_path": {"ms": float(done_seq[-1]),
+                                 "updates_per_s": upd / (done_seq[-1] * 1e-3),
+                                 "latency_ms_p50": float(np.percentile(done_seq, 50)),
+                                 "latency_ms_p99": float(np.percentile(done_seq, 99)),
+                                 "own_time_ms_p50": float(np.percentile(t_alone, 50)),
+                                 "own_time_ms_p99": float(np.percentile(t_alone, 99)),
+                                 "launch": "sph_step per instance, one after another"},
+        "batched_equals_single_bitwise": bool(same),
+    }
 
 
 def run_native(args):
@@ -412,6 +525,10 @@ def run_native(args):
                "sample": f"one oracle step (plain C FP64, OpenMP) of the same {n:,}-particle "
                          f"{args.workload} from its initial conditions: {tc:.1f} s"}
 
+    ensemble = None
+    if not args.no_ensemble and args.workload == "patch" and world == 1:
+        ensemble = run_ensemble(args, B, dev)
+
     clocks = sampler.summary(w0, w1) if sampler else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -421,7 +538,7 @@ def run_native(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (state ~0.2 GB + neighbour list ~0.4 GB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "steady_state": steady,
+            "steady_state": steady, "ensemble": ensemble,
             "clocks": clocks, "status": B.STATUS_NAMES.get(status),
             "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
             "launches_per_phase": phase_launches}

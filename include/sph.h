@@ -94,7 +94,9 @@ typedef struct {
 /* View of the context-owned neighbour list, valid until the next call that
  * rebuilds it. Rows are in the library's internal (Morton cell) order:
  * internal row k belongs to caller particle order[k], and every idx entry is
- * an internal row number. Row k lists first its gather set
+ * an internal row number. After a batch step (sph_batch_step) the rows are
+ * the slots of all instances; the empty slots between instances have
+ * order[k] = -1 and empty rows. Row k lists first its gather set
  * N_k = { j : r_kj < 2 h_k } (ngather[k] entries), then the rest of the
  * symmetric set S_k = { j : r_kj < 2 max(h_k, h_j) }. Entry order within each
  * part is unspecified. All pointers are device pointers; *nnz_dev is the
@@ -113,6 +115,19 @@ typedef struct {
  * 100-neighbour workloads). Allocates all scratch once; later calls allocate
  * nothing. On failure *out is NULL. */
 sph_status sph_ctx_create(sph_ctx **out, int64_t n_capacity, int64_t nnz_capacity, int device);
+
+/* Largest number of instances of one batch (the instance id takes the top 8
+ * bits of the 32-bit sort key). */
+#define SPH_MAX_INSTANCES 256
+
+/* As sph_ctx_create, for batches of up to max_instances independent
+ * problems with n_capacity particles in total (sph_batch_set / _step).
+ * Internally every instance starts on a 256-slot boundary, so up to
+ * 255 (max_instances - 1) extra slots are allocated. max_instances outside
+ * [1, SPH_MAX_INSTANCES] returns SPH_E_INVAL. The paper runs one problem per
+ * job; batching independent problems on one GPU has no counterpart in it. */
+sph_status sph_ctx_create_batch(sph_ctx **out, int64_t n_capacity, int64_t nnz_capacity,
+                                int32_t max_instances, int device);
 
 /* Free the context and its device memory (synchronises the device). NULL is a no-op. */
 void sph_ctx_destroy(sph_ctx *ctx);
@@ -146,6 +161,31 @@ sph_status sph_forces(sph_ctx *ctx, const sph_params *prm, sph_particles *P, voi
  * end, together with h, rho, p, c, a, du, mumax, nnb of the last step. */
 sph_status sph_step(sph_ctx *ctx, const sph_params *prm, sph_particles *P, int nsteps,
                     void *stream);
+
+/* Describe a batch of ninst independent problems for sph_batch_step.
+ * counts[k] (host array) is the number of particles of instance k; the
+ * caller's particle arrays hold the instances back to back, instance k at
+ * [sum_{l<k} counts[l], ... + counts[k]). params[k] (host array) are its
+ * parameters; all instances must share `precision`. Instances never
+ * interact: each has its own cell grid, neighbour sets, time step and time.
+ * An instance's results are bit-identical to a single-problem sph_step of it
+ * with the same parameters. Copies the descriptors to the device and waits
+ * for the copy (synchronises `stream`). SPH_E_INVAL for ninst outside
+ * [1, max_instances], a negative count, invalid params, or more particles
+ * than the capacity. Any single-problem call replaces the batch. */
+sph_status sph_batch_set(sph_ctx *ctx, int32_t ninst, const int64_t *counts,
+                         const sph_params *params, void *stream);
+
+/* sph_step for every instance of the batch: P holds all instances' arrays
+ * (P->n = total particles); P->dt and P->time are device arrays of ninst
+ * doubles (per-instance time step and time). Enqueues only kernel launches,
+ * so it can be captured in a CUDA graph and replayed while the batch is
+ * unchanged. SPH_E_INVAL if P->n differs from the batch's total. */
+sph_status sph_batch_step(sph_ctx *ctx, sph_particles *P, int nsteps, void *stream);
+
+/* Rows of the current neighbour list (the n of sph_neighbors): the particle
+ * count of a single problem; for a batch, the slots of all instances. */
+int64_t sph_neighbor_rows(const sph_ctx *ctx);
 
 /* Copy the neighbour list of the last sph_build_neighbors (or last step of
  * sph_step) into caller HOST buffers, synchronously after the stream's work:

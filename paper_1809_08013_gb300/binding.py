@@ -78,6 +78,12 @@ def load(rebuild: bool = True):
     L.sph_last_hnoconv.argtypes = [_DP]
     L.sph_ctx_create.restype = C.c_int
     L.sph_ctx_create.argtypes = [P(_DP), C.c_int64, C.c_int64, C.c_int]
+    L.sph_ctx_create_batch.restype = C.c_int
+    L.sph_ctx_create_batch.argtypes = [P(_DP), C.c_int64, C.c_int64, C.c_int32, C.c_int]
+    L.sph_batch_set.restype = C.c_int
+    L.sph_batch_set.argtypes = [_DP, C.c_int32, P(C.c_int64), P(SphParams), _DP]
+    L.sph_batch_step.restype = C.c_int
+    L.sph_batch_step.argtypes = [_DP, P(SphParticles), C.c_int, _DP]
     L.sph_ctx_destroy.restype = None
     L.sph_ctx_destroy.argtypes = [_DP]
     L.sph_build_neighbors.restype = C.c_int
@@ -98,6 +104,8 @@ def load(rebuild: bool = True):
     L.sph_timing_read.argtypes = [_DP, _DP, _DP, _DP]
     L.sph_launch_count.restype = C.c_int64
     L.sph_launch_count.argtypes = [_DP]
+    L.sph_neighbor_rows.restype = C.c_int64
+    L.sph_neighbor_rows.argtypes = [_DP]
     L.sph_probe_fma_peak.restype = C.c_int
     L.sph_probe_fma_peak.argtypes = [C.c_int, C.c_int, _DP, C.POINTER(C.c_double)]
     _lib = L
@@ -143,9 +151,9 @@ def particles(arrays: dict) -> SphParticles:
     return s
 
 
-def alloc_arrays(state: dict, device="cuda"):
+def alloc_arrays(state: dict, device="cuda", ninst: int = 1):
     """Device arrays for a host state dict (numpy arrays x..u): the state
-    itself plus outputs, nnb, and the time / dt scalars."""
+    itself plus outputs, nnb, and the time / dt scalars (one per instance)."""
     import torch
     out = {}
     n = len(state["x"])
@@ -154,8 +162,8 @@ def alloc_arrays(state: dict, device="cuda"):
     for f in OUT_FIELDS:
         out[f] = torch.zeros(n, dtype=torch.float64, device=device)
     out["nnb"] = torch.zeros(n, dtype=torch.int32, device=device)
-    out["time"] = torch.zeros(1, dtype=torch.float64, device=device)
-    out["dt"] = torch.zeros(1, dtype=torch.float64, device=device)
+    out["time"] = torch.zeros(ninst, dtype=torch.float64, device=device)
+    out["dt"] = torch.zeros(ninst, dtype=torch.float64, device=device)
     return out
 
 
@@ -169,19 +177,20 @@ def _stream(stream):
 class Context:
     """Owns an sph_ctx: scratch, cell table and neighbour list on one device."""
 
-    def __init__(self, n_capacity: int, nnz_capacity: int | None = None, device: int = 0):
+    def __init__(self, n_capacity: int, nnz_capacity: int | None = None, device: int = 0,
+                 max_instances: int = 1):
         self.lib = load()
         if nnz_capacity is None:
             nnz_capacity = max(1024, 160 * int(n_capacity))
         h = C.c_void_p()
-        st = self.lib.sph_ctx_create(C.byref(h), int(n_capacity), int(nnz_capacity), int(device))
+        st = self.lib.sph_ctx_create_batch(C.byref(h), int(n_capacity), int(nnz_capacity),
+                                           int(max_instances), int(device))
         if st != SPH_OK:
-            raise SphError(st, "sph_ctx_create failed")
+            raise SphError(st, "sph_ctx_create_batch failed")
         self.h = h
         self.n_capacity = int(n_capacity)
         self.nnz_capacity = int(nnz_capacity)
         self.device = device
-        self._n_last = 0
 
     def close(self):
         if getattr(self, "h", None):
@@ -204,7 +213,6 @@ class Context:
     def build_neighbors(self, prm, arrays: dict, stream=None) -> SphNeighbors:
         P = particles(arrays)
         nb = SphNeighbors()
-        self._n_last = int(P.n)
         self._check(self.lib.sph_build_neighbors(self.h, C.byref(params(prm)), C.byref(P),
                                                  C.byref(nb), _stream(stream)))
         return nb
@@ -223,9 +231,20 @@ class Context:
 
     def step(self, prm, arrays: dict, nsteps: int = 1, stream=None):
         P = particles(arrays)
-        self._n_last = int(P.n)
         self._check(self.lib.sph_step(self.h, C.byref(params(prm)), C.byref(P), int(nsteps),
                                       _stream(stream)))
+
+    def batch_set(self, counts, prms, stream=None):
+        """Describe a batch: counts[k] particles of instance k (instances back
+        to back in the arrays), prms[k] its parameters."""
+        k = len(counts)
+        cnt = (C.c_int64 * k)(*[int(v) for v in counts])
+        pa = (SphParams * k)(*[params(p) for p in prms])
+        self._check(self.lib.sph_batch_set(self.h, k, cnt, pa, _stream(stream)))
+
+    def batch_step(self, arrays: dict, nsteps: int = 1, stream=None):
+        P = particles(arrays)
+        self._check(self.lib.sph_batch_step(self.h, C.byref(P), int(nsteps), _stream(stream)))
 
     def sync(self, stream=None) -> int:
         """Wait for the stream; return the device status (SPH_OK, SPH_E_CAPACITY,
@@ -255,7 +274,7 @@ class Context:
         """Neighbour list of the last build as host numpy arrays (offsets,
         idx, ngather, order); rows in internal order, see sph_neighbors."""
         import numpy as np
-        n = int(self._n_last)
+        n = int(self.lib.sph_neighbor_rows(self.h))
         off = np.zeros(n + 1, dtype=np.int64)
         ng = np.zeros(max(n, 1), dtype=np.int32)
         order = np.zeros(max(n, 1), dtype=np.int32)

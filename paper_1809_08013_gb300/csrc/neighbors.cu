@@ -25,6 +25,8 @@
 // iteration count never stalls other particles.
 #include <math_constants.h>
 
+#include <algorithm>
+
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -347,8 +349,8 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
 }
 
 __global__ void __launch_bounds__(kThreads, 3)
-k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
-          const float4* __restrict__ fpos, const int2* __restrict__ cells,
+k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos,
+          const int2* __restrict__ cells,
           int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ gslab,
           double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
           int32_t* __restrict__ wl, unsigned* __restrict__ status) {
@@ -357,7 +359,12 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < n;
+    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);  // one per block
+    const Grid* __restrict__ g = B.grid + inst;
+    const KParams& kp = B.kp[inst];
+    cells += g->cbase;
+    const bool inb = i < n;
+    const bool valid = inb && slot_real(B, inst, i);
     double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
     float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
@@ -366,8 +373,9 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
     }
     double h = pi.w, lo = 0.0, hi = CUDART_INF;
     const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
+    const int max_it = kp.max_h_iter;
     int cnt = 0, it = 0;
-    bool active = valid && kp.max_h_iter > 0, conv = false, deferred = false;
+    bool active = valid && max_it > 0, conv = false, deferred = false;
     int32_t* slab = gslab + (valid ? i : 0) * kGSlab;
     const bool per = g->periodic_z != 0;
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
@@ -457,7 +465,7 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
             if (cnt >= lowb && cnt <= highb) {
                 conv = true;
                 active = false;
-            } else if (it >= kp.max_h_iter) {
+            } else if (it >= max_it) {
                 active = false;
             } else if (cnt < lowb) {
                 lo = h;
@@ -468,7 +476,14 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
             }
         }
     }
-    if (!valid || deferred) return;
+    if (!valid) {
+        if (inb) {  // empty slot: empty row
+            nnb[i] = 0;
+            ngather[i] = 0;
+        }
+        return;
+    }
+    if (deferred) return;
     posh[i].w = h;
     nnb[i] = cnt;
     ngather[i] = cnt;
@@ -482,8 +497,8 @@ k_h_union(int64_t n, const Grid* __restrict__ g, KParams kp, double4_32a* posh,
 // Phase 2: one warp per handed-over particle (persistent grid over the
 // worklist), continuing its bisection where phase 1 stopped.
 __global__ void __launch_bounds__(kThreads)
-k_h_iterate(const Grid* __restrict__ g, KParams kp, double4_32a* posh,
-            const float4* __restrict__ fpos, const int2* __restrict__ cells,
+k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
+            const int2* __restrict__ cells,
             int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
             int32_t* __restrict__ gslab, const double* __restrict__ hs_lo,
             const double* __restrict__ hs_hi, const int32_t* __restrict__ hs_it,
@@ -494,21 +509,26 @@ k_h_iterate(const Grid* __restrict__ g, KParams kp, double4_32a* posh,
     const unsigned count = *(volatile unsigned*)&status[3];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const unsigned lt = (1u << lane) - 1u;
-    const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nwarps) {
         const int64_t i = wl[w];
+        const int inst = slot_inst(B, i);
+        const Grid* __restrict__ g = B.grid + inst;
+        const KParams& kp = B.kp[inst];
+        const int2* __restrict__ cl = cells + g->cbase;
+        const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
+        const int max_it = kp.max_h_iter;
         const double4_32a pi = posh[i];
         const float4 fi = fpos[i];
         double h = pi.w, lo = hs_lo[i], hi = hs_hi[i];
         int cnt = 0;
         bool conv = false;
         int32_t* slab = gslab + i * kGSlab;
-        for (int it = hs_it[i]; it < kp.max_h_iter; ++it) {
+        for (int it = hs_it[i]; it < max_it; ++it) {
             const double R = 2.0 * h;
             const Thr t = thresholds(R, g);
             double R2 = -1.0;  // (2h)^2 in FP64, formed on first use
             int c = 0;
-            particle_pass<1>(g, cells, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
+            particle_pass<1>(g, cl, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
                              [&](bool valid, int j) {
                                  bool in = false, bd = false;
                                  if (valid && j != i) {
@@ -532,7 +552,7 @@ k_h_iterate(const Grid* __restrict__ g, KParams kp, double4_32a* posh,
                 conv = true;
                 break;
             }
-            if (it == kp.max_h_iter - 1) break;
+            if (it == max_it - 1) break;
             if (cnt < lowb) {
                 lo = h;
                 h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
@@ -556,21 +576,27 @@ k_h_iterate(const Grid* __restrict__ g, KParams kp, double4_32a* posh,
 
 // Per-particle FP32 thresholds at the final h.
 __global__ void __launch_bounds__(kThreads)
-k_finalize_h(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ posh,
+k_finalize_h(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              float4* __restrict__ fpos, float* __restrict__ tin, int32_t* __restrict__ ocnt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const Thr t = thresholds(2.0 * posh[i].w, g);
+    ocnt[i] = 0;
+    const int inst = slot_inst(B, i);
+    if (!slot_real(B, inst, i)) return;
+    const Thr t = thresholds(2.0 * posh[i].w, B.grid + inst);
     fpos[i].w = t.tout;
     tin[i] = t.tin;
-    ocnt[i] = 0;
 }
 
-// Per-cell max h, and the global max (one atomic per block).
+// Per-cell max h, and the instance's max (one atomic per block); blockIdx.y
+// is the instance.
 __global__ void __launch_bounds__(kThreads)
-k_cell_hmax(const Grid* __restrict__ gc, Grid* gw, const int2* __restrict__ cells,
+k_cell_hmax(Batch B, Grid* gw, const int2* __restrict__ cells,
             const double4_32a* __restrict__ posh, unsigned long long* __restrict__ cell_hmax) {
-    const long long nc = gc->ncells;
+    const int inst = blockIdx.y;
+    const long long nc = B.grid[inst].ncells, cb = B.grid[inst].cbase;
+    cells += cb;
+    cell_hmax += cb;
     long long bmax = 0;  // bits of positive doubles order like their values
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
          c += (long long)gridDim.x * blockDim.x) {
@@ -594,7 +620,7 @@ k_cell_hmax(const Grid* __restrict__ gc, Grid* gw, const int2* __restrict__ cell
     if (threadIdx.x == 0) {
         long long m = sh[0];
         for (int w = 1; w < kThreads / 32; ++w) m = sh[w] > m ? sh[w] : m;
-        atomicMax(&gw->hmax_bits, (unsigned long long)m);
+        atomicMax(&gw[inst].hmax_bits, (unsigned long long)m);
     }
 }
 
@@ -606,13 +632,16 @@ k_cell_hmax(const Grid* __restrict__ gc, Grid* gw, const int2* __restrict__ cell
 // k_rowlen forms |S_i|, and k_compose writes each CSR row: the gather slab,
 // then the outer slab sorted by index (deterministic rows).
 __global__ void __launch_bounds__(kThreads)
-k_outer(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ posh,
+k_outer(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const float4* __restrict__ fpos, const float* __restrict__ tin,
         const int32_t* __restrict__ ngather, const int32_t* __restrict__ gslab,
         int32_t* __restrict__ ocnt, int32_t* __restrict__ oslab, unsigned* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n || (status[2] & IF_SLAB_OVF)) return;
+    const int inst = slot_inst(B, i);
+    if (!slot_real(B, inst, i)) return;
+    const Grid* __restrict__ g = B.grid + inst;
     const int ng = ngather[i];
     const float4 fi = fpos[i];
     // the slab row is read up front so the dependent loads of the entries overlap
@@ -703,7 +732,7 @@ k_compose(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __restr
 // A cell is visited when its box lies within 2 max(h_i, max h of the cell).
 template <bool FILL>
 __global__ void __launch_bounds__(kThreads)
-k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ posh,
+k_csr(int64_t n, Batch B, const double4_32a* __restrict__ posh,
       const float4* __restrict__ fpos, const float* __restrict__ tin,
       const int2* __restrict__ cells, const unsigned long long* __restrict__ cell_hmax,
       int32_t* __restrict__ rowlen, int32_t* __restrict__ ngather,
@@ -720,6 +749,17 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
     }
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = gw; i < n; i += nwarps) {  // persistent: one warp per particle in turn
+    const int inst = slot_inst(B, i);
+    if (!slot_real(B, inst, i)) {
+        if (!FILL && lane == 0) {
+            rowlen[i] = 0;
+            ngather[i] = 0;
+        }
+        continue;
+    }
+    const Grid* __restrict__ g = B.grid + inst;
+    const int2* __restrict__ cl = cells + g->cbase;
+    const unsigned long long* __restrict__ chm = cell_hmax + g->cbase;
     const double4_32a pi = posh[i];
     const float4 fi = fpos[i];
     const float tin_i = tin[i];
@@ -735,7 +775,7 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
         po_end = offsets[i + 1];
     }
     int cg = 0, co = 0;
-    particle_pass<2>(g, cells, cell_hmax, fi, Rbig, hib, s_start[warp], s_pref[warp],
+    particle_pass<2>(g, cl, chm, fi, Rbig, hib, s_start[warp], s_pref[warp],
                         [&](bool valid, int j) {
         bool in_i = false, in_j = false;
         if (valid && j != i) {
@@ -782,19 +822,22 @@ k_csr(int64_t n, const Grid* __restrict__ g, const double4_32a* __restrict__ pos
     }
 }
 
-void launch_h_search(sph_ctx* c, const KParams& kp, cudaStream_t s) {
+void launch_h_search(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     double4_32a* posh = c->posh[c->cur];
+    const Batch B = batch_of(c);
     c->launches += 4;
-    k_h_union<<<nb, kThreads, 0, s>>>(n, c->grid, kp, posh, c->fpos, c->cells, c->nnb, c->ngather,
+    k_h_union<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb, c->ngather,
                                       c->gslab, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->status);
-    k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(c->grid, kp, posh, c->fpos, c->cells,
-                                                       c->nnb, c->ngather, c->gslab, c->hs_lo,
-                                                       c->hs_hi, c->hs_it, c->wl, c->status);
-    k_finalize_h<<<nb, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->ocnt);
-    k_cell_hmax<<<kReduceBlocks, kThreads, 0, s>>>(c->grid, c->grid, c->cells, posh, c->cell_hmax);
+    k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(B, posh, c->fpos, c->cells, c->nnb,
+                                                       c->ngather, c->gslab, c->hs_lo, c->hs_hi,
+                                                       c->hs_it, c->wl, c->status);
+    k_finalize_h<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ocnt);
+    const unsigned gx = (unsigned)std::max(2, kReduceBlocks / c->ninst);
+    k_cell_hmax<<<dim3(gx, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->grid, c->cells, posh,
+                                                                  c->cell_hmax);
 }
 
 void launch_csr(sph_ctx* c, cudaStream_t s) {
@@ -807,19 +850,20 @@ void launch_csr(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const unsigned nbw = (unsigned)((n * 32 + kThreads - 1) / kThreads);
     double4_32a* posh = c->posh[c->cur];
+    const Batch B = batch_of(c);
     c->launches += 8;
-    k_outer<<<nbw, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->ngather, c->gslab,
-                                     c->ocnt, c->oslab, c->status);
+    k_outer<<<nbw, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ngather, c->gslab, c->ocnt,
+                                     c->oslab, c->status);
     k_rowlen<<<nb, kThreads, 0, s>>>(n, c->ngather, c->ocnt, c->rowlen, c->status);
-    k_csr<false><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
-                                          c->cell_hmax, c->rowlen, c->ngather, nullptr, nullptr,
-                                          c->nnzcap, c->status);
+    k_csr<false><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->cells,
+                                                        c->cell_hmax, c->rowlen, c->ngather,
+                                                        nullptr, nullptr, c->nnzcap, c->status);
     launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s);
     k_compose<<<nbw, kThreads, 0, s>>>(n, c->ngather, c->gslab, c->ocnt, c->oslab, c->offsets,
                                        c->idx, c->nnzcap, c->status);
-    k_csr<true><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, c->grid, posh, c->fpos, c->tin, c->cells,
-                                         c->cell_hmax, c->rowlen, c->ngather, c->offsets, c->idx,
-                                         c->nnzcap, c->status);
+    k_csr<true><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->cells,
+                                                       c->cell_hmax, c->rowlen, c->ngather,
+                                                       c->offsets, c->idx, c->nnzcap, c->status);
 }
 
 }  // namespace sph

@@ -96,16 +96,20 @@ __device__ __forceinline__ void eos(const KParams& kp, double rho, double u, dou
 // written: therm = (rho/2, p/rho^2, alpha c/2, h/2), kern = (1/h, 1/h^4).
 template <bool FUSE>
 __global__ void __launch_bounds__(kThreads)
-k_density(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+k_density(int64_t n, Batch B, const double4_32a* __restrict__ posh,
           const double4_32a* __restrict__ velm, const double* __restrict__ ue,
           const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
           const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
           double2* __restrict__ kern, double* __restrict__ pint, double* __restrict__ cint) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || offsets[n] > nnzcap) return;
+    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
+    if (i >= n || !slot_real(B, inst, i) || offsets[n] > nnzcap) return;
+    const KParams& kp = B.kp[inst];
     const double4_32a pi = posh[i];
     const double hinv = 1.0 / pi.w;
     const long long half_bits = bits(0.5 * kp.lz);
+    const bool per = kp.periodic_z != 0;
+    const double lz = kp.lz;
     double acc = 0.0;
     const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
     for (int64_t e = e0; e < e1; ++e) {
@@ -114,7 +118,7 @@ k_density(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
         const double mj = velm[j].w;
         const double dx = pi.x - pj.x, dy = pi.y - pj.y;
         double dz = pi.z - pj.z;
-        if (kp.periodic_z) dz = wrap_z(dz, half_bits, kp.lz);
+        if (per) dz = wrap_z(dz, half_bits, lz);
         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
         // r2 > 0 for j != i unless two particles coincide; r = r2 / sqrt(r2)
         const double q = bits(r2) > 0 ? r2 * rsqrt_nr(r2) * hinv : 0.0;
@@ -135,27 +139,28 @@ k_density(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
     }
 }
 
-void launch_density(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s) {
-    if (kp.precision == PREC_MIXED) {
+void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
+    if (c->prec == PREC_MIXED) {
         launch_pack_mx(c, false, s);
-        launch_density_mx(c, kp, fuse_eos, s);
+        launch_density_mx(c, fuse_eos, s);
         return;
     }
-    if (kp.precision != PREC_FP64_NATIVE) {
-        launch_density_df(c, kp, fuse_eos, s);
+    if (c->prec != PREC_FP64_NATIVE) {
+        launch_density_df(c, fuse_eos, s);
         return;
     }
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const int b = c->cur;
+    const Batch B = batch_of(c);
     c->launches += 1;
     if (fuse_eos)
-        k_density<true><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->ue[b],
+        k_density<true><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->ue[b],
                                                 c->offsets, c->ngather, c->idx, c->nnzcap,
                                                 c->therm, c->kern, c->pint, c->cint);
     else
-        k_density<false><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->ue[b],
+        k_density<false><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->ue[b],
                                                  c->offsets, c->ngather, c->idx, c->nnzcap,
                                                  c->therm, c->kern, c->pint, c->cint);
 }
@@ -190,19 +195,23 @@ void launch_eos_caller(const KParams& kp, const sph_particles* P, cudaStream_t s
 // R = 1 / ((r^2 + eta2 hb^2) rhob): mu = hb v.r rhob R and 1/rhob = (r^2 +
 // eta2 hb^2) R; Pi = mu (beta mu - alpha cb) / rhob.
 __global__ void __launch_bounds__(kThreads)
-k_forces(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+k_forces(int64_t n, Batch B, const double4_32a* __restrict__ posh,
          const double4_32a* __restrict__ velm, const double4_32a* __restrict__ therm,
          const double2* __restrict__ kern, const double* __restrict__ cint,
          const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
          double4_32a* __restrict__ acc, double* __restrict__ mumax, double* __restrict__ dt_part) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
     double dtc = CUDART_INF;
-    if (i < n && offsets[n] <= nnzcap) {
+    if (i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap) {
+        const KParams& kp = B.kp[inst];
         const double4_32a pi = posh[i];
         const double4_32a vi = velm[i];
         const double4_32a ti = therm[i];
         const double2 ki = kern[i];
         const long long half_bits = bits(0.5 * kp.lz);
+        const bool per = kp.periodic_z != 0;
+        const double lz = kp.lz;
         const double eta2 = kp.eta2, beta = kp.beta;
         double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0, sv = 0.0;
         long long mum = 0;  // bits of max |mu| (non-negative doubles order as integers)
@@ -215,7 +224,7 @@ k_forces(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
             const double2 kj = __ldg(&kern[j]);
             const double dx = pi.x - pj.x, dy = pi.y - pj.y;
             double dz = pi.z - pj.z;
-            if (kp.periodic_z) dz = wrap_z(dz, half_bits, kp.lz);
+            if (per) dz = wrap_z(dz, half_bits, lz);
             const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
             if (bits(r2) == 0) continue;  // coincident particles exert no force
             const double rinv = rsqrt_nr(r2);
@@ -248,7 +257,9 @@ k_forces(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
         acc[i] = make_double4_32a(-sx, -sy, -sz, fma(ti.y, sp, 0.5 * sv));
         mumax[i] = mu_max;
         const double ci = cint[i];
-        dtc = pi.w / (ci + 1.2 * (kp.alpha * ci + kp.beta * mu_max));
+        // parameters re-read here rather than kept in registers across the loop
+        const KParams& ke = B.kp[slot_inst(B, (int64_t)blockIdx.x * blockDim.x)];
+        dtc = pi.w / (ci + 1.2 * (ke.alpha * ci + ke.beta * mu_max));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
@@ -262,12 +273,16 @@ k_forces(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
     }
 }
 
-// dt = cfl * min over the block partials; optionally time += dt.
+// One block per instance: dt[k] = cfl_k * min over the instance's block
+// partials; time[k] += dt[k] when time is given.
 __global__ void __launch_bounds__(kThreads)
-k_dt_finish(const double* __restrict__ part, int np, double cfl, double* __restrict__ dt_out,
+k_dt_finish(const double* __restrict__ part, Batch B, double* __restrict__ dt_out,
             double* __restrict__ time) {
+    const int inst = blockIdx.x;
+    const int64_t b0 = B.ioff[inst] / kSlotAlign;
+    const int64_t nbk = (B.icnt[inst] + kSlotAlign - 1) / kSlotAlign;
     double m = CUDART_INF;
-    for (int k = threadIdx.x; k < np; k += blockDim.x) m = fmin(m, part[k]);
+    for (int64_t k = threadIdx.x; k < nbk; k += blockDim.x) m = fmin(m, part[b0 + k]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
     __shared__ double sh[kThreads / 32];
@@ -276,41 +291,43 @@ k_dt_finish(const double* __restrict__ part, int np, double cfl, double* __restr
     if (threadIdx.x == 0) {
         double r = sh[0];
         for (int w = 1; w < kThreads / 32; ++w) r = fmin(r, sh[w]);
-        const double dt = cfl * r;
-        *dt_out = dt;
-        if (time) *time = *time + dt;
+        const double dt = B.kp[inst].cfl * r;
+        dt_out[inst] = dt;
+        if (time) time[inst] = time[inst] + dt;
     }
 }
 
-void launch_forces(sph_ctx* c, const KParams& kp, double* dt_out, double* time_inout,
-                   cudaStream_t s) {
+void launch_forces(sph_ctx* c, double* dt_out, double* time_inout, cudaStream_t s) {
     const int64_t n = c->n;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const int b = c->cur;
+    const Batch B = batch_of(c);
     c->launches += 1;
-    if (kp.precision == PREC_MIXED)
-        launch_forces_mx(c, kp, s);
-    else if (kp.precision != PREC_FP64_NATIVE)
-        launch_forces_df(c, kp, s);
+    if (c->prec == PREC_MIXED)
+        launch_forces_mx(c, s);
+    else if (c->prec != PREC_FP64_NATIVE)
+        launch_forces_df(c, s);
     else if (n > 0) {
         c->launches += 1;
-        k_forces<<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->therm, c->kern,
+        k_forces<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->therm, c->kern,
                                          c->cint, c->offsets, c->idx, c->nnzcap, c->acc,
                                          c->mumax, c->dt_part);
     }
-    k_dt_finish<<<1, kThreads, 0, s>>>(c->dt_part, n > 0 ? (int)nb : 0, kp.cfl, dt_out,
-                                       time_inout);
+    k_dt_finish<<<c->ninst, kThreads, 0, s>>>(c->dt_part, B, dt_out, time_inout);
 }
 
 // ------------------------------------------------------------ leapfrog
 // Kick-drift (reading of Algorithm 1 step 6): v += dt a, u += dt du,
 // x += dt v (new v); z wrapped into [-lz/2, lz/2) when periodic.
 __global__ void __launch_bounds__(kThreads)
-k_leapfrog(int64_t n, KParams kp, const double* __restrict__ dtp, double4_32a* __restrict__ posh,
+k_leapfrog(int64_t n, Batch B, const double* __restrict__ dtp, double4_32a* __restrict__ posh,
            double4_32a* __restrict__ velm, double* __restrict__ ue, const double4_32a* __restrict__ acc) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const double dt = *dtp;
+    const int inst = slot_inst(B, k);
+    if (!slot_real(B, inst, k)) return;
+    const KParams& kp = B.kp[inst];
+    const double dt = dtp[inst];
     double4_32a p = posh[k];
     double4_32a v = velm[k];
     const double4_32a a = acc[k];
@@ -330,13 +347,13 @@ k_leapfrog(int64_t n, KParams kp, const double* __restrict__ dtp, double4_32a* _
     velm[k] = v;
 }
 
-void launch_leapfrog(sph_ctx* c, const KParams& kp, const double* dt, cudaStream_t s) {
+void launch_leapfrog(sph_ctx* c, const double* dt, cudaStream_t s) {
     const int64_t n = c->n;
     if (n == 0) return;
     const int b = c->cur;
     c->launches += 1;
     k_leapfrog<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-        n, kp, dt, c->posh[b], c->velm[b], c->ue[b], c->acc);
+        n, batch_of(c), dt, c->posh[b], c->velm[b], c->ue[b], c->acc);
 }
 
 // ------------------------------------------------------------ scatter
@@ -352,6 +369,7 @@ k_scatter(int64_t n, unsigned f, ScatterSrc S, sph_particles P) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t o = S.order[k];
+    if (o < 0) return;  // empty slot
     if (f & (SC_POS | SC_H)) {
         const double4_32a p = S.posh[k];
         if (f & SC_POS) { P.x[o] = p.x; P.y[o] = p.y; P.z[o] = p.z; }

@@ -74,25 +74,29 @@ __device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, d
 // ------------------------------------------------------------ density
 template <bool FUSE>
 __global__ void __launch_bounds__(kThreads)
-k_density_df(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const float2* __restrict__ mdf, const double* __restrict__ ue,
              const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
              const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
              double2* __restrict__ kern, float4* __restrict__ dpk, double* __restrict__ pint,
              double* __restrict__ cint) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || offsets[n] > nnzcap) return;
+    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
+    if (i >= n || !slot_real(B, inst, i) || offsets[n] > nnzcap) return;
+    const KParams& kp = B.kp[inst];
     const double4_32a pi = posh[i];
     const double hinv = 1.0 / pi.w;
     const df Hi = dfl::from_double_fp64(hinv);
     const long long half_bits = bitsd(0.5 * kp.lz);
+    const bool per = kp.periodic_z != 0;
+    const double lz = kp.lz;
     df acc = ld2(mdf, i);  // self term m_i W(0, h_i): shape 1
     const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
     for (int64_t e = e0; e < e1; ++e) {
         const int j = __ldg(&idx[e]);
         const double4_32a pj = posh[j];
         double dz = pi.z - pj.z;
-        if (kp.periodic_z) dz = wrap_z_d(dz, half_bits, kp.lz);
+        if (per) dz = wrap_z_d(dz, half_bits, lz);
         const df X = dfl::from_double(pi.x - pj.x), Y = dfl::from_double(pi.y - pj.y);
         const df Z = dfl::from_double(dz);
         const df r2 = dfl::add(dfl::add(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
@@ -120,18 +124,19 @@ k_density_df(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
     }
 }
 
-void launch_density_df(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s) {
+void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
+    const Batch B = batch_of(c);
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const int b = c->cur;
     c->launches += 1;
     if (fuse_eos)
-        k_density_df<true><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->mdf, c->ue[b], c->offsets,
+        k_density_df<true><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->mdf, c->ue[b], c->offsets,
                                                    c->ngather, c->idx, c->nnzcap, c->therm,
                                                    c->kern, c->dpk, c->pint, c->cint);
     else
-        k_density_df<false><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->mdf, c->ue[b],
+        k_density_df<false><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->mdf, c->ue[b],
                                                     c->offsets, c->ngather, c->idx, c->nnzcap,
                                                     c->therm, c->kern, c->dpk, c->pint, c->cint);
 }
@@ -141,21 +146,25 @@ void launch_density_df(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_
 // f(q_j)/h_j^4)/r, one shared reciprocal R = 1/((r^2 + eta2 hb^2) rhob) for the
 // viscosity, mu = hb v.r rhob R, 1/rhob = (r^2 + eta2 hb^2) R.
 __global__ void __launch_bounds__(kThreads, 3)
-k_forces_df(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
             const float2* __restrict__ mdf, const double* __restrict__ cint,
             const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
             double4_32a* __restrict__ acc, double* __restrict__ mumax,
             double* __restrict__ dt_part) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
     double dtc = CUDART_INF;
-    if (i < n && offsets[n] <= nnzcap) {
+    if (i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap) {
+        const KParams& kp = B.kp[inst];
         const double4_32a pi = posh[i];
         const double4_32a vi = velm[i];
         const float4 a0 = dpk[3 * i], a1 = dpk[3 * i + 1], a2 = dpk[3 * i + 2];
         const df Hi = {a0.x, a0.y}, Ki = {a0.z, a0.w}, Ai = {a1.x, a1.y}, hhi = {a1.z, a1.w};
         const df rhi = {a2.x, a2.y}, cai = {a2.z, a2.w};
         const long long half_bits = bitsd(0.5 * kp.lz);
+        const bool per = kp.periodic_z != 0;
+        const double lz = kp.lz;
         const df c_half_pi = dfl::from_double_fp64(0.5 * kInvPiD);
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
@@ -169,7 +178,7 @@ k_forces_df(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
             const float4 b0 = __ldg(&dpk[3 * j]), b1 = __ldg(&dpk[3 * j + 1]);
             const float4 b2 = __ldg(&dpk[3 * j + 2]);
             double dz = pi.z - pj.z;
-            if (kp.periodic_z) dz = wrap_z_d(dz, half_bits, kp.lz);
+            if (per) dz = wrap_z_d(dz, half_bits, lz);
             const df X = dfl::from_double(pi.x - pj.x), Y = dfl::from_double(pi.y - pj.y);
             const df Z = dfl::from_double(dz);
             const df r2 = dfl::add(dfl::add(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
@@ -210,7 +219,9 @@ k_forces_df(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
         const double mu_max = dfl::to_double(mumx);
         mumax[i] = mu_max;
         const double ci = cint[i];
-        dtc = pi.w / (ci + 1.2 * (kp.alpha * ci + kp.beta * mu_max));
+        // parameters re-read here rather than kept in registers across the loop
+        const KParams& ke = B.kp[slot_inst(B, (int64_t)blockIdx.x * blockDim.x)];
+        dtc = pi.w / (ci + 1.2 * (ke.alpha * ci + ke.beta * mu_max));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
@@ -224,13 +235,14 @@ k_forces_df(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
     }
 }
 
-void launch_forces_df(sph_ctx* c, const KParams& kp, cudaStream_t s) {
+void launch_forces_df(sph_ctx* c, cudaStream_t s) {
+    const Batch B = batch_of(c);
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const int b = c->cur;
     c->launches += 1;
-    k_forces_df<<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->velm[b], c->dpk, c->mdf, c->cint,
+    k_forces_df<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->dpk, c->mdf, c->cint,
                                         c->offsets, c->idx, c->nnzcap, c->acc, c->mumax,
                                         c->dt_part);
 }

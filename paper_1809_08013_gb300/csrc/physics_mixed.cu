@@ -159,13 +159,15 @@ k_pack_mx(int64_t n, const double4_32a* __restrict__ posh, const double4_32a* __
 
 template <bool FUSE>
 __global__ void __launch_bounds__(kThreads)
-k_density_mx(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const double* __restrict__ ue, float4* __restrict__ mpk,
              const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
              const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
              double* __restrict__ pint, double* __restrict__ cint) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || offsets[n] > nnzcap) return;
+    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
+    if (i >= n || !slot_real(B, inst, i) || offsets[n] > nnzcap) return;
+    const KParams& kp = B.kp[inst];
     const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1];
     const float hinv = a1.w;
     const ZWrap zw = make_zwrap(kp);
@@ -197,14 +199,16 @@ k_density_mx(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_forces_mx(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
+k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const float4* __restrict__ mpk, const double* __restrict__ cint,
             const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
             double4_32a* __restrict__ acc, double* __restrict__ mumax,
             double* __restrict__ dt_part) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
     double dtc = CUDART_INF;
-    if (i < n && offsets[n] <= nnzcap) {
+    if (i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap) {
+        const KParams& kp = B.kp[inst];
         const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1], a2 = mpk[5 * i + 2];
         const float4 a3 = mpk[5 * i + 3], a4 = mpk[5 * i + 4];
         const ZWrap zw = make_zwrap(kp);
@@ -253,7 +257,9 @@ k_forces_mx(int64_t n, KParams kp, const double4_32a* __restrict__ posh,
                                   fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)));
         mumax[i] = (double)mum;
         const double ci = cint[i];
-        dtc = posh[i].w / (ci + 1.2 * (kp.alpha * ci + kp.beta * (double)mum));
+        // parameters re-read here rather than kept in registers across the loop
+        const KParams& ke = B.kp[slot_inst(B, (int64_t)blockIdx.x * blockDim.x)];
+        dtc = posh[i].w / (ci + 1.2 * (ke.alpha * ci + ke.beta * (double)mum));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
@@ -279,29 +285,31 @@ void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s) {
         k_pack_mx<false><<<nb, kThreads, 0, s>>>(n, c->posh[b], c->velm[b], c->therm, c->mpk);
 }
 
-void launch_density_mx(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s) {
+void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
+    const Batch B = batch_of(c);
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const int b = c->cur;
     c->launches += 1;
     if (fuse_eos)
-        k_density_mx<true><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->ue[b], c->mpk, c->offsets,
+        k_density_mx<true><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->ue[b], c->mpk, c->offsets,
                                                    c->ngather, c->idx, c->nnzcap, c->therm,
                                                    c->pint, c->cint);
     else
-        k_density_mx<false><<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->ue[b], c->mpk,
+        k_density_mx<false><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->ue[b], c->mpk,
                                                     c->offsets, c->ngather, c->idx, c->nnzcap,
                                                     c->therm, c->pint, c->cint);
 }
 
-void launch_forces_mx(sph_ctx* c, const KParams& kp, cudaStream_t s) {
+void launch_forces_mx(sph_ctx* c, cudaStream_t s) {
+    const Batch B = batch_of(c);
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const int b = c->cur;
     c->launches += 1;
-    k_forces_mx<<<nb, kThreads, 0, s>>>(n, kp, c->posh[b], c->mpk, c->cint, c->offsets, c->idx,
+    k_forces_mx<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->mpk, c->cint, c->offsets, c->idx,
                                         c->nnzcap, c->acc, c->mumax, c->dt_part);
 }
 

@@ -11,30 +11,43 @@
 namespace sph {
 
 // ------------------------------------------------------------------ state I/O
+// Caller arrays (instances back to back) into the slot layout: instance k's
+// particle r goes to slot ioff[k] + r; empty slots get an inert state and
+// order = -1.
 __global__ void __launch_bounds__(kThreads)
-k_load_state(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
-             const double* __restrict__ z, const double* __restrict__ h,
-             const double* __restrict__ vx, const double* __restrict__ vy,
-             const double* __restrict__ vz, const double* __restrict__ m,
-             const double* __restrict__ u, double4_32a* __restrict__ posh,
-             double4_32a* __restrict__ velm, double* __restrict__ ue, int32_t* __restrict__ order) {
+k_load_state(int64_t n, Batch B, const int64_t* __restrict__ coff, const double* __restrict__ x,
+             const double* __restrict__ y, const double* __restrict__ z,
+             const double* __restrict__ h, const double* __restrict__ vx,
+             const double* __restrict__ vy, const double* __restrict__ vz,
+             const double* __restrict__ m, const double* __restrict__ u,
+             double4_32a* __restrict__ posh, double4_32a* __restrict__ velm,
+             double* __restrict__ ue, int32_t* __restrict__ order) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    posh[k] = make_double4_32a(x[k], y[k], z[k], h[k]);
-    velm[k] = make_double4_32a(vx ? vx[k] : 0.0, vy ? vy[k] : 0.0, vz ? vz[k] : 0.0, m ? m[k] : 0.0);
-    ue[k] = u ? u[k] : 0.0;
-    order[k] = (int32_t)k;
+    const int inst = slot_inst(B, k);
+    const int64_t r = k - __ldg(&B.ioff[inst]);
+    if (r >= __ldg(&B.icnt[inst])) {
+        posh[k] = make_double4_32a(0.0, 0.0, 0.0, 1.0);
+        velm[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        ue[k] = 0.0;
+        order[k] = -1;
+        return;
+    }
+    const int64_t c = __ldg(&coff[inst]) + r;
+    posh[k] = make_double4_32a(x[c], y[c], z[c], h[c]);
+    velm[k] = make_double4_32a(vx ? vx[c] : 0.0, vy ? vy[c] : 0.0, vz ? vz[c] : 0.0, m ? m[c] : 0.0);
+    ue[k] = u ? u[c] : 0.0;
+    order[k] = (int32_t)c;
 }
 
 void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s) {
-    const int64_t n = P->n;
-    c->n = n;
+    const int64_t n = c->n;
     if (n == 0) return;
     const int b = c->cur;
     c->launches += 1;
     k_load_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-        n, P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m, P->u, c->posh[b], c->velm[b],
-        c->ue[b], c->order[b]);
+        n, batch_of(c), c->coff, P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m, P->u,
+        c->posh[b], c->velm[b], c->ue[b], c->order[b]);
 }
 
 // Re-read the caller's arrays into the sorted order of the last build and
@@ -53,6 +66,7 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t o = order[k];
+    if (o < 0) return;  // empty slot
     const double hh = h[o];
     posh[k] = make_double4_32a(x[o], y[o], z[o], hh);
     const double mm = m[o];
@@ -85,21 +99,20 @@ void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, 
 }
 
 // ------------------------------------------------------------ bbox and grid
+// One partial per block of kSlotAlign slots (one instance): min x, y, z,
+// -max x, y, z, -max h, sum h over its particles, reduced in a fixed order.
 __global__ void __launch_bounds__(kThreads)
-k_bbox(int64_t n, const double4_32a* __restrict__ posh, double* __restrict__ part) {
-    double mn0 = CUDART_INF, mn1 = CUDART_INF, mn2 = CUDART_INF;
-    double mx0 = -CUDART_INF, mx1 = -CUDART_INF, mx2 = -CUDART_INF;
-    double hmx = 0.0, hs = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
+k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh, double* __restrict__ part) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[8] = {CUDART_INF, CUDART_INF, CUDART_INF, CUDART_INF,
+                   CUDART_INF, CUDART_INF, CUDART_INF, 0.0};
+    if (k < n && slot_real(B, slot_inst(B, k), k)) {
         const double4_32a p = posh[k];
-        mn0 = fmin(mn0, p.x); mx0 = fmax(mx0, p.x);
-        mn1 = fmin(mn1, p.y); mx1 = fmax(mx1, p.y);
-        mn2 = fmin(mn2, p.z); mx2 = fmax(mx2, p.z);
-        hmx = fmax(hmx, p.w);
-        hs += p.w;
+        v[0] = p.x; v[1] = p.y; v[2] = p.z;
+        v[3] = -p.x; v[4] = -p.y; v[5] = -p.z;
+        v[6] = -p.w;
+        v[7] = p.w;
     }
-    double v[8] = {mn0, mn1, mn2, -mx0, -mx1, -mx2, -hmx, hs};
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -129,28 +142,59 @@ __device__ __forceinline__ int grid_count(double ext, double w, double* wout) {
     return (int)c;
 }
 
-// One block: reduce the bbox partials and derive the cell grid. The cell width
-// is 2 <h> cell_scale (<h> the mean smoothing length); the neighbour sets do
-// not depend on it, only the number of candidates and cells visited do.
-__global__ void __launch_bounds__(32)
-k_grid_setup(const double* __restrict__ part, int nb, int64_t n, KParams kp, int64_t cellcap,
-             Grid* __restrict__ g, unsigned* __restrict__ status) {
+// One block per instance: reduce the instance's bbox partials (fixed order:
+// thread t takes partials t, t + 1024, ..., then a fixed tree) and derive its
+// cell grid. The cell width is 2 <h> cell_scale (<h> the mean smoothing
+// length), widened while the grid would exceed the instance's cell budget;
+// the neighbour sets do not depend on it, only the candidates visited do.
+constexpr int kGridThreads = 1024;
+
+__global__ void __launch_bounds__(kGridThreads)
+k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
+             unsigned* __restrict__ status) {
+    const int inst = blockIdx.x;
+    const int64_t n = B.icnt[inst];
+    const int64_t b0 = B.ioff[inst] / kSlotAlign;
+    const int64_t nbk = (n + kSlotAlign - 1) / kSlotAlign;
+    double v[8] = {CUDART_INF, CUDART_INF, CUDART_INF, CUDART_INF,
+                   CUDART_INF, CUDART_INF, CUDART_INF, 0.0};
+    for (int64_t b = threadIdx.x; b < nbk; b += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) v[q] = fmin(v[q], part[(b0 + b) * 8 + q]);
+        v[7] += part[(b0 + b) * 8 + 7];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) v[q] = fmin(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+        v[7] += __shfl_xor_sync(0xffffffffu, v[7], o);
+    }
+    __shared__ double sh[kGridThreads / 32][8];
     __shared__ double r[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < 8; ++q) sh[warp][q] = v[q];
+    __syncthreads();
     if (threadIdx.x < 8) {
         const int q = threadIdx.x;
-        double a = (q == 7) ? 0.0 : CUDART_INF;
-        for (int b = 0; b < nb; ++b) a = (q == 7) ? a + part[b * 8 + q] : fmin(a, part[b * 8 + q]);
+        double a = sh[0][q];
+        for (int w = 1; w < kGridThreads / 32; ++w) a = (q == 7) ? a + sh[w][q] : fmin(a, sh[w][q]);
         r[q] = a;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
+    const KParams kp = B.kp[inst];
+    Grid* g = grid + inst;
+    const long long cellcap = g->cap;
     double mn[3] = {r[0], r[1], r[2]};
     double mx[3] = {-r[3], -r[4], -r[5]};
     if (n == 0) {
         for (int d = 0; d < 3; ++d) { mn[d] = 0.0; mx[d] = 0.0; }
     }
-    status[2] = 0u;
-    status[3] = 0u;
+    if (inst == 0) {
+        status[2] = 0u;
+        status[3] = 0u;
+    }
     const double hmean = n > 0 ? r[7] / (double)n : 1.0;
     double w = 2.0 * hmean * kp.cell_scale;
     if (!(w > 0.0) || !isfinite(w)) w = 1.0;
@@ -228,16 +272,25 @@ __device__ __forceinline__ int cell_coord(double v, double lo, double inv, int n
     return (int)f;
 }
 
+// key = instance (top 8 bits) | 24-bit Morton code of the particle's cell in
+// its instance's grid; empty slots take their instance's largest code, and
+// the stable sort keeps them after the instance's particles.
 __global__ void __launch_bounds__(kThreads)
-k_keys(int64_t n, const double4_32a* __restrict__ posh, const Grid* __restrict__ g,
-       uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+k_keys(int64_t n, Batch B, const double4_32a* __restrict__ posh, uint32_t* __restrict__ keys,
+       int32_t* __restrict__ vals) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const double4_32a p = posh[k];
-    const int kx = cell_coord(p.x, g->lo[0], g->inv_w[0], g->n[0]);
-    const int ky = cell_coord(p.y, g->lo[1], g->inv_w[1], g->n[1]);
-    const int kz = cell_coord(p.z, g->lo[2], g->inv_w[2], g->n[2]);
-    keys[k] = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+    const int inst = slot_inst(B, k);
+    uint32_t code = 0xffffffu;
+    if (slot_real(B, inst, k)) {
+        const Grid* g = B.grid + inst;
+        const double4_32a p = posh[k];
+        const int kx = cell_coord(p.x, g->lo[0], g->inv_w[0], g->n[0]);
+        const int ky = cell_coord(p.y, g->lo[1], g->inv_w[1], g->n[1]);
+        const int kz = cell_coord(p.z, g->lo[2], g->inv_w[2], g->n[2]);
+        code = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+    }
+    keys[k] = ((uint32_t)inst << 24) | code;
     vals[k] = (int32_t)k;
 }
 
@@ -332,45 +385,54 @@ k_permute(int64_t n, const int32_t* __restrict__ perm, const double4_32a* __rest
     fpos[k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
 }
 
+// Clear each instance's cells (blockIdx.y = instance).
 __global__ void __launch_bounds__(kThreads)
-k_cells_clear(const Grid* __restrict__ g, int2* __restrict__ cells,
-              unsigned long long* __restrict__ cell_hmax) {
-    const long long nc = g->ncells;
+k_cells_clear(Batch B, int2* __restrict__ cells, unsigned long long* __restrict__ cell_hmax) {
+    const Grid* g = B.grid + blockIdx.y;
+    const long long nc = g->ncells, cb = g->cbase;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
          c += (long long)gridDim.x * blockDim.x) {
-        cells[c] = make_int2(0, 0);
-        cell_hmax[c] = 0ull;
+        cells[cb + c] = make_int2(0, 0);
+        cell_hmax[cb + c] = 0ull;
     }
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_cells_mark(int64_t n, const uint32_t* __restrict__ keys, const Grid* __restrict__ g,
-             int2* __restrict__ cells) {
+k_cells_mark(int64_t n, Batch B, const uint32_t* __restrict__ keys, int2* __restrict__ cells) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    const int inst = slot_inst(B, k);
+    const int64_t a = __ldg(&B.ioff[inst]), e = a + __ldg(&B.icnt[inst]);
+    if (k >= e) return;  // empty slot
     const uint32_t key = keys[k];
-    const bool first = (k == 0) || keys[k - 1] != key;
-    const bool last = (k == n - 1) || keys[k + 1] != key;
+    const bool first = (k == a) || keys[k - 1] != key;
+    const bool last = (k == e - 1) || keys[k + 1] != key;
     if (!(first || last)) return;
-    const int kx = compact3(key), ky = compact3(key >> 1), kz = compact3(key >> 2);
-    const long long lin = ((long long)kz * g->n[1] + ky) * g->n[0] + kx;
+    const Grid* g = B.grid + inst;
+    const uint32_t code = key & 0xffffffu;
+    const int kx = compact3(code), ky = compact3(code >> 1), kz = compact3(code >> 2);
+    const long long lin = g->cbase + ((long long)kz * g->n[1] + ky) * g->n[0] + kx;
     if (first) cells[lin].x = (int)k;
     if (last) cells[lin].y = (int)(k + 1);
 }
 
-void launch_build_cells(sph_ctx* c, const KParams& kp, cudaStream_t s) {
+void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
-    c->launches += 2;
-    k_bbox<<<kReduceBlocks, kThreads, 0, s>>>(n, c->posh[c->cur], c->red_part);
-    k_grid_setup<<<1, 32, 0, s>>>(c->red_part, kReduceBlocks, n, kp, c->cellcap, c->grid,
-                                  c->status);
+    const Batch B = batch_of(c);
+    c->launches += 1;
+    if (nb > 0) {
+        c->launches += 1;
+        k_bbox<<<nb, kThreads, 0, s>>>(n, B, c->posh[c->cur], c->red_part);
+    }
+    k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status);
     if (n == 0) return;
-    c->launches += 1 + 3 * 5 + 3;
-    k_keys<<<nb, kThreads, 0, s>>>(n, c->posh[c->cur], c->grid, c->keys[0], c->vals[0]);
+    const int passes = c->ninst > 1 ? 4 : 3;
+    c->launches += 1 + passes * 5 + 3;
+    k_keys<<<nb, kThreads, 0, s>>>(n, B, c->posh[c->cur], c->keys[0], c->vals[0]);
     const int nsb = (int)((n + kRadixTile - 1) / kRadixTile);
     int src = 0;
-    for (int pass = 0; pass < 3; ++pass) {
+    for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
         k_radix_hist<<<nsb, kThreads, 0, s>>>(c->keys[src], n, shift, c->hist, nsb);
         launch_scan_u32(c->hist, (int64_t)256 * nsb, c->hist_part, s);
@@ -384,8 +446,8 @@ void launch_build_cells(sph_ctx* c, const KParams& kp, cudaStream_t s) {
                                        c->order[a], c->posh[b], c->velm[b], c->ue[b], c->order[b],
                                        c->fpos, c->mdf);
     c->cur = b;
-    k_cells_clear<<<kReduceBlocks, kThreads, 0, s>>>(c->grid, c->cells, c->cell_hmax);
-    k_cells_mark<<<nb, kThreads, 0, s>>>(n, c->keys[src], c->grid, c->cells);
+    k_cells_clear<<<dim3(64, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->cells, c->cell_hmax);
+    k_cells_mark<<<nb, kThreads, 0, s>>>(n, B, c->keys[src], c->cells);
 }
 
 }  // namespace sph

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "sph_internal.cuh"
 
@@ -90,7 +91,7 @@ void free_all(sph_ctx* c) {
                     c->order[1], c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist,
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->gslab, c->oslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
-                    c->status, c->scratch_scalar};
+                    c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -119,9 +120,73 @@ void free_events(sph_ctx* c) {
 
 }  // namespace
 
+namespace sph {
+
+// Batch-of-one descriptors for a single problem of n particles, written on the
+// stream (kernel arguments are captured at launch, so back-to-back calls with
+// different parameters cannot overwrite each other's).
+__global__ void __launch_bounds__(kThreads)
+k_set_single(KParams kp, int64_t n, long long cap, int64_t nblk, int32_t* __restrict__ blk,
+             int64_t* __restrict__ ioff, int64_t* __restrict__ icnt, int64_t* __restrict__ coff,
+             KParams* __restrict__ kpi, Grid* __restrict__ grid) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t b = t; b < nblk; b += (int64_t)gridDim.x * blockDim.x) blk[b] = 0;
+    if (t == 0) {
+        kpi[0] = kp;
+        ioff[0] = 0;
+        ioff[1] = n;
+        icnt[0] = n;
+        coff[0] = 0;
+        coff[1] = n;
+        grid[0].cbase = 0;
+        grid[0].cap = cap;
+    }
+}
+
+void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s) {
+    c->n = n;
+    c->ntot = n;
+    c->ninst = 1;
+    c->prec = kp.precision;
+    const int64_t nblk = (n + kSlotAlign - 1) / kSlotAlign;
+    const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((nblk + kThreads - 1) / kThreads, 1), 1024);
+    c->launches += 1;
+    k_set_single<<<nb, kThreads, 0, s>>>(kp, n, instance_cell_cap(n), nblk, c->blk, c->ioff,
+                                         c->icnt, c->coff, c->kpi, c->grid);
+}
+
+// nsteps steps of the current batch: the caller's arrays are read into the
+// slot layout, and the final state is written back after the last step.
+void run_steps(sph_ctx* c, sph_particles* P, int nsteps, cudaStream_t s) {
+    mark(c, -1, s);
+    launch_load_state(c, P, s);
+    for (int k = 0; k < nsteps; ++k) {
+        launch_build_cells(c, s);
+        mark(c, SPH_PHASE_CELLS, s);
+        launch_h_search(c, s);
+        mark(c, SPH_PHASE_HSEARCH, s);
+        launch_csr(c, s);
+        mark(c, SPH_PHASE_CSR, s);
+        launch_density(c, true, s);
+        mark(c, SPH_PHASE_DENSITY, s);
+        launch_forces(c, P->dt, P->time, s);
+        mark(c, SPH_PHASE_FORCES, s);
+        launch_leapfrog(c, P->dt, s);
+        if (k == nsteps - 1)
+            launch_scatter(c, P, SC_POS | SC_VEL | SC_H | SC_U | SC_RHO | SC_PC | SC_ACC |
+                                     SC_MUMAX | SC_NNB, s);
+        mark(c, SPH_PHASE_UPDATE, s);
+        if (c->timing) c->timed_steps += 1;
+    }
+}
+
+}  // namespace sph
+
 extern "C" {
 
 int64_t sph_launch_count(const sph_ctx* c) { return c ? c->launches : 0; }
+
+int64_t sph_neighbor_rows(const sph_ctx* c) { return c ? c->n : 0; }
 
 sph_status sph_timing_enable(sph_ctx* c, int enable) {
     if (!c) return SPH_E_INVAL;
@@ -191,9 +256,17 @@ const char* sph_last_error(const sph_ctx* c) { return c ? c->err : "context is N
 int64_t sph_last_hnoconv(const sph_ctx* c) { return c ? c->last_hnoconv : 0; }
 
 sph_status sph_ctx_create(sph_ctx** out, int64_t ncap, int64_t nnzcap, int device) {
+    return sph_ctx_create_batch(out, ncap, nnzcap, 1, device);
+}
+
+sph_status sph_ctx_create_batch(sph_ctx** out, int64_t ncap, int64_t nnzcap, int32_t max_instances,
+                                int device) {
     if (!out) return SPH_E_INVAL;
     *out = nullptr;
-    if (ncap < 0 || nnzcap < 0 || ncap > (int64_t)INT32_MAX - 1 || nnzcap > ((int64_t)1 << 40))
+    if (max_instances < 1 || max_instances > SPH_MAX_INSTANCES) return SPH_E_INVAL;
+    // slots: the particles plus the gaps that start every instance on a block boundary
+    const int64_t nslots = ncap + (int64_t)(kSlotAlign - 1) * (max_instances - 1);
+    if (ncap < 0 || nnzcap < 0 || nslots > (int64_t)INT32_MAX - 1 || nnzcap > ((int64_t)1 << 40))
         return SPH_E_INVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -208,9 +281,13 @@ sph_status sph_ctx_create(sph_ctx** out, int64_t ncap, int64_t nnzcap, int devic
     c->device = device;
     c->ncap = ncap;
     c->nnzcap = nnzcap;
-    c->cellcap = std::min<int64_t>(std::max<int64_t>(2 * ncap, 32768),
-                                   (int64_t)kMaxCellsPerAxis * kMaxCellsPerAxis * kMaxCellsPerAxis);
-    const size_t N = (size_t)std::max<int64_t>(ncap, 1);
+    c->maxinst = max_instances;
+    c->ninst = 1;
+    // per-instance budgets instance_cell_cap(n_k) sum to at most this
+    c->cellcap = std::min<int64_t>(2 * ncap + (int64_t)kMinInstanceCells * max_instances,
+                                   (int64_t)max_instances * kMaxCellsPerAxis * kMaxCellsPerAxis *
+                                       kMaxCellsPerAxis);
+    const size_t N = (size_t)std::max<int64_t>(nslots, 1);
     const size_t nsb = (N + kRadixTile - 1) / kRadixTile;
     const size_t nfb = (N + kThreads - 1) / kThreads;
     bool ok = true;
@@ -226,14 +303,18 @@ sph_status sph_ctx_create(sph_ctx** out, int64_t ncap, int64_t nnzcap, int devic
          dalloc(&c->cells, (size_t)c->cellcap) && dalloc(&c->cell_hmax, (size_t)c->cellcap) &&
          dalloc(&c->nnb, N) && dalloc(&c->ngather, N) && dalloc(&c->rowlen, N) &&
          dalloc(&c->offsets, N + 1) && dalloc(&c->row_part, (size_t)scan_parts(N) + 1) &&
-         dalloc(&c->idx, (size_t)nnzcap) && dalloc(&c->red_part, (size_t)kReduceBlocks * 8) &&
-         dalloc(&c->dt_part, nfb) && dalloc(&c->grid, 1) && dalloc(&c->status, 4) &&
+         dalloc(&c->idx, (size_t)nnzcap) && dalloc(&c->red_part, nfb * 8) &&
+         dalloc(&c->dt_part, nfb) && dalloc(&c->grid, (size_t)max_instances) &&
+         dalloc(&c->status, 4) && dalloc(&c->blk, nfb) &&
+         dalloc(&c->ioff, (size_t)max_instances + 1) && dalloc(&c->icnt, (size_t)max_instances) &&
+         dalloc(&c->coff, (size_t)max_instances + 1) && dalloc(&c->kpi, (size_t)max_instances) &&
          dalloc(&c->gslab, N * kGSlab) && dalloc(&c->oslab, N * kOSlab) && dalloc(&c->ocnt, N) &&
          dalloc(&c->hs_lo, N) && dalloc(&c->hs_hi, N) && dalloc(&c->hs_it, N) && dalloc(&c->wl, N) &&
          dalloc(&c->scratch_scalar, 2);
     ok = ok && cudaMallocHost((void**)&c->status_host, 2 * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemset(c->status, 0, 4 * sizeof(unsigned)) == cudaSuccess &&
-         cudaMemset(c->offsets, 0, sizeof(int64_t)) == cudaSuccess;
+         cudaMemset(c->offsets, 0, sizeof(int64_t)) == cudaSuccess &&
+         cudaMemset(c->grid, 0, (size_t)max_instances * sizeof(Grid)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -268,9 +349,10 @@ sph_status sph_build_neighbors(sph_ctx* c, const sph_params* prm, sph_particles*
     DeviceGuard dg(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const KParams kp = kparams(prm);
+    launch_set_single(c, kp, P->n, s);
     launch_load_state(c, P, s);
-    launch_build_cells(c, kp, s);
-    launch_h_search(c, kp, s);
+    launch_build_cells(c, s);
+    launch_h_search(c, s);
     launch_csr(c, s);
     launch_scatter(c, P, SC_H | SC_NNB, s);
     if ((st = check_launch(c, "sph_build_neighbors")) != SPH_OK) return st;
@@ -286,6 +368,10 @@ sph_status sph_build_neighbors(sph_ctx* c, const sph_params* prm, sph_particles*
 }
 
 static sph_status need_build(sph_ctx* c, const sph_particles* P) {
+    if (c->ninst != 1) {
+        set_err(c, "the last build was a batch of %d instances: use sph_batch_step", c->ninst);
+        return SPH_E_INVAL;
+    }
     if (P->n != c->n) {
         set_err(c, "n = %lld differs from the last sph_build_neighbors (n = %lld)",
                 (long long)P->n, (long long)c->n);
@@ -304,8 +390,9 @@ sph_status sph_density(sph_ctx* c, const sph_params* prm, sph_particles* P, void
     DeviceGuard dg(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const KParams kp = kparams(prm);
+    launch_set_single(c, kp, P->n, s);
     launch_gather_state(c, P, kp, GATHER_DENSITY, s);
-    launch_density(c, kp, false, s);
+    launch_density(c, false, s);
     launch_scatter(c, P, SC_RHO, s);
     return check_launch(c, "sph_density");
 }
@@ -338,9 +425,10 @@ sph_status sph_forces(sph_ctx* c, const sph_params* prm, sph_particles* P, void*
     DeviceGuard dg(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const KParams kp = kparams(prm);
+    launch_set_single(c, kp, P->n, s);
     launch_gather_state(c, P, kp, GATHER_FORCES, s);
     if (kp.precision == PREC_MIXED) launch_pack_mx(c, true, s);
-    launch_forces(c, kp, P->dt, nullptr, s);
+    launch_forces(c, P->dt, nullptr, s);
     launch_scatter(c, P, SC_ACC | SC_MUMAX, s);
     return check_launch(c, "sph_forces");
 }
@@ -359,28 +447,99 @@ sph_status sph_step(sph_ctx* c, const sph_params* prm, sph_particles* P, int nst
     }
     DeviceGuard dg(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const KParams kp = kparams(prm);
-    mark(c, -1, s);
-    launch_load_state(c, P, s);
-    for (int k = 0; k < nsteps; ++k) {
-        launch_build_cells(c, kp, s);
-        mark(c, SPH_PHASE_CELLS, s);
-        launch_h_search(c, kp, s);
-        mark(c, SPH_PHASE_HSEARCH, s);
-        launch_csr(c, s);
-        mark(c, SPH_PHASE_CSR, s);
-        launch_density(c, kp, true, s);
-        mark(c, SPH_PHASE_DENSITY, s);
-        launch_forces(c, kp, P->dt, P->time, s);
-        mark(c, SPH_PHASE_FORCES, s);
-        launch_leapfrog(c, kp, P->dt, s);
-        if (k == nsteps - 1)
-            launch_scatter(c, P, SC_POS | SC_VEL | SC_H | SC_U | SC_RHO | SC_PC | SC_ACC |
-                                     SC_MUMAX | SC_NNB, s);
-        mark(c, SPH_PHASE_UPDATE, s);
-        if (c->timing) c->timed_steps += 1;
-    }
+    launch_set_single(c, kparams(prm), P->n, s);
+    run_steps(c, P, nsteps, s);
     return check_launch(c, "sph_step");
+}
+
+sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts,
+                         const sph_params* params, void* stream) {
+    if (!c) return SPH_E_INVAL;
+    if (ninst < 1 || ninst > c->maxinst || !counts || !params) {
+        set_err(c, "ninst = %d outside [1, %d] or NULL arrays", (int)ninst, c->maxinst);
+        return SPH_E_INVAL;
+    }
+    std::vector<int64_t> ioff(ninst + 1), coff(ninst + 1), icnt(ninst);
+    std::vector<KParams> kpi(ninst);
+    std::vector<Grid> grid(ninst);
+    int64_t slots = 0, tot = 0;
+    long long cells = 0;
+    for (int k = 0; k < ninst; ++k) {
+        sph_status st = check_params(c, &params[k]);
+        if (st != SPH_OK) return st;
+        if (params[k].precision != params[0].precision) {
+            set_err(c, "instances of a batch must share the precision");
+            return SPH_E_INVAL;
+        }
+        if (counts[k] < 0) {
+            set_err(c, "counts[%d] < 0", k);
+            return SPH_E_INVAL;
+        }
+        ioff[k] = slots;
+        coff[k] = tot;
+        icnt[k] = counts[k];
+        tot += counts[k];
+        slots += counts[k];
+        if (k + 1 < ninst) slots = (slots + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
+        kpi[k] = kparams(&params[k]);
+        memset(&grid[k], 0, sizeof(Grid));
+        grid[k].cbase = cells;
+        grid[k].cap = instance_cell_cap(counts[k]);
+        cells += grid[k].cap;
+    }
+    ioff[ninst] = slots;
+    coff[ninst] = tot;
+    if (tot > c->ncap || cells > c->cellcap) {
+        set_err(c, "batch of %lld particles exceeds the capacity %lld", (long long)tot,
+                (long long)c->ncap);
+        return SPH_E_INVAL;
+    }
+    const int64_t nblk = (slots + kSlotAlign - 1) / kSlotAlign;
+    std::vector<int32_t> blk((size_t)std::max<int64_t>(nblk, 1), 0);
+    for (int k = 0; k < ninst; ++k)
+        for (int64_t b = ioff[k] / kSlotAlign; b < (ioff[k] + icnt[k] + kSlotAlign - 1) / kSlotAlign; ++b)
+            blk[(size_t)b] = k;
+    DeviceGuard dg(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(c->ioff, ioff.data(), (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->coff, coff.data(), (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->icnt, icnt.data(), ninst * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->kpi, kpi.data(), ninst * sizeof(KParams), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->grid, grid.data(), ninst * sizeof(Grid), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nblk > 0)
+        e = cudaMemcpyAsync(c->blk, blk.data(), nblk * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host arrays die with this call
+    if (e != cudaSuccess) {
+        set_err(c, "sph_batch_set: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        return SPH_E_CUDA;
+    }
+    c->n = slots;
+    c->ntot = tot;
+    c->ninst = ninst;
+    c->prec = params[0].precision;
+    return SPH_OK;
+}
+
+sph_status sph_batch_step(sph_ctx* c, sph_particles* P, int nsteps, void* stream) {
+    if (!c) return SPH_E_INVAL;
+    if (!P) { set_err(c, "particles is NULL"); return SPH_E_INVAL; }
+    if (nsteps < 0) { set_err(c, "nsteps < 0"); return SPH_E_INVAL; }
+    if (P->n != c->ntot) {
+        set_err(c, "n = %lld differs from the batch (%lld particles)", (long long)P->n,
+                (long long)c->ntot);
+        return SPH_E_INVAL;
+    }
+    NEED(P->dt); NEED(P->time);
+    if (P->n > 0) {
+        NEED(P->x); NEED(P->y); NEED(P->z); NEED(P->vx); NEED(P->vy); NEED(P->vz);
+        NEED(P->m); NEED(P->h); NEED(P->u); NEED(P->rho); NEED(P->p); NEED(P->c);
+        NEED(P->ax); NEED(P->ay); NEED(P->az); NEED(P->du);
+    }
+    DeviceGuard dg(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    run_steps(c, P, nsteps, s);
+    return check_launch(c, "sph_batch_step");
 }
 
 sph_status sph_neighbors_to_host(sph_ctx* c, int64_t* offsets, int32_t* idx,

@@ -53,6 +53,8 @@ struct Grid {
     double hmean;
     unsigned long long hmax_bits;  // bits of max h after the h search
     long long ncells;
+    long long cbase;  // first entry of this instance's cells in the cell tables
+    long long cap;    // cells this instance may use (sets the smallest cell width)
     float lof[3], wf[3], invwf[3];
     float lzf, halflzf;
     float slop[3];   // absolute slack added to query boxes (FP32 rounding cover)
@@ -64,6 +66,40 @@ struct KParams {
     int eos, n_target, n_tol, max_h_iter, periodic_z, precision;
     double rho0, c0, gamma, alpha, beta, eta2, cfl, lz, cell_scale;
 };
+
+// Instances of a batch. Instance k holds the internal slots
+// [ioff[k], ioff[k] + icnt[k]); ioff[k] is a multiple of kSlotAlign and the
+// slots between the end of one instance and the start of the next are empty
+// (skipped by every kernel). blk[b] is the instance of the slots
+// [b kSlotAlign, (b + 1) kSlotAlign), so a 256-thread block, and each of its
+// warps, belongs to one instance. A single problem is a batch of one with
+// ioff[0] = 0: an instance is processed identically alone and in a batch.
+constexpr int kSlotAlign = 256;
+constexpr int kMaxInstances = 256;  // instance id = top 8 bits of the 32-bit sort key
+constexpr int kMinInstanceCells = 4096;
+
+struct Batch {
+    const int32_t* blk;
+    const int64_t* ioff;
+    const int64_t* icnt;
+    const Grid* grid;
+    const KParams* kp;
+};
+
+__device__ __forceinline__ int slot_inst(const Batch& B, int64_t i) {
+    return __ldg(&B.blk[i / kSlotAlign]);
+}
+__device__ __forceinline__ bool slot_real(const Batch& B, int inst, int64_t i) {
+    return i - __ldg(&B.ioff[inst]) < __ldg(&B.icnt[inst]);
+}
+
+// Cells an instance of n particles may use.
+inline long long instance_cell_cap(int64_t n) {
+    const long long m = (long long)kMaxCellsPerAxis * kMaxCellsPerAxis * kMaxCellsPerAxis;
+    long long c = 2 * (long long)n;
+    if (c < kMinInstanceCells) c = kMinInstanceCells;
+    return c < m ? c : m;
+}
 
 inline KParams kparams(const sph_params* p) {
     KParams k;
@@ -80,7 +116,14 @@ inline KParams kparams(const sph_params* p) {
 struct sph_ctx {
     int device;
     int64_t ncap, nnzcap, cellcap;
-    int64_t n;              // particles of the last build
+    int64_t n;              // internal slots of the current batch (particles, plus the
+                            // empty slots between instances)
+    int64_t ntot;           // particles of the current batch
+    int ninst, maxinst;     // instances of the current batch / capacity
+    int prec;               // precision of the current batch
+    int32_t* blk;           // instance of each block of kSlotAlign slots
+    int64_t *ioff, *icnt, *coff;  // per instance: first slot, particles, first caller index
+    sph::KParams* kpi;      // per-instance parameters
     int cur;                // current buffer of the double-buffered state
     double4_32a *posh[2], *velm[2];     // permuted with the particles (double-buffered)
     double* ue[2];                  // specific internal energy u
@@ -114,7 +157,7 @@ struct sph_ctx {
     int32_t* wl;            // their indices (count in status[3])
     double* red_part;       // bbox partials: kReduceBlocks x 8
     double* dt_part;        // per force block
-    sph::Grid* grid;
+    sph::Grid* grid;        // per instance
     unsigned* status;       // [0] bits, [1] non-converged count, [2] internal flags,
                             // [3] h-search worklist length
     unsigned* status_host;  // pinned mirror
@@ -134,31 +177,38 @@ struct sph_ctx {
 
 namespace sph {
 
+inline Batch batch_of(const sph_ctx* c) { return Batch{c->blk, c->ioff, c->icnt, c->grid, c->kpi}; }
+
+// ---- sph_abi.cu
+// Describe a single problem of n particles (a batch of one) on the stream.
+void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s);
+
 // ---- sort.cu
 void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s);
 void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, int what,
                          cudaStream_t s);
-void launch_build_cells(sph_ctx* c, const KParams& kp, cudaStream_t s);
+void launch_build_cells(sph_ctx* c, cudaStream_t s);
 
 // ---- neighbors.cu
-void launch_h_search(sph_ctx* c, const KParams& kp, cudaStream_t s);
+void launch_h_search(sph_ctx* c, cudaStream_t s);
 void launch_csr(sph_ctx* c, cudaStream_t s);
 
 // ---- physics.cu
 enum { GATHER_DENSITY = 1, GATHER_FORCES = 2 };
-void launch_density(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s);
+void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s);
 // ---- physics_df.cu (precision 0)
-void launch_density_df(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s);
-void launch_forces_df(sph_ctx* c, const KParams& kp, cudaStream_t s);
+void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s);
+void launch_forces_df(sph_ctx* c, cudaStream_t s);
 enum { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP64_NATIVE = 2 };
 // ---- physics_mixed.cu (precision 1)
 void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s);
-void launch_density_mx(sph_ctx* c, const KParams& kp, bool fuse_eos, cudaStream_t s);
-void launch_forces_mx(sph_ctx* c, const KParams& kp, cudaStream_t s);
+void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s);
+void launch_forces_mx(sph_ctx* c, cudaStream_t s);
 void launch_eos_caller(const KParams& kp, const sph_particles* P, cudaStream_t s);
-void launch_forces(sph_ctx* c, const KParams& kp, double* dt_out, double* time_inout,
-                   cudaStream_t s);
-void launch_leapfrog(sph_ctx* c, const KParams& kp, const double* dt, cudaStream_t s);
+// forces, then per instance dt[k] = cfl min_i (...) and time[k] += dt[k]
+// (dt_out, time_inout: device arrays of ninst entries; time_inout may be NULL)
+void launch_forces(sph_ctx* c, double* dt_out, double* time_inout, cudaStream_t s);
+void launch_leapfrog(sph_ctx* c, const double* dt, cudaStream_t s);
 void launch_scatter(sph_ctx* c, const sph_particles* P, unsigned fields, cudaStream_t s);
 
 enum : unsigned {

@@ -1,0 +1,187 @@
+"""Batches of independent problems (sph_batch_set / sph_batch_step): every
+instance of a batch must give bit for bit the result of stepping it alone,
+its neighbour list must stay inside the instance, and the batched step must
+replay unchanged from a CUDA graph. Instances mix sizes, equations of state,
+periodicity and velocity fields.
+"""
+import numpy as np
+import pytest
+
+from paper_1809_08013_gb300 import ics
+from parity_util import TOL_FP64, canon_oracle, normwise, same_sets, scaled
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FIELDS_OUT = ("x", "y", "z", "vx", "vy", "vz", "h", "u", "rho", "p", "c", "ax", "ay", "az",
+              "du", "mumax", "nnb")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_08013_gb300 import binding
+    binding.load()
+    return binding
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def instances(precision):
+    out = []
+    s, p = ics.square_patch(12, seed=21, omega=3.0)
+    out.append((s, p))
+    s, p = ics.square_patch(17, seed=22, omega=7.0)
+    out.append((ics.random_velocities(s, seed=23, scale=1.5), p))
+    out.append(ics.evrard(3000, seed=24))
+    s, p = ics.square_patch(10, seed=25)
+    out.append((s, p))
+    s, p = ics.evrard(5000, seed=26)
+    out.append((ics.random_velocities(s, seed=27, scale=0.2), p))
+    for _, p in out:
+        p.precision = precision
+    return out
+
+
+def concat(states):
+    return {k: np.concatenate([s[k] for s in states]) for k in ics.FIELDS}
+
+
+def run_batch(B, insts, nsteps, max_instances=None):
+    counts = [len(s["x"]) for s, _ in insts]
+    ctx = B.Context(sum(counts), max_instances=max_instances or len(insts))
+    ctx.batch_set(counts, [p for _, p in insts])
+    arr = B.alloc_arrays(concat([s for s, _ in insts]), ninst=len(insts))
+    ctx.batch_step(arr, nsteps=nsteps)
+    st = ctx.sync()
+    return ctx, arr, counts, st
+
+
+def run_alone(B, s, p, nsteps):
+    ctx = B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.step(p, arr, nsteps=nsteps)
+    ctx.sync()
+    return arr
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_instances_bit_identical_to_alone(B, precision):
+    insts = instances(precision)
+    _, arr, counts, st = run_batch(B, insts, nsteps=3)
+    assert st in (B.SPH_OK, B.SPH_E_HNOCONV)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    dt, tm = host(arr["dt"]), host(arr["time"])
+    for k, (s, p) in enumerate(insts):
+        alone = run_alone(B, s, p, nsteps=3)
+        for f in FIELDS_OUT:
+            a = host(arr[f])[off[k]:off[k + 1]]
+            b = host(alone[f])
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), (k, f)
+        assert dt[k] == host(alone["dt"])[0] and tm[k] == host(alone["time"])[0], k
+
+
+def test_batch_neighbour_lists_stay_in_their_instance(B, orc):
+    insts = instances(0)
+    ctx, arr, counts, _ = run_batch(B, insts, nsteps=1)
+    offs, idx, ng, order = ctx.neighbors_to_host()
+    coff = np.concatenate([[0], np.cumsum(counts)])
+    inst_of_caller = np.repeat(np.arange(len(counts)), counts)
+    lens = np.diff(offs)
+    # empty slots have no caller particle and no row
+    assert np.all(lens[order < 0] == 0)
+    assert np.count_nonzero(order >= 0) == sum(counts)
+    assert np.array_equal(np.sort(order[order >= 0]), np.arange(sum(counts)))
+    rows = np.repeat(np.arange(len(order)), lens)
+    pos = np.arange(len(idx)) - np.repeat(offs[:-1], lens)
+    flag = (pos < np.repeat(ng, lens)).astype(np.int8)
+    rc, cc = order[rows].astype(np.int64), order[idx].astype(np.int64)
+    assert np.all(rc >= 0) and np.all(cc >= 0)
+    # every entry joins two particles of the same instance
+    ik = inst_of_caller[rc]
+    assert np.array_equal(ik, inst_of_caller[cc])
+    # and each instance's sets equal the oracle's for the state the step started from
+    for k, (s, p) in enumerate(insts):
+        o = orc.pipeline(p, s)
+        m = ik == k
+        r, c, f = rc[m] - coff[k], cc[m] - coff[k], flag[m]
+        key = np.lexsort((f, c, r))
+        assert same_sets((r[key], c[key], f[key]), canon_oracle(o["off"], o["idx"], o["ng"])), k
+
+
+def test_batch_one_step_matches_oracle(B, orc):
+    insts = instances(0)
+    _, arr, counts, _ = run_batch(B, insts, nsteps=1)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for k, (s, p) in enumerate(insts):
+        o = orc.pipeline(p, s)
+        sl = slice(off[k], off[k + 1])
+        assert np.array_equal(host(arr["h"])[sl].view(np.int64), o["h"].view(np.int64)), k
+        assert normwise(host(arr["rho"])[sl], o["rho"]) <= TOL_FP64, k
+        for f, sc in (("ax", "scale_a"), ("ay", "scale_a"), ("az", "scale_a"), ("du", "scale_du")):
+            ref = o[f]
+            if np.max(np.abs(ref)) == 0.0 and np.max(o[sc]) == 0.0:
+                assert np.max(np.abs(host(arr[f])[sl])) == 0.0, (k, f)
+            else:
+                assert scaled(host(arr[f])[sl], ref, o[sc]) <= TOL_FP64, (k, f)
+        assert abs(host(arr["dt"])[k] - o["dt"]) <= TOL_FP64 * o["dt"], k
+
+
+def test_batch_step_replays_from_a_cuda_graph(B):
+    insts = instances(0)
+    counts = [len(s["x"]) for s, _ in insts]
+    ctx = B.Context(sum(counts), max_instances=8)
+    ctx.batch_set(counts, [p for _, p in insts])
+    state = concat([s for s, _ in insts])
+    eager = B.alloc_arrays(state, ninst=len(insts))
+    ctx.batch_step(eager, nsteps=2)
+    ctx.sync()
+    arr = B.alloc_arrays(state, ninst=len(insts))
+    ic = {k: arr[k].clone() for k in B.STATE_FIELDS}
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.batch_step(arr, nsteps=2, stream=s)
+    for rep in range(2):  # replay twice from the initial conditions
+        for k in B.STATE_FIELDS:
+            arr[k].copy_(ic[k])
+        arr["time"].zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
+        for f in FIELDS_OUT + ("dt", "time"):
+            assert np.array_equal(host(arr[f]).view(np.uint8), host(eager[f]).view(np.uint8)), (rep, f)
+
+
+def test_batch_invalid_arguments(B):
+    insts = instances(0)
+    counts = [len(s["x"]) for s, _ in insts]
+    ctx = B.Context(sum(counts), max_instances=4)
+    with pytest.raises(B.SphError) as e:  # more instances than the context holds
+        ctx.batch_set(counts, [p for _, p in insts])
+    assert e.value.status == B.SPH_E_INVAL
+    ctx = B.Context(sum(counts) - 1, max_instances=8)
+    with pytest.raises(B.SphError):  # more particles than the capacity
+        ctx.batch_set(counts, [p for _, p in insts])
+    ctx = B.Context(sum(counts), max_instances=8)
+    prms = [p for _, p in insts]
+    prms[2] = ics.SphParams(**{**prms[2].as_dict(), "precision": 1})
+    with pytest.raises(B.SphError):  # mixed precisions in one batch
+        ctx.batch_set(counts, prms)
+    ctx.batch_set(counts, [p for _, p in insts])
+    arr = B.alloc_arrays(concat([s for s, _ in insts[:-1]]), ninst=len(insts))
+    with pytest.raises(B.SphError):  # arrays do not match the batch
+        ctx.batch_step(arr, nsteps=1)
+
+
+def test_batch_of_one_equals_single_problem(B):
+    s, p = ics.square_patch(13, seed=31)
+    _, arr, _, _ = run_batch(B, [(s, p)], nsteps=2, max_instances=3)
+    alone = run_alone(B, s, p, nsteps=2)
+    for f in FIELDS_OUT:
+        assert np.array_equal(host(arr[f]).view(np.uint8), host(alone[f]).view(np.uint8)), f
