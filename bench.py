@@ -80,6 +80,10 @@ def parse():
     ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64")
     ap.add_argument("--cell-scale", type=float, default=0.0,
                     help="neighbour-search cell width / (2 <h>); 0 = library default")
+    ap.add_argument("--pair-threads", type=int, default=0,
+                    help="lanes per particle in the pair sums (0 = library default)")
+    ap.add_argument("--defer-lanes", type=int, default=0,
+                    help="h-search hand-over threshold (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the batched-ensemble measurement")
@@ -130,6 +134,8 @@ def make_workload(args, n=None):
         s, prm = ics.square_patch(side, seed=seed)
     prm.precision = PRECISION[args.precision]
     prm.cell_scale = args.cell_scale
+    prm.pair_threads = args.pair_threads
+    prm.defer_lanes = args.defer_lanes
     return s, prm
 
 
@@ -293,6 +299,10 @@ def _run_ensemble(args, B, dev, stream):
     ctx.batch_step(arr, nsteps=1, stream=stream)  # warm-up
     ctx.sync(stream)
     reset()
+    tune = ctx.autotune(arr, nsteps=2, stream=stream)  # knobs of the whole batch
+    ctx.sync(stream)
+    tuned = {"cell_scale": tune["cell_scale"], "pair_threads": tune["pair_threads"],
+             "defer_lanes": tune["defer_lanes"]}
     torch.cuda.synchronize(dev)
     g = torch.cuda.CUDAGraph()
     l0 = ctx.launch_count()
@@ -319,7 +329,9 @@ def _run_ensemble(args, B, dev, stream):
     t_alone = []
     same = True
     off = np.concatenate([[0], np.cumsum(counts)])
+    from paper_1809_08013_gb300 import ics
     for k, (s, p) in enumerate(insts):
+        p = ics.SphParams(**{**p.as_dict(), **tuned})  # the same knobs as the batch
         a = B.alloc_arrays(s, device=dev)
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -353,6 +365,10 @@ def _run_ensemble(args, B, dev, stream):
                                  "own_time_ms_p99": float(np.percentile(t_alone, 99)),
                                  "launch": "sph_step per instance, one after another"},
         "batched_equals_single_bitwise": bool(same),
+        "autotune": {"chosen": tuned, "trials": tune["trials"],
+                     "method": "sph_autotune: one coordinate-descent pass over pair_threads "
+                               "{1,2,4}, cell_scale {1,1.25,1.5}, defer_lanes {8,16}; 2 timed "
+                               "steps per trial"},
     }
 
 

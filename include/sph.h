@@ -64,6 +64,16 @@ typedef struct {
                                 viscosity terms, sums kept in double-float (~1e-7),
                             2 = the same sums with native FP64 arithmetic.
                             Other values: SPH_E_INVAL. */
+    int32_t pair_threads; /* lanes per particle in the density and force sums: 1, 2, 4
+                             or 8 (0 selects 2 for precision 1, else 1); the lanes of a
+                             particle split its
+                             neighbour row and combine their sums in a fixed order.
+                             Ignored by precision 2. A tuning knob (sph_autotune): the
+                             sums round differently for each value */
+    int32_t defer_lanes;  /* h search: a warp of 32 particles hands its particles still
+                             searching to one warp each once at most this many remain
+                             (0 selects 8; at most 32). A tuning knob: h and the
+                             neighbour sets do not depend on it */
     double rho0, c0;     /* Tait: p = c0^2 rho0 / 7 ((rho/rho0)^7 - 1), c = c0 (rho/rho0)^3 */
     double gamma;        /* ideal gas: p = (gamma - 1) rho u, c = sqrt(gamma (gamma - 1) u) */
     double alpha, beta;  /* Monaghan artificial viscosity */
@@ -186,6 +196,47 @@ sph_status sph_batch_step(sph_ctx *ctx, sph_particles *P, int nsteps, void *stre
 /* Rows of the current neighbour list (the n of sph_neighbors): the particle
  * count of a single problem; for a batch, the slots of all instances. */
 int64_t sph_neighbor_rows(const sph_ctx *ctx);
+
+/* Search space of sph_autotune (host arrays of candidate values). */
+#define SPH_TUNE_MAX_TRIALS 16
+typedef struct {
+    const double *cell_scales;   int32_t n_cell_scales;   /* each > 0 */
+    const int32_t *pair_threads; int32_t n_pair_threads;  /* each 1, 2, 4 or 8 */
+    const int32_t *defer_lanes;  int32_t n_defer_lanes;   /* each in [1, 32] */
+} sph_tune_space;
+
+typedef struct {
+    double cell_scale;
+    int32_t pair_threads, defer_lanes;
+    double ms_per_step;
+} sph_tune_trial;
+
+typedef struct {
+    double cell_scale;           /* the chosen knobs ... */
+    int32_t pair_threads, defer_lanes;
+    double ms_per_step;          /* ... and their device time per step */
+    int32_t n_trials;
+    sph_tune_trial trials[SPH_TUNE_MAX_TRIALS];  /* every setting timed, in order */
+} sph_tune_result;
+
+/* Choose the performance knobs of the current batch (or single problem of
+ * the last call) by timing: for each candidate, the caller's state P is
+ * loaded, one step runs untimed and nsteps steps are timed with CUDA events
+ * on `stream`. One coordinate-descent pass from the current knobs, in the
+ * order pair_threads, cell_scale, defer_lanes, keeps the fastest value of
+ * each. The knobs change neither h nor the neighbour sets; the sums round
+ * differently with pair_threads. P is not modified (dt and time of the
+ * trials go to context scratch); the context keeps the chosen knobs for
+ * sph_batch_step until the next sph_batch_set, and a single-problem call
+ * takes them from its sph_params. space = NULL uses cell_scale {1, 1.25,
+ * 1.5}, pair_threads {1, 2, 4}, defer_lanes {8, 16}. Synchronises the
+ * stream (not capturable). SPH_E_INVAL for nsteps < 1, P->n different from
+ * the batch, invalid candidates or more than SPH_TUNE_MAX_TRIALS of them.
+ * Device conditions of the trial runs (h non-convergence) stay in the
+ * status word for the next sph_sync. This knob search has no counterpart in
+ * the paper (its codes are tuned per machine by hand). */
+sph_status sph_autotune(sph_ctx *ctx, sph_particles *P, int nsteps, const sph_tune_space *space,
+                        sph_tune_result *out, void *stream);
 
 /* Copy the neighbour list of the last sph_build_neighbors (or last step of
  * sph_step) into caller HOST buffers, synchronously after the stream's work:

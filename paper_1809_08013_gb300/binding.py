@@ -25,6 +25,7 @@ class SphParams(C.Structure):
     _fields_ = [
         ("eos", C.c_int32), ("n_target", C.c_int32), ("n_tol", C.c_int32),
         ("max_h_iter", C.c_int32), ("periodic_z", C.c_int32), ("precision", C.c_int32),
+        ("pair_threads", C.c_int32), ("defer_lanes", C.c_int32),
         ("rho0", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
         ("alpha", C.c_double), ("beta", C.c_double), ("eta2", C.c_double),
         ("cfl", C.c_double), ("lz", C.c_double), ("cell_scale", C.c_double),
@@ -43,6 +44,26 @@ class SphParticles(C.Structure):
 class SphNeighbors(C.Structure):
     _fields_ = [("n", C.c_int64), ("offsets", _DP), ("idx", _DP), ("ngather", _DP),
                 ("order", _DP), ("nnz_dev", _DP)]
+
+
+class SphTuneSpace(C.Structure):
+    _fields_ = [("cell_scales", _DP), ("n_cell_scales", C.c_int32),
+                ("pair_threads", _DP), ("n_pair_threads", C.c_int32),
+                ("defer_lanes", _DP), ("n_defer_lanes", C.c_int32)]
+
+
+class SphTuneTrial(C.Structure):
+    _fields_ = [("cell_scale", C.c_double), ("pair_threads", C.c_int32),
+                ("defer_lanes", C.c_int32), ("ms_per_step", C.c_double)]
+
+
+SPH_TUNE_MAX_TRIALS = 16
+
+
+class SphTuneResult(C.Structure):
+    _fields_ = [("cell_scale", C.c_double), ("pair_threads", C.c_int32),
+                ("defer_lanes", C.c_int32), ("ms_per_step", C.c_double),
+                ("n_trials", C.c_int32), ("trials", SphTuneTrial * SPH_TUNE_MAX_TRIALS)]
 
 
 class SphError(RuntimeError):
@@ -82,6 +103,9 @@ def load(rebuild: bool = True):
     L.sph_ctx_create_batch.argtypes = [P(_DP), C.c_int64, C.c_int64, C.c_int32, C.c_int]
     L.sph_batch_set.restype = C.c_int
     L.sph_batch_set.argtypes = [_DP, C.c_int32, P(C.c_int64), P(SphParams), _DP]
+    L.sph_autotune.restype = C.c_int
+    L.sph_autotune.argtypes = [_DP, P(SphParticles), C.c_int, P(SphTuneSpace), P(SphTuneResult),
+                               _DP]
     L.sph_batch_step.restype = C.c_int
     L.sph_batch_step.argtypes = [_DP, P(SphParticles), C.c_int, _DP]
     L.sph_ctx_destroy.restype = None
@@ -125,7 +149,9 @@ def probe_fma_peak(device: int = 0, fp64: bool = True, stream=None) -> float:
 def params(p) -> SphParams:
     """Marshal an object with the SphParams attributes (see ics.SphParams)."""
     return SphParams(int(p.eos), int(p.n_target), int(p.n_tol), int(p.max_h_iter),
-                     int(p.periodic_z), int(getattr(p, "precision", 0)), float(p.rho0), float(p.c0), float(p.gamma),
+                     int(p.periodic_z), int(getattr(p, "precision", 0)),
+                     int(getattr(p, "pair_threads", 0)), int(getattr(p, "defer_lanes", 0)),
+                     float(p.rho0), float(p.c0), float(p.gamma),
                      float(p.alpha), float(p.beta), float(p.eta2), float(p.cfl), float(p.lz),
                      float(getattr(p, "cell_scale", 0.0)))
 
@@ -245,6 +271,32 @@ class Context:
     def batch_step(self, arrays: dict, nsteps: int = 1, stream=None):
         P = particles(arrays)
         self._check(self.lib.sph_batch_step(self.h, C.byref(P), int(nsteps), _stream(stream)))
+
+    def autotune(self, arrays: dict, nsteps: int = 2, cell_scales=None, pair_threads=None,
+                 defer_lanes=None, stream=None) -> dict:
+        """Time the knob candidates on the current batch (see sph_autotune);
+        None for all three lists uses the library's default search space."""
+        P = particles(arrays)
+        res = SphTuneResult()
+        sp = None
+        keep = []
+        if cell_scales is not None or pair_threads is not None or defer_lanes is not None:
+            cs = (C.c_double * max(1, len(cell_scales or [])))(*(cell_scales or []))
+            tp = (C.c_int32 * max(1, len(pair_threads or [])))(*(pair_threads or []))
+            dl = (C.c_int32 * max(1, len(defer_lanes or [])))(*(defer_lanes or []))
+            keep = [cs, tp, dl]
+            sp = SphTuneSpace(C.cast(cs, _DP), len(cell_scales or []), C.cast(tp, _DP),
+                              len(pair_threads or []), C.cast(dl, _DP), len(defer_lanes or []))
+        self._check(self.lib.sph_autotune(self.h, C.byref(P), int(nsteps),
+                                          C.byref(sp) if sp is not None else None,
+                                          C.byref(res), _stream(stream)))
+        del keep
+        trials = [{"cell_scale": t.cell_scale, "pair_threads": t.pair_threads,
+                   "defer_lanes": t.defer_lanes, "ms_per_step": t.ms_per_step}
+                  for t in res.trials[:res.n_trials]]
+        return {"cell_scale": res.cell_scale, "pair_threads": res.pair_threads,
+                "defer_lanes": res.defer_lanes, "ms_per_step": res.ms_per_step,
+                "trials": trials}
 
     def sync(self, stream=None) -> int:
         """Wait for the stream; return the device status (SPH_OK, SPH_E_CAPACITY,

@@ -134,6 +134,18 @@ __device__ __forceinline__ df from_double(double d) {
 // Per-particle conversion back to FP64 (two conversions and one FP64 add).
 __device__ __forceinline__ double to_double(df x) { return (double)x.hi + (double)x.lo; }
 
+// Sum over groups of T consecutive lanes (T a power of two <= 32), returned to
+// every lane of the group: a fixed butterfly, independent of timing.
+template <int T>
+__device__ __forceinline__ df lane_sum(df v) {
+#pragma unroll
+    for (int o = 1; o < T; o <<= 1) {
+        const df w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = add(v, w);
+    }
+    return v;
+}
+
 // Per-particle pack of the double-float force kernel (48 B per particle):
 //   dpk[3k] = (1/h, 1/h^4), dpk[3k+1] = (p/rho^2, h/2), dpk[3k+2] = (rho/2, alpha c/2).
 __device__ __forceinline__ void write_pack(float4* __restrict__ dpk, int64_t k, double hinv,

@@ -305,10 +305,9 @@ __device__ __forceinline__ void particle_pass(const Grid* __restrict__ g,
 // Phase 1: one warp per 32 consecutive (Morton-sorted) particles, one lane
 // per particle. Each pass counts N_i(h) for every still-searching lane over
 // the union of their query boxes (candidates staged once for the warp) and
-// records the gather set in the slab. While more than kDeferLanes lanes are
+// records the gather set in the slab. While more than defer_lanes lanes are
 // still searching the warp keeps going; the stragglers are then handed, with
 // their bisection state, to the per-particle kernel below through a worklist.
-constexpr int kDeferLanes = 8;
 
 // Test the 32 staged candidates of a warp against every lane's particle and
 // fold the outcome into that lane's count and gather slab. Candidates are
@@ -374,6 +373,7 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
     double h = pi.w, lo = 0.0, hi = CUDART_INF;
     const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
     const int max_it = kp.max_h_iter;
+    const int defer = kp.defer_lanes;
     int cnt = 0, it = 0;
     bool active = valid && max_it > 0, conv = false, deferred = false;
     int32_t* slab = gslab + (valid ? i : 0) * kGSlab;
@@ -394,7 +394,7 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
         // z, which is each lane's minimum image while the warp spans < lz/4.
         const float zc = __shfl_sync(kFull, fi.z, __ffs(am) - 1);
         const bool wide = per && (hzz - lzz > 0.25f * g->lzf);
-        if ((pass > 0 && __popc(am) <= kDeferLanes) || wide) {
+        if ((pass > 0 && __popc(am) <= defer) || wide) {
             if (active) {
                 deferred = true;
                 active = false;

@@ -274,13 +274,15 @@ k_forces(int64_t n, Batch B, const double4_32a* __restrict__ posh,
 }
 
 // One block per instance: dt[k] = cfl_k * min over the instance's block
-// partials; time[k] += dt[k] when time is given.
+// partials; time[k] += dt[k] when time is given. The force kernel ran with
+// tpp lanes per particle, so a block covered kThreads / tpp particles.
 __global__ void __launch_bounds__(kThreads)
-k_dt_finish(const double* __restrict__ part, Batch B, double* __restrict__ dt_out,
+k_dt_finish(const double* __restrict__ part, Batch B, int tpp, double* __restrict__ dt_out,
             double* __restrict__ time) {
     const int inst = blockIdx.x;
-    const int64_t b0 = B.ioff[inst] / kSlotAlign;
-    const int64_t nbk = (B.icnt[inst] + kSlotAlign - 1) / kSlotAlign;
+    const int64_t per_block = kThreads / tpp;
+    const int64_t b0 = B.ioff[inst] / per_block;
+    const int64_t nbk = (B.icnt[inst] + per_block - 1) / per_block;
     double m = CUDART_INF;
     for (int64_t k = threadIdx.x; k < nbk; k += blockDim.x) m = fmin(m, part[b0 + k]);
 #pragma unroll
@@ -313,7 +315,9 @@ void launch_forces(sph_ctx* c, double* dt_out, double* time_inout, cudaStream_t 
                                          c->cint, c->offsets, c->idx, c->nnzcap, c->acc,
                                          c->mumax, c->dt_part);
     }
-    k_dt_finish<<<c->ninst, kThreads, 0, s>>>(c->dt_part, B, dt_out, time_inout);
+    k_dt_finish<<<c->ninst, kThreads, 0, s>>>(c->dt_part, B,
+                                              c->prec == PREC_FP64_NATIVE ? 1 : c->tpp, dt_out,
+                                              time_inout);
 }
 
 // ------------------------------------------------------------ leapfrog

@@ -72,7 +72,8 @@ __device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, d
 }  // namespace
 
 // ------------------------------------------------------------ density
-template <bool FUSE>
+// T lanes per particle: lane s of particle i takes row entries s, s + T, ...
+template <bool FUSE, int T>
 __global__ void __launch_bounds__(kThreads)
 k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const float2* __restrict__ mdf, const double* __restrict__ ue,
@@ -80,19 +81,24 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
              double2* __restrict__ kern, float4* __restrict__ dpk, double* __restrict__ pint,
              double* __restrict__ cint) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
-    if (i >= n || !slot_real(B, inst, i) || offsets[n] > nnzcap) return;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
+    const int sub = (int)(threadIdx.x % T);
+    const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
+    const bool act = i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap;
+    if (T == 1 && !act) return;
     const KParams& kp = B.kp[inst];
-    const double4_32a pi = posh[i];
+    double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
+    df acc = {0.0f, 0.0f};
+    if (act) {
+    pi = posh[i];
     const double hinv = 1.0 / pi.w;
     const df Hi = dfl::from_double_fp64(hinv);
     const long long half_bits = bitsd(0.5 * kp.lz);
     const bool per = kp.periodic_z != 0;
     const double lz = kp.lz;
-    df acc = ld2(mdf, i);  // self term m_i W(0, h_i): shape 1
+    if (sub == 0) acc = ld2(mdf, i);  // self term m_i W(0, h_i): shape 1
     const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
-    for (int64_t e = e0; e < e1; ++e) {
+    for (int64_t e = e0 + sub; e < e1; e += T) {
         const int j = __ldg(&idx[e]);
         const double4_32a pj = posh[j];
         double dz = pi.z - pj.z;
@@ -107,6 +113,12 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         }
         acc = dfl::add(acc, dfl::mul(ld2(mdf, j), w));
     }
+    }
+    if (T > 1) {
+        acc = dfl::lane_sum<T>(acc);
+        if (!act || sub != 0) return;
+    }
+    const double hinv = 1.0 / pi.w;
     const double sigma = hinv * hinv * hinv * kInvPiD;
     const double rho = dfl::to_double(acc) * sigma;
     if (FUSE) {
@@ -124,27 +136,38 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     }
 }
 
-void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
-    const Batch B = batch_of(c);
+template <bool FUSE, int T>
+static void density_df_t(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
-    if (n == 0) return;
-    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
+    k_density_df<FUSE, T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->mdf, c->ue[b],
+                                                  c->offsets, c->ngather, c->idx, c->nnzcap,
+                                                  c->therm, c->kern, c->dpk, c->pint, c->cint);
+}
+
+template <bool FUSE>
+static void density_df_f(sph_ctx* c, cudaStream_t s) {
+    switch (c->tpp) {
+        case 2: density_df_t<FUSE, 2>(c, s); break;
+        case 4: density_df_t<FUSE, 4>(c, s); break;
+        case 8: density_df_t<FUSE, 8>(c, s); break;
+        default: density_df_t<FUSE, 1>(c, s); break;
+    }
+}
+
+void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
+    if (c->n == 0) return;
     c->launches += 1;
-    if (fuse_eos)
-        k_density_df<true><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->mdf, c->ue[b], c->offsets,
-                                                   c->ngather, c->idx, c->nnzcap, c->therm,
-                                                   c->kern, c->dpk, c->pint, c->cint);
-    else
-        k_density_df<false><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->mdf, c->ue[b],
-                                                    c->offsets, c->ngather, c->idx, c->nnzcap,
-                                                    c->therm, c->kern, c->dpk, c->pint, c->cint);
+    if (fuse_eos) density_df_f<true>(c, s);
+    else density_df_f<false>(c, s);
 }
 
 // ------------------------------------------------------------ forces + dt
 // Definitions as in physics.cu; algebra: Fbar = (0.5/pi)(f(q_i)/h_i^4 +
 // f(q_j)/h_j^4)/r, one shared reciprocal R = 1/((r^2 + eta2 hb^2) rhob) for the
 // viscosity, mu = hb v.r rhob R, 1/rhob = (r^2 + eta2 hb^2) R.
+template <int T>
 __global__ void __launch_bounds__(kThreads, 3)
 k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
@@ -152,10 +175,14 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
             double4_32a* __restrict__ acc, double* __restrict__ mumax,
             double* __restrict__ dt_part) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
+    const int sub = (int)(threadIdx.x % T);
+    const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
+    const bool act = i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap;
     double dtc = CUDART_INF;
-    if (i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap) {
+    df sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sp = {0.f, 0.f}, sv = {0.f, 0.f};
+    df mumx = {0.f, 0.f};
+    if (act) {
         const KParams& kp = B.kp[inst];
         const double4_32a pi = posh[i];
         const double4_32a vi = velm[i];
@@ -168,10 +195,8 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const df c_half_pi = dfl::from_double_fp64(0.5 * kInvPiD);
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
-        df sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sp = {0.f, 0.f}, sv = {0.f, 0.f};
-        df mumx = {0.f, 0.f};
         const int64_t e0 = offsets[i], e1 = offsets[i + 1];
-        for (int64_t e = e0; e < e1; ++e) {
+        for (int64_t e = e0 + sub; e < e1; e += T) {
             const int j = __ldg(&idx[e]);
             const double4_32a pj = posh[j];
             const double4_32a vj = velm[j];
@@ -213,15 +238,30 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             sp = dfl::add(sp, mFv);
             sv = dfl::add(sv, dfl::mul(mFv, Pi));
         }
-        const double Aid = dfl::to_double(Ai);
+    }
+    if (T > 1) {
+        sx = dfl::lane_sum<T>(sx);
+        sy = dfl::lane_sum<T>(sy);
+        sz = dfl::lane_sum<T>(sz);
+        sp = dfl::lane_sum<T>(sp);
+        sv = dfl::lane_sum<T>(sv);
+#pragma unroll
+        for (int o = 1; o < T; o <<= 1) {  // largest (hi, lo): a total order
+            const df w = {__shfl_xor_sync(0xffffffffu, mumx.hi, o),
+                          __shfl_xor_sync(0xffffffffu, mumx.lo, o)};
+            if (w.hi > mumx.hi || (w.hi == mumx.hi && w.lo > mumx.lo)) mumx = w;
+        }
+    }
+    if (act && sub == 0) {
+        const double Aid = (double)dpk[3 * i + 1].x + (double)dpk[3 * i + 1].y;
         acc[i] = make_double4_32a(-dfl::to_double(sx), -dfl::to_double(sy), -dfl::to_double(sz),
                                   fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)));
         const double mu_max = dfl::to_double(mumx);
         mumax[i] = mu_max;
         const double ci = cint[i];
         // parameters re-read here rather than kept in registers across the loop
-        const KParams& ke = B.kp[slot_inst(B, (int64_t)blockIdx.x * blockDim.x)];
-        dtc = pi.w / (ci + 1.2 * (ke.alpha * ci + ke.beta * mu_max));
+        const KParams& ke = B.kp[slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T)];
+        dtc = posh[i].w / (ci + 1.2 * (ke.alpha * ci + ke.beta * mu_max));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
@@ -235,16 +275,25 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     }
 }
 
-void launch_forces_df(sph_ctx* c, cudaStream_t s) {
-    const Batch B = batch_of(c);
+template <int T>
+static void forces_df_t(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
-    if (n == 0) return;
-    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
+    k_forces_df<T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->velm[b], c->dpk,
+                                           c->mdf, c->cint, c->offsets, c->idx, c->nnzcap,
+                                           c->acc, c->mumax, c->dt_part);
+}
+
+void launch_forces_df(sph_ctx* c, cudaStream_t s) {
+    if (c->n == 0) return;
     c->launches += 1;
-    k_forces_df<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->dpk, c->mdf, c->cint,
-                                        c->offsets, c->idx, c->nnzcap, c->acc, c->mumax,
-                                        c->dt_part);
+    switch (c->tpp) {
+        case 2: forces_df_t<2>(c, s); break;
+        case 4: forces_df_t<4>(c, s); break;
+        case 8: forces_df_t<8>(c, s); break;
+        default: forces_df_t<1>(c, s); break;
+    }
 }
 
 }  // namespace sph

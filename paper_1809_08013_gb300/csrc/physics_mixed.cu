@@ -157,23 +157,28 @@ k_pack_mx(int64_t n, const double4_32a* __restrict__ posh, const double4_32a* __
     }
 }
 
-template <bool FUSE>
+// T lanes per particle: lane s of particle i takes row entries s, s + T, ...
+template <bool FUSE, int T>
 __global__ void __launch_bounds__(kThreads)
 k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const double* __restrict__ ue, float4* __restrict__ mpk,
              const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
              const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
              double* __restrict__ pint, double* __restrict__ cint) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
-    if (i >= n || !slot_real(B, inst, i) || offsets[n] > nnzcap) return;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
+    const int sub = (int)(threadIdx.x % T);
+    const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
+    const bool act = i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap;
+    if (T == 1 && !act) return;
     const KParams& kp = B.kp[inst];
+    df acc = {0.0f, 0.0f};
+    if (act) {
     const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1];
     const float hinv = a1.w;
     const ZWrap zw = make_zwrap(kp);
-    df acc = {a0.w, 0.0f};  // self term m_i W(0, h_i): shape 1
+    if (sub == 0) acc = df{a0.w, 0.0f};  // self term m_i W(0, h_i): shape 1
     const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
-    for (int64_t e = e0; e < e1; ++e) {
+    for (int64_t e = e0 + sub; e < e1; e += T) {
         const int j = __ldg(&idx[e]);
         const float4 b0 = __ldg(&mpk[5 * j]), b1 = __ldg(&mpk[5 * j + 1]);
         const float dx = rel(a0.x, a1.x, b0.x, b1.x), dy = rel(a0.y, a1.y, b0.y, b1.y);
@@ -181,6 +186,11 @@ k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float q = r2 > 0.0f ? r2 * rsqrt_f(r2) * hinv : 0.0f;
         acc = dfl::addf(acc, b0.w * w_shape_f(q));
+    }
+    }
+    if (T > 1) {
+        acc = dfl::lane_sum<T>(acc);
+        if (!act || sub != 0) return;
     }
     const double hd = posh[i].w;
     const double hid = 1.0 / hd;
@@ -198,26 +208,29 @@ k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     }
 }
 
+template <int T>
 __global__ void __launch_bounds__(kThreads)
 k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const float4* __restrict__ mpk, const double* __restrict__ cint,
             const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
             double4_32a* __restrict__ acc, double* __restrict__ mumax,
             double* __restrict__ dt_part) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
+    const int sub = (int)(threadIdx.x % T);
+    const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
+    const bool act = i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap;
     double dtc = CUDART_INF;
-    if (i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap) {
+    df sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sp = {0.f, 0.f}, sv = {0.f, 0.f};
+    float mum = 0.0f;
+    if (act) {
         const KParams& kp = B.kp[inst];
         const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1], a2 = mpk[5 * i + 2];
         const float4 a3 = mpk[5 * i + 3], a4 = mpk[5 * i + 4];
         const ZWrap zw = make_zwrap(kp);
         const float eta2 = (float)kp.eta2, beta = (float)kp.beta;
         const float cpi = 0.5f * kInvPiF;
-        df sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sp = {0.f, 0.f}, sv = {0.f, 0.f};
-        float mum = 0.0f;
         const int64_t e0 = offsets[i], e1 = offsets[i + 1];
-        for (int64_t e = e0; e < e1; ++e) {
+        for (int64_t e = e0 + sub; e < e1; e += T) {
             const int j = __ldg(&idx[e]);
             const float4 b0 = __ldg(&mpk[5 * j]), b1 = __ldg(&mpk[5 * j + 1]);
             const float4 b2 = __ldg(&mpk[5 * j + 2]), b3 = __ldg(&mpk[5 * j + 3]);
@@ -252,13 +265,24 @@ k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             sp = dfl::addf(sp, mFv);
             sv = dfl::addf(sv, mFv * Pi);
         }
-        const double Aid = (double)a3.w;
+    }
+    if (T > 1) {
+        sx = dfl::lane_sum<T>(sx);
+        sy = dfl::lane_sum<T>(sy);
+        sz = dfl::lane_sum<T>(sz);
+        sp = dfl::lane_sum<T>(sp);
+        sv = dfl::lane_sum<T>(sv);
+#pragma unroll
+        for (int o = 1; o < T; o <<= 1) mum = fmaxf(mum, __shfl_xor_sync(0xffffffffu, mum, o));
+    }
+    if (act && sub == 0) {
+        const double Aid = (double)mpk[5 * i + 3].w;
         acc[i] = make_double4_32a(-dfl::to_double(sx), -dfl::to_double(sy), -dfl::to_double(sz),
                                   fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)));
         mumax[i] = (double)mum;
         const double ci = cint[i];
         // parameters re-read here rather than kept in registers across the loop
-        const KParams& ke = B.kp[slot_inst(B, (int64_t)blockIdx.x * blockDim.x)];
+        const KParams& ke = B.kp[slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T)];
         dtc = posh[i].w / (ci + 1.2 * (ke.alpha * ci + ke.beta * (double)mum));
     }
 #pragma unroll
@@ -285,32 +309,52 @@ void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s) {
         k_pack_mx<false><<<nb, kThreads, 0, s>>>(n, c->posh[b], c->velm[b], c->therm, c->mpk);
 }
 
-void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
-    const Batch B = batch_of(c);
+template <bool FUSE, int T>
+static void density_mx_t(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
-    if (n == 0) return;
-    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
+    k_density_mx<FUSE, T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->ue[b], c->mpk,
+                                                  c->offsets, c->ngather, c->idx, c->nnzcap,
+                                                  c->therm, c->pint, c->cint);
+}
+
+template <bool FUSE>
+static void density_mx_f(sph_ctx* c, cudaStream_t s) {
+    switch (c->tpp) {
+        case 2: density_mx_t<FUSE, 2>(c, s); break;
+        case 4: density_mx_t<FUSE, 4>(c, s); break;
+        case 8: density_mx_t<FUSE, 8>(c, s); break;
+        default: density_mx_t<FUSE, 1>(c, s); break;
+    }
+}
+
+void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
+    if (c->n == 0) return;
     c->launches += 1;
-    if (fuse_eos)
-        k_density_mx<true><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->ue[b], c->mpk, c->offsets,
-                                                   c->ngather, c->idx, c->nnzcap, c->therm,
-                                                   c->pint, c->cint);
-    else
-        k_density_mx<false><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->ue[b], c->mpk,
-                                                    c->offsets, c->ngather, c->idx, c->nnzcap,
-                                                    c->therm, c->pint, c->cint);
+    if (fuse_eos) density_mx_f<true>(c, s);
+    else density_mx_f<false>(c, s);
+}
+
+template <int T>
+static void forces_mx_t(sph_ctx* c, cudaStream_t s) {
+    const int64_t n = c->n;
+    const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
+    const int b = c->cur;
+    k_forces_mx<T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->mpk, c->cint,
+                                           c->offsets, c->idx, c->nnzcap, c->acc, c->mumax,
+                                           c->dt_part);
 }
 
 void launch_forces_mx(sph_ctx* c, cudaStream_t s) {
-    const Batch B = batch_of(c);
-    const int64_t n = c->n;
-    if (n == 0) return;
-    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
-    const int b = c->cur;
+    if (c->n == 0) return;
     c->launches += 1;
-    k_forces_mx<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->mpk, c->cint, c->offsets, c->idx,
-                                        c->nnzcap, c->acc, c->mumax, c->dt_part);
+    switch (c->tpp) {
+        case 2: forces_mx_t<2>(c, s); break;
+        case 4: forces_mx_t<4>(c, s); break;
+        case 8: forces_mx_t<8>(c, s); break;
+        default: forces_mx_t<1>(c, s); break;
+    }
 }
 
 }  // namespace sph

@@ -52,6 +52,15 @@ sph_status check_params(sph_ctx* c, const sph_params* p) {
         set_err(c, "precision must be 0 (FP64-accurate), 1 (mixed) or 2 (FP64 pipe)");
         return SPH_E_INVAL;
     }
+    if (!(p->pair_threads == 0 || p->pair_threads == 1 || p->pair_threads == 2 ||
+          p->pair_threads == 4 || p->pair_threads == 8)) {
+        set_err(c, "pair_threads must be 0, 1, 2, 4 or 8");
+        return SPH_E_INVAL;
+    }
+    if (p->defer_lanes < 0 || p->defer_lanes > 32) {
+        set_err(c, "defer_lanes must be in [0, 32]");
+        return SPH_E_INVAL;
+    }
     if (p->max_h_iter < 1 || p->n_target < 1 || p->n_tol < 0) {
         set_err(c, "bad h-search parameters");
         return SPH_E_INVAL;
@@ -91,7 +100,8 @@ void free_all(sph_ctx* c) {
                     c->order[1], c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist,
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->gslab, c->oslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
-                    c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi};
+                    c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
+                    c->tune_dt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -148,11 +158,28 @@ void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s)
     c->ntot = n;
     c->ninst = 1;
     c->prec = kp.precision;
+    c->tpp = kp.precision == PREC_FP64_NATIVE ? 1 : kp.pair_threads;
     const int64_t nblk = (n + kSlotAlign - 1) / kSlotAlign;
     const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((nblk + kThreads - 1) / kThreads, 1), 1024);
     c->launches += 1;
     k_set_single<<<nb, kThreads, 0, s>>>(kp, n, instance_cell_cap(n), nblk, c->blk, c->ioff,
                                          c->icnt, c->coff, c->kpi, c->grid);
+}
+
+// One step of the current batch on the state held in the context (Algorithm
+// 1 steps 1-6); dt and time are device arrays of ninst entries.
+void launch_step(sph_ctx* c, double* dt, double* time, cudaStream_t s) {
+    launch_build_cells(c, s);
+    mark(c, SPH_PHASE_CELLS, s);
+    launch_h_search(c, s);
+    mark(c, SPH_PHASE_HSEARCH, s);
+    launch_csr(c, s);
+    mark(c, SPH_PHASE_CSR, s);
+    launch_density(c, true, s);
+    mark(c, SPH_PHASE_DENSITY, s);
+    launch_forces(c, dt, time, s);
+    mark(c, SPH_PHASE_FORCES, s);
+    launch_leapfrog(c, dt, s);
 }
 
 // nsteps steps of the current batch: the caller's arrays are read into the
@@ -161,17 +188,7 @@ void run_steps(sph_ctx* c, sph_particles* P, int nsteps, cudaStream_t s) {
     mark(c, -1, s);
     launch_load_state(c, P, s);
     for (int k = 0; k < nsteps; ++k) {
-        launch_build_cells(c, s);
-        mark(c, SPH_PHASE_CELLS, s);
-        launch_h_search(c, s);
-        mark(c, SPH_PHASE_HSEARCH, s);
-        launch_csr(c, s);
-        mark(c, SPH_PHASE_CSR, s);
-        launch_density(c, true, s);
-        mark(c, SPH_PHASE_DENSITY, s);
-        launch_forces(c, P->dt, P->time, s);
-        mark(c, SPH_PHASE_FORCES, s);
-        launch_leapfrog(c, P->dt, s);
+        launch_step(c, P->dt, P->time, s);
         if (k == nsteps - 1)
             launch_scatter(c, P, SC_POS | SC_VEL | SC_H | SC_U | SC_RHO | SC_PC | SC_ACC |
                                      SC_MUMAX | SC_NNB, s);
@@ -304,13 +321,14 @@ sph_status sph_ctx_create_batch(sph_ctx** out, int64_t ncap, int64_t nnzcap, int
          dalloc(&c->nnb, N) && dalloc(&c->ngather, N) && dalloc(&c->rowlen, N) &&
          dalloc(&c->offsets, N + 1) && dalloc(&c->row_part, (size_t)scan_parts(N) + 1) &&
          dalloc(&c->idx, (size_t)nnzcap) && dalloc(&c->red_part, nfb * 8) &&
-         dalloc(&c->dt_part, nfb) && dalloc(&c->grid, (size_t)max_instances) &&
+         dalloc(&c->dt_part, nfb * kMaxPairThreads) && dalloc(&c->grid, (size_t)max_instances) &&
          dalloc(&c->status, 4) && dalloc(&c->blk, nfb) &&
          dalloc(&c->ioff, (size_t)max_instances + 1) && dalloc(&c->icnt, (size_t)max_instances) &&
          dalloc(&c->coff, (size_t)max_instances + 1) && dalloc(&c->kpi, (size_t)max_instances) &&
          dalloc(&c->gslab, N * kGSlab) && dalloc(&c->oslab, N * kOSlab) && dalloc(&c->ocnt, N) &&
          dalloc(&c->hs_lo, N) && dalloc(&c->hs_hi, N) && dalloc(&c->hs_it, N) && dalloc(&c->wl, N) &&
          dalloc(&c->scratch_scalar, 2);
+    ok = ok && dalloc(&c->tune_dt, 2 * (size_t)max_instances);
     ok = ok && cudaMallocHost((void**)&c->status_host, 2 * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemset(c->status, 0, 4 * sizeof(unsigned)) == cudaSuccess &&
          cudaMemset(c->offsets, 0, sizeof(int64_t)) == cudaSuccess &&
@@ -467,8 +485,9 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts,
     for (int k = 0; k < ninst; ++k) {
         sph_status st = check_params(c, &params[k]);
         if (st != SPH_OK) return st;
-        if (params[k].precision != params[0].precision) {
-            set_err(c, "instances of a batch must share the precision");
+        if (params[k].precision != params[0].precision ||
+            params[k].pair_threads != params[0].pair_threads) {
+            set_err(c, "instances of a batch must share precision and pair_threads");
             return SPH_E_INVAL;
         }
         if (counts[k] < 0) {
@@ -518,6 +537,7 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts,
     c->ntot = tot;
     c->ninst = ninst;
     c->prec = params[0].precision;
+    c->tpp = c->prec == PREC_FP64_NATIVE ? 1 : kpi[0].pair_threads;
     return SPH_OK;
 }
 

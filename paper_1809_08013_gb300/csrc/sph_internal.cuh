@@ -28,6 +28,7 @@ constexpr int kRadixItems = 8;                      // keys per thread in the so
 constexpr int kRadixTile = kThreads * kRadixItems;  // 2048 keys per block
 constexpr int kScanTile = kThreads * 8;             // elements per block in scans
 constexpr int kReduceBlocks = 304;                  // 2 x 152 SMs
+constexpr int kMaxPairThreads = 8;                  // lanes per particle in the pair kernels
 
 // device status word
 enum : unsigned {
@@ -63,7 +64,7 @@ struct Grid {
 
 // Parameters copied by value into kernels.
 struct KParams {
-    int eos, n_target, n_tol, max_h_iter, periodic_z, precision;
+    int eos, n_target, n_tol, max_h_iter, periodic_z, precision, pair_threads, defer_lanes;
     double rho0, c0, gamma, alpha, beta, eta2, cfl, lz, cell_scale;
 };
 
@@ -108,6 +109,8 @@ inline KParams kparams(const sph_params* p) {
     k.rho0 = p->rho0; k.c0 = p->c0; k.gamma = p->gamma; k.alpha = p->alpha;
     k.beta = p->beta; k.eta2 = p->eta2; k.cfl = p->cfl; k.lz = p->lz;
     k.cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 1.25;
+    k.pair_threads = p->pair_threads > 0 ? p->pair_threads : (p->precision == 1 ? 2 : 1);
+    k.defer_lanes = p->defer_lanes > 0 ? p->defer_lanes : 8;
     return k;
 }
 
@@ -121,6 +124,7 @@ struct sph_ctx {
     int64_t ntot;           // particles of the current batch
     int ninst, maxinst;     // instances of the current batch / capacity
     int prec;               // precision of the current batch
+    int tpp;                // lanes per particle of the pair kernels (1, 2, 4, 8)
     int32_t* blk;           // instance of each block of kSlotAlign slots
     int64_t *ioff, *icnt, *coff;  // per instance: first slot, particles, first caller index
     sph::KParams* kpi;      // per-instance parameters
@@ -156,12 +160,13 @@ struct sph_ctx {
     int32_t* hs_it;         // counts already done for them
     int32_t* wl;            // their indices (count in status[3])
     double* red_part;       // bbox partials: kReduceBlocks x 8
-    double* dt_part;        // per force block
+    double* dt_part;        // per force block (kMaxPairThreads per kThreads slots)
     sph::Grid* grid;        // per instance
     unsigned* status;       // [0] bits, [1] non-converged count, [2] internal flags,
                             // [3] h-search worklist length
     unsigned* status_host;  // pinned mirror
     double* scratch_scalar; // [0] internal dt, [1] internal time
+    double* tune_dt;        // 2 x maxinst: dt and time of the autotuner's trial runs
     int64_t last_hnoconv;
     // launch accounting and optional per-phase event timing
     int64_t launches;
@@ -182,6 +187,8 @@ inline Batch batch_of(const sph_ctx* c) { return Batch{c->blk, c->ioff, c->icnt,
 // ---- sph_abi.cu
 // Describe a single problem of n particles (a batch of one) on the stream.
 void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s);
+// One step of the current batch on the context's state (dt, time: ninst each).
+void launch_step(sph_ctx* c, double* dt, double* time, cudaStream_t s);
 
 // ---- sort.cu
 void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s);

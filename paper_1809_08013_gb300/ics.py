@@ -67,6 +67,8 @@ class SphParams:
     cell_scale: float = 0.0      # neighbour-search cell width / (2 <h>); 0 = library default
     precision: int = 0           # pair arithmetic: 0 FP64-accurate, 1 mixed FP32/double-float,
                                  # 2 native FP64 (the oracle is FP64 throughout)
+    pair_threads: int = 0        # lanes per particle in the pair sums (0 = library default)
+    defer_lanes: int = 0         # h-search hand-over threshold (0 = library default)
 
     def as_dict(self) -> dict:
         return dataclasses.asdict(self)

@@ -50,9 +50,30 @@ def test_ctx_create_rejects_bad_sizes(lib):
     assert not h.value
 
 
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of include/sph.h, as the C compiler lays it out."""
+    import os
+    import subprocess
+    import tempfile
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    body = "".join(f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src = ("#include <stddef.h>\n#include <stdio.h>\n#include \"sph.h\"\n"
+           f'int main(void) {{ printf("%zu\\n", sizeof({struct})); {body} return 0; }}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        with open(c, "w") as f:
+            f.write(src)
+        subprocess.check_call(["gcc", "-I", inc, c, "-o", exe])
+        out = [int(v) for v in subprocess.check_output([exe]).split()]
+    return out[0], out[1:]
+
+
 def test_param_struct_layout_matches_header():
-    # offsets of the C struct (int32 x 6, then 9 doubles)
-    assert C.sizeof(binding.SphParams) == 6 * 4 + 9 * 8
-    assert binding.SphParams.rho0.offset == 24
-    assert C.sizeof(binding.SphParticles) == 8 + 20 * 8
-    assert C.sizeof(binding.SphNeighbors) == 8 + 5 * 8
+    # the ctypes mirrors must lay out exactly like the C structs of the header
+    for cls, name in ((binding.SphParams, "sph_params"), (binding.SphParticles, "sph_particles"),
+                      (binding.SphNeighbors, "sph_neighbors"), (binding.SphTuneSpace, "sph_tune_space"),
+                      (binding.SphTuneTrial, "sph_tune_trial"), (binding.SphTuneResult, "sph_tune_result")):
+        fields = [f for f, _ in cls._fields_]
+        size, offs = _c_layout(name, fields)
+        assert C.sizeof(cls) == size, name
+        assert [getattr(cls, f).offset for f in fields] == offs, name

@@ -69,9 +69,11 @@ def run_alone(B, s, p, nsteps):
     return arr
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_batch_instances_bit_identical_to_alone(B, precision):
+@pytest.mark.parametrize("precision,tpp", [(0, 0), (1, 0), (0, 4), (1, 2)])
+def test_batch_instances_bit_identical_to_alone(B, precision, tpp):
     insts = instances(precision)
+    for _, p in insts:
+        p.pair_threads = tpp
     _, arr, counts, st = run_batch(B, insts, nsteps=3)
     assert st in (B.SPH_OK, B.SPH_E_HNOCONV)
     off = np.concatenate([[0], np.cumsum(counts)])
@@ -185,3 +187,40 @@ def test_batch_of_one_equals_single_problem(B):
     alone = run_alone(B, s, p, nsteps=2)
     for f in FIELDS_OUT:
         assert np.array_equal(host(arr[f]).view(np.uint8), host(alone[f]).view(np.uint8)), f
+
+
+def test_autotune_picks_a_candidate_and_keeps_results_exact(B):
+    insts = instances(0)
+    counts = [len(s["x"]) for s, _ in insts]
+    ctx = B.Context(sum(counts), max_instances=len(insts))
+    ctx.batch_set(counts, [p for _, p in insts])
+    state = concat([s for s, _ in insts])
+    arr = B.alloc_arrays(state, ninst=len(insts))
+    before = {k: host(arr[k]).copy() for k in B.STATE_FIELDS}
+    res = ctx.autotune(arr, nsteps=1, cell_scales=[1.0, 1.5], pair_threads=[1, 2],
+                       defer_lanes=[8, 16])
+    # the caller's state is untouched by the trial runs
+    for k in B.STATE_FIELDS:
+        assert np.array_equal(host(arr[k]), before[k]), k
+    assert res["cell_scale"] in (1.0, 1.25, 1.5)
+    assert res["pair_threads"] in (1, 2) and res["defer_lanes"] in (8, 16)
+    assert 1 <= len(res["trials"]) <= 6
+    assert res["ms_per_step"] == min(t["ms_per_step"] for t in res["trials"])
+    ctx.sync()
+    # the batch now runs with the chosen knobs: still bit-identical to a single
+    # problem given the same knobs, and h / neighbour counts do not depend on them
+    ctx.batch_step(arr, nsteps=2)
+    assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for k, (s, p) in enumerate(insts):
+        q = ics.SphParams(**{**p.as_dict(), "cell_scale": res["cell_scale"],
+                             "pair_threads": res["pair_threads"],
+                             "defer_lanes": res["defer_lanes"]})
+        alone = run_alone(B, s, q, nsteps=2)
+        for f in FIELDS_OUT:
+            a = host(arr[f])[off[k]:off[k + 1]]
+            assert np.array_equal(a.view(np.uint8), host(alone[f]).view(np.uint8)), (k, f)
+        plain = run_alone(B, s, p, nsteps=1)
+        tuned1 = run_alone(B, s, q, nsteps=1)
+        assert np.array_equal(host(plain["h"]), host(tuned1["h"])), k
+        assert np.array_equal(host(plain["nnb"]), host(tuned1["nnb"])), k

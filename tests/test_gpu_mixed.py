@@ -124,6 +124,19 @@ def test_mixed_one_step(B, orc, name):
         assert v <= TOL_MIXED, (k, v)
 
 
+@pytest.mark.parametrize("tpp", [2, 4])
+def test_mixed_with_several_lanes_per_particle(B, orc, tpp):
+    s, prm, o = oracle_of(orc, "evrard_moving")
+    prm = ics.SphParams(**{**prm.as_dict(), "pair_threads": tpp})
+    ctx = B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=1)
+    ctx.sync()
+    err = field_errors(arr, o)
+    for k in ("rho", "ax", "ay", "az", "du", "mumax"):
+        assert err[k] <= TOL_MIXED, (k, err[k])
+
+
 def test_mixed_is_a_distinct_path(B, orc):
     # the FP32 pair terms leave a trace well above the FP64 path's round-off:
     # a dispatch that silently ran the FP64 kernels would fail here

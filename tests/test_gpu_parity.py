@@ -133,6 +133,23 @@ def test_one_step_matches_oracle(B, orc, name):
     assert abs(host(arr["time"])[0] - ex["time"]) <= TOL_FP64 * ex["time"]
 
 
+@pytest.mark.parametrize("tpp", [2, 4, 8])
+def test_one_step_with_several_lanes_per_particle(B, orc, tpp):
+    # the pair sums split over tpp lanes per particle round differently but
+    # stay within the FP64 bar
+    s, prm, o, _ = oracle_of(orc, "patch_ragged_av")
+    prm = ics.SphParams(**{**prm.as_dict(), "pair_threads": tpp})
+    ctx = B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=1)
+    ctx.sync()
+    for k in ("rho", "p", "c"):
+        assert normwise(host(arr[k]), o[k]) <= TOL_FP64, k
+    for k in ("ax", "ay", "az", "du", "mumax"):
+        assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
+    assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
+
+
 def test_three_steps_drift_is_small(B, orc):
     # trajectories are reported as drift: an ulp-level position difference can
     # flip a count at a bisection boundary, so only a loose bound is held
