@@ -12,7 +12,6 @@
 // pass, in the order lanes, cell width, hand-over).
 #include <string.h>
 
-#include <vector>
 
 #include "sph_internal.cuh"
 
