@@ -89,6 +89,12 @@ def parse():
                     help="skip the batched-ensemble measurement")
     ap.add_argument("--ensemble-steps", type=int, default=50)
     ap.add_argument("--ensemble-count", type=int, default=256)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the serving stream (the full configuration has 2000)")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-quantum", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -372,6 +378,73 @@ def _run_ensemble(args, B, dev, stream):
     }
 
 
+def run_serving(args, B, dev):
+    """Configuration 5: a Poisson stream of patch / Evrard requests served by
+    continuous batching (paper_1809_08013_gb300.serve) in FP64 and in mixed
+    precision, against the plain single-instance FP64 path taking the same
+    requests one at a time in arrival order."""
+    import numpy as np
+    import torch
+
+    from paper_1809_08013_gb300 import serve
+    torch.cuda.empty_cache()
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": f"{args.serve_requests} requests, Poisson arrivals at {args.serve_rate}/s, "
+                       f"patch (omega ~ U[2,8]) or Evrard 50/50, N log-uniform in [8000, 1e6], "
+                       f"steps ~ U{{10..100}}, device budget {args.serve_budget_gb} GB, "
+                       f"quantum {args.serve_quantum} steps, admission in arrival order",
+           "latency_unit": "s"}
+    base = serve.make_stream(args.serve_requests, args.serve_rate, seed=5)
+    with torch.cuda.stream(stream):
+        # the single-instance FP64 path, one request at a time (time alone per request)
+        one = B.Context(max(r.n for r in base), device=dev.index)
+        run_time, alone = {}, {}
+        for r in base:
+            st, p = serve.initial_state(r, 0)
+            a = B.alloc_arrays(st, device=dev)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            one.step(p, a, nsteps=r.steps, stream=stream)
+            f1.record(stream)
+            torch.cuda.synchronize(dev)
+            run_time[r.rid] = f0.elapsed_time(f1) * 1e-3
+            if r.rid < 16:
+                alone[r.rid] = {f: a[f].cpu().numpy() for f in ("x", "vx", "h", "u", "rho")}
+        one.sync(stream)
+        del one
+        out["single_instance_fp64"] = serve.fifo_single(
+            [dataclasses_replace(r) for r in base], run_time)
+        bpp = serve.Server.bytes_per_particle()
+        cap = int(args.serve_budget_gb * 1e9 / bpp)
+        for prec, name in ((0, "batched_fp64"), (1, "batched_mixed")):
+            reqs = serve.make_stream(args.serve_requests, args.serve_rate, seed=5)
+            states = {r.rid: serve.initial_state(r, prec) for r in reqs}
+            srv = serve.Server(cap, max_instances=256, quantum=args.serve_quantum,
+                               device=dev.index, stream=stream,
+                               result_fields=("x", "vx", "h", "u", "rho"),
+                               keep_result=lambda r: r.rid < 16)
+            summ = serve.serve(srv, reqs, states, clock="real")
+            summ["capacity_particles"] = cap
+            summ["device_bytes_per_particle"] = bpp
+            summ["ticks"] = srv.ticks
+            summ["status"] = B.STATUS_NAMES.get(srv.status)
+            if prec == 0:
+                summ["results_equal_single_instance_bitwise"] = bool(all(
+                    np.array_equal(reqs[k].result[f].view(np.uint8), v.view(np.uint8))
+                    for k, ref in alone.items() for f, v in ref.items()))
+                summ["compared_requests"] = len(alone)
+            out[name] = summ
+            del srv
+            torch.cuda.empty_cache()
+    return out
+
+
+def dataclasses_replace(r):
+    import dataclasses
+    return dataclasses.replace(r)
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -544,6 +617,9 @@ def run_native(args):
     ensemble = None
     if not args.no_ensemble and args.workload == "patch" and world == 1:
         ensemble = run_ensemble(args, B, dev)
+    serving = None
+    if not args.no_serving and args.workload == "patch" and world == 1:
+        serving = run_serving(args, B, dev)
 
     clocks = sampler.summary(w0, w1) if sampler else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -554,7 +630,7 @@ def run_native(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (state ~0.2 GB + neighbour list ~0.4 GB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "steady_state": steady, "ensemble": ensemble,
+            "steady_state": steady, "ensemble": ensemble, "serving": serving,
             "clocks": clocks, "status": B.STATUS_NAMES.get(status),
             "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
             "launches_per_phase": phase_launches}

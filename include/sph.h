@@ -139,6 +139,11 @@ sph_status sph_ctx_create(sph_ctx **out, int64_t n_capacity, int64_t nnz_capacit
 sph_status sph_ctx_create_batch(sph_ctx **out, int64_t n_capacity, int64_t nnz_capacity,
                                 int32_t max_instances, int device);
 
+/* Device bytes a context of these capacities allocates (each allocation
+ * rounded up to 256 bytes), without allocating; -1 for invalid sizes. Lets a
+ * caller fit contexts into a memory budget. */
+int64_t sph_ctx_bytes(int64_t n_capacity, int64_t nnz_capacity, int32_t max_instances);
+
 /* Free the context and its device memory (synchronises the device). NULL is a no-op. */
 void sph_ctx_destroy(sph_ctx *ctx);
 
@@ -173,10 +178,11 @@ sph_status sph_step(sph_ctx *ctx, const sph_params *prm, sph_particles *P, int n
                     void *stream);
 
 /* Describe a batch of ninst independent problems for sph_batch_step.
- * counts[k] (host array) is the number of particles of instance k; the
- * caller's particle arrays hold the instances back to back, instance k at
- * [sum_{l<k} counts[l], ... + counts[k]). params[k] (host array) are its
- * parameters; all instances must share `precision`. Instances never
+ * counts[k] (host array) is the number of particles of instance k, held in
+ * the caller's arrays at [first[k], first[k] + counts[k]) (first: host array,
+ * ranges must not overlap; NULL = back to back from index 0). params[k]
+ * (host array) are its parameters; all instances must share `precision`
+ * and `pair_threads`. Instances never
  * interact: each has its own cell grid, neighbour sets, time step and time.
  * An instance's results are bit-identical to a single-problem sph_step of it
  * with the same parameters. Copies the descriptors to the device and waits
@@ -184,13 +190,15 @@ sph_status sph_step(sph_ctx *ctx, const sph_params *prm, sph_particles *P, int n
  * [1, max_instances], a negative count, invalid params, or more particles
  * than the capacity. Any single-problem call replaces the batch. */
 sph_status sph_batch_set(sph_ctx *ctx, int32_t ninst, const int64_t *counts,
-                         const sph_params *params, void *stream);
+                         const int64_t *first, const sph_params *params, void *stream);
 
 /* sph_step for every instance of the batch: P holds all instances' arrays
- * (P->n = total particles); P->dt and P->time are device arrays of ninst
- * doubles (per-instance time step and time). Enqueues only kernel launches,
- * so it can be captured in a CUDA graph and replayed while the batch is
- * unchanged. SPH_E_INVAL if P->n differs from the batch's total. */
+ * (P->n = their length, at least the end of the last instance; entries
+ * outside the instances are not touched); P->dt and P->time are device
+ * arrays of ninst doubles (per-instance time step and time). Enqueues only
+ * kernel launches, so it can be captured in a CUDA graph and replayed while
+ * the batch is unchanged. SPH_E_INVAL if P->n is too short. Splitting a run
+ * into several calls gives the same bits as one call. */
 sph_status sph_batch_step(sph_ctx *ctx, sph_particles *P, int nsteps, void *stream);
 
 /* Rows of the current neighbour list (the n of sph_neighbors): the particle
@@ -230,7 +238,7 @@ typedef struct {
  * sph_batch_step until the next sph_batch_set, and a single-problem call
  * takes them from its sph_params. space = NULL uses cell_scale {1, 1.25,
  * 1.5}, pair_threads {1, 2, 4}, defer_lanes {8, 16}. Synchronises the
- * stream (not capturable). SPH_E_INVAL for nsteps < 1, P->n different from
+ * stream (not capturable). SPH_E_INVAL for nsteps < 1, P->n too short for
  * the batch, invalid candidates or more than SPH_TUNE_MAX_TRIALS of them.
  * Device conditions of the trial runs (h non-convergence) stay in the
  * status word for the next sph_sync. This knob search has no counterpart in

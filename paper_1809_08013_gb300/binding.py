@@ -99,10 +99,12 @@ def load(rebuild: bool = True):
     L.sph_last_hnoconv.argtypes = [_DP]
     L.sph_ctx_create.restype = C.c_int
     L.sph_ctx_create.argtypes = [P(_DP), C.c_int64, C.c_int64, C.c_int]
+    L.sph_ctx_bytes.restype = C.c_int64
+    L.sph_ctx_bytes.argtypes = [C.c_int64, C.c_int64, C.c_int32]
     L.sph_ctx_create_batch.restype = C.c_int
     L.sph_ctx_create_batch.argtypes = [P(_DP), C.c_int64, C.c_int64, C.c_int32, C.c_int]
     L.sph_batch_set.restype = C.c_int
-    L.sph_batch_set.argtypes = [_DP, C.c_int32, P(C.c_int64), P(SphParams), _DP]
+    L.sph_batch_set.argtypes = [_DP, C.c_int32, P(C.c_int64), P(C.c_int64), P(SphParams), _DP]
     L.sph_autotune.restype = C.c_int
     L.sph_autotune.argtypes = [_DP, P(SphParticles), C.c_int, P(SphTuneSpace), P(SphTuneResult),
                                _DP]
@@ -134,6 +136,13 @@ def load(rebuild: bool = True):
     L.sph_probe_fma_peak.argtypes = [C.c_int, C.c_int, _DP, C.POINTER(C.c_double)]
     _lib = L
     return L
+
+
+def ctx_bytes(n_capacity: int, nnz_capacity: int | None = None, max_instances: int = 1) -> int:
+    """Device bytes of a context with these capacities (see sph_ctx_bytes)."""
+    if nnz_capacity is None:
+        nnz_capacity = max(1024, 160 * int(n_capacity))
+    return int(load().sph_ctx_bytes(int(n_capacity), int(nnz_capacity), int(max_instances)))
 
 
 def probe_fma_peak(device: int = 0, fp64: bool = True, stream=None) -> float:
@@ -260,13 +269,15 @@ class Context:
         self._check(self.lib.sph_step(self.h, C.byref(params(prm)), C.byref(P), int(nsteps),
                                       _stream(stream)))
 
-    def batch_set(self, counts, prms, stream=None):
-        """Describe a batch: counts[k] particles of instance k (instances back
-        to back in the arrays), prms[k] its parameters."""
+    def batch_set(self, counts, prms, first=None, stream=None):
+        """Describe a batch: counts[k] particles of instance k, at
+        [first[k], first[k] + counts[k]) of the arrays (None: back to back),
+        prms[k] its parameters."""
         k = len(counts)
         cnt = (C.c_int64 * k)(*[int(v) for v in counts])
+        fst = None if first is None else (C.c_int64 * k)(*[int(v) for v in first])
         pa = (SphParams * k)(*[params(p) for p in prms])
-        self._check(self.lib.sph_batch_set(self.h, k, cnt, pa, _stream(stream)))
+        self._check(self.lib.sph_batch_set(self.h, k, cnt, fst, pa, _stream(stream)))
 
     def batch_step(self, arrays: dict, nsteps: int = 1, stream=None):
         P = particles(arrays)

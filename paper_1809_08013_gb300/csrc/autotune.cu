@@ -68,7 +68,7 @@ extern "C" sph_status sph_autotune(sph_ctx* c, sph_particles* P, int nsteps,
                                    const sph_tune_space* space, sph_tune_result* out,
                                    void* stream) {
     if (!c || !P || !out || nsteps < 1) return SPH_E_INVAL;
-    if (P->n != c->ntot) return SPH_E_INVAL;
+    if (P->n < c->cext) return SPH_E_INVAL;
     if (P->n > 0 && (!P->x || !P->y || !P->z || !P->h || !P->m)) return SPH_E_INVAL;
     static const double kCs[] = {1.0, 1.25, 1.5};
     static const int32_t kTpp[] = {1, 2, 4};

@@ -1,8 +1,14 @@
 // sort.cu -- Algorithm 1 step 1 ("build tree"), done as Morton-sorted cell
 // lists: bounding box and cell grid on the device, 24-bit Morton key of each
-// particle's cell, a stable LSD radix sort (3 passes of 8 bits), the
-// permutation of the particle state into sorted order, and the [start, end)
-// range of every occupied cell.
+// particle's cell, a stable LSD radix sort (3 passes of 8 bits, one more for
+// the instance id of a batch), the permutation of the particle state into
+// sorted order, and the [start, end) range of every occupied cell.
+//
+// The keys are sorted in caller order (each particle at its "rank" roff[k] +
+// its index within its instance), not in the order the previous step left,
+// so particles of one cell always end up ordered by caller index: the
+// internal order -- and with it every summation order -- depends only on the
+// positions, and a run split into several calls gives the same bits as one.
 #include <math_constants.h>
 
 #include "df.cuh"
@@ -21,16 +27,17 @@ k_load_state(int64_t n, Batch B, const int64_t* __restrict__ coff, const double*
              const double* __restrict__ vy, const double* __restrict__ vz,
              const double* __restrict__ m, const double* __restrict__ u,
              double4_32a* __restrict__ posh, double4_32a* __restrict__ velm,
-             double* __restrict__ ue, int32_t* __restrict__ order) {
+             double* __restrict__ ue, int32_t* __restrict__ order, double4_32a* __restrict__ posh2,
+             double4_32a* __restrict__ velm2, double* __restrict__ ue2, int32_t* __restrict__ order2) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int inst = slot_inst(B, k);
     const int64_t r = k - __ldg(&B.ioff[inst]);
-    if (r >= __ldg(&B.icnt[inst])) {
-        posh[k] = make_double4_32a(0.0, 0.0, 0.0, 1.0);
-        velm[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-        ue[k] = 0.0;
-        order[k] = -1;
+    if (r >= __ldg(&B.icnt[inst])) {  // empty slot, inert in both buffers (never permuted)
+        posh[k] = posh2[k] = make_double4_32a(0.0, 0.0, 0.0, 1.0);
+        velm[k] = velm2[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        ue[k] = ue2[k] = 0.0;
+        order[k] = order2[k] = -1;
         return;
     }
     const int64_t c = __ldg(&coff[inst]) + r;
@@ -47,7 +54,8 @@ void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s) {
     c->launches += 1;
     k_load_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         n, batch_of(c), c->coff, P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m, P->u,
-        c->posh[b], c->velm[b], c->ue[b], c->order[b]);
+        c->posh[b], c->velm[b], c->ue[b], c->order[b], c->posh[1 - b], c->velm[1 - b],
+        c->ue[1 - b], c->order[1 - b]);
 }
 
 // Re-read the caller's arrays into the sorted order of the last build and
@@ -273,25 +281,25 @@ __device__ __forceinline__ int cell_coord(double v, double lo, double inv, int n
 }
 
 // key = instance (top 8 bits) | 24-bit Morton code of the particle's cell in
-// its instance's grid; empty slots take their instance's largest code, and
-// the stable sort keeps them after the instance's particles.
+// its instance's grid, stored at the particle's rank roff[k] + (caller index
+// - coff[k]) with its current slot as the value.
 __global__ void __launch_bounds__(kThreads)
-k_keys(int64_t n, Batch B, const double4_32a* __restrict__ posh, uint32_t* __restrict__ keys,
-       int32_t* __restrict__ vals) {
+k_keys(int64_t n, Batch B, const int64_t* __restrict__ coff, const int64_t* __restrict__ roff,
+       const double4_32a* __restrict__ posh, const int32_t* __restrict__ order,
+       uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int inst = slot_inst(B, k);
-    uint32_t code = 0xffffffu;
-    if (slot_real(B, inst, k)) {
-        const Grid* g = B.grid + inst;
-        const double4_32a p = posh[k];
-        const int kx = cell_coord(p.x, g->lo[0], g->inv_w[0], g->n[0]);
-        const int ky = cell_coord(p.y, g->lo[1], g->inv_w[1], g->n[1]);
-        const int kz = cell_coord(p.z, g->lo[2], g->inv_w[2], g->n[2]);
-        code = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
-    }
-    keys[k] = ((uint32_t)inst << 24) | code;
-    vals[k] = (int32_t)k;
+    if (!slot_real(B, inst, k)) return;
+    const Grid* g = B.grid + inst;
+    const double4_32a p = posh[k];
+    const int kx = cell_coord(p.x, g->lo[0], g->inv_w[0], g->n[0]);
+    const int ky = cell_coord(p.y, g->lo[1], g->inv_w[1], g->n[1]);
+    const int kz = cell_coord(p.z, g->lo[2], g->inv_w[2], g->n[2]);
+    const uint32_t code = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+    const int64_t q = __ldg(&roff[inst]) + ((int64_t)order[k] - __ldg(&coff[inst]));
+    keys[q] = ((uint32_t)inst << 24) | code;
+    vals[q] = (int32_t)k;
 }
 
 // --------------------------------------------------------- stable radix sort
@@ -365,15 +373,20 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vi
 }
 
 // ------------------------------------------------------ permute and cells
+// Sorted rank p of instance i goes to slot ioff[i] + (p - roff[i]).
 __global__ void __launch_bounds__(kThreads)
-k_permute(int64_t n, const int32_t* __restrict__ perm, const double4_32a* __restrict__ posh_in,
+k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
+          const uint32_t* __restrict__ keys, const int32_t* __restrict__ perm,
+          const double4_32a* __restrict__ posh_in,
           const double4_32a* __restrict__ velm_in, const double* __restrict__ u_in,
           const int32_t* __restrict__ order_in, double4_32a* __restrict__ posh_out,
           double4_32a* __restrict__ velm_out, double* __restrict__ u_out,
           int32_t* __restrict__ order_out, float4* __restrict__ fpos, float2* __restrict__ mdf) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int64_t o = perm[k];
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ntot) return;
+    const int inst = (int)(keys[r] >> 24);
+    const int64_t k = __ldg(&B.ioff[inst]) + (r - __ldg(&roff[inst]));
+    const int64_t o = perm[r];
     const double4_32a p = posh_in[o];
     posh_out[k] = p;
     const double4_32a v = velm_in[o];
@@ -397,17 +410,19 @@ k_cells_clear(Batch B, int2* __restrict__ cells, unsigned long long* __restrict_
     }
 }
 
+// Cell ranges (in slots) from the sorted keys (in ranks).
 __global__ void __launch_bounds__(kThreads)
-k_cells_mark(int64_t n, Batch B, const uint32_t* __restrict__ keys, int2* __restrict__ cells) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int inst = slot_inst(B, k);
-    const int64_t a = __ldg(&B.ioff[inst]), e = a + __ldg(&B.icnt[inst]);
-    if (k >= e) return;  // empty slot
-    const uint32_t key = keys[k];
-    const bool first = (k == a) || keys[k - 1] != key;
-    const bool last = (k == e - 1) || keys[k + 1] != key;
+k_cells_mark(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
+             const uint32_t* __restrict__ keys, int2* __restrict__ cells) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ntot) return;
+    const uint32_t key = keys[r];
+    const int inst = (int)(key >> 24);
+    const int64_t a = __ldg(&roff[inst]), e = a + __ldg(&B.icnt[inst]);
+    const bool first = (r == a) || keys[r - 1] != key;
+    const bool last = (r == e - 1) || keys[r + 1] != key;
     if (!(first || last)) return;
+    const int64_t k = __ldg(&B.ioff[inst]) + (r - a);
     const Grid* g = B.grid + inst;
     const uint32_t code = key & 0xffffffu;
     const int kx = compact3(code), ky = compact3(code >> 1), kz = compact3(code >> 2);
@@ -427,27 +442,31 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     }
     k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status);
     if (n == 0) return;
+    const int64_t nt = c->ntot;
+    if (nt == 0) return;
+    const unsigned nbt = (unsigned)((nt + kThreads - 1) / kThreads);
     const int passes = c->ninst > 1 ? 4 : 3;
     c->launches += 1 + passes * 5 + 3;
-    k_keys<<<nb, kThreads, 0, s>>>(n, B, c->posh[c->cur], c->keys[0], c->vals[0]);
-    const int nsb = (int)((n + kRadixTile - 1) / kRadixTile);
+    k_keys<<<nb, kThreads, 0, s>>>(n, B, c->coff, c->roff, c->posh[c->cur], c->order[c->cur],
+                                   c->keys[0], c->vals[0]);
+    const int nsb = (int)((nt + kRadixTile - 1) / kRadixTile);
     int src = 0;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
-        k_radix_hist<<<nsb, kThreads, 0, s>>>(c->keys[src], n, shift, c->hist, nsb);
+        k_radix_hist<<<nsb, kThreads, 0, s>>>(c->keys[src], nt, shift, c->hist, nsb);
         launch_scan_u32(c->hist, (int64_t)256 * nsb, c->hist_part, s);
-        k_radix_scatter<<<nsb, kThreads, 0, s>>>(c->keys[src], c->vals[src], n, shift, c->hist,
+        k_radix_scatter<<<nsb, kThreads, 0, s>>>(c->keys[src], c->vals[src], nt, shift, c->hist,
                                                   nsb, c->keys[1 - src], c->vals[1 - src]);
         src = 1 - src;
     }
     // sorted keys / permutation now in keys[src], vals[src]
     const int a = c->cur, b = 1 - c->cur;
-    k_permute<<<nb, kThreads, 0, s>>>(n, c->vals[src], c->posh[a], c->velm[a], c->ue[a],
-                                       c->order[a], c->posh[b], c->velm[b], c->ue[b], c->order[b],
-                                       c->fpos, c->mdf);
+    k_permute<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->vals[src], c->posh[a],
+                                        c->velm[a], c->ue[a], c->order[a], c->posh[b], c->velm[b],
+                                        c->ue[b], c->order[b], c->fpos, c->mdf);
     c->cur = b;
     k_cells_clear<<<dim3(64, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->cells, c->cell_hmax);
-    k_cells_mark<<<nb, kThreads, 0, s>>>(n, B, c->keys[src], c->cells);
+    k_cells_mark<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->cells);
 }
 
 }  // namespace sph

@@ -101,7 +101,7 @@ void free_all(sph_ctx* c) {
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->gslab, c->oslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
-                    c->tune_dt};
+                    c->tune_dt, c->roff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -128,6 +128,61 @@ void free_events(sph_ctx* c) {
     c->ev_cap = c->ev_used = 0;
 }
 
+// per-instance budgets instance_cell_cap(n_k) sum to at most this
+int64_t cell_capacity(int64_t ncap, int64_t max_instances) {
+    return std::min<int64_t>(2 * ncap + (int64_t)kMinInstanceCells * max_instances,
+                             max_instances * kMaxCellsPerAxis * kMaxCellsPerAxis *
+                                 kMaxCellsPerAxis);
+}
+
+// Device allocations of a context, listed once: with dry = true only their
+// total size is computed (sph_ctx_bytes).
+struct Allocator {
+    bool dry;
+    size_t bytes;
+    template <class T>
+    bool operator()(T** p, size_t count) {
+        if (count == 0) count = 1;
+        bytes += (count * sizeof(T) + 255) / 256 * 256;
+        if (dry) {
+            *p = nullptr;
+            return true;
+        }
+        return dalloc(p, count);
+    }
+};
+
+bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
+    const int64_t max_instances = c->maxinst;
+    const int64_t nnzcap = c->nnzcap;
+    const size_t N = (size_t)std::max<int64_t>(nslots, 1);
+    const size_t nsb = (N + kRadixTile - 1) / kRadixTile;
+    const size_t nfb = (N + kThreads - 1) / kThreads;
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+        ok = ok && al(&c->posh[b], N) && al(&c->velm[b], N) && al(&c->ue[b], N) &&
+             al(&c->order[b], N) && al(&c->keys[b], N) && al(&c->vals[b], N);
+    }
+    ok = ok && al(&c->therm, N) && al(&c->kern, N) && al(&c->acc, N) &&
+         al(&c->pint, N) && al(&c->cint, N) && al(&c->dpk, 3 * N) &&
+         al(&c->mdf, N) && al(&c->mpk, 5 * N) &&
+         al(&c->mumax, N) && al(&c->fpos, N) && al(&c->tin, N) &&
+         al(&c->hist, 256 * nsb) && al(&c->hist_part, (size_t)scan_parts(256 * nsb) + 1) &&
+         al(&c->cells, (size_t)c->cellcap) && al(&c->cell_hmax, (size_t)c->cellcap) &&
+         al(&c->nnb, N) && al(&c->ngather, N) && al(&c->rowlen, N) &&
+         al(&c->offsets, N + 1) && al(&c->row_part, (size_t)scan_parts(N) + 1) &&
+         al(&c->idx, (size_t)nnzcap) && al(&c->red_part, nfb * 8) &&
+         al(&c->dt_part, nfb * kMaxPairThreads) && al(&c->grid, (size_t)max_instances) &&
+         al(&c->status, 4) && al(&c->blk, nfb) &&
+         al(&c->ioff, (size_t)max_instances + 1) && al(&c->icnt, (size_t)max_instances) &&
+         al(&c->coff, (size_t)max_instances + 1) && al(&c->kpi, (size_t)max_instances) &&
+         al(&c->roff, (size_t)max_instances + 1) &&
+         al(&c->gslab, N * kGSlab) && al(&c->oslab, N * kOSlab) && al(&c->ocnt, N) &&
+         al(&c->hs_lo, N) && al(&c->hs_hi, N) && al(&c->hs_it, N) && al(&c->wl, N) &&
+         al(&c->scratch_scalar, 2) && al(&c->tune_dt, 2 * (size_t)max_instances);
+    return ok;
+}
+
 }  // namespace
 
 namespace sph {
@@ -138,7 +193,7 @@ namespace sph {
 __global__ void __launch_bounds__(kThreads)
 k_set_single(KParams kp, int64_t n, long long cap, int64_t nblk, int32_t* __restrict__ blk,
              int64_t* __restrict__ ioff, int64_t* __restrict__ icnt, int64_t* __restrict__ coff,
-             KParams* __restrict__ kpi, Grid* __restrict__ grid) {
+             int64_t* __restrict__ roff, KParams* __restrict__ kpi, Grid* __restrict__ grid) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t b = t; b < nblk; b += (int64_t)gridDim.x * blockDim.x) blk[b] = 0;
     if (t == 0) {
@@ -148,6 +203,8 @@ k_set_single(KParams kp, int64_t n, long long cap, int64_t nblk, int32_t* __rest
         icnt[0] = n;
         coff[0] = 0;
         coff[1] = n;
+        roff[0] = 0;
+        roff[1] = n;
         grid[0].cbase = 0;
         grid[0].cap = cap;
     }
@@ -156,6 +213,7 @@ k_set_single(KParams kp, int64_t n, long long cap, int64_t nblk, int32_t* __rest
 void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s) {
     c->n = n;
     c->ntot = n;
+    c->cext = n;
     c->ninst = 1;
     c->prec = kp.precision;
     c->tpp = kp.precision == PREC_FP64_NATIVE ? 1 : kp.pair_threads;
@@ -163,7 +221,7 @@ void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s)
     const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((nblk + kThreads - 1) / kThreads, 1), 1024);
     c->launches += 1;
     k_set_single<<<nb, kThreads, 0, s>>>(kp, n, instance_cell_cap(n), nblk, c->blk, c->ioff,
-                                         c->icnt, c->coff, c->kpi, c->grid);
+                                         c->icnt, c->coff, c->roff, c->kpi, c->grid);
 }
 
 // One step of the current batch on the state held in the context (Algorithm
@@ -272,6 +330,19 @@ const char* sph_last_error(const sph_ctx* c) { return c ? c->err : "context is N
 
 int64_t sph_last_hnoconv(const sph_ctx* c) { return c ? c->last_hnoconv : 0; }
 
+int64_t sph_ctx_bytes(int64_t ncap, int64_t nnzcap, int32_t max_instances) {
+    if (ncap < 0 || nnzcap < 0 || max_instances < 1 || max_instances > SPH_MAX_INSTANCES) return -1;
+    sph_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.ncap = ncap;
+    c.nnzcap = nnzcap;
+    c.maxinst = max_instances;
+    c.cellcap = cell_capacity(ncap, max_instances);
+    Allocator A{true, 0};
+    allocate_all(&c, ncap + (int64_t)(kSlotAlign - 1) * (max_instances - 1), A);
+    return (int64_t)A.bytes;
+}
+
 sph_status sph_ctx_create(sph_ctx** out, int64_t ncap, int64_t nnzcap, int device) {
     return sph_ctx_create_batch(out, ncap, nnzcap, 1, device);
 }
@@ -300,35 +371,9 @@ sph_status sph_ctx_create_batch(sph_ctx** out, int64_t ncap, int64_t nnzcap, int
     c->nnzcap = nnzcap;
     c->maxinst = max_instances;
     c->ninst = 1;
-    // per-instance budgets instance_cell_cap(n_k) sum to at most this
-    c->cellcap = std::min<int64_t>(2 * ncap + (int64_t)kMinInstanceCells * max_instances,
-                                   (int64_t)max_instances * kMaxCellsPerAxis * kMaxCellsPerAxis *
-                                       kMaxCellsPerAxis);
-    const size_t N = (size_t)std::max<int64_t>(nslots, 1);
-    const size_t nsb = (N + kRadixTile - 1) / kRadixTile;
-    const size_t nfb = (N + kThreads - 1) / kThreads;
-    bool ok = true;
-    for (int b = 0; b < 2; ++b) {
-        ok = ok && dalloc(&c->posh[b], N) && dalloc(&c->velm[b], N) && dalloc(&c->ue[b], N) &&
-             dalloc(&c->order[b], N) && dalloc(&c->keys[b], N) && dalloc(&c->vals[b], N);
-    }
-    ok = ok && dalloc(&c->therm, N) && dalloc(&c->kern, N) && dalloc(&c->acc, N) &&
-         dalloc(&c->pint, N) && dalloc(&c->cint, N) && dalloc(&c->dpk, 3 * N) &&
-         dalloc(&c->mdf, N) && dalloc(&c->mpk, 5 * N) &&
-         dalloc(&c->mumax, N) && dalloc(&c->fpos, N) && dalloc(&c->tin, N) &&
-         dalloc(&c->hist, 256 * nsb) && dalloc(&c->hist_part, (size_t)scan_parts(256 * nsb) + 1) &&
-         dalloc(&c->cells, (size_t)c->cellcap) && dalloc(&c->cell_hmax, (size_t)c->cellcap) &&
-         dalloc(&c->nnb, N) && dalloc(&c->ngather, N) && dalloc(&c->rowlen, N) &&
-         dalloc(&c->offsets, N + 1) && dalloc(&c->row_part, (size_t)scan_parts(N) + 1) &&
-         dalloc(&c->idx, (size_t)nnzcap) && dalloc(&c->red_part, nfb * 8) &&
-         dalloc(&c->dt_part, nfb * kMaxPairThreads) && dalloc(&c->grid, (size_t)max_instances) &&
-         dalloc(&c->status, 4) && dalloc(&c->blk, nfb) &&
-         dalloc(&c->ioff, (size_t)max_instances + 1) && dalloc(&c->icnt, (size_t)max_instances) &&
-         dalloc(&c->coff, (size_t)max_instances + 1) && dalloc(&c->kpi, (size_t)max_instances) &&
-         dalloc(&c->gslab, N * kGSlab) && dalloc(&c->oslab, N * kOSlab) && dalloc(&c->ocnt, N) &&
-         dalloc(&c->hs_lo, N) && dalloc(&c->hs_hi, N) && dalloc(&c->hs_it, N) && dalloc(&c->wl, N) &&
-         dalloc(&c->scratch_scalar, 2);
-    ok = ok && dalloc(&c->tune_dt, 2 * (size_t)max_instances);
+    c->cellcap = cell_capacity(ncap, max_instances);
+    Allocator A{false, 0};
+    bool ok = allocate_all(c, nslots, A);
     ok = ok && cudaMallocHost((void**)&c->status_host, 2 * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemset(c->status, 0, 4 * sizeof(unsigned)) == cudaSuccess &&
          cudaMemset(c->offsets, 0, sizeof(int64_t)) == cudaSuccess &&
@@ -470,14 +515,14 @@ sph_status sph_step(sph_ctx* c, const sph_params* prm, sph_particles* P, int nst
     return check_launch(c, "sph_step");
 }
 
-sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts,
+sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const int64_t* first,
                          const sph_params* params, void* stream) {
     if (!c) return SPH_E_INVAL;
     if (ninst < 1 || ninst > c->maxinst || !counts || !params) {
         set_err(c, "ninst = %d outside [1, %d] or NULL arrays", (int)ninst, c->maxinst);
         return SPH_E_INVAL;
     }
-    std::vector<int64_t> ioff(ninst + 1), coff(ninst + 1), icnt(ninst);
+    std::vector<int64_t> ioff(ninst + 1), coff(ninst + 1), roff(ninst + 1), icnt(ninst);
     std::vector<KParams> kpi(ninst);
     std::vector<Grid> grid(ninst);
     int64_t slots = 0, tot = 0;
@@ -494,8 +539,13 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts,
             set_err(c, "counts[%d] < 0", k);
             return SPH_E_INVAL;
         }
+        if (first && first[k] < 0) {
+            set_err(c, "first[%d] < 0", k);
+            return SPH_E_INVAL;
+        }
         ioff[k] = slots;
-        coff[k] = tot;
+        roff[k] = tot;
+        coff[k] = first ? first[k] : tot;
         icnt[k] = counts[k];
         tot += counts[k];
         slots += counts[k];
@@ -507,7 +557,23 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts,
         cells += grid[k].cap;
     }
     ioff[ninst] = slots;
-    coff[ninst] = tot;
+    roff[ninst] = tot;
+    int64_t ext = tot;
+    if (first) {  // the instances' caller ranges must not overlap
+        std::vector<int> ord(ninst);
+        for (int k = 0; k < ninst; ++k) ord[k] = k;
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return coff[a] < coff[b]; });
+        ext = 0;
+        for (int q = 0; q < ninst; ++q) {
+            const int k = ord[q];
+            if (q > 0 && counts[k] > 0 && coff[k] < ext) {
+                set_err(c, "instance %d overlaps an earlier one in the caller arrays", k);
+                return SPH_E_INVAL;
+            }
+            if (counts[k] > 0) ext = std::max(ext, coff[k] + counts[k]);
+        }
+    }
+    coff[ninst] = ext;
     if (tot > c->ncap || cells > c->cellcap) {
         set_err(c, "batch of %lld particles exceeds the capacity %lld", (long long)tot,
                 (long long)c->ncap);
@@ -523,6 +589,7 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts,
     cudaError_t e = cudaMemcpyAsync(c->ioff, ioff.data(), (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->coff, coff.data(), (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->icnt, icnt.data(), ninst * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->roff, roff.data(), (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->kpi, kpi.data(), ninst * sizeof(KParams), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->grid, grid.data(), ninst * sizeof(Grid), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && nblk > 0)
@@ -535,6 +602,7 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts,
     }
     c->n = slots;
     c->ntot = tot;
+    c->cext = ext;
     c->ninst = ninst;
     c->prec = params[0].precision;
     c->tpp = c->prec == PREC_FP64_NATIVE ? 1 : kpi[0].pair_threads;
@@ -545,9 +613,9 @@ sph_status sph_batch_step(sph_ctx* c, sph_particles* P, int nsteps, void* stream
     if (!c) return SPH_E_INVAL;
     if (!P) { set_err(c, "particles is NULL"); return SPH_E_INVAL; }
     if (nsteps < 0) { set_err(c, "nsteps < 0"); return SPH_E_INVAL; }
-    if (P->n != c->ntot) {
-        set_err(c, "n = %lld differs from the batch (%lld particles)", (long long)P->n,
-                (long long)c->ntot);
+    if (P->n < c->cext) {
+        set_err(c, "n = %lld: the batch's instances extend to index %lld of the arrays",
+                (long long)P->n, (long long)c->cext);
         return SPH_E_INVAL;
     }
     NEED(P->dt); NEED(P->time);

@@ -127,6 +127,8 @@ struct sph_ctx {
     int tpp;                // lanes per particle of the pair kernels (1, 2, 4, 8)
     int32_t* blk;           // instance of each block of kSlotAlign slots
     int64_t *ioff, *icnt, *coff;  // per instance: first slot, particles, first caller index
+    int64_t* roff;          // per instance: first sort rank (sum of the earlier counts)
+    int64_t cext;           // caller arrays must hold this many entries (max coff + icnt)
     sph::KParams* kpi;      // per-instance parameters
     int cur;                // current buffer of the double-buffered state
     double4_32a *posh[2], *velm[2];     // permuted with the particles (double-buffered)

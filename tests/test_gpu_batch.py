@@ -133,6 +133,37 @@ def test_batch_one_step_matches_oracle(B, orc):
         assert abs(host(arr["dt"])[k] - o["dt"]) <= TOL_FP64 * o["dt"], k
 
 
+def test_batch_instances_anywhere_in_the_arrays(B):
+    # instances at scattered, out-of-order offsets of longer arrays (a memory
+    # arena): same bits as alone, and entries outside the instances untouched
+    insts = instances(0)
+    counts = [len(s["x"]) for s, _ in insts]
+    first = [30000, 100, 9000, 52000, 18000]
+    n = 60000
+    rng = np.random.Generator(np.random.PCG64(5))
+    state = {k: rng.uniform(-1, 1, n) for k in ics.FIELDS}
+    for (s, _), f0 in zip(insts, first):
+        for k in ics.FIELDS:
+            state[k][f0:f0 + len(s["x"])] = s[k]
+    ctx = B.Context(n, max_instances=8)
+    ctx.batch_set(counts, [p for _, p in insts], first=first)
+    arr = B.alloc_arrays(state, ninst=len(insts))
+    before = {k: host(arr[k]).copy() for k in FIELDS_OUT}
+    ctx.batch_step(arr, nsteps=2)
+    assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
+    inside = np.zeros(n, bool)
+    for k, ((s, p), f0) in enumerate(zip(insts, first)):
+        alone = run_alone(B, s, p, nsteps=2)
+        sl = slice(f0, f0 + len(s["x"]))
+        inside[sl] = True
+        for f in FIELDS_OUT:
+            assert np.array_equal(host(arr[f])[sl].view(np.uint8), host(alone[f]).view(np.uint8)), (k, f)
+    for f in FIELDS_OUT:
+        assert np.array_equal(host(arr[f])[~inside], before[f][~inside]), f
+    with pytest.raises(B.SphError):  # overlapping instances
+        ctx.batch_set(counts, [p for _, p in insts], first=[0, 100, 200, 300, 400])
+
+
 def test_batch_step_replays_from_a_cuda_graph(B):
     insts = instances(0)
     counts = [len(s["x"]) for s, _ in insts]

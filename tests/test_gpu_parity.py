@@ -165,6 +165,23 @@ def test_three_steps_drift_is_small(B, orc):
     assert flips <= len(s["x"]) // 100
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_split_run_equals_one_run(B, precision):
+    # the internal order is a function of the positions only (keys are sorted
+    # in caller order), so 2 + 3 steps in two calls give the bits of 5 steps
+    s, prm = _case("patch_ragged_av")
+    prm = ics.SphParams(**{**prm.as_dict(), "precision": precision})
+    ctx = B.Context(len(s["x"]))
+    one = B.alloc_arrays(s)
+    ctx.step(prm, one, nsteps=5)
+    two = B.alloc_arrays(s)
+    ctx.step(prm, two, nsteps=2)
+    ctx.step(prm, two, nsteps=3)
+    ctx.sync()
+    for k in one:
+        assert np.array_equal(host(one[k]).view(np.uint8), host(two[k]).view(np.uint8)), k
+
+
 def test_deterministic(B):
     s, prm = _case("patch_ragged_av")
     outs = []
