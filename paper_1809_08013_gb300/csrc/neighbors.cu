@@ -347,18 +347,16 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3)
-k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos,
-          const int2* __restrict__ cells,
-          int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ gslab,
-          double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
-          int32_t* __restrict__ wl, unsigned* __restrict__ status) {
-    __shared__ float4 s_f[kThreads / 32][32];
-    __shared__ int s_i[kThreads / 32][32];
-    const int warp = threadIdx.x >> 5;
+// The 32 particles i0 .. i0 + 31 (one per lane; all of one instance).
+__device__ __forceinline__ void union_group(
+    int64_t i0, int64_t n, const Batch& B, double4_32a* posh, const float4* __restrict__ fpos,
+    const int2* __restrict__ cells, int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
+    int32_t* __restrict__ gslab, double* __restrict__ hs_lo, double* __restrict__ hs_hi,
+    int32_t* __restrict__ hs_it, int32_t* __restrict__ wl, unsigned* __restrict__ status,
+    float4* st, int* sidx) {
     const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);  // one per block
+    const int64_t i = i0 + lane;
+    const int inst = slot_inst(B, i0);
     const Grid* __restrict__ g = B.grid + inst;
     const KParams& kp = B.kp[inst];
     cells += g->cbase;
@@ -379,8 +377,7 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
     int32_t* slab = gslab + (valid ? i : 0) * kGSlab;
     const bool per = g->periodic_z != 0;
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-    float4* st = s_f[warp];
-    int* sidx = s_i[warp];
+    const unsigned lt = (1u << lane) - 1u;
     for (int pass = 0;; ++pass) {  // pass is warp-uniform; it (per lane) stops at convergence
         const unsigned am = __ballot_sync(kFull, active);
         if (!am) break;
@@ -413,6 +410,12 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
         double R2 = -1.0;
         int c = 0, fill = 0;  // fill: staged candidates (warp-uniform)
         const float Rq2 = Rq * Rq;
+        // Query box of the warp: a candidate within 2h_i (FP64) of an active lane i
+        // lies inside it. The slop (>= 1e-3 cell widths + 1.2e-7 X) covers the FP32
+        // rounding of both coordinates and of the periodic shift.
+        const float bx0 = lx - g->slop[0], bx1 = hx + g->slop[0];
+        const float by0 = ly - g->slop[1], by1 = hy + g->slop[1];
+        const float bz0 = lzz - g->slop[2], bz1 = hzz + g->slop[2];
         for (int kz = z0; kz <= z1; ++kz) {
             const int cz = per ? wrapi(kz, nz) : kz;
             const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
@@ -425,27 +428,42 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
                     const float gx = axis_gap(fi.x, kx, g, 0);
                     if (!__any_sync(kFull, active && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < Rq2))
                         continue;
-                    // append the cell's particles to the staging buffer; run full chunks
-                    for (int s0 = se.x; s0 < se.y;) {
-                        const int take = min(32 - fill, se.y - s0);
-                        if (lane < take) {
-                            float4 f = __ldg(&fpos[s0 + lane]);
+                    // append the cell's particles that lie in the warp's query box to
+                    // the staging buffer (ballot-compacted, so the order of the kept
+                    // candidates is unchanged); run full chunks
+                    for (int s0 = se.x; s0 < se.y; s0 += 32) {
+                        const int j = s0 + lane;
+                        bool ok = j < se.y;
+                        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (ok) {
+                            f = __ldg(&fpos[j]);
                             if (per) {
                                 const float d = f.z - zc;
                                 if (d > g->halflzf) f.z -= g->lzf;
                                 else if (d < -g->halflzf) f.z += g->lzf;
                             }
-                            st[fill + lane] = f;
-                            sidx[fill + lane] = s0 + lane;
+                            ok = f.x >= bx0 && f.x <= bx1 && f.y >= by0 && f.y <= by1 &&
+                                 f.z >= bz0 && f.z <= bz1;
                         }
-                        fill += take;
-                        s0 += take;
-                        if (fill == 32) {
-                            __syncwarp();
-                            union_chunk(st, sidx, fi, t, active, i, pi, R, R2, posh, g, slab, c);
-                            __syncwarp();
-                            fill = 0;
+                        const unsigned m = __ballot_sync(kFull, ok);
+                        if (!m) continue;
+                        const int r = __popc(m & lt), cnt = __popc(m), room = 32 - fill;
+                        if (ok && r < room) {
+                            st[fill + r] = f;
+                            sidx[fill + r] = j;
                         }
+                        if (cnt < room) {
+                            fill += cnt;
+                            continue;
+                        }
+                        __syncwarp();
+                        union_chunk(st, sidx, fi, t, active, i, pi, R, R2, posh, g, slab, c);
+                        __syncwarp();
+                        if (ok && r >= room) {
+                            st[r - room] = f;
+                            sidx[r - room] = j;
+                        }
+                        fill = cnt - room;
                     }
                 }
             }
@@ -491,6 +509,31 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
     if (!conv) {
         atomicOr(&status[0], (unsigned)ST_HNOCONV);
         atomicAdd(&status[1], 1u);
+    }
+}
+
+// Persistent: warps take groups of 32 particles from a counter, so a group
+// whose particles straddle far-apart cells (a jump of the Morton curve: a
+// large query box, many candidates) delays one warp, not a whole wave.
+__global__ void __launch_bounds__(kThreads, 3)
+k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos,
+          const int2* __restrict__ cells,
+          int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ gslab,
+          double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
+          int32_t* __restrict__ wl, unsigned* __restrict__ status,
+          unsigned long long* __restrict__ wctr) {
+    __shared__ float4 s_f[kThreads / 32][32];
+    __shared__ int s_i[kThreads / 32][32];
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long ngroups = (n + 31) / 32;
+    for (;;) {
+        long long gi = 0;
+        if (lane == 0) gi = (long long)atomicAdd(wctr, 1ull);
+        gi = __shfl_sync(kFull, gi, 0);
+        if (gi >= ngroups) break;
+        union_group(gi * 32, n, B, posh, fpos, cells, nnb, ngather, gslab, hs_lo, hs_hi, hs_it,
+                    wl, status, s_f[warp], s_i[warp]);
     }
 }
 
@@ -829,8 +872,10 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
     double4_32a* posh = c->posh[c->cur];
     const Batch B = batch_of(c);
     c->launches += 4;
-    k_h_union<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb, c->ngather,
-                                      c->gslab, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->status);
+    const int64_t nbu = std::min<int64_t>((int64_t)c->nsm * 3, ((n + 31) / 32 + 7) / 8);
+    k_h_union<<<(unsigned)nbu, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb,
+                                                 c->ngather, c->gslab, c->hs_lo, c->hs_hi,
+                                                 c->hs_it, c->wl, c->status, c->wctr);
     k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(B, posh, c->fpos, c->cells, c->nnb,
                                                        c->ngather, c->gslab, c->hs_lo, c->hs_hi,
                                                        c->hs_it, c->wl, c->status);

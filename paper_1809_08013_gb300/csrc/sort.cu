@@ -159,7 +159,7 @@ constexpr int kGridThreads = 1024;
 
 __global__ void __launch_bounds__(kGridThreads)
 k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
-             unsigned* __restrict__ status) {
+             unsigned* __restrict__ status, unsigned long long* __restrict__ wctr) {
     const int inst = blockIdx.x;
     const int64_t n = B.icnt[inst];
     const int64_t b0 = B.ioff[inst] / kSlotAlign;
@@ -202,6 +202,7 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     if (inst == 0) {
         status[2] = 0u;
         status[3] = 0u;
+        wctr[0] = 0ull;
     }
     const double hmean = n > 0 ? r[7] / (double)n : 1.0;
     double w = 2.0 * hmean * kp.cell_scale;
@@ -440,7 +441,7 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
         c->launches += 1;
         k_bbox<<<nb, kThreads, 0, s>>>(n, B, c->posh[c->cur], c->red_part);
     }
-    k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status);
+    k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status, c->wctr);
     if (n == 0) return;
     const int64_t nt = c->ntot;
     if (nt == 0) return;

@@ -101,7 +101,7 @@ void free_all(sph_ctx* c) {
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->gslab, c->oslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
-                    c->tune_dt, c->roff};
+                    c->tune_dt, c->roff, c->wctr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -179,7 +179,8 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->roff, (size_t)max_instances + 1) &&
          al(&c->gslab, N * kGSlab) && al(&c->oslab, N * kOSlab) && al(&c->ocnt, N) &&
          al(&c->hs_lo, N) && al(&c->hs_hi, N) && al(&c->hs_it, N) && al(&c->wl, N) &&
-         al(&c->scratch_scalar, 2) && al(&c->tune_dt, 2 * (size_t)max_instances);
+         al(&c->scratch_scalar, 2) && al(&c->tune_dt, 2 * (size_t)max_instances) &&
+         al(&c->wctr, 4);
     return ok;
 }
 
@@ -372,6 +373,11 @@ sph_status sph_ctx_create_batch(sph_ctx** out, int64_t ncap, int64_t nnzcap, int
     c->maxinst = max_instances;
     c->ninst = 1;
     c->cellcap = cell_capacity(ncap, max_instances);
+    if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        c->nsm < 1) {
+        cudaGetLastError();
+        c->nsm = 1;
+    }
     Allocator A{false, 0};
     bool ok = allocate_all(c, nslots, A);
     ok = ok && cudaMallocHost((void**)&c->status_host, 2 * sizeof(unsigned)) == cudaSuccess;

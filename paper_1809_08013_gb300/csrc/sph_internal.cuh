@@ -164,6 +164,8 @@ struct sph_ctx {
     double* red_part;       // bbox partials: kReduceBlocks x 8
     double* dt_part;        // per force block (kMaxPairThreads per kThreads slots)
     sph::Grid* grid;        // per instance
+    unsigned long long* wctr;  // work counters of persistent kernels (zeroed per build)
+    int nsm;                // streaming multiprocessors of the device
     unsigned* status;       // [0] bits, [1] non-converged count, [2] internal flags,
                             // [3] h-search worklist length
     unsigned* status_host;  // pinned mirror
