@@ -42,13 +42,16 @@ FLOPS_PAIR_BASE = 51
 FLOPS_PAIR_AV = 17
 
 # DRAM traffic of one force-kernel launch from an ncu capture (dram__bytes_read.sum
-# + dram__bytes_write.sum), scaled to a launch here by the number of pairs it
-# processes (profiles/k_forces_df_patch343k.md for FP64). It is reported only
-# while the kernel sources hash to the version that was captured.
+# + dram__bytes_write.sum) on the 70^3 patch, scaled to a launch here by the
+# number of pairs it processes (profiles/kernels_patch343k.md). It is reported
+# only while the kernel's sources hash to the version that was captured.
 FORCES_TRAFFIC = {
-    "fp64": {"sources": ("physics_df.cu", "df.cuh", "sph_internal.cuh"),
-             "sha1": "c1ceb5aa5b5fff5a222bc19cbd251d88a64787e7",
-             "bytes": 197.3e6 + 14.21e6, "pairs": 34642666},
+    "fp64": {"sources": ("physics_df.cu", "df.cuh"),
+             "sha1": "45eeffb5431deeba81e3a611a40e3cfb2a8b7ec3",
+             "bytes": 198.2e6 + 15.35e6, "pairs": 34640886},
+    "mixed": {"sources": ("physics_mixed.cu", "df.cuh"),
+              "sha1": "1334895800e47d7cb2de5410ae7d774efbefc2ab",
+              "bytes": 185.7e6 + 11.08e6, "pairs": 34640886},
 }
 
 

@@ -107,36 +107,80 @@ void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, 
 }
 
 // ------------------------------------------------------------ bbox and grid
-// One partial per block of kSlotAlign slots (one instance): min x, y, z,
-// -max x, y, z, -max h, sum h over its particles, reduced in a fixed order.
-__global__ void __launch_bounds__(kThreads)
-k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh, double* __restrict__ part) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double v[8] = {CUDART_INF, CUDART_INF, CUDART_INF, CUDART_INF,
-                   CUDART_INF, CUDART_INF, CUDART_INF, 0.0};
-    if (k < n && slot_real(B, slot_inst(B, k), k)) {
-        const double4_32a p = posh[k];
-        v[0] = p.x; v[1] = p.y; v[2] = p.z;
-        v[3] = -p.x; v[4] = -p.y; v[5] = -p.z;
-        v[6] = -p.w;
-        v[7] = p.w;
-    }
+// Min / max of doubles as signed 64-bit integer min / max of order-preserving
+// keys (GB300's FP64 pipe is narrow; integer compares are not on it).
+__device__ __forceinline__ long long okey(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double okey_inv(long long k) {
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+
+constexpr long long kKeyMax = 0x7fffffffffffffffLL, kKeyMin = -kKeyMax - 1;
+
+// Bounding-box partials: min x, y, z and max x, y, z, h (as keys) and the
+// sum of h over the particles of each group of kSlotAlign slots (one
+// instance), one warp per group, reduced in a fixed order.
+struct BoxPart {
+    long long mn[3], mx[4];
+    double hs;
+};
+
+__device__ __forceinline__ void box_init(BoxPart& b) {
+    for (int d = 0; d < 3; ++d) b.mn[d] = kKeyMax;
+    for (int d = 0; d < 4; ++d) b.mx[d] = kKeyMin;
+    b.hs = 0.0;
+}
+
+__device__ __forceinline__ void box_warp_reduce(BoxPart& b) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int q = 0; q < 7; ++q) v[q] = fmin(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
-        v[7] += __shfl_xor_sync(0xffffffffu, v[7], o);
+        for (int d = 0; d < 3; ++d) {
+            const long long v = __shfl_xor_sync(0xffffffffu, b.mn[d], o);
+            b.mn[d] = v < b.mn[d] ? v : b.mn[d];
+        }
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const long long v = __shfl_xor_sync(0xffffffffu, b.mx[d], o);
+            b.mx[d] = v > b.mx[d] ? v : b.mx[d];
+        }
+        b.hs += __shfl_xor_sync(0xffffffffu, b.hs, o);
     }
-    __shared__ double sh[kThreads / 32][8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int q = 0; q < 8; ++q) sh[warp][q] = v[q];
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        const int q = threadIdx.x;
-        double r = sh[0][q];
-        for (int w = 1; w < kThreads / 32; ++w) r = (q == 7) ? r + sh[w][q] : fmin(r, sh[w][q]);
-        part[blockIdx.x * 8 + q] = r;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh, double* __restrict__ part) {
+    const int lane = threadIdx.x & 31;
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (grp * kSlotAlign >= n) return;  // warp-uniform
+    const int inst = slot_inst(B, grp * kSlotAlign);
+    const int64_t end = __ldg(&B.ioff[inst]) + __ldg(&B.icnt[inst]);
+    BoxPart b;
+    box_init(b);
+#pragma unroll
+    for (int q = 0; q < kSlotAlign / 32; ++q) {
+        const int64_t k = grp * kSlotAlign + q * 32 + lane;
+        if (k < end) {
+            const double4_32a p = posh[k];
+            const long long kx = okey(p.x), ky = okey(p.y), kz = okey(p.z), kh = okey(p.w);
+            b.mn[0] = kx < b.mn[0] ? kx : b.mn[0];
+            b.mn[1] = ky < b.mn[1] ? ky : b.mn[1];
+            b.mn[2] = kz < b.mn[2] ? kz : b.mn[2];
+            b.mx[0] = kx > b.mx[0] ? kx : b.mx[0];
+            b.mx[1] = ky > b.mx[1] ? ky : b.mx[1];
+            b.mx[2] = kz > b.mx[2] ? kz : b.mx[2];
+            b.mx[3] = kh > b.mx[3] ? kh : b.mx[3];
+            b.hs += p.w;
+        }
+    }
+    box_warp_reduce(b);
+    if (lane == 0) {
+        double* o = part + grp * 8;
+        for (int d = 0; d < 3; ++d) o[d] = __longlong_as_double(b.mn[d]);
+        for (int d = 0; d < 4; ++d) o[3 + d] = __longlong_as_double(b.mx[d]);
+        o[7] = b.hs;
     }
 }
 
@@ -164,30 +208,40 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     const int64_t n = B.icnt[inst];
     const int64_t b0 = B.ioff[inst] / kSlotAlign;
     const int64_t nbk = (n + kSlotAlign - 1) / kSlotAlign;
-    double v[8] = {CUDART_INF, CUDART_INF, CUDART_INF, CUDART_INF,
-                   CUDART_INF, CUDART_INF, CUDART_INF, 0.0};
+    BoxPart v;
+    box_init(v);
     for (int64_t b = threadIdx.x; b < nbk; b += blockDim.x) {
-#pragma unroll
-        for (int q = 0; q < 7; ++q) v[q] = fmin(v[q], part[(b0 + b) * 8 + q]);
-        v[7] += part[(b0 + b) * 8 + 7];
+        const double* o = part + (b0 + b) * 8;
+        for (int d = 0; d < 3; ++d) {
+            const long long k = __double_as_longlong(o[d]);
+            v.mn[d] = k < v.mn[d] ? k : v.mn[d];
+        }
+        for (int d = 0; d < 4; ++d) {
+            const long long k = __double_as_longlong(o[3 + d]);
+            v.mx[d] = k > v.mx[d] ? k : v.mx[d];
+        }
+        v.hs += o[7];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int q = 0; q < 7; ++q) v[q] = fmin(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
-        v[7] += __shfl_xor_sync(0xffffffffu, v[7], o);
-    }
-    __shared__ double sh[kGridThreads / 32][8];
+    box_warp_reduce(v);
+    __shared__ BoxPart sh[kGridThreads / 32];
     __shared__ double r[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int q = 0; q < 8; ++q) sh[warp][q] = v[q];
+    if (lane == 0) sh[warp] = v;
     __syncthreads();
-    if (threadIdx.x < 8) {
-        const int q = threadIdx.x;
-        double a = sh[0][q];
-        for (int w = 1; w < kGridThreads / 32; ++w) a = (q == 7) ? a + sh[w][q] : fmin(a, sh[w][q]);
-        r[q] = a;
+    if (threadIdx.x == 0) {
+        BoxPart a = sh[0];
+        for (int w = 1; w < kGridThreads / 32; ++w) {
+            for (int d = 0; d < 3; ++d) a.mn[d] = sh[w].mn[d] < a.mn[d] ? sh[w].mn[d] : a.mn[d];
+            for (int d = 0; d < 4; ++d) a.mx[d] = sh[w].mx[d] > a.mx[d] ? sh[w].mx[d] : a.mx[d];
+            a.hs += sh[w].hs;
+        }
+        // the layout the grid derivation below reads: min x, y, z, -max x, y, z, -max h, sum h
+        for (int d = 0; d < 3; ++d) {
+            r[d] = okey_inv(a.mn[d]);
+            r[3 + d] = -okey_inv(a.mx[d]);
+        }
+        r[6] = -okey_inv(a.mx[3]);
+        r[7] = a.hs;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -274,10 +328,14 @@ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
     return v;
 }
 
-__device__ __forceinline__ int cell_coord(double v, double lo, double inv, int n) {
-    double f = floor((v - lo) * inv);
-    if (!(f >= 0.0)) return 0;  // also catches NaN
-    if (f > (double)(n - 1)) return n - 1;
+// Cell index along one axis, in FP32 from the truncated float of v (integer
+// operations, no FP64 pipe). The neighbour search widens every query box by
+// the grid's slop (>= 1e-3 cell widths), far more than these roundings, so
+// any particle within reach of a query lies in a cell the query visits.
+__device__ __forceinline__ int cell_coord(double v, float lo, float inv, int n) {
+    const float f = floorf((dfl::from_double(v).hi - lo) * inv);
+    if (!(f >= 0.0f)) return 0;  // also catches NaN
+    if (f > (float)(n - 1)) return n - 1;
     return (int)f;
 }
 
@@ -294,9 +352,9 @@ k_keys(int64_t n, Batch B, const int64_t* __restrict__ coff, const int64_t* __re
     if (!slot_real(B, inst, k)) return;
     const Grid* g = B.grid + inst;
     const double4_32a p = posh[k];
-    const int kx = cell_coord(p.x, g->lo[0], g->inv_w[0], g->n[0]);
-    const int ky = cell_coord(p.y, g->lo[1], g->inv_w[1], g->n[1]);
-    const int kz = cell_coord(p.z, g->lo[2], g->inv_w[2], g->n[2]);
+    const int kx = cell_coord(p.x, g->lof[0], g->invwf[0], g->n[0]);
+    const int ky = cell_coord(p.y, g->lof[1], g->invwf[1], g->n[1]);
+    const int kz = cell_coord(p.z, g->lof[2], g->invwf[2], g->n[2]);
     const uint32_t code = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
     const int64_t q = __ldg(&roff[inst]) + ((int64_t)order[k] - __ldg(&coff[inst]));
     keys[q] = ((uint32_t)inst << 24) | code;
@@ -437,9 +495,11 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const Batch B = batch_of(c);
     c->launches += 1;
-    if (nb > 0) {
+    if (nb > 0) {  // one warp per group of kSlotAlign slots
         c->launches += 1;
-        k_bbox<<<nb, kThreads, 0, s>>>(n, B, c->posh[c->cur], c->red_part);
+        const int64_t groups = (n + kSlotAlign - 1) / kSlotAlign;
+        k_bbox<<<(unsigned)((groups * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+            n, B, c->posh[c->cur], c->red_part);
     }
     k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status, c->wctr);
     if (n == 0) return;
