@@ -309,15 +309,22 @@ __device__ __forceinline__ void particle_pass(const Grid* __restrict__ g,
 // still searching the warp keeps going; the stragglers are then handed, with
 // their bisection state, to the per-particle kernel below through a worklist.
 
+// Cell index of a (float) coordinate along axis d, clamped to the grid; only
+// used to cluster the lanes of a warp, so FP32 rounding is harmless.
+__device__ __forceinline__ int lane_cell(float v, const Grid* __restrict__ g, int d) {
+    const float lo = (d == 2 && g->periodic_z) ? -g->halflzf : g->lof[d];
+    const int k = (int)floorf((v - lo) * g->invwf[d]);
+    return min(max(k, 0), g->n[d] - 1);
+}
+
 // Test the 32 staged candidates of a warp against every lane's particle and
 // fold the outcome into that lane's count and gather slab. Candidates are
 // (float x, y, z) already moved to the lane's periodic image; sidx holds
 // their particle indices. Padding slots sit far away.
 __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const int* __restrict__ sidx,
                                             const float4& fi, const Thr& t, bool active, int64_t i,
-                                            const double4_32a& pi, double R, double& R2,
-                                            const double4_32a* posh, const Grid* __restrict__ g,
-                                            int32_t* slab, int& c) {
+                                            double h, double& R2, const double4_32a* posh,
+                                            const Grid* __restrict__ g, int32_t* slab, int& c) {
     unsigned in = 0u, bd = 0u;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
@@ -329,13 +336,16 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
     }
     if (!active) return;
     bd &= ~in;
-    while (bd) {  // the ~1e-5-wide border band: exact FP64 test
+    while (bd) {  // the ~1e-5-wide border band: exact FP64 test (rare: reloads p_i)
         const int k = __ffs(bd) - 1;
         bd &= bd - 1u;
         const int j = sidx[k];
         if (j == i) continue;
-        if (R2 < 0.0) R2 = __dmul_rn(R, R);
-        if (exact_r2(pi, posh[j], g) < R2) in |= 1u << k;
+        if (R2 < 0.0) {
+            const double R = 2.0 * h;
+            R2 = __dmul_rn(R, R);
+        }
+        if (exact_r2(posh[i], posh[j], g) < R2) in |= 1u << k;
     }
     while (in) {
         const int k = __ffs(in) - 1;
@@ -362,13 +372,12 @@ __device__ __forceinline__ void union_group(
     cells += g->cbase;
     const bool inb = i < n;
     const bool valid = inb && slot_real(B, inst, i);
-    double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
     float4 fi = make_float4(0.f, 0.f, 0.f, 0.f);
+    double h = 1.0, lo = 0.0, hi = CUDART_INF;
     if (valid) {
-        pi = posh[i];
+        h = posh[i].w;
         fi = fpos[i];
     }
-    double h = pi.w, lo = 0.0, hi = CUDART_INF;
     const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
     const int max_it = kp.max_h_iter;
     const int defer = kp.defer_lanes;
@@ -384,12 +393,9 @@ __device__ __forceinline__ void union_group(
         const double R = 2.0 * h;
         const Thr t = thresholds(R, g);
         const float Rq = reach_f32(h);
-        const float lx = wmin(active ? fi.x - Rq : CUDART_INF_F), hx = wmax(active ? fi.x + Rq : -CUDART_INF_F);
-        const float ly = wmin(active ? fi.y - Rq : CUDART_INF_F), hy = wmax(active ? fi.y + Rq : -CUDART_INF_F);
         const float lzz = wmin(active ? fi.z - Rq : CUDART_INF_F), hzz = wmax(active ? fi.z + Rq : -CUDART_INF_F);
-        // Periodic z: candidates are moved to the image nearest the warp's reference
+        // Periodic z: candidates are moved to the image nearest a reference lane's
         // z, which is each lane's minimum image while the warp spans < lz/4.
-        const float zc = __shfl_sync(kFull, fi.z, __ffs(am) - 1);
         const bool wide = per && (hzz - lzz > 0.25f * g->lzf);
         if ((pass > 0 && __popc(am) <= defer) || wide) {
             if (active) {
@@ -403,79 +409,101 @@ __device__ __forceinline__ void union_group(
             }
             break;
         }
-        int x0, x1, y0, y1, z0, z1;
-        box_range(lx, hx, g, 0, x0, x1);
-        box_range(ly, hy, g, 1, y0, y1);
-        box_range(lzz, hzz, g, 2, z0, z1);
+        // The active lanes are served in clusters: the first remaining lane and
+        // every remaining lane whose cell is within one cell of it. A warp whose
+        // particles straddle a jump of the Morton curve thus searches two
+        // compact boxes instead of one box spanning both places.
+        const int mcx = lane_cell(fi.x, g, 0), mcy = lane_cell(fi.y, g, 1);
+        const int mcz = lane_cell(fi.z, g, 2);
         double R2 = -1.0;
-        int c = 0, fill = 0;  // fill: staged candidates (warp-uniform)
-        const float Rq2 = Rq * Rq;
-        // Query box of the warp: a candidate within 2h_i (FP64) of an active lane i
-        // lies inside it. The slop (>= 1e-3 cell widths + 1.2e-7 X) covers the FP32
-        // rounding of both coordinates and of the periodic shift.
-        const float bx0 = lx - g->slop[0], bx1 = hx + g->slop[0];
-        const float by0 = ly - g->slop[1], by1 = hy + g->slop[1];
-        const float bz0 = lzz - g->slop[2], bz1 = hzz + g->slop[2];
-        for (int kz = z0; kz <= z1; ++kz) {
-            const int cz = per ? wrapi(kz, nz) : kz;
-            const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
-            for (int ky = y0; ky <= y1; ++ky) {
-                const long long row = ((long long)cz * ny + ky) * nx;
-                const float gy = axis_gap(fi.y, ky, g, 1);
-                for (int kx = x0; kx <= x1; ++kx) {
-                    const int2 se = __ldg(&cells[row + kx]);
-                    if (se.y <= se.x) continue;
-                    const float gx = axis_gap(fi.x, kx, g, 0);
-                    if (!__any_sync(kFull, active && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < Rq2))
-                        continue;
-                    // append the cell's particles that lie in the warp's query box to
-                    // the staging buffer (ballot-compacted, so the order of the kept
-                    // candidates is unchanged); run full chunks
-                    for (int s0 = se.x; s0 < se.y; s0 += 32) {
-                        const int j = s0 + lane;
-                        bool ok = j < se.y;
-                        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (ok) {
-                            f = __ldg(&fpos[j]);
-                            if (per) {
-                                const float d = f.z - zc;
-                                if (d > g->halflzf) f.z -= g->lzf;
-                                else if (d < -g->halflzf) f.z += g->lzf;
-                            }
-                            ok = f.x >= bx0 && f.x <= bx1 && f.y >= by0 && f.y <= by1 &&
-                                 f.z >= bz0 && f.z <= bz1;
-                        }
-                        const unsigned m = __ballot_sync(kFull, ok);
-                        if (!m) continue;
-                        const int r = __popc(m & lt), cnt = __popc(m), room = 32 - fill;
-                        if (ok && r < room) {
-                            st[fill + r] = f;
-                            sidx[fill + r] = j;
-                        }
-                        if (cnt < room) {
-                            fill += cnt;
+        int c = 0;
+        unsigned todo = am;
+        while (todo) {
+            const int a = __ffs(todo) - 1;
+            const int ax = __shfl_sync(kFull, mcx, a), ay = __shfl_sync(kFull, mcy, a);
+            const int az = __shfl_sync(kFull, mcz, a);
+            int dzc = abs(mcz - az);
+            if (per) dzc = min(dzc, nz - dzc);
+            const bool mine = ((todo >> lane) & 1u) && abs(mcx - ax) <= 1 && abs(mcy - ay) <= 1 &&
+                              dzc <= 1;
+            todo &= ~__ballot_sync(kFull, mine);
+            const float sx0 = wmin(mine ? fi.x - Rq : CUDART_INF_F), sx1 = wmax(mine ? fi.x + Rq : -CUDART_INF_F);
+            const float sy0 = wmin(mine ? fi.y - Rq : CUDART_INF_F), sy1 = wmax(mine ? fi.y + Rq : -CUDART_INF_F);
+            const float sz0 = wmin(mine ? fi.z - Rq : CUDART_INF_F), sz1 = wmax(mine ? fi.z + Rq : -CUDART_INF_F);
+            const float zc = __shfl_sync(kFull, fi.z, a);
+            int x0, x1, y0, y1, z0, z1;
+            box_range(sx0, sx1, g, 0, x0, x1);
+            box_range(sy0, sy1, g, 1, y0, y1);
+            box_range(sz0, sz1, g, 2, z0, z1);
+            int fill = 0;  // staged candidates (warp-uniform)
+            const float Rq2 = Rq * Rq;
+            // Query box of the cluster: a candidate within 2h_i (FP64) of one of its
+            // lanes lies inside it. The slop (>= 1e-3 cell widths + 1.2e-7 X)
+            // covers the FP32 rounding of both coordinates and of the periodic shift.
+            const float bx0 = sx0 - g->slop[0], bx1 = sx1 + g->slop[0];
+            const float by0 = sy0 - g->slop[1], by1 = sy1 + g->slop[1];
+            const float bz0 = sz0 - g->slop[2], bz1 = sz1 + g->slop[2];
+            for (int kz = z0; kz <= z1; ++kz) {
+                const int cz = per ? wrapi(kz, nz) : kz;
+                const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
+                for (int ky = y0; ky <= y1; ++ky) {
+                    const long long row = ((long long)cz * ny + ky) * nx;
+                    const float gy = axis_gap(fi.y, ky, g, 1);
+                    for (int kx = x0; kx <= x1; ++kx) {
+                        const int2 se = __ldg(&cells[row + kx]);
+                        if (se.y <= se.x) continue;
+                        const float gx = axis_gap(fi.x, kx, g, 0);
+                        if (!__any_sync(kFull, mine && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < Rq2))
                             continue;
+                        // append the cell's particles that lie in the query box to the
+                        // staging buffer (ballot-compacted, so the order of the kept
+                        // candidates is unchanged); run full chunks
+                        for (int s0 = se.x; s0 < se.y; s0 += 32) {
+                            const int j = s0 + lane;
+                            bool ok = j < se.y;
+                            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (ok) {
+                                f = __ldg(&fpos[j]);
+                                if (per) {
+                                    const float d = f.z - zc;
+                                    if (d > g->halflzf) f.z -= g->lzf;
+                                    else if (d < -g->halflzf) f.z += g->lzf;
+                                }
+                                ok = f.x >= bx0 && f.x <= bx1 && f.y >= by0 && f.y <= by1 &&
+                                     f.z >= bz0 && f.z <= bz1;
+                            }
+                            const unsigned m = __ballot_sync(kFull, ok);
+                            if (!m) continue;
+                            const int r = __popc(m & lt), cnt = __popc(m), room = 32 - fill;
+                            if (ok && r < room) {
+                                st[fill + r] = f;
+                                sidx[fill + r] = j;
+                            }
+                            if (cnt < room) {
+                                fill += cnt;
+                                continue;
+                            }
+                            __syncwarp();
+                            union_chunk(st, sidx, fi, t, mine, i, h, R2, posh, g, slab, c);
+                            __syncwarp();
+                            if (ok && r >= room) {
+                                st[r - room] = f;
+                                sidx[r - room] = j;
+                            }
+                            fill = cnt - room;
                         }
-                        __syncwarp();
-                        union_chunk(st, sidx, fi, t, active, i, pi, R, R2, posh, g, slab, c);
-                        __syncwarp();
-                        if (ok && r >= room) {
-                            st[r - room] = f;
-                            sidx[r - room] = j;
-                        }
-                        fill = cnt - room;
                     }
                 }
             }
-        }
-        if (fill > 0) {  // last partial chunk: pad with far-away slots
-            if (lane >= fill) {
-                st[lane] = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
-                sidx[lane] = -1;
+            if (fill > 0) {  // last partial chunk: pad with far-away slots
+                if (lane >= fill) {
+                    st[lane] = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
+                    sidx[lane] = -1;
+                }
+                __syncwarp();
+                union_chunk(st, sidx, fi, t, mine, i, h, R2, posh, g, slab, c);
+                __syncwarp();
             }
-            __syncwarp();
-            union_chunk(st, sidx, fi, t, active, i, pi, R, R2, posh, g, slab, c);
-            __syncwarp();
         }
         if (active) {
             cnt = c;
@@ -515,7 +543,9 @@ __device__ __forceinline__ void union_group(
 // Persistent: warps take groups of 32 particles from a counter, so a group
 // whose particles straddle far-apart cells (a jump of the Morton curve: a
 // large query box, many candidates) delays one warp, not a whole wave.
-__global__ void __launch_bounds__(kThreads, 3)
+constexpr int kUnionBlocksPerSM = 2;
+
+__global__ void __launch_bounds__(kThreads, kUnionBlocksPerSM)
 k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos,
           const int2* __restrict__ cells,
           int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ gslab,
@@ -872,7 +902,7 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
     double4_32a* posh = c->posh[c->cur];
     const Batch B = batch_of(c);
     c->launches += 4;
-    const int64_t nbu = std::min<int64_t>((int64_t)c->nsm * 3, ((n + 31) / 32 + 7) / 8);
+    const int64_t nbu = std::min<int64_t>((int64_t)c->nsm * kUnionBlocksPerSM, ((n + 31) / 32 + 7) / 8);
     k_h_union<<<(unsigned)nbu, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb,
                                                  c->ngather, c->gslab, c->hs_lo, c->hs_hi,
                                                  c->hs_it, c->wl, c->status, c->wctr);
