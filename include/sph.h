@@ -123,7 +123,11 @@ typedef struct {
 /* Create a context on CUDA device `device` for up to n_capacity particles and
  * nnz_capacity neighbour-list entries (about 1.1 x 105 per particle for the
  * 100-neighbour workloads). Allocates all scratch once; later calls allocate
- * nothing. On failure *out is NULL. */
+ * nothing. On failure *out is NULL. The steps keep each particle's row of
+ * S_i in a fixed slab of 224 entries (at most 128 of them the gather set);
+ * the nnz_capacity-entry CSR is written for sph_build_neighbors and
+ * sph_neighbors_to_host, and by a step only when some row does not fit its
+ * slab (then SPH_E_CAPACITY if the CSR does not fit either). */
 sph_status sph_ctx_create(sph_ctx **out, int64_t n_capacity, int64_t nnz_capacity, int device);
 
 /* Largest number of instances of one batch (the instance id takes the top 8
@@ -259,7 +263,7 @@ sph_status sph_neighbors_to_host(sph_ctx *ctx, int64_t *offsets, int32_t *idx,
 enum {
     SPH_PHASE_CELLS = 0,    /* load, bounding box, Morton keys, radix sort, permute, cell ranges */
     SPH_PHASE_HSEARCH = 1,  /* h search, FP32 thresholds, per-cell max h */
-    SPH_PHASE_CSR = 2,      /* neighbour-list count, scan, fill */
+    SPH_PHASE_CSR = 2,      /* rows of S_i: outer sets, sorted; lengths */
     SPH_PHASE_DENSITY = 3,  /* density with the equation of state fused */
     SPH_PHASE_FORCES = 4,   /* momentum, energy, viscosity, dt partials and dt */
     SPH_PHASE_UPDATE = 5,   /* kick-drift update and the final write-back */

@@ -90,14 +90,7 @@ __device__ __forceinline__ float f_r2(const float4& a, const float4& b, const Gr
 // The defining FP64 squared distance, operation by operation.
 __device__ __forceinline__ double exact_r2(const double4_32a& a, const double4_32a& b,
                                            const Grid* __restrict__ g) {
-    const double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y);
-    double dz = __dsub_rn(a.z, b.z);
-    if (g->periodic_z) {
-        const double half = __dmul_rn(0.5, g->lz);
-        if (dz > half) dz = __dsub_rn(dz, g->lz);
-        else if (dz < -half) dz = __dadd_rn(dz, g->lz);
-    }
-    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return exact_r2_def(a, b, g->periodic_z != 0, g->lz);
 }
 
 __device__ __forceinline__ int wrapi(int k, int n) {
@@ -361,7 +354,7 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
 __device__ __forceinline__ void union_group(
     int64_t i0, int64_t n, const Batch& B, double4_32a* posh, const float4* __restrict__ fpos,
     const int2* __restrict__ cells, int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
-    int32_t* __restrict__ gslab, double* __restrict__ hs_lo, double* __restrict__ hs_hi,
+    int32_t* __restrict__ rslab, double* __restrict__ hs_lo, double* __restrict__ hs_hi,
     int32_t* __restrict__ hs_it, int32_t* __restrict__ wl, unsigned* __restrict__ status,
     float4* st, int* sidx) {
     const int lane = threadIdx.x & 31;
@@ -383,7 +376,7 @@ __device__ __forceinline__ void union_group(
     const int defer = kp.defer_lanes;
     int cnt = 0, it = 0;
     bool active = valid && max_it > 0, conv = false, deferred = false;
-    int32_t* slab = gslab + (valid ? i : 0) * kGSlab;
+    int32_t* slab = rslab + (valid ? i : 0) * kRSlab;
     const bool per = g->periodic_z != 0;
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
     const unsigned lt = (1u << lane) - 1u;
@@ -548,7 +541,7 @@ constexpr int kUnionBlocksPerSM = 2;
 __global__ void __launch_bounds__(kThreads, kUnionBlocksPerSM)
 k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos,
           const int2* __restrict__ cells,
-          int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ gslab,
+          int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ rslab,
           double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
           int32_t* __restrict__ wl, unsigned* __restrict__ status,
           unsigned long long* __restrict__ wctr) {
@@ -562,7 +555,7 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
         if (lane == 0) gi = (long long)atomicAdd(wctr, 1ull);
         gi = __shfl_sync(kFull, gi, 0);
         if (gi >= ngroups) break;
-        union_group(gi * 32, n, B, posh, fpos, cells, nnb, ngather, gslab, hs_lo, hs_hi, hs_it,
+        union_group(gi * 32, n, B, posh, fpos, cells, nnb, ngather, rslab, hs_lo, hs_hi, hs_it,
                     wl, status, s_f[warp], s_i[warp]);
     }
 }
@@ -573,7 +566,7 @@ __global__ void __launch_bounds__(kThreads)
 k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
             const int2* __restrict__ cells,
             int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
-            int32_t* __restrict__ gslab, const double* __restrict__ hs_lo,
+            int32_t* __restrict__ rslab, const double* __restrict__ hs_lo,
             const double* __restrict__ hs_hi, const int32_t* __restrict__ hs_it,
             const int32_t* __restrict__ wl, unsigned* __restrict__ status) {
     __shared__ int s_start[kThreads / 32][32], s_pref[kThreads / 32][32];
@@ -595,7 +588,7 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
         double h = pi.w, lo = hs_lo[i], hi = hs_hi[i];
         int cnt = 0;
         bool conv = false;
-        int32_t* slab = gslab + i * kGSlab;
+        int32_t* slab = rslab + i * kRSlab;
         for (int it = hs_it[i]; it < max_it; ++it) {
             const double R = 2.0 * h;
             const Thr t = thresholds(R, g);
@@ -698,17 +691,18 @@ k_cell_hmax(Batch B, Grid* gw, const int2* __restrict__ cells,
 }
 
 // ------------------------------------------------------------ CSR
-// Slab path (normal case). The h search left N_i in the gather slab. The
-// rest of S_i is the transpose of the non-mutual gather pairs:
-// S_j \ N_j = { i : j in N_i and i not in N_j }. k_outer scans the gather
-// slabs, appends such i to j's outer slab (atomic slot, so unordered),
-// k_rowlen forms |S_i|, and k_compose writes each CSR row: the gather slab,
-// then the outer slab sorted by index (deterministic rows).
+// Slab path (normal case). The h search left N_i at the start of row i of the
+// row slab. The rest of S_i is the transpose of the non-mutual gather pairs:
+// S_j \ N_j = { i : j in N_i and i not in N_j }: k_outer scans the gather
+// sets and appends such i after N_j (atomic slot, so unordered),
+// k_rowlen_sort sorts each outer part by index (deterministic rows) and forms
+// |S_i|; k_compose copies the rows into a CSR when a caller asks for the
+// neighbour list.
 __global__ void __launch_bounds__(kThreads)
 k_outer(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const float4* __restrict__ fpos, const float* __restrict__ tin,
-        const int32_t* __restrict__ ngather, const int32_t* __restrict__ gslab,
-        int32_t* __restrict__ ocnt, int32_t* __restrict__ oslab, unsigned* __restrict__ status) {
+        const int32_t* __restrict__ ngather, int32_t* __restrict__ rslab,
+        int32_t* __restrict__ ocnt, unsigned* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n || (status[2] & IF_SLAB_OVF)) return;
@@ -723,7 +717,7 @@ k_outer(int64_t n, Batch B, const double4_32a* __restrict__ posh,
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
         const int s = k * 32 + lane;
-        jj[k] = s < ng ? __ldg(&gslab[i * kGSlab + s]) : -1;
+        jj[k] = s < ng ? rslab[i * kRSlab + s] : -1;
     }
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
@@ -741,60 +735,53 @@ k_outer(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const double Rj = 2.0 * pj.w;
             in_j = exact_r2(posh[i], pj, g) < __dmul_rn(Rj, Rj);
         }
-        if (!in_j) {
-            const int q = atomicAdd(&ocnt[j], 1);
-            if (q < kOSlab) oslab[(int64_t)j * kOSlab + q] = (int32_t)i;
+        if (!in_j) {  // i joins the outer part of row j, after j's gather set
+            const int q = __ldg(&ngather[j]) + atomicAdd(&ocnt[j], 1);
+            if (q < kRSlab) rslab[(int64_t)j * kRSlab + q] = (int32_t)i;
             else atomicOr(&status[2], (unsigned)IF_SLAB_OVF);
         }
     }
 }
 
+// Row lengths, and the outer part of each row (appended in atomic order)
+// sorted by index in place, one thread per row (rows hold a few outer
+// entries): the rows, and every sum over them, become deterministic.
 __global__ void __launch_bounds__(kThreads)
-k_rowlen(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __restrict__ ocnt,
-         int32_t* __restrict__ rowlen, const unsigned* __restrict__ status) {
+k_rowlen_sort(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __restrict__ ocnt,
+              int32_t* __restrict__ rowlen, int32_t* __restrict__ rslab,
+              const unsigned* __restrict__ status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || (status[2] & IF_SLAB_OVF)) return;
-    rowlen[i] = ngather[i] + ocnt[i];
+    const int ng = ngather[i], no = ocnt[i];
+    rowlen[i] = ng + no;
+    int32_t* row = rslab + i * kRSlab + ng;
+    for (int a = 1; a < no; ++a) {  // insertion sort
+        const int32_t v = row[a];
+        int b = a - 1;
+        while (b >= 0 && row[b] > v) {
+            row[b + 1] = row[b];
+            --b;
+        }
+        row[b + 1] = v;
+    }
 }
 
+// The rows as a CSR (for callers of the neighbour list): a copy of each row.
 __global__ void __launch_bounds__(kThreads)
-k_compose(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __restrict__ gslab,
-          const int32_t* __restrict__ ocnt, const int32_t* __restrict__ oslab,
+k_compose(int64_t n, const int32_t* __restrict__ rowlen, const int32_t* __restrict__ rslab,
           const int64_t* __restrict__ offsets, int32_t* __restrict__ idx, int64_t nnzcap,
           unsigned* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (status[2] & IF_SLAB_OVF) return;
+    if (status[2] & IF_SLAB_OVF) return;  // the fallback wrote the CSR
     if (offsets[n] > nnzcap) {
         if (i == 0 && lane == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
         return;
     }
     if (i >= n) return;
     const int64_t off = offsets[i];
-    const int ng = ngather[i], no = ocnt[i];
-    for (int s = lane; s < ng; s += 32) idx[off + s] = __ldg(&gslab[i * kGSlab + s]);
-    // outer part sorted by index: rank of each entry among the row's entries
-    constexpr int kPer = kOSlab / 32;
-    int v[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int s = k * 32 + lane;
-        v[k] = s < no ? __ldg(&oslab[i * kOSlab + s]) : 0x7fffffff;
-    }
-    int rank[kPer] = {};
-    for (int t = 0; t < no; ++t) {  // no is warp-uniform; rows hold a few outer entries
-        int w = __shfl_sync(kFull, v[0], t & 31);
-#pragma unroll
-        for (int k2 = 1; k2 < kPer; ++k2) {
-            const int w2 = __shfl_sync(kFull, v[k2], t & 31);
-            w = (t >> 5) == k2 ? w2 : w;
-        }
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) rank[k] += w < v[k];
-    }
-#pragma unroll
-    for (int k = 0; k < kPer; ++k)
-        if (k * 32 + lane < no) idx[off + ng + rank[k]] = v[k];
+    const int len = rowlen[i];
+    for (int s = lane; s < len; s += 32) idx[off + s] = __ldg(&rslab[i * kRSlab + s]);
 }
 
 // Fallback (a row overflowed a slab): the full two-pass build below.
@@ -904,10 +891,10 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
     c->launches += 4;
     const int64_t nbu = std::min<int64_t>((int64_t)c->nsm * kUnionBlocksPerSM, ((n + 31) / 32 + 7) / 8);
     k_h_union<<<(unsigned)nbu, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb,
-                                                 c->ngather, c->gslab, c->hs_lo, c->hs_hi,
+                                                 c->ngather, c->rslab, c->hs_lo, c->hs_hi,
                                                  c->hs_it, c->wl, c->status, c->wctr);
     k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(B, posh, c->fpos, c->cells, c->nnb,
-                                                       c->ngather, c->gslab, c->hs_lo, c->hs_hi,
+                                                       c->ngather, c->rslab, c->hs_lo, c->hs_hi,
                                                        c->hs_it, c->wl, c->status);
     k_finalize_h<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ocnt);
     const unsigned gx = (unsigned)std::max(2, kReduceBlocks / c->ninst);
@@ -917,6 +904,7 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
 
 void launch_csr(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
+    c->csr_ready = false;
     if (n == 0) {
         c->launches += 1;
         cudaMemsetAsync(c->offsets, 0, sizeof(int64_t), s);
@@ -926,19 +914,28 @@ void launch_csr(sph_ctx* c, cudaStream_t s) {
     const unsigned nbw = (unsigned)((n * 32 + kThreads - 1) / kThreads);
     double4_32a* posh = c->posh[c->cur];
     const Batch B = batch_of(c);
-    c->launches += 8;
-    k_outer<<<nbw, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ngather, c->gslab, c->ocnt,
-                                     c->oslab, c->status);
-    k_rowlen<<<nb, kThreads, 0, s>>>(n, c->ngather, c->ocnt, c->rowlen, c->status);
+    c->launches += 6;
+    k_outer<<<nbw, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ngather, c->rslab, c->ocnt,
+                                     c->status);
+    k_rowlen_sort<<<nb, kThreads, 0, s>>>(n, c->ngather, c->ocnt, c->rowlen, c->rslab, c->status);
+    // fallback (a row did not fit its slab): the full two-pass build into the CSR
     k_csr<false><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->cells,
                                                         c->cell_hmax, c->rowlen, c->ngather,
                                                         nullptr, nullptr, c->nnzcap, c->status);
     launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s);
-    k_compose<<<nbw, kThreads, 0, s>>>(n, c->ngather, c->gslab, c->ocnt, c->oslab, c->offsets,
-                                       c->idx, c->nnzcap, c->status);
     k_csr<true><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->cells,
                                                        c->cell_hmax, c->rowlen, c->ngather,
                                                        c->offsets, c->idx, c->nnzcap, c->status);
+}
+
+void launch_compose(sph_ctx* c, cudaStream_t s) {
+    const int64_t n = c->n;
+    c->csr_ready = true;
+    if (n == 0) return;
+    const unsigned nbw = (unsigned)((n * 32 + kThreads - 1) / kThreads);
+    c->launches += 1;
+    k_compose<<<nbw, kThreads, 0, s>>>(n, c->rowlen, c->rslab, c->offsets, c->idx, c->nnzcap,
+                                       c->status);
 }
 
 }  // namespace sph

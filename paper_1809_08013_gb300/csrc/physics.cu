@@ -98,12 +98,13 @@ template <bool FUSE>
 __global__ void __launch_bounds__(kThreads)
 k_density(int64_t n, Batch B, const double4_32a* __restrict__ posh,
           const double4_32a* __restrict__ velm, const double* __restrict__ ue,
-          const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
-          const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
+          Rows R, double4_32a* __restrict__ therm,
           double2* __restrict__ kern, double* __restrict__ pint, double* __restrict__ cint) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
-    if (i >= n || !slot_real(B, inst, i) || offsets[n] > nnzcap) return;
+    const int32_t* ent = nullptr;
+    int len = 0;
+    if (i >= n || !slot_real(B, inst, i) || !row_of(R, n, i, true, ent, len)) return;
     const KParams& kp = B.kp[inst];
     const double4_32a pi = posh[i];
     const double hinv = 1.0 / pi.w;
@@ -111,9 +112,8 @@ k_density(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     const bool per = kp.periodic_z != 0;
     const double lz = kp.lz;
     double acc = 0.0;
-    const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
-    for (int64_t e = e0; e < e1; ++e) {
-        const int j = __ldg(&idx[e]);
+    for (int e = 0; e < len; ++e) {
+        const int j = __ldg(&ent[e]);
         const double4_32a pj = posh[j];
         const double mj = velm[j].w;
         const double dx = pi.x - pj.x, dy = pi.y - pj.y;
@@ -157,11 +157,11 @@ void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
     c->launches += 1;
     if (fuse_eos)
         k_density<true><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->ue[b],
-                                                c->offsets, c->ngather, c->idx, c->nnzcap,
+                                                rows_of(c),
                                                 c->therm, c->kern, c->pint, c->cint);
     else
         k_density<false><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->ue[b],
-                                                 c->offsets, c->ngather, c->idx, c->nnzcap,
+                                                 rows_of(c),
                                                  c->therm, c->kern, c->pint, c->cint);
 }
 
@@ -198,12 +198,14 @@ __global__ void __launch_bounds__(kThreads)
 k_forces(int64_t n, Batch B, const double4_32a* __restrict__ posh,
          const double4_32a* __restrict__ velm, const double4_32a* __restrict__ therm,
          const double2* __restrict__ kern, const double* __restrict__ cint,
-         const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
+         Rows R,
          double4_32a* __restrict__ acc, double* __restrict__ mumax, double* __restrict__ dt_part) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
     double dtc = CUDART_INF;
-    if (i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap) {
+    const int32_t* ent = nullptr;
+    int len = 0;
+    if (i < n && slot_real(B, inst, i) && row_of(R, n, i, false, ent, len)) {
         const KParams& kp = B.kp[inst];
         const double4_32a pi = posh[i];
         const double4_32a vi = velm[i];
@@ -215,9 +217,8 @@ k_forces(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const double eta2 = kp.eta2, beta = kp.beta;
         double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0, sv = 0.0;
         long long mum = 0;  // bits of max |mu| (non-negative doubles order as integers)
-        const int64_t e0 = offsets[i], e1 = offsets[i + 1];
-        for (int64_t e = e0; e < e1; ++e) {
-            const int j = __ldg(&idx[e]);
+        for (int e = 0; e < len; ++e) {
+            const int j = __ldg(&ent[e]);
             const double4_32a pj = posh[j];
             const double4_32a vj = velm[j];
             const double4_32a tj = therm[j];
@@ -312,7 +313,7 @@ void launch_forces(sph_ctx* c, double* dt_out, double* time_inout, cudaStream_t 
     else if (n > 0) {
         c->launches += 1;
         k_forces<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->therm, c->kern,
-                                         c->cint, c->offsets, c->idx, c->nnzcap, c->acc,
+                                         c->cint, rows_of(c), c->acc,
                                          c->mumax, c->dt_part);
     }
     k_dt_finish<<<c->ninst, kThreads, 0, s>>>(c->dt_part, B,

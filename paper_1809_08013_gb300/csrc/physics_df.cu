@@ -50,7 +50,8 @@ __device__ __forceinline__ df dw_shape(df q) {
     return q.hi < 1.0f ? fin : (q.hi < 2.0f ? fout : zero);
 }
 
-__device__ __forceinline__ df ld2(const float2* p, int64_t k) {
+// the mass as a double-float
+__device__ __forceinline__ df ldm(const float2* p, int64_t k) {
     const float2 v = __ldg(&p[k]);
     return {v.x, v.y};
 }
@@ -77,14 +78,15 @@ template <bool FUSE, int T>
 __global__ void __launch_bounds__(kThreads)
 k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const float2* __restrict__ mdf, const double* __restrict__ ue,
-             const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
-             const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
+             Rows R, double4_32a* __restrict__ therm,
              double2* __restrict__ kern, float4* __restrict__ dpk, double* __restrict__ pint,
              double* __restrict__ cint) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
     const int sub = (int)(threadIdx.x % T);
     const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
-    const bool act = i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap;
+    const int32_t* ent = nullptr;
+    int len = 0;
+    const bool act = i < n && slot_real(B, inst, i) && row_of(R, n, i, true, ent, len);
     if (T == 1 && !act) return;
     const KParams& kp = B.kp[inst];
     double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
@@ -96,11 +98,11 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     const long long half_bits = bitsd(0.5 * kp.lz);
     const bool per = kp.periodic_z != 0;
     const double lz = kp.lz;
-    if (sub == 0) acc = ld2(mdf, i);  // self term m_i W(0, h_i): shape 1
-    const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
-    for (int64_t e = e0 + sub; e < e1; e += T) {
-        const int j = __ldg(&idx[e]);
+    if (sub == 0) acc = ldm(mdf, i);  // self term m_i W(0, h_i): shape 1
+    for (int e = sub; e < len; e += T) {
+        const int j = __ldg(&ent[e]);
         const double4_32a pj = posh[j];
+        const df mj = ldm(mdf, j);
         double dz = pi.z - pj.z;
         if (per) dz = wrap_z_d(dz, half_bits, lz);
         const df X = dfl::from_double(pi.x - pj.x), Y = dfl::from_double(pi.y - pj.y);
@@ -111,7 +113,7 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const df q = dfl::mul(dfl::mul(r2, dfl::rsqrt(r2)), Hi);
             w = w_shape(q);
         }
-        acc = dfl::add(acc, dfl::mul(ld2(mdf, j), w));
+        acc = dfl::add(acc, dfl::mul(mj, w));
     }
     }
     if (T > 1) {
@@ -142,7 +144,7 @@ static void density_df_t(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
     k_density_df<FUSE, T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->mdf, c->ue[b],
-                                                  c->offsets, c->ngather, c->idx, c->nnzcap,
+                                                  rows_of(c),
                                                   c->therm, c->kern, c->dpk, c->pint, c->cint);
 }
 
@@ -172,13 +174,15 @@ __global__ void __launch_bounds__(kThreads, 3)
 k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
             const float2* __restrict__ mdf, const double* __restrict__ cint,
-            const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
+            Rows R,
             double4_32a* __restrict__ acc, double* __restrict__ mumax,
             double* __restrict__ dt_part) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
     const int sub = (int)(threadIdx.x % T);
     const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
-    const bool act = i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap;
+    const int32_t* ent = nullptr;
+    int len = 0;
+    const bool act = i < n && slot_real(B, inst, i) && row_of(R, n, i, false, ent, len);
     double dtc = CUDART_INF;
     df sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sp = {0.f, 0.f}, sv = {0.f, 0.f};
     df mumx = {0.f, 0.f};
@@ -195,9 +199,8 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const df c_half_pi = dfl::from_double_fp64(0.5 * kInvPiD);
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
-        const int64_t e0 = offsets[i], e1 = offsets[i + 1];
-        for (int64_t e = e0 + sub; e < e1; e += T) {
-            const int j = __ldg(&idx[e]);
+        for (int e = sub; e < len; e += T) {
+            const int j = __ldg(&ent[e]);
             const double4_32a pj = posh[j];
             const double4_32a vj = velm[j];
             const float4 b0 = __ldg(&dpk[3 * j]), b1 = __ldg(&dpk[3 * j + 1]);
@@ -229,7 +232,7 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
                 Pi = dfl::mul(dfl::mul(mu, t), dfl::mul(d1, R));
                 if (-mu.hi > mumx.hi) mumx = dfl::neg(mu);
             }
-            const df mF = dfl::mul(ld2(mdf, j), Fb);
+            const df mF = dfl::mul(ldm(mdf, j), Fb);
             const df g = dfl::mul(mF, dfl::add(dfl::add(Ai, df{b1.x, b1.y}), Pi));
             sx = dfl::add(sx, dfl::mul(g, X));
             sy = dfl::add(sy, dfl::mul(g, Y));
@@ -281,7 +284,7 @@ static void forces_df_t(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
     k_forces_df<T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->velm[b], c->dpk,
-                                           c->mdf, c->cint, c->offsets, c->idx, c->nnzcap,
+                                           c->mdf, c->cint, rows_of(c),
                                            c->acc, c->mumax, c->dt_part);
 }
 

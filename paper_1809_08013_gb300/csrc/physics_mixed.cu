@@ -162,13 +162,14 @@ template <bool FUSE, int T>
 __global__ void __launch_bounds__(kThreads)
 k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const double* __restrict__ ue, float4* __restrict__ mpk,
-             const int64_t* __restrict__ offsets, const int32_t* __restrict__ ngather,
-             const int32_t* __restrict__ idx, int64_t nnzcap, double4_32a* __restrict__ therm,
+             Rows R, double4_32a* __restrict__ therm,
              double* __restrict__ pint, double* __restrict__ cint) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
     const int sub = (int)(threadIdx.x % T);
     const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
-    const bool act = i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap;
+    const int32_t* ent = nullptr;
+    int len = 0;
+    const bool act = i < n && slot_real(B, inst, i) && row_of(R, n, i, true, ent, len);
     if (T == 1 && !act) return;
     const KParams& kp = B.kp[inst];
     df acc = {0.0f, 0.0f};
@@ -177,9 +178,8 @@ k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     const float hinv = a1.w;
     const ZWrap zw = make_zwrap(kp);
     if (sub == 0) acc = df{a0.w, 0.0f};  // self term m_i W(0, h_i): shape 1
-    const int64_t e0 = offsets[i], e1 = e0 + ngather[i];
-    for (int64_t e = e0 + sub; e < e1; e += T) {
-        const int j = __ldg(&idx[e]);
+    for (int e = sub; e < len; e += T) {
+        const int j = __ldg(&ent[e]);
         const float4 b0 = __ldg(&mpk[5 * j]), b1 = __ldg(&mpk[5 * j + 1]);
         const float dx = rel(a0.x, a1.x, b0.x, b1.x), dy = rel(a0.y, a1.y, b0.y, b1.y);
         const float dz = rel_z(a0.z, a1.z, b0.z, b1.z, zw);
@@ -212,13 +212,15 @@ template <int T>
 __global__ void __launch_bounds__(kThreads)
 k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const float4* __restrict__ mpk, const double* __restrict__ cint,
-            const int64_t* __restrict__ offsets, const int32_t* __restrict__ idx, int64_t nnzcap,
+            Rows R,
             double4_32a* __restrict__ acc, double* __restrict__ mumax,
             double* __restrict__ dt_part) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
     const int sub = (int)(threadIdx.x % T);
     const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
-    const bool act = i < n && slot_real(B, inst, i) && offsets[n] <= nnzcap;
+    const int32_t* ent = nullptr;
+    int len = 0;
+    const bool act = i < n && slot_real(B, inst, i) && row_of(R, n, i, false, ent, len);
     double dtc = CUDART_INF;
     df sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sp = {0.f, 0.f}, sv = {0.f, 0.f};
     float mum = 0.0f;
@@ -229,9 +231,8 @@ k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const ZWrap zw = make_zwrap(kp);
         const float eta2 = (float)kp.eta2, beta = (float)kp.beta;
         const float cpi = 0.5f * kInvPiF;
-        const int64_t e0 = offsets[i], e1 = offsets[i + 1];
-        for (int64_t e = e0 + sub; e < e1; e += T) {
-            const int j = __ldg(&idx[e]);
+        for (int e = sub; e < len; e += T) {
+            const int j = __ldg(&ent[e]);
             const float4 b0 = __ldg(&mpk[5 * j]), b1 = __ldg(&mpk[5 * j + 1]);
             const float4 b2 = __ldg(&mpk[5 * j + 2]), b3 = __ldg(&mpk[5 * j + 3]);
             const float4 b4 = __ldg(&mpk[5 * j + 4]);
@@ -315,7 +316,7 @@ static void density_mx_t(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
     k_density_mx<FUSE, T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->ue[b], c->mpk,
-                                                  c->offsets, c->ngather, c->idx, c->nnzcap,
+                                                  rows_of(c),
                                                   c->therm, c->pint, c->cint);
 }
 
@@ -342,7 +343,7 @@ static void forces_mx_t(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
     k_forces_mx<T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->mpk, c->cint,
-                                           c->offsets, c->idx, c->nnzcap, c->acc, c->mumax,
+                                           rows_of(c), c->acc, c->mumax,
                                            c->dt_part);
 }
 

@@ -99,7 +99,7 @@ void free_all(sph_ctx* c) {
                     c->therm, c->kern, c->acc, c->pint, c->cint, c->dpk, c->mdf, c->mpk, c->mumax, c->fpos, c->tin, c->order[0],
                     c->order[1], c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist,
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
-                    c->offsets, c->row_part, c->idx, c->gslab, c->oslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
+                    c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
                     c->tune_dt, c->roff, c->wctr};
     for (void* p : ptrs)
@@ -177,7 +177,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->ioff, (size_t)max_instances + 1) && al(&c->icnt, (size_t)max_instances) &&
          al(&c->coff, (size_t)max_instances + 1) && al(&c->kpi, (size_t)max_instances) &&
          al(&c->roff, (size_t)max_instances + 1) &&
-         al(&c->gslab, N * kGSlab) && al(&c->oslab, N * kOSlab) && al(&c->ocnt, N) &&
+         al(&c->rslab, N * kRSlab) && al(&c->ocnt, N) &&
          al(&c->hs_lo, N) && al(&c->hs_hi, N) && al(&c->hs_it, N) && al(&c->wl, N) &&
          al(&c->scratch_scalar, 2) && al(&c->tune_dt, 2 * (size_t)max_instances) &&
          al(&c->wctr, 4);
@@ -423,6 +423,7 @@ sph_status sph_build_neighbors(sph_ctx* c, const sph_params* prm, sph_particles*
     launch_build_cells(c, s);
     launch_h_search(c, s);
     launch_csr(c, s);
+    launch_compose(c, s);
     launch_scatter(c, P, SC_H | SC_NNB, s);
     if ((st = check_launch(c, "sph_build_neighbors")) != SPH_OK) return st;
     if (out) {
@@ -643,6 +644,7 @@ sph_status sph_neighbors_to_host(sph_ctx* c, int64_t* offsets, int32_t* idx,
     DeviceGuard dg(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = c->n;
+    if (!c->csr_ready) launch_compose(c, s);  // rows of the last step are in slab form
     int64_t nnz = 0;
     cudaError_t e = cudaMemcpyAsync(&nnz, c->offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

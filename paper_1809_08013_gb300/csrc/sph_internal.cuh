@@ -40,7 +40,8 @@ enum : unsigned {
     IF_SLAB_OVF = 1u,   // a row did not fit the gather/outer slabs: full CSR kernels run
 };
 constexpr int kGSlab = 128;  // gather-set slots per particle (>= n_target + n_tol)
-constexpr int kOSlab = 96;   // outer-set slots per particle (patch max ~40, Evrard ~64)
+constexpr int kRSlab = 224;  // row slots per particle: gather set, then the outer set
+                             // (outer sets: patch max ~40, Evrard ~64)
 
 // Cell grid, computed on the device from the particle bounding box each build.
 struct Grid {
@@ -155,8 +156,10 @@ struct sph_ctx {
     int64_t* offsets;
     int64_t* row_part;      // scan partials of the row lengths
     int32_t* idx;
-    int32_t* gslab;         // kGSlab per particle: gather set of the last h-search count
-    int32_t* oslab;         // kOSlab per particle: outer set (r < 2 h_j only), unordered
+    int32_t* rslab;         // kRSlab per particle: row i of S_i = the gather set of the last
+                            // h-search count (ngather[i]), then the outer set (ocnt[i],
+                            // r < 2 h_j only, sorted); rowlen[i] = ngather[i] + ocnt[i]
+    bool csr_ready;         // offsets / idx hold the rows as a CSR
     int32_t* ocnt;          // outer-set sizes
     double *hs_lo, *hs_hi;  // bisection bracket of particles handed to the per-particle search
     int32_t* hs_it;         // counts already done for them
@@ -188,6 +191,50 @@ namespace sph {
 
 inline Batch batch_of(const sph_ctx* c) { return Batch{c->blk, c->ioff, c->icnt, c->grid, c->kpi}; }
 
+// Rows of S_i for the pair kernels: the row slab unless a row overflowed it
+// (device flag IF_SLAB_OVF), in which case the CSR built by the fallback.
+struct Rows {
+    const int32_t* rslab;
+    const int32_t* idx;
+    const int64_t* offsets;
+    const int32_t* rowlen;   // |S_i| (either form)
+    const int32_t* ngather;  // |N_i|: the first ngather[i] entries of a row
+    const unsigned* status;
+    int64_t nnzcap;
+};
+
+inline Rows rows_of(const sph_ctx* c) {
+    return Rows{c->rslab, c->idx, c->offsets, c->rowlen, c->ngather, c->status, c->nnzcap};
+}
+
+// The defining FP64 squared distance, operation by operation (minimum image
+// along z when periodic): (dx dx + dy dy) + dz dz, each operation rounded.
+__device__ __forceinline__ double exact_r2_def(const double4_32a& a, const double4_32a& b,
+                                               bool periodic_z, double lz) {
+    const double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y);
+    double dz = __dsub_rn(a.z, b.z);
+    if (periodic_z) {
+        const double half = __dmul_rn(0.5, lz);
+        if (dz > half) dz = __dsub_rn(dz, lz);
+        else if (dz < -half) dz = __dadd_rn(dz, lz);
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Entries and length of row i (the whole row, or its gather part); false when
+// the rows cannot be read (a fallback CSR over capacity).
+__device__ __forceinline__ bool row_of(const Rows& R, int64_t n, int64_t i, bool gather_only,
+                                       const int32_t*& ent, int& len) {
+    if (!(R.status[2] & IF_SLAB_OVF)) {
+        ent = R.rslab + i * kRSlab;
+    } else {
+        if (R.offsets[n] > R.nnzcap) return false;
+        ent = R.idx + R.offsets[i];
+    }
+    len = gather_only ? R.ngather[i] : R.rowlen[i];
+    return true;
+}
+
 // ---- sph_abi.cu
 // Describe a single problem of n particles (a batch of one) on the stream.
 void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s);
@@ -202,7 +249,10 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s);
 
 // ---- neighbors.cu
 void launch_h_search(sph_ctx* c, cudaStream_t s);
+// the rows of S_i (slab form; the full two-pass CSR build if a row overflows)
 void launch_csr(sph_ctx* c, cudaStream_t s);
+// the rows as a CSR in offsets / idx (a copy in slab form; nothing after a fallback)
+void launch_compose(sph_ctx* c, cudaStream_t s);
 
 // ---- physics.cu
 enum { GATHER_DENSITY = 1, GATHER_FORCES = 2 };

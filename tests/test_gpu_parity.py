@@ -277,10 +277,14 @@ def test_perfect_lattice_reports_non_convergence(B, orc):
 
 
 def test_capacity_overflow_is_reported_not_fatal(B):
+    # the step keeps its rows in per-particle slabs; the CSR of the neighbour
+    # list (nnz_capacity entries) is only needed when a caller asks for it
     s, prm = _case("patch27k")
     ctx = B.Context(len(s["x"]), nnz_capacity=1000)
     arr = B.alloc_arrays(s)
     ctx.step(prm, arr, nsteps=1)
+    assert ctx.sync() == B.SPH_OK
+    ctx.build_neighbors(prm, arr)
     assert ctx.sync() == B.SPH_E_CAPACITY
     # a context with room works afterwards on the same device
     ctx2 = B.Context(len(s["x"]))
@@ -318,6 +322,19 @@ def test_slab_overflow_uses_full_build(B, orc):
     assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
     ctx.density(prm, arr)
     assert normwise(host(arr["rho"]), o["rho"]) <= TOL_FP64
+    for k in ("rho", "p", "c"):
+        arr[k].copy_(torch.from_numpy(o[k]))
+    ctx.forces(prm, arr)  # the pair kernels read the fallback CSR
+    for k in ("ax", "ay", "az", "du"):
+        assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
+    # and a whole step through the fallback
+    arr2 = B.alloc_arrays(s)
+    ctx.step(prm, arr2, nsteps=1)
+    assert ctx.sync() == B.SPH_OK
+    for k in ("rho", "p"):
+        assert normwise(host(arr2[k]), o[k]) <= TOL_FP64, k
+    for k in ("ax", "ay", "az"):
+        assert scaled(host(arr2[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
 
 
 @pytest.mark.parametrize("cell_scale", [0.5, 0.75, 1.5])
