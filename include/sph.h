@@ -143,8 +143,9 @@ sph_status sph_ctx_create(sph_ctx **out, int64_t n_capacity, int64_t nnz_capacit
 sph_status sph_ctx_create_batch(sph_ctx **out, int64_t n_capacity, int64_t nnz_capacity,
                                 int32_t max_instances, int device);
 
-/* Device bytes a context of these capacities allocates (each allocation
- * rounded up to 256 bytes), without allocating; -1 for invalid sizes. Lets a
+/* Device bytes a context of these capacities allocates on the current device
+ * (each allocation rounded up to 256 bytes; a few buffers scale with the
+ * device's SM count), without allocating; -1 for invalid sizes. Lets a
  * caller fit contexts into a memory budget. */
 int64_t sph_ctx_bytes(int64_t n_capacity, int64_t nnz_capacity, int32_t max_instances);
 

@@ -314,10 +314,13 @@ __device__ __forceinline__ int lane_cell(float v, const Grid* __restrict__ g, in
 // fold the outcome into that lane's count and gather slab. Candidates are
 // (float x, y, z) already moved to the lane's periodic image; sidx holds
 // their particle indices. Padding slots sit far away.
+// rec: instead of counting, record (r^2 in FP32, j) of every candidate that
+// may lie within the thresholds' radius (r2 <= Tout) in recb (up to kRec).
 __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const int* __restrict__ sidx,
-                                            const float4& fi, const Thr& t, bool active, int64_t i,
-                                            double h, double& R2, const double4_32a* posh,
-                                            const Grid* __restrict__ g, int32_t* slab, int& c) {
+                                            const float4& fi, const Thr& t, bool active, bool rec,
+                                            int64_t i, double h, double& R2,
+                                            const double4_32a* posh, const Grid* __restrict__ g,
+                                            int32_t* slab, int& c, int2* recb, int& nrec) {
     unsigned in = 0u, bd = 0u;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
@@ -328,6 +331,20 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
         if (r2 <= t.tout) bd |= 1u << k;
     }
     if (!active) return;
+    if (rec) {
+        while (bd) {
+            const int k = __ffs(bd) - 1;
+            bd &= bd - 1u;
+            const int j = sidx[k];
+            if (j == i) continue;
+            const float4 q = st[k];
+            const float dx = fi.x - q.x, dy = fi.y - q.y, dz = fi.z - q.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (nrec < kRec) recb[nrec] = make_int2(__float_as_int(r2), j);
+            ++nrec;
+        }
+        return;
+    }
     bd &= ~in;
     while (bd) {  // the ~1e-5-wide border band: exact FP64 test (rare: reloads p_i)
         const int k = __ffs(bd) - 1;
@@ -350,13 +367,39 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
     }
 }
 
+// |N_i(hh)| from the records of a record pass made at a radius >= 2 hh, with
+// the same decisions as a counting pass (FP32 thresholds, exact FP64 test in
+// the band between them); with slab, N_i(hh) is also written, in the order of
+// the records, which is the order a counting pass would have found them in.
+__device__ int count_records(const int2* recb, int nrec, double hh, const Grid* __restrict__ g,
+                             const double4_32a* posh, int64_t i, int32_t* slab) {
+    const double R = 2.0 * hh;
+    const Thr t = thresholds(R, g);
+    double R2 = -1.0;
+    int c = 0;
+    for (int q = 0; q < nrec; ++q) {
+        const int2 e = recb[q];
+        const float r2 = __int_as_float(e.x);
+        bool in = r2 < t.tin;
+        if (!in && r2 <= t.tout) {
+            if (R2 < 0.0) R2 = __dmul_rn(R, R);
+            in = exact_r2(posh[i], posh[e.y], g) < R2;
+        }
+        if (in) {
+            if (slab && c < kGSlab) slab[c] = e.y;
+            ++c;
+        }
+    }
+    return c;
+}
+
 // The 32 particles i0 .. i0 + 31 (one per lane; all of one instance).
 __device__ __forceinline__ void union_group(
     int64_t i0, int64_t n, const Batch& B, double4_32a* posh, const float4* __restrict__ fpos,
     const int2* __restrict__ cells, int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
     int32_t* __restrict__ rslab, double* __restrict__ hs_lo, double* __restrict__ hs_hi,
     int32_t* __restrict__ hs_it, int32_t* __restrict__ wl, unsigned* __restrict__ status,
-    float4* st, int* sidx) {
+    float4* st, int* sidx, int2* recb) {
     const int lane = threadIdx.x & 31;
     const int64_t i = i0 + lane;
     const int inst = slot_inst(B, i0);
@@ -383,9 +426,14 @@ __device__ __forceinline__ void union_group(
     for (int pass = 0;; ++pass) {  // pass is warp-uniform; it (per lane) stops at convergence
         const unsigned am = __ballot_sync(kFull, active);
         if (!am) break;
-        const double R = 2.0 * h;
-        const Thr t = thresholds(R, g);
-        const float Rq = reach_f32(h);
+        // Pass 0 counts N_i(h). Later passes record every candidate within 2 hs,
+        // hs = the largest h the bisection can still test without growing (hi, or
+        // h while hi is unbounded), and resolve the following counts from the
+        // records: a search from a poor initial h takes ~2 passes, not ~8.
+        const bool rec = pass > 0;
+        const double hs = rec && !isinf(hi) ? hi : h;
+        const Thr t = thresholds(2.0 * hs, g);
+        const float Rq = reach_f32(hs);
         const float lzz = wmin(active ? fi.z - Rq : CUDART_INF_F), hzz = wmax(active ? fi.z + Rq : -CUDART_INF_F);
         // Periodic z: candidates are moved to the image nearest a reference lane's
         // z, which is each lane's minimum image while the warp spans < lz/4.
@@ -409,7 +457,7 @@ __device__ __forceinline__ void union_group(
         const int mcx = lane_cell(fi.x, g, 0), mcy = lane_cell(fi.y, g, 1);
         const int mcz = lane_cell(fi.z, g, 2);
         double R2 = -1.0;
-        int c = 0;
+        int c = 0, nrec = 0;
         unsigned todo = am;
         while (todo) {
             const int a = __ffs(todo) - 1;
@@ -477,7 +525,8 @@ __device__ __forceinline__ void union_group(
                                 continue;
                             }
                             __syncwarp();
-                            union_chunk(st, sidx, fi, t, mine, i, h, R2, posh, g, slab, c);
+                            union_chunk(st, sidx, fi, t, mine, rec, i, h, R2, posh, g, slab, c,
+                                        recb, nrec);
                             __syncwarp();
                             if (ok && r >= room) {
                                 st[r - room] = f;
@@ -494,11 +543,29 @@ __device__ __forceinline__ void union_group(
                     sidx[lane] = -1;
                 }
                 __syncwarp();
-                union_chunk(st, sidx, fi, t, mine, i, h, R2, posh, g, slab, c);
+                union_chunk(st, sidx, fi, t, mine, rec, i, h, R2, posh, g, slab, c, recb, nrec);
                 __syncwarp();
             }
         }
-        if (active) {
+        if (active && rec && nrec > kRec) {  // too many to record: one warp of its own
+            deferred = true;
+            active = false;
+            posh[i].w = h;
+            hs_lo[i] = lo;
+            hs_hi[i] = hi;
+            hs_it[i] = it;
+            wl[atomicAdd(&status[3], 1u)] = (int32_t)i;
+        }
+        // counts of this pass (or from its records) and the bisection updates
+        for (bool counted = !rec; active;) {
+            if (rec) {
+                if (h > hs) break;  // beyond the recorded radius: another pass
+                c = count_records(recb, nrec, h, g, posh, i, nullptr);
+            } else if (counted) {
+                counted = false;  // c holds this pass's count
+            } else {
+                break;
+            }
             cnt = c;
             ++it;
             if (cnt >= lowb && cnt <= highb) {
@@ -513,6 +580,8 @@ __device__ __forceinline__ void union_group(
                 hi = h;
                 h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
             }
+            if (!rec) break;
+            if (!active) count_records(recb, nrec, h, g, posh, i, slab);  // N_i(h) of the final h
         }
     }
     if (!valid) {
@@ -536,15 +605,13 @@ __device__ __forceinline__ void union_group(
 // Persistent: warps take groups of 32 particles from a counter, so a group
 // whose particles straddle far-apart cells (a jump of the Morton curve: a
 // large query box, many candidates) delays one warp, not a whole wave.
-constexpr int kUnionBlocksPerSM = 2;
-
 __global__ void __launch_bounds__(kThreads, kUnionBlocksPerSM)
 k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos,
           const int2* __restrict__ cells,
           int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ rslab,
           double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
           int32_t* __restrict__ wl, unsigned* __restrict__ status,
-          unsigned long long* __restrict__ wctr) {
+          unsigned long long* __restrict__ wctr, int2* __restrict__ recs) {
     __shared__ float4 s_f[kThreads / 32][32];
     __shared__ int s_i[kThreads / 32][32];
     const int warp = threadIdx.x >> 5;
@@ -556,7 +623,8 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
         gi = __shfl_sync(kFull, gi, 0);
         if (gi >= ngroups) break;
         union_group(gi * 32, n, B, posh, fpos, cells, nnb, ngather, rslab, hs_lo, hs_hi, hs_it,
-                    wl, status, s_f[warp], s_i[warp]);
+                    wl, status, s_f[warp], s_i[warp],
+                    recs + ((int64_t)(blockIdx.x * (kThreads / 32) + warp) * 32 + lane) * kRec);
     }
 }
 
@@ -892,7 +960,7 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
     const int64_t nbu = std::min<int64_t>((int64_t)c->nsm * kUnionBlocksPerSM, ((n + 31) / 32 + 7) / 8);
     k_h_union<<<(unsigned)nbu, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb,
                                                  c->ngather, c->rslab, c->hs_lo, c->hs_hi,
-                                                 c->hs_it, c->wl, c->status, c->wctr);
+                                                 c->hs_it, c->wl, c->status, c->wctr, c->recs);
     k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(B, posh, c->fpos, c->cells, c->nnb,
                                                        c->ngather, c->rslab, c->hs_lo, c->hs_hi,
                                                        c->hs_it, c->wl, c->status);

@@ -101,7 +101,7 @@ void free_all(sph_ctx* c) {
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
-                    c->tune_dt, c->roff, c->wctr};
+                    c->tune_dt, c->roff, c->wctr, c->recs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -180,7 +180,8 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->rslab, N * kRSlab) && al(&c->ocnt, N) &&
          al(&c->hs_lo, N) && al(&c->hs_hi, N) && al(&c->hs_it, N) && al(&c->wl, N) &&
          al(&c->scratch_scalar, 2) && al(&c->tune_dt, 2 * (size_t)max_instances) &&
-         al(&c->wctr, 4);
+         al(&c->wctr, 4) &&
+         al(&c->recs, (size_t)c->nsm * kUnionBlocksPerSM * kThreads * kRec);
     return ok;
 }
 
@@ -339,6 +340,13 @@ int64_t sph_ctx_bytes(int64_t ncap, int64_t nnzcap, int32_t max_instances) {
     c.nnzcap = nnzcap;
     c.maxinst = max_instances;
     c.cellcap = cell_capacity(ncap, max_instances);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        c.nsm < 1) {
+        cudaGetLastError();
+        c.nsm = 256;  // no device to ask: an upper bound for the per-SM scratch
+    }
     Allocator A{true, 0};
     allocate_all(&c, ncap + (int64_t)(kSlotAlign - 1) * (max_instances - 1), A);
     return (int64_t)A.bytes;

@@ -40,6 +40,8 @@ enum : unsigned {
     IF_SLAB_OVF = 1u,   // a row did not fit the gather/outer slabs: full CSR kernels run
 };
 constexpr int kGSlab = 128;  // gather-set slots per particle (>= n_target + n_tol)
+constexpr int kRec = 256;    // h search: candidates recorded per lane in flight
+constexpr int kUnionBlocksPerSM = 2;  // resident blocks of the persistent h search
 constexpr int kRSlab = 224;  // row slots per particle: gather set, then the outer set
                              // (outer sets: patch max ~40, Evrard ~64)
 
@@ -168,6 +170,7 @@ struct sph_ctx {
     double* dt_part;        // per force block (kMaxPairThreads per kThreads slots)
     sph::Grid* grid;        // per instance
     unsigned long long* wctr;  // work counters of persistent kernels (zeroed per build)
+    int2* recs;             // h search records: kRec per lane of the persistent grid
     int nsm;                // streaming multiprocessors of the device
     unsigned* status;       // [0] bits, [1] non-converged count, [2] internal flags,
                             // [3] h-search worklist length
