@@ -484,6 +484,18 @@ __device__ __forceinline__ void union_group(
             const float bx0 = sx0 - g->slop[0], bx1 = sx1 + g->slop[0];
             const float by0 = sy0 - g->slop[1], by1 = sy1 + g->slop[1];
             const float bz0 = sz0 - g->slop[2], bz1 = sz1 + g->slop[2];
+            // and in a ball around the cluster's centre o: |q - o| <= |q - p_i| + |p_i - o|
+            // <= Rq_i + |p_i - o| for a candidate q within reach of lane i
+            const float ox = 0.5f * (wmin(mine ? fi.x : CUDART_INF_F) + wmax(mine ? fi.x : -CUDART_INF_F));
+            const float oy = 0.5f * (wmin(mine ? fi.y : CUDART_INF_F) + wmax(mine ? fi.y : -CUDART_INF_F));
+            const float oz = 0.5f * (wmin(mine ? fi.z : CUDART_INF_F) + wmax(mine ? fi.z : -CUDART_INF_F));
+            float rb = 0.0f;
+            if (mine) {
+                const float ex = fi.x - ox, ey = fi.y - oy, ez = fi.z - oz;
+                rb = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex))) + Rq;
+            }
+            rb = wmax(rb) * 1.00001f + fmaxf(g->slop[0], fmaxf(g->slop[1], g->slop[2]));
+            const float rb2 = rb * rb;
             for (int kz = z0; kz <= z1; ++kz) {
                 const int cz = per ? wrapi(kz, nz) : kz;
                 const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
@@ -510,8 +522,10 @@ __device__ __forceinline__ void union_group(
                                     if (d > g->halflzf) f.z -= g->lzf;
                                     else if (d < -g->halflzf) f.z += g->lzf;
                                 }
+                                const float qx = f.x - ox, qy = f.y - oy, qz = f.z - oz;
                                 ok = f.x >= bx0 && f.x <= bx1 && f.y >= by0 && f.y <= by1 &&
-                                     f.z >= bz0 && f.z <= bz1;
+                                     f.z >= bz0 && f.z <= bz1 &&
+                                     fmaf(qz, qz, fmaf(qy, qy, qx * qx)) <= rb2;
                             }
                             const unsigned m = __ballot_sync(kFull, ok);
                             if (!m) continue;
