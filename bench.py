@@ -376,7 +376,7 @@ def _run_ensemble(args, B, dev, stream):
         "batched_equals_single_bitwise": bool(same),
         "autotune": {"chosen": tuned, "trials": tune["trials"],
                      "method": "sph_autotune: one coordinate-descent pass over pair_threads "
-                               "{1,2,4}, cell_scale {1,1.25,1.5}, defer_lanes {8,16}; 2 timed "
+                               "{1,2,4}, cell_scale {0.875,1,1.25}, defer_lanes {8,16}; 2 timed "
                                "steps per trial"},
     }
 

@@ -72,7 +72,7 @@ typedef struct {
                              sums round differently for each value */
     int32_t defer_lanes;  /* h search: a warp of 32 particles hands its particles still
                              searching to one warp each once at most this many remain
-                             (0 selects 8; at most 32). A tuning knob: h and the
+                             (0 selects 16; at most 32). A tuning knob: h and the
                              neighbour sets do not depend on it */
     double rho0, c0;     /* Tait: p = c0^2 rho0 / 7 ((rho/rho0)^7 - 1), c = c0 (rho/rho0)^3 */
     double gamma;        /* ideal gas: p = (gamma - 1) rho u, c = sqrt(gamma (gamma - 1) u) */
@@ -80,8 +80,9 @@ typedef struct {
     double eta2;         /* eta^2 in mu_ij = hb v.r / (r^2 + eta^2 hb^2), e.g. 0.01 */
     double cfl;          /* dt = cfl * min h / (c + 1.2 (alpha c + beta mumax)) */
     double lz;           /* period along z when periodic_z = 1 */
-    double cell_scale;   /* cell width = 2 <h> cell_scale (0 selects the default 1.25); a tuning
-                            knob of the neighbour search, results do not depend on it */
+    double cell_scale;   /* cell width = 2 <h> cell_scale (0 selects the default 1.0); a tuning
+                            knob of the neighbour search: h and the neighbour sets do not
+                            depend on it */
 } sph_params;
 
 /* Caller-owned particle arrays (device pointers, caller order, length n). */
@@ -241,8 +242,8 @@ typedef struct {
  * differently with pair_threads. P is not modified (dt and time of the
  * trials go to context scratch); the context keeps the chosen knobs for
  * sph_batch_step until the next sph_batch_set, and a single-problem call
- * takes them from its sph_params. space = NULL uses cell_scale {1, 1.25,
- * 1.5}, pair_threads {1, 2, 4}, defer_lanes {8, 16}. Synchronises the
+ * takes them from its sph_params. space = NULL uses cell_scale {0.875, 1,
+ * 1.25}, pair_threads {1, 2, 4}, defer_lanes {8, 16}. Synchronises the
  * stream (not capturable). SPH_E_INVAL for nsteps < 1, P->n too short for
  * the batch, invalid candidates or more than SPH_TUNE_MAX_TRIALS of them.
  * Device conditions of the trial runs (h non-convergence) stay in the

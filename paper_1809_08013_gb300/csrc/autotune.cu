@@ -70,7 +70,7 @@ extern "C" sph_status sph_autotune(sph_ctx* c, sph_particles* P, int nsteps,
     if (!c || !P || !out || nsteps < 1) return SPH_E_INVAL;
     if (P->n < c->cext) return SPH_E_INVAL;
     if (P->n > 0 && (!P->x || !P->y || !P->z || !P->h || !P->m)) return SPH_E_INVAL;
-    static const double kCs[] = {1.0, 1.25, 1.5};
+    static const double kCs[] = {0.875, 1.0, 1.25};
     static const int32_t kTpp[] = {1, 2, 4};
     static const int32_t kDefer[] = {8, 16};
     sph_tune_space d = {kCs, 3, kTpp, 3, kDefer, 2};
