@@ -70,7 +70,7 @@ def forces_traffic(kind, pairs):
     return ref["bytes"] * pairs / ref["pairs"]
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -99,7 +99,7 @@ def parse():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-quantum", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -107,6 +107,25 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: replicas run the same work, so the job ends
+    when the last one does (an all-reduce of one number, outside the timed
+    region; nothing of the SPH data is exchanged)."""
+    if world == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, n, steps, ms_max):
+    """Particle updates per second of the whole job: every rank advances its
+    own n-particle replica `steps` steps, all within ms_max milliseconds."""
+    return world * n * steps / (ms_max * 1e-3)
 
 
 PRECISION = {"fp64": 0, "mixed": 1}
@@ -525,12 +544,8 @@ def run_native(args):
     if status not in (B.SPH_OK, B.SPH_E_HNOCONV):
         raise RuntimeError(f"timed status {B.STATUS_NAMES.get(status)}: {ctx.error()}")
 
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * n * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(world, n, args.steps, ms_max)
 
     # step 0 alone from the initial conditions (the longest h search): the timed
     # run's first step is this same work, so the rest gives the steady state
@@ -572,13 +587,9 @@ def run_native(args):
             hdt.copy_(arr["dt"], non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize(dev)
-        ems = f0.elapsed_time(f1)
-        if world > 1:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(f0.elapsed_time(f1), world, dev)
         ctx.sync(stream)
-        e2e = {"value": world * n * args.steps / (ems * 1e-3), "unit": UNIT,
+        e2e = {"value": whole_job_rate(world, n, args.steps, ems), "unit": UNIT,
                "h2d_bytes_per_step": 8 * len(B.STATE_FIELDS) * n,
                "d2h_bytes_per_step": 8 * len(B.STATE_FIELDS) * n + 8}
 
