@@ -26,7 +26,8 @@ _CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared
 class OrcParams(C.Structure):
     _fields_ = [
         ("eos", C.c_int32), ("n_target", C.c_int32), ("n_tol", C.c_int32),
-        ("max_h_iter", C.c_int32), ("periodic_z", C.c_int32), ("pad_", C.c_int32),
+        ("max_h_iter", C.c_int32), ("periodic_z", C.c_int32), ("kernel", C.c_int32),
+        ("gradients", C.c_int32), ("sinc_n", C.c_int32),
         ("rho0", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
         ("alpha", C.c_double), ("beta", C.c_double), ("eta2", C.c_double),
         ("cfl", C.c_double), ("lz", C.c_double),
@@ -59,6 +60,15 @@ def lib():
         L.orc_W.argtypes = [C.c_double, C.c_double]
         L.orc_dWdr.restype = C.c_double
         L.orc_dWdr.argtypes = [C.c_double, C.c_double]
+        L.orc_sinc_norm.restype = C.c_double
+        L.orc_sinc_norm.argtypes = [C.c_int]
+        L.orc_kernel_W.restype = C.c_double
+        L.orc_kernel_W.argtypes = [_P, C.c_double, C.c_double]
+        L.orc_kernel_dWdr.restype = C.c_double
+        L.orc_kernel_dWdr.argtypes = [_P, C.c_double, C.c_double]
+        L.orc_iad.argtypes = [_P, C.c_int64] + [_D] * 6 + [_I64, _I32, _I32, _D]
+        L.orc_iad_gradient.argtypes = ([_P, C.c_int64] + [_D] * 6 + [_I64, _I32, _I32] +
+                                       [_D] * 5)
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_get_threads.restype = C.c_int
         L.orc_count_brute.restype = C.c_int64
@@ -71,8 +81,8 @@ def lib():
         L.orc_csr_fill.argtypes = [_P, C.c_int64, _D, _D, _D, _D, _I64, _I32, _I32, C.c_int]
         L.orc_density.argtypes = [_P, C.c_int64, _D, _D, _D, _D, _D, _I64, _I32, _I32, _D]
         L.orc_eos.argtypes = [_P, C.c_int64, _D, _D, _D, _D]
-        L.orc_forces.argtypes = [_P, C.c_int64] + [_D] * 11 + [_I64, _I32] + [_D] * 5
-        L.orc_forces_scale.argtypes = [_P, C.c_int64] + [_D] * 11 + [_I64, _I32] + [_D] * 3
+        L.orc_forces.argtypes = [_P, C.c_int64] + [_D] * 11 + [_I64, _I32] + [_D] * 6
+        L.orc_forces_scale.argtypes = [_P, C.c_int64] + [_D] * 11 + [_I64, _I32] + [_D] * 4
         L.orc_dt.restype = C.c_double
         L.orc_dt.argtypes = [_P, C.c_int64, _D, _D, _D]
         L.orc_leapfrog.argtypes = [_P, C.c_int64, C.c_double] + [_D] * 11
@@ -85,7 +95,9 @@ def lib():
 def params(p) -> OrcParams:
     """Marshal an object with the SphParams attributes into the oracle's struct."""
     return OrcParams(int(p.eos), int(p.n_target), int(p.n_tol), int(p.max_h_iter),
-                     int(p.periodic_z), 0, float(p.rho0), float(p.c0), float(p.gamma),
+                     int(p.periodic_z), int(getattr(p, "kernel", 0)),
+                     int(getattr(p, "gradients", 0)), int(getattr(p, "sinc_n", 5)),
+                     float(p.rho0), float(p.c0), float(p.gamma),
                      float(p.alpha), float(p.beta), float(p.eta2), float(p.cfl), float(p.lz))
 
 
@@ -112,6 +124,62 @@ def W(r: float, h: float) -> float:
 
 def dWdr(r: float, h: float) -> float:
     return lib().orc_dWdr(float(r), float(h))
+
+
+def sinc_norm(n: int) -> float:
+    """Normalisation B_n of the sinc kernel S(pi q / 2)^n."""
+    return float(lib().orc_sinc_norm(int(n)))
+
+
+def kernel_W(prm, r: float, h: float) -> float:
+    """W(r, h) of the kernel prm.kernel selects (0 M4, 1 Wendland C2, 2 sinc)."""
+    P = params(prm)
+    return float(lib().orc_kernel_W(C.byref(P), float(r), float(h)))
+
+
+def kernel_dWdr(prm, r: float, h: float) -> float:
+    P = params(prm)
+    return float(lib().orc_kernel_dWdr(C.byref(P), float(r), float(h)))
+
+
+def _csr_args(off, idx, ng=None):
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    if len(idx) == 0:
+        idx = np.zeros(1, dtype=np.int32)
+    out = [off.ctypes.data_as(_I64), idx.ctypes.data_as(_I32)]
+    keep = [off, idx]
+    if ng is not None:
+        ng = np.ascontiguousarray(ng, dtype=np.int32)
+        out.append(ng.ctypes.data_as(_I32))
+        keep.append(ng)
+    return out, keep
+
+
+def iad(prm, s: dict, rho, off, idx, ng):
+    """IAD matrices C_i = tau_i^-1, shape (n, 6): xx, xy, xz, yy, yz, zz."""
+    arrs = [_c64(s[k]) for k in ("x", "y", "z", "m", "h")]
+    rho = _c64(rho)
+    n = len(arrs[0])
+    cm = np.zeros((max(n, 1), 6))
+    a, keep = _csr_args(off, idx, ng)
+    P = params(prm)
+    lib().orc_iad(C.byref(P), n, *[_d(v) for v in arrs], _d(rho), *a, _d(cm))
+    return cm[:n]
+
+
+def iad_gradient(prm, s: dict, rho, off, idx, ng, cm, f):
+    """IAD gradient of the per-particle field f; returns (gx, gy, gz)."""
+    arrs = [_c64(s[k]) for k in ("x", "y", "z", "m", "h")]
+    rho, f = _c64(rho), _c64(f)
+    cm = np.ascontiguousarray(cm, dtype=np.float64)
+    n = len(arrs[0])
+    out = [np.empty(n) for _ in range(3)]
+    a, keep = _csr_args(off, idx, ng)
+    P = params(prm)
+    lib().orc_iad_gradient(C.byref(P), n, *[_d(v) for v in arrs], _d(rho), *a, _d(cm), _d(f),
+                           *[_d(v) for v in out])
+    return tuple(out)
 
 
 def count_brute(prm, x, y, z, i: int, h: float) -> int:
@@ -179,8 +247,17 @@ def eos(prm, rho, u):
     return p, c
 
 
-def forces(prm, s: dict, rho, p, c, off, idx):
-    """Returns (ax, ay, az, du, mumax) for the state dict s (x..u)."""
+def _cmat(prm, cm, n):
+    if int(getattr(prm, "gradients", 0)) == 1:
+        if cm is None:
+            raise ValueError("IAD gradients need the matrices of iad()")
+        return np.ascontiguousarray(cm, dtype=np.float64).reshape(-1)
+    return np.zeros(1)
+
+
+def forces(prm, s: dict, rho, p, c, off, idx, cm=None):
+    """Returns (ax, ay, az, du, mumax) for the state dict s (x..u); cm are the
+    IAD matrices when prm.gradients == 1."""
     arrs = [_c64(s[k]) for k in ("x", "y", "z", "vx", "vy", "vz", "m", "h")]
     rho, p, c = _c64(rho), _c64(p), _c64(c)
     off = np.ascontiguousarray(off, dtype=np.int64)
@@ -189,13 +266,15 @@ def forces(prm, s: dict, rho, p, c, off, idx):
         idx = np.zeros(1, dtype=np.int32)
     n = len(arrs[0])
     out = [np.empty(n) for _ in range(5)]
+    cmf = _cmat(prm, cm, n)
     P = params(prm)
     lib().orc_forces(C.byref(P), n, *[_d(a) for a in arrs], _d(rho), _d(p), _d(c),
-                     off.ctypes.data_as(_I64), idx.ctypes.data_as(_I32), *[_d(a) for a in out])
+                     off.ctypes.data_as(_I64), idx.ctypes.data_as(_I32), _d(cmf),
+                     *[_d(a) for a in out])
     return tuple(out)
 
 
-def forces_scale(prm, s: dict, rho, p, c, off, idx):
+def forces_scale(prm, s: dict, rho, p, c, off, idx, cm=None):
     """Per-particle magnitudes of the summed force terms (sa, sdu, smu); see
     orc_forces_scale."""
     arrs = [_c64(s[k]) for k in ("x", "y", "z", "vx", "vy", "vz", "m", "h")]
@@ -206,9 +285,10 @@ def forces_scale(prm, s: dict, rho, p, c, off, idx):
         idx = np.zeros(1, dtype=np.int32)
     n = len(arrs[0])
     out = [np.empty(n) for _ in range(3)]
+    cmf = _cmat(prm, cm, n)
     P = params(prm)
     lib().orc_forces_scale(C.byref(P), n, *[_d(a) for a in arrs], _d(rho), _d(p), _d(c),
-                           off.ctypes.data_as(_I64), idx.ctypes.data_as(_I32),
+                           off.ctypes.data_as(_I64), idx.ctypes.data_as(_I32), _d(cmf),
                            *[_d(a) for a in out])
     return tuple(out)
 
@@ -260,8 +340,9 @@ def pipeline(prm, s: dict):
     s2["h"] = h
     rho = density(prm, s["x"], s["y"], s["z"], s["m"], h, off, idx, ng)
     p, c = eos(prm, rho, s["u"])
-    ax, ay, az, du, mumax = forces(prm, s2, rho, p, c, off, idx)
-    sa, sdu, smu = forces_scale(prm, s2, rho, p, c, off, idx)
+    cm = iad(prm, s2, rho, off, idx, ng) if int(getattr(prm, "gradients", 0)) == 1 else None
+    ax, ay, az, du, mumax = forces(prm, s2, rho, p, c, off, idx, cm)
+    sa, sdu, smu = forces_scale(prm, s2, rho, p, c, off, idx, cm)
     return dict(h=h, nnb=nnb, conv=conv, off=off, idx=idx, ng=ng, rho=rho, p=p, c=c, ax=ax,
                 ay=ay, az=az, du=du, mumax=mumax, dt=dt(prm, h, c, mumax),
-                scale_a=sa, scale_du=sdu, scale_mu=smu)
+                scale_a=sa, scale_du=sdu, scale_mu=smu, iad=cm)

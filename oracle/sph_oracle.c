@@ -31,7 +31,9 @@ typedef struct {
     int32_t n_tol;       /* accepted |n - n_target| (5) */
     int32_t max_h_iter;  /* h iterations before giving up */
     int32_t periodic_z;  /* 1: minimum image along z with period lz */
-    int32_t pad_;
+    int32_t kernel;      /* 0 = M4 cubic spline, 1 = Wendland C2, 2 = sinc (Table 1) */
+    int32_t gradients;   /* 0 = kernel derivatives, 1 = IAD (Table 1) */
+    int32_t sinc_n;      /* exponent n of the sinc kernel (kernel 2) */
     double rho0, c0, gamma, alpha, beta, eta2, cfl, lz;
 } orc_params;
 
@@ -86,6 +88,111 @@ double orc_dWdr(double r, double h)
         return k * (-0.75 * t * t);
     }
     return 0.0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Kernel variants (Tables 1 and 2 name the M4 spline, the Wendland and the
+ * sinc kernels; the paper prints none of them, so each is the textbook form
+ * in 3D with support 2h, written for q = r/h):
+ *
+ *  Wendland C2 (Wendland 1995, compact support H = 2h):
+ *    W     = 21/(16 pi h^3) (1 - q/2)^4 (1 + 2 q)         q < 2
+ *    dW/dr = -105/(16 pi h^4) q (1 - q/2)^3              q < 2
+ *  since d/dq [(1 - q/2)^4 (1 + 2q)] = 2 (1 - q/2)^3 ((1 - q/2) - (1 + 2q))
+ *  = -5 q (1 - q/2)^3.
+ *
+ *  Sinc (Cabezon, Garcia-Senz and Relano 2008), x = pi q / 2, S(x) = sin x / x:
+ *    W     = B_n / h^3 S(x)^n                            q < 2
+ *    dW/dr = B_n / h^4 (pi / 2) n S(x)^(n-1) S'(x),  S'(x) = (x cos x - sin x) / x^2
+ *  with S(0) = 1, S'(0) = 0 and the normalisation
+ *    B_n = 1 / (4 pi int_0^2 q^2 S(pi q / 2)^n dq)
+ *  taken by composite Simpson quadrature (orc_sinc_norm).
+ * ------------------------------------------------------------------------- */
+static double orc_ipow(double v, int k)
+{
+    double r = 1.0;
+    for (int e = 0; e < k; ++e) r = r * v;
+    return r;
+}
+
+static double orc_sinc(double x)
+{
+    return x == 0.0 ? 1.0 : sin(x) / x;
+}
+
+static double orc_dsinc(double x)
+{
+    return x == 0.0 ? 0.0 : (x * cos(x) - sin(x)) / (x * x);
+}
+
+/* B_n by composite Simpson on [0, 2] with 2^16 panels, Kahan-summed. */
+double orc_sinc_norm(int n)
+{
+    const int64_t panels = INT64_C(1) << 16;
+    const double hq = 2.0 / (double)panels;
+    double sum = 0.0, comp = 0.0;
+    for (int64_t k = 0; k <= panels; ++k) {
+        double q = hq * (double)k;
+        double f = q * q * orc_ipow(orc_sinc(0.5 * ORC_PI * q), n);
+        double wgt = (k == 0 || k == panels) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
+        double y = wgt * f - comp;
+        double t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    }
+    double integral = sum * hq / 3.0;
+    return 1.0 / (4.0 * ORC_PI * integral);
+}
+
+/* The selected kernel with its normalisation evaluated once per call. */
+typedef struct {
+    int kind, n;
+    double Bn; /* sinc normalisation (kind 2) */
+} orc_kern;
+
+static orc_kern orc_kern_of(const orc_params *P)
+{
+    orc_kern k = {P->kernel, P->sinc_n, 0.0};
+    if (k.kind == 2) k.Bn = orc_sinc_norm(k.n);
+    return k;
+}
+
+static double orc_kW(const orc_kern *K, double r, double h)
+{
+    if (K->kind == 0) return orc_W(r, h);
+    double q = r / h;
+    if (!(q < 2.0)) return 0.0;
+    if (K->kind == 1) {
+        double t = 1.0 - 0.5 * q;
+        return 21.0 / (16.0 * ORC_PI * h * h * h) * (t * t * t * t * (1.0 + 2.0 * q));
+    }
+    return K->Bn / (h * h * h) * orc_ipow(orc_sinc(0.5 * ORC_PI * q), K->n);
+}
+
+static double orc_kdWdr(const orc_kern *K, double r, double h)
+{
+    if (K->kind == 0) return orc_dWdr(r, h);
+    double q = r / h;
+    if (!(q < 2.0)) return 0.0;
+    if (K->kind == 1) {
+        double t = 1.0 - 0.5 * q;
+        return -105.0 / (16.0 * ORC_PI * h * h * h * h) * (q * t * t * t);
+    }
+    double x = 0.5 * ORC_PI * q;
+    return K->Bn / (h * h * h * h) * (0.5 * ORC_PI) *
+           ((double)K->n * orc_ipow(orc_sinc(x), K->n - 1) * orc_dsinc(x));
+}
+
+double orc_kernel_W(const orc_params *P, double r, double h)
+{
+    orc_kern K = orc_kern_of(P);
+    return orc_kW(&K, r, h);
+}
+
+double orc_kernel_dWdr(const orc_params *P, double r, double h)
+{
+    orc_kern K = orc_kern_of(P);
+    return orc_kdWdr(&K, r, h);
 }
 
 /* Pair vector r_ij = r_i - r_j; along z the minimum image with period lz when
@@ -496,22 +603,109 @@ int orc_csr_fill(const orc_params *P, int64_t n, const double *x, const double *
 
 /* ---------------------------------------------------------------------------
  * Density summation (Section 2, step 3 "density"): standard volume elements,
- *   rho_i = m_i W(0, h_i) + sum_{j in N_i} m_j W(r_ij, h_i).
+ *   rho_i = m_i W(0, h_i) + sum_{j in N_i} m_j W(r_ij, h_i),
+ * with W the selected kernel.
  * ------------------------------------------------------------------------- */
 void orc_density(const orc_params *P, int64_t n, const double *x, const double *y,
                  const double *z, const double *m, const double *h, const int64_t *offsets,
                  const int32_t *idx, const int32_t *ngather, double *rho)
 {
+    orc_kern K = orc_kern_of(P);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
-        double s = m[i] * orc_W(0.0, h[i]);
+        double s = m[i] * orc_kW(&K, 0.0, h[i]);
         for (int64_t e = offsets[i]; e < offsets[i] + ngather[i]; ++e) {
             int64_t j = idx[e];
             double d[3];
             orc_pair(P, x, y, z, i, j, d);
-            s = s + m[j] * orc_W(sqrt(orc_r2(d)), h[i]);
+            s = s + m[j] * orc_kW(&K, sqrt(orc_r2(d)), h[i]);
         }
         rho[i] = s;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Integral approach to derivatives, IAD (Table 1 "Gradients calculation";
+ * Garcia-Senz, Cabezon and Escartin 2012). With volume elements V_j = m_j /
+ * rho_j and the gather set N_i, the symmetric 3x3 matrix
+ *   tau_i = sum_{j in N_i} V_j W(r_ij, h_i) (r_j - r_i) (r_j - r_i)^T
+ * is inverted, C_i = tau_i^(-1) (adjugate over determinant; a singular tau
+ * gives C_i = 0). Stored per particle as (xx, xy, xz, yy, yz, zz).
+ * The IAD gradient of a field f,
+ *   grad f_i = C_i sum_{j in N_i} V_j (f_j - f_i) W(r_ij, h_i) (r_j - r_i),
+ * is exact for every linear f, because the sum is then tau_i grad f.
+ * ------------------------------------------------------------------------- */
+static void orc_inv3(const double *t, double *cm)
+{
+    double a = t[0], b = t[1], c = t[2], d = t[3], e = t[4], f = t[5];
+    /* cofactors of the symmetric matrix [[a b c] [b d e] [c e f]] */
+    double c00 = d * f - e * e, c01 = c * e - b * f, c02 = b * e - c * d;
+    double c11 = a * f - c * c, c12 = b * c - a * e, c22 = a * d - b * b;
+    double det = a * c00 + b * c01 + c * c02;
+    if (det == 0.0) {
+        for (int k = 0; k < 6; ++k) cm[k] = 0.0;
+        return;
+    }
+    cm[0] = c00 / det; cm[1] = c01 / det; cm[2] = c02 / det;
+    cm[3] = c11 / det; cm[4] = c12 / det; cm[5] = c22 / det;
+}
+
+void orc_iad(const orc_params *P, int64_t n, const double *x, const double *y, const double *z,
+             const double *m, const double *h, const double *rho, const int64_t *offsets,
+             const int32_t *idx, const int32_t *ngather, double *cmat)
+{
+    orc_kern K = orc_kern_of(P);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int64_t e = offsets[i]; e < offsets[i] + ngather[i]; ++e) {
+            int64_t j = idx[e];
+            double d[3];
+            orc_pair(P, x, y, z, i, j, d);
+            double r = sqrt(orc_r2(d));
+            double w = m[j] / rho[j] * orc_kW(&K, r, h[i]);
+            /* (r_j - r_i) = -d; the outer product is the same for +-d */
+            t[0] = t[0] + w * d[0] * d[0];
+            t[1] = t[1] + w * d[0] * d[1];
+            t[2] = t[2] + w * d[0] * d[2];
+            t[3] = t[3] + w * d[1] * d[1];
+            t[4] = t[4] + w * d[1] * d[2];
+            t[5] = t[5] + w * d[2] * d[2];
+        }
+        orc_inv3(t, cmat + 6 * i);
+    }
+}
+
+/* C v for the symmetric matrix c = (xx, xy, xz, yy, yz, zz). */
+static void orc_symv(const double *c, const double *v, double *o)
+{
+    o[0] = c[0] * v[0] + c[1] * v[1] + c[2] * v[2];
+    o[1] = c[1] * v[0] + c[3] * v[1] + c[4] * v[2];
+    o[2] = c[2] * v[0] + c[4] * v[1] + c[5] * v[2];
+}
+
+void orc_iad_gradient(const orc_params *P, int64_t n, const double *x, const double *y,
+                      const double *z, const double *m, const double *h, const double *rho,
+                      const int64_t *offsets, const int32_t *idx, const int32_t *ngather,
+                      const double *cmat, const double *f, double *gx, double *gy, double *gz)
+{
+    orc_kern K = orc_kern_of(P);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int64_t e = offsets[i]; e < offsets[i] + ngather[i]; ++e) {
+            int64_t j = idx[e];
+            double d[3];
+            orc_pair(P, x, y, z, i, j, d);
+            double r = sqrt(orc_r2(d));
+            double w = m[j] / rho[j] * (f[j] - f[i]) * orc_kW(&K, r, h[i]);
+            for (int k = 0; k < 3; ++k) s[k] = s[k] - w * d[k]; /* r_j - r_i = -d */
+        }
+        double g[3];
+        orc_symv(cmat + 6 * i, s, g);
+        gx[i] = g[0];
+        gy[i] = g[1];
+        gz[i] = g[2];
     }
 }
 
@@ -558,14 +752,39 @@ void orc_eos(const orc_params *P, int64_t n, const double *rho, const double *u,
  *   du_i  = A_i sum_j m_j Fbar_ij (v_ij . r_ij)
  *           + 1/2 sum_j m_j Pi_ij Fbar_ij (v_ij . r_ij)
  *   mumax_i = max_j |mu_ij|
- * A pair at zero separation contributes nothing.
+ * A pair at zero separation contributes nothing. dW/dr is the selected
+ * kernel's.
+ *
+ * IAD gradients (gradients = 1) replace the symmetrised kernel gradient
+ * Fbar_ij r_ij by the symmetrised IAD one,
+ *   G_ij = 1/2 (W(r, h_i) C_i (r_j - r_i) + W(r, h_j) C_j (r_j - r_i))
+ * (the IAD estimate of grad_i W(r_ij, h) at each particle's own h and C;
+ * each W zero outside its own support), in every place it appears:
+ *   a_i  = - sum_j m_j (A_i + A_j + Pi_ij) G_ij
+ *   du_i = A_i sum_j m_j G_ij . v_ij + 1/2 sum_j m_j Pi_ij G_ij . v_ij
+ * G_ji = -G_ij, so total momentum and total energy are conserved as with
+ * kernel derivatives (angular momentum is not: G_ij need not be parallel to
+ * r_ij).
  * ------------------------------------------------------------------------- */
+static void orc_iad_pair(const orc_kern *K, const double *cmat, int64_t i, int64_t j,
+                         const double *h, double r, const double *d, double *G)
+{
+    double rji[3] = {-d[0], -d[1], -d[2]};
+    double ui[3], uj[3];
+    orc_symv(cmat + 6 * i, rji, ui);
+    orc_symv(cmat + 6 * j, rji, uj);
+    double wi = orc_kW(K, r, h[i]), wj = orc_kW(K, r, h[j]);
+    for (int k = 0; k < 3; ++k) G[k] = 0.5 * (wi * ui[k] + wj * uj[k]);
+}
+
 void orc_forces(const orc_params *P, int64_t n, const double *x, const double *y,
                 const double *z, const double *vx, const double *vy, const double *vz,
                 const double *m, const double *h, const double *rho, const double *p,
-                const double *c, const int64_t *offsets, const int32_t *idx, double *ax,
-                double *ay, double *az, double *du, double *mumax)
+                const double *c, const int64_t *offsets, const int32_t *idx, const double *cmat,
+                double *ax, double *ay, double *az, double *du, double *mumax)
 {
+    orc_kern K = orc_kern_of(P);
+    int iad = P->gradients == 1;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double Ai = p[i] / (rho[i] * rho[i]);
@@ -577,7 +796,6 @@ void orc_forces(const orc_params *P, int64_t n, const double *x, const double *y
             double r2 = orc_r2(d);
             if (r2 == 0.0) continue;
             double r = sqrt(r2);
-            double Fb = 0.5 * (orc_dWdr(r, h[i]) + orc_dWdr(r, h[j])) / r;
             double wx = vx[i] - vx[j], wy = vy[i] - vy[j], wz = vz[i] - vz[j];
             double vr = (wx * d[0] + wy * d[1]) + wz * d[2];
             double Pi = 0.0, mu = 0.0;
@@ -589,12 +807,25 @@ void orc_forces(const orc_params *P, int64_t n, const double *x, const double *y
                 Pi = (-P->alpha * cb * mu + P->beta * mu * mu) / rb;
             }
             double Aj = p[j] / (rho[j] * rho[j]);
-            double g = m[j] * (Ai + Aj + Pi) * Fb;
-            sx = sx + g * d[0];
-            sy = sy + g * d[1];
-            sz = sz + g * d[2];
-            sp = sp + m[j] * Fb * vr;
-            sv = sv + m[j] * Pi * Fb * vr;
+            if (iad) {
+                double G[3];
+                orc_iad_pair(&K, cmat, i, j, h, r, d, G);
+                double Gv = (G[0] * wx + G[1] * wy) + G[2] * wz;
+                double g = m[j] * (Ai + Aj + Pi);
+                sx = sx + g * G[0];
+                sy = sy + g * G[1];
+                sz = sz + g * G[2];
+                sp = sp + m[j] * Gv;
+                sv = sv + m[j] * Pi * Gv;
+            } else {
+                double Fb = 0.5 * (orc_kdWdr(&K, r, h[i]) + orc_kdWdr(&K, r, h[j])) / r;
+                double g = m[j] * (Ai + Aj + Pi) * Fb;
+                sx = sx + g * d[0];
+                sy = sy + g * d[1];
+                sz = sz + g * d[2];
+                sp = sp + m[j] * Fb * vr;
+                sv = sv + m[j] * Pi * Fb * vr;
+            }
             double amu = fabs(mu);
             if (amu > mum) mum = amu;
         }
@@ -609,8 +840,9 @@ void orc_forces(const orc_params *P, int64_t n, const double *x, const double *y
 /* Conditioning scales of the force sums, for comparing two implementations
  * whose sums round differently: per particle the sums of the magnitudes of
  * the terms that the definitions above add up,
- *   sa_i  = sum_j m_j |A_i + A_j + Pi_ij| |Fbar_ij| |r_ij|
- *   sdu_i = |A_i| sum_j m_j |Fbar_ij| |v_ij| |r_ij| + 1/2 sum_j m_j |Pi_ij Fbar_ij| |v_ij| |r_ij|
+ *   sa_i  = sum_j m_j |A_i + A_j + Pi_ij| |g_ij|
+ *   sdu_i = |A_i| sum_j m_j |g_ij| |v_ij| + 1/2 sum_j m_j |Pi_ij| |g_ij| |v_ij|
+ * with g_ij = Fbar_ij r_ij, or G_ij with IAD gradients,
  *   smu_i = max_j hb |v_ij| |r_ij| / (r^2 + eta2 hb^2)
  * Rounding in v_ij . r_ij alone is bounded by a few ulps of |v_ij| |r_ij|, so
  * a field whose exact value is zero (du and mu under rigid rotation) carries
@@ -618,9 +850,11 @@ void orc_forces(const orc_params *P, int64_t n, const double *x, const double *y
 void orc_forces_scale(const orc_params *P, int64_t n, const double *x, const double *y,
                       const double *z, const double *vx, const double *vy, const double *vz,
                       const double *m, const double *h, const double *rho, const double *p,
-                      const double *c, const int64_t *offsets, const int32_t *idx, double *sa,
-                      double *sdu, double *smu)
+                      const double *c, const int64_t *offsets, const int32_t *idx,
+                      const double *cmat, double *sa, double *sdu, double *smu)
 {
+    orc_kern K = orc_kern_of(P);
+    int iad = P->gradients == 1;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double Ai = p[i] / (rho[i] * rho[i]);
@@ -632,7 +866,15 @@ void orc_forces_scale(const orc_params *P, int64_t n, const double *x, const dou
             double r2 = orc_r2(d);
             if (r2 == 0.0) continue;
             double r = sqrt(r2);
-            double Fb = 0.5 * (orc_dWdr(r, h[i]) + orc_dWdr(r, h[j])) / r;
+            /* |grad|: |Fbar_ij| r, or |G_ij| with IAD */
+            double gabs;
+            if (iad) {
+                double G[3];
+                orc_iad_pair(&K, cmat, i, j, h, r, d, G);
+                gabs = sqrt((G[0] * G[0] + G[1] * G[1]) + G[2] * G[2]);
+            } else {
+                gabs = fabs(0.5 * (orc_kdWdr(&K, r, h[i]) + orc_kdWdr(&K, r, h[j])) / r) * r;
+            }
             double wx = vx[i] - vx[j], wy = vy[i] - vy[j], wz = vz[i] - vz[j];
             double vr = (wx * d[0] + wy * d[1]) + wz * d[2];
             double vabs = sqrt((wx * wx + wy * wy) + wz * wz);
@@ -645,9 +887,9 @@ void orc_forces_scale(const orc_params *P, int64_t n, const double *x, const dou
                 Pi = (-P->alpha * cb * mu + P->beta * mu * mu) / rb;
             }
             double Aj = p[j] / (rho[j] * rho[j]);
-            s1 = s1 + m[j] * fabs(Ai + Aj + Pi) * fabs(Fb) * r;
-            s2 = s2 + m[j] * fabs(Fb) * vabs * r;
-            s3 = s3 + m[j] * fabs(Pi * Fb) * vabs * r;
+            s1 = s1 + m[j] * fabs(Ai + Aj + Pi) * gabs;
+            s2 = s2 + m[j] * gabs * vabs;
+            s3 = s3 + m[j] * fabs(Pi) * gabs * vabs;
             double mus = hb * vabs * r / (r2 + P->eta2 * hb * hb);
             if (mus > s4) s4 = mus;
         }
@@ -701,8 +943,8 @@ void orc_leapfrog(const orc_params *P, int64_t n, double dt, double *x, double *
 }
 
 /* ---------------------------------------------------------------------------
- * Whole time step, Algorithm 1 order: neighbours and h, density, EOS,
- * forces, dt, update. State arrays are updated in place; rho, p, c, a, du,
+ * Whole time step, Algorithm 1 order: neighbours and h, density, EOS, (the
+ * IAD matrices when selected), forces, dt, update. State arrays are updated in place; rho, p, c, a, du,
  * mumax receive the values of the last step's force evaluation. stats (may be
  * NULL) receives { nnz of the last step, non-converged particles summed over
  * the steps }. Returns 0, or -1 on allocation failure.
@@ -717,9 +959,11 @@ int orc_step(const orc_params *P, int64_t n, int nsteps, double *x, double *y, d
     uint8_t *conv = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     int64_t *off = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
     double *hn = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *cm = P->gradients == 1 ? (double *)malloc((size_t)(n > 0 ? n : 1) * 6 * sizeof(double))
+                                   : NULL;
     int rc = 0;
     int64_t bad_total = 0, nnz = 0;
-    if (!nnb || !ng || !conv || !off || !hn) { rc = -1; goto done; }
+    if (!nnb || !ng || !conv || !off || !hn || (P->gradients == 1 && !cm)) { rc = -1; goto done; }
     for (int s = 0; s < nsteps; ++s) {
         int64_t bad = orc_h_iterate(P, n, x, y, z, h, hn, nnb, conv, 0);
         if (bad < 0) { rc = -1; goto done; }
@@ -734,7 +978,9 @@ int orc_step(const orc_params *P, int64_t n, int nsteps, double *x, double *y, d
         if (orc_csr_fill(P, n, x, y, z, h, off, idx, ng, 0) != 0) { free(idx); rc = -1; goto done; }
         orc_density(P, n, x, y, z, m, h, off, idx, ng, rho);
         orc_eos(P, n, rho, u, p, c);
-        orc_forces(P, n, x, y, z, vx, vy, vz, m, h, rho, p, c, off, idx, ax, ay, az, du, mumax);
+        if (P->gradients == 1) orc_iad(P, n, x, y, z, m, h, rho, off, idx, ng, cm);
+        orc_forces(P, n, x, y, z, vx, vy, vz, m, h, rho, p, c, off, idx, cm, ax, ay, az, du,
+                   mumax);
         free(idx);
         double dt = orc_dt(P, n, h, c, mumax);
         orc_leapfrog(P, n, dt, x, y, z, vx, vy, vz, u, ax, ay, az, du);
@@ -743,6 +989,6 @@ int orc_step(const orc_params *P, int64_t n, int nsteps, double *x, double *y, d
     }
 done:
     if (stats) { stats[0] = nnz; stats[1] = bad_total; }
-    free(nnb); free(ng); free(conv); free(off); free(hn);
+    free(nnb); free(ng); free(conv); free(off); free(hn); free(cm);
     return rc;
 }

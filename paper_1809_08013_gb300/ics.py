@@ -43,6 +43,13 @@ FIELDS = ("x", "y", "z", "vx", "vy", "vz", "m", "h", "u")
 EOS_TAIT = 0
 EOS_IDEAL = 1
 
+KERNEL_M4 = 0        # M4 cubic spline (Table 1)
+KERNEL_WENDLAND = 1  # Wendland C2 (Table 1)
+KERNEL_SINC = 2      # sinc kernel S(pi q / 2)^n (Table 1)
+
+GRAD_KERNEL = 0      # kernel-derivative gradients (Table 1)
+GRAD_IAD = 1         # integral approach to derivatives (Table 1)
+
 
 @dataclasses.dataclass
 class SphParams:
@@ -69,6 +76,9 @@ class SphParams:
                                  # 2 native FP64 (the oracle is FP64 throughout)
     pair_threads: int = 0        # lanes per particle in the pair sums (0 = library default)
     defer_lanes: int = 0         # h-search hand-over threshold (0 = library default)
+    kernel: int = KERNEL_M4      # 0 M4 cubic spline, 1 Wendland C2, 2 sinc
+    gradients: int = GRAD_KERNEL # 0 kernel derivatives, 1 IAD
+    sinc_n: int = 5              # exponent of the sinc kernel (2..12)
 
     def as_dict(self) -> dict:
         return dataclasses.asdict(self)
@@ -78,12 +88,46 @@ def _empty_state(n: int) -> dict:
     return {f: np.zeros(n, dtype=np.float64) for f in FIELDS}
 
 
+def patch_pressure(x, y, omega: float, rho: float, side: float = 1.0, terms: int = 64,
+                   chunk: int = 1 << 15):
+    """Initial pressure of the rotating square patch (Section 4.1.1): the
+    solution of the incompressible pressure Poisson equation lap p = 2 rho
+    omega^2 on the square of side L with p = 0 on its edges, as the double
+    sine series over odd m and n (the printed series is garbled: it writes x
+    where y is meant, and its m = 0 or n = 0 terms are singular),
+
+      p = rho sum_{m, n odd} -32 omega^2 / (m n pi^2 ((m pi/L)^2 + (n pi/L)^2))
+                             sin(m pi x'/L) sin(n pi y'/L),
+
+    with x' = x + L/2, y' = y + L/2 measured from the patch corner. `terms`
+    odd values of each index are summed."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    k = 2.0 * np.arange(terms, dtype=np.float64) + 1.0   # odd m, n
+    kk = (k * math.pi / side) ** 2
+    coef = -32.0 * omega * omega / (np.outer(k, k) * math.pi ** 2 * (kk[:, None] + kk[None, :]))
+    out = np.empty(x.shape)
+    for a in range(0, x.size, chunk):
+        xs = x.reshape(-1)[a:a + chunk] + 0.5 * side
+        ys = y.reshape(-1)[a:a + chunk] + 0.5 * side
+        sx = np.sin(np.outer(k, xs) * (math.pi / side))
+        sy = np.sin(np.outer(k, ys) * (math.pi / side))
+        out.reshape(-1)[a:a + chunk] = rho * np.einsum("mi,mn,ni->i", sx, coef, sy)
+    return out
+
+
 def square_patch(n_side: int, seed: int, omega: float = 5.0, rho0: float = 1000.0,
-                 c0: float = 50.0, jitter: float = 0.01):
+                 c0: float = 50.0, jitter: float = 0.01, pressure_ic: bool = False,
+                 pressure_terms: int = 64):
     """Rotating square patch on an n_side^3 lattice in [-0.5, 0.5]^3.
 
     Returns (state, params). state maps each name in FIELDS to a float64
     array of length n_side**3 in lattice order (x fastest).
+
+    pressure_ic: start from the series pressure of patch_pressure instead of
+    p = 0. Reading: with the Tait equation the pressure fixes the density,
+    rho = rho0 (1 + 7 p / (c0^2 rho0))^(1/7), and each particle carries the
+    mass rho dx^3 of its lattice cell, so the summed density starts near it.
     """
     if n_side < 1:
         raise ValueError("n_side must be >= 1")
@@ -101,6 +145,9 @@ def square_patch(n_side: int, seed: int, omega: float = 5.0, rho0: float = 1000.
     s["vx"][:] = omega * s["y"]
     s["vy"][:] = -omega * s["x"]
     s["m"][:] = rho0 * dx ** 3
+    if pressure_ic:
+        p0 = patch_pressure(s["x"], s["y"], omega, rho0, 1.0, pressure_terms)
+        s["m"][:] = rho0 * (1.0 + 7.0 * p0 / (c0 * c0 * rho0)) ** (1.0 / 7.0) * dx ** 3
     s["h"][:] = 1.4395 * dx
     s["u"][:] = 0.0
     prm = SphParams(eos=EOS_TAIT, rho0=rho0, c0=c0, periodic_z=1, lz=1.0)
