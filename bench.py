@@ -41,6 +41,26 @@ UNIT = "particle-updates/s"
 FLOPS_PAIR_BASE = 51
 FLOPS_PAIR_AV = 17
 
+
+def variant_flops(kernel, gradients, sinc_n):
+    """Counted FP64 work of the Table 1 variants, by the same rule (each +, -,
+    *, / and sqrt = 1; sin and cos not counted). Shapes: the derivative f of
+    M4 and Wendland C2 takes 5 operations and the sinc one n + 6 (x, S = sin
+    x / x, S^(n-1), (x cos x - sin x) / x^2, n S^(n-1) S'); the value g takes 6
+    (M4), 7 (Wendland) or n + 1 (sinc). Returns (per pair of S_i in the force
+    pass, its viscosity extra, per pair of N_i in the IAD matrix pass).
+    Kernel derivatives: FLOPS_PAIR_BASE with the two derivative shapes
+    swapped. IAD force pair: pair vector 3, r^2 5, r 1, q_i and q_j 2, two
+    values g, their h^-3 wnorm factors 4, C_i r and C_j r 30, G 12, v_ij 3,
+    v.r 5, G.v 5, (A_i + A_j + Pi) m_j 3, times G 3, acceleration 3, energy
+    sums 4 -> 83 + 2 g. IAD matrix pair: pair vector 3, r^2 5, r 1, q 1, g,
+    m_j / rho_j 1, the weight 1, the six products and sums 15 -> 27 + g."""
+    f = {0: 5, 1: 5, 2: sinc_n + 6}[kernel]
+    g = {0: 6, 1: 7, 2: sinc_n + 1}[kernel]
+    if gradients == 1:
+        return 83 + 2 * g, FLOPS_PAIR_AV, 27 + g
+    return FLOPS_PAIR_BASE - 2 * 5 + 2 * f, FLOPS_PAIR_AV, 0
+
 # DRAM traffic of one force-kernel launch from an ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum) on the 70^3 patch, scaled to a launch here by the
 # number of pairs it processes (profiles/kernels_patch343k.md). It is reported
@@ -93,6 +113,9 @@ def parse(argv=None):
     ap.add_argument("--ensemble-steps", type=int, default=50)
     ap.add_argument("--ensemble-count", type=int, default=256)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the Table 1 variants (Wendland, sinc, IAD) at the bench size")
+    ap.add_argument("--variant-steps", type=int, default=5)
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving stream (the full configuration has 2000)")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
@@ -400,6 +423,85 @@ def _run_ensemble(args, B, dev, stream):
     }
 
 
+VARIANTS = (("M4, kernel derivatives, native FP64", 0, 0, 5),
+            ("Wendland C2, kernel derivatives", 1, 0, 5),
+            ("sinc n=5, kernel derivatives", 2, 0, 5),
+            ("M4, IAD gradients", 0, 1, 5),
+            ("Wendland C2, IAD gradients", 1, 1, 5))
+
+
+def run_variants(args, B, dev, fp64_peak):
+    """The Table 1 variants on the benchmark workload: each a separate run of
+    --variant-steps steps from the initial conditions (after one untimed
+    step), all in the native FP64 pair kernels (the M4 line is the same path
+    with the default kernel, for comparison). Roofline of the force phase
+    (k_forces / k_iad + k_forces_iad, with k_dt_finish) against the FP64
+    FMA-chain probe, from the counted flops of variant_flops."""
+    import numpy as np
+    import torch
+    s, base = make_workload(args)
+    n = len(s["x"])
+    ctx = B.Context(n, device=dev.index)
+    arr = B.alloc_arrays(s, device=dev)
+    ic = {k: arr[k].clone() for k in B.STATE_FIELDS}
+    stream = torch.cuda.current_stream(dev)
+    out = []
+    for name, kernel, grads, sn in VARIANTS:
+        prm = ics_params_copy(base)
+        prm.precision = 2
+        prm.kernel, prm.gradients, prm.sinc_n = kernel, grads, sn
+
+        def reset():
+            for k in B.STATE_FIELDS:
+                arr[k].copy_(ic[k])
+            arr["time"].zero_()
+
+        reset()
+        ctx.step(prm, arr, nsteps=1, stream=stream)
+        ctx.sync(stream)
+        reset()
+        torch.cuda.synchronize(dev)
+        ctx.timing_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(prm, arr, nsteps=args.variant_steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        phase_ms, _, tsteps = ctx.timing_read()
+        ctx.timing_enable(False)
+        st = ctx.sync(stream)
+        f_av, nnz = av_fraction(B, ctx, arr, prm.periodic_z)
+        ngather = int(arr["nnb"].sum().item())
+        base_f, av_f, iad_f = variant_flops(kernel, grads, sn)
+        flops = nnz * (base_f + av_f * f_av) + ngather * iad_f
+        forces_s = phase_ms["forces"] * 1e-3 / max(tsteps, 1)
+        ach = flops / forces_s / 1e12
+        out.append({"variant": name, "kernel": kernel, "gradients": grads,
+                    "sinc_n": sn if kernel == 2 else None,
+                    "ms_per_step": ms / args.variant_steps,
+                    "value": n * args.variant_steps / (ms * 1e-3), "unit": UNIT,
+                    "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
+                    "status": B.STATUS_NAMES.get(st),
+                    "roofline": {"bound": "alu", "kernel": "k_iad + k_forces_iad" if grads
+                                 else "k_forces", "achieved": ach, "peak": fp64_peak / 1e12,
+                                 "unit": "TFLOP/s", "frac": ach / (fp64_peak / 1e12),
+                                 "flops_per_launch": flops,
+                                 "counted": {"pair": base_f, "pair_av": av_f,
+                                             "iad_pair": iad_f},
+                                 "peak_source": "FP64 FMA-chain probe, this run"}})
+    del ctx
+    torch.cuda.empty_cache()
+    return {"workload": workload_name(args).split(", FP64")[0], "steps": args.variant_steps,
+            "runs": out}
+
+
+def ics_params_copy(p):
+    import dataclasses
+    return dataclasses.replace(p)
+
+
 def run_serving(args, B, dev):
     """Configuration 5: a Poisson stream of patch / Evrard requests served by
     continuous batching (paper_1809_08013_gb300.serve) in FP64 and in mixed
@@ -634,6 +736,9 @@ def run_native(args):
     serving = None
     if not args.no_serving and args.workload == "patch" and world == 1:
         serving = run_serving(args, B, dev)
+    variants = None
+    if not args.no_variants and args.workload == "patch" and world == 1:
+        variants = run_variants(args, B, dev, fp64_peak)
 
     clocks = sampler.summary(w0, w1) if sampler else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -645,6 +750,7 @@ def run_native(args):
                        "l2": "inputs larger than L2 (state ~0.2 GB + neighbour list ~0.4 GB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "steady_state": steady, "ensemble": ensemble, "serving": serving,
+            "variants": variants,
             "clocks": clocks, "status": B.STATUS_NAMES.get(status),
             "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
             "launches_per_phase": phase_launches}

@@ -83,7 +83,29 @@ typedef struct {
     double cell_scale;   /* cell width = 2 <h> cell_scale (0 selects the default 1.0); a tuning
                             knob of the neighbour search: h and the neighbour sets do not
                             depend on it */
+    /* Variants of Table 1 (support 2h for all kernels, q = r/h). Any choice but
+       (0, 0) runs the density and force sums in native FP64 (as precision 2;
+       pair_threads is ignored) and needs precision 0 or 2: with precision 1
+       it is SPH_E_INVAL. The neighbour search does not depend on them. */
+    int32_t kernel;      /* SPH_KERNEL_*: 0 = M4 cubic spline (1/(pi h^3)) (t^3/4 - s^3),
+                            t = max(2-q, 0), s = max(1-q, 0);
+                            1 = Wendland C2, 21/(16 pi h^3) (1 - q/2)^4 (1 + 2q) for q < 2;
+                            2 = sinc, B_n/h^3 (sin x / x)^n, x = pi q / 2, q < 2, with
+                            B_n = 1 / (4 pi int_0^2 q^2 (sin x / x)^n dq) */
+    int32_t gradients;   /* SPH_GRAD_*: 0 = kernel derivatives; 1 = IAD, integral approach
+                            to derivatives: C_i = tau_i^-1 with tau_i = sum_{j in N_i}
+                            (m_j/rho_j) W(r_ij, h_i) (r_j - r_i)(r_j - r_i)^T (C_i = 0 if
+                            tau_i is singular), and the symmetrised pair gradient
+                            G_ij = (W(r_ij, h_i) C_i + W(r_ij, h_j) C_j)(r_j - r_i) / 2
+                            in place of Fbar_ij r_ij in the momentum and energy sums */
+    int32_t sinc_n;      /* exponent n of the sinc kernel, 2..12 (read when kernel = 2) */
 } sph_params;
+
+#define SPH_KERNEL_M4 0
+#define SPH_KERNEL_WENDLAND_C2 1
+#define SPH_KERNEL_SINC 2
+#define SPH_GRAD_KERNEL 0
+#define SPH_GRAD_IAD 1
 
 /* Caller-owned particle arrays (device pointers, caller order, length n). */
 typedef struct {

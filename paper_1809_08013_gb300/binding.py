@@ -29,6 +29,7 @@ class SphParams(C.Structure):
         ("rho0", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
         ("alpha", C.c_double), ("beta", C.c_double), ("eta2", C.c_double),
         ("cfl", C.c_double), ("lz", C.c_double), ("cell_scale", C.c_double),
+        ("kernel", C.c_int32), ("gradients", C.c_int32), ("sinc_n", C.c_int32),
     ]
 
 
@@ -162,7 +163,8 @@ def params(p) -> SphParams:
                      int(getattr(p, "pair_threads", 0)), int(getattr(p, "defer_lanes", 0)),
                      float(p.rho0), float(p.c0), float(p.gamma),
                      float(p.alpha), float(p.beta), float(p.eta2), float(p.cfl), float(p.lz),
-                     float(getattr(p, "cell_scale", 0.0)))
+                     float(getattr(p, "cell_scale", 0.0)), int(getattr(p, "kernel", 0)),
+                     int(getattr(p, "gradients", 0)), int(getattr(p, "sinc_n", 5)))
 
 
 def _ptr(t):

@@ -36,7 +36,7 @@ struct Knobs {
 void set_knobs(sph_ctx* c, const Knobs& k, cudaStream_t s) {
     c->launches += 1;
     k_set_knobs<<<1, 256, 0, s>>>(c->kpi, c->ninst, k.cs, k.tpp, k.defer);
-    c->tpp = c->prec == PREC_FP64_NATIVE ? 1 : k.tpp;
+    c->tpp = native_pairs(c) ? 1 : k.tpp;
 }
 
 // Device milliseconds per step of nsteps steps after one untimed step, from

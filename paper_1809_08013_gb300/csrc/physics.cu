@@ -13,8 +13,6 @@
 
 namespace sph {
 
-constexpr double kInvPi = 0.31830988618379067154;
-
 // ---- FP64-pipe economy helpers. GB300 issues FP64 arithmetic at 1/64 of
 // the FP32 rate, so compares, selects, sign tests and clamps are done with
 // integer operations on the IEEE bit patterns (which order non-negative
@@ -76,6 +74,47 @@ __device__ __forceinline__ double dw_shape(double q) {
     return qb < kOneBits ? fin : (qb < kTwoBits ? fout : 0.0);
 }
 
+// ---- Table 1 kernel variants, as shapes g (W = wnorm h^-3 g(q)) and f
+// (dW/dr = dnorm h^-4 f(q)), zero from q = 2 on:
+//   Wendland C2: g = (1 - q/2)^4 (1 + 2q), f = -q (1 - q/2)^3
+//     (wnorm = 21/(16 pi), dnorm = 105/(16 pi));
+//   sinc: with x = pi q / 2 and S = sin x / x, g = S^n and
+//     f = n S^(n-1) (x cos x - sin x) / x^2 (wnorm = B_n, dnorm = B_n pi / 2).
+__device__ __forceinline__ double ipow(double v, int k) {
+    double r = 1.0;
+    for (int e = 0; e < k; ++e) r *= v;
+    return r;
+}
+
+template <int KER>
+__device__ __forceinline__ double kw(double q, int sn) {
+    if (KER == KER_M4) return w_shape(q);
+    if (!(bits(q) < kTwoBits)) return 0.0;
+    if (KER == KER_WENDLAND) {
+        const double t = 1.0 - 0.5 * q;
+        const double t2 = t * t;
+        return (t2 * t2) * (1.0 + 2.0 * q);
+    }
+    const double x = (0.5 * kPi) * q;
+    return bits(x) == 0 ? 1.0 : ipow(sin(x) / x, sn);
+}
+
+template <int KER>
+__device__ __forceinline__ double kdw(double q, int sn) {
+    if (KER == KER_M4) return dw_shape(q);
+    if (!(bits(q) < kTwoBits)) return 0.0;
+    if (KER == KER_WENDLAND) {
+        const double t = 1.0 - 0.5 * q;
+        return -(q * ((t * t) * t));
+    }
+    const double x = (0.5 * kPi) * q;
+    if (bits(x) == 0) return 0.0;
+    double sx, cx;
+    sincos(x, &sx, &cx);
+    const double S = sx / x;
+    return ((double)sn * ipow(S, sn - 1)) * ((x * cx - sx) / (x * x));
+}
+
 __device__ __forceinline__ void eos(const KParams& kp, double rho, double u, double& p, double& c) {
     if (kp.eos == 0) {
         const double x = rho / kp.rho0;
@@ -94,7 +133,7 @@ __device__ __forceinline__ void eos(const KParams& kp, double rho, double u, dou
 // rho_i = m_i W(0, h_i) + sum_{j in N_i} m_j W(r_ij, h_i). With FUSE the EOS
 // follows in the same thread and the pair kernels' per-particle packs are
 // written: therm = (rho/2, p/rho^2, alpha c/2, h/2), kern = (1/h, 1/h^4).
-template <bool FUSE>
+template <bool FUSE, int KER>
 __global__ void __launch_bounds__(kThreads)
 k_density(int64_t n, Batch B, const double4_32a* __restrict__ posh,
           const double4_32a* __restrict__ velm, const double* __restrict__ ue,
@@ -111,6 +150,7 @@ k_density(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     const long long half_bits = bits(0.5 * kp.lz);
     const bool per = kp.periodic_z != 0;
     const double lz = kp.lz;
+    const int sn = kp.sinc_n;
     double acc = 0.0;
     for (int e = 0; e < len; ++e) {
         const int j = __ldg(&ent[e]);
@@ -122,10 +162,10 @@ k_density(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
         // r2 > 0 for j != i unless two particles coincide; r = r2 / sqrt(r2)
         const double q = bits(r2) > 0 ? r2 * rsqrt_nr(r2) * hinv : 0.0;
-        acc = fma(mj, w_shape(q), acc);
+        acc = fma(mj, kw<KER>(q, sn), acc);
     }
-    const double sigma = hinv * hinv * hinv * kInvPi;
-    const double rho = (velm[i].w + acc) * sigma;
+    const double sigma = hinv * hinv * hinv * (KER == KER_M4 ? kInvPi : B.kp[inst].wnorm);
+    const double rho = (velm[i].w + acc) * sigma;  // g(0) = 1 for every kernel
     if (FUSE) {
         double p, c;
         eos(kp, rho, ue[i], p, c);
@@ -145,7 +185,7 @@ void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
         launch_density_mx(c, fuse_eos, s);
         return;
     }
-    if (c->prec != PREC_FP64_NATIVE) {
+    if (!native_pairs(c)) {
         launch_density_df(c, fuse_eos, s);
         return;
     }
@@ -155,14 +195,18 @@ void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
     const int b = c->cur;
     const Batch B = batch_of(c);
     c->launches += 1;
-    if (fuse_eos)
-        k_density<true><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->ue[b],
-                                                rows_of(c),
-                                                c->therm, c->kern, c->pint, c->cint);
-    else
-        k_density<false><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->ue[b],
-                                                 rows_of(c),
-                                                 c->therm, c->kern, c->pint, c->cint);
+    auto go = [&](auto kern_fn) {
+        kern_fn<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->ue[b], rows_of(c),
+                                        c->therm, c->kern, c->pint, c->cint);
+    };
+    switch (c->kern_kind * 2 + (fuse_eos ? 1 : 0)) {
+        case 0: go(k_density<false, KER_M4>); break;
+        case 1: go(k_density<true, KER_M4>); break;
+        case 2: go(k_density<false, KER_WENDLAND>); break;
+        case 3: go(k_density<true, KER_WENDLAND>); break;
+        case 4: go(k_density<false, KER_SINC>); break;
+        default: go(k_density<true, KER_SINC>); break;
+    }
 }
 
 // ------------------------------------------------------------ EOS (caller arrays)
@@ -194,6 +238,7 @@ void launch_eos_caller(const KParams& kp, const sph_particles* P, cudaStream_t s
 // shape f above; both divisions of the viscosity share one reciprocal,
 // R = 1 / ((r^2 + eta2 hb^2) rhob): mu = hb v.r rhob R and 1/rhob = (r^2 +
 // eta2 hb^2) R; Pi = mu (beta mu - alpha cb) / rhob.
+template <int KER>
 __global__ void __launch_bounds__(kThreads)
 k_forces(int64_t n, Batch B, const double4_32a* __restrict__ posh,
          const double4_32a* __restrict__ velm, const double4_32a* __restrict__ therm,
@@ -215,6 +260,8 @@ k_forces(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const bool per = kp.periodic_z != 0;
         const double lz = kp.lz;
         const double eta2 = kp.eta2, beta = kp.beta;
+        const int sn = kp.sinc_n;
+        const double cpi = 0.5 * (KER == KER_M4 ? kInvPi : kp.dnorm);
         double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0, sv = 0.0;
         long long mum = 0;  // bits of max |mu| (non-negative doubles order as integers)
         for (int e = 0; e < len; ++e) {
@@ -230,8 +277,8 @@ k_forces(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             if (bits(r2) == 0) continue;  // coincident particles exert no force
             const double rinv = rsqrt_nr(r2);
             const double r = r2 * rinv;
-            const double fa = dw_shape(r * ki.x), fb = dw_shape(r * kj.x);
-            const double Fb = fma(ki.y, fa, kj.y * fb) * ((0.5 * kInvPi) * rinv);
+            const double fa = kdw<KER>(r * ki.x, sn), fb = kdw<KER>(r * kj.x, sn);
+            const double Fb = fma(ki.y, fa, kj.y * fb) * (cpi * rinv);
             const double wx = vi.x - vj.x, wy = vi.y - vj.y, wz = vi.z - vj.z;
             const double vr = fma(wz, dz, fma(wy, dy, wx * dx));
             double Pi = 0.0;
@@ -261,6 +308,160 @@ k_forces(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         // parameters re-read here rather than kept in registers across the loop
         const KParams& ke = B.kp[slot_inst(B, (int64_t)blockIdx.x * blockDim.x)];
         dtc = pi.w / (ci + 1.2 * (ke.alpha * ci + ke.beta * mu_max));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
+    __shared__ double sh[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dtc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = sh[0];
+        for (int w = 1; w < kThreads / 32; ++w) m = fmin(m, sh[w]);
+        dt_part[blockIdx.x] = m;
+    }
+}
+
+// ------------------------------------------------------------ IAD (Table 1)
+// tau_i = sum_{j in N_i} (m_j / rho_j) W(r_ij, h_i) (r_j - r_i)(r_j - r_i)^T and
+// C_i = tau_i^-1 by the adjugate (C_i = 0 when det tau_i = 0). rho_j comes
+// from the force pack (therm.x = rho / 2), so this runs after the density.
+template <int KER>
+__global__ void __launch_bounds__(kThreads)
+k_iad(int64_t n, Batch B, const double4_32a* __restrict__ posh,
+      const double4_32a* __restrict__ velm, const double4_32a* __restrict__ therm, Rows R,
+      double4_32a* __restrict__ ca, double2* __restrict__ cb) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
+    const int32_t* ent = nullptr;
+    int len = 0;
+    if (i >= n || !slot_real(B, inst, i) || !row_of(R, n, i, true, ent, len)) return;
+    const KParams& kp = B.kp[inst];
+    const double4_32a pi = posh[i];
+    const double hinv = 1.0 / pi.w;
+    const long long half_bits = bits(0.5 * kp.lz);
+    const bool per = kp.periodic_z != 0;
+    const double lz = kp.lz;
+    const int sn = kp.sinc_n;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0, t5 = 0.0;
+    for (int e = 0; e < len; ++e) {
+        const int j = __ldg(&ent[e]);
+        const double4_32a pj = posh[j];
+        const double dx = pi.x - pj.x, dy = pi.y - pj.y;
+        double dz = pi.z - pj.z;
+        if (per) dz = wrap_z(dz, half_bits, lz);
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double q = bits(r2) > 0 ? r2 * rsqrt_nr(r2) * hinv : 0.0;
+        const double w = (velm[j].w / (2.0 * therm[j].x)) * kw<KER>(q, sn);
+        const double wx = w * dx, wy = w * dy;
+        t0 = fma(wx, dx, t0);
+        t1 = fma(wx, dy, t1);
+        t2 = fma(wx, dz, t2);
+        t3 = fma(wy, dy, t3);
+        t4 = fma(wy, dz, t4);
+        t5 = fma(w * dz, dz, t5);
+    }
+    const double sg = hinv * hinv * hinv * (KER == KER_M4 ? kInvPi : B.kp[inst].wnorm);
+    t0 *= sg; t1 *= sg; t2 *= sg; t3 *= sg; t4 *= sg; t5 *= sg;
+    // cofactors of [[t0 t1 t2] [t1 t3 t4] [t2 t4 t5]]
+    const double c00 = t3 * t5 - t4 * t4, c01 = t2 * t4 - t1 * t5, c02 = t1 * t4 - t2 * t3;
+    const double c11 = t0 * t5 - t2 * t2, c12 = t1 * t2 - t0 * t4, c22 = t0 * t3 - t1 * t1;
+    const double det = t0 * c00 + t1 * c01 + t2 * c02;
+    if (det == 0.0) {
+        ca[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        cb[i] = make_double2(0.0, 0.0);
+        return;
+    }
+    ca[i] = make_double4_32a(c00 / det, c01 / det, c02 / det, c11 / det);
+    cb[i] = make_double2(c12 / det, c22 / det);
+}
+
+// Forces with IAD gradients: the pair gradient Fbar r_ij becomes
+//   G_ij = (W(r, h_i) C_i + W(r, h_j) C_j) (r_j - r_i) / 2
+// in the momentum and energy sums (viscosity, mu and dt as in k_forces):
+//   a_i  = -sum m_j (A_i + A_j + Pi) G_ij
+//   du_i = A_i sum m_j G_ij . v_ij + 1/2 sum m_j Pi G_ij . v_ij
+// With W = wnorm h^-3 g(q): G_ij = -(wnorm/2) (h_i^-3 g_i C_i + h_j^-3 g_j C_j) r_ij.
+template <int KER>
+__global__ void __launch_bounds__(kThreads)
+k_forces_iad(int64_t n, Batch B, const double4_32a* __restrict__ posh,
+             const double4_32a* __restrict__ velm, const double4_32a* __restrict__ therm,
+             const double2* __restrict__ kern, const double* __restrict__ cint,
+             const double4_32a* __restrict__ ca, const double2* __restrict__ cb, Rows R,
+             double4_32a* __restrict__ acc, double* __restrict__ mumax,
+             double* __restrict__ dt_part) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
+    double dtc = CUDART_INF;
+    const int32_t* ent = nullptr;
+    int len = 0;
+    if (i < n && slot_real(B, inst, i) && row_of(R, n, i, false, ent, len)) {
+        const KParams& kp = B.kp[inst];
+        const double4_32a pi = posh[i];
+        const double4_32a vi = velm[i];
+        const double4_32a ti = therm[i];
+        const double hi = kern[i].x;
+        const double hi3 = hi * hi * hi;
+        const double4_32a ci = ca[i];
+        const double2 ci2 = cb[i];
+        const long long half_bits = bits(0.5 * kp.lz);
+        const bool per = kp.periodic_z != 0;
+        const double lz = kp.lz;
+        const double eta2 = kp.eta2, beta = kp.beta;
+        const int sn = kp.sinc_n;
+        const double kg = -0.5 * (KER == KER_M4 ? kInvPi : kp.wnorm);
+        double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0, sv = 0.0;
+        long long mum = 0;
+        for (int e = 0; e < len; ++e) {
+            const int j = __ldg(&ent[e]);
+            const double4_32a pj = posh[j];
+            const double4_32a vj = velm[j];
+            const double4_32a tj = therm[j];
+            const double hj = __ldg(&kern[j].x);
+            const double4_32a cj = ca[j];
+            const double2 cj2 = cb[j];
+            const double dx = pi.x - pj.x, dy = pi.y - pj.y;
+            double dz = pi.z - pj.z;
+            if (per) dz = wrap_z(dz, half_bits, lz);
+            const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            if (bits(r2) == 0) continue;
+            const double r = r2 * rsqrt_nr(r2);
+            const double wi = hi3 * kw<KER>(r * hi, sn);
+            const double wj = (hj * hj * hj) * kw<KER>(r * hj, sn);
+            // M = wi C_i + wj C_j (symmetric), G = kg M r_ij
+            const double m00 = fma(wi, ci.x, wj * cj.x), m01 = fma(wi, ci.y, wj * cj.y);
+            const double m02 = fma(wi, ci.z, wj * cj.z), m11 = fma(wi, ci.w, wj * cj.w);
+            const double m12 = fma(wi, ci2.x, wj * cj2.x), m22 = fma(wi, ci2.y, wj * cj2.y);
+            const double gx = kg * fma(m02, dz, fma(m01, dy, m00 * dx));
+            const double gy = kg * fma(m12, dz, fma(m11, dy, m01 * dx));
+            const double gz = kg * fma(m22, dz, fma(m12, dy, m02 * dx));
+            const double wx = vi.x - vj.x, wy = vi.y - vj.y, wz = vi.z - vj.z;
+            const double vr = fma(wz, dz, fma(wy, dy, wx * dx));
+            double Pi = 0.0;
+            if (__double2hiint(vr) < 0) {
+                const double hb = ti.w + tj.w;
+                const double d1 = fma(eta2 * hb, hb, r2);
+                const double rb = ti.x + tj.x;
+                const double Rr = rcp_nr(d1 * rb);
+                const double mu = ((hb * vr) * rb) * Rr;
+                Pi = (mu * fma(beta, mu, -(ti.z + tj.z))) * (d1 * Rr);
+                const long long ab = bits(mu) & 0x7fffffffffffffffLL;
+                mum = ab > mum ? ab : mum;
+            }
+            const double gv = fma(gz, wz, fma(gy, wy, gx * wx));
+            const double g = vj.w * ((ti.y + tj.y) + Pi);
+            sx = fma(g, gx, sx);
+            sy = fma(g, gy, sy);
+            sz = fma(g, gz, sz);
+            const double mgv = vj.w * gv;
+            sp += mgv;
+            sv = fma(mgv, Pi, sv);
+        }
+        const double mu_max = __longlong_as_double(mum);
+        acc[i] = make_double4_32a(-sx, -sy, -sz, fma(ti.y, sp, 0.5 * sv));
+        mumax[i] = mu_max;
+        const double c = cint[i];
+        const KParams& ke = B.kp[slot_inst(B, (int64_t)blockIdx.x * blockDim.x)];
+        dtc = pi.w / (c + 1.2 * (ke.alpha * c + ke.beta * mu_max));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
@@ -308,17 +509,33 @@ void launch_forces(sph_ctx* c, double* dt_out, double* time_inout, cudaStream_t 
     c->launches += 1;
     if (c->prec == PREC_MIXED)
         launch_forces_mx(c, s);
-    else if (c->prec != PREC_FP64_NATIVE)
+    else if (!native_pairs(c))
         launch_forces_df(c, s);
-    else if (n > 0) {
+    else if (n > 0 && c->grad_kind == 1) {
+        c->launches += 2;
+        const Rows R = rows_of(c);
+        auto go = [&](auto iad_fn, auto forces_fn) {
+            iad_fn<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->therm, R, c->iad_a,
+                                           c->iad_b);
+            forces_fn<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->therm, c->kern,
+                                              c->cint, c->iad_a, c->iad_b, R, c->acc, c->mumax,
+                                              c->dt_part);
+        };
+        if (c->kern_kind == KER_WENDLAND) go(k_iad<KER_WENDLAND>, k_forces_iad<KER_WENDLAND>);
+        else if (c->kern_kind == KER_SINC) go(k_iad<KER_SINC>, k_forces_iad<KER_SINC>);
+        else go(k_iad<KER_M4>, k_forces_iad<KER_M4>);
+    } else if (n > 0) {
         c->launches += 1;
-        k_forces<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->therm, c->kern,
-                                         c->cint, rows_of(c), c->acc,
-                                         c->mumax, c->dt_part);
+        auto go = [&](auto forces_fn) {
+            forces_fn<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->therm, c->kern,
+                                              c->cint, rows_of(c), c->acc, c->mumax, c->dt_part);
+        };
+        if (c->kern_kind == KER_WENDLAND) go(k_forces<KER_WENDLAND>);
+        else if (c->kern_kind == KER_SINC) go(k_forces<KER_SINC>);
+        else go(k_forces<KER_M4>);
     }
-    k_dt_finish<<<c->ninst, kThreads, 0, s>>>(c->dt_part, B,
-                                              c->prec == PREC_FP64_NATIVE ? 1 : c->tpp, dt_out,
-                                              time_inout);
+    k_dt_finish<<<c->ninst, kThreads, 0, s>>>(c->dt_part, B, native_pairs(c) ? 1 : c->tpp,
+                                              dt_out, time_inout);
 }
 
 // ------------------------------------------------------------ leapfrog

@@ -1,5 +1,6 @@
 // sph_abi.cu -- the extern "C" entry points declared in include/sph.h:
 // argument checks, context allocation, and the launch sequence of each call.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -65,6 +66,22 @@ sph_status check_params(sph_ctx* c, const sph_params* p) {
         set_err(c, "bad h-search parameters");
         return SPH_E_INVAL;
     }
+    if (p->kernel < KER_M4 || p->kernel > KER_SINC) {
+        set_err(c, "kernel must be 0 (M4), 1 (Wendland C2) or 2 (sinc)");
+        return SPH_E_INVAL;
+    }
+    if (p->kernel == KER_SINC && (p->sinc_n < 2 || p->sinc_n > 12)) {
+        set_err(c, "sinc_n must be in [2, 12]");
+        return SPH_E_INVAL;
+    }
+    if (p->gradients != 0 && p->gradients != 1) {
+        set_err(c, "gradients must be 0 (kernel derivatives) or 1 (IAD)");
+        return SPH_E_INVAL;
+    }
+    if (p->precision == PREC_MIXED && (p->kernel != KER_M4 || p->gradients != 0)) {
+        set_err(c, "the Table 1 variants need precision 0 or 2");
+        return SPH_E_INVAL;
+    }
     if (p->periodic_z && !(p->lz > 0.0)) { set_err(c, "periodic_z needs lz > 0"); return SPH_E_INVAL; }
     if (!(p->cfl > 0.0)) { set_err(c, "cfl must be > 0"); return SPH_E_INVAL; }
     return SPH_OK;
@@ -101,7 +118,7 @@ void free_all(sph_ctx* c) {
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
-                    c->tune_dt, c->roff, c->wctr, c->recs};
+                    c->tune_dt, c->roff, c->wctr, c->recs, c->iad_a, c->iad_b};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -166,7 +183,8 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
     ok = ok && al(&c->therm, N) && al(&c->kern, N) && al(&c->acc, N) &&
          al(&c->pint, N) && al(&c->cint, N) && al(&c->dpk, 3 * N) &&
          al(&c->mdf, N) && al(&c->mpk, 5 * N) &&
-         al(&c->mumax, N) && al(&c->fpos, N) && al(&c->tin, N) &&
+         al(&c->mumax, N) && al(&c->iad_a, N) && al(&c->iad_b, N) &&
+         al(&c->fpos, N) && al(&c->tin, N) &&
          al(&c->hist, 256 * nsb) && al(&c->hist_part, (size_t)scan_parts(256 * nsb) + 1) &&
          al(&c->cells, (size_t)c->cellcap) && al(&c->cell_hmax, (size_t)c->cellcap) &&
          al(&c->nnb, N) && al(&c->ngather, N) && al(&c->rowlen, N) &&
@@ -188,6 +206,50 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
 }  // namespace
 
 namespace sph {
+
+// B_n = 1 / (4 pi int_0^2 q^2 (sin x / x)^n dq), x = pi q / 2, by 16-point
+// Gauss-Legendre quadrature on 64 equal panels (the integrand is analytic, so
+// this is exact to rounding). The nodes are the roots of the Legendre
+// polynomial P_16, found by Newton's method on its three-term recurrence
+// (k P_k = (2k - 1) t P_{k-1} - (k - 1) P_{k-2}) from the Chebyshev-like
+// guesses cos(pi (i - 1/4) / (m + 1/2)); the weights are
+// 2 / ((1 - t^2) P_16'(t)^2).
+double sinc_norm(int n) {
+    constexpr int m = 16, panels = 64;
+    double t[m], w[m];
+    for (int i = 0; i < m; ++i) {
+        double z = cos(kPi * (i + 0.75) / (m + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= m; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = m * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-17) break;
+        }
+        t[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    const double hp = 2.0 / panels;
+    double sum = 0.0;
+    for (int a = 0; a < panels; ++a) {
+        double ps = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double q = hp * (a + 0.5 * (t[i] + 1.0));
+            const double x = 0.5 * kPi * q;
+            const double sx = sin(x) / x;
+            double pw = 1.0;
+            for (int e = 0; e < n; ++e) pw *= sx;
+            ps += w[i] * q * q * pw;
+        }
+        sum += 0.5 * hp * ps;
+    }
+    return 1.0 / (4.0 * kPi * sum);
+}
 
 // Batch-of-one descriptors for a single problem of n particles, written on the
 // stream (kernel arguments are captured at launch, so back-to-back calls with
@@ -218,7 +280,9 @@ void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s)
     c->cext = n;
     c->ninst = 1;
     c->prec = kp.precision;
-    c->tpp = kp.precision == PREC_FP64_NATIVE ? 1 : kp.pair_threads;
+    c->kern_kind = kp.kernel;
+    c->grad_kind = kp.gradients;
+    c->tpp = native_pairs(c) ? 1 : kp.pair_threads;
     const int64_t nblk = (n + kSlotAlign - 1) / kSlotAlign;
     const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((nblk + kThreads - 1) / kThreads, 1), 1024);
     c->launches += 1;
@@ -546,8 +610,11 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const
         sph_status st = check_params(c, &params[k]);
         if (st != SPH_OK) return st;
         if (params[k].precision != params[0].precision ||
-            params[k].pair_threads != params[0].pair_threads) {
-            set_err(c, "instances of a batch must share precision and pair_threads");
+            params[k].pair_threads != params[0].pair_threads ||
+            params[k].kernel != params[0].kernel || params[k].gradients != params[0].gradients ||
+            (params[k].kernel == KER_SINC && params[k].sinc_n != params[0].sinc_n)) {
+            set_err(c, "instances of a batch must share precision, pair_threads, kernel, "
+                       "gradients and sinc_n");
             return SPH_E_INVAL;
         }
         if (counts[k] < 0) {
@@ -620,7 +687,9 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const
     c->cext = ext;
     c->ninst = ninst;
     c->prec = params[0].precision;
-    c->tpp = c->prec == PREC_FP64_NATIVE ? 1 : kpi[0].pair_threads;
+    c->kern_kind = params[0].kernel;
+    c->grad_kind = params[0].gradients;
+    c->tpp = native_pairs(c) ? 1 : kpi[0].pair_threads;
     return SPH_OK;
 }
 

@@ -66,10 +66,22 @@ struct Grid {
 };
 
 // Parameters copied by value into kernels.
+// kernel / gradients select the Table 1 variants; wnorm and dnorm are the
+// kernel's normalisations, W = wnorm h^-3 g(q) and dW/dr = dnorm h^-4 f(q)
+// with the shapes g and f of physics.cu.
 struct KParams {
     int eos, n_target, n_tol, max_h_iter, periodic_z, precision, pair_threads, defer_lanes;
+    int kernel, gradients, sinc_n;
     double rho0, c0, gamma, alpha, beta, eta2, cfl, lz, cell_scale;
+    double wnorm, dnorm;
 };
+
+enum { KER_M4 = 0, KER_WENDLAND = 1, KER_SINC = 2 };
+enum { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP64_NATIVE = 2 };
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInvPi = 0.31830988618379067154;  // 1/pi
+// B_n of the sinc kernel (host; Gauss-Legendre quadrature)
+double sinc_norm(int n);
 
 // Instances of a batch. Instance k holds the internal slots
 // [ioff[k], ioff[k] + icnt[k]); ioff[k] is a multiple of kSlotAlign and the
@@ -114,6 +126,18 @@ inline KParams kparams(const sph_params* p) {
     k.cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 1.0;
     k.pair_threads = p->pair_threads > 0 ? p->pair_threads : (p->precision == 1 ? 2 : 1);
     k.defer_lanes = p->defer_lanes > 0 ? p->defer_lanes : 16;
+    k.kernel = p->kernel;
+    k.gradients = p->gradients;
+    k.sinc_n = p->sinc_n;
+    if (p->kernel == KER_WENDLAND) {
+        k.wnorm = 21.0 / (16.0 * kPi);
+        k.dnorm = 105.0 / (16.0 * kPi);
+    } else if (p->kernel == KER_SINC) {
+        k.wnorm = sinc_norm(p->sinc_n);
+        k.dnorm = k.wnorm * (0.5 * kPi);
+    } else {
+        k.wnorm = k.dnorm = kInvPi;
+    }
     return k;
 }
 
@@ -127,6 +151,7 @@ struct sph_ctx {
     int64_t ntot;           // particles of the current batch
     int ninst, maxinst;     // instances of the current batch / capacity
     int prec;               // precision of the current batch
+    int kern_kind, grad_kind;  // Table 1 variants of the current batch (KER_*, 0/1)
     int tpp;                // lanes per particle of the pair kernels (1, 2, 4, 8)
     int32_t* blk;           // instance of each block of kSlotAlign slots
     int64_t *ioff, *icnt, *coff;  // per instance: first slot, particles, first caller index
@@ -145,6 +170,8 @@ struct sph_ctx {
     float2* mdf;            // mass as a float pair
     float4* mpk;            // 5 per particle: pack of the mixed-precision pair kernels
     double* mumax;
+    double4_32a* iad_a;     // IAD matrices C_i: (xx, xy, xz, yy) ...
+    double2* iad_b;         // ... and (yz, zz)
     float4* fpos;
     float* tin;
     int32_t* order[2];
@@ -193,6 +220,12 @@ struct sph_ctx {
 namespace sph {
 
 inline Batch batch_of(const sph_ctx* c) { return Batch{c->blk, c->ioff, c->icnt, c->grid, c->kpi}; }
+
+// The pair sums run in the native FP64 kernels: precision 2, or any Table 1
+// variant (those exist only there).
+inline bool native_pairs(const sph_ctx* c) {
+    return c->prec == PREC_FP64_NATIVE || c->kern_kind != KER_M4 || c->grad_kind != 0;
+}
 
 // Rows of S_i for the pair kernels: the row slab unless a row overflowed it
 // (device flag IF_SLAB_OVF), in which case the CSR built by the fallback.
@@ -263,7 +296,6 @@ void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s);
 // ---- physics_df.cu (precision 0)
 void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s);
 void launch_forces_df(sph_ctx* c, cudaStream_t s);
-enum { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP64_NATIVE = 2 };
 // ---- physics_mixed.cu (precision 1)
 void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s);
 void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s);
