@@ -67,8 +67,8 @@ def variant_flops(kernel, gradients, sinc_n):
 # only while the kernel's sources hash to the version that was captured.
 FORCES_TRAFFIC = {
     "fp64": {"sources": ("physics_df.cu", "df.cuh"),
-             "sha1": "3826e881eb7383f3adb7800be141d99ac27de662",
-             "bytes": 222.38e6 + 15.01e6, "pairs": 34640886},
+             "sha1": "aa218733e277dec6bb68c9f902f13106a953fc45",
+             "bytes": 222.47e6 + 11.18e6, "pairs": 34640886},
     "mixed": {"sources": ("physics_mixed.cu", "df.cuh"),
               "sha1": "98df40880c6a6cb19ee02be786496a8504e8c592",
               "bytes": 216.04e6 + 11.42e6, "pairs": 34640886},
@@ -423,20 +423,23 @@ def _run_ensemble(args, B, dev, stream):
     }
 
 
-VARIANTS = (("M4, kernel derivatives, native FP64", 0, 0, 5),
-            ("Wendland C2, kernel derivatives", 1, 0, 5),
-            ("sinc n=5, kernel derivatives", 2, 0, 5),
-            ("M4, IAD gradients", 0, 1, 5),
-            ("Wendland C2, IAD gradients", 1, 1, 5))
+# (name, kernel, gradients, sinc_n, precision): kernel derivatives with the M4
+# or Wendland kernel run in double-float at precision 0 and on the FP64 pipe
+# at precision 2; the sinc kernel and IAD always take the FP64-pipe kernels.
+VARIANTS = (("M4, kernel derivatives, FP64 pipe (precision 2)", 0, 0, 5, 2),
+            ("Wendland C2, kernel derivatives, double-float (precision 0)", 1, 0, 5, 0),
+            ("Wendland C2, kernel derivatives, FP64 pipe (precision 2)", 1, 0, 5, 2),
+            ("sinc n=5, kernel derivatives, FP64 pipe", 2, 0, 5, 0),
+            ("M4, IAD gradients, FP64 pipe", 0, 1, 5, 0),
+            ("Wendland C2, IAD gradients, FP64 pipe", 1, 1, 5, 0))
 
 
 def run_variants(args, B, dev, fp64_peak):
     """The Table 1 variants on the benchmark workload: each a separate run of
     --variant-steps steps from the initial conditions (after one untimed
-    step), all in the native FP64 pair kernels (the M4 line is the same path
-    with the default kernel, for comparison). Roofline of the force phase
-    (k_forces / k_iad + k_forces_iad, with k_dt_finish) against the FP64
-    FMA-chain probe, from the counted flops of variant_flops."""
+    step), with the pair kernels VARIANTS names. Roofline of the force phase
+    (the force kernel, with k_volume + k_iad for IAD and k_dt_finish) against
+    the FP64 FMA-chain probe, from the counted flops of variant_flops."""
     import numpy as np
     import torch
     s, base = make_workload(args)
@@ -446,9 +449,9 @@ def run_variants(args, B, dev, fp64_peak):
     ic = {k: arr[k].clone() for k in B.STATE_FIELDS}
     stream = torch.cuda.current_stream(dev)
     out = []
-    for name, kernel, grads, sn in VARIANTS:
+    for name, kernel, grads, sn, prec in VARIANTS:
         prm = ics_params_copy(base)
-        prm.precision = 2
+        prm.precision = prec
         prm.kernel, prm.gradients, prm.sinc_n = kernel, grads, sn
 
         def reset():
@@ -484,8 +487,11 @@ def run_variants(args, B, dev, fp64_peak):
                     "value": n * args.variant_steps / (ms * 1e-3), "unit": UNIT,
                     "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
                     "status": B.STATUS_NAMES.get(st),
-                    "roofline": {"bound": "alu", "kernel": "k_iad + k_forces_iad" if grads
-                                 else "k_forces", "achieved": ach, "peak": fp64_peak / 1e12,
+                    "precision": prec,
+                    "roofline": {"bound": "alu", "kernel": "k_volume + k_iad + k_forces_iad"
+                                 if grads else ("k_forces_df" if prec == 0 and kernel != 2
+                                                else "k_forces"),
+                                 "achieved": ach, "peak": fp64_peak / 1e12,
                                  "unit": "TFLOP/s", "frac": ach / (fp64_peak / 1e12),
                                  "flops_per_launch": flops,
                                  "counted": {"pair": base_f, "pair_av": av_f,

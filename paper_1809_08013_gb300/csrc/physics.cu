@@ -322,13 +322,26 @@ k_forces(int64_t n, Batch B, const double4_32a* __restrict__ posh,
 }
 
 // ------------------------------------------------------------ IAD (Table 1)
-// tau_i = sum_{j in N_i} (m_j / rho_j) W(r_ij, h_i) (r_j - r_i)(r_j - r_i)^T and
-// C_i = tau_i^-1 by the adjugate (C_i = 0 when det tau_i = 0). rho_j comes
-// from the force pack (therm.x = rho / 2), so this runs after the density.
+// Volume elements V_i = m_i / rho_i, once per particle (rho from the force
+// pack, therm.x = rho / 2), so that the matrix pass reads one number per
+// neighbour and divides nowhere.
+__global__ void __launch_bounds__(kThreads)
+k_volume(int64_t n, Batch B, const double4_32a* __restrict__ velm,
+         const double4_32a* __restrict__ therm, double* __restrict__ vol) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int inst = slot_inst(B, i);
+    if (!slot_real(B, inst, i)) return;
+    vol[i] = velm[i].w / (2.0 * therm[i].x);
+}
+
+// tau_i = sum_{j in N_i} V_j W(r_ij, h_i) (r_j - r_i)(r_j - r_i)^T and
+// C_i = tau_i^-1 by the adjugate (C_i = 0 when det tau_i = 0); after the
+// density (V_j needs rho_j).
 template <int KER>
 __global__ void __launch_bounds__(kThreads)
 k_iad(int64_t n, Batch B, const double4_32a* __restrict__ posh,
-      const double4_32a* __restrict__ velm, const double4_32a* __restrict__ therm, Rows R,
+      const double* __restrict__ vol, Rows R,
       double4_32a* __restrict__ ca, double2* __restrict__ cb) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int inst = slot_inst(B, (int64_t)blockIdx.x * blockDim.x);
@@ -351,7 +364,7 @@ k_iad(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         if (per) dz = wrap_z(dz, half_bits, lz);
         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
         const double q = bits(r2) > 0 ? r2 * rsqrt_nr(r2) * hinv : 0.0;
-        const double w = (velm[j].w / (2.0 * therm[j].x)) * kw<KER>(q, sn);
+        const double w = __ldg(&vol[j]) * kw<KER>(q, sn);
         const double wx = w * dx, wy = w * dy;
         t0 = fma(wx, dx, t0);
         t1 = fma(wx, dy, t1);
@@ -512,11 +525,11 @@ void launch_forces(sph_ctx* c, double* dt_out, double* time_inout, cudaStream_t 
     else if (!native_pairs(c))
         launch_forces_df(c, s);
     else if (n > 0 && c->grad_kind == 1) {
-        c->launches += 2;
+        c->launches += 3;
         const Rows R = rows_of(c);
+        k_volume<<<nb, kThreads, 0, s>>>(n, B, c->velm[b], c->therm, c->vol);
         auto go = [&](auto iad_fn, auto forces_fn) {
-            iad_fn<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->therm, R, c->iad_a,
-                                           c->iad_b);
+            iad_fn<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->vol, R, c->iad_a, c->iad_b);
             forces_fn<<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->therm, c->kern,
                                               c->cint, c->iad_a, c->iad_b, R, c->acc, c->mumax,
                                               c->dt_part);

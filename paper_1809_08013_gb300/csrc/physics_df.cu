@@ -50,6 +50,28 @@ __device__ __forceinline__ df dw_shape(df q) {
     return q.hi < 1.0f ? fin : (q.hi < 2.0f ? fout : zero);
 }
 
+// Wendland C2 shapes (Table 1): g = (1 - q/2)^4 (1 + 2q), f = -q (1 - q/2)^3,
+// zero from q = 2 on; the normalisations 21/(16 pi) and 105/(16 pi) are
+// applied by the caller.
+template <int KER>
+__device__ __forceinline__ df w_shape_k(df q) {
+    if (KER == KER_M4) return w_shape(q);
+    const df t = dfl::addf(dfl::scale2(dfl::neg(q), 0.5f), 1.0f);
+    const df t2 = dfl::sqr(t);
+    const df g = dfl::mul(dfl::sqr(t2), dfl::addf(dfl::scale2(q, 2.0f), 1.0f));
+    const df zero = {0.0f, 0.0f};
+    return q.hi < 2.0f ? g : zero;
+}
+
+template <int KER>
+__device__ __forceinline__ df dw_shape_k(df q) {
+    if (KER == KER_M4) return dw_shape(q);
+    const df t = dfl::addf(dfl::scale2(dfl::neg(q), 0.5f), 1.0f);
+    const df f = dfl::neg(dfl::mul(q, dfl::mul(dfl::sqr(t), t)));
+    const df zero = {0.0f, 0.0f};
+    return q.hi < 2.0f ? f : zero;
+}
+
 // the mass as a double-float
 __device__ __forceinline__ df ldm(const float2* p, int64_t k) {
     const float2 v = __ldg(&p[k]);
@@ -74,7 +96,9 @@ __device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, d
 
 // ------------------------------------------------------------ density
 // T lanes per particle: lane s of particle i takes row entries s, s + T, ...
-template <bool FUSE, int T>
+// KER: the M4 spline or the Wendland C2 kernel (the other Table 1 variants
+// run in physics.cu).
+template <bool FUSE, int T, int KER>
 __global__ void __launch_bounds__(kThreads)
 k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const float2* __restrict__ mdf, const double* __restrict__ ue,
@@ -111,7 +135,7 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         df w = {1.0f, 0.0f};  // coincident particles: q = 0
         if (r2.hi > 0.0f) {
             const df q = dfl::mul(dfl::mul(r2, dfl::rsqrt(r2)), Hi);
-            w = w_shape(q);
+            w = w_shape_k<KER>(q);
         }
         acc = dfl::add(acc, dfl::mul(mj, w));
     }
@@ -121,7 +145,7 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         if (!act || sub != 0) return;
     }
     const double hinv = 1.0 / pi.w;
-    const double sigma = hinv * hinv * hinv * kInvPiD;
+    const double sigma = hinv * hinv * hinv * (KER == KER_M4 ? kInvPiD : kp.wnorm);
     const double rho = dfl::to_double(acc) * sigma;
     if (FUSE) {
         double p, c;
@@ -143,9 +167,14 @@ static void density_df_t(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
-    k_density_df<FUSE, T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->mdf, c->ue[b],
-                                                  rows_of(c),
-                                                  c->therm, c->kern, c->dpk, c->pint, c->cint);
+    if (c->kern_kind == KER_WENDLAND)
+        k_density_df<FUSE, T, KER_WENDLAND><<<nb, kThreads, 0, s>>>(
+            n, batch_of(c), c->posh[b], c->mdf, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
+            c->pint, c->cint);
+    else
+        k_density_df<FUSE, T, KER_M4><<<nb, kThreads, 0, s>>>(
+            n, batch_of(c), c->posh[b], c->mdf, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
+            c->pint, c->cint);
 }
 
 template <bool FUSE>
@@ -169,7 +198,7 @@ void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
 // Definitions as in physics.cu; algebra: Fbar = (0.5/pi)(f(q_i)/h_i^4 +
 // f(q_j)/h_j^4)/r, one shared reciprocal R = 1/((r^2 + eta2 hb^2) rhob) for the
 // viscosity, mu = hb v.r rhob R, 1/rhob = (r^2 + eta2 hb^2) R.
-template <int T>
+template <int T, int KER>
 __global__ void __launch_bounds__(kThreads, 3)
 k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
@@ -196,7 +225,7 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const long long half_bits = bitsd(0.5 * kp.lz);
         const bool per = kp.periodic_z != 0;
         const double lz = kp.lz;
-        const df c_half_pi = dfl::from_double_fp64(0.5 * kInvPiD);
+        const df c_half_pi = dfl::from_double_fp64(0.5 * (KER == KER_M4 ? kInvPiD : kp.dnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
         for (int e = sub; e < len; e += T) {
@@ -213,8 +242,8 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             if (!(r2.hi > 0.0f)) continue;  // coincident particles exert no force
             const df rinv = dfl::rsqrt(r2);
             const df r = dfl::mul(r2, rinv);
-            const df fa = dw_shape(dfl::mul(r, Hi));
-            const df fb = dw_shape(dfl::mul(r, df{b0.x, b0.y}));
+            const df fa = dw_shape_k<KER>(dfl::mul(r, Hi));
+            const df fb = dw_shape_k<KER>(dfl::mul(r, df{b0.x, b0.y}));
             const df Fb = dfl::mul(dfl::add(dfl::mul(Ki, fa), dfl::mul(df{b0.z, b0.w}, fb)),
                                    dfl::mul(rinv, c_half_pi));
             const df WX = dfl::from_double(vi.x - vj.x), WY = dfl::from_double(vi.y - vj.y);
@@ -283,9 +312,14 @@ static void forces_df_t(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
-    k_forces_df<T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->velm[b], c->dpk,
-                                           c->mdf, c->cint, rows_of(c),
-                                           c->acc, c->mumax, c->dt_part);
+    if (c->kern_kind == KER_WENDLAND)
+        k_forces_df<T, KER_WENDLAND><<<nb, kThreads, 0, s>>>(
+            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->mdf, c->cint, rows_of(c), c->acc,
+            c->mumax, c->dt_part);
+    else
+        k_forces_df<T, KER_M4><<<nb, kThreads, 0, s>>>(
+            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->mdf, c->cint, rows_of(c), c->acc,
+            c->mumax, c->dt_part);
 }
 
 void launch_forces_df(sph_ctx* c, cudaStream_t s) {

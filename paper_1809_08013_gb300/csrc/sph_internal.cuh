@@ -172,6 +172,7 @@ struct sph_ctx {
     double* mumax;
     double4_32a* iad_a;     // IAD matrices C_i: (xx, xy, xz, yy) ...
     double2* iad_b;         // ... and (yz, zz)
+    double* vol;            // IAD volume elements m / rho
     float4* fpos;
     float* tin;
     int32_t* order[2];
@@ -221,10 +222,11 @@ namespace sph {
 
 inline Batch batch_of(const sph_ctx* c) { return Batch{c->blk, c->ioff, c->icnt, c->grid, c->kpi}; }
 
-// The pair sums run in the native FP64 kernels: precision 2, or any Table 1
-// variant (those exist only there).
+// The pair sums run in the native FP64 kernels: precision 2, the sinc kernel
+// or IAD gradients (those variants exist only there; the M4 and Wendland C2
+// kernels with kernel derivatives also run in double-float).
 inline bool native_pairs(const sph_ctx* c) {
-    return c->prec == PREC_FP64_NATIVE || c->kern_kind != KER_M4 || c->grad_kind != 0;
+    return c->prec == PREC_FP64_NATIVE || c->kern_kind == KER_SINC || c->grad_kind != 0;
 }
 
 // Rows of S_i for the pair kernels: the row slab unless a row overflowed it

@@ -3,6 +3,8 @@ gradients) and of the Section 4.1.1 pressure initial conditions with the CPU
 oracle: FP64 fields within 1e-12 normwise per call and per step from
 identical inputs, bit-exact h; the variants run alone and batched with the
 same bits; invalid combinations are rejected before any launch."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -109,8 +111,42 @@ def test_variant_one_step_matches_oracle(B, orc, name, var):
     assert abs(host(arr["dt"])[0] - ex["dt"]) <= TOL_FP64 * ex["dt"]
 
 
+@pytest.mark.parametrize("lanes", [1, 4])
+@pytest.mark.parametrize("name", INPUTS)
+def test_wendland_double_float_path(B, orc, name, lanes):
+    # Wendland C2 with kernel derivatives at precision 0 runs in the
+    # double-float kernels (like M4): per call and one step against the oracle
+    s, prm0, o = oracle_of(orc, name, (1, 0, 5), precision=0)
+    prm = dataclasses.replace(prm0, pair_threads=lanes)  # the cached parameters stay as they are
+    ctx = B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.build_neighbors(prm, arr)
+    ctx.density(prm, arr)
+    assert normwise(host(arr["rho"]), o["rho"]) <= TOL_FP64
+    for k in ("rho", "p", "c"):
+        arr[k].copy_(torch.from_numpy(o[k]))
+    ctx.forces(prm, arr)
+    assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
+    _check_forces(arr, o, B)
+    st_o, ex = orc.step(prm, s, nsteps=1)
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=1)
+    assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
+    for k in ("rho", "p", "c"):
+        assert normwise(host(arr[k]), ex[k]) <= TOL_FP64, k
+    for k in ("ax", "ay", "az", "du"):
+        assert scaled(host(arr[k]), ex[k], o[SCALE[k]]) <= TOL_FP64, k
+    # and it is not the native FP64 kernel (different rounding, same values)
+    prm.precision = 2
+    arr2 = B.alloc_arrays(s)
+    ctx.step(prm, arr2, nsteps=1)
+    ctx.sync()
+    assert not np.array_equal(host(arr2["ax"]), host(arr["ax"]))
+
+
 def test_variant_with_precision_0_runs_the_fp64_kernels(B):
-    # any variant takes the native FP64 pair kernels: precision 0 and 2 give the same bits
+    # IAD (and the sinc kernel) take the native FP64 pair kernels: precision 0
+    # and 2 give the same bits
     s, prm = _input("patch_ragged_av")
     prm.kernel, prm.gradients = 1, 1
     out = []
