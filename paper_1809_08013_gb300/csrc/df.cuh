@@ -131,6 +131,36 @@ __device__ __forceinline__ df from_double(double d) {
     return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
 }
 
+// ---- Exact coordinate differences without the FP64 pipe.
+// Once per step each coordinate becomes a 64-bit fixed-point number
+// X = rint(x 2^k), with k per instance such that |X| < 2^61 (x is exact in it
+// wherever ulp(x) >= 2^-k; elsewhere rounded by at most 2^-(k+1), a
+// negligible absolute error), split as X = c2 2^42 + c1 2^21 + c0 with c2
+// signed and c1, c0 in [0, 2^21). The chunks are stored pre-scaled as floats
+// c2 2^(42-k), c1 2^(21-k), c0 2^-k, each exact. For two particles the three
+// chunkwise differences are exact floats too (at most 21 significant bits),
+// and their double-float sum is x_i - x_j to within ~2^-48 of its size: the
+// only rounding of the whole difference.
+struct fx3 {
+    float c2, c1, c0;
+};
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// k in [-60, 100] (so every scaled chunk is a normal float)
+__device__ __forceinline__ fx3 to_fx(double x, int k) {
+    const double sc = __longlong_as_double((long long)(1023 + k) << 52);  // 2^k
+    const long long X = __double2ll_rn(x * sc);
+    return {(float)(X >> 42) * pow2f(42 - k), (float)((X >> 21) & 0x1fffffLL) * pow2f(21 - k),
+            (float)(X & 0x1fffffLL) * pow2f(-k)};
+}
+
+// The double-float value of the exact chunk differences a2 + a1 + a0.
+__device__ __forceinline__ df fx_sum(float a2, float a1, float a0) {
+    const df s = two_sum(a2, a1);
+    return addf(s, a0);
+}
+
 // Per-particle conversion back to FP64 (two conversions and one FP64 add).
 __device__ __forceinline__ double to_double(df x) { return (double)x.hi + (double)x.lo; }
 

@@ -3,13 +3,16 @@
 //
 // Same definitions as physics.cu (cubic-spline gather density; momentum and
 // energy with Monaghan viscosity over S_i; time-step candidate). GB300 issues
-// FP64 at 1/64 of the FP32 rate; here the FP64 pipe only forms the six
-// coordinate and velocity differences of a pair (x_i - x_j is the one place
-// where 53-bit inputs meet), each difference is split exactly enough into a
-// float pair by integer operations, and everything else -- r^2, 1/r, the
-// kernel polynomials, the viscosity, the sums -- runs in ~48-bit double-float
-// (df.cuh). Per-particle inputs (1/h, 1/h^4, p/rho^2, h/2, rho/2, alpha c/2,
-// m) are converted once per step into a float pack read for every neighbour.
+// FP64 at 1/64 of the FP32 rate, so the pair loops keep off the FP64 pipe
+// almost entirely. Position differences come from the exact fixed-point
+// chunks of each particle's coordinates (dfl::to_fx, written once per step):
+// three exact FP32 subtractions and one double-float sum per component. Only
+// the velocity differences of the force kernel are formed in FP64 and then
+// split into float pairs by integer operations. Everything else -- r^2, 1/r,
+// the kernel polynomials, the viscosity, the sums -- runs in ~48-bit
+// double-float (df.cuh). Per-particle inputs (1/h, 1/h^4, p/rho^2, h/2, rho/2,
+// alpha c/2, m) are converted once per step into float packs read for every
+// neighbour.
 #include <math_constants.h>
 
 #include "df.cuh"
@@ -22,13 +25,6 @@ using dfl::df;
 namespace {
 
 constexpr double kInvPiD = 0.31830988618379067154;
-
-__device__ __forceinline__ long long bitsd(double v) { return __double_as_longlong(v); }
-
-__device__ __forceinline__ double wrap_z_d(double dz, long long half_bits, double lz) {
-    if ((bitsd(dz) & 0x7fffffffffffffffLL) > half_bits) dz -= copysign(lz, dz);
-    return dz;
-}
 
 // pi h^3 W as a function of q >= 0 (cubic spline).
 __device__ __forceinline__ df w_shape(df q) {
@@ -72,10 +68,18 @@ __device__ __forceinline__ df dw_shape_k(df q) {
     return q.hi < 2.0f ? f : zero;
 }
 
-// the mass as a double-float
-__device__ __forceinline__ df ldm(const float2* p, int64_t k) {
-    const float2 v = __ldg(&p[k]);
-    return {v.x, v.y};
+// Minimum image along z on the chunk differences (dfl::to_fx): when |dz| >
+// lz/2 (decided on the leading chunk, which is within ~2^-18 |x|max of dz and
+// so unambiguous for any pair of a row), subtract sign(dz) lz chunk by chunk;
+// each chunk difference stays exact.
+__device__ __forceinline__ void wrap_fx(float& z2, float& z1, float& z0, float hlz, float L2,
+                                        float L1, float L0) {
+    if (fabsf(z2) > hlz) {
+        const float sg = copysignf(1.0f, z2);
+        z2 = __fsub_rn(z2, sg * L2);
+        z1 = __fsub_rn(z1, sg * L1);
+        z0 = __fsub_rn(z0, sg * L0);
+    }
 }
 
 __device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, double& p, double& c) {
@@ -101,7 +105,7 @@ __device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, d
 template <bool FUSE, int T, int KER>
 __global__ void __launch_bounds__(kThreads)
 k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
-             const float2* __restrict__ mdf, const double* __restrict__ ue,
+             const float4* __restrict__ xpk, const double* __restrict__ ue,
              Rows R, double4_32a* __restrict__ therm,
              double2* __restrict__ kern, float4* __restrict__ dpk, double* __restrict__ pint,
              double* __restrict__ cint) {
@@ -119,18 +123,21 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     pi = posh[i];
     const double hinv = 1.0 / pi.w;
     const df Hi = dfl::from_double_fp64(hinv);
-    const long long half_bits = bitsd(0.5 * kp.lz);
+    const Grid& g = B.grid[inst];
     const bool per = kp.periodic_z != 0;
-    const double lz = kp.lz;
-    if (sub == 0) acc = ldm(mdf, i);  // self term m_i W(0, h_i): shape 1
+    const float hlz = g.halflzf, L2 = g.lzc[0], L1 = g.lzc[1], L0 = g.lzc[2];
+    const float4 I0 = xpk[3 * i], I1 = xpk[3 * i + 1], I2 = xpk[3 * i + 2];
+    if (sub == 0) acc = df{I0.w, I1.w};  // self term m_i W(0, h_i): shape 1
     for (int e = sub; e < len; e += T) {
         const int j = __ldg(&ent[e]);
-        const double4_32a pj = posh[j];
-        const df mj = ldm(mdf, j);
-        double dz = pi.z - pj.z;
-        if (per) dz = wrap_z_d(dz, half_bits, lz);
-        const df X = dfl::from_double(pi.x - pj.x), Y = dfl::from_double(pi.y - pj.y);
-        const df Z = dfl::from_double(dz);
+        const float4 J0 = __ldg(&xpk[3 * j]), J1 = __ldg(&xpk[3 * j + 1]);
+        const float4 J2 = __ldg(&xpk[3 * j + 2]);
+        const df mj = {J0.w, J1.w};
+        float z2 = __fsub_rn(I0.z, J0.z), z1 = __fsub_rn(I1.z, J1.z), z0 = __fsub_rn(I2.z, J2.z);
+        if (per) wrap_fx(z2, z1, z0, hlz, L2, L1, L0);
+        const df X = dfl::fx_sum(__fsub_rn(I0.x, J0.x), __fsub_rn(I1.x, J1.x), __fsub_rn(I2.x, J2.x));
+        const df Y = dfl::fx_sum(__fsub_rn(I0.y, J0.y), __fsub_rn(I1.y, J1.y), __fsub_rn(I2.y, J2.y));
+        const df Z = dfl::fx_sum(z2, z1, z0);
         const df r2 = dfl::add(dfl::add(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
         df w = {1.0f, 0.0f};  // coincident particles: q = 0
         if (r2.hi > 0.0f) {
@@ -169,11 +176,11 @@ static void density_df_t(sph_ctx* c, cudaStream_t s) {
     const int b = c->cur;
     if (c->kern_kind == KER_WENDLAND)
         k_density_df<FUSE, T, KER_WENDLAND><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->mdf, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
+            n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
             c->pint, c->cint);
     else
         k_density_df<FUSE, T, KER_M4><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->mdf, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
+            n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
             c->pint, c->cint);
 }
 
@@ -202,7 +209,7 @@ template <int T, int KER>
 __global__ void __launch_bounds__(kThreads, 3)
 k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
-            const float2* __restrict__ mdf, const double* __restrict__ cint,
+            const float4* __restrict__ xpk, const double* __restrict__ cint,
             Rows R,
             double4_32a* __restrict__ acc, double* __restrict__ mumax,
             double* __restrict__ dt_part) {
@@ -217,27 +224,29 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     df mumx = {0.f, 0.f};
     if (act) {
         const KParams& kp = B.kp[inst];
-        const double4_32a pi = posh[i];
         const double4_32a vi = velm[i];
+        const float4 I0 = xpk[3 * i], I1 = xpk[3 * i + 1], I2 = xpk[3 * i + 2];
         const float4 a0 = dpk[3 * i], a1 = dpk[3 * i + 1], a2 = dpk[3 * i + 2];
         const df Hi = {a0.x, a0.y}, Ki = {a0.z, a0.w}, Ai = {a1.x, a1.y}, hhi = {a1.z, a1.w};
         const df rhi = {a2.x, a2.y}, cai = {a2.z, a2.w};
-        const long long half_bits = bitsd(0.5 * kp.lz);
+        const Grid& gr = B.grid[inst];
         const bool per = kp.periodic_z != 0;
-        const double lz = kp.lz;
+        const float hlz = gr.halflzf, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
         const df c_half_pi = dfl::from_double_fp64(0.5 * (KER == KER_M4 ? kInvPiD : kp.dnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
         for (int e = sub; e < len; e += T) {
             const int j = __ldg(&ent[e]);
-            const double4_32a pj = posh[j];
+            const float4 J0 = __ldg(&xpk[3 * j]), J1 = __ldg(&xpk[3 * j + 1]);
+            const float4 J2 = __ldg(&xpk[3 * j + 2]);
             const double4_32a vj = velm[j];
             const float4 b0 = __ldg(&dpk[3 * j]), b1 = __ldg(&dpk[3 * j + 1]);
             const float4 b2 = __ldg(&dpk[3 * j + 2]);
-            double dz = pi.z - pj.z;
-            if (per) dz = wrap_z_d(dz, half_bits, lz);
-            const df X = dfl::from_double(pi.x - pj.x), Y = dfl::from_double(pi.y - pj.y);
-            const df Z = dfl::from_double(dz);
+            float z2 = __fsub_rn(I0.z, J0.z), z1 = __fsub_rn(I1.z, J1.z), z0 = __fsub_rn(I2.z, J2.z);
+            if (per) wrap_fx(z2, z1, z0, hlz, L2, L1, L0);
+            const df X = dfl::fx_sum(__fsub_rn(I0.x, J0.x), __fsub_rn(I1.x, J1.x), __fsub_rn(I2.x, J2.x));
+            const df Y = dfl::fx_sum(__fsub_rn(I0.y, J0.y), __fsub_rn(I1.y, J1.y), __fsub_rn(I2.y, J2.y));
+            const df Z = dfl::fx_sum(z2, z1, z0);
             const df r2 = dfl::add(dfl::add(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
             if (!(r2.hi > 0.0f)) continue;  // coincident particles exert no force
             const df rinv = dfl::rsqrt(r2);
@@ -261,7 +270,7 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
                 Pi = dfl::mul(dfl::mul(mu, t), dfl::mul(d1, R));
                 if (-mu.hi > mumx.hi) mumx = dfl::neg(mu);
             }
-            const df mF = dfl::mul(ldm(mdf, j), Fb);
+            const df mF = dfl::mul(df{J0.w, J1.w}, Fb);
             const df g = dfl::mul(mF, dfl::add(dfl::add(Ai, df{b1.x, b1.y}), Pi));
             sx = dfl::add(sx, dfl::mul(g, X));
             sy = dfl::add(sy, dfl::mul(g, Y));
@@ -314,11 +323,11 @@ static void forces_df_t(sph_ctx* c, cudaStream_t s) {
     const int b = c->cur;
     if (c->kern_kind == KER_WENDLAND)
         k_forces_df<T, KER_WENDLAND><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->mdf, c->cint, rows_of(c), c->acc,
+            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
             c->mumax, c->dt_part);
     else
         k_forces_df<T, KER_M4><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->mdf, c->cint, rows_of(c), c->acc,
+            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
             c->mumax, c->dt_part);
 }
 

@@ -58,6 +58,18 @@ void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s) {
         c->ue[1 - b], c->order[1 - b]);
 }
 
+// Pack of the double-float pair kernels for particle k: the fixed-point chunks
+// of its position (dfl::to_fx, exponent of its instance) and its mass,
+//   xpk[3k] = (x.c2, y.c2, z.c2, m.hi), xpk[3k+1] = (x.c1, y.c1, z.c1, m.lo),
+//   xpk[3k+2] = (x.c0, y.c0, z.c0, 0).
+__device__ __forceinline__ void write_xpk(float4* __restrict__ xpk, int64_t k, const double4_32a& p,
+                                          const dfl::df& m, int fxk) {
+    const dfl::fx3 X = dfl::to_fx(p.x, fxk), Y = dfl::to_fx(p.y, fxk), Z = dfl::to_fx(p.z, fxk);
+    xpk[3 * k + 0] = make_float4(X.c2, Y.c2, Z.c2, m.hi);
+    xpk[3 * k + 1] = make_float4(X.c1, Y.c1, Z.c1, m.lo);
+    xpk[3 * k + 2] = make_float4(X.c0, Y.c0, Z.c0, 0.0f);
+}
+
 // Re-read the caller's arrays into the sorted order of the last build and
 // derive the per-particle quantities the pair kernels load for j.
 __global__ void __launch_bounds__(kThreads)
@@ -70,16 +82,18 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
                const double* __restrict__ cs, double4_32a* __restrict__ posh,
                double4_32a* __restrict__ velm, double4_32a* __restrict__ therm,
                double2* __restrict__ kern, double* __restrict__ cint, float4* __restrict__ dpk,
-               float2* __restrict__ mdf) {
+               float2* __restrict__ mdf, float4* __restrict__ xpk, const Grid* __restrict__ grid) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t o = order[k];
     if (o < 0) return;  // empty slot
     const double hh = h[o];
-    posh[k] = make_double4_32a(x[o], y[o], z[o], hh);
+    const double4_32a ps = make_double4_32a(x[o], y[o], z[o], hh);
+    posh[k] = ps;
     const double mm = m[o];
     const dfl::df md = dfl::from_double_fp64(mm);
     mdf[k] = make_float2(md.hi, md.lo);
+    write_xpk(xpk, k, ps, md, grid[0].fxk);  // a single problem: instance 0
     if (what == GATHER_DENSITY) {
         velm[k] = make_double4_32a(0.0, 0.0, 0.0, mm);
     } else {
@@ -103,7 +117,8 @@ void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, 
     c->launches += 1;
     k_gather_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         n, what, kp.alpha, c->order[b], P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m,
-        P->rho, P->p, P->c, c->posh[b], c->velm[b], c->therm, c->kern, c->cint, c->dpk, c->mdf);
+        P->rho, P->p, P->c, c->posh[b], c->velm[b], c->therm, c->kern, c->cint, c->dpk, c->mdf,
+        c->xpk, c->grid);
 }
 
 // ------------------------------------------------------------ bbox and grid
@@ -304,6 +319,16 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     const double u24 = 5.9604644775390625e-08;
     g->eC = __double2float_ru(u24 * (4.0 * X + (per ? 2.0 * kp.lz : 0.0)) * 1.0001 + 1e-37);
     g->eR = __double2float_ru(u24 * 2.02 * 1.0001);
+    // fixed-point exponent of the coordinate chunks (dfl::to_fx): |x| 2^k < 2^61
+    int ex = 0;
+    frexp(X, &ex);  // X < 2^ex
+    int k = X > 0.0 && isfinite(X) ? 61 - ex : 61;
+    k = k < -60 ? -60 : (k > 100 ? 100 : k);
+    g->fxk = k;
+    const dfl::fx3 L = dfl::to_fx(per ? kp.lz : 0.0, k);
+    g->lzc[0] = L.c2;
+    g->lzc[1] = L.c1;
+    g->lzc[2] = L.c0;
     g->hmean = hmean;
     g->hmax_bits = 0ull;
     g->ncells = (long long)cnt[0] * cnt[1] * cnt[2];
@@ -440,7 +465,8 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
           const double4_32a* __restrict__ velm_in, const double* __restrict__ u_in,
           const int32_t* __restrict__ order_in, double4_32a* __restrict__ posh_out,
           double4_32a* __restrict__ velm_out, double* __restrict__ u_out,
-          int32_t* __restrict__ order_out, float4* __restrict__ fpos, float2* __restrict__ mdf) {
+          int32_t* __restrict__ order_out, float4* __restrict__ fpos, float2* __restrict__ mdf,
+          float4* __restrict__ xpk) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ntot) return;
     const int inst = (int)(keys[r] >> 24);
@@ -452,6 +478,7 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
     velm_out[k] = v;
     const dfl::df m = dfl::from_double_fp64(v.w);
     mdf[k] = make_float2(m.hi, m.lo);
+    write_xpk(xpk, k, p, m, B.grid[inst].fxk);
     u_out[k] = u_in[o];
     order_out[k] = order_in[o];
     fpos[k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
@@ -524,7 +551,7 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const int a = c->cur, b = 1 - c->cur;
     k_permute<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->vals[src], c->posh[a],
                                         c->velm[a], c->ue[a], c->order[a], c->posh[b], c->velm[b],
-                                        c->ue[b], c->order[b], c->fpos, c->mdf);
+                                        c->ue[b], c->order[b], c->fpos, c->mdf, c->xpk);
     c->cur = b;
     k_cells_clear<<<dim3(64, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->cells, c->cell_hmax);
     k_cells_mark<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->cells);

@@ -63,6 +63,8 @@ struct Grid {
     float lzf, halflzf;
     float slop[3];   // absolute slack added to query boxes (FP32 rounding cover)
     float eC, eR;    // FP32-error bound of a coordinate difference: e(R) <= eC + eR * R
+    int fxk;         // fixed-point exponent of the coordinate chunks: |x| 2^fxk < 2^61
+    float lzc[3];    // lz 2^fxk as chunks (scaled like the coordinates' chunks)
 };
 
 // Parameters copied by value into kernels.
@@ -168,6 +170,8 @@ struct sph_ctx {
     double* cint;
     float4* dpk;            // 3 per particle: double-float pack of the force kernel
     float2* mdf;            // mass as a float pair
+    float4* xpk;            // 3 per particle: exact fixed-point chunks of the position
+                            // and the mass as a float pair (double-float pair kernels)
     float4* mpk;            // 5 per particle: pack of the mixed-precision pair kernels
     double* mumax;
     double4_32a* iad_a;     // IAD matrices C_i: (xx, xy, xz, yy) ...
