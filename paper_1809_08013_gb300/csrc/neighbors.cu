@@ -315,10 +315,13 @@ __device__ __forceinline__ int lane_cell(float v, const Grid* __restrict__ g, in
 // (float x, y, z) already moved to the lane's periodic image; sidx holds
 // their particle indices. Padding slots sit far away.
 // rec: instead of counting, record (r^2 in FP32, j) of every candidate that
-// may lie within the thresholds' radius (r2 <= Tout) in recb (up to kRec).
+// may lie within the thresholds' radius (r2 <= Tout) in recb (up to kRec),
+// except those with r2 < tin_lo, certainly within 2 lo (lo the bisection's
+// lower bound, so within 2 h for every h still to be tried): those go to the
+// gather slab and the count c at once.
 __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const int* __restrict__ sidx,
                                             const float4& fi, const Thr& t, bool active, bool rec,
-                                            int64_t i, double h, double& R2,
+                                            float tin_lo, int64_t i, double h, double& R2,
                                             const double4_32a* posh, const Grid* __restrict__ g,
                                             int32_t* slab, int& c, int2* recb, int& nrec) {
     unsigned in = 0u, bd = 0u;
@@ -340,6 +343,11 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
             const float4 q = st[k];
             const float dx = fi.x - q.x, dy = fi.y - q.y, dz = fi.z - q.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (r2 < tin_lo) {
+                if (c < kGSlab) slab[c] = j;
+                ++c;
+                continue;
+            }
             if (nrec < kRec) recb[nrec] = make_int2(__float_as_int(r2), j);
             ++nrec;
         }
@@ -367,16 +375,17 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
     }
 }
 
-// |N_i(hh)| from the records of a record pass made at a radius >= 2 hh, with
+// |N_i(hh)| from the c0 neighbours certainly within 2 lo <= 2 hh (already in
+// the slab) and the records of a record pass made at a radius >= 2 hh, with
 // the same decisions as a counting pass (FP32 thresholds, exact FP64 test in
-// the band between them); with slab, N_i(hh) is also written, in the order of
-// the records, which is the order a counting pass would have found them in.
+// the band between them); with slab, the recorded members of N_i(hh) are
+// appended after the first c0, in record order.
 __device__ int count_records(const int2* recb, int nrec, double hh, const Grid* __restrict__ g,
-                             const double4_32a* posh, int64_t i, int32_t* slab) {
+                             const double4_32a* posh, int64_t i, int32_t* slab, int c0) {
     const double R = 2.0 * hh;
     const Thr t = thresholds(R, g);
     double R2 = -1.0;
-    int c = 0;
+    int c = c0;
     for (int q = 0; q < nrec; ++q) {
         const int2 e = recb[q];
         const float r2 = __int_as_float(e.x);
@@ -433,6 +442,7 @@ __device__ __forceinline__ void union_group(
         const bool rec = pass > 0;
         const double hs = rec && !isinf(hi) ? hi : h;
         const Thr t = thresholds(2.0 * hs, g);
+        const float tin_lo = rec && lo > 0.0 ? thresholds(2.0 * lo, g).tin : -1.0f;
         const float Rq = reach_f32(hs);
         const float lzz = wmin(active ? fi.z - Rq : CUDART_INF_F), hzz = wmax(active ? fi.z + Rq : -CUDART_INF_F);
         // Periodic z: candidates are moved to the image nearest a reference lane's
@@ -539,8 +549,8 @@ __device__ __forceinline__ void union_group(
                                 continue;
                             }
                             __syncwarp();
-                            union_chunk(st, sidx, fi, t, mine, rec, i, h, R2, posh, g, slab, c,
-                                        recb, nrec);
+                            union_chunk(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g,
+                                        slab, c, recb, nrec);
                             __syncwarp();
                             if (ok && r >= room) {
                                 st[r - room] = f;
@@ -557,7 +567,8 @@ __device__ __forceinline__ void union_group(
                     sidx[lane] = -1;
                 }
                 __syncwarp();
-                union_chunk(st, sidx, fi, t, mine, rec, i, h, R2, posh, g, slab, c, recb, nrec);
+                union_chunk(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g, slab, c, recb,
+                            nrec);
                 __syncwarp();
             }
         }
@@ -571,10 +582,11 @@ __device__ __forceinline__ void union_group(
             wl[atomicAdd(&status[3], 1u)] = (int32_t)i;
         }
         // counts of this pass (or from its records) and the bisection updates
+        const int cbase = rec ? c : 0;  // a record pass: the neighbours within 2 lo
         for (bool counted = !rec; active;) {
             if (rec) {
                 if (h > hs) break;  // beyond the recorded radius: another pass
-                c = count_records(recb, nrec, h, g, posh, i, nullptr);
+                c = count_records(recb, nrec, h, g, posh, i, nullptr, cbase);
             } else if (counted) {
                 counted = false;  // c holds this pass's count
             } else {
@@ -595,7 +607,7 @@ __device__ __forceinline__ void union_group(
                 h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
             }
             if (!rec) break;
-            if (!active) count_records(recb, nrec, h, g, posh, i, slab);  // N_i(h) of the final h
+            if (!active) count_records(recb, nrec, h, g, posh, i, slab, cbase);  // N_i(final h)
         }
     }
     if (!valid) {
