@@ -155,10 +155,17 @@ __device__ __forceinline__ fx3 to_fx(double x, int k) {
             (float)(X & 0x1fffffLL) * pow2f(-k)};
 }
 
-// The double-float value of the exact chunk differences a2 + a1 + a0.
+// The double-float value of the exact chunk differences a2 + a1 + a0
+// (a2, a1, a0 multiples of 2^(42-k), 2^(21-k), 2^-k; |a1| < 2^(43-k),
+// |a0| < 2^(22-k)). Fast2Sum is exact for (a2, a1): either |a2| >= |a1| in
+// exponent, or a2 = 0, or 2^(42-k) <= |a2| < |a1| and a2 + a1 is a multiple
+// of 2^(21-k) below 2^(44-k), i.e. representable, in which case Fast2Sum
+// returns it with a zero error term. Then t = lo + a0 is rounded once (|t| <
+// ulp(hi)/2 + 2^(22-k) <= |hi| unless hi = 0) and folded in by Fast2Sum:
+// the result is within ~2^-48 of the exact difference.
 __device__ __forceinline__ df fx_sum(float a2, float a1, float a0) {
-    const df s = two_sum(a2, a1);
-    return addf(s, a0);
+    const df s = fast_two_sum(a2, a1);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a0));
 }
 
 // Per-particle conversion back to FP64 (two conversions and one FP64 add).
