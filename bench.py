@@ -61,16 +61,17 @@ def variant_flops(kernel, gradients, sinc_n):
         return 83 + 2 * g, FLOPS_PAIR_AV, 27 + g
     return FLOPS_PAIR_BASE - 2 * 5 + 2 * f, FLOPS_PAIR_AV, 0
 
-# DRAM traffic of one force-kernel launch from an ncu capture (dram__bytes_read.sum
-# + dram__bytes_write.sum) on the 70^3 patch, scaled to a launch here by the
-# number of pairs it processes (profiles/kernels_patch343k.md). It is reported
-# only while the kernel's sources hash to the version that was captured.
+# DRAM traffic of one force-kernel launch (the default two lanes per particle)
+# from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 70^3
+# patch, scaled to a launch here by the number of pairs it processes
+# (profiles/kernels_patch343k.md). It is reported only while the kernel's
+# sources hash to the version that was captured.
 FORCES_TRAFFIC = {
     "fp64": {"sources": ("physics_df.cu", "df.cuh"),
-             "sha1": "e0882b5df4c45257af8e2025317e00e905c9e900",
-             "bytes": 236.21e6 + 15.23e6, "pairs": 34640886},
+             "sha1": "d3039ac6a26f95c20d1fc56ce1ff81e54c364896",
+             "bytes": 235.79e6 + 9.86e6, "pairs": 34640886},
     "mixed": {"sources": ("physics_mixed.cu", "df.cuh"),
-              "sha1": "cd641f0eb4a1d4c532988822ec2236b235b05bef",
+              "sha1": "09687ae25b5c288306d8be871c2280cb4dab677a",
               "bytes": 216.04e6 + 11.42e6, "pairs": 34640886},
 }
 

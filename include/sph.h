@@ -65,7 +65,7 @@ typedef struct {
                             2 = the same sums with native FP64 arithmetic.
                             Other values: SPH_E_INVAL. */
     int32_t pair_threads; /* lanes per particle in the density and force sums: 1, 2, 4
-                             or 8 (0 selects 2 for precision 1, else 1); the lanes of a
+                             or 8 (0 selects 2); the lanes of a
                              particle split its
                              neighbour row and combine their sums in a fixed order.
                              Ignored by precision 2. A tuning knob (sph_autotune): the

@@ -126,7 +126,7 @@ inline KParams kparams(const sph_params* p) {
     k.rho0 = p->rho0; k.c0 = p->c0; k.gamma = p->gamma; k.alpha = p->alpha;
     k.beta = p->beta; k.eta2 = p->eta2; k.cfl = p->cfl; k.lz = p->lz;
     k.cell_scale = p->cell_scale > 0.0 ? p->cell_scale : 1.0;
-    k.pair_threads = p->pair_threads > 0 ? p->pair_threads : (p->precision == 1 ? 2 : 1);
+    k.pair_threads = p->pair_threads > 0 ? p->pair_threads : 2;
     k.defer_lanes = p->defer_lanes > 0 ? p->defer_lanes : 16;
     k.kernel = p->kernel;
     k.gradients = p->gradients;

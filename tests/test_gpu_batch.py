@@ -69,7 +69,7 @@ def run_alone(B, s, p, nsteps):
     return arr
 
 
-@pytest.mark.parametrize("precision,tpp", [(0, 0), (1, 0), (0, 4), (1, 2)])
+@pytest.mark.parametrize("precision,tpp", [(0, 0), (1, 0), (0, 1), (0, 4), (1, 4)])
 def test_batch_instances_bit_identical_to_alone(B, precision, tpp):
     insts = instances(precision)
     for _, p in insts:

@@ -124,7 +124,7 @@ def test_mixed_one_step(B, orc, name):
         assert v <= TOL_MIXED, (k, v)
 
 
-@pytest.mark.parametrize("tpp", [2, 4])
+@pytest.mark.parametrize("tpp", [1, 4])
 def test_mixed_with_several_lanes_per_particle(B, orc, tpp):
     s, prm, o = oracle_of(orc, "evrard_moving")
     prm = ics.SphParams(**{**prm.as_dict(), "pair_threads": tpp})
