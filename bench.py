@@ -576,6 +576,58 @@ def dataclasses_replace(r):
     return dataclasses.replace(r)
 
 
+def gpu_small_case(args, B, dev, steps=20):
+    """The 30^3 = 27,000-particle patch (seed 1, the small configuration) on
+    the GPU: one sph_step(steps) call from the initial conditions, after one
+    untimed call. It fits in L2; a latency figure, not a roofline case."""
+    import torch
+    from paper_1809_08013_gb300 import ics
+    s, prm = ics.square_patch(30, seed=1)
+    prm.precision = PRECISION[args.precision]
+    n = len(s["x"])
+    ctx = B.Context(n, device=dev.index)
+    arr = B.alloc_arrays(s, device=dev)
+    ic = {k: arr[k].clone() for k in B.STATE_FIELDS}
+    stream = torch.cuda.current_stream(dev)
+    ctx.step(prm, arr, nsteps=steps, stream=stream)
+    ctx.sync(stream)
+    for k in B.STATE_FIELDS:
+        arr[k].copy_(ic[k])
+    arr["time"].zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    ctx.step(prm, arr, nsteps=steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    st = ctx.sync(stream)
+    return {"workload": f"rotating patch 30^3 = {n:,} particles, {steps} steps from the initial "
+                        f"conditions", "ms_per_step": ms / steps,
+            "value": n * steps / (ms * 1e-3), "unit": UNIT, "status": B.STATUS_NAMES.get(st)}
+
+
+def oracle_small_case(oracle, args):
+    """The oracle on the 30^3 = 27,000-particle patch (seed 1, the small
+    configuration), one step from the initial conditions, on all host cores
+    and on one."""
+    from paper_1809_08013_gb300 import ics
+    s, prm = ics.square_patch(30, seed=1)
+    prm.precision = PRECISION[args.precision]
+    n = len(s["x"])
+    out = {"workload": f"rotating patch 30^3 = {n:,} particles, one step"}
+    cores = oracle.get_threads()
+    for label, k in (("all_cores", cores), ("one_core", 1)):
+        oracle.set_threads(k)
+        t0 = time.perf_counter()
+        oracle.step(prm, s, nsteps=1)
+        t = time.perf_counter() - t0
+        out[label] = {"cores": k, "seconds": t, "value": n / t, "unit": UNIT}
+    oracle.set_threads(cores)
+    return out
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -735,7 +787,12 @@ def run_native(args):
         tc = time.perf_counter() - t0
         cpu = {"value": n / tc, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                "sample": f"one oracle step (plain C FP64, OpenMP) of the same {n:,}-particle "
-                         f"{args.workload} from its initial conditions: {tc:.1f} s"}
+                         f"{args.workload} from its initial conditions: {tc:.1f} s",
+               "gpu_speedup": value / (n / tc)}
+        if args.workload == "patch":
+            cpu["small_case"] = oracle_small_case(oracle, args)
+
+    small = gpu_small_case(args, B, dev) if args.workload == "patch" and world == 1 else None
 
     ensemble = None
     if not args.no_ensemble and args.workload == "patch" and world == 1:
@@ -756,7 +813,7 @@ def run_native(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (state ~0.2 GB + neighbour list ~0.4 GB)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "steady_state": steady, "ensemble": ensemble, "serving": serving,
+            "steady_state": steady, "small_case": small, "ensemble": ensemble, "serving": serving,
             "variants": variants,
             "clocks": clocks, "status": B.STATUS_NAMES.get(status),
             "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
