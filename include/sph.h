@@ -205,6 +205,20 @@ sph_status sph_forces(sph_ctx *ctx, const sph_params *prm, sph_particles *P, voi
 sph_status sph_step(sph_ctx *ctx, const sph_params *prm, sph_particles *P, int nsteps,
                     void *stream);
 
+/* sph_step on HOST arrays: the same nsteps iterations, with every pointer of
+ * P a host pointer (pinned memory lets the copies run asynchronously; any
+ * host memory works). On the stream it copies x, y, z, vx, vy, vz, m, h, u
+ * and *time to device staging buffers owned by the context, runs the steps,
+ * and copies back x..u, *time, *dt and each of rho, p, c, ax, ay, az, du,
+ * mumax, nnb that is not NULL (only the state fields and time, dt are
+ * required). The staging (17 doubles and one int32 per particle of capacity)
+ * is allocated by the first call (SPH_E_NOMEM if that fails) and freed with
+ * the context; sph_ctx_bytes does not include it. Asynchronous like
+ * sph_step: the host arrays hold the results after sph_sync (or a stream
+ * synchronisation). nsteps = 0 copies nothing. */
+sph_status sph_step_host(sph_ctx *ctx, const sph_params *prm, sph_particles *P, int nsteps,
+                         void *stream);
+
 /* Describe a batch of ninst independent problems for sph_batch_step.
  * counts[k] (host array) is the number of particles of instance k, held in
  * the caller's arrays at [first[k], first[k] + counts[k]) (first: host array,

@@ -121,6 +121,8 @@ def load(rebuild: bool = True):
         fn.argtypes = [_DP, P(SphParams), P(SphParticles), _DP]
     L.sph_step.restype = C.c_int
     L.sph_step.argtypes = [_DP, P(SphParams), P(SphParticles), C.c_int, _DP]
+    L.sph_step_host.restype = C.c_int
+    L.sph_step_host.argtypes = [_DP, P(SphParams), P(SphParticles), C.c_int, _DP]
     L.sph_neighbors_to_host.restype = C.c_int
     L.sph_neighbors_to_host.argtypes = [_DP, _DP, _DP, C.c_int64, _DP, _DP, _DP]
     L.sph_sync.restype = C.c_int
@@ -185,6 +187,30 @@ def particles(arrays: dict) -> SphParticles:
             if not t.is_cuda or not t.is_contiguous():
                 raise ValueError(f"{f} must be a contiguous CUDA tensor")
             setattr(s, f, t.data_ptr())
+    return s
+
+
+def host_particles(arrays: dict) -> SphParticles:
+    """The C struct over HOST arrays: numpy arrays or CPU torch tensors
+    (float64, contiguous; 'nnb' int32; 'time' and 'dt' of one element).
+    Missing names become NULL."""
+    import numpy as np
+    n = int(len(arrays["x"]))
+    s = SphParticles()
+    s.n = n
+    for f in STATE_FIELDS + OUT_FIELDS + ("nnb", "time", "dt"):
+        a = arrays.get(f)
+        if a is None:
+            continue
+        if isinstance(a, np.ndarray):
+            want = np.int32 if f == "nnb" else np.float64
+            if a.dtype != want or not a.flags.c_contiguous:
+                raise ValueError(f"{f} must be a contiguous {np.dtype(want).name} array")
+            setattr(s, f, a.ctypes.data)
+        else:
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError(f"{f} must be a contiguous host tensor")
+            setattr(s, f, a.data_ptr())
     return s
 
 
@@ -270,6 +296,14 @@ class Context:
         P = particles(arrays)
         self._check(self.lib.sph_step(self.h, C.byref(params(prm)), C.byref(P), int(nsteps),
                                       _stream(stream)))
+
+    def step_host(self, prm, arrays: dict, nsteps: int = 1, stream=None):
+        """sph_step_host: `arrays` are host arrays (see host_particles); the
+        library copies them in, steps, and copies the results back on the
+        stream (pinned memory makes the copies asynchronous)."""
+        P = host_particles(arrays)
+        self._check(self.lib.sph_step_host(self.h, C.byref(params(prm)), C.byref(P), int(nsteps),
+                                           _stream(stream)))
 
     def batch_set(self, counts, prms, first=None, stream=None):
         """Describe a batch: counts[k] particles of instance k, at

@@ -118,7 +118,8 @@ void free_all(sph_ctx* c) {
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
-                    c->tune_dt, c->roff, c->wctr, c->recs, c->iad_a, c->iad_b, c->vol, c->xpk};
+                    c->tune_dt, c->roff, c->wctr, c->recs, c->iad_a, c->iad_b, c->vol, c->xpk,
+                    c->stage, c->stage_nnb};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -592,6 +593,73 @@ sph_status sph_step(sph_ctx* c, const sph_params* prm, sph_particles* P, int nst
     launch_set_single(c, kparams(prm), P->n, s);
     run_steps(c, P, nsteps, s);
     return check_launch(c, "sph_step");
+}
+
+sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, int nsteps,
+                         void* stream) {
+    if (!c) return SPH_E_INVAL;
+    sph_status st;
+    if ((st = check_params(c, prm)) != SPH_OK || (st = check_particles(c, H)) != SPH_OK) return st;
+    if (nsteps < 0) { set_err(c, "nsteps < 0"); return SPH_E_INVAL; }
+    NEED(H->dt); NEED(H->time);
+    const int64_t n = H->n;
+    if (n > 0) {
+        NEED(H->x); NEED(H->y); NEED(H->z); NEED(H->vx); NEED(H->vy); NEED(H->vz);
+        NEED(H->m); NEED(H->h); NEED(H->u);
+    }
+    if (nsteps == 0) return SPH_OK;
+    DeviceGuard dg(c->device);
+    const size_t N = (size_t)std::max<int64_t>(c->ncap, 1);
+    if (!c->stage) {
+        if (cudaMalloc((void**)&c->stage, (17 * N + 2) * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&c->stage_nnb, N * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            if (c->stage) cudaFree(c->stage);
+            c->stage = nullptr;
+            c->stage_nnb = nullptr;
+            set_err(c, "sph_step_host: staging allocation failed");
+            return SPH_E_NOMEM;
+        }
+    }
+    // device view: the state fields first (in/out), then the outputs
+    double* sg = c->stage;
+    double** hf[17] = {&H->x, &H->y, &H->z, &H->vx, &H->vy, &H->vz, &H->m, &H->h, &H->u,
+                       &H->rho, &H->p, &H->c, &H->ax, &H->ay, &H->az, &H->du, &H->mumax};
+    sph_particles D;
+    memset(&D, 0, sizeof D);
+    D.n = n;
+    double** df[17] = {&D.x, &D.y, &D.z, &D.vx, &D.vy, &D.vz, &D.m, &D.h, &D.u,
+                       &D.rho, &D.p, &D.c, &D.ax, &D.ay, &D.az, &D.du, &D.mumax};
+    for (int f = 0; f < 17; ++f) *df[f] = sg + (size_t)f * N;
+    if (!H->mumax) D.mumax = nullptr;
+    D.nnb = H->nnb ? c->stage_nnb : nullptr;
+    D.time = sg + 17 * N;
+    D.dt = sg + 17 * N + 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 9 && e == cudaSuccess && n > 0; ++f)
+        e = cudaMemcpyAsync(*df[f], *hf[f], bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D.time, H->time, sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, "sph_step_host: %s", cudaGetErrorString(e));
+        return SPH_E_CUDA;
+    }
+    launch_set_single(c, kparams(prm), n, s);
+    run_steps(c, &D, nsteps, s);
+    for (int f = 0; f < 17 && e == cudaSuccess && n > 0; ++f)
+        if (*hf[f]) e = cudaMemcpyAsync(*hf[f], *df[f], bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && H->nnb && n > 0)
+        e = cudaMemcpyAsync(H->nnb, D.nnb, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(H->time, D.time, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(H->dt, D.dt, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, "sph_step_host: %s", cudaGetErrorString(e));
+        return SPH_E_CUDA;
+    }
+    return check_launch(c, "sph_step_host");
 }
 
 sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const int64_t* first,

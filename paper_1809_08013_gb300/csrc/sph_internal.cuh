@@ -209,6 +209,8 @@ struct sph_ctx {
     unsigned* status_host;  // pinned mirror
     double* scratch_scalar; // [0] internal dt, [1] internal time
     double* tune_dt;        // 2 x maxinst: dt and time of the autotuner's trial runs
+    double* stage;          // sph_step_host staging: 17 x ncap doubles + time, dt (lazy)
+    int32_t* stage_nnb;     // and ncap int32
     int64_t last_hnoconv;
     // launch accounting and optional per-phase event timing
     int64_t launches;

@@ -37,6 +37,7 @@ def test_null_context_is_rejected_without_launch(lib):
     assert lib.sph_eos(None, C.byref(prm), C.byref(P), None) == binding.SPH_E_INVAL
     assert lib.sph_forces(None, C.byref(prm), C.byref(P), None) == binding.SPH_E_INVAL
     assert lib.sph_step(None, C.byref(prm), C.byref(P), 1, None) == binding.SPH_E_INVAL
+    assert lib.sph_step_host(None, C.byref(prm), C.byref(P), 1, None) == binding.SPH_E_INVAL
     assert lib.sph_sync(None, None) == binding.SPH_E_INVAL
     assert lib.sph_last_error(None) == b"context is NULL"
     lib.sph_ctx_destroy(None)  # no-op
