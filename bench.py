@@ -424,15 +424,17 @@ def _run_ensemble(args, B, dev, stream):
     }
 
 
-# (name, kernel, gradients, sinc_n, precision): kernel derivatives with the M4
-# or Wendland kernel run in double-float at precision 0 and on the FP64 pipe
-# at precision 2; the sinc kernel and IAD always take the FP64-pipe kernels.
+# (name, kernel, gradients, sinc_n, precision): the M4 and Wendland kernels
+# (kernel derivatives or IAD) run in double-float at precision 0 and on the FP64
+# pipe at precision 2; the sinc kernel always takes the FP64-pipe kernels.
 VARIANTS = (("M4, kernel derivatives, FP64 pipe (precision 2)", 0, 0, 5, 2),
             ("Wendland C2, kernel derivatives, double-float (precision 0)", 1, 0, 5, 0),
             ("Wendland C2, kernel derivatives, FP64 pipe (precision 2)", 1, 0, 5, 2),
             ("sinc n=5, kernel derivatives, FP64 pipe", 2, 0, 5, 0),
-            ("M4, IAD gradients, FP64 pipe", 0, 1, 5, 0),
-            ("Wendland C2, IAD gradients, FP64 pipe", 1, 1, 5, 0))
+            ("M4, IAD gradients, double-float (precision 0)", 0, 1, 5, 0),
+            ("Wendland C2, IAD gradients, double-float (precision 0)", 1, 1, 5, 0),
+            ("M4, IAD gradients, FP64 pipe (precision 2)", 0, 1, 5, 2),
+            ("sinc n=5, IAD gradients, FP64 pipe", 2, 1, 5, 0))
 
 
 def run_variants(args, B, dev, fp64_peak):
@@ -489,9 +491,7 @@ def run_variants(args, B, dev, fp64_peak):
                     "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
                     "status": B.STATUS_NAMES.get(st),
                     "precision": prec,
-                    "roofline": {"bound": "alu", "kernel": "k_volume + k_iad + k_forces_iad"
-                                 if grads else ("k_forces_df" if prec == 0 and kernel != 2
-                                                else "k_forces"),
+                    "roofline": {"bound": "alu", "kernel": kernel_names(kernel, grads, prec),
                                  "achieved": ach, "peak": fp64_peak / 1e12,
                                  "unit": "TFLOP/s", "frac": ach / (fp64_peak / 1e12),
                                  "flops_per_launch": flops,
@@ -502,6 +502,14 @@ def run_variants(args, B, dev, fp64_peak):
     torch.cuda.empty_cache()
     return {"workload": workload_name(args).split(", FP64")[0], "steps": args.variant_steps,
             "runs": out}
+
+
+def kernel_names(kernel, grads, prec):
+    """The force phase's kernels of a variant run."""
+    df = prec == 0 and kernel != 2
+    if grads:
+        return "k_volume_df + k_iad_df + k_forces_iad_df" if df else "k_volume + k_iad + k_forces_iad"
+    return "k_forces_df" if df else "k_forces"
 
 
 def ics_params_copy(p):

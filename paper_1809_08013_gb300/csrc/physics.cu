@@ -522,6 +522,8 @@ void launch_forces(sph_ctx* c, double* dt_out, double* time_inout, cudaStream_t 
     c->launches += 1;
     if (c->prec == PREC_MIXED)
         launch_forces_mx(c, s);
+    else if (!native_pairs(c) && c->grad_kind == 1)
+        launch_forces_iad_df(c, s);
     else if (!native_pairs(c))
         launch_forces_df(c, s);
     else if (n > 0 && c->grad_kind == 1) {

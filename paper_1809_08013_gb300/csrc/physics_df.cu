@@ -342,4 +342,260 @@ void launch_forces_df(sph_ctx* c, cudaStream_t s) {
     }
 }
 
+// ------------------------------------------------------------ IAD (Table 1)
+// The double-float IAD path (M4 and Wendland C2; definitions as in physics.cu).
+// Volume elements V = m / rho as float pairs, once per particle.
+__global__ void __launch_bounds__(kThreads)
+k_volume_df(int64_t n, Batch B, const double4_32a* __restrict__ velm,
+            const double4_32a* __restrict__ therm, float2* __restrict__ vdf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int inst = slot_inst(B, i);
+    if (!slot_real(B, inst, i)) return;
+    const df v = dfl::from_double_fp64(velm[i].w / (2.0 * therm[i].x));
+    vdf[i] = make_float2(v.hi, v.lo);
+}
+
+// tau_i = sum_{j in N_i} V_j W(r_ij, h_i) (r_j - r_i)(r_j - r_i)^T summed in
+// double-float (T lanes per particle, fixed butterfly), then scaled, inverted
+// in FP64 by the adjugate (C_i = 0 if singular) and stored as float pairs:
+//   cpk[3i] = (C00, C01), cpk[3i+1] = (C02, C11), cpk[3i+2] = (C12, C22).
+template <int T, int KER>
+__global__ void __launch_bounds__(kThreads)
+k_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
+         const float4* __restrict__ xpk, const float2* __restrict__ vdf, Rows R,
+         float4* __restrict__ cpk) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
+    const int sub = (int)(threadIdx.x % T);
+    const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
+    const int32_t* ent = nullptr;
+    int len = 0;
+    const bool act = i < n && slot_real(B, inst, i) && row_of(R, n, i, true, ent, len);
+    if (T == 1 && !act) return;
+    df t[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) t[k] = df{0.0f, 0.0f};
+    double hinv = 1.0;
+    if (act) {
+        hinv = 1.0 / posh[i].w;
+        const df Hi = dfl::from_double_fp64(hinv);
+        const Grid& g = B.grid[inst];
+        const bool per = B.kp[inst].periodic_z != 0;
+        const float hlz = g.halflzf, L2 = g.lzc[0], L1 = g.lzc[1], L0 = g.lzc[2];
+        const float4 I0 = xpk[3 * i], I1 = xpk[3 * i + 1], I2 = xpk[3 * i + 2];
+        for (int e = sub; e < len; e += T) {
+            const int j = __ldg(&ent[e]);
+            const float4 J0 = __ldg(&xpk[3 * j]), J1 = __ldg(&xpk[3 * j + 1]);
+            const float4 J2 = __ldg(&xpk[3 * j + 2]);
+            const float2 vj = __ldg(&vdf[j]);
+            float z2 = __fsub_rn(I0.z, J0.z), z1 = __fsub_rn(I1.z, J1.z), z0 = __fsub_rn(I2.z, J2.z);
+            if (per) wrap_fx(z2, z1, z0, hlz, L2, L1, L0);
+            const df X = dfl::fx_sum(__fsub_rn(I0.x, J0.x), __fsub_rn(I1.x, J1.x), __fsub_rn(I2.x, J2.x));
+            const df Y = dfl::fx_sum(__fsub_rn(I0.y, J0.y), __fsub_rn(I1.y, J1.y), __fsub_rn(I2.y, J2.y));
+            const df Z = dfl::fx_sum(z2, z1, z0);
+            const df r2 = dfl::add(dfl::add(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
+            if (!(r2.hi > 0.0f)) continue;  // r = 0 adds nothing to tau
+            const df q = dfl::mul(dfl::mul(r2, dfl::rsqrt(r2)), Hi);
+            const df w = dfl::mul(df{vj.x, vj.y}, w_shape_k<KER>(q));
+            const df wx = dfl::mul(w, X), wy = dfl::mul(w, Y);
+            t[0] = dfl::add(t[0], dfl::mul(wx, X));
+            t[1] = dfl::add(t[1], dfl::mul(wx, Y));
+            t[2] = dfl::add(t[2], dfl::mul(wx, Z));
+            t[3] = dfl::add(t[3], dfl::mul(wy, Y));
+            t[4] = dfl::add(t[4], dfl::mul(wy, Z));
+            t[5] = dfl::add(t[5], dfl::mul(dfl::mul(w, Z), Z));
+        }
+    }
+    if (T > 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) t[k] = dfl::lane_sum<T>(t[k]);
+        if (!act || sub != 0) return;
+    }
+    const double sg = hinv * hinv * hinv * (KER == KER_M4 ? kInvPiD : B.kp[inst].wnorm);
+    double a[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a[k] = dfl::to_double(t[k]) * sg;
+    const double c00 = a[3] * a[5] - a[4] * a[4], c01 = a[2] * a[4] - a[1] * a[5];
+    const double c02 = a[1] * a[4] - a[2] * a[3], c11 = a[0] * a[5] - a[2] * a[2];
+    const double c12 = a[1] * a[2] - a[0] * a[4], c22 = a[0] * a[3] - a[1] * a[1];
+    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    const double id = det == 0.0 ? 0.0 : 1.0 / det;
+    const df C[6] = {dfl::from_double_fp64(c00 * id), dfl::from_double_fp64(c01 * id),
+                     dfl::from_double_fp64(c02 * id), dfl::from_double_fp64(c11 * id),
+                     dfl::from_double_fp64(c12 * id), dfl::from_double_fp64(c22 * id)};
+    cpk[3 * i + 0] = make_float4(C[0].hi, C[0].lo, C[1].hi, C[1].lo);
+    cpk[3 * i + 1] = make_float4(C[2].hi, C[2].lo, C[3].hi, C[3].lo);
+    cpk[3 * i + 2] = make_float4(C[4].hi, C[4].lo, C[5].hi, C[5].lo);
+}
+
+// symmetric 3x3 (in the cpk order) times a vector, in double-float
+__device__ __forceinline__ void symv_df(const df* M, const df& x, const df& y, const df& z, df& ox,
+                                        df& oy, df& oz) {
+    ox = dfl::add(dfl::add(dfl::mul(M[0], x), dfl::mul(M[1], y)), dfl::mul(M[2], z));
+    oy = dfl::add(dfl::add(dfl::mul(M[1], x), dfl::mul(M[3], y)), dfl::mul(M[4], z));
+    oz = dfl::add(dfl::add(dfl::mul(M[2], x), dfl::mul(M[4], y)), dfl::mul(M[5], z));
+}
+
+// Forces with IAD gradients: as k_forces_df with F r_ij replaced by
+// G_ij = -(wnorm / 2) (h_i^-3 g(q_i) C_i + h_j^-3 g(q_j) C_j) r_ij.
+template <int T, int KER>
+__global__ void __launch_bounds__(kThreads, 2)
+k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
+                const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
+                const float4* __restrict__ xpk, const float4* __restrict__ cpk,
+                const double* __restrict__ cint, Rows R, double4_32a* __restrict__ acc,
+                double* __restrict__ mumax, double* __restrict__ dt_part) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
+    const int sub = (int)(threadIdx.x % T);
+    const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
+    const int32_t* ent = nullptr;
+    int len = 0;
+    const bool act = i < n && slot_real(B, inst, i) && row_of(R, n, i, false, ent, len);
+    double dtc = CUDART_INF;
+    df sx = {0.f, 0.f}, sy = {0.f, 0.f}, sz = {0.f, 0.f}, sp = {0.f, 0.f}, sv = {0.f, 0.f};
+    df mumx = {0.f, 0.f};
+    if (act) {
+        const KParams& kp = B.kp[inst];
+        const double4_32a vi = velm[i];
+        const float4 I0 = xpk[3 * i], I1 = xpk[3 * i + 1], I2 = xpk[3 * i + 2];
+        const float4 a0 = dpk[3 * i], a1 = dpk[3 * i + 1], a2 = dpk[3 * i + 2];
+        const df Hi = {a0.x, a0.y}, Ai = {a1.x, a1.y}, hhi = {a1.z, a1.w};
+        const df rhi = {a2.x, a2.y}, cai = {a2.z, a2.w};
+        const df Hi3 = dfl::mul(Hi, dfl::sqr(Hi));
+        const float4 c0 = cpk[3 * i], c1 = cpk[3 * i + 1], c2 = cpk[3 * i + 2];
+        const df Ci[6] = {{c0.x, c0.y}, {c0.z, c0.w}, {c1.x, c1.y},
+                          {c1.z, c1.w}, {c2.x, c2.y}, {c2.z, c2.w}};
+        const Grid& gr = B.grid[inst];
+        const bool per = kp.periodic_z != 0;
+        const float hlz = gr.halflzf, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
+        const df kg = dfl::from_double_fp64(-0.5 * (KER == KER_M4 ? kInvPiD : kp.wnorm));
+        const df eta2 = dfl::from_double_fp64(kp.eta2);
+        const df betad = dfl::from_double_fp64(kp.beta);
+        for (int e = sub; e < len; e += T) {
+            const int j = __ldg(&ent[e]);
+            const float4 J0 = __ldg(&xpk[3 * j]), J1 = __ldg(&xpk[3 * j + 1]);
+            const float4 J2 = __ldg(&xpk[3 * j + 2]);
+            const double4_32a vj = velm[j];
+            const float4 b0 = __ldg(&dpk[3 * j]), b1 = __ldg(&dpk[3 * j + 1]);
+            const float4 b2 = __ldg(&dpk[3 * j + 2]);
+            float z2 = __fsub_rn(I0.z, J0.z), z1 = __fsub_rn(I1.z, J1.z), z0 = __fsub_rn(I2.z, J2.z);
+            if (per) wrap_fx(z2, z1, z0, hlz, L2, L1, L0);
+            const df X = dfl::fx_sum(__fsub_rn(I0.x, J0.x), __fsub_rn(I1.x, J1.x), __fsub_rn(I2.x, J2.x));
+            const df Y = dfl::fx_sum(__fsub_rn(I0.y, J0.y), __fsub_rn(I1.y, J1.y), __fsub_rn(I2.y, J2.y));
+            const df Z = dfl::fx_sum(z2, z1, z0);
+            const df r2 = dfl::add(dfl::add(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
+            if (!(r2.hi > 0.0f)) continue;  // coincident particles exert no force
+            const df r = dfl::mul(r2, dfl::rsqrt(r2));
+            const df Hj = {b0.x, b0.y};
+            const df wi = dfl::mul(Hi3, w_shape_k<KER>(dfl::mul(r, Hi)));
+            const df wj = dfl::mul(dfl::mul(Hj, dfl::sqr(Hj)), w_shape_k<KER>(dfl::mul(r, Hj)));
+            df M[6];
+            {
+                const float4 d0 = __ldg(&cpk[3 * j]), d1 = __ldg(&cpk[3 * j + 1]);
+                const float4 d2 = __ldg(&cpk[3 * j + 2]);
+                const df Cj[6] = {{d0.x, d0.y}, {d0.z, d0.w}, {d1.x, d1.y},
+                                  {d1.z, d1.w}, {d2.x, d2.y}, {d2.z, d2.w}};
+#pragma unroll
+                for (int k = 0; k < 6; ++k) M[k] = dfl::add(dfl::mul(wi, Ci[k]), dfl::mul(wj, Cj[k]));
+            }
+            df Gx, Gy, Gz;
+            symv_df(M, X, Y, Z, Gx, Gy, Gz);
+            Gx = dfl::mul(kg, Gx);
+            Gy = dfl::mul(kg, Gy);
+            Gz = dfl::mul(kg, Gz);
+            const df WX = dfl::from_double(vi.x - vj.x), WY = dfl::from_double(vi.y - vj.y);
+            const df WZ = dfl::from_double(vi.z - vj.z);
+            const df vr = dfl::add(dfl::add(dfl::mul(WX, X), dfl::mul(WY, Y)), dfl::mul(WZ, Z));
+            df Pi = {0.f, 0.f};
+            if (vr.hi < 0.0f) {
+                const df hb = dfl::add(hhi, df{b1.z, b1.w});
+                const df d1 = dfl::add(r2, dfl::mul(dfl::mul(eta2, hb), hb));
+                const df rb = dfl::add(rhi, df{b2.x, b2.y});
+                const df Rr = dfl::rcp(dfl::mul(d1, rb));
+                const df mu = dfl::mul(dfl::mul(dfl::mul(hb, vr), rb), Rr);
+                const df cb = dfl::add(cai, df{b2.z, b2.w});
+                const df tt = dfl::add(dfl::mul(betad, mu), dfl::neg(cb));
+                Pi = dfl::mul(dfl::mul(mu, tt), dfl::mul(d1, Rr));
+                if (-mu.hi > mumx.hi) mumx = dfl::neg(mu);
+            }
+            const df mj = {J0.w, J1.w};
+            const df g = dfl::mul(mj, dfl::add(dfl::add(Ai, df{b1.x, b1.y}), Pi));
+            sx = dfl::add(sx, dfl::mul(g, Gx));
+            sy = dfl::add(sy, dfl::mul(g, Gy));
+            sz = dfl::add(sz, dfl::mul(g, Gz));
+            const df Gv = dfl::add(dfl::add(dfl::mul(Gx, WX), dfl::mul(Gy, WY)), dfl::mul(Gz, WZ));
+            const df mGv = dfl::mul(mj, Gv);
+            sp = dfl::add(sp, mGv);
+            sv = dfl::add(sv, dfl::mul(mGv, Pi));
+        }
+    }
+    if (T > 1) {
+        sx = dfl::lane_sum<T>(sx);
+        sy = dfl::lane_sum<T>(sy);
+        sz = dfl::lane_sum<T>(sz);
+        sp = dfl::lane_sum<T>(sp);
+        sv = dfl::lane_sum<T>(sv);
+#pragma unroll
+        for (int o = 1; o < T; o <<= 1) {
+            const df w = {__shfl_xor_sync(0xffffffffu, mumx.hi, o),
+                          __shfl_xor_sync(0xffffffffu, mumx.lo, o)};
+            if (w.hi > mumx.hi || (w.hi == mumx.hi && w.lo > mumx.lo)) mumx = w;
+        }
+    }
+    if (act && sub == 0) {
+        const double Aid = (double)dpk[3 * i + 1].x + (double)dpk[3 * i + 1].y;
+        acc[i] = make_double4_32a(-dfl::to_double(sx), -dfl::to_double(sy), -dfl::to_double(sz),
+                                  fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)));
+        const double mu_max = dfl::to_double(mumx);
+        mumax[i] = mu_max;
+        const double ci = cint[i];
+        const KParams& ke = B.kp[slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T)];
+        dtc = posh[i].w / (ci + 1.2 * (ke.alpha * ci + ke.beta * mu_max));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
+    __shared__ double sh[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dtc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = sh[0];
+        for (int w = 1; w < kThreads / 32; ++w) m = fmin(m, sh[w]);
+        dt_part[blockIdx.x] = m;
+    }
+}
+
+template <int T, int KER>
+static void iad_df_t(sph_ctx* c, cudaStream_t s) {
+    const int64_t n = c->n;
+    const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
+    const int b = c->cur;
+    const Batch B = batch_of(c);
+    const Rows R = rows_of(c);
+    k_iad_df<T, KER><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->xpk, c->vdf, R, c->cpk);
+    k_forces_iad_df<T, KER><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->dpk, c->xpk,
+                                                    c->cpk, c->cint, R, c->acc, c->mumax,
+                                                    c->dt_part);
+}
+
+template <int KER>
+static void iad_df_k(sph_ctx* c, cudaStream_t s) {
+    switch (c->tpp) {
+        case 2: iad_df_t<2, KER>(c, s); break;
+        case 4: iad_df_t<4, KER>(c, s); break;
+        case 8: iad_df_t<8, KER>(c, s); break;
+        default: iad_df_t<1, KER>(c, s); break;
+    }
+}
+
+void launch_forces_iad_df(sph_ctx* c, cudaStream_t s) {
+    const int64_t n = c->n;
+    if (n == 0) return;
+    c->launches += 3;
+    const int b = c->cur;
+    k_volume_df<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        n, batch_of(c), c->velm[b], c->therm, c->vdf);
+    if (c->kern_kind == KER_WENDLAND) iad_df_k<KER_WENDLAND>(c, s);
+    else iad_df_k<KER_M4>(c, s);
+}
+
 }  // namespace sph

@@ -119,7 +119,7 @@ void free_all(sph_ctx* c) {
                     c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
                     c->tune_dt, c->roff, c->wctr, c->recs, c->iad_a, c->iad_b, c->vol, c->xpk,
-                    c->stage, c->stage_nnb};
+                    c->stage, c->stage_nnb, c->vdf, c->cpk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -184,7 +184,8 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
     ok = ok && al(&c->therm, N) && al(&c->kern, N) && al(&c->acc, N) &&
          al(&c->pint, N) && al(&c->cint, N) && al(&c->dpk, 3 * N) &&
          al(&c->mdf, N) && al(&c->xpk, 3 * N) && al(&c->mpk, 5 * N) &&
-         al(&c->mumax, N) && al(&c->iad_a, N) && al(&c->iad_b, N) && al(&c->vol, N) &&
+         al(&c->mumax, N) && al(&c->iad_a, N) && al(&c->iad_b, N) && al(&c->vol, N) && al(&c->vdf, N) &&
+         al(&c->cpk, 3 * N) &&
          al(&c->fpos, N) && al(&c->tin, N) &&
          al(&c->hist, 256 * nsb) && al(&c->hist_part, (size_t)scan_parts(256 * nsb) + 1) &&
          al(&c->cells, (size_t)c->cellcap) && al(&c->cell_hmax, (size_t)c->cellcap) &&

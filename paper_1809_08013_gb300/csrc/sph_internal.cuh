@@ -177,6 +177,8 @@ struct sph_ctx {
     double4_32a* iad_a;     // IAD matrices C_i: (xx, xy, xz, yy) ...
     double2* iad_b;         // ... and (yz, zz)
     double* vol;            // IAD volume elements m / rho
+    float2* vdf;            // the same as float pairs (double-float IAD)
+    float4* cpk;            // 3 per particle: IAD matrix C_i as float pairs
     float4* fpos;
     float* tin;
     int32_t* order[2];
@@ -228,11 +230,11 @@ namespace sph {
 
 inline Batch batch_of(const sph_ctx* c) { return Batch{c->blk, c->ioff, c->icnt, c->grid, c->kpi}; }
 
-// The pair sums run in the native FP64 kernels: precision 2, the sinc kernel
-// or IAD gradients (those variants exist only there; the M4 and Wendland C2
-// kernels with kernel derivatives also run in double-float).
+// The pair sums run in the native FP64 kernels: precision 2 or the sinc
+// kernel (which exists only there). The M4 and Wendland C2 kernels, with
+// kernel-derivative or IAD gradients, also run in double-float.
 inline bool native_pairs(const sph_ctx* c) {
-    return c->prec == PREC_FP64_NATIVE || c->kern_kind == KER_SINC || c->grad_kind != 0;
+    return c->prec == PREC_FP64_NATIVE || c->kern_kind == KER_SINC;
 }
 
 // Rows of S_i for the pair kernels: the row slab unless a row overflowed it
@@ -304,6 +306,7 @@ void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s);
 // ---- physics_df.cu (precision 0)
 void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s);
 void launch_forces_df(sph_ctx* c, cudaStream_t s);
+void launch_forces_iad_df(sph_ctx* c, cudaStream_t s);  // IAD: volumes, matrices, forces
 // ---- physics_mixed.cu (precision 1)
 void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s);
 void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s);

@@ -18,8 +18,11 @@ torch = pytest.importorskip("torch")
 SCALE = {"ax": "scale_a", "ay": "scale_a", "az": "scale_a", "du": "scale_du",
          "mumax": "scale_mu"}
 
-# (kernel, gradients, sinc_n)
-VARIANTS = [(1, 0, 5), (2, 0, 5), (0, 1, 5), (1, 1, 5), (2, 1, 6)]
+# (kernel, gradients, sinc_n) and the precision: 2 runs every variant in the
+# FP64-pipe kernels; 0 runs M4 and Wendland (kernel derivatives or IAD) in the
+# double-float kernels and sinc in the FP64-pipe ones
+VARIANTS = [((1, 0, 5), 2), ((2, 0, 5), 2), ((0, 1, 5), 2), ((1, 1, 5), 2), ((2, 1, 6), 2),
+            ((0, 1, 5), 0), ((1, 1, 5), 0), ((2, 1, 6), 0)]
 INPUTS = ["patch_ragged_av", "evrard12k"]
 
 
@@ -69,9 +72,9 @@ def _check_forces(arr, o, B):
 
 
 @pytest.mark.parametrize("name", INPUTS)
-@pytest.mark.parametrize("var", VARIANTS)
-def test_variant_density_forces_from_identical_inputs(B, orc, name, var):
-    s, prm, o = oracle_of(orc, name, var)
+@pytest.mark.parametrize("var,prec", VARIANTS)
+def test_variant_density_forces_from_identical_inputs(B, orc, name, var, prec):
+    s, prm, o = oracle_of(orc, name, var, precision=prec)
     ctx = B.Context(len(s["x"]))
     arr = B.alloc_arrays(s)
     ctx.build_neighbors(prm, arr)
@@ -87,9 +90,9 @@ def test_variant_density_forces_from_identical_inputs(B, orc, name, var):
 
 
 @pytest.mark.parametrize("name", INPUTS)
-@pytest.mark.parametrize("var", VARIANTS)
-def test_variant_one_step_matches_oracle(B, orc, name, var):
-    s, prm, o = oracle_of(orc, name, var)
+@pytest.mark.parametrize("var,prec", VARIANTS)
+def test_variant_one_step_matches_oracle(B, orc, name, var, prec):
+    s, prm, o = oracle_of(orc, name, var, precision=prec)
     st_o, ex = orc.step(prm, s, nsteps=1)
     ctx = B.Context(len(s["x"]))
     arr = B.alloc_arrays(s)
@@ -111,12 +114,14 @@ def test_variant_one_step_matches_oracle(B, orc, name, var):
     assert abs(host(arr["dt"])[0] - ex["dt"]) <= TOL_FP64 * ex["dt"]
 
 
+@pytest.mark.parametrize("var", [(1, 0, 5), (0, 1, 5), (1, 1, 5)])
 @pytest.mark.parametrize("lanes", [1, 4])
 @pytest.mark.parametrize("name", INPUTS)
-def test_wendland_double_float_path(B, orc, name, lanes):
-    # Wendland C2 with kernel derivatives at precision 0 runs in the
-    # double-float kernels (like M4): per call and one step against the oracle
-    s, prm0, o = oracle_of(orc, name, (1, 0, 5), precision=0)
+def test_double_float_variants_with_lanes(B, orc, name, lanes, var):
+    # Wendland C2 with kernel derivatives, and IAD with M4 or Wendland, at
+    # precision 0 run in the double-float kernels: per call and one step
+    # against the oracle with 1 and 4 lanes per particle
+    s, prm0, o = oracle_of(orc, name, var, precision=0)
     prm = dataclasses.replace(prm0, pair_threads=lanes)  # the cached parameters stay as they are
     ctx = B.Context(len(s["x"]))
     arr = B.alloc_arrays(s)
@@ -144,11 +149,12 @@ def test_wendland_double_float_path(B, orc, name, lanes):
     assert not np.array_equal(host(arr2["ax"]), host(arr["ax"]))
 
 
-def test_variant_with_precision_0_runs_the_fp64_kernels(B):
-    # IAD (and the sinc kernel) take the native FP64 pair kernels: precision 0
-    # and 2 give the same bits
+@pytest.mark.parametrize("grads", [0, 1])
+def test_sinc_with_precision_0_runs_the_fp64_kernels(B, grads):
+    # the sinc kernel exists only in the FP64-pipe kernels: precision 0 and 2
+    # give the same bits
     s, prm = _input("patch_ragged_av")
-    prm.kernel, prm.gradients = 1, 1
+    prm.kernel, prm.gradients = 2, grads
     out = []
     for prec in (0, 2):
         prm.precision = prec
@@ -188,13 +194,15 @@ def test_mixed_precision_rejects_variants(B, var):
     assert e.value.status == B.SPH_E_INVAL
 
 
-def test_variants_batched_equal_alone(B):
-    # two IAD + sinc instances of different sizes in one batch: each equals its run alone
+@pytest.mark.parametrize("var", [(2, 1, 4), (1, 1, 5)])
+def test_variants_batched_equal_alone(B, var):
+    # two IAD instances of different sizes in one batch (sinc on the FP64 pipe,
+    # Wendland in double-float): each equals its run alone
     insts = []
     for k, side in enumerate((9, 14)):
         s, p = ics.square_patch(side, seed=200 + k, omega=3.0 + k)
         s = ics.random_velocities(s, seed=210 + k, scale=1.0)
-        p.kernel, p.gradients, p.sinc_n = 2, 1, 4
+        p.kernel, p.gradients, p.sinc_n = var
         insts.append((s, p))
     alone = []
     for s, p in insts:
