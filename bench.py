@@ -424,17 +424,17 @@ def _run_ensemble(args, B, dev, stream):
     }
 
 
-# (name, kernel, gradients, sinc_n, precision): the M4 and Wendland kernels
-# (kernel derivatives or IAD) run in double-float at precision 0 and on the FP64
-# pipe at precision 2; the sinc kernel always takes the FP64-pipe kernels.
+# (name, kernel, gradients, sinc_n, precision): every kernel and gradient
+# variant runs in double-float at precision 0 and on the FP64 pipe at precision 2.
 VARIANTS = (("M4, kernel derivatives, FP64 pipe (precision 2)", 0, 0, 5, 2),
             ("Wendland C2, kernel derivatives, double-float (precision 0)", 1, 0, 5, 0),
             ("Wendland C2, kernel derivatives, FP64 pipe (precision 2)", 1, 0, 5, 2),
-            ("sinc n=5, kernel derivatives, FP64 pipe", 2, 0, 5, 0),
+            ("sinc n=5, kernel derivatives, double-float (precision 0)", 2, 0, 5, 0),
+            ("sinc n=5, kernel derivatives, FP64 pipe (precision 2)", 2, 0, 5, 2),
             ("M4, IAD gradients, double-float (precision 0)", 0, 1, 5, 0),
             ("Wendland C2, IAD gradients, double-float (precision 0)", 1, 1, 5, 0),
-            ("M4, IAD gradients, FP64 pipe (precision 2)", 0, 1, 5, 2),
-            ("sinc n=5, IAD gradients, FP64 pipe", 2, 1, 5, 0))
+            ("sinc n=5, IAD gradients, double-float (precision 0)", 2, 1, 5, 0),
+            ("M4, IAD gradients, FP64 pipe (precision 2)", 0, 1, 5, 2))
 
 
 def run_variants(args, B, dev, fp64_peak):
@@ -506,7 +506,7 @@ def run_variants(args, B, dev, fp64_peak):
 
 def kernel_names(kernel, grads, prec):
     """The force phase's kernels of a variant run."""
-    df = prec == 0 and kernel != 2
+    df = prec == 0
     if grads:
         return "k_volume_df + k_iad_df + k_forces_iad_df" if df else "k_volume + k_iad + k_forces_iad"
     return "k_forces_df" if df else "k_forces"

@@ -46,25 +46,89 @@ __device__ __forceinline__ df dw_shape(df q) {
     return q.hi < 1.0f ? fin : (q.hi < 2.0f ? fout : zero);
 }
 
-// Wendland C2 shapes (Table 1): g = (1 - q/2)^4 (1 + 2q), f = -q (1 - q/2)^3,
-// zero from q = 2 on; the normalisations 21/(16 pi) and 105/(16 pi) are
-// applied by the caller.
+// ---- Sinc kernel in double-float. With x = pi q / 2 <= pi and y = x^2,
+//   S(x) = sin x / x = sum_k (-1)^k y^k / (2k+1)!           (k = 0..14)
+//   S'(x) = x Q(y),  Q(y) = sum_k (-1)^k 2k y^(k-1) / (2k+1)!  (k = 1..14)
+// (the Taylor series of sin x / x and its term-by-term derivative; the
+// first omitted terms are below 3e-19 at x = pi, and neither form cancels at
+// small x). Coefficients as float pairs, computed at compile time.
+struct F2 {
+    float hi, lo;
+};
+
+constexpr F2 split_f2(double v) {
+    return F2{static_cast<float>(v), static_cast<float>(v - static_cast<double>(static_cast<float>(v)))};
+}
+
+constexpr int kSincTerms = 15;
+
+struct SincTab {
+    F2 p[kSincTerms];
+    F2 q[kSincTerms - 1];
+};
+
+constexpr SincTab make_sinc_tab() {
+    SincTab t{};
+    double inv = 1.0;  // 1 / (2k+1)!
+    for (int k = 0; k < kSincTerms; ++k) {
+        if (k > 0) inv = inv / ((2.0 * k) * (2.0 * k + 1.0));
+        const double sgn = (k % 2) ? -1.0 : 1.0;
+        t.p[k] = split_f2(sgn * inv);
+        if (k > 0) t.q[k - 1] = split_f2(sgn * 2.0 * k * inv);
+    }
+    return t;
+}
+
+__constant__ SincTab kSinc = make_sinc_tab();
+constexpr F2 kHalfPi = split_f2(0.5 * kPi);
+
+template <int M>
+__device__ __forceinline__ df horner(const F2* c, df y) {
+    df acc = {c[M - 1].hi, c[M - 1].lo};
+#pragma unroll
+    for (int k = M - 2; k >= 0; --k) acc = dfl::add(dfl::mul(acc, y), df{c[k].hi, c[k].lo});
+    return acc;
+}
+
+__device__ __forceinline__ df ipow_df(df v, int k) {
+    df r = {1.0f, 0.0f};
+    for (int e = 0; e < k; ++e) r = dfl::mul(r, v);
+    return r;
+}
+
+// Kernel shapes by kind (sn: the sinc exponent), zero from q = 2 on; the
+// normalisations (wnorm, dnorm) are applied by the caller.
+//   Wendland C2 (Table 1): g = (1 - q/2)^4 (1 + 2q), f = -q (1 - q/2)^3;
+//   sinc: g = S^n, f = n S^(n-1) S'(x) (dW/dr takes pi/2 into dnorm).
 template <int KER>
-__device__ __forceinline__ df w_shape_k(df q) {
+__device__ __forceinline__ df w_shape_k(df q, int sn) {
     if (KER == KER_M4) return w_shape(q);
+    const df zero = {0.0f, 0.0f};
+    if (KER == KER_SINC) {
+        if (!(q.hi < 2.0f)) return zero;
+        const df x = dfl::mul(q, df{kHalfPi.hi, kHalfPi.lo});
+        return ipow_df(horner<kSincTerms>(kSinc.p, dfl::sqr(x)), sn);
+    }
     const df t = dfl::addf(dfl::scale2(dfl::neg(q), 0.5f), 1.0f);
     const df t2 = dfl::sqr(t);
     const df g = dfl::mul(dfl::sqr(t2), dfl::addf(dfl::scale2(q, 2.0f), 1.0f));
-    const df zero = {0.0f, 0.0f};
     return q.hi < 2.0f ? g : zero;
 }
 
 template <int KER>
-__device__ __forceinline__ df dw_shape_k(df q) {
+__device__ __forceinline__ df dw_shape_k(df q, int sn) {
     if (KER == KER_M4) return dw_shape(q);
+    const df zero = {0.0f, 0.0f};
+    if (KER == KER_SINC) {
+        if (!(q.hi < 2.0f)) return zero;
+        const df x = dfl::mul(q, df{kHalfPi.hi, kHalfPi.lo});
+        const df y = dfl::sqr(x);
+        const df S = horner<kSincTerms>(kSinc.p, y);
+        const df dS = dfl::mul(x, horner<kSincTerms - 1>(kSinc.q, y));
+        return dfl::mul(dfl::mulf(ipow_df(S, sn - 1), (float)sn), dS);
+    }
     const df t = dfl::addf(dfl::scale2(dfl::neg(q), 0.5f), 1.0f);
     const df f = dfl::neg(dfl::mul(q, dfl::mul(dfl::sqr(t), t)));
-    const df zero = {0.0f, 0.0f};
     return q.hi < 2.0f ? f : zero;
 }
 
@@ -100,8 +164,7 @@ __device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, d
 
 // ------------------------------------------------------------ density
 // T lanes per particle: lane s of particle i takes row entries s, s + T, ...
-// KER: the M4 spline or the Wendland C2 kernel (the other Table 1 variants
-// run in physics.cu).
+// KER: the M4 spline, the Wendland C2 or the sinc kernel.
 template <bool FUSE, int T, int KER>
 __global__ void __launch_bounds__(kThreads)
 k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
@@ -122,6 +185,7 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     if (act) {
     pi = posh[i];
     const double hinv = 1.0 / pi.w;
+    const int sn = kp.sinc_n;
     const df Hi = dfl::from_double_fp64(hinv);
     const Grid& g = B.grid[inst];
     const bool per = kp.periodic_z != 0;
@@ -142,7 +206,7 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         df w = {1.0f, 0.0f};  // coincident particles: q = 0
         if (r2.hi > 0.0f) {
             const df q = dfl::mul(dfl::mul(r2, dfl::rsqrt(r2)), Hi);
-            w = w_shape_k<KER>(q);
+            w = w_shape_k<KER>(q, sn);
         }
         acc = dfl::add(acc, dfl::mul(mj, w));
     }
@@ -178,6 +242,10 @@ static void density_df_t(sph_ctx* c, cudaStream_t s) {
         k_density_df<FUSE, T, KER_WENDLAND><<<nb, kThreads, 0, s>>>(
             n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
             c->pint, c->cint);
+    else if (c->kern_kind == KER_SINC)
+        k_density_df<FUSE, T, KER_SINC><<<nb, kThreads, 0, s>>>(
+            n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
+            c->pint, c->cint);
     else
         k_density_df<FUSE, T, KER_M4><<<nb, kThreads, 0, s>>>(
             n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
@@ -206,7 +274,7 @@ void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
 // f(q_j)/h_j^4)/r, one shared reciprocal R = 1/((r^2 + eta2 hb^2) rhob) for the
 // viscosity, mu = hb v.r rhob R, 1/rhob = (r^2 + eta2 hb^2) R.
 template <int T, int KER>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, KER == KER_SINC ? 2 : 3)
 k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
             const float4* __restrict__ xpk, const double* __restrict__ cint,
@@ -232,6 +300,7 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const Grid& gr = B.grid[inst];
         const bool per = kp.periodic_z != 0;
         const float hlz = gr.halflzf, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
+        const int sn = kp.sinc_n;
         const df c_half_pi = dfl::from_double_fp64(0.5 * (KER == KER_M4 ? kInvPiD : kp.dnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
@@ -251,8 +320,8 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             if (!(r2.hi > 0.0f)) continue;  // coincident particles exert no force
             const df rinv = dfl::rsqrt(r2);
             const df r = dfl::mul(r2, rinv);
-            const df fa = dw_shape_k<KER>(dfl::mul(r, Hi));
-            const df fb = dw_shape_k<KER>(dfl::mul(r, df{b0.x, b0.y}));
+            const df fa = dw_shape_k<KER>(dfl::mul(r, Hi), sn);
+            const df fb = dw_shape_k<KER>(dfl::mul(r, df{b0.x, b0.y}), sn);
             const df Fb = dfl::mul(dfl::add(dfl::mul(Ki, fa), dfl::mul(df{b0.z, b0.w}, fb)),
                                    dfl::mul(rinv, c_half_pi));
             const df WX = dfl::from_double(vi.x - vj.x), WY = dfl::from_double(vi.y - vj.y);
@@ -325,6 +394,10 @@ static void forces_df_t(sph_ctx* c, cudaStream_t s) {
         k_forces_df<T, KER_WENDLAND><<<nb, kThreads, 0, s>>>(
             n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
             c->mumax, c->dt_part);
+    else if (c->kern_kind == KER_SINC)
+        k_forces_df<T, KER_SINC><<<nb, kThreads, 0, s>>>(
+            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
+            c->mumax, c->dt_part);
     else
         k_forces_df<T, KER_M4><<<nb, kThreads, 0, s>>>(
             n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
@@ -378,6 +451,7 @@ k_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     double hinv = 1.0;
     if (act) {
         hinv = 1.0 / posh[i].w;
+        const int sn = B.kp[inst].sinc_n;
         const df Hi = dfl::from_double_fp64(hinv);
         const Grid& g = B.grid[inst];
         const bool per = B.kp[inst].periodic_z != 0;
@@ -396,7 +470,7 @@ k_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const df r2 = dfl::add(dfl::add(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
             if (!(r2.hi > 0.0f)) continue;  // r = 0 adds nothing to tau
             const df q = dfl::mul(dfl::mul(r2, dfl::rsqrt(r2)), Hi);
-            const df w = dfl::mul(df{vj.x, vj.y}, w_shape_k<KER>(q));
+            const df w = dfl::mul(df{vj.x, vj.y}, w_shape_k<KER>(q, sn));
             const df wx = dfl::mul(w, X), wy = dfl::mul(w, Y);
             t[0] = dfl::add(t[0], dfl::mul(wx, X));
             t[1] = dfl::add(t[1], dfl::mul(wx, Y));
@@ -468,6 +542,7 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const Grid& gr = B.grid[inst];
         const bool per = kp.periodic_z != 0;
         const float hlz = gr.halflzf, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
+        const int sn = kp.sinc_n;
         const df kg = dfl::from_double_fp64(-0.5 * (KER == KER_M4 ? kInvPiD : kp.wnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
@@ -487,8 +562,8 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             if (!(r2.hi > 0.0f)) continue;  // coincident particles exert no force
             const df r = dfl::mul(r2, dfl::rsqrt(r2));
             const df Hj = {b0.x, b0.y};
-            const df wi = dfl::mul(Hi3, w_shape_k<KER>(dfl::mul(r, Hi)));
-            const df wj = dfl::mul(dfl::mul(Hj, dfl::sqr(Hj)), w_shape_k<KER>(dfl::mul(r, Hj)));
+            const df wi = dfl::mul(Hi3, w_shape_k<KER>(dfl::mul(r, Hi), sn));
+            const df wj = dfl::mul(dfl::mul(Hj, dfl::sqr(Hj)), w_shape_k<KER>(dfl::mul(r, Hj), sn));
             df M[6];
             {
                 const float4 d0 = __ldg(&cpk[3 * j]), d1 = __ldg(&cpk[3 * j + 1]);
@@ -595,6 +670,7 @@ void launch_forces_iad_df(sph_ctx* c, cudaStream_t s) {
     k_volume_df<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         n, batch_of(c), c->velm[b], c->therm, c->vdf);
     if (c->kern_kind == KER_WENDLAND) iad_df_k<KER_WENDLAND>(c, s);
+    else if (c->kern_kind == KER_SINC) iad_df_k<KER_SINC>(c, s);
     else iad_df_k<KER_M4>(c, s);
 }
 

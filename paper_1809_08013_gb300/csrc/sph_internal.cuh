@@ -230,12 +230,9 @@ namespace sph {
 
 inline Batch batch_of(const sph_ctx* c) { return Batch{c->blk, c->ioff, c->icnt, c->grid, c->kpi}; }
 
-// The pair sums run in the native FP64 kernels: precision 2 or the sinc
-// kernel (which exists only there). The M4 and Wendland C2 kernels, with
-// kernel-derivative or IAD gradients, also run in double-float.
-inline bool native_pairs(const sph_ctx* c) {
-    return c->prec == PREC_FP64_NATIVE || c->kern_kind == KER_SINC;
-}
+// The pair sums run in the native FP64 kernels at precision 2; at precision
+// 0 every kernel and gradient variant runs in double-float.
+inline bool native_pairs(const sph_ctx* c) { return c->prec == PREC_FP64_NATIVE; }
 
 // Rows of S_i for the pair kernels: the row slab unless a row overflowed it
 // (device flag IF_SLAB_OVF), in which case the CSR built by the fallback.
