@@ -346,3 +346,44 @@ def test_neighbours_do_not_depend_on_cell_width(B, orc, cell_scale):
     assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
     off, idx, ng, order = ctx.neighbors_to_host()
     assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
+
+
+def _moved(name):
+    """Inputs far from the unit box: the chunk exponent, the FP32 border band
+    of the h search and the periodic wrap all follow the coordinates' range."""
+    if name == "evrard_translated":
+        s, prm = ics.evrard(4000, seed=61)
+        s = ics.random_velocities(s, seed=62, scale=0.5)
+        s["x"] = s["x"] + 1000.0
+        s["y"] = s["y"] - 500.0
+        s["z"] = s["z"] + 250.0
+        return s, prm
+    s, prm = ics.square_patch(14, seed=63)
+    s = ics.random_velocities(s, seed=64, scale=1.0)
+    sc = 1e-6
+    for k in ("x", "y", "z", "h"):
+        s[k] = s[k] * sc
+    s["m"] = s["m"] * sc ** 3   # the same density
+    prm.lz = prm.lz * sc
+    return s, prm
+
+
+@pytest.mark.parametrize("name", ["evrard_translated", "patch_micro"])
+@pytest.mark.parametrize("precision", [0, 2])
+def test_far_from_unit_box(B, orc, name, precision):
+    s, prm = _moved(name)
+    prm.precision = precision
+    o = orc.pipeline(prm, s)
+    ctx, arr, st = gpu_build(B, prm, s)
+    assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
+    off, idx, ng, order = ctx.neighbors_to_host()
+    assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
+    ctx.density(prm, arr)
+    assert normwise(host(arr["rho"]), o["rho"]) <= TOL_FP64
+    for k in ("rho", "p", "c"):
+        arr[k].copy_(torch.from_numpy(o[k]))
+    ctx.forces(prm, arr)
+    ctx.sync()
+    for k in ("ax", "ay", "az", "du", "mumax"):
+        assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
+    assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
