@@ -24,8 +24,6 @@ using dfl::df;
 
 namespace {
 
-constexpr double kInvPiD = 0.31830988618379067154;
-
 // pi h^3 W as a function of q >= 0 (cubic spline).
 __device__ __forceinline__ df w_shape(df q) {
     const df q2 = dfl::sqr(q);
@@ -216,7 +214,7 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         if (!act || sub != 0) return;
     }
     const double hinv = 1.0 / pi.w;
-    const double sigma = hinv * hinv * hinv * (KER == KER_M4 ? kInvPiD : kp.wnorm);
+    const double sigma = hinv * hinv * hinv * (KER == KER_M4 ? kInvPi : kp.wnorm);
     const double rho = dfl::to_double(acc) * sigma;
     if (FUSE) {
         double p, c;
@@ -301,7 +299,7 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const bool per = kp.periodic_z != 0;
         const float hlz = gr.halflzf, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
         const int sn = kp.sinc_n;
-        const df c_half_pi = dfl::from_double_fp64(0.5 * (KER == KER_M4 ? kInvPiD : kp.dnorm));
+        const df c_half_pi = dfl::from_double_fp64(0.5 * (KER == KER_M4 ? kInvPi : kp.dnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
         for (int e = sub; e < len; e += T) {
@@ -485,7 +483,7 @@ k_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         for (int k = 0; k < 6; ++k) t[k] = dfl::lane_sum<T>(t[k]);
         if (!act || sub != 0) return;
     }
-    const double sg = hinv * hinv * hinv * (KER == KER_M4 ? kInvPiD : B.kp[inst].wnorm);
+    const double sg = hinv * hinv * hinv * (KER == KER_M4 ? kInvPi : B.kp[inst].wnorm);
     double a[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) a[k] = dfl::to_double(t[k]) * sg;
@@ -543,7 +541,7 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const bool per = kp.periodic_z != 0;
         const float hlz = gr.halflzf, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
         const int sn = kp.sinc_n;
-        const df kg = dfl::from_double_fp64(-0.5 * (KER == KER_M4 ? kInvPiD : kp.wnorm));
+        const df kg = dfl::from_double_fp64(-0.5 * (KER == KER_M4 ? kInvPi : kp.wnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
         for (int e = sub; e < len; e += T) {

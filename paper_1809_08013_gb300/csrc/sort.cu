@@ -82,7 +82,7 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
                const double* __restrict__ cs, double4_32a* __restrict__ posh,
                double4_32a* __restrict__ velm, double4_32a* __restrict__ therm,
                double2* __restrict__ kern, double* __restrict__ cint, float4* __restrict__ dpk,
-               float2* __restrict__ mdf, float4* __restrict__ xpk, const Grid* __restrict__ grid) {
+               float4* __restrict__ xpk, const Grid* __restrict__ grid) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t o = order[k];
@@ -91,9 +91,7 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
     const double4_32a ps = make_double4_32a(x[o], y[o], z[o], hh);
     posh[k] = ps;
     const double mm = m[o];
-    const dfl::df md = dfl::from_double_fp64(mm);
-    mdf[k] = make_float2(md.hi, md.lo);
-    write_xpk(xpk, k, ps, md, grid[0].fxk);  // a single problem: instance 0
+    write_xpk(xpk, k, ps, dfl::from_double_fp64(mm), grid[0].fxk);  // a single problem: instance 0
     if (what == GATHER_DENSITY) {
         velm[k] = make_double4_32a(0.0, 0.0, 0.0, mm);
     } else {
@@ -117,8 +115,8 @@ void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, 
     c->launches += 1;
     k_gather_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         n, what, kp.alpha, c->order[b], P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m,
-        P->rho, P->p, P->c, c->posh[b], c->velm[b], c->therm, c->kern, c->cint, c->dpk, c->mdf,
-        c->xpk, c->grid);
+        P->rho, P->p, P->c, c->posh[b], c->velm[b], c->therm, c->kern, c->cint, c->dpk, c->xpk,
+        c->grid);
 }
 
 // ------------------------------------------------------------ bbox and grid
@@ -465,8 +463,7 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
           const double4_32a* __restrict__ velm_in, const double* __restrict__ u_in,
           const int32_t* __restrict__ order_in, double4_32a* __restrict__ posh_out,
           double4_32a* __restrict__ velm_out, double* __restrict__ u_out,
-          int32_t* __restrict__ order_out, float4* __restrict__ fpos, float2* __restrict__ mdf,
-          float4* __restrict__ xpk) {
+          int32_t* __restrict__ order_out, float4* __restrict__ fpos, float4* __restrict__ xpk) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ntot) return;
     const int inst = (int)(keys[r] >> 24);
@@ -476,9 +473,7 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
     posh_out[k] = p;
     const double4_32a v = velm_in[o];
     velm_out[k] = v;
-    const dfl::df m = dfl::from_double_fp64(v.w);
-    mdf[k] = make_float2(m.hi, m.lo);
-    write_xpk(xpk, k, p, m, B.grid[inst].fxk);
+    write_xpk(xpk, k, p, dfl::from_double_fp64(v.w), B.grid[inst].fxk);
     u_out[k] = u_in[o];
     order_out[k] = order_in[o];
     fpos[k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
@@ -551,7 +546,7 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const int a = c->cur, b = 1 - c->cur;
     k_permute<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->vals[src], c->posh[a],
                                         c->velm[a], c->ue[a], c->order[a], c->posh[b], c->velm[b],
-                                        c->ue[b], c->order[b], c->fpos, c->mdf, c->xpk);
+                                        c->ue[b], c->order[b], c->fpos, c->xpk);
     c->cur = b;
     k_cells_clear<<<dim3(64, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->cells, c->cell_hmax);
     k_cells_mark<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->cells);

@@ -113,7 +113,7 @@ bool dalloc(T** p, size_t count) {
 
 void free_all(sph_ctx* c) {
     void* ptrs[] = {c->posh[0], c->posh[1], c->velm[0], c->velm[1], c->ue[0], c->ue[1],
-                    c->therm, c->kern, c->acc, c->pint, c->cint, c->dpk, c->mdf, c->mpk, c->mumax, c->fpos, c->tin, c->order[0],
+                    c->therm, c->kern, c->acc, c->pint, c->cint, c->dpk, c->mpk, c->mumax, c->fpos, c->tin, c->order[0],
                     c->order[1], c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist,
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
@@ -183,7 +183,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
     }
     ok = ok && al(&c->therm, N) && al(&c->kern, N) && al(&c->acc, N) &&
          al(&c->pint, N) && al(&c->cint, N) && al(&c->dpk, 3 * N) &&
-         al(&c->mdf, N) && al(&c->xpk, 3 * N) && al(&c->mpk, 5 * N) &&
+         al(&c->xpk, 3 * N) && al(&c->mpk, 5 * N) &&
          al(&c->mumax, N) && al(&c->iad_a, N) && al(&c->iad_b, N) && al(&c->vol, N) && al(&c->vdf, N) &&
          al(&c->cpk, 3 * N) &&
          al(&c->fpos, N) && al(&c->tin, N) &&

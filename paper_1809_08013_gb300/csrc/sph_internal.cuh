@@ -169,7 +169,6 @@ struct sph_ctx {
     double* pint;
     double* cint;
     float4* dpk;            // 3 per particle: double-float pack of the force kernel
-    float2* mdf;            // mass as a float pair
     float4* xpk;            // 3 per particle: exact fixed-point chunks of the position
                             // and the mass as a float pair (double-float pair kernels)
     float4* mpk;            // 5 per particle: pack of the mixed-precision pair kernels
