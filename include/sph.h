@@ -83,10 +83,10 @@ typedef struct {
     double cell_scale;   /* cell width = 2 <h> cell_scale (0 selects the default 1.0); a tuning
                             knob of the neighbour search: h and the neighbour sets do not
                             depend on it */
-    /* Variants of Table 1 (support 2h for all kernels, q = r/h). Any choice but
-       (0, 0) runs the density and force sums in native FP64 (as precision 2;
-       pair_threads is ignored) and needs precision 0 or 2: with precision 1
-       it is SPH_E_INVAL. The neighbour search does not depend on them. */
+    /* Variants of Table 1 (support 2h for all kernels, q = r/h). They run in
+       the double-float pair kernels at precision 0 and on the FP64 pipe at
+       precision 2; with precision 1 any choice but (0, 0) is SPH_E_INVAL. The
+       neighbour search does not depend on them. */
     int32_t kernel;      /* SPH_KERNEL_*: 0 = M4 cubic spline (1/(pi h^3)) (t^3/4 - s^3),
                             t = max(2-q, 0), s = max(1-q, 0);
                             1 = Wendland C2, 21/(16 pi h^3) (1 - q/2)^4 (1 + 2q) for q < 2;
