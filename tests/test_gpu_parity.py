@@ -387,3 +387,27 @@ def test_far_from_unit_box(B, orc, name, precision):
     for k in ("ax", "ay", "az", "du", "mumax"):
         assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
     assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("var", [(0, 0), (2, 1)])
+def test_coincident_particles(B, orc, precision, var):
+    # a particle and its copy at the same place (r = 0): the density counts
+    # the copy at W(0), the forces and the IAD matrix skip the pair
+    s, prm = ics.square_patch(12, seed=71)
+    s = ics.random_velocities(s, seed=72, scale=1.0)
+    s = {k: np.concatenate([v, v[[400, 900]]]) for k, v in s.items()}
+    prm.precision = precision
+    prm.kernel, prm.gradients = var
+    o = orc.pipeline(prm, s)
+    ctx, arr, st = gpu_build(B, prm, s)
+    assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
+    ctx.density(prm, arr)
+    assert normwise(host(arr["rho"]), o["rho"]) <= TOL_FP64
+    for k in ("rho", "p", "c"):
+        arr[k].copy_(torch.from_numpy(o[k]))
+    ctx.forces(prm, arr)
+    ctx.sync()
+    for k in ("ax", "ay", "az", "du", "mumax"):
+        assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
+    assert np.all(np.isfinite(host(arr["ax"])))
