@@ -14,7 +14,7 @@ Workloads (Section 4.1, Table 5):
   omega = 5. Tait equation of state with rho0 = 1000, c0 = 50, u = 0.
 * Evrard collapse (Section 4.1.2): a sphere of radius R = 1 and mass M = 1
   with rho(r) = M / (2 pi R^2 r) (the Evrard density profile), u0 = 0.05,
-  ideal gas gamma = 5/3, v = 0. Self-gravity is not part of this build.
+  ideal gas gamma = 5/3, v = 0. Self-gravity (Algorithm 1 step 4) is not computed.
 
 Readings where the paper is silent or garbled:
 
