@@ -83,6 +83,11 @@ def header_functions() -> list:
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(sph_\w+)\s*\(", text, re.M)))
 
 
+def lib_path() -> str:
+    """Path of the in-tree libsph.so (built if missing or stale)."""
+    return _build.build()
+
+
 def load(rebuild: bool = True):
     """Load libsph.so (building it first if sources changed). Raises if it cannot."""
     global _lib

@@ -78,3 +78,39 @@ def test_param_struct_layout_matches_header():
         size, offs = _c_layout(name, fields)
         assert C.sizeof(cls) == size, name
         assert [getattr(cls, f).offset for f in fields] == offs, name
+
+def test_plain_c_caller_compiles_and_links(lib):
+    # the header is plain C99 and every symbol the example calls resolves
+    # against the library at link time (the program is not run here)
+    import os
+    import subprocess
+    import tempfile
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    so = binding.lib_path()
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "example")
+        subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                               os.path.join(root, "tests", "c_abi_example.c"),
+                               "-L", os.path.dirname(so), "-l:" + os.path.basename(so),
+                               "-Wl,-rpath," + os.path.dirname(so), "-lm", "-o", exe])
+        assert os.path.getsize(exe) > 0
+
+
+@pytest.mark.gpu
+def test_plain_c_caller_runs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    import subprocess
+    import tempfile
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    so = binding.lib_path()
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "example")
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(root, "include"),
+                               os.path.join(root, "tests", "c_abi_example.c"),
+                               "-L", os.path.dirname(so), "-l:" + os.path.basename(so),
+                               "-Wl,-rpath," + os.path.dirname(so), "-lm", "-o", exe])
+        out = subprocess.check_output([exe], text=True)
+    assert "sm_103a" in out and "dt=" in out
