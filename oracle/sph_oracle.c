@@ -602,7 +602,7 @@ int orc_csr_fill(const orc_params *P, int64_t n, const double *x, const double *
 }
 
 /* ---------------------------------------------------------------------------
- * Density summation (Section 2, step 3 "density"): standard volume elements,
+ * Density summation (Section 2, Algorithm 1 step 3, the density): standard volume elements,
  *   rho_i = m_i W(0, h_i) + sum_{j in N_i} m_j W(r_ij, h_i),
  * with W the selected kernel.
  * ------------------------------------------------------------------------- */
@@ -625,7 +625,7 @@ void orc_density(const orc_params *P, int64_t n, const double *x, const double *
 }
 
 /* ---------------------------------------------------------------------------
- * Integral approach to derivatives, IAD (Table 1 "Gradients calculation";
+ * Integral approach to derivatives, IAD (the gradients column of Table 1;
  * Garcia-Senz, Cabezon and Escartin 2012). With volume elements V_j = m_j /
  * rho_j and the gather set N_i, the symmetric 3x3 matrix
  *   tau_i = sum_{j in N_i} V_j W(r_ij, h_i) (r_j - r_i) (r_j - r_i)^T
@@ -736,9 +736,10 @@ void orc_eos(const orc_params *P, int64_t n, const double *rho, const double *u,
 }
 
 /* ---------------------------------------------------------------------------
- * Momentum and energy with Monaghan artificial viscosity (Section 2, step 3
- * "acceleration, rate of change of internal energy"; Table 1 "standard"
- * volume elements and "kernel derivatives" gradients). For j in S_i:
+ * Momentum and energy with Monaghan artificial viscosity (Section 2,
+ * Algorithm 1 step 3: the accelerations and the rates of change of the
+ * internal energy; Table 1: standard volume elements, gradients from kernel
+ * derivatives). For j in S_i:
  *   r_ij = r_i - r_j, v_ij = v_i - v_j, r = |r_ij|
  *   Fbar_ij = (dW/dr(r, h_i) + dW/dr(r, h_j)) / 2 / r  (each zero outside its
  *             own support), so grad_i Wbar_ij = Fbar_ij r_ij

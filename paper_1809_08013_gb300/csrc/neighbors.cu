@@ -1,4 +1,4 @@
-// neighbors.cu -- Algorithm 1 step 2 ("find neighbours and smoothing length").
+// neighbors.cu -- Algorithm 1 step 2: the neighbours and the smoothing length.
 //
 // Pair test. The definition is the FP64 test r_ij^2 < (2h)^2 with
 // r^2 = (dx dx + dy dy) + dz dz, each operation rounded on its own (minimum

@@ -1,4 +1,4 @@
-// sort.cu -- Algorithm 1 step 1 ("build tree"), done as Morton-sorted cell
+// sort.cu -- Algorithm 1 step 1 (the tree build), done as Morton-sorted cell
 // lists: bounding box and cell grid on the device, 24-bit Morton key of each
 // particle's cell, a stable LSD radix sort (3 passes of 8 bits, one more for
 // the instance id of a batch), the permutation of the particle state into
