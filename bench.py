@@ -376,6 +376,8 @@ def _run_ensemble(args, B, dev, stream):
     batched = {k: arr[k].cpu().numpy() for k in ("x", "y", "z", "vx", "vy", "vz", "h", "u")}
     del g
 
+    staged = _run_staged(B, dev, stream, insts, counts, tuned, K, batched)
+
     # the plain single-instance path, one instance after another on one context
     one = B.Context(max(counts), device=dev.index)
     t_alone = []
@@ -416,12 +418,95 @@ def _run_ensemble(args, B, dev, stream):
                                  "own_time_ms_p50": float(np.percentile(t_alone, 50)),
                                  "own_time_ms_p99": float(np.percentile(t_alone, 99)),
                                  "launch": "sph_step per instance, one after another"},
+        "staged": staged,
         "batched_equals_single_bitwise": bool(same),
         "autotune": {"chosen": tuned, "trials": tune["trials"],
                      "method": "sph_autotune: one coordinate-descent pass over pair_threads "
                                "{1,2,4}, cell_scale {0.875,1,1.25}, defer_lanes {8,16}; 2 timed "
                                "steps per trial"},
     }
+
+
+def _run_staged(B, dev, stream, insts, counts, tuned, K, batched, stages=4):
+    """The ensemble as `stages` batches run back to back, the instances taken
+    in order of size and cut into groups of about equal particle count, each
+    group its own context and captured graph of sph_batch_step(K). An
+    instance's latency is the end of its group's replay, so the small
+    instances finish early; the results equal the one-graph batch's bitwise."""
+    import numpy as np
+    import torch
+    from paper_1809_08013_gb300 import ics
+    order = np.argsort(np.array(counts), kind="stable")
+    tot = int(sum(counts))
+    groups, cur, acc = [], [], 0
+    for k in order:
+        cur.append(int(k))
+        acc += counts[k]
+        if len(groups) < stages - 1 and acc >= tot * (len(groups) + 1) / stages:
+            groups.append(cur)
+            cur = []
+    if cur:
+        groups.append(cur)
+    runs = []
+    for gi in groups:
+        sub = [insts[k] for k in gi]
+        cnt = [counts[k] for k in gi]
+        state = {f: np.concatenate([s[f] for s, _ in sub]) for f in B.STATE_FIELDS}
+        ctx = B.Context(sum(cnt), max_instances=len(sub), device=dev.index)
+        ctx.batch_set(cnt, [ics.SphParams(**{**p.as_dict(), **tuned}) for _, p in sub],
+                      stream=stream)
+        arr = B.alloc_arrays(state, device=dev, ninst=len(sub))
+        ic = {f: arr[f].clone() for f in B.STATE_FIELDS}
+
+        def reset(arr=arr, ic=ic):
+            for f in B.STATE_FIELDS:
+                arr[f].copy_(ic[f])
+            arr["time"].zero_()
+
+        ctx.batch_step(arr, nsteps=1, stream=stream)  # untimed
+        ctx.sync(stream)
+        reset()
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            ctx.batch_step(arr, nsteps=K, stream=stream)
+        g.replay()  # warm replay
+        torch.cuda.synchronize(dev)
+        reset()
+        torch.cuda.synchronize(dev)
+        runs.append((ctx, arr, g))
+    e0 = torch.cuda.Event(enable_timing=True)
+    ends = [torch.cuda.Event(enable_timing=True) for _ in runs]
+    e0.record(stream)
+    for (_, _, g), e in zip(runs, ends):
+        g.replay()
+        e.record(stream)
+    torch.cuda.synchronize(dev)
+    t_end = [e0.elapsed_time(e) for e in ends]
+    st = max(ctx.sync(stream) for ctx, _, _ in runs)
+    lat = np.concatenate([[t_end[q]] * len(gi) for q, gi in enumerate(groups)])
+    off = np.concatenate([[0], np.cumsum(counts)])
+    same = True
+    for (ctx, arr, _), gi in zip(runs, groups):
+        host = {f: arr[f].cpu().numpy() for f in batched}
+        pos = 0
+        for k in gi:
+            for f in batched:
+                same = same and np.array_equal(host[f][pos:pos + counts[k]].view(np.uint8),
+                                               batched[f][off[k]:off[k + 1]].view(np.uint8))
+            pos += counts[k]
+    for ctx, arr, g in runs:
+        del g
+    del runs
+    torch.cuda.empty_cache()
+    return {"stages": len(groups), "instances_per_stage": [len(gi) for gi in groups],
+            "particles_per_stage": [int(sum(counts[k] for k in gi)) for gi in groups],
+            "stage_end_ms": t_end, "ms": t_end[-1],
+            "updates_per_s": tot * K / (t_end[-1] * 1e-3),
+            "latency_ms_p50": float(np.percentile(lat, 50)),
+            "latency_ms_p99": float(np.percentile(lat, 99)),
+            "launch": f"{len(groups)} CUDA graphs of sph_batch_step, smallest instances first",
+            "equals_batched_bitwise": bool(same), "status": B.STATUS_NAMES.get(st)}
 
 
 # (name, kernel, gradients, sinc_n, precision): every kernel and gradient
