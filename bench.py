@@ -427,15 +427,11 @@ def _run_ensemble(args, B, dev, stream):
     }
 
 
-def _run_staged(B, dev, stream, insts, counts, tuned, K, batched, stages=4):
-    """The ensemble as `stages` batches run back to back, the instances taken
-    in order of size and cut into groups of about equal particle count, each
-    group its own context and captured graph of sph_batch_step(K). An
-    instance's latency is the end of its group's replay, so the small
-    instances finish early; the results equal the one-graph batch's bitwise."""
+def stage_groups(counts, stages):
+    """Instance indices in order of size (stable), cut into at most `stages`
+    consecutive groups, a group closing once the running particle count
+    reaches the next multiple of total / stages."""
     import numpy as np
-    import torch
-    from paper_1809_08013_gb300 import ics
     order = np.argsort(np.array(counts), kind="stable")
     tot = int(sum(counts))
     groups, cur, acc = [], [], 0
@@ -447,6 +443,20 @@ def _run_staged(B, dev, stream, insts, counts, tuned, K, batched, stages=4):
             cur = []
     if cur:
         groups.append(cur)
+    return groups
+
+
+def _run_staged(B, dev, stream, insts, counts, tuned, K, batched, stages=4):
+    """The ensemble as `stages` batches run back to back, the instances taken
+    in order of size and cut into groups of about equal particle count, each
+    group its own context and captured graph of sph_batch_step(K). An
+    instance's latency is the end of its group's replay, so the small
+    instances finish early; the results equal the one-graph batch's bitwise."""
+    import numpy as np
+    import torch
+    from paper_1809_08013_gb300 import ics
+    tot = int(sum(counts))
+    groups = stage_groups(counts, stages)
     runs = []
     for gi in groups:
         sub = [insts[k] for k in gi]

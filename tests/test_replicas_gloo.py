@@ -80,3 +80,4 @@ def test_two_gloo_replicas(tmp_path, capfd):
 def test_single_rank_needs_no_process_group():
     assert bench.max_over_ranks(12.5, 1, None) == 12.5
     assert bench.whole_job_rate(1, 1000, 10, 2.0) == pytest.approx(5e6)
+
