@@ -15,6 +15,12 @@ hydrodynamics only) of 10^6 particles with the mixed-precision pair kernels.
 N > 1 runs under torchrun as independent replicas (one instance per GPU, no
 collective on the data path; the barrier and max-over-ranks timing only).
 --impl reference times the CPU oracle on the host cores instead.
+
+Besides value / e2e (through sph_step_host on pinned host arrays) / roofline /
+cpu_baseline / clocks, the line carries the steady state (steps 2..K), the
+27k-particle small case, the 256-instance ensemble (one graph, staged by size,
+and one instance at a time), the serving stream, and the Table 1 variants at
+the benchmark size; --no-ensemble, --no-serving, --no-variants skip them.
 """
 from __future__ import annotations
 
