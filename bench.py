@@ -9,7 +9,7 @@ step through the C ABI (sph_step). Prints one JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
                   [--workload patch|evrard] [--precision fp64|mixed]
 
---workload evrard --precision mixed is the Evrard collapse (Section 4.1.2,
+--workload evrard --precision mixed is the Evrard collapse (Section 5.1.2,
 hydrodynamics only) of 10^6 particles with the mixed-precision pair kernels.
 
 N > 1 runs under torchrun as independent replicas (one instance per GPU, no
@@ -168,13 +168,13 @@ def workload_name(args, n=None):
             "positions, h, neighbour sets and integration)")
     if args.workload == "evrard":
         n = n or args.n
-        return (f"Evrard collapse, hydrodynamics only, {n:,} particles (Section 4.1.2: R=M=1, "
+        return (f"Evrard collapse, hydrodynamics only, {n:,} particles (Section 5.1.2: R=M=1, "
                 f"rho ~ 1/r sampled r=R sqrt(U), u=0.05, ideal gas gamma=5/3, v=0), {prec}, "
                 f"cubic spline, h iterated to 100+-5 neighbours every step, Monaghan AV alpha=1 "
                 f"beta=2, CFL 0.3, kick-drift leapfrog from the initial conditions")
     side = args.side if n is None else round(n ** (1 / 3))
     n = side ** 3
-    return (f"rotating square patch {side}^3 = {n:,} particles (Section 4.1.1: lattice dx=1/{side}, "
+    return (f"rotating square patch {side}^3 = {n:,} particles (Section 5.1.1: lattice dx=1/{side}, "
             f"jitter 0.01 dx, omega=5, rho0=1000, Tait c0=50, periodic z), {prec}, cubic spline, "
             f"h iterated to 100+-5 neighbours every step, Monaghan AV alpha=1 beta=2, CFL 0.3, "
             f"kick-drift leapfrog from the initial conditions")

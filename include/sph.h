@@ -1,7 +1,7 @@
 /*
  * sph.h -- C ABI of libsph, the GB300 (sm_103a) implementation of the SPH
  * time-step hot path of "Towards a Mini-App for Smoothed Particle
- * Hydrodynamics at Exascale" (arXiv 1809.08013), Section 2, Algorithm 1:
+ * Hydrodynamics at Exascale" (arXiv 1809.08013), Section 3, Algorithm 1:
  *
  *   1. build tree            -> Morton-sorted uniform cell lists
  *   2. find neighbours and h -> sph_build_neighbors
@@ -50,7 +50,7 @@ typedef enum {
     SPH_E_TIMEOUT = 6    /* reserved for bounded device waits */
 } sph_status;
 
-/* Physical and numerical parameters (Section 4.1 workloads). */
+/* Physical and numerical parameters (Section 5.1 workloads). */
 typedef struct {
     int32_t eos;         /* 0 = Tait (square patch), 1 = ideal gas (Evrard) */
     int32_t n_target;    /* target neighbour count, e.g. 100 */
@@ -175,7 +175,7 @@ int64_t sph_ctx_bytes(int64_t n_capacity, int64_t nnz_capacity, int32_t max_inst
 /* Free the context and its device memory (synchronises the device). NULL is a no-op. */
 void sph_ctx_destroy(sph_ctx *ctx);
 
-/* Algorithm 1 steps 1-2 (Section 2 and its footnote: h follows a target
+/* Algorithm 1 steps 1-2 (Section 3 and its footnote: h follows a target
  * neighbour count). Reads x, y, z, h (and m, v, u, which it also copies into
  * the context); sorts the particles by the Morton code of their cell; runs
  * the bracketing h search per particle (count of N_i(h) must reach

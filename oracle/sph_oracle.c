@@ -1,6 +1,6 @@
 /*
  * sph_oracle.c -- plain, slow, obviously correct FP64 CPU oracle of one SPH
- * time step (paper Section 2, Algorithm 1: build tree, find neighbours and
+ * time step (paper Section 3, Algorithm 1: build tree, find neighbours and
  * smoothing length, SPH kernels, new time step, update).
  *
  * TEST INFRASTRUCTURE. Only the test-suite, the smoke check and the CPU
@@ -196,7 +196,7 @@ double orc_kernel_dWdr(const orc_params *P, double r, double h)
 }
 
 /* Pair vector r_ij = r_i - r_j; along z the minimum image with period lz when
- * periodic_z is set (Section 4.1.1: the patch is periodic in Z). */
+ * periodic_z is set (Section 5.1.1: the patch is periodic in Z). */
 static inline void orc_pair(const orc_params *P, const double *x, const double *y,
                             const double *z, int64_t i, int64_t j, double *d)
 {
@@ -354,7 +354,7 @@ static void orc_grid_query(const orc_grid *g, double px, double py, double pz, d
 }
 
 /* ---------------------------------------------------------------------------
- * Neighbour counting (Algorithm 1 step 2; footnote of Section 2: the run aims
+ * Neighbour counting (Algorithm 1 step 2; footnote of Section 3: the run aims
  * at a target neighbour count which sets h). Gather set of i at radius 2h:
  *   N_i(h) = { j != i : r_ij^2 < (2h)^2 },  n_i = |N_i|.
  * ------------------------------------------------------------------------- */
@@ -392,7 +392,7 @@ static int64_t orc_count_grid(const orc_grid *g, const orc_params *P, const doub
 }
 
 /* ---------------------------------------------------------------------------
- * Smoothing-length iteration (reading of the Section 2 footnote; the paper
+ * Smoothing-length iteration (reading of the Section 3 footnote; the paper
  * gives no update rule). Bracketing search that uses only correctly rounded
  * + - * and compares, so every conforming implementation reaches the same
  * bits:
@@ -602,7 +602,7 @@ int orc_csr_fill(const orc_params *P, int64_t n, const double *x, const double *
 }
 
 /* ---------------------------------------------------------------------------
- * Density summation (Section 2, Algorithm 1 step 3, the density): standard volume elements,
+ * Density summation (Section 3, Algorithm 1 step 3, the density): standard volume elements,
  *   rho_i = m_i W(0, h_i) + sum_{j in N_i} m_j W(r_ij, h_i),
  * with W the selected kernel.
  * ------------------------------------------------------------------------- */
@@ -713,7 +713,7 @@ void orc_iad_gradient(const orc_params *P, int64_t n, const double *x, const dou
  * Equation of state.
  *  Tait (square patch): p = (c0^2 rho0 / 7) (x^7 - 1), x = rho/rho0, with
  *    x^7 = ((x^2)^2 x^2) x; sound speed c = sqrt(dp/drho) = c0 x^3.
- *  Ideal gas (Evrard, Section 4.1.2, gamma = 5/3): p = (gamma - 1) rho u,
+ *  Ideal gas (Evrard, Section 5.1.2, gamma = 5/3): p = (gamma - 1) rho u,
  *    c = sqrt(gamma (gamma - 1) u).
  * ------------------------------------------------------------------------- */
 void orc_eos(const orc_params *P, int64_t n, const double *rho, const double *u, double *p,
@@ -736,7 +736,7 @@ void orc_eos(const orc_params *P, int64_t n, const double *rho, const double *u,
 }
 
 /* ---------------------------------------------------------------------------
- * Momentum and energy with Monaghan artificial viscosity (Section 2,
+ * Momentum and energy with Monaghan artificial viscosity (Section 3,
  * Algorithm 1 step 3: the accelerations and the rates of change of the
  * internal energy; Table 1: standard volume elements, gradients from kernel
  * derivatives). For j in S_i:

@@ -10,7 +10,7 @@
 // directed-rounding FP32 operations (thresholds()), so every decision equals
 // the FP64 one and the neighbour sets are exact.
 //
-// h search (reading of the Section 2 footnote: h follows a target neighbour
+// h search (reading of the Section 3 footnote: h follows a target neighbour
 // count): bracketing search using only correctly rounded * and +,
 //   n < target - tol: lo = h; h = (hi == inf) ? 1.25 h : (lo + hi) / 2
 //   n > target + tol: hi = h; h = (lo == 0)   ? 0.8 h  : (lo + hi) / 2

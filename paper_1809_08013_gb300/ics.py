@@ -6,13 +6,13 @@ parameters of each workload. It holds none of the SPH arithmetic (kernel,
 density, equation of state, forces, integration); the CUDA path and the CPU
 oracle both receive its arrays unchanged.
 
-Workloads (Section 4.1, Table 5):
+Workloads (Section 5.1, Table 5):
 
-* Rotating square patch (Section 4.1.1): a 3D cube of particles on a cubic
+* Rotating square patch (Section 5.1.1): a 3D cube of particles on a cubic
   lattice filling [-0.5, 0.5]^3, periodic along z, rotating rigidly with
   v_x = omega*y, v_y = -omega*x (the rigid-rotation velocity equation),
   omega = 5. Tait equation of state with rho0 = 1000, c0 = 50, u = 0.
-* Evrard collapse (Section 4.1.2): a sphere of radius R = 1 and mass M = 1
+* Evrard collapse (Section 5.1.2): a sphere of radius R = 1 and mass M = 1
   with rho(r) = M / (2 pi R^2 r) (the Evrard density profile), u0 = 0.05,
   ideal gas gamma = 5/3, v = 0. Self-gravity (Algorithm 1 step 4) is not computed.
 
@@ -90,7 +90,7 @@ def _empty_state(n: int) -> dict:
 
 def patch_pressure(x, y, omega: float, rho: float, side: float = 1.0, terms: int = 64,
                    chunk: int = 1 << 15):
-    """Initial pressure of the rotating square patch (Section 4.1.1): the
+    """Initial pressure of the rotating square patch (Section 5.1.1): the
     solution of the incompressible pressure Poisson equation lap p = 2 rho
     omega^2 on the square of side L with p = 0 on its edges, as the double
     sine series over odd m and n (the printed series is garbled: it writes x

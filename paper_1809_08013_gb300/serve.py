@@ -1,7 +1,7 @@
 """Serving loop on the batch API (continuous batching).
 
-Requests -- a rotating square patch (Section 4.1.1) or an Evrard sphere
-(Section 4.1.2, hydrodynamics only) of some size, to be advanced some number
+Requests -- a rotating square patch (Section 5.1.1) or an Evrard sphere
+(Section 5.1.2, hydrodynamics only) of some size, to be advanced some number
 of steps -- arrive over time. A request is admitted as soon as the batch has
 a free instance slot and its particles fit in the device arena (a fixed
 budget of device memory, allocated once); its state then stays resident on

@@ -1,7 +1,7 @@
 """Parity of the mixed-precision pair kernels (precision = 1: FP32 relative
 coordinates, FP32 kernel, gradient and viscosity terms, double-float sums;
 positions, h, neighbour sets, dt and integration in FP64) with the FP64
-oracle on the Evrard collapse (Section 4.1.2, hydrodynamics only) and the
+oracle on the Evrard collapse (Section 5.1.2, hydrodynamics only) and the
 rotating square patch.
 
 Bar: density and acceleration within 1e-5 (normwise; cancelling sums against

@@ -2,7 +2,7 @@
 seeded inputs: bit-exact h and neighbour sets, FP64 fields within 1e-12
 normwise, per call and per step from identical inputs; plus edge cases.
 
-Workloads (Section 4.1): the rotating square patch at 30^3 (27,000 particles,
+Workloads (Section 5.1): the rotating square patch at 30^3 (27,000 particles,
 one step) and 100^3 (1,000,000, the benchmark size), a ragged 17^3 patch with
 random velocities (viscosity active), a variable-h patch, and an Evrard
 sphere of 20,000 particles.

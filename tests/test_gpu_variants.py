@@ -1,5 +1,5 @@
 """Parity of the Table 1 variants on the GPU (Wendland C2 and sinc kernels, IAD
-gradients) and of the Section 4.1.1 pressure initial conditions with the CPU
+gradients) and of the Section 5.1.1 pressure initial conditions with the CPU
 oracle: FP64 fields within 1e-12 normwise per call and per step from
 identical inputs, bit-exact h; the variants run alone and batched with the
 same bits; invalid combinations are rejected before any launch."""
@@ -235,7 +235,7 @@ def test_batch_rejects_mixed_variants(B):
 
 @pytest.mark.parametrize("var", [(0, 0, 5), (1, 1, 5)])
 def test_pressure_initial_conditions_one_step(B, orc, var):
-    # variable masses from the series pressure (Section 4.1.1)
+    # variable masses from the series pressure (Section 5.1.1)
     s, prm = ics.square_patch(16, seed=220, pressure_ic=True)
     prm.kernel, prm.gradients, prm.sinc_n = var
     o = orc.pipeline(prm, s)

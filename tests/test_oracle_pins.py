@@ -4,7 +4,7 @@ conservation laws, brute-force and library (k-d tree) neighbour sets,
 hand-derived two-particle closed forms, and the statistics of the inputs.
 
 The paper prints no worked example; each test names the passage or reading
-it checks (Section 2 / Algorithm 1, Table 1, Section 4.1).
+it checks (Section 3 / Algorithm 1, Table 1, Section 5.1).
 """
 import math
 import os
@@ -445,7 +445,7 @@ def test_step_conserves_linear_momentum(orc):
 
 
 # --------------------------------------------------------------------------
-# Inputs (Section 4.1): the seeded generators
+# Inputs (Section 5.1): the seeded generators
 # --------------------------------------------------------------------------
 def test_evrard_sampler_statistics():
     stats = pytest.importorskip("scipy.stats")

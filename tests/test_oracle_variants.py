@@ -1,5 +1,5 @@
 """Pins of the oracle's variants of Table 1 (Wendland C2 and sinc kernels, IAD
-gradients) and of the initial-pressure series of Section 4.1.1, against facts
+gradients) and of the initial-pressure series of Section 5.1.1, against facts
 fixed by the mathematics: kernel normalisation by independent quadrature, a
 closed-form normalisation, finite differences, lattice sums by integer
 enumeration, exactness of IAD on linear fields, conservation laws, and a
@@ -245,7 +245,7 @@ def test_iad_uniform_pressure_lattice_interior_is_force_free(orc):
 
 
 # --------------------------------------------------------------------------
-# Initial pressure of the rotating square patch (Section 4.1.1)
+# Initial pressure of the rotating square patch (Section 5.1.1)
 # --------------------------------------------------------------------------
 def test_patch_pressure_vanishes_on_the_edges_and_is_symmetric():
     t = np.linspace(-0.5, 0.5, 23)
