@@ -348,11 +348,16 @@ const char *sph_last_error(const sph_ctx *ctx);
  *  - h, c, mumax (mumax may be NULL = all zero) are device arrays of length n;
  *    *dt is a device scalar written on `stream` (the current device's).
  *  - Its scratch is a static device array inside the library, which every GPU
- *    that loads the library holds until the process exits. The first call on
- *    a device looks up that array's device address (cudaGetSymbolAddress); make
- *    this first call before any stream capture. No call allocates.
+ *    that loads the library holds until the process exits. Each call looks up
+ *    that array's device address in the current context (cudaGetSymbolAddress);
+ *    the first lookup in a context may load the library's device code there,
+ *    so make the first call before any stream capture. No call allocates.
  *  - n > SPH_NOALLOC_MAX_N, n < 0, cfl <= 0 or a NULL required pointer returns
  *    SPH_E_INVAL and launches nothing; n = 0 writes +inf.
+ *  - A CUDA error already pending when the call starts (from the caller's
+ *    earlier work) returns SPH_E_CUDA with nothing launched and is left
+ *    pending for the caller's own check; SPH_E_CUDA otherwise means this
+ *    call's lookup or launch failed.
  *  - All calls on a device share the scratch: calls that may overlap on the
  *    GPU (different streams without ordering) race; serialise them. */
 sph_status sph_dt_noalloc(const sph_params *prm, int64_t n, const double *h, const double *c,

@@ -10,15 +10,12 @@
 // context buffer. The array (SPH_NOALLOC_MAX_N / 256 doubles, 64 KiB) is
 // part of the library image: every GPU that loads the library holds it until
 // the process exits.
-#include <mutex>
-
 #include "sph_internal.cuh"
 
 namespace sph {
 
 constexpr int kNoAllocThreads = 256;
 constexpr int kNoAllocMaxBlocks = (int)(SPH_NOALLOC_MAX_N / kNoAllocThreads);
-constexpr int kNoAllocMaxDevices = 64;
 static_assert((int64_t)kNoAllocMaxBlocks * kNoAllocThreads == SPH_NOALLOC_MAX_N,
               "SPH_NOALLOC_MAX_N must be a multiple of the block size");
 
@@ -66,21 +63,18 @@ k_noalloc_dt_finish(const double* __restrict__ part, int nb, double cfl, double*
     }
 }
 
-// Device address of g_noalloc_dt_part, looked up once per device. In host
-// code the array's name is only a host-side handle, never a device address.
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_ptr[kNoAllocMaxDevices];
-
-static cudaError_t noalloc_scratch(int device, double** out) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_dt_part);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[device] = (double*)p;
-    }
-    *out = g_noalloc_ptr[device];
-    return cudaSuccess;
+// Device address of g_noalloc_dt_part in the current context. In host code
+// the array's name is only a host-side handle, never a device address. The
+// address belongs to a CUDA context, not to a device number, so it is asked
+// for on every call rather than cached: after a device reset, or with another
+// context made current, a cached address could point at freed memory or into
+// another context. The first lookup in a context may load the library's
+// module there, which is why the first call should come before any capture.
+static cudaError_t noalloc_scratch(double** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_dt_part);
+    *out = (double*)p;
+    return e;
 }
 
 }  // namespace sph
@@ -92,21 +86,21 @@ extern "C" sph_status sph_dt_noalloc(const sph_params* prm, int64_t n, const dou
     if (!prm || !dt || n < 0 || !(prm->cfl > 0.0)) return SPH_E_INVAL;
     if (n > SPH_NOALLOC_MAX_N) return SPH_E_INVAL;  // beyond the static scratch
     if (n > 0 && (!h || !c)) return SPH_E_INVAL;
-    int device = -1;
-    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kNoAllocMaxDevices) {
-        cudaGetLastError();
-        return SPH_E_CUDA;
-    }
+    // An error left pending by the caller's earlier work is reported, not
+    // cleared, so the caller's own check still sees it.
+    if (cudaPeekAtLastError() != cudaSuccess) return SPH_E_CUDA;
     double* part = nullptr;
-    if (noalloc_scratch(device, &part) != cudaSuccess) {
-        cudaGetLastError();
+    if (noalloc_scratch(&part) != cudaSuccess) {
+        cudaGetLastError();  // this call's own failure
         return SPH_E_CUDA;
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int nb = (int)((n + kNoAllocThreads - 1) / kNoAllocThreads);
-    if (nb > 0)
+    if (nb > 0) {
         k_noalloc_dt_partial<<<nb, kNoAllocThreads, 0, s>>>(n, prm->alpha, prm->beta, h, c, mumax,
                                                             part);
+        if (cudaGetLastError() != cudaSuccess) return SPH_E_CUDA;
+    }
     k_noalloc_dt_finish<<<1, kNoAllocThreads, 0, s>>>(part, nb, prm->cfl, dt);
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_E_CUDA;
 }

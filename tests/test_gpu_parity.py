@@ -11,10 +11,10 @@ import numpy as np
 import pytest
 
 from paper_1809_08013_gb300 import ics
-from parity_util import TOL_FP64, canon_gpu, canon_oracle, normwise, same_sets, scaled
+from parity_util import (TOL_FP64, canon_gpu, canon_oracle, check, force_err, normwise,
+                         same_sets, state_err)
 
-SCALE = {"ax": "scale_a", "ay": "scale_a", "az": "scale_a", "du": "scale_du",
-         "mumax": "scale_mu"}
+FORCES = ("ax", "ay", "az", "du", "mumax")
 
 pytestmark = pytest.mark.gpu
 
@@ -96,13 +96,7 @@ def test_density_eos_forces_from_identical_inputs(B, orc, name):
     arr["c"].copy_(torch.from_numpy(o["c"]))
     ctx.forces(prm, arr)
     assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
-    for k in ("ax", "ay", "az", "du", "mumax"):
-        ref = o[k]
-        got = host(arr[k])
-        if np.max(np.abs(ref)) == 0.0 and np.max(o[SCALE[k]]) == 0.0:
-            assert np.max(np.abs(got)) == 0.0, k
-        else:
-            assert scaled(got, ref, o[SCALE[k]]) <= TOL_FP64, k
+    check({k: force_err(k, host(arr[k]), o[k], o, prm.periodic_z) for k in FORCES}, TOL_FP64)
     assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
 
 
@@ -114,21 +108,13 @@ def test_one_step_matches_oracle(B, orc, name):
     arr = B.alloc_arrays(s)
     ctx.step(prm, arr, nsteps=1)
     ctx.sync()
-    for k in ("x", "y", "z"):
-        assert normwise(host(arr[k]), st_o[k]) <= TOL_FP64, k
-    # v = v0 + dt a and u = u0 + dt du: measured against dt times the summed-term
-    # scale as well (v_z of the z-periodic patch is dt times a cancelling sum)
-    for k in ("vx", "vy", "vz"):
-        assert scaled(host(arr[k]), st_o[k], ex["dt"] * o["scale_a"]) <= TOL_FP64, k
-    assert scaled(host(arr["u"]), st_o["u"], ex["dt"] * o["scale_du"]) <= TOL_FP64
+    per = prm.periodic_z
+    err = {k: state_err(k, host(arr[k]), st_o[k], o, per, ex["dt"])
+           for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
+    err.update({k: normwise(host(arr[k]), ex[k]) for k in ("rho", "p", "c")})
+    err.update({k: force_err(k, host(arr[k]), ex[k], o, per) for k in FORCES})
+    check(err, TOL_FP64)
     assert np.array_equal(host(arr["h"]).view(np.int64), st_o["h"].view(np.int64))
-    for k in ("rho", "p", "c"):
-        assert normwise(host(arr[k]), ex[k]) <= TOL_FP64, k
-    for k in ("ax", "ay", "az", "du", "mumax"):
-        if np.max(np.abs(ex[k])) == 0.0 and np.max(o[SCALE[k]]) == 0.0:
-            assert np.max(np.abs(host(arr[k]))) == 0.0, k
-        else:
-            assert scaled(host(arr[k]), ex[k], o[SCALE[k]]) <= TOL_FP64, k
     assert abs(host(arr["dt"])[0] - ex["dt"]) <= TOL_FP64 * ex["dt"]
     assert abs(host(arr["time"])[0] - ex["time"]) <= TOL_FP64 * ex["time"]
 
@@ -143,10 +129,9 @@ def test_one_step_with_several_lanes_per_particle(B, orc, tpp):
     arr = B.alloc_arrays(s)
     ctx.step(prm, arr, nsteps=1)
     ctx.sync()
-    for k in ("rho", "p", "c"):
-        assert normwise(host(arr[k]), o[k]) <= TOL_FP64, k
-    for k in ("ax", "ay", "az", "du", "mumax"):
-        assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
+    err = {k: normwise(host(arr[k]), o[k]) for k in ("rho", "p", "c")}
+    err.update({k: force_err(k, host(arr[k]), o[k], o, prm.periodic_z) for k in FORCES})
+    check(err, TOL_FP64)
     assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
 
 
@@ -211,15 +196,12 @@ def test_full_size_one_step_1m(B, orc):
     assert np.array_equal(host(arr["nnb"]), o["nnb"])
     off, idx, ng, order = ctx.neighbors_to_host()
     assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
-    for k in ("rho", "p", "c"):
-        assert normwise(host(arr[k]), o[k]) <= TOL_FP64, k
-    for k in ("ax", "ay", "az", "du", "mumax"):
-        assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
-    for k in ("x", "y", "z"):
-        assert normwise(host(arr[k]), st_o[k]) <= TOL_FP64, k
-    for k in ("vx", "vy", "vz"):
-        assert scaled(host(arr[k]), st_o[k], o["dt"] * o["scale_a"]) <= TOL_FP64, k
-    assert scaled(host(arr["u"]), st_o["u"], o["dt"] * o["scale_du"]) <= TOL_FP64
+    per = prm.periodic_z
+    err = {k: normwise(host(arr[k]), o[k]) for k in ("rho", "p", "c")}
+    err.update({k: force_err(k, host(arr[k]), o[k], o, per) for k in FORCES})
+    err.update({k: state_err(k, host(arr[k]), st_o[k], o, per, o["dt"])
+                for k in ("x", "y", "z", "vx", "vy", "vz", "u")})
+    check(err, TOL_FP64)
     assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
 
 
@@ -325,16 +307,14 @@ def test_slab_overflow_uses_full_build(B, orc):
     for k in ("rho", "p", "c"):
         arr[k].copy_(torch.from_numpy(o[k]))
     ctx.forces(prm, arr)  # the pair kernels read the fallback CSR
-    for k in ("ax", "ay", "az", "du"):
-        assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
+    check({k: force_err(k, host(arr[k]), o[k], o, prm.periodic_z) for k in FORCES}, TOL_FP64)
     # and a whole step through the fallback
     arr2 = B.alloc_arrays(s)
     ctx.step(prm, arr2, nsteps=1)
     assert ctx.sync() == B.SPH_OK
-    for k in ("rho", "p"):
-        assert normwise(host(arr2[k]), o[k]) <= TOL_FP64, k
-    for k in ("ax", "ay", "az"):
-        assert scaled(host(arr2[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
+    err = {k: normwise(host(arr2[k]), o[k]) for k in ("rho", "p")}
+    err.update({k: force_err(k, host(arr2[k]), o[k], o, prm.periodic_z) for k in FORCES})
+    check(err, TOL_FP64)
 
 
 @pytest.mark.parametrize("cell_scale", [0.5, 0.75, 1.5])
@@ -384,8 +364,7 @@ def test_far_from_unit_box(B, orc, name, precision):
         arr[k].copy_(torch.from_numpy(o[k]))
     ctx.forces(prm, arr)
     ctx.sync()
-    for k in ("ax", "ay", "az", "du", "mumax"):
-        assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
+    check({k: force_err(k, host(arr[k]), o[k], o, prm.periodic_z) for k in FORCES}, TOL_FP64)
     assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
 
 
@@ -408,6 +387,5 @@ def test_coincident_particles(B, orc, precision, var):
         arr[k].copy_(torch.from_numpy(o[k]))
     ctx.forces(prm, arr)
     ctx.sync()
-    for k in ("ax", "ay", "az", "du", "mumax"):
-        assert scaled(host(arr[k]), o[k], o[SCALE[k]]) <= TOL_FP64, k
+    check({k: force_err(k, host(arr[k]), o[k], o, prm.periodic_z) for k in FORCES}, TOL_FP64)
     assert np.all(np.isfinite(host(arr["ax"])))

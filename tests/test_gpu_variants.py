@@ -9,14 +9,13 @@ import numpy as np
 import pytest
 
 from paper_1809_08013_gb300 import ics
-from parity_util import TOL_FP64, normwise, scaled
+from parity_util import TOL_FP64, check, force_err, normwise, state_err
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-SCALE = {"ax": "scale_a", "ay": "scale_a", "az": "scale_a", "du": "scale_du",
-         "mumax": "scale_mu"}
+FORCES = ("ax", "ay", "az", "du", "mumax")
 
 # (kernel, gradients, sinc_n) and the precision: 2 runs every variant in the
 # FP64-pipe kernels, 0 in the double-float kernels
@@ -61,13 +60,8 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def _check_forces(arr, o, B):
-    for k in ("ax", "ay", "az", "du", "mumax"):
-        ref, got = o[k], host(arr[k])
-        if np.max(np.abs(ref)) == 0.0 and np.max(o[SCALE[k]]) == 0.0:
-            assert np.max(np.abs(got)) == 0.0, k
-        else:
-            assert scaled(got, ref, o[SCALE[k]]) <= TOL_FP64, k
+def _check_forces(arr, o, prm):
+    check({k: force_err(k, host(arr[k]), o[k], o, prm.periodic_z) for k in FORCES}, TOL_FP64)
 
 
 @pytest.mark.parametrize("name", INPUTS)
@@ -84,7 +78,7 @@ def test_variant_density_forces_from_identical_inputs(B, orc, name, var, prec):
         arr[k].copy_(torch.from_numpy(o[k]))
     ctx.forces(prm, arr)
     assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
-    _check_forces(arr, o, B)
+    _check_forces(arr, o, prm)
     assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
 
 
@@ -97,19 +91,13 @@ def test_variant_one_step_matches_oracle(B, orc, name, var, prec):
     arr = B.alloc_arrays(s)
     ctx.step(prm, arr, nsteps=1)
     assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
-    for k in ("x", "y", "z"):
-        assert normwise(host(arr[k]), st_o[k]) <= TOL_FP64, k
-    for k in ("vx", "vy", "vz"):
-        assert scaled(host(arr[k]), st_o[k], ex["dt"] * o["scale_a"]) <= TOL_FP64, k
-    assert scaled(host(arr["u"]), st_o["u"], ex["dt"] * o["scale_du"]) <= TOL_FP64
+    per = prm.periodic_z
+    err = {k: state_err(k, host(arr[k]), st_o[k], o, per, ex["dt"])
+           for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
+    err.update({k: normwise(host(arr[k]), ex[k]) for k in ("rho", "p", "c")})
+    err.update({k: force_err(k, host(arr[k]), ex[k], o, per) for k in FORCES})
+    check(err, TOL_FP64)
     assert np.array_equal(host(arr["h"]).view(np.int64), st_o["h"].view(np.int64))
-    for k in ("rho", "p", "c"):
-        assert normwise(host(arr[k]), ex[k]) <= TOL_FP64, k
-    for k in ("ax", "ay", "az", "du", "mumax"):
-        if np.max(np.abs(ex[k])) == 0.0 and np.max(o[SCALE[k]]) == 0.0:
-            assert np.max(np.abs(host(arr[k]))) == 0.0, k
-        else:
-            assert scaled(host(arr[k]), ex[k], o[SCALE[k]]) <= TOL_FP64, k
     assert abs(host(arr["dt"])[0] - ex["dt"]) <= TOL_FP64 * ex["dt"]
 
 
@@ -130,15 +118,14 @@ def test_double_float_variants_with_lanes(B, orc, name, lanes, var):
         arr[k].copy_(torch.from_numpy(o[k]))
     ctx.forces(prm, arr)
     assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
-    _check_forces(arr, o, B)
+    _check_forces(arr, o, prm)
     st_o, ex = orc.step(prm, s, nsteps=1)
     arr = B.alloc_arrays(s)
     ctx.step(prm, arr, nsteps=1)
     assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
-    for k in ("rho", "p", "c"):
-        assert normwise(host(arr[k]), ex[k]) <= TOL_FP64, k
-    for k in ("ax", "ay", "az", "du"):
-        assert scaled(host(arr[k]), ex[k], o[SCALE[k]]) <= TOL_FP64, k
+    err = {k: normwise(host(arr[k]), ex[k]) for k in ("rho", "p", "c")}
+    err.update({k: force_err(k, host(arr[k]), ex[k], o, prm.periodic_z) for k in FORCES})
+    check(err, TOL_FP64)
     # and it is not the native FP64 kernel (different rounding, same values)
     prm.precision = 2
     arr2 = B.alloc_arrays(s)
@@ -245,7 +232,6 @@ def test_pressure_initial_conditions_one_step(B, orc, var):
     ctx.step(prm, arr, nsteps=1)
     assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
     assert np.array_equal(host(arr["h"]).view(np.int64), st_o["h"].view(np.int64))
-    for k in ("rho", "p"):
-        assert normwise(host(arr[k]), ex[k]) <= TOL_FP64, k
-    for k in ("ax", "ay", "az"):
-        assert scaled(host(arr[k]), ex[k], o[SCALE[k]]) <= TOL_FP64, k
+    err = {k: normwise(host(arr[k]), ex[k]) for k in ("rho", "p")}
+    err.update({k: force_err(k, host(arr[k]), ex[k], o, prm.periodic_z) for k in FORCES})
+    check(err, TOL_FP64)
