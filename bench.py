@@ -1,26 +1,35 @@
 #!/usr/bin/env python3
 """SPH time-step benchmark (arXiv 1809.08013, Algorithm 1) on one GB300.
 
-Default workload: rotating square patch, 100^3 = 1,000,000 particles, FP64,
-20 leapfrog steps from the initial conditions (neighbour lists rebuilt and h
-iterated to 100 +- 5 every step). One benchmark "step" is one full SPH time
-step through the C ABI (sph_step). Prints one JSON line.
+Default workload: rotating square patch, 100^3 = 1,000,000 particles, FP64
+accuracy (the double-float pair kernels), 20 leapfrog steps from the initial
+conditions (neighbour lists rebuilt and h iterated to 100 +- 5 every step).
+One benchmark "step" is one full SPH time step through the C ABI (sph_step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                  [--workload patch|evrard] [--precision fp64|mixed]
+                  [--workload patch|evrard] [--precision fp64|mixed|fp64-pipe]
 
 --workload evrard --precision mixed is the Evrard collapse (Section 5.1.2,
-hydrodynamics only) of 10^6 particles with the mixed-precision pair kernels.
+hydrodynamics only) of 10^6 particles with the mixed-precision pair kernels;
+--precision fp64-pipe runs the pair sums in native FP64 arithmetic.
 
 N > 1 runs under torchrun as independent replicas (one instance per GPU, no
 collective on the data path; the barrier and max-over-ranks timing only).
 --impl reference times the CPU oracle on the host cores instead.
 
-Besides value / e2e (through sph_step_host on pinned host arrays) / roofline /
-cpu_baseline / clocks, the line carries the steady state (steps 2..K), the
-27k-particle small case, the 256-instance ensemble (one graph, staged by size,
-and one instance at a time), the serving stream, and the Table 1 variants at
-the benchmark size; --no-ensemble, --no-serving, --no-variants skip them.
+Output, three JSON lines on rank 0, the headline last:
+  {"detail": ...}   every record in full (phases, the ensemble with its
+                    autotuner trials, the serving stream, the Table 1 variants);
+  {"summary": ...}  the same records in a few numbers each: steady state, the
+                    27k small case, the Evrard 10^6 mixed-precision run, the 1M
+                    patch with FP64-pipe pair sums, the 256-instance ensemble
+                    (FP64 and mixed), the 2,000-request serving stream (batched
+                    FP64, batched mixed, one at a time FP64, latency split),
+                    the variants;
+  headline          metric, value, e2e (through sph_step_host on pinned host
+                    arrays), roofline of the dominant kernel, cpu_baseline,
+                    clocks, gpu_launches.
+--no-ensemble, --no-serving, --no-variants, --no-extra-workloads skip legs.
 """
 from __future__ import annotations
 
@@ -67,25 +76,24 @@ def variant_flops(kernel, gradients, sinc_n):
         return 83 + 2 * g, FLOPS_PAIR_AV, 27 + g
     return FLOPS_PAIR_BASE - 2 * 5 + 2 * f, FLOPS_PAIR_AV, 0
 
-# DRAM traffic of one force-kernel launch (the default two lanes per particle)
-# from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the 70^3
-# patch, scaled to a launch here by the number of pairs it processes
-# (profiles/kernels_patch343k.md). It is reported only while the kernel's
-# sources hash to the version that was captured.
-FORCES_TRAFFIC = {
-    "fp64": {"sources": ("physics_df.cu", "df.cuh"),
-             "sha1": "f4cb76b21c4a17d05e8ba54dc3c878facac7216a",
-             "bytes": 235.84e6 + 10.04e6, "pairs": 34640886},
-    "mixed": {"sources": ("physics_mixed.cu", "df.cuh"),
-              "sha1": "09687ae25b5c288306d8be871c2280cb4dab677a",
-              "bytes": 216.04e6 + 11.42e6, "pairs": 34640886},
-}
+# Counted work of one pair term by the per-pair figure of the scope table
+# (about 75 operations per pair of S_i with the viscosity branch folded in),
+# reported next to the count above.
+FLOPS_PAIR_TABLE = 75
+
+# ncu evidence for the dominant kernel of each precision, from one capture of
+# that kernel at the benchmark size (profiles/<kernel>_patch1m.md or
+# _evrard1m.md): DRAM bytes read + written per launch, warp instructions per
+# launch, and the share of cycles with an instruction issued. Each entry is
+# used only while the kernel's sources hash to the captured version (sha1 of
+# the files listed, in order); otherwise the bench reports null.
+NCU_EVIDENCE = {}
 
 
-def forces_traffic(kind, pairs):
+def ncu_evidence(kind):
     import hashlib
-    ref = FORCES_TRAFFIC.get(kind)
-    if ref is None or pairs <= 0:
+    ref = NCU_EVIDENCE.get(kind)
+    if ref is None:
         return None
     h = hashlib.sha1()
     src = os.path.join(ROOT, "paper_1809_08013_gb300", "csrc")
@@ -94,7 +102,7 @@ def forces_traffic(kind, pairs):
             h.update(fh.read())
     if h.hexdigest() != ref["sha1"]:
         return None
-    return ref["bytes"] * pairs / ref["pairs"]
+    return ref
 
 
 def parse(argv=None):
@@ -107,7 +115,7 @@ def parse(argv=None):
     ap.add_argument("--seed", type=int, default=None, help="default 2 (patch), 3 (evrard)")
     ap.add_argument("--workload", choices=("patch", "evrard"), default="patch")
     ap.add_argument("--n", type=int, default=1_000_000, help="Evrard particle count")
-    ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64")
+    ap.add_argument("--precision", choices=("fp64", "mixed", "fp64-pipe"), default="fp64")
     ap.add_argument("--cell-scale", type=float, default=0.0,
                     help="neighbour-search cell width / (2 <h>); 0 = library default")
     ap.add_argument("--pair-threads", type=int, default=0,
@@ -123,8 +131,12 @@ def parse(argv=None):
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the Table 1 variants (Wendland, sinc, IAD) at the bench size")
     ap.add_argument("--variant-steps", type=int, default=5)
-    ap.add_argument("--serve-requests", type=int, default=200,
-                    help="requests of the serving stream (the full configuration has 2000)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving stream (the configuration's 2000)")
+    ap.add_argument("--serve-tick-s", type=float, default=0.25,
+                    help="target seconds per serving tick (steps per tick adapt to it)")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="skip the Evrard mixed-precision and FP64-pipe runs")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-quantum", type=int, default=10)
@@ -158,14 +170,20 @@ def whole_job_rate(world, n, steps, ms_max):
     return world * n * steps / (ms_max * 1e-3)
 
 
-PRECISION = {"fp64": 0, "mixed": 1}
-DTYPE = {"fp64": "f64", "mixed": "f32 pair terms + f64 state"}
+PRECISION = {"fp64": 0, "mixed": 1, "fp64-pipe": 2}
+# The arithmetic of the pair sums; state, h, neighbour sets, dt and the
+# integration are FP64 in all three.
+DTYPE = {"fp64": "df64: float-float pair sums on the FP32 pipes (~48-bit significand, FP64 "
+                 "state; held to the 1e-12 FP64 tolerance)",
+         "mixed": "mixed: f32 pair terms, float-float sums, f64 state",
+         "fp64-pipe": "f64"}
 
 
 def workload_name(args, n=None):
-    prec = ("FP64" if args.precision == "fp64" else
-            "mixed precision (FP32 relative-coordinate pair terms, double-float sums, FP64 "
-            "positions, h, neighbour sets and integration)")
+    prec = {"fp64": "FP64 accuracy (double-float pair sums)",
+            "fp64-pipe": "FP64 (native FP64 pair sums)",
+            "mixed": "mixed precision (FP32 relative-coordinate pair terms, double-float sums, "
+                     "FP64 positions, h, neighbour sets and integration)"}[args.precision]
     if args.workload == "evrard":
         n = n or args.n
         return (f"Evrard collapse, hydrodynamics only, {n:,} particles (Section 5.1.2: R=M=1, "
@@ -323,7 +341,7 @@ def ensemble_instances(count, precision, seed=1000):
     return out
 
 
-def run_ensemble(args, B, dev):
+def run_ensemble(args, B, dev, precision):
     """Batched ensemble (one CUDA graph of sph_batch_step over all instances)
     against the single-instance path run one instance after another.
     Latency of an instance = time from submission to its result: in the
@@ -333,14 +351,16 @@ def run_ensemble(args, B, dev):
     import torch
     stream = torch.cuda.Stream(device=dev)  # graphs are captured on a non-default stream
     with torch.cuda.stream(stream):
-        return _run_ensemble(args, B, dev, stream)
+        out = _run_ensemble(args, B, dev, stream, precision)
+    torch.cuda.empty_cache()
+    return out
 
 
-def _run_ensemble(args, B, dev, stream):
+def _run_ensemble(args, B, dev, stream, precision):
     import numpy as np
     import torch
     K = args.ensemble_steps
-    insts = ensemble_instances(args.ensemble_count, args.precision)
+    insts = ensemble_instances(args.ensemble_count, precision)
     counts = [len(s["x"]) for s, _ in insts]
     ntot = sum(counts)
     state = {k: np.concatenate([s[k] for s, _ in insts]) for k in B.STATE_FIELDS}
@@ -410,7 +430,7 @@ def _run_ensemble(args, B, dev, stream):
     return {
         "workload": f"{len(insts)} rotating patches, N log-uniform in [4096, 262144] rounded to "
                     f"cubes (sum {ntot:,}), omega ~ U[2,8], seeds 1000+k, {K} steps each, "
-                    f"{args.precision}",
+                    f"{precision}",
         "instances": len(insts), "particles": ntot, "steps": K,
         "batched": {"ms": t_batch, "updates_per_s": upd / (t_batch * 1e-3),
                     "latency_ms_p50": t_batch, "latency_ms_p99": t_batch,
@@ -601,7 +621,7 @@ def run_variants(args, B, dev, fp64_peak):
                                  "peak_source": "FP64 FMA-chain probe, this run"}})
     del ctx
     torch.cuda.empty_cache()
-    return {"workload": workload_name(args).split(", FP64")[0], "steps": args.variant_steps,
+    return {"workload": workload_name(args).split(", FP64 accuracy")[0], "steps": args.variant_steps,
             "runs": out}
 
 
@@ -632,7 +652,8 @@ def run_serving(args, B, dev):
     out = {"workload": f"{args.serve_requests} requests, Poisson arrivals at {args.serve_rate}/s, "
                        f"patch (omega ~ U[2,8]) or Evrard 50/50, N log-uniform in [8000, 1e6], "
                        f"steps ~ U{{10..100}}, device budget {args.serve_budget_gb} GB, "
-                       f"quantum {args.serve_quantum} steps, admission in arrival order",
+                       f"ticks of about {args.serve_tick_s} s (at most {args.serve_quantum} "
+                       f"steps), admission in arrival order",
            "latency_unit": "s"}
     base = serve.make_stream(args.serve_requests, args.serve_rate, seed=5)
     with torch.cuda.stream(stream):
@@ -661,7 +682,7 @@ def run_serving(args, B, dev):
             reqs = serve.make_stream(args.serve_requests, args.serve_rate, seed=5)
             states = {r.rid: serve.initial_state(r, prec) for r in reqs}
             srv = serve.Server(cap, max_instances=256, quantum=args.serve_quantum,
-                               device=dev.index, stream=stream,
+                               device=dev.index, stream=stream, tick_s=args.serve_tick_s,
                                result_fields=("x", "vx", "h", "u", "rho"),
                                keep_result=lambda r: r.rid < 16)
             summ = serve.serve(srv, reqs, states, clock="real")
@@ -737,26 +758,52 @@ def oracle_small_case(oracle, args):
     return out
 
 
-def run_native(args):
+def forces_roofline(B, ctx, arr, prm, phase_ms, tsteps, fp64_peak, fp32_peak):
+    """Roofline of the force phase, the dominant kernel of a step: counted
+    flops per launch (pairs of S_i x the per-pair count, with the viscosity
+    branch weighted by its measured share) over the phase's CUDA-event time,
+    against the FMA probe of the pipe the arithmetic runs on -- the FP32 pipe
+    for the double-float and mixed kernels, the FP64 pipe for native FP64."""
+    f_av, nnz = av_fraction(B, ctx, arr, prm.periodic_z)
+    flops = nnz * (FLOPS_PAIR_BASE + FLOPS_PAIR_AV * f_av)
+    sec = phase_ms["forces"] * 1e-3 / max(tsteps, 1)
+    achieved = flops / sec / 1e12
+    kind = {0: "df", 1: "mixed", 2: "fp64"}[prm.precision]
+    kernel = {"df": "k_forces_df", "mixed": "k_forces_mx", "fp64": "k_forces"}[kind]
+    peak = (fp64_peak if kind == "fp64" else fp32_peak) / 1e12
+    ev = ncu_evidence(kind)
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak,
+           "traffic": ev["dram_bytes"] * nnz / ev["pairs"] if ev else None,
+           "kernel": kernel + " (+ k_dt_finish)",
+           "peak_source": ("FP64" if kind == "fp64" else "FP32") +
+                          " FMA-chain probe of this GPU in this run (sph_probe_fma_peak), 2 flops "
+                          "per FMA: the pipe the pair arithmetic runs on",
+           "counted_flops_per_pair": f"{FLOPS_PAIR_BASE} + {FLOPS_PAIR_AV} when v.r < 0",
+           "flops_per_launch": flops, "pairs_per_launch": nnz, "av_pair_fraction": f_av,
+           "achieved_at_75_per_pair": nnz * FLOPS_PAIR_TABLE / sec / 1e12,
+           "fp64_probe_tflops": fp64_peak / 1e12, "fp32_probe_tflops": fp32_peak / 1e12,
+           "ms_per_launch": sec * 1e3}
+    if ev:
+        out["issue"] = {"warp_inst_per_pair": ev["warp_inst"] / ev["pairs"],
+                        "lane_inst_per_pair": 32 * ev["warp_inst"] / ev["pairs"],
+                        "issue_active": ev["issue_active"], "source": ev["profile"]}
+    return out
+
+
+def measure_workload(args, B, dev, fp64_peak, fp32_peak, e2e=True, sampler=None):
+    """One workload through sph_step: W untimed warm-up steps, the state reset
+    to the initial conditions, then K timed steps in one call (CUDA events on
+    the launching stream, per-phase events inside the library), step 0 alone
+    (steady state = the rest), the end-to-end rate through sph_step_host on
+    pinned host arrays, and the force phase's roofline."""
     import numpy as np
     import torch
     import torch.distributed as dist
-
-    from paper_1809_08013_gb300 import binding as B
-
     rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
-                                init_method="env://")
-    if not torch.cuda.is_available():
-        raise RuntimeError("the native arm needs a CUDA device")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    B.load()
-
     s, prm = make_workload(args)
     n = len(s["x"])
-    ctx = B.Context(n, device=local)
+    ctx = B.Context(n, device=dev.index)
     arr = B.alloc_arrays(s, device=dev)
     ic = {k: arr[k].clone() for k in B.STATE_FIELDS}
     stream = torch.cuda.current_stream(dev)
@@ -766,28 +813,14 @@ def run_native(args):
             arr[k].copy_(ic[k])
         arr["time"].zero_()
 
-    fp64_peak = B.probe_fma_peak(local, fp64=True, stream=stream)
-    fp32_peak = B.probe_fma_peak(local, fp64=False, stream=stream)
-
-    # warm-up (untimed), then back to the initial conditions
     ctx.step(prm, arr, nsteps=args.warmup, stream=stream)
     st = ctx.sync(stream)
     if st not in (B.SPH_OK, B.SPH_E_HNOCONV):
         raise RuntimeError(f"warm-up status {B.STATUS_NAMES.get(st)}: {ctx.error()}")
     reset()
     torch.cuda.synchronize(dev)
-
-    uuid = None
-    try:
-        u = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
-        if u is not None:
-            us = str(u)
-            uuid = us if us.startswith("GPU-") else "GPU-" + us
-    except Exception:
-        uuid = None
-    sampler = ClockSampler(uuid) if rank == 0 else None
-    time.sleep(1.0 if sampler else 0.0)
-
+    if sampler is not None:
+        time.sleep(1.0)
     ctx.timing_enable(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -808,14 +841,14 @@ def run_native(args):
     phase_ms, phase_launches, tsteps = ctx.timing_read()
     ctx.timing_enable(False)
     status = ctx.sync(stream)
-    if sampler:
-        time.sleep(0.3)
-        sampler.stop()
     if status not in (B.SPH_OK, B.SPH_E_HNOCONV):
         raise RuntimeError(f"timed status {B.STATUS_NAMES.get(status)}: {ctx.error()}")
-
     ms_max = max_over_ranks(ms, world, dev)
-    value = whole_job_rate(world, n, args.steps, ms_max)
+    out = {"n": n, "prm": prm, "state": s, "ms": ms_max, "ms_per_step": ms_max / args.steps,
+           "value": whole_job_rate(world, n, args.steps, ms_max), "launches": launches,
+           "status": B.STATUS_NAMES.get(status), "wall": (w0, w1),
+           "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
+           "launches_per_phase": phase_launches}
 
     # step 0 alone from the initial conditions (the longest h search): the timed
     # run's first step is this same work, so the rest gives the steady state
@@ -829,15 +862,16 @@ def run_native(args):
     torch.cuda.synchronize(dev)
     step0_ms = g0.elapsed_time(g1)
     ctx.sync(stream)
-    steady = None
+    out["steady_state"] = None
     if args.steps > 1 and ms > step0_ms:
         sms = (ms - step0_ms) / (args.steps - 1)
-        steady = {"ms_per_step": sms, "value": world * n / (sms * 1e-3), "step0_ms": step0_ms,
-                  "steps": f"2-{args.steps} of the timed run (total minus a separate step 0)"}
+        out["steady_state"] = {"ms_per_step": sms, "value": world * n / (sms * 1e-3),
+                               "step0_ms": step0_ms,
+                               "steps": f"2-{args.steps} of the timed run (total minus a separate "
+                                        f"step 0)"}
 
-    # end to end through the public API: pinned host state in, one step, state out
-    e2e = None
-    if not args.no_e2e:
+    out["e2e"] = None
+    if e2e:
         # through the C ABI on HOST buffers (sph_step_host): every step copies
         # the state in from pinned host memory, steps, and copies it back
         ic_host = {k: torch.from_numpy(np.ascontiguousarray(s[k])) for k in B.STATE_FIELDS}
@@ -860,35 +894,115 @@ def run_native(args):
         torch.cuda.synchronize(dev)
         ems = max_over_ranks(f0.elapsed_time(f1), world, dev)
         ctx.sync(stream)
-        e2e = {"value": whole_job_rate(world, n, args.steps, ems), "unit": UNIT,
-               "h2d_bytes_per_step": 8 * len(B.STATE_FIELDS) * n + 8,
-               "d2h_bytes_per_step": 8 * len(B.STATE_FIELDS) * n + 16,
-               "api": "sph_step_host (C ABI, pinned host arrays; copies inside the call)"}
+        out["e2e"] = {"value": whole_job_rate(world, n, args.steps, ems), "unit": UNIT,
+                      "h2d_bytes_per_step": 8 * len(B.STATE_FIELDS) * n + 8,
+                      "d2h_bytes_per_step": 8 * len(B.STATE_FIELDS) * n + 16,
+                      "api": "sph_step_host (C ABI, pinned host arrays; copies inside the call)"}
+    out["roofline"] = None
+    if rank == 0:
+        # the last step of the timed configuration again, for its neighbour list
+        reset()
+        ctx.step(prm, arr, nsteps=args.steps, stream=stream)
+        ctx.sync(stream)
+        out["roofline"] = forces_roofline(B, ctx, arr, prm, phase_ms, tsteps, fp64_peak,
+                                          fp32_peak)
+    del ctx, arr, ic
+    torch.cuda.empty_cache()
+    return out
+
+
+def _r(x, nd=4):
+    """Round for the compact summary line (None passes through)."""
+    if x is None:
+        return None
+    return float(f"{x:.{nd}g}")
+
+
+def summary_of(main, extra, small, ensembles, serving, variants):
+    """A few numbers per record, short enough to stay in a log's tail."""
+    sm = {}
+    if main.get("steady_state"):
+        sm["steady_ms_per_step"] = _r(main["steady_state"]["ms_per_step"])
+        sm["step0_ms"] = _r(main["steady_state"]["step0_ms"])
+    sm["phases_ms"] = {k: _r(v, 3) for k, v in main["phases_ms_per_step"].items()}
+    if small:
+        sm["patch27k_ms_per_step"] = _r(small["ms_per_step"])
+    for name, r in extra.items():
+        sm[name] = {"value": _r(r["value"]), "ms_per_step": _r(r["ms_per_step"]),
+                    "e2e": _r(r["e2e"]["value"]) if r.get("e2e") else None,
+                    "roofline_frac": _r(r["roofline"]["frac"], 3) if r.get("roofline") else None,
+                    "forces_ms": _r(r["phases_ms_per_step"]["forces"], 3)}
+    for prec, e in ensembles.items():
+        sm[f"ensemble_{prec}"] = {
+            "batched_ups": _r(e["batched"]["updates_per_s"]),
+            "staged_p50_p99_s": [_r(e["staged"]["latency_ms_p50"] / 1e3, 3),
+                                 _r(e["staged"]["latency_ms_p99"] / 1e3, 3)],
+            "single_ups": _r(e["single_instance_path"]["updates_per_s"]),
+            "single_p50_p99_s": [_r(e["single_instance_path"]["latency_ms_p50"] / 1e3, 3),
+                                 _r(e["single_instance_path"]["latency_ms_p99"] / 1e3, 3)],
+            "bitwise": e["batched_equals_single_bitwise"]}
+    if serving:
+        sv = {"requests": (serving.get("batched_fp64") or {}).get("requests")}
+        for k in ("batched_fp64", "batched_mixed", "single_instance_fp64"):
+            r = serving.get(k)
+            if not r:
+                continue
+            d = {"p50_p99_s": [_r(r["latency_p50"], 3), _r(r["latency_p99"], 3)],
+                 "served_ups": _r(r["served_updates_per_s"])}
+            if "split" in r:
+                d["p99_tickwait_queue_run_s"] = [_r(r["split"][q]["p99"], 3)
+                                                 for q in ("tick_wait", "queueing", "run")]
+            sv[k] = d
+        sv["offered_ups"] = _r(serving["batched_fp64"]["offered_updates_per_s"]) \
+            if "batched_fp64" in serving else None
+        sm["serving"] = sv
+    if variants:
+        sm["variants_ms_frac"] = [[v["kernel"], v["gradients"], v["precision"],
+                                   _r(v["ms_per_step"], 3), _r(v["roofline"]["frac"], 3)]
+                                  for v in variants["runs"]]
+    return sm
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1809_08013_gb300 import binding as B
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                init_method="env://")
+    if not torch.cuda.is_available():
+        raise RuntimeError("the native arm needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.load()
+    stream = torch.cuda.current_stream(dev)
+    fp64_peak = B.probe_fma_peak(local, fp64=True, stream=stream)
+    fp32_peak = B.probe_fma_peak(local, fp64=False, stream=stream)
+
+    uuid = None
+    try:
+        u = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+        if u is not None:
+            us = str(u)
+            uuid = us if us.startswith("GPU-") else "GPU-" + us
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    main = measure_workload(args, B, dev, fp64_peak, fp32_peak, e2e=not args.no_e2e,
+                            sampler=sampler)
+    if sampler:
+        time.sleep(0.3)
+        sampler.stop()
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (forces): counted FP64 flops per launch
-    f_av, nnz = av_fraction(B, ctx, arr, prm.periodic_z)
-    flops_launch = nnz * (FLOPS_PAIR_BASE + FLOPS_PAIR_AV * f_av)
-    forces_s = phase_ms["forces"] * 1e-3 / max(tsteps, 1)
-    achieved = flops_launch / forces_s / 1e12
-    mixed = args.precision == "mixed"
-    peak = (fp32_peak if mixed else fp64_peak) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "traffic": forces_traffic("mixed" if mixed else "fp64", nnz),
-                "kernel": "k_forces_mx (+ k_dt_finish)" if mixed else "k_forces_df (+ k_dt_finish)",
-                "peak_source": ("FP32" if mixed else "FP64") +
-                               " FMA-chain probe on this GPU in this run (sph_probe_fma_peak), "
-                               "2 flops per FMA",
-                "fp64_probe_tflops": fp64_peak / 1e12,
-                "fp32_probe_tflops": fp32_peak / 1e12,
-                "flops_per_launch": flops_launch, "pairs_per_launch": nnz,
-                "av_pair_fraction": f_av}
-
+    s, prm, n = main["state"], main["prm"], main["n"]
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         import oracle
@@ -899,36 +1013,56 @@ def run_native(args):
         cpu = {"value": n / tc, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                "sample": f"one oracle step (plain C FP64, OpenMP) of the same {n:,}-particle "
                          f"{args.workload} from its initial conditions: {tc:.1f} s",
-               "gpu_speedup": value / (n / tc)}
+               "gpu_speedup": main["value"] / (n / tc)}
         if args.workload == "patch":
             cpu["small_case"] = oracle_small_case(oracle, args)
 
+    solo = world == 1 and args.workload == "patch" and args.precision == "fp64"
     small = gpu_small_case(args, B, dev) if args.workload == "patch" and world == 1 else None
+    extra = {}
+    if solo and not args.no_extra_workloads:
+        # configuration 3 (Evrard 10^6, mixed precision) and the benchmark patch
+        # with native FP64 pair sums, each the same K steps from its initial
+        # conditions
+        for name, wl, prec in (("evrard_mixed", "evrard", "mixed"),
+                               ("fp64_pipe", "patch", "fp64-pipe")):
+            a2 = argparse.Namespace(**{**vars(args), "workload": wl, "precision": prec,
+                                       "seed": None})
+            r = measure_workload(a2, B, dev, fp64_peak, fp32_peak, e2e=not args.no_e2e)
+            r["workload"] = workload_name(a2, r["n"])
+            extra[name] = r
+    ensembles = {}
+    if solo and not args.no_ensemble:
+        for prec in ("fp64", "mixed"):
+            ensembles[prec] = run_ensemble(args, B, dev, prec)
+    serving = run_serving(args, B, dev) if solo and not args.no_serving else None
+    variants = run_variants(args, B, dev, fp64_peak) if solo and not args.no_variants else None
 
-    ensemble = None
-    if not args.no_ensemble and args.workload == "patch" and world == 1:
-        ensemble = run_ensemble(args, B, dev)
-    serving = None
-    if not args.no_serving and args.workload == "patch" and world == 1:
-        serving = run_serving(args, B, dev)
-    variants = None
-    if not args.no_variants and args.workload == "patch" and world == 1:
-        variants = run_variants(args, B, dev, fp64_peak)
+    clocks = sampler.summary(*main["wall"]) if sampler else None
 
-    clocks = sampler.summary(w0, w1) if sampler else None
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+    def public(r):
+        return {k: v for k, v in r.items() if k not in ("prm", "state", "wall")}
+
+    detail = {"main": public(main), "extra_workloads": {k: public(v) for k, v in extra.items()},
+              "small_case": small, "ensemble": ensembles, "serving": serving,
+              "variants": variants}
+    print(json.dumps({"detail": detail}), flush=True)
+    print(json.dumps({"summary": summary_of(main, extra, small, ensembles, serving, variants)}),
+          flush=True)
+    rl = dict(main["roofline"])
+    for k in ("fp64_probe_tflops", "fp32_probe_tflops", "achieved_at_75_per_pair",
+              "counted_flops_per_pair", "av_pair_fraction", "pairs_per_launch", "peak_source"):
+        rl.pop(k, None)
+    cpu_short = {k: v for k, v in (cpu or {}).items() if k != "small_case"} or None
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": workload_name(args), "n_particles": n,
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (state ~0.2 GB + neighbour list ~0.4 GB)"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "steady_state": steady, "small_case": small, "ensemble": ensemble, "serving": serving,
-            "variants": variants,
-            "clocks": clocks, "status": B.STATUS_NAMES.get(status),
-            "phases_ms_per_step": {k: v / max(tsteps, 1) for k, v in phase_ms.items()},
-            "launches_per_phase": phase_launches}
+                       "l2": "inputs larger than L2 (state ~0.2 GB + neighbour rows ~0.9 GB)"},
+            "roofline": rl, "cpu_baseline": cpu_short, "e2e": main["e2e"],
+            "gpu_launches": main["launches"], "clocks": clocks, "status": main["status"]}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

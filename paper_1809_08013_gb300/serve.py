@@ -10,7 +10,18 @@ together: each tick runs sph_batch_step over every resident instance for up
 to `quantum` steps, then retires the finished ones (their results are copied
 to the host and their arena range freed) and admits waiting requests, so new
 work joins while older work is still running. Arrivals are served in order
-(a request that does not fit waits, and so do the ones behind it).
+(a request that does not fit waits, and so do the ones behind it). With
+`tick_s` set, a tick takes as many steps as fit in about tick_s seconds at
+the throughput measured so far (at least one, at most `quantum`), so a
+request that arrives during a tick waits about tick_s, whatever the number
+of resident particles.
+
+Latency of a request = done - arrival, split into three parts:
+  tick wait = first admission chance - arrival (the tick running when it
+              arrived had to end first),
+  queueing  = admitted - first admission chance (no free slot or memory, or
+              an earlier request still waiting),
+  run       = done - admitted (resident, sharing the device with the others).
 
 A request's result is the same, bit for bit, as stepping it alone with
 sph_step: instances of a batch never interact, and a run split over several
@@ -41,6 +52,7 @@ class Request:
     steps: int
     seed: int
     omega: float = 5.0
+    chance: float = math.nan   # first admission attempt at or after arrival
     admitted: float = math.nan
     done: float = math.nan
     result: dict | None = None
@@ -123,7 +135,8 @@ class Server:
 
     def __init__(self, capacity: int, max_instances: int = 256, quantum: int = 10,
                  device: int = 0, stream=None, nnz_per_particle: int = 160,
-                 result_fields: tuple = OUT_FIELDS + ("nnb",), keep_result=None):
+                 result_fields: tuple = OUT_FIELDS + ("nnb",), keep_result=None,
+                 tick_s: float | None = None):
         import torch
 
         from . import binding
@@ -134,6 +147,8 @@ class Server:
         self.capacity = int(capacity)
         self.max_instances = int(max_instances)
         self.quantum = int(quantum)
+        self.tick_s = tick_s
+        self.rate = None  # particle-steps per second of the ticks so far
         self.result_fields = tuple(result_fields)
         self.keep_result = keep_result  # None: keep every result on the host
         self.ctx = binding.Context(capacity, nnz_capacity=nnz_per_particle * capacity,
@@ -177,6 +192,10 @@ class Server:
         if not self.active:
             return []
         k = min(self.quantum, min(r.left for r in self.active))
+        resident = sum(r.req.n for r in self.active)
+        if self.tick_s is not None and self.rate is not None:
+            k = max(1, min(k, int(self.tick_s * self.rate / resident)))
+        t0 = time.perf_counter()
         self.ctx.batch_set([r.req.n for r in self.active], [r.params for r in self.active],
                            first=[r.first for r in self.active], stream=self.stream)
         arrays = dict(self.arr)
@@ -199,6 +218,8 @@ class Server:
         st = self.ctx.sync(self.stream)
         if st != self.B.SPH_OK:
             self.status = st
+        r_now = resident * k / max(time.perf_counter() - t0, 1e-9)
+        self.rate = r_now if self.rate is None else 0.5 * (self.rate + r_now)
         self.active = keep
         return [r.req for r in done]
 
@@ -217,6 +238,11 @@ def serve(server: Server, requests: list, states: dict, clock: str = "real") -> 
     finished = []
     while pending or server.active:
         t = now()
+        for r in pending:  # admission chances come between ticks
+            if r.arrival > t:
+                break
+            if math.isnan(r.chance):
+                r.chance = t
         while pending and pending[0].arrival <= t and server.can_admit(pending[0].n):
             r = pending.popleft()
             server.admit(r, *states[r.rid], now=t)
@@ -240,16 +266,26 @@ def serve(server: Server, requests: list, states: dict, clock: str = "real") -> 
     return summarize(finished)
 
 
+def _pct(v) -> dict:
+    return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+
+
 def summarize(reqs: list) -> dict:
     lat = np.array([r.done - r.arrival for r in reqs])
     upd = sum(r.n * r.steps for r in reqs)
     first = min(r.arrival for r in reqs)
     last_arrival = max(r.arrival for r in reqs)
     end = max(r.done for r in reqs)
-    return {"requests": len(reqs), "updates": upd,
-            "latency_p50": float(np.percentile(lat, 50)), "latency_p99": float(np.percentile(lat, 99)),
-            "makespan": end - first, "served_updates_per_s": upd / max(end - first, 1e-12),
-            "offered_updates_per_s": upd / max(last_arrival - first, 1e-12)}
+    out = {"requests": len(reqs), "updates": upd,
+           "latency_p50": float(np.percentile(lat, 50)), "latency_p99": float(np.percentile(lat, 99)),
+           "makespan": end - first, "served_updates_per_s": upd / max(end - first, 1e-12),
+           "offered_updates_per_s": upd / max(last_arrival - first, 1e-12)}
+    if all(not math.isnan(r.chance) and not math.isnan(r.admitted) for r in reqs):
+        out["split"] = {
+            "tick_wait": _pct([r.chance - r.arrival for r in reqs]),
+            "queueing": _pct([r.admitted - r.chance for r in reqs]),
+            "run": _pct([r.done - r.admitted for r in reqs])}
+    return out
 
 
 def fifo_single(requests: list, run_time: dict) -> dict:
@@ -259,6 +295,8 @@ def fifo_single(requests: list, run_time: dict) -> dict:
     end = 0.0
     for r in sorted(requests, key=lambda r: (r.arrival, r.rid)):
         start = max(r.arrival, end)
+        r.chance = r.arrival  # nothing runs in ticks here: no tick wait
+        r.admitted = start
         end = start + run_time[r.rid]
         r.done = end
     return summarize(requests)

@@ -32,3 +32,32 @@ def test_variant_flop_counts():
 
 def test_whole_job_rate():
     assert bench.whole_job_rate(4, 1_000_000, 20, 100.0) == pytest.approx(8e8)
+
+
+def test_summary_line_is_compact():
+    # the summary line must stay short enough to survive in a log's tail next
+    # to the headline: a few numbers per record
+    import json
+    main = {"steady_state": {"ms_per_step": 5.05, "step0_ms": 8.6},
+            "phases_ms_per_step": {k: 1.23456 for k in
+                                   ("cells", "hsearch", "csr", "density", "forces", "update")}}
+    rec = {"value": 2.3e8, "ms_per_step": 4.33, "e2e": {"value": 1.8e8},
+           "roofline": {"frac": 0.0812}, "phases_ms_per_step": {"forces": 0.91}}
+    ens = {"batched": {"updates_per_s": 1.77e8},
+           "staged": {"latency_ms_p50": 1430.0, "latency_ms_p99": 4280.0},
+           "single_instance_path": {"updates_per_s": 7.9e7, "latency_ms_p50": 4710.0,
+                                    "latency_ms_p99": 9410.0},
+           "batched_equals_single_bitwise": True}
+    srv = {"latency_p50": 2.6, "latency_p99": 6.7, "served_updates_per_s": 1.71e8,
+           "offered_updates_per_s": 2.4e8, "requests": 2000,
+           "split": {q: {"p50": 0.1, "p99": 1.2} for q in ("tick_wait", "queueing", "run")}}
+    serving = {"batched_fp64": srv, "batched_mixed": srv, "single_instance_fp64": srv}
+    variants = {"runs": [{"kernel": k, "gradients": g, "precision": p, "ms_per_step": 21.47,
+                          "roofline": {"frac": 0.348}}
+                         for k, g, p in [(0, 0, 2)] * 9]}
+    sm = bench.summary_of(main, {"evrard_mixed": rec, "fp64_pipe": rec}, {"ms_per_step": 0.64},
+                          {"fp64": ens, "mixed": ens}, serving, variants)
+    txt = json.dumps({"summary": sm})
+    assert len(txt) < 1500, len(txt)
+    assert sm["serving"]["requests"] == 2000
+    assert sm["evrard_mixed"]["roofline_frac"] == 0.0812

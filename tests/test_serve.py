@@ -46,6 +46,26 @@ def test_fifo_single_timeline():
     assert s["latency_p50"] == pytest.approx(np.percentile([2.0, 3.0, 3.5, 1.0], 50))
 
 
+def test_latency_split_adds_up():
+    # latency = tick wait + queueing + run for every request
+    reqs = [serve.Request(k, arrival=a, kind="patch", n=8, steps=1, seed=k)
+            for k, a in enumerate([0.0, 0.3, 0.6])]
+    for r, (ch, ad, dn) in zip(reqs, [(0.0, 0.0, 1.0), (1.0, 1.0, 2.5), (1.0, 2.5, 4.0)]):
+        r.chance, r.admitted, r.done = ch, ad, dn
+    s = serve.summarize(reqs)
+    sp = s["split"]
+    assert sp["tick_wait"]["p50"] == pytest.approx(0.4)
+    assert sp["queueing"]["p50"] == pytest.approx(0.0) and sp["queueing"]["p99"] > 1.4
+    assert sp["run"]["p50"] == pytest.approx(1.5)
+    for r in reqs:
+        assert (r.chance - r.arrival) + (r.admitted - r.chance) + (r.done - r.admitted) == \
+            pytest.approx(r.done - r.arrival)
+    # one at a time: no tick wait, the wait is all queueing
+    f = serve.fifo_single(reqs, {0: 2.0, 1: 2.0, 2: 1.0})
+    assert f["split"]["tick_wait"]["p99"] == 0.0
+    assert f["split"]["queueing"]["p50"] == pytest.approx(1.7)
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", [0, 1])
 def test_served_results_equal_alone(precision):
