@@ -47,8 +47,27 @@ typedef enum {
                             affected step are not valid; recreate with more capacity */
     SPH_E_HNOCONV = 5,   /* some particle's h search ended outside n_target +- n_tol;
                             results are still computed with its last h */
-    SPH_E_TIMEOUT = 6    /* reserved for bounded device waits */
+    SPH_E_TIMEOUT = 6,   /* reserved for bounded device waits */
+    SPH_E_RANGE = 7      /* precision 0 or 1: some per-particle quantity of the pair
+                            kernels lies outside the range they hold (see below); the
+                            density and force outputs of the affected step are not
+                            valid at their stated accuracy. Precision 2 never raises it */
 } sph_status;
+
+/* Range of the pair kernels at precision 0 (float pairs) and 1 (FP32).
+ * Those kernels work in units of their own, chosen per instance and per step
+ * as powers of two: length 2^uL at or just above the mean h, mass 2^uM at or
+ * just above the largest m, velocity 2^uV at or just above a velocity scale
+ * (the largest |v| component, or c0 for Tait, or sqrt(gamma (gamma - 1)
+ * max u) for an ideal gas, whichever is larger). Scaling by powers of two is
+ * exact, so the caller's choice of units (SI, cgs, code units) does not
+ * change the results; in those units every quantity a pair term needs is
+ * O(1). The step reports SPH_E_RANGE (through sph_sync) when, in them, some
+ * particle has 1/h outside [2^-16, 2^16] (h more than 2^16 away from the
+ * mean h of its instance), or rho, |p/rho^2| or alpha c above 2^64, or when
+ * the coordinates span more than about 2^120 smoothing lengths: input
+ * outside what float-pair arithmetic can hold at FP64 accuracy. Use
+ * precision 2 for such input. */
 
 /* Physical and numerical parameters (Section 5.1 workloads). */
 typedef struct {
@@ -323,8 +342,8 @@ sph_status sph_timing_read(sph_ctx *ctx, double *ms, int64_t *launches, int64_t 
 int64_t sph_launch_count(const sph_ctx *ctx);
 
 /* Wait for the stream, then return and clear the device status: SPH_OK, or
- * the most severe of SPH_E_CAPACITY and SPH_E_HNOCONV raised since the last
- * sph_sync. */
+ * the most severe of SPH_E_CAPACITY, SPH_E_RANGE and SPH_E_HNOCONV (in that
+ * order) raised since the last sph_sync. */
 sph_status sph_sync(sph_ctx *ctx, void *stream);
 
 /* Number of particles whose h search did not converge since the last

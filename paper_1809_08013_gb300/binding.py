@@ -12,9 +12,10 @@ import re
 
 from . import build as _build
 
-SPH_OK, SPH_E_INVAL, SPH_E_NOMEM, SPH_E_CUDA, SPH_E_CAPACITY, SPH_E_HNOCONV, SPH_E_TIMEOUT = range(7)
+(SPH_OK, SPH_E_INVAL, SPH_E_NOMEM, SPH_E_CUDA, SPH_E_CAPACITY, SPH_E_HNOCONV, SPH_E_TIMEOUT,
+ SPH_E_RANGE) = range(8)
 STATUS_NAMES = {0: "SPH_OK", 1: "SPH_E_INVAL", 2: "SPH_E_NOMEM", 3: "SPH_E_CUDA",
-                4: "SPH_E_CAPACITY", 5: "SPH_E_HNOCONV", 6: "SPH_E_TIMEOUT"}
+                4: "SPH_E_CAPACITY", 5: "SPH_E_HNOCONV", 6: "SPH_E_TIMEOUT", 7: "SPH_E_RANGE"}
 
 PHASES = ("cells", "hsearch", "csr", "density", "forces", "update")
 STATE_FIELDS = ("x", "y", "z", "vx", "vy", "vz", "m", "h", "u")
@@ -352,7 +353,7 @@ class Context:
 
     def sync(self, stream=None) -> int:
         """Wait for the stream; return the device status (SPH_OK, SPH_E_CAPACITY,
-        SPH_E_HNOCONV) without raising."""
+        SPH_E_RANGE, SPH_E_HNOCONV) without raising."""
         return int(self.lib.sph_sync(self.h, _stream(stream)))
 
     def timing_enable(self, on: bool = True):

@@ -115,9 +115,14 @@ __device__ __forceinline__ df from_double_fp64(double d) {
 // hi, which the double-float operations accept. Meant for pair differences:
 // |d| < 2^-60 maps to 0 (an absolute error far below any use here) and |d|
 // is assumed below 2^60 (larger magnitudes saturate).
-__device__ __forceinline__ df from_double(double d) {
+// With sh, the result is d 2^sh (sh moves the exponent; the thresholds then
+// apply to d 2^sh): how a difference in the caller's units enters the pair
+// kernels' units.
+__device__ __forceinline__ df from_double(double d, int sh = 0) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return {0.0f, 0.0f};  // zero (and subnormal differences: below any use)
+    e += sh;
     if (e < 1023 - 60) return {0.0f, 0.0f};
     e = e > 1023 + 60 ? 1023 + 60 : e;
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
@@ -137,22 +142,23 @@ __device__ __forceinline__ df from_double(double d) {
 // wherever ulp(x) >= 2^-k; elsewhere rounded by at most 2^-(k+1), a
 // negligible absolute error), split as X = c2 2^42 + c1 2^21 + c0 with c2
 // signed and c1, c0 in [0, 2^21). The chunks are stored pre-scaled as floats
-// c2 2^(42-k), c1 2^(21-k), c0 2^-k, each exact. For two particles the three
-// chunkwise differences are exact floats too (at most 21 significant bits),
-// and their double-float sum is x_i - x_j to within ~2^-48 of its size: the
-// only rounding of the whole difference.
+// c2 2^(42-f), c1 2^(21-f), c0 2^-f with f = k + uL (the coordinate in the
+// length unit 2^uL of the pair kernels), each exact. For two particles the
+// three chunkwise differences are exact floats too (at most 21 significant
+// bits), and their double-float sum is (x_i - x_j) 2^-uL to within ~2^-48 of
+// its size: the only rounding of the whole difference.
 struct fx3 {
     float c2, c1, c0;
 };
 
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
-// k in [-60, 100] (so every scaled chunk is a normal float)
-__device__ __forceinline__ fx3 to_fx(double x, int k) {
+// k in [-1000, 1000], f in [-60, 100] (so every scaled chunk is a normal float)
+__device__ __forceinline__ fx3 to_fx(double x, int k, int f) {
     const double sc = __longlong_as_double((long long)(1023 + k) << 52);  // 2^k
     const long long X = __double2ll_rn(x * sc);
-    return {(float)(X >> 42) * pow2f(42 - k), (float)((X >> 21) & 0x1fffffLL) * pow2f(21 - k),
-            (float)(X & 0x1fffffLL) * pow2f(-k)};
+    return {(float)(X >> 42) * pow2f(42 - f), (float)((X >> 21) & 0x1fffffLL) * pow2f(21 - f),
+            (float)(X & 0x1fffffLL) * pow2f(-f)};
 }
 
 // The double-float value of the exact chunk differences a2 + a1 + a0
@@ -183,14 +189,48 @@ __device__ __forceinline__ df lane_sum(df v) {
     return v;
 }
 
-// Per-particle pack of the double-float force kernel (48 B per particle):
+// The pair kernels' units (length 2^uL, mass 2^uM, velocity 2^uV) of one
+// instance. A quantity of dimension L^a M^b V^c goes from the caller's units
+// into them by the factor L^a M^b V^c of the exact powers of two below.
+struct PairUnits {
+    double L, M, V;  // 2^-uL, 2^-uM, 2^-uV
+};
+
+__host__ __device__ __forceinline__ PairUnits pair_units(int uL, int uM, int uV) {
+    union { long long i; double d; } l, m, v;
+    l.i = (long long)(1023 - uL) << 52;
+    m.i = (long long)(1023 - uM) << 52;
+    v.i = (long long)(1023 - uV) << 52;
+    return {l.d, m.d, v.d};
+}
+
+// The range every float-pair quantity of a pack must lie in, in the pair
+// kernels' units, for the kernel arithmetic to stay within the normal float
+// range with ample room (no product of pair terms overflows, and the low
+// parts of the terms that carry the sums stay normal): h within 2^16 of the
+// instance's mean h; rho, |p/rho^2| and alpha c below 2^64.
+__device__ __forceinline__ bool pack_in_range(double hinv_u, double rho_u, double A_u, double ac_u) {
+    return hinv_u >= 0x1p-16 && hinv_u <= 0x1p16 && rho_u <= 0x1p64 && fabs(A_u) <= 0x1p64 &&
+           ac_u <= 0x1p64;
+}
+
+// Per-particle pack of the double-float force kernel (48 B per particle), in
+// the pair kernels' units:
 //   dpk[3k] = (1/h, 1/h^4), dpk[3k+1] = (p/rho^2, h/2), dpk[3k+2] = (rho/2, alpha c/2).
+// A particle outside pack_in_range sets `range_bit` in *status.
 __device__ __forceinline__ void write_pack(float4* __restrict__ dpk, int64_t k, double hinv,
-                                           double A, double h, double rho, double alpha, double c) {
-    const double h2 = hinv * hinv;
-    const df a = from_double_fp64(hinv), b = from_double_fp64(h2 * h2);
-    const df cA = from_double_fp64(A), d = from_double_fp64(0.5 * h);
-    const df e = from_double_fp64(0.5 * rho), f = from_double_fp64(0.5 * alpha * c);
+                                           double A, double h, double rho, double alpha, double c,
+                                           const PairUnits& U, unsigned* status,
+                                           unsigned range_bit) {
+    const double hu = hinv / U.L;                           // 1/h:     L^-1
+    const double h2 = hu * hu;
+    const double Au = A * (U.L * U.L * U.L * U.V * U.V / U.M);  // p/rho^2: L^3 V^2 M^-1
+    const double ru = 0.5 * rho * (U.M / (U.L * U.L * U.L));    // rho:     M L^-3
+    const double cu = 0.5 * alpha * c * U.V;                    // c:       V
+    if (!pack_in_range(hu, ru, Au, cu)) atomicOr(status, range_bit);
+    const df a = from_double_fp64(hu), b = from_double_fp64(h2 * h2);
+    const df cA = from_double_fp64(Au), d = from_double_fp64(0.5 * h * U.L);
+    const df e = from_double_fp64(ru), f = from_double_fp64(cu);
     dpk[3 * k + 0] = make_float4(a.hi, a.lo, b.hi, b.lo);
     dpk[3 * k + 1] = make_float4(cA.hi, cA.lo, d.hi, d.lo);
     dpk[3 * k + 2] = make_float4(e.hi, e.lo, f.hi, f.lo);

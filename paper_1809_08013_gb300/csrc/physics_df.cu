@@ -12,7 +12,11 @@
 // the kernel polynomials, the viscosity, the sums -- runs in ~48-bit
 // double-float (df.cuh). Per-particle inputs (1/h, 1/h^4, p/rho^2, h/2, rho/2,
 // alpha c/2, m) are converted once per step into float packs read for every
-// neighbour.
+// neighbour. Everything the pair loops hold is in the instance's pair units
+// (Grid::uL, uM, uV: powers of two near the mean h, the largest mass and a
+// velocity scale), so the float exponent range holds it whatever units the
+// caller uses; the sums are taken back to the caller's units exactly, by
+// powers of two, when they are written out.
 #include <math_constants.h>
 
 #include "df.cuh"
@@ -169,7 +173,7 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const float4* __restrict__ xpk, const double* __restrict__ ue,
              Rows R, double4_32a* __restrict__ therm,
              double2* __restrict__ kern, float4* __restrict__ dpk, double* __restrict__ pint,
-             double* __restrict__ cint) {
+             double* __restrict__ cint, unsigned* status) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
     const int sub = (int)(threadIdx.x % T);
     const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
@@ -182,12 +186,12 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     df acc = {0.0f, 0.0f};
     if (act) {
     pi = posh[i];
+    const Grid& g = B.grid[inst];
     const double hinv = 1.0 / pi.w;
     const int sn = kp.sinc_n;
-    const df Hi = dfl::from_double_fp64(hinv);
-    const Grid& g = B.grid[inst];
+    const df Hi = dfl::from_double_fp64(hinv * p2d(g.uL));  // 1/h in the length unit
     const bool per = kp.periodic_z != 0;
-    const float hlz = g.halflzf, L2 = g.lzc[0], L1 = g.lzc[1], L0 = g.lzc[2];
+    const float hlz = g.hlzc, L2 = g.lzc[0], L1 = g.lzc[1], L0 = g.lzc[2];
     const float4 I0 = xpk[3 * i], I1 = xpk[3 * i + 1], I2 = xpk[3 * i + 2];
     if (sub == 0) acc = df{I0.w, I1.w};  // self term m_i W(0, h_i): shape 1
     for (int e = sub; e < len; e += T) {
@@ -213,9 +217,10 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         acc = dfl::lane_sum<T>(acc);
         if (!act || sub != 0) return;
     }
+    const Grid& g = B.grid[inst];
     const double hinv = 1.0 / pi.w;
     const double sigma = hinv * hinv * hinv * (KER == KER_M4 ? kInvPi : kp.wnorm);
-    const double rho = dfl::to_double(acc) * sigma;
+    const double rho = dfl::to_double(acc) * p2d(g.uM) * sigma;  // masses back from the mass unit
     if (FUSE) {
         double p, c;
         eos_d(kp, rho, ue[i], p, c);
@@ -223,7 +228,8 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         therm[i] = make_double4_32a(0.5 * rho, A, 0.5 * kp.alpha * c, 0.5 * pi.w);
         const double h2 = hinv * hinv;
         kern[i] = make_double2(hinv, h2 * h2);
-        dfl::write_pack(dpk, i, hinv, A, pi.w, rho, kp.alpha, c);
+        dfl::write_pack(dpk, i, hinv, A, pi.w, rho, kp.alpha, c, dfl::pair_units(g.uL, g.uM, g.uV),
+                        status, ST_RANGE);
         pint[i] = p;
         cint[i] = c;
     } else {
@@ -239,15 +245,15 @@ static void density_df_t(sph_ctx* c, cudaStream_t s) {
     if (c->kern_kind == KER_WENDLAND)
         k_density_df<FUSE, T, KER_WENDLAND><<<nb, kThreads, 0, s>>>(
             n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
-            c->pint, c->cint);
+            c->pint, c->cint, c->status);
     else if (c->kern_kind == KER_SINC)
         k_density_df<FUSE, T, KER_SINC><<<nb, kThreads, 0, s>>>(
             n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
-            c->pint, c->cint);
+            c->pint, c->cint, c->status);
     else
         k_density_df<FUSE, T, KER_M4><<<nb, kThreads, 0, s>>>(
             n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
-            c->pint, c->cint);
+            c->pint, c->cint, c->status);
 }
 
 template <bool FUSE>
@@ -297,7 +303,8 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const df rhi = {a2.x, a2.y}, cai = {a2.z, a2.w};
         const Grid& gr = B.grid[inst];
         const bool per = kp.periodic_z != 0;
-        const float hlz = gr.halflzf, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
+        const float hlz = gr.hlzc, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
+        const int vsh = -gr.uV;  // velocity differences into the velocity unit
         const int sn = kp.sinc_n;
         const df c_half_pi = dfl::from_double_fp64(0.5 * (KER == KER_M4 ? kInvPi : kp.dnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
@@ -322,8 +329,8 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const df fb = dw_shape_k<KER>(dfl::mul(r, df{b0.x, b0.y}), sn);
             const df Fb = dfl::mul(dfl::add(dfl::mul(Ki, fa), dfl::mul(df{b0.z, b0.w}, fb)),
                                    dfl::mul(rinv, c_half_pi));
-            const df WX = dfl::from_double(vi.x - vj.x), WY = dfl::from_double(vi.y - vj.y);
-            const df WZ = dfl::from_double(vi.z - vj.z);
+            const df WX = dfl::from_double(vi.x - vj.x, vsh), WY = dfl::from_double(vi.y - vj.y, vsh);
+            const df WZ = dfl::from_double(vi.z - vj.z, vsh);
             const df vr = dfl::add(dfl::add(dfl::mul(WX, X), dfl::mul(WY, Y)), dfl::mul(WZ, Z));
             df Pi = {0.f, 0.f};
             if (vr.hi < 0.0f) {
@@ -361,10 +368,14 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         }
     }
     if (act && sub == 0) {
+        // back to the caller's units: a ~ V^2 / L, du ~ V^3 / L, mu ~ V
+        const Grid& gu = B.grid[slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T)];
+        const double sa = p2d(2 * gu.uV - gu.uL), su = p2d(3 * gu.uV - gu.uL);
         const double Aid = (double)dpk[3 * i + 1].x + (double)dpk[3 * i + 1].y;
-        acc[i] = make_double4_32a(-dfl::to_double(sx), -dfl::to_double(sy), -dfl::to_double(sz),
-                                  fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)));
-        const double mu_max = dfl::to_double(mumx);
+        acc[i] = make_double4_32a(-dfl::to_double(sx) * sa, -dfl::to_double(sy) * sa,
+                                  -dfl::to_double(sz) * sa,
+                                  fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)) * su);
+        const double mu_max = dfl::to_double(mumx) * p2d(gu.uV);
         mumax[i] = mu_max;
         const double ci = cint[i];
         // parameters re-read here rather than kept in registers across the loop
@@ -423,7 +434,8 @@ k_volume_df(int64_t n, Batch B, const double4_32a* __restrict__ velm,
     if (i >= n) return;
     const int inst = slot_inst(B, i);
     if (!slot_real(B, inst, i)) return;
-    const df v = dfl::from_double_fp64(velm[i].w / (2.0 * therm[i].x));
+    // m / rho (a volume, L^3) in the length unit
+    const df v = dfl::from_double_fp64(velm[i].w / (2.0 * therm[i].x) * p2d(-3 * B.grid[inst].uL));
     vdf[i] = make_float2(v.hi, v.lo);
 }
 
@@ -446,14 +458,14 @@ k_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     df t[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) t[k] = df{0.0f, 0.0f};
-    double hinv = 1.0;
+    double hinv = 1.0;  // in the length unit: tau and C then come out in it too
     if (act) {
-        hinv = 1.0 / posh[i].w;
+        const Grid& g = B.grid[inst];
+        hinv = 1.0 / posh[i].w * p2d(g.uL);
         const int sn = B.kp[inst].sinc_n;
         const df Hi = dfl::from_double_fp64(hinv);
-        const Grid& g = B.grid[inst];
         const bool per = B.kp[inst].periodic_z != 0;
-        const float hlz = g.halflzf, L2 = g.lzc[0], L1 = g.lzc[1], L0 = g.lzc[2];
+        const float hlz = g.hlzc, L2 = g.lzc[0], L1 = g.lzc[1], L0 = g.lzc[2];
         const float4 I0 = xpk[3 * i], I1 = xpk[3 * i + 1], I2 = xpk[3 * i + 2];
         for (int e = sub; e < len; e += T) {
             const int j = __ldg(&ent[e]);
@@ -539,7 +551,8 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
                           {c1.z, c1.w}, {c2.x, c2.y}, {c2.z, c2.w}};
         const Grid& gr = B.grid[inst];
         const bool per = kp.periodic_z != 0;
-        const float hlz = gr.halflzf, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
+        const float hlz = gr.hlzc, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
+        const int vsh = -gr.uV;  // velocity differences into the velocity unit
         const int sn = kp.sinc_n;
         const df kg = dfl::from_double_fp64(-0.5 * (KER == KER_M4 ? kInvPi : kp.wnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
@@ -576,8 +589,8 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             Gx = dfl::mul(kg, Gx);
             Gy = dfl::mul(kg, Gy);
             Gz = dfl::mul(kg, Gz);
-            const df WX = dfl::from_double(vi.x - vj.x), WY = dfl::from_double(vi.y - vj.y);
-            const df WZ = dfl::from_double(vi.z - vj.z);
+            const df WX = dfl::from_double(vi.x - vj.x, vsh), WY = dfl::from_double(vi.y - vj.y, vsh);
+            const df WZ = dfl::from_double(vi.z - vj.z, vsh);
             const df vr = dfl::add(dfl::add(dfl::mul(WX, X), dfl::mul(WY, Y)), dfl::mul(WZ, Z));
             df Pi = {0.f, 0.f};
             if (vr.hi < 0.0f) {
@@ -616,10 +629,14 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         }
     }
     if (act && sub == 0) {
+        // back to the caller's units: a ~ V^2 / L, du ~ V^3 / L, mu ~ V
+        const Grid& gu = B.grid[slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T)];
+        const double sa = p2d(2 * gu.uV - gu.uL), su = p2d(3 * gu.uV - gu.uL);
         const double Aid = (double)dpk[3 * i + 1].x + (double)dpk[3 * i + 1].y;
-        acc[i] = make_double4_32a(-dfl::to_double(sx), -dfl::to_double(sy), -dfl::to_double(sz),
-                                  fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)));
-        const double mu_max = dfl::to_double(mumx);
+        acc[i] = make_double4_32a(-dfl::to_double(sx) * sa, -dfl::to_double(sy) * sa,
+                                  -dfl::to_double(sz) * sa,
+                                  fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)) * su);
+        const double mu_max = dfl::to_double(mumx) * p2d(gu.uV);
         mumax[i] = mu_max;
         const double ci = cint[i];
         const KParams& ke = B.kp[slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T)];

@@ -12,6 +12,11 @@
 // a relative error of a few 2^-24. Along the periodic z axis the wrap is
 // applied to the exact high difference (see rel_z).
 //
+// Every quantity of the pack is in the instance's pair units (Grid::uL, uM,
+// uV; powers of two near the mean h, the largest mass and a velocity scale),
+// so FP32 holds it whatever units the caller uses; the sums go back to the
+// caller's units exactly when they are written out.
+//
 // Per-particle pack, five float4 (80 B):
 //   mpk[5k]   = (x_hi, y_hi, z_hi, m)      mpk[5k+1] = (x_lo, y_lo, z_lo, 1/h)
 //   mpk[5k+2] = (vx_hi, vy_hi, vz_hi, 1/h^4)  mpk[5k+3] = (vx_lo, vy_lo, vz_lo, p/rho^2)
@@ -47,11 +52,12 @@ struct ZWrap {
     float half, lzh, lzl;
 };
 
-__device__ __forceinline__ ZWrap make_zwrap(const KParams& kp) {
+__device__ __forceinline__ ZWrap make_zwrap(const KParams& kp, const Grid& g) {
     ZWrap w;
     w.per = kp.periodic_z != 0;
-    w.lzh = __double2float_rn(kp.lz);
-    w.lzl = __double2float_rn(kp.lz - (double)w.lzh);
+    const double lz = kp.lz * p2d(-g.uL);  // in the length unit
+    w.lzh = __double2float_rn(lz);
+    w.lzl = __double2float_rn(lz - (double)w.lzh);
     w.half = 0.5f * w.lzh;
     return w;
 }
@@ -114,14 +120,20 @@ __device__ __forceinline__ void eos_m(const KParams& kp, double rho, double u, d
 
 }  // namespace
 
-// Thermodynamic part of the pack (1/h^4, p/rho^2, h/2, rho/2, alpha c/2).
+// Thermodynamic part of the pack (1/h^4, p/rho^2, h/2, rho/2, alpha c/2), in
+// the pair units; a particle outside dfl::pack_in_range raises ST_RANGE.
 __device__ __forceinline__ void pack_thermo(float4* __restrict__ mpk, int64_t k, double h,
-                                            double rho, double A, double alpha, double c) {
-    const double hinv = 1.0 / h;
-    const double h2 = hinv * hinv;
+                                            double rho, double A, double alpha, double c,
+                                            const dfl::PairUnits& U, unsigned* status) {
+    const double hu = 1.0 / (h * U.L);
+    const double h2 = hu * hu;
+    const double Au = A * (U.L * U.L * U.L * U.V * U.V / U.M);  // L^3 V^2 M^-1
+    const double ru = 0.5 * rho * (U.M / (U.L * U.L * U.L));    // M L^-3
+    const double cu = 0.5 * alpha * c * U.V;
+    if (!dfl::pack_in_range(hu, ru, Au, cu)) atomicOr(status, (unsigned)ST_RANGE);
     mpk[5 * k + 2].w = (float)(h2 * h2);
-    mpk[5 * k + 3].w = (float)A;
-    mpk[5 * k + 4] = make_float4((float)(0.5 * h), (float)(0.5 * rho), (float)(0.5 * alpha * c), 0.0f);
+    mpk[5 * k + 3].w = (float)Au;
+    mpk[5 * k + 4] = make_float4((float)(0.5 * h * U.L), (float)ru, (float)cu, 0.0f);
 }
 
 // Position / velocity / mass / 1/h part of the pack from the sorted state;
@@ -129,28 +141,30 @@ __device__ __forceinline__ void pack_thermo(float4* __restrict__ mpk, int64_t k,
 // alpha c/2, h/2) (a standalone force call, where density ran elsewhere).
 template <bool THERMO>
 __global__ void __launch_bounds__(kThreads)
-k_pack_mx(int64_t n, const double4_32a* __restrict__ posh, const double4_32a* __restrict__ velm,
-          const double4_32a* __restrict__ therm, float4* __restrict__ mpk) {
+k_pack_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
+          const double4_32a* __restrict__ velm, const double4_32a* __restrict__ therm,
+          float4* __restrict__ mpk, unsigned* status) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    const Grid& g = B.grid[slot_inst(B, k)];
+    const dfl::PairUnits U = dfl::pair_units(g.uL, g.uM, g.uV);
     const double4_32a p = posh[k];
     const double4_32a v = velm[k];
     float xh, xl, yh, yl, zh, zl, ah, al, bh, bl, ch, cl;
-    split2(p.x, xh, xl);
-    split2(p.y, yh, yl);
-    split2(p.z, zh, zl);
-    split2(v.x, ah, al);
-    split2(v.y, bh, bl);
-    split2(v.z, ch, cl);
-    const double hinv = 1.0 / p.w;
-    mpk[5 * k + 0] = make_float4(xh, yh, zh, (float)v.w);
+    split2(p.x * U.L, xh, xl);
+    split2(p.y * U.L, yh, yl);
+    split2(p.z * U.L, zh, zl);
+    split2(v.x * U.V, ah, al);
+    split2(v.y * U.V, bh, bl);
+    split2(v.z * U.V, ch, cl);
+    const double hinv = 1.0 / (p.w * U.L);
+    mpk[5 * k + 0] = make_float4(xh, yh, zh, (float)(v.w * U.M));
     mpk[5 * k + 1] = make_float4(xl, yl, zl, (float)hinv);
     if (THERMO) {
         const double4_32a t = therm[k];
-        const double h2 = hinv * hinv;
-        mpk[5 * k + 2] = make_float4(ah, bh, ch, (float)(h2 * h2));
-        mpk[5 * k + 3] = make_float4(al, bl, cl, (float)t.y);
-        mpk[5 * k + 4] = make_float4((float)t.w, (float)t.x, (float)t.z, 0.0f);
+        mpk[5 * k + 2] = make_float4(ah, bh, ch, 0.0f);
+        mpk[5 * k + 3] = make_float4(al, bl, cl, 0.0f);
+        pack_thermo(mpk, k, p.w, 2.0 * t.x, t.y, 1.0, 2.0 * t.z, U, status);
     } else {
         mpk[5 * k + 2] = make_float4(ah, bh, ch, 0.0f);
         mpk[5 * k + 3] = make_float4(al, bl, cl, 0.0f);
@@ -163,7 +177,7 @@ __global__ void __launch_bounds__(kThreads)
 k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const double* __restrict__ ue, float4* __restrict__ mpk,
              Rows R, double4_32a* __restrict__ therm,
-             double* __restrict__ pint, double* __restrict__ cint) {
+             double* __restrict__ pint, double* __restrict__ cint, unsigned* status) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
     const int sub = (int)(threadIdx.x % T);
     const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
@@ -176,7 +190,7 @@ k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     if (act) {
     const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1];
     const float hinv = a1.w;
-    const ZWrap zw = make_zwrap(kp);
+    const ZWrap zw = make_zwrap(kp, B.grid[inst]);
     if (sub == 0) acc = df{a0.w, 0.0f};  // self term m_i W(0, h_i): shape 1
     for (int e = sub; e < len; e += T) {
         const int j = __ldg(&ent[e]);
@@ -192,15 +206,16 @@ k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         acc = dfl::lane_sum<T>(acc);
         if (!act || sub != 0) return;
     }
+    const Grid& g = B.grid[inst];
     const double hd = posh[i].w;
     const double hid = 1.0 / hd;
-    const double rho = dfl::to_double(acc) * (hid * hid * hid * 0.31830988618379067154);
+    const double rho = dfl::to_double(acc) * p2d(g.uM) * (hid * hid * hid * 0.31830988618379067154);
     if (FUSE) {
         double p, c;
         eos_m(kp, rho, ue[i], p, c);
         const double A = p / (rho * rho);
         therm[i] = make_double4_32a(0.5 * rho, A, 0.5 * kp.alpha * c, 0.5 * hd);
-        pack_thermo(mpk, i, hd, rho, A, kp.alpha, c);
+        pack_thermo(mpk, i, hd, rho, A, kp.alpha, c, dfl::pair_units(g.uL, g.uM, g.uV), status);
         pint[i] = p;
         cint[i] = c;
     } else {
@@ -228,7 +243,7 @@ k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const KParams& kp = B.kp[inst];
         const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1], a2 = mpk[5 * i + 2];
         const float4 a3 = mpk[5 * i + 3], a4 = mpk[5 * i + 4];
-        const ZWrap zw = make_zwrap(kp);
+        const ZWrap zw = make_zwrap(kp, B.grid[inst]);
         const float eta2 = (float)kp.eta2, beta = (float)kp.beta;
         const float cpi = 0.5f * kInvPiF;
         for (int e = sub; e < len; e += T) {
@@ -277,14 +292,20 @@ k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         for (int o = 1; o < T; o <<= 1) mum = fmaxf(mum, __shfl_xor_sync(0xffffffffu, mum, o));
     }
     if (act && sub == 0) {
+        // back to the caller's units: a ~ V^2 / L, du ~ V^3 / L, mu ~ V
+        const int ins = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
+        const Grid& gu = B.grid[ins];
+        const double sa = p2d(2 * gu.uV - gu.uL), su = p2d(3 * gu.uV - gu.uL);
         const double Aid = (double)mpk[5 * i + 3].w;
-        acc[i] = make_double4_32a(-dfl::to_double(sx), -dfl::to_double(sy), -dfl::to_double(sz),
-                                  fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)));
-        mumax[i] = (double)mum;
+        acc[i] = make_double4_32a(-dfl::to_double(sx) * sa, -dfl::to_double(sy) * sa,
+                                  -dfl::to_double(sz) * sa,
+                                  fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)) * su);
+        const double mu_max = (double)mum * p2d(gu.uV);
+        mumax[i] = mu_max;
         const double ci = cint[i];
         // parameters re-read here rather than kept in registers across the loop
-        const KParams& ke = B.kp[slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T)];
-        dtc = posh[i].w / (ci + 1.2 * (ke.alpha * ci + ke.beta * (double)mum));
+        const KParams& ke = B.kp[ins];
+        dtc = posh[i].w / (ci + 1.2 * (ke.alpha * ci + ke.beta * mu_max));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
@@ -305,9 +326,11 @@ void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s) {
     const int b = c->cur;
     c->launches += 1;
     if (thermo)
-        k_pack_mx<true><<<nb, kThreads, 0, s>>>(n, c->posh[b], c->velm[b], c->therm, c->mpk);
+        k_pack_mx<true><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->velm[b], c->therm,
+                                                c->mpk, c->status);
     else
-        k_pack_mx<false><<<nb, kThreads, 0, s>>>(n, c->posh[b], c->velm[b], c->therm, c->mpk);
+        k_pack_mx<false><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->velm[b], c->therm,
+                                                 c->mpk, c->status);
 }
 
 template <bool FUSE, int T>
@@ -317,7 +340,7 @@ static void density_mx_t(sph_ctx* c, cudaStream_t s) {
     const int b = c->cur;
     k_density_mx<FUSE, T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->ue[b], c->mpk,
                                                   rows_of(c),
-                                                  c->therm, c->pint, c->cint);
+                                                  c->therm, c->pint, c->cint, c->status);
 }
 
 template <bool FUSE>

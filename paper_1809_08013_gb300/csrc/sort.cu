@@ -59,12 +59,16 @@ void launch_load_state(sph_ctx* c, const sph_particles* P, cudaStream_t s) {
 }
 
 // Pack of the double-float pair kernels for particle k: the fixed-point chunks
-// of its position (dfl::to_fx, exponent of its instance) and its mass,
+// of its position (dfl::to_fx, exponents of its instance) and its mass, both
+// in the pair kernels' units of the instance,
 //   xpk[3k] = (x.c2, y.c2, z.c2, m.hi), xpk[3k+1] = (x.c1, y.c1, z.c1, m.lo),
 //   xpk[3k+2] = (x.c0, y.c0, z.c0, 0).
 __device__ __forceinline__ void write_xpk(float4* __restrict__ xpk, int64_t k, const double4_32a& p,
-                                          const dfl::df& m, int fxk) {
-    const dfl::fx3 X = dfl::to_fx(p.x, fxk), Y = dfl::to_fx(p.y, fxk), Z = dfl::to_fx(p.z, fxk);
+                                          double mass, const Grid& g) {
+    const int f = g.fxk + g.uL;
+    const dfl::fx3 X = dfl::to_fx(p.x, g.fxk, f), Y = dfl::to_fx(p.y, g.fxk, f);
+    const dfl::fx3 Z = dfl::to_fx(p.z, g.fxk, f);
+    const dfl::df m = dfl::from_double_fp64(mass * p2d(-g.uM));
     xpk[3 * k + 0] = make_float4(X.c2, Y.c2, Z.c2, m.hi);
     xpk[3 * k + 1] = make_float4(X.c1, Y.c1, Z.c1, m.lo);
     xpk[3 * k + 2] = make_float4(X.c0, Y.c0, Z.c0, 0.0f);
@@ -82,7 +86,7 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
                const double* __restrict__ cs, double4_32a* __restrict__ posh,
                double4_32a* __restrict__ velm, double4_32a* __restrict__ therm,
                double2* __restrict__ kern, double* __restrict__ cint, float4* __restrict__ dpk,
-               float4* __restrict__ xpk, const Grid* __restrict__ grid) {
+               float4* __restrict__ xpk, const Grid* __restrict__ grid, unsigned* status) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t o = order[k];
@@ -91,7 +95,8 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
     const double4_32a ps = make_double4_32a(x[o], y[o], z[o], hh);
     posh[k] = ps;
     const double mm = m[o];
-    write_xpk(xpk, k, ps, dfl::from_double_fp64(mm), grid[0].fxk);  // a single problem: instance 0
+    const Grid& g = grid[0];  // a single problem: instance 0
+    write_xpk(xpk, k, ps, mm, g);
     if (what == GATHER_DENSITY) {
         velm[k] = make_double4_32a(0.0, 0.0, 0.0, mm);
     } else {
@@ -102,7 +107,8 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
         const double A = p[o] / (r * r);
         therm[k] = make_double4_32a(0.5 * r, A, 0.5 * alpha * c, 0.5 * hh);
         kern[k] = make_double2(hinv, h2 * h2);
-        dfl::write_pack(dpk, k, hinv, A, hh, r, alpha, c);
+        dfl::write_pack(dpk, k, hinv, A, hh, r, alpha, c, dfl::pair_units(g.uL, g.uM, g.uV),
+                        status, ST_RANGE);
         cint[k] = c;
     }
 }
@@ -116,7 +122,7 @@ void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, 
     k_gather_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         n, what, kp.alpha, c->order[b], P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m,
         P->rho, P->p, P->c, c->posh[b], c->velm[b], c->therm, c->kern, c->cint, c->dpk, c->xpk,
-        c->grid);
+        c->grid, c->status);
 }
 
 // ------------------------------------------------------------ bbox and grid
@@ -132,17 +138,20 @@ __device__ __forceinline__ double okey_inv(long long k) {
 
 constexpr long long kKeyMax = 0x7fffffffffffffffLL, kKeyMin = -kKeyMax - 1;
 
-// Bounding-box partials: min x, y, z and max x, y, z, h (as keys) and the
-// sum of h over the particles of each group of kSlotAlign slots (one
-// instance), one warp per group, reduced in a fixed order.
+// Bounding-box partials: min x, y, z and max x, y, z, h, m, |v| (largest
+// component), u (as keys) and the sum of h over the particles of each group
+// of kSlotAlign slots (one instance), one warp per group, reduced in a fixed
+// order. Stored as kBoxStride doubles per group: mn[3], mx[7], hs.
+constexpr int kBoxMax = 7;
+
 struct BoxPart {
-    long long mn[3], mx[4];
+    long long mn[3], mx[kBoxMax];
     double hs;
 };
 
 __device__ __forceinline__ void box_init(BoxPart& b) {
     for (int d = 0; d < 3; ++d) b.mn[d] = kKeyMax;
-    for (int d = 0; d < 4; ++d) b.mx[d] = kKeyMin;
+    for (int d = 0; d < kBoxMax; ++d) b.mx[d] = kKeyMin;
     b.hs = 0.0;
 }
 
@@ -155,7 +164,7 @@ __device__ __forceinline__ void box_warp_reduce(BoxPart& b) {
             b.mn[d] = v < b.mn[d] ? v : b.mn[d];
         }
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
+        for (int d = 0; d < kBoxMax; ++d) {
             const long long v = __shfl_xor_sync(0xffffffffu, b.mx[d], o);
             b.mx[d] = v > b.mx[d] ? v : b.mx[d];
         }
@@ -164,7 +173,9 @@ __device__ __forceinline__ void box_warp_reduce(BoxPart& b) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh, double* __restrict__ part) {
+k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
+       const double4_32a* __restrict__ velm, const double* __restrict__ ue,
+       double* __restrict__ part) {
     const int lane = threadIdx.x & 31;
     const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (grp * kSlotAlign >= n) return;  // warp-uniform
@@ -186,14 +197,20 @@ k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh, double* __restr
             b.mx[2] = kz > b.mx[2] ? kz : b.mx[2];
             b.mx[3] = kh > b.mx[3] ? kh : b.mx[3];
             b.hs += p.w;
+            const double4_32a v = velm[k];
+            const long long km = okey(v.w), ku = okey(ue[k]);
+            const long long kv = okey(fmax(fabs(v.x), fmax(fabs(v.y), fabs(v.z))));
+            b.mx[4] = km > b.mx[4] ? km : b.mx[4];
+            b.mx[5] = kv > b.mx[5] ? kv : b.mx[5];
+            b.mx[6] = ku > b.mx[6] ? ku : b.mx[6];
         }
     }
     box_warp_reduce(b);
     if (lane == 0) {
-        double* o = part + grp * 8;
+        double* o = part + grp * kBoxStride;
         for (int d = 0; d < 3; ++d) o[d] = __longlong_as_double(b.mn[d]);
-        for (int d = 0; d < 4; ++d) o[3 + d] = __longlong_as_double(b.mx[d]);
-        o[7] = b.hs;
+        for (int d = 0; d < kBoxMax; ++d) o[3 + d] = __longlong_as_double(b.mx[d]);
+        o[3 + kBoxMax] = b.hs;
     }
 }
 
@@ -224,20 +241,20 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     BoxPart v;
     box_init(v);
     for (int64_t b = threadIdx.x; b < nbk; b += blockDim.x) {
-        const double* o = part + (b0 + b) * 8;
+        const double* o = part + (b0 + b) * kBoxStride;
         for (int d = 0; d < 3; ++d) {
             const long long k = __double_as_longlong(o[d]);
             v.mn[d] = k < v.mn[d] ? k : v.mn[d];
         }
-        for (int d = 0; d < 4; ++d) {
+        for (int d = 0; d < kBoxMax; ++d) {
             const long long k = __double_as_longlong(o[3 + d]);
             v.mx[d] = k > v.mx[d] ? k : v.mx[d];
         }
-        v.hs += o[7];
+        v.hs += o[3 + kBoxMax];
     }
     box_warp_reduce(v);
     __shared__ BoxPart sh[kGridThreads / 32];
-    __shared__ double r[8];
+    __shared__ double r[11];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) sh[warp] = v;
     __syncthreads();
@@ -245,7 +262,7 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
         BoxPart a = sh[0];
         for (int w = 1; w < kGridThreads / 32; ++w) {
             for (int d = 0; d < 3; ++d) a.mn[d] = sh[w].mn[d] < a.mn[d] ? sh[w].mn[d] : a.mn[d];
-            for (int d = 0; d < 4; ++d) a.mx[d] = sh[w].mx[d] > a.mx[d] ? sh[w].mx[d] : a.mx[d];
+            for (int d = 0; d < kBoxMax; ++d) a.mx[d] = sh[w].mx[d] > a.mx[d] ? sh[w].mx[d] : a.mx[d];
             a.hs += sh[w].hs;
         }
         // the layout the grid derivation below reads: min x, y, z, -max x, y, z, -max h, sum h
@@ -255,6 +272,9 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
         }
         r[6] = -okey_inv(a.mx[3]);
         r[7] = a.hs;
+        r[8] = okey_inv(a.mx[4]);   // max m
+        r[9] = okey_inv(a.mx[5]);   // max |v| component
+        r[10] = okey_inv(a.mx[6]);  // max u
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -317,16 +337,38 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     const double u24 = 5.9604644775390625e-08;
     g->eC = __double2float_ru(u24 * (4.0 * X + (per ? 2.0 * kp.lz : 0.0)) * 1.0001 + 1e-37);
     g->eR = __double2float_ru(u24 * 2.02 * 1.0001);
-    // fixed-point exponent of the coordinate chunks (dfl::to_fx): |x| 2^k < 2^61
+    // Units of the pair kernels (Grid::uL, uM, uV): the power of two at or
+    // just above the mean h, the largest mass and a velocity scale (the
+    // largest |v| component, or the sound speed the parameters imply if that
+    // is larger: c0 for Tait, sqrt(gamma (gamma - 1) max u) for an ideal gas).
+    auto unit_exp = [](double v) {
+        int e = 0;
+        if (!(v > 0.0) || !isfinite(v)) return 0;
+        frexp(v, &e);  // v < 2^e
+        return e < -300 ? -300 : (e > 300 ? 300 : e);
+    };
+    double vs = n > 0 ? r[9] : 0.0;
+    if (kp.eos == 0) vs = fmax(vs, fabs(kp.c0));
+    else if (n > 0 && r[10] > 0.0) vs = fmax(vs, sqrt(kp.gamma * (kp.gamma - 1.0) * r[10]));
+    g->uL = unit_exp(hmean);
+    g->uM = unit_exp(n > 0 ? r[8] : 0.0);
+    g->uV = unit_exp(vs);
+    // fixed-point exponent of the coordinate chunks (dfl::to_fx): |x| 2^k < 2^61,
+    // and the chunks' float exponent k + uL must keep them normal floats
     int ex = 0;
     frexp(X, &ex);  // X < 2^ex
     int k = X > 0.0 && isfinite(X) ? 61 - ex : 61;
-    k = k < -60 ? -60 : (k > 100 ? 100 : k);
+    k = k < -1000 ? -1000 : (k > 1000 ? 1000 : k);
+    if (k + g->uL > 100 || k + g->uL < -60) {  // coordinates out of all proportion to h
+        k = k + g->uL > 100 ? 100 - g->uL : -60 - g->uL;
+        atomicOr(&status[0], (unsigned)ST_RANGE);
+    }
     g->fxk = k;
-    const dfl::fx3 L = dfl::to_fx(per ? kp.lz : 0.0, k);
+    const dfl::fx3 L = dfl::to_fx(per ? kp.lz : 0.0, k, k + g->uL);
     g->lzc[0] = L.c2;
     g->lzc[1] = L.c1;
     g->lzc[2] = L.c0;
+    g->hlzc = (float)(0.5 * kp.lz * p2d(-g->uL));
     g->hmean = hmean;
     g->hmax_bits = 0ull;
     g->ncells = (long long)cnt[0] * cnt[1] * cnt[2];
@@ -473,7 +515,7 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
     posh_out[k] = p;
     const double4_32a v = velm_in[o];
     velm_out[k] = v;
-    write_xpk(xpk, k, p, dfl::from_double_fp64(v.w), B.grid[inst].fxk);
+    write_xpk(xpk, k, p, v.w, B.grid[inst]);
     u_out[k] = u_in[o];
     order_out[k] = order_in[o];
     fpos[k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
@@ -521,7 +563,7 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
         c->launches += 1;
         const int64_t groups = (n + kSlotAlign - 1) / kSlotAlign;
         k_bbox<<<(unsigned)((groups * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            n, B, c->posh[c->cur], c->red_part);
+            n, B, c->posh[c->cur], c->velm[c->cur], c->ue[c->cur], c->red_part);
     }
     k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status, c->wctr);
     if (n == 0) return;

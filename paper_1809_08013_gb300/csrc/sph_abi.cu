@@ -191,7 +191,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->cells, (size_t)c->cellcap) && al(&c->cell_hmax, (size_t)c->cellcap) &&
          al(&c->nnb, N) && al(&c->ngather, N) && al(&c->rowlen, N) &&
          al(&c->offsets, N + 1) && al(&c->row_part, (size_t)scan_parts(N) + 1) &&
-         al(&c->idx, (size_t)nnzcap) && al(&c->red_part, nfb * 8) &&
+         al(&c->idx, (size_t)nnzcap) && al(&c->red_part, nfb * kBoxStride) &&
          al(&c->dt_part, nfb * kMaxPairThreads) && al(&c->grid, (size_t)max_instances) &&
          al(&c->status, 4) && al(&c->blk, nfb) &&
          al(&c->ioff, (size_t)max_instances + 1) && al(&c->icnt, (size_t)max_instances) &&
@@ -842,6 +842,11 @@ sph_status sph_sync(sph_ctx* c, void* stream) {
     if (bits & ST_CAPACITY) {
         set_err(c, "neighbour list exceeded nnz capacity %lld", (long long)c->nnzcap);
         return SPH_E_CAPACITY;
+    }
+    if (bits & ST_RANGE) {
+        set_err(c, "a per-particle quantity of the float-pair pair kernels left their range "
+                   "(use precision 2 for this input)");
+        return SPH_E_RANGE;
     }
     if (bits & ST_HNOCONV) {
         set_err(c, "%lld particle(s) did not reach the target neighbour count",

@@ -29,11 +29,13 @@ constexpr int kRadixTile = kThreads * kRadixItems;  // 2048 keys per block
 constexpr int kScanTile = kThreads * 8;             // elements per block in scans
 constexpr int kReduceBlocks = 304;                  // 2 x 152 SMs
 constexpr int kMaxPairThreads = 8;                  // lanes per particle in the pair kernels
+constexpr int kBoxStride = 12;                      // doubles per bounding-box partial
 
 // device status word
 enum : unsigned {
     ST_CAPACITY = 1u,   // neighbour list exceeded nnz capacity
     ST_HNOCONV = 2u,    // some h search did not converge
+    ST_RANGE = 4u,      // a float-pair quantity left the range of the pair kernels
 };
 // internal flags (status[2], cleared at every build)
 enum : unsigned {
@@ -64,8 +66,25 @@ struct Grid {
     float slop[3];   // absolute slack added to query boxes (FP32 rounding cover)
     float eC, eR;    // FP32-error bound of a coordinate difference: e(R) <= eC + eR * R
     int fxk;         // fixed-point exponent of the coordinate chunks: |x| 2^fxk < 2^61
-    float lzc[3];    // lz 2^fxk as chunks (scaled like the coordinates' chunks)
+    float lzc[3];    // lz as chunks, in the pair kernels' length unit
+    float hlzc;      // lz / 2 in that unit (the wrap test on chunk differences)
+    // Units of the float-pair (precision 0) and FP32 (precision 1) pair
+    // kernels: length 2^uL, mass 2^uM, velocity 2^uV, powers of two taken
+    // from the instance's mean h, largest m and a velocity scale, so that the
+    // quantities those kernels hold are O(1) whatever units the caller uses.
+    // Multiplying by a power of two is exact, and every operation of the pair
+    // sums commutes with it while its operands stay in the normal float
+    // range, so in units where everything is already O(1) the results are
+    // the same bits as without the rescaling.
+    int uL, uM, uV;
 };
+
+// 2^e as a double, exactly (e in [-1022, 1023]); integer operations only.
+__host__ __device__ __forceinline__ double p2d(int e) {
+    union { long long i; double d; } u;
+    u.i = (long long)(1023 + e) << 52;
+    return u.d;
+}
 
 // Parameters copied by value into kernels.
 // kernel / gradients select the Table 1 variants; wnorm and dnorm are the
@@ -199,7 +218,7 @@ struct sph_ctx {
     double *hs_lo, *hs_hi;  // bisection bracket of particles handed to the per-particle search
     int32_t* hs_it;         // counts already done for them
     int32_t* wl;            // their indices (count in status[3])
-    double* red_part;       // bbox partials: kReduceBlocks x 8
+    double* red_part;       // bbox partials: kBoxStride per group of kSlotAlign slots
     double* dt_part;        // per force block (kMaxPairThreads per kThreads slots)
     sph::Grid* grid;        // per instance
     unsigned long long* wctr;  // work counters of persistent kernels (zeroed per build)
