@@ -821,7 +821,8 @@ def measure_workload(args, B, dev, fp64_peak, fp32_peak, e2e=True, sampler=None)
     torch.cuda.synchronize(dev)
     if sampler is not None:
         time.sleep(1.0)
-    ctx.timing_enable(True)
+    # the timed region: one sph_step(K) call as a user makes it (each step
+    # replays the library's captured step graph)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -838,12 +839,19 @@ def measure_workload(args, B, dev, fp64_peak, fp32_peak, e2e=True, sampler=None)
         dist.barrier()
     launches = ctx.launch_count() - l0
     ms = e0.elapsed_time(e1)
-    phase_ms, phase_launches, tsteps = ctx.timing_read()
-    ctx.timing_enable(False)
     status = ctx.sync(stream)
     if status not in (B.SPH_OK, B.SPH_E_HNOCONV):
         raise RuntimeError(f"timed status {B.STATUS_NAMES.get(status)}: {ctx.error()}")
     ms_max = max_over_ranks(ms, world, dev)
+    # the same K steps again with per-phase CUDA events inside the library
+    # (the kernels launched one by one between the events): the phase split
+    # and the force phase's time per launch for the roofline
+    reset()
+    ctx.timing_enable(True)
+    ctx.step(prm, arr, nsteps=args.steps, stream=stream)
+    phase_ms, phase_launches, tsteps = ctx.timing_read()
+    ctx.timing_enable(False)
+    ctx.sync(stream)
     out = {"n": n, "prm": prm, "state": s, "ms": ms_max, "ms_per_step": ms_max / args.steps,
            "value": whole_job_rate(world, n, args.steps, ms_max), "launches": launches,
            "status": B.STATUS_NAMES.get(status), "wall": (w0, w1),
@@ -904,6 +912,7 @@ def measure_workload(args, B, dev, fp64_peak, fp32_peak, e2e=True, sampler=None)
         reset()
         ctx.step(prm, arr, nsteps=args.steps, stream=stream)
         ctx.sync(stream)
+        out["phase_timed_total_ms_per_step"] = sum(phase_ms.values()) / max(tsteps, 1)
         out["roofline"] = forces_roofline(B, ctx, arr, prm, phase_ms, tsteps, fp64_peak,
                                           fp32_peak)
     del ctx, arr, ic

@@ -44,6 +44,8 @@ __device__ __forceinline__ df add(df x, df y) {
     return fast_two_sum(s.hi, e);
 }
 
+__device__ __forceinline__ df sub(df x, df y) { return add(x, neg(y)); }
+
 __device__ __forceinline__ df addf(df x, float b) {
     const df s = two_sum(x.hi, b);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
@@ -190,18 +192,26 @@ __device__ __forceinline__ df lane_sum(df v) {
 }
 
 // The pair kernels' units (length 2^uL, mass 2^uM, velocity 2^uV) of one
-// instance. A quantity of dimension L^a M^b V^c goes from the caller's units
-// into them by the factor L^a M^b V^c of the exact powers of two below.
+// instance, as the exact power-of-two factors that take each packed quantity
+// from the caller's units into them (a quantity of dimension L^a M^b V^c is
+// multiplied by 2^-(a uL + b uM + c uV)).
 struct PairUnits {
-    double L, M, V;  // 2^-uL, 2^-uM, 2^-uV
+    double L;     // lengths (h):              2^-uL
+    double iL;    // inverse lengths (1/h):    2^uL
+    double M;     // masses:                   2^-uM
+    double V;     // velocities (c, v):        2^-uV
+    double rho;   // densities, M L^-3:        2^(3 uL - uM)
+    double A;     // p / rho^2, L^3 V^2 M^-1:  2^(uM - 3 uL - 2 uV)
 };
 
+__host__ __device__ __forceinline__ double pow2(int e) {
+    union { long long i; double d; } u;
+    u.i = (long long)(1023 + e) << 52;
+    return u.d;
+}
+
 __host__ __device__ __forceinline__ PairUnits pair_units(int uL, int uM, int uV) {
-    union { long long i; double d; } l, m, v;
-    l.i = (long long)(1023 - uL) << 52;
-    m.i = (long long)(1023 - uM) << 52;
-    v.i = (long long)(1023 - uV) << 52;
-    return {l.d, m.d, v.d};
+    return {pow2(-uL), pow2(uL), pow2(-uM), pow2(-uV), pow2(3 * uL - uM), pow2(uM - 3 * uL - 2 * uV)};
 }
 
 // The range every float-pair quantity of a pack must lie in, in the pair
@@ -222,11 +232,11 @@ __device__ __forceinline__ void write_pack(float4* __restrict__ dpk, int64_t k, 
                                            double A, double h, double rho, double alpha, double c,
                                            const PairUnits& U, unsigned* status,
                                            unsigned range_bit) {
-    const double hu = hinv / U.L;                           // 1/h:     L^-1
+    const double hu = hinv * U.iL;
     const double h2 = hu * hu;
-    const double Au = A * (U.L * U.L * U.L * U.V * U.V / U.M);  // p/rho^2: L^3 V^2 M^-1
-    const double ru = 0.5 * rho * (U.M / (U.L * U.L * U.L));    // rho:     M L^-3
-    const double cu = 0.5 * alpha * c * U.V;                    // c:       V
+    const double Au = A * U.A;
+    const double ru = 0.5 * rho * U.rho;
+    const double cu = 0.5 * alpha * c * U.V;
     if (!pack_in_range(hu, ru, Au, cu)) atomicOr(status, range_bit);
     const df a = from_double_fp64(hu), b = from_double_fp64(h2 * h2);
     const df cA = from_double_fp64(Au), d = from_double_fp64(0.5 * h * U.L);

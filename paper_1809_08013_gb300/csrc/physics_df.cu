@@ -6,9 +6,9 @@
 // FP64 at 1/64 of the FP32 rate, so the pair loops keep off the FP64 pipe
 // almost entirely. Position differences come from the exact fixed-point
 // chunks of each particle's coordinates (dfl::to_fx, written once per step):
-// three exact FP32 subtractions and one double-float sum per component. Only
-// the velocity differences of the force kernel are formed in FP64 and then
-// split into float pairs by integer operations. Everything else -- r^2, 1/r,
+// three exact FP32 subtractions and one double-float sum per component. The
+// velocities are float pairs (written once per step), and their differences
+// double-float subtractions. Everything else -- r^2, 1/r,
 // the kernel polynomials, the viscosity, the sums -- runs in ~48-bit
 // double-float (df.cuh). Per-particle inputs (1/h, 1/h^4, p/rho^2, h/2, rho/2,
 // alpha c/2, m) are converted once per step into float packs read for every
@@ -39,13 +39,19 @@ __device__ __forceinline__ df w_shape(df q) {
     return q.hi < 1.0f ? win : (q.hi < 2.0f ? wout : zero);
 }
 
-// pi h^4 dW/dr as a function of q >= 0.
+// pi h^4 dW/dr as a function of q >= 0. Both pieces are one product
+// (q + a)(b q + c) with the coefficients of q's piece:
+//   q < 1:      q (2.25 q - 3)                        (a, b, c) = (0, 2.25, -3)
+//   1 <= q < 2: (q - 2)(1.5 - 0.75 q) = -0.75 (2 - q)^2    (a, b, c) = (-2, -0.75, 1.5)
+// q + a is exact (TwoSum), and near q = 2 both factors are small with an
+// absolute error ~2^-47, so the product's absolute error stays ~2^-47 |2 - q|.
 __device__ __forceinline__ df dw_shape(df q) {
-    const df fin = dfl::mul(q, dfl::addf(dfl::mulf(q, 2.25f), -3.0f));  // q (2.25 q - 3)
-    const df t = dfl::addf(dfl::neg(q), 2.0f);
-    const df fout = dfl::mulf(dfl::sqr(t), -0.75f);                       // -0.75 (2 - q)^2
+    const bool in = q.hi < 1.0f;
+    const df u = dfl::addf(q, in ? 0.0f : -2.0f);
+    const df v = dfl::addf(dfl::mulf(q, in ? 2.25f : -0.75f), in ? -3.0f : 1.5f);
+    const df f = dfl::mul(u, v);
     const df zero = {0.0f, 0.0f};
-    return q.hi < 1.0f ? fin : (q.hi < 2.0f ? fout : zero);
+    return q.hi < 2.0f ? f : zero;
 }
 
 // ---- Sinc kernel in double-float. With x = pi q / 2 <= pi and y = x^2,
@@ -280,7 +286,8 @@ void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
 template <int T, int KER>
 __global__ void __launch_bounds__(kThreads, KER == KER_SINC ? 2 : 3)
 k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
-            const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
+            const float4* __restrict__ vpa, const float2* __restrict__ vpb,
+            const float4* __restrict__ dpk,
             const float4* __restrict__ xpk, const double* __restrict__ cint,
             Rows R,
             double4_32a* __restrict__ acc, double* __restrict__ mumax,
@@ -296,7 +303,9 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     df mumx = {0.f, 0.f};
     if (act) {
         const KParams& kp = B.kp[inst];
-        const double4_32a vi = velm[i];
+        const float4 va = vpa[i];
+        const float2 vb = vpb[i];
+        const df VXi = {va.x, va.y}, VYi = {va.z, va.w}, VZi = {vb.x, vb.y};
         const float4 I0 = xpk[3 * i], I1 = xpk[3 * i + 1], I2 = xpk[3 * i + 2];
         const float4 a0 = dpk[3 * i], a1 = dpk[3 * i + 1], a2 = dpk[3 * i + 2];
         const df Hi = {a0.x, a0.y}, Ki = {a0.z, a0.w}, Ai = {a1.x, a1.y}, hhi = {a1.z, a1.w};
@@ -304,7 +313,6 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const Grid& gr = B.grid[inst];
         const bool per = kp.periodic_z != 0;
         const float hlz = gr.hlzc, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
-        const int vsh = -gr.uV;  // velocity differences into the velocity unit
         const int sn = kp.sinc_n;
         const df c_half_pi = dfl::from_double_fp64(0.5 * (KER == KER_M4 ? kInvPi : kp.dnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
@@ -313,7 +321,8 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const int j = __ldg(&ent[e]);
             const float4 J0 = __ldg(&xpk[3 * j]), J1 = __ldg(&xpk[3 * j + 1]);
             const float4 J2 = __ldg(&xpk[3 * j + 2]);
-            const double4_32a vj = velm[j];
+            const float4 wa = __ldg(&vpa[j]);
+            const float2 wb = __ldg(&vpb[j]);
             const float4 b0 = __ldg(&dpk[3 * j]), b1 = __ldg(&dpk[3 * j + 1]);
             const float4 b2 = __ldg(&dpk[3 * j + 2]);
             float z2 = __fsub_rn(I0.z, J0.z), z1 = __fsub_rn(I1.z, J1.z), z0 = __fsub_rn(I2.z, J2.z);
@@ -329,8 +338,8 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const df fb = dw_shape_k<KER>(dfl::mul(r, df{b0.x, b0.y}), sn);
             const df Fb = dfl::mul(dfl::add(dfl::mul(Ki, fa), dfl::mul(df{b0.z, b0.w}, fb)),
                                    dfl::mul(rinv, c_half_pi));
-            const df WX = dfl::from_double(vi.x - vj.x, vsh), WY = dfl::from_double(vi.y - vj.y, vsh);
-            const df WZ = dfl::from_double(vi.z - vj.z, vsh);
+            const df WX = dfl::sub(VXi, df{wa.x, wa.y}), WY = dfl::sub(VYi, df{wa.z, wa.w});
+            const df WZ = dfl::sub(VZi, df{wb.x, wb.y});
             const df vr = dfl::add(dfl::add(dfl::mul(WX, X), dfl::mul(WY, Y)), dfl::mul(WZ, Z));
             df Pi = {0.f, 0.f};
             if (vr.hi < 0.0f) {
@@ -401,15 +410,15 @@ static void forces_df_t(sph_ctx* c, cudaStream_t s) {
     const int b = c->cur;
     if (c->kern_kind == KER_WENDLAND)
         k_forces_df<T, KER_WENDLAND><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
+            n, batch_of(c), c->posh[b], c->vpa, c->vpb, c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
             c->mumax, c->dt_part);
     else if (c->kern_kind == KER_SINC)
         k_forces_df<T, KER_SINC><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
+            n, batch_of(c), c->posh[b], c->vpa, c->vpb, c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
             c->mumax, c->dt_part);
     else
         k_forces_df<T, KER_M4><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->velm[b], c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
+            n, batch_of(c), c->posh[b], c->vpa, c->vpb, c->dpk, c->xpk, c->cint, rows_of(c), c->acc,
             c->mumax, c->dt_part);
 }
 
@@ -525,7 +534,8 @@ __device__ __forceinline__ void symv_df(const df* M, const df& x, const df& y, c
 template <int T, int KER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
-                const double4_32a* __restrict__ velm, const float4* __restrict__ dpk,
+                const float4* __restrict__ vpa, const float2* __restrict__ vpb,
+                const float4* __restrict__ dpk,
                 const float4* __restrict__ xpk, const float4* __restrict__ cpk,
                 const double* __restrict__ cint, Rows R, double4_32a* __restrict__ acc,
                 double* __restrict__ mumax, double* __restrict__ dt_part) {
@@ -540,7 +550,9 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     df mumx = {0.f, 0.f};
     if (act) {
         const KParams& kp = B.kp[inst];
-        const double4_32a vi = velm[i];
+        const float4 va = vpa[i];
+        const float2 vb = vpb[i];
+        const df VXi = {va.x, va.y}, VYi = {va.z, va.w}, VZi = {vb.x, vb.y};
         const float4 I0 = xpk[3 * i], I1 = xpk[3 * i + 1], I2 = xpk[3 * i + 2];
         const float4 a0 = dpk[3 * i], a1 = dpk[3 * i + 1], a2 = dpk[3 * i + 2];
         const df Hi = {a0.x, a0.y}, Ai = {a1.x, a1.y}, hhi = {a1.z, a1.w};
@@ -552,7 +564,6 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const Grid& gr = B.grid[inst];
         const bool per = kp.periodic_z != 0;
         const float hlz = gr.hlzc, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
-        const int vsh = -gr.uV;  // velocity differences into the velocity unit
         const int sn = kp.sinc_n;
         const df kg = dfl::from_double_fp64(-0.5 * (KER == KER_M4 ? kInvPi : kp.wnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
@@ -561,7 +572,8 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const int j = __ldg(&ent[e]);
             const float4 J0 = __ldg(&xpk[3 * j]), J1 = __ldg(&xpk[3 * j + 1]);
             const float4 J2 = __ldg(&xpk[3 * j + 2]);
-            const double4_32a vj = velm[j];
+            const float4 wa = __ldg(&vpa[j]);
+            const float2 wb = __ldg(&vpb[j]);
             const float4 b0 = __ldg(&dpk[3 * j]), b1 = __ldg(&dpk[3 * j + 1]);
             const float4 b2 = __ldg(&dpk[3 * j + 2]);
             float z2 = __fsub_rn(I0.z, J0.z), z1 = __fsub_rn(I1.z, J1.z), z0 = __fsub_rn(I2.z, J2.z);
@@ -589,8 +601,8 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             Gx = dfl::mul(kg, Gx);
             Gy = dfl::mul(kg, Gy);
             Gz = dfl::mul(kg, Gz);
-            const df WX = dfl::from_double(vi.x - vj.x, vsh), WY = dfl::from_double(vi.y - vj.y, vsh);
-            const df WZ = dfl::from_double(vi.z - vj.z, vsh);
+            const df WX = dfl::sub(VXi, df{wa.x, wa.y}), WY = dfl::sub(VYi, df{wa.z, wa.w});
+            const df WZ = dfl::sub(VZi, df{wb.x, wb.y});
             const df vr = dfl::add(dfl::add(dfl::mul(WX, X), dfl::mul(WY, Y)), dfl::mul(WZ, Z));
             df Pi = {0.f, 0.f};
             if (vr.hi < 0.0f) {
@@ -662,7 +674,7 @@ static void iad_df_t(sph_ctx* c, cudaStream_t s) {
     const Batch B = batch_of(c);
     const Rows R = rows_of(c);
     k_iad_df<T, KER><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->xpk, c->vdf, R, c->cpk);
-    k_forces_iad_df<T, KER><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->velm[b], c->dpk, c->xpk,
+    k_forces_iad_df<T, KER><<<nb, kThreads, 0, s>>>(n, B, c->posh[b], c->vpa, c->vpb, c->dpk, c->xpk,
                                                     c->cpk, c->cint, R, c->acc, c->mumax,
                                                     c->dt_part);
 }

@@ -74,10 +74,21 @@ __device__ __forceinline__ void write_xpk(float4* __restrict__ xpk, int64_t k, c
     xpk[3 * k + 2] = make_float4(X.c0, Y.c0, Z.c0, 0.0f);
 }
 
+// Velocity of particle k as float pairs in the velocity unit 2^uV of its
+// instance (the double-float force kernels' view of it).
+__device__ __forceinline__ void write_vpk(float4* __restrict__ vpa, float2* __restrict__ vpb,
+                                          int64_t k, const double4_32a& v, const Grid& g) {
+    const double sv = p2d(-g.uV);
+    const dfl::df x = dfl::from_double_fp64(v.x * sv), y = dfl::from_double_fp64(v.y * sv);
+    const dfl::df z = dfl::from_double_fp64(v.z * sv);
+    vpa[k] = make_float4(x.hi, x.lo, y.hi, y.lo);
+    vpb[k] = make_float2(z.hi, z.lo);
+}
+
 // Re-read the caller's arrays into the sorted order of the last build and
 // derive the per-particle quantities the pair kernels load for j.
 __global__ void __launch_bounds__(kThreads)
-k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ order,
+k_gather_state(int64_t n, int what, int precision, double alpha, const int32_t* __restrict__ order,
                const double* __restrict__ x, const double* __restrict__ y,
                const double* __restrict__ z, const double* __restrict__ h,
                const double* __restrict__ vx, const double* __restrict__ vy,
@@ -86,7 +97,8 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
                const double* __restrict__ cs, double4_32a* __restrict__ posh,
                double4_32a* __restrict__ velm, double4_32a* __restrict__ therm,
                double2* __restrict__ kern, double* __restrict__ cint, float4* __restrict__ dpk,
-               float4* __restrict__ xpk, const Grid* __restrict__ grid, unsigned* status) {
+               float4* __restrict__ xpk, float4* __restrict__ vpa, float2* __restrict__ vpb,
+               const Grid* __restrict__ grid, unsigned* status) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t o = order[k];
@@ -100,15 +112,18 @@ k_gather_state(int64_t n, int what, double alpha, const int32_t* __restrict__ or
     if (what == GATHER_DENSITY) {
         velm[k] = make_double4_32a(0.0, 0.0, 0.0, mm);
     } else {
-        velm[k] = make_double4_32a(vx[o], vy[o], vz[o], mm);
+        const double4_32a vv = make_double4_32a(vx[o], vy[o], vz[o], mm);
+        velm[k] = vv;
+        if (precision == PREC_FP64) write_vpk(vpa, vpb, k, vv, g);
         const double r = rho[o], c = cs[o];
         const double hinv = 1.0 / hh;
         const double h2 = hinv * hinv;
         const double A = p[o] / (r * r);
         therm[k] = make_double4_32a(0.5 * r, A, 0.5 * alpha * c, 0.5 * hh);
         kern[k] = make_double2(hinv, h2 * h2);
-        dfl::write_pack(dpk, k, hinv, A, hh, r, alpha, c, dfl::pair_units(g.uL, g.uM, g.uV),
-                        status, ST_RANGE);
+        if (precision == PREC_FP64)  // the double-float kernels' pack
+            dfl::write_pack(dpk, k, hinv, A, hh, r, alpha, c, dfl::pair_units(g.uL, g.uM, g.uV),
+                            status, ST_RANGE);
         cint[k] = c;
     }
 }
@@ -120,9 +135,9 @@ void launch_gather_state(sph_ctx* c, const sph_particles* P, const KParams& kp, 
     const int b = c->cur;
     c->launches += 1;
     k_gather_state<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-        n, what, kp.alpha, c->order[b], P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m,
+        n, what, kp.precision, kp.alpha, c->order[b], P->x, P->y, P->z, P->h, P->vx, P->vy, P->vz, P->m,
         P->rho, P->p, P->c, c->posh[b], c->velm[b], c->therm, c->kern, c->cint, c->dpk, c->xpk,
-        c->grid, c->status);
+        c->vpa, c->vpb, c->grid, c->status);
 }
 
 // ------------------------------------------------------------ bbox and grid
@@ -361,7 +376,7 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     k = k < -1000 ? -1000 : (k > 1000 ? 1000 : k);
     if (k + g->uL > 100 || k + g->uL < -60) {  // coordinates out of all proportion to h
         k = k + g->uL > 100 ? 100 - g->uL : -60 - g->uL;
-        atomicOr(&status[0], (unsigned)ST_RANGE);
+        if (kp.precision == PREC_FP64) atomicOr(&status[0], (unsigned)ST_RANGE);
     }
     g->fxk = k;
     const dfl::fx3 L = dfl::to_fx(per ? kp.lz : 0.0, k, k + g->uL);
@@ -505,7 +520,8 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
           const double4_32a* __restrict__ velm_in, const double* __restrict__ u_in,
           const int32_t* __restrict__ order_in, double4_32a* __restrict__ posh_out,
           double4_32a* __restrict__ velm_out, double* __restrict__ u_out,
-          int32_t* __restrict__ order_out, float4* __restrict__ fpos, float4* __restrict__ xpk) {
+          int32_t* __restrict__ order_out, float4* __restrict__ fpos, float4* __restrict__ xpk,
+          float4* __restrict__ vpa, float2* __restrict__ vpb) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ntot) return;
     const int inst = (int)(keys[r] >> 24);
@@ -516,6 +532,7 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
     const double4_32a v = velm_in[o];
     velm_out[k] = v;
     write_xpk(xpk, k, p, v.w, B.grid[inst]);
+    if (B.kp[inst].precision == PREC_FP64) write_vpk(vpa, vpb, k, v, B.grid[inst]);
     u_out[k] = u_in[o];
     order_out[k] = order_in[o];
     fpos[k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
@@ -588,7 +605,7 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const int a = c->cur, b = 1 - c->cur;
     k_permute<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->vals[src], c->posh[a],
                                         c->velm[a], c->ue[a], c->order[a], c->posh[b], c->velm[b],
-                                        c->ue[b], c->order[b], c->fpos, c->xpk);
+                                        c->ue[b], c->order[b], c->fpos, c->xpk, c->vpa, c->vpb);
     c->cur = b;
     k_cells_clear<<<dim3(64, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->cells, c->cell_hmax);
     k_cells_mark<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->cells);

@@ -118,7 +118,7 @@ void free_all(sph_ctx* c) {
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
                     c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
-                    c->tune_dt, c->roff, c->wctr, c->recs, c->iad_a, c->iad_b, c->vol, c->xpk,
+                    c->tune_dt, c->roff, c->wctr, c->recs, c->iad_a, c->iad_b, c->vol, c->xpk, c->vpa, c->vpb,
                     c->stage, c->stage_nnb, c->vdf, c->cpk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -183,7 +183,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
     }
     ok = ok && al(&c->therm, N) && al(&c->kern, N) && al(&c->acc, N) &&
          al(&c->pint, N) && al(&c->cint, N) && al(&c->dpk, 3 * N) &&
-         al(&c->xpk, 3 * N) && al(&c->mpk, 5 * N) &&
+         al(&c->xpk, 3 * N) && al(&c->vpa, N) && al(&c->vpb, N) && al(&c->mpk, 4 * N) &&
          al(&c->mumax, N) && al(&c->iad_a, N) && al(&c->iad_b, N) && al(&c->vol, N) && al(&c->vdf, N) &&
          al(&c->cpk, 3 * N) &&
          al(&c->fpos, N) && al(&c->tin, N) &&
@@ -308,13 +308,79 @@ void launch_step(sph_ctx* c, double* dt, double* time, cudaStream_t s) {
     launch_leapfrog(c, dt, s);
 }
 
+void drop_step_graphs(sph_ctx* c) {
+    for (auto& g : c->sg) {
+        if (g.valid) cudaGraphExecDestroy(g.exec);
+        g.valid = false;
+    }
+}
+
+// One step of the current batch through the cached graph of its parity,
+// captured (on the context's private stream) when missing or when anything
+// the launches bake in has changed. Returns false, with nothing enqueued,
+// when a graph cannot be made or launched: the caller then launches the step
+// directly. Replaying gives the same kernels in the same order as launching
+// them, so the results are the same bits.
+bool step_graph(sph_ctx* c, double* dt, double* time, cudaStream_t s) {
+    const int par = c->cur;
+    const int64_t key[9] = {c->n, c->ntot, c->ninst, c->prec, c->tpp, c->kern_kind, c->grad_kind,
+                            (int64_t)(intptr_t)dt, (int64_t)(intptr_t)time};
+    sph_ctx::StepGraph& g = c->sg[par];
+    if (!g.valid || memcmp(g.key, key, sizeof key) != 0) {
+        if (g.valid) cudaGraphExecDestroy(g.exec);
+        g.valid = false;
+        if (!c->gstream && cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess) {
+            c->gstream = nullptr;
+            cudaGetLastError();
+            return false;
+        }
+        const int64_t l0 = c->launches;
+        if (cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        launch_step(c, dt, time, c->gstream);  // recorded, not run
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->gstream, &graph);
+        const int64_t nl = c->launches - l0;
+        c->launches = l0;
+        c->cur = par;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        g.valid = true;
+        g.launches = nl;
+        memcpy(g.key, key, sizeof key);
+    }
+    if (cudaGraphLaunch(g.exec, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    c->cur = 1 - par;  // what the step's sort does to the state buffers
+    c->launches += g.launches;
+    c->csr_ready = false;
+    return true;
+}
+
 // nsteps steps of the current batch: the caller's arrays are read into the
 // slot layout, and the final state is written back after the last step.
+// Each step replays the step graph of its parity, unless per-phase timing is
+// on (events between the phases) or the stream is being captured already
+// (the caller is recording the launches into a graph of its own).
 void run_steps(sph_ctx* c, sph_particles* P, int nsteps, cudaStream_t s) {
     mark(c, -1, s);
     launch_load_state(c, P, s);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;  // unknown: launch directly
+    }
+    const bool graphs = !c->timing && c->n > 0 && cs == cudaStreamCaptureStatusNone;
     for (int k = 0; k < nsteps; ++k) {
-        launch_step(c, P->dt, P->time, s);
+        if (!(graphs && step_graph(c, P->dt, P->time, s))) launch_step(c, P->dt, P->time, s);
         if (k == nsteps - 1)
             launch_scatter(c, P, SC_POS | SC_VEL | SC_H | SC_U | SC_RHO | SC_PC | SC_ACC |
                                      SC_MUMAX | SC_NNB, s);
@@ -478,6 +544,8 @@ void sph_ctx_destroy(sph_ctx* c) {
     if (!c) return;
     DeviceGuard dg(c->device);
     cudaDeviceSynchronize();
+    drop_step_graphs(c);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     free_events(c);
     free_all(c);
     delete c;

@@ -190,7 +190,9 @@ struct sph_ctx {
     float4* dpk;            // 3 per particle: double-float pack of the force kernel
     float4* xpk;            // 3 per particle: exact fixed-point chunks of the position
                             // and the mass as a float pair (double-float pair kernels)
-    float4* mpk;            // 5 per particle: pack of the mixed-precision pair kernels
+    float4* vpa;            // velocity as float pairs in the velocity unit of the pair
+    float2* vpb;            // kernels: (vx.hi, vx.lo, vy.hi, vy.lo) and (vz.hi, vz.lo)
+    float4* mpk;            // 4 per particle: pack of the mixed-precision pair kernels
     double* mumax;
     double4_32a* iad_a;     // IAD matrices C_i: (xx, xy, xz, yy) ...
     double2* iad_b;         // ... and (yz, zz)
@@ -241,6 +243,16 @@ struct sph_ctx {
     int64_t mark_launches;  // launches at the previous marker
     int64_t phase_launches[SPH_NPHASES];
     int64_t timed_steps;
+    // One step of the current batch as a CUDA graph, per parity of the
+    // double-buffered state (cur at the start of the step), replayed by
+    // sph_step / sph_batch_step instead of its ~35 separate launches.
+    struct StepGraph {
+        bool valid;
+        int64_t key[9];          // what the launches bake in (sizes, kinds, dt/time pointers)
+        cudaGraphExec_t exec;
+        int64_t launches;        // kernels of one step
+    } sg[2];
+    cudaStream_t gstream;   // private stream the step graphs are captured on (lazy)
     char err[512];
 };
 

@@ -56,8 +56,9 @@ def _rescaled(s, prm, kl, km):
     return s2, p2
 
 
-SCALE_OUT = {"x": 1, "y": 1, "z": 1, "h": 1, "ax": -1, "ay": -1, "az": -1, "du": -1, "dt": 1,
-             "time": 1}
+# exponent of each output's factor, in units of kl
+SCALE_OUT = {"x": 1, "y": 1, "z": 1, "h": 1, "m": 3, "ax": -1, "ay": -1, "az": -1, "du": -1,
+             "dt": 1, "time": 1}
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
