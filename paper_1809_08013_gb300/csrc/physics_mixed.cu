@@ -5,22 +5,22 @@
 // FP64 (the neighbour sets are the exact FP64 ones). Definitions as in
 // physics.cu; results are within ~1e-6 of the FP64 evaluation.
 //
-// Relative coordinates without the FP64 pipe: each FP64 position is split
-// once per step into a float pair hi + lo; for a pair, (hi_i - hi_j) is exact
-// when the two highs are within a factor of two (and within 2^-24 |dx|
-// otherwise), so dx = (hi_i - hi_j) + (lo_i - lo_j) carries a relative error
-// of a few 2^-24. Along the periodic z axis the wrap is applied to the exact
-// high difference (see rel_z). Velocities are single floats: v_ij is the FP32
-// difference of the two, within 2^-24 (|v_i| + |v_j|) of the exact one.
+// Relative coordinates without the FP64 pipe: each FP64 position (and
+// velocity) is split once per step into a float pair hi + lo; for a pair,
+// (hi_i - hi_j) is exact when the two highs are within a factor of two (and
+// within 2^-24 |dx| otherwise), so dx = (hi_i - hi_j) + (lo_i - lo_j) carries
+// a relative error of a few 2^-24. Along the periodic z axis the wrap is
+// applied to the exact high difference (see rel_z).
 //
 // Every quantity of the pack is in the instance's pair units (Grid::uL, uM,
 // uV; powers of two near the mean h, the largest mass and a velocity scale),
 // so FP32 holds it whatever units the caller uses; the sums go back to the
 // caller's units exactly when they are written out.
 //
-// Per-particle pack, four float4 (64 B, two 32-byte sectors):
-//   mpk[4k]   = (x_hi, y_hi, z_hi, m)      mpk[4k+1] = (x_lo, y_lo, z_lo, 1/h)
-//   mpk[4k+2] = (vx, vy, vz, 1/h^4)        mpk[4k+3] = (p/rho^2, h/2, rho/2, alpha c/2)
+// Per-particle pack, five float4 (80 B):
+//   mpk[5k]   = (x_hi, y_hi, z_hi, m)      mpk[5k+1] = (x_lo, y_lo, z_lo, 1/h)
+//   mpk[5k+2] = (vx_hi, vy_hi, vz_hi, 1/h^4)  mpk[5k+3] = (vx_lo, vy_lo, vz_lo, p/rho^2)
+//   mpk[5k+4] = (h/2, rho/2, alpha c/2, 0)
 #include <math_constants.h>
 
 #include "df.cuh"
@@ -29,8 +29,6 @@
 namespace sph {
 
 using dfl::df;
-
-constexpr int kMx = 4;  // float4 per particle in the pack
 
 namespace {
 
@@ -133,8 +131,9 @@ __device__ __forceinline__ void pack_thermo(float4* __restrict__ mpk, int64_t k,
     const double ru = 0.5 * rho * U.rho;
     const double cu = 0.5 * alpha * c * U.V;
     if (!dfl::pack_in_range(hu, ru, Au, cu)) atomicOr(status, (unsigned)ST_RANGE);
-    mpk[kMx * k + 2].w = (float)(h2 * h2);
-    mpk[kMx * k + 3] = make_float4((float)Au, (float)(0.5 * h * U.L), (float)ru, (float)cu);
+    mpk[5 * k + 2].w = (float)(h2 * h2);
+    mpk[5 * k + 3].w = (float)Au;
+    mpk[5 * k + 4] = make_float4((float)(0.5 * h * U.L), (float)ru, (float)cu, 0.0f);
 }
 
 // Position / velocity / mass / 1/h part of the pack from the sorted state;
@@ -151,17 +150,24 @@ k_pack_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     const dfl::PairUnits U = dfl::pair_units(g.uL, g.uM, g.uV);
     const double4_32a p = posh[k];
     const double4_32a v = velm[k];
-    float xh, xl, yh, yl, zh, zl;
+    float xh, xl, yh, yl, zh, zl, ah, al, bh, bl, ch, cl;
     split2(p.x * U.L, xh, xl);
     split2(p.y * U.L, yh, yl);
     split2(p.z * U.L, zh, zl);
+    split2(v.x * U.V, ah, al);
+    split2(v.y * U.V, bh, bl);
+    split2(v.z * U.V, ch, cl);
     const double hinv = U.iL / p.w;
-    mpk[kMx * k + 0] = make_float4(xh, yh, zh, (float)(v.w * U.M));
-    mpk[kMx * k + 1] = make_float4(xl, yl, zl, (float)hinv);
-    mpk[kMx * k + 2] = make_float4((float)(v.x * U.V), (float)(v.y * U.V), (float)(v.z * U.V), 0.0f);
+    mpk[5 * k + 0] = make_float4(xh, yh, zh, (float)(v.w * U.M));
+    mpk[5 * k + 1] = make_float4(xl, yl, zl, (float)hinv);
     if (THERMO) {
         const double4_32a t = therm[k];
+        mpk[5 * k + 2] = make_float4(ah, bh, ch, 0.0f);
+        mpk[5 * k + 3] = make_float4(al, bl, cl, 0.0f);
         pack_thermo(mpk, k, p.w, 2.0 * t.x, t.y, 1.0, 2.0 * t.z, U, status);
+    } else {
+        mpk[5 * k + 2] = make_float4(ah, bh, ch, 0.0f);
+        mpk[5 * k + 3] = make_float4(al, bl, cl, 0.0f);
     }
 }
 
@@ -182,13 +188,13 @@ k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     const KParams& kp = B.kp[inst];
     df acc = {0.0f, 0.0f};
     if (act) {
-    const float4 a0 = mpk[kMx * i], a1 = mpk[kMx * i + 1];
+    const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1];
     const float hinv = a1.w;
     const ZWrap zw = make_zwrap(kp, B.grid[inst]);
     if (sub == 0) acc = df{a0.w, 0.0f};  // self term m_i W(0, h_i): shape 1
     for (int e = sub; e < len; e += T) {
         const int j = __ldg(&ent[e]);
-        const float4 b0 = __ldg(&mpk[kMx * j]), b1 = __ldg(&mpk[kMx * j + 1]);
+        const float4 b0 = __ldg(&mpk[5 * j]), b1 = __ldg(&mpk[5 * j + 1]);
         const float dx = rel(a0.x, a1.x, b0.x, b1.x), dy = rel(a0.y, a1.y, b0.y, b1.y);
         const float dz = rel_z(a0.z, a1.z, b0.z, b1.z, zw);
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -235,15 +241,16 @@ k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     float mum = 0.0f;
     if (act) {
         const KParams& kp = B.kp[inst];
-        const float4 a0 = mpk[kMx * i], a1 = mpk[kMx * i + 1], a2 = mpk[kMx * i + 2];
-        const float4 a3 = mpk[kMx * i + 3];
+        const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1], a2 = mpk[5 * i + 2];
+        const float4 a3 = mpk[5 * i + 3], a4 = mpk[5 * i + 4];
         const ZWrap zw = make_zwrap(kp, B.grid[inst]);
         const float eta2 = (float)kp.eta2, beta = (float)kp.beta;
         const float cpi = 0.5f * kInvPiF;
         for (int e = sub; e < len; e += T) {
             const int j = __ldg(&ent[e]);
-            const float4 b0 = __ldg(&mpk[kMx * j]), b1 = __ldg(&mpk[kMx * j + 1]);
-            const float4 b2 = __ldg(&mpk[kMx * j + 2]), b3 = __ldg(&mpk[kMx * j + 3]);
+            const float4 b0 = __ldg(&mpk[5 * j]), b1 = __ldg(&mpk[5 * j + 1]);
+            const float4 b2 = __ldg(&mpk[5 * j + 2]), b3 = __ldg(&mpk[5 * j + 3]);
+            const float4 b4 = __ldg(&mpk[5 * j + 4]);
             const float dx = rel(a0.x, a1.x, b0.x, b1.x), dy = rel(a0.y, a1.y, b0.y, b1.y);
             const float dz = rel_z(a0.z, a1.z, b0.z, b1.z, zw);
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -252,20 +259,21 @@ k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const float r = r2 * rinv;
             const float fa = dw_shape_f(r * a1.w), fb = dw_shape_f(r * b1.w);
             const float Fb = fmaf(a2.w, fa, b2.w * fb) * (cpi * rinv);
-            const float wx = a2.x - b2.x, wy = a2.y - b2.y, wz = a2.z - b2.z;
+            const float wx = rel(a2.x, a3.x, b2.x, b3.x), wy = rel(a2.y, a3.y, b2.y, b3.y);
+            const float wz = rel(a2.z, a3.z, b2.z, b3.z);
             const float vr = fmaf(wz, dz, fmaf(wy, dy, wx * dx));
             float Pi = 0.0f;
             if (vr < 0.0f) {
-                const float hb = a3.y + b3.y;
+                const float hb = a4.x + b4.x;
                 const float d1 = fmaf(eta2 * hb, hb, r2);
-                const float rb = a3.z + b3.z;
+                const float rb = a4.y + b4.y;
                 const float R = rcp_f(d1 * rb);
                 const float mu = hb * vr * rb * R;
-                Pi = mu * fmaf(beta, mu, -(a3.w + b3.w)) * (d1 * R);
+                Pi = mu * fmaf(beta, mu, -(a4.z + b4.z)) * (d1 * R);
                 mum = fmaxf(mum, -mu);
             }
             const float mF = b0.w * Fb;
-            const float g = mF * ((a3.x + b3.x) + Pi);
+            const float g = mF * ((a3.w + b3.w) + Pi);
             sx = dfl::addf(sx, g * dx);
             sy = dfl::addf(sy, g * dy);
             sz = dfl::addf(sz, g * dz);
@@ -288,7 +296,7 @@ k_forces_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const int ins = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
         const Grid& gu = B.grid[ins];
         const double sa = p2d(2 * gu.uV - gu.uL), su = p2d(3 * gu.uV - gu.uL);
-        const double Aid = (double)mpk[kMx * i + 3].x;
+        const double Aid = (double)mpk[5 * i + 3].w;
         acc[i] = make_double4_32a(-dfl::to_double(sx) * sa, -dfl::to_double(sy) * sa,
                                   -dfl::to_double(sz) * sa,
                                   fma(Aid, dfl::to_double(sp), 0.5 * dfl::to_double(sv)) * su);

@@ -183,7 +183,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
     }
     ok = ok && al(&c->therm, N) && al(&c->kern, N) && al(&c->acc, N) &&
          al(&c->pint, N) && al(&c->cint, N) && al(&c->dpk, 3 * N) &&
-         al(&c->xpk, 3 * N) && al(&c->vpa, N) && al(&c->vpb, N) && al(&c->mpk, 4 * N) &&
+         al(&c->xpk, 3 * N) && al(&c->vpa, N) && al(&c->vpb, N) && al(&c->mpk, 5 * N) &&
          al(&c->mumax, N) && al(&c->iad_a, N) && al(&c->iad_b, N) && al(&c->vol, N) && al(&c->vdf, N) &&
          al(&c->cpk, 3 * N) &&
          al(&c->fpos, N) && al(&c->tin, N) &&

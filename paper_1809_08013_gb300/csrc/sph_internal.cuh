@@ -192,7 +192,7 @@ struct sph_ctx {
                             // and the mass as a float pair (double-float pair kernels)
     float4* vpa;            // velocity as float pairs in the velocity unit of the pair
     float2* vpb;            // kernels: (vx.hi, vx.lo, vy.hi, vy.lo) and (vz.hi, vz.lo)
-    float4* mpk;            // 4 per particle: pack of the mixed-precision pair kernels
+    float4* mpk;            // 5 per particle: pack of the mixed-precision pair kernels
     double* mumax;
     double4_32a* iad_a;     // IAD matrices C_i: (xx, xy, xz, yy) ...
     double2* iad_b;         // ... and (yz, zz)
