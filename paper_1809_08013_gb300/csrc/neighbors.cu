@@ -655,7 +655,16 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
 }
 
 // Phase 2: one warp per handed-over particle (persistent grid over the
-// worklist), continuing its bisection where phase 1 stopped.
+// worklist), continuing its bisection where phase 1 stopped. A walk over the
+// cells records, in shared memory and in walk order, every candidate that may
+// lie within 2 hs, hs = the largest h the bisection can still test without a
+// new walk (hi once bracketed; 1.25 h, the next growth step, before); the
+// counts at every h <= hs then come from the records with the same FP32 /
+// exact FP64 decisions as a walk, and the gather set is written in the order
+// a walk at h would find it. Only growth beyond hs (or more candidates than
+// the record buffer holds) walks the cells again.
+constexpr int kRecW = 512;  // records per warp
+
 __global__ void __launch_bounds__(kThreads)
 k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
             const int2* __restrict__ cells,
@@ -664,11 +673,13 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
             const double* __restrict__ hs_hi, const int32_t* __restrict__ hs_it,
             const int32_t* __restrict__ wl, unsigned* __restrict__ status) {
     __shared__ int s_start[kThreads / 32][32], s_pref[kThreads / 32][32];
+    __shared__ int2 s_rec[kThreads / 32][kRecW];  // (FP32 r^2 bits, j)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const unsigned count = *(volatile unsigned*)&status[3];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const unsigned lt = (1u << lane) - 1u;
+    int2* rec = s_rec[warp];
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nwarps) {
         const int64_t i = wl[w];
         const int inst = slot_inst(B, i);
@@ -683,30 +694,81 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
         int cnt = 0;
         bool conv = false;
         int32_t* slab = rslab + i * kRSlab;
+        double hs = -1.0;  // radius / 2 the records cover (none yet)
+        int nrec = 0;
         for (int it = hs_it[i]; it < max_it; ++it) {
             const double R = 2.0 * h;
             const Thr t = thresholds(R, g);
             double R2 = -1.0;  // (2h)^2 in FP64, formed on first use
             int c = 0;
-            particle_pass<1>(g, cl, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
-                             [&](bool valid, int j) {
-                                 bool in = false, bd = false;
-                                 if (valid && j != i) {
-                                     const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
-                                     in = r2f < t.tin;
-                                     bd = !in && r2f <= t.tout;
-                                 }
-                                 if (__any_sync(kFull, bd) && bd) {
-                                     if (R2 < 0.0) R2 = __dmul_rn(R, R);
-                                     in = exact_r2(pi, posh[j], g) < R2;
-                                 }
-                                 const unsigned m = __ballot_sync(kFull, in);
-                                 if (in) {
-                                     const int q = c + __popc(m & lt);
-                                     if (q < kGSlab) slab[q] = j;
-                                 }
-                                 c += __popc(m);
-                             });
+            if (!(h <= hs)) {
+                // walk the cells once more and record everything that may lie
+                // within 2 hs of the particle
+                hs = isinf(hi) ? __dmul_rn(h, 1.25) : hi;
+                const float tout_s = thresholds(2.0 * hs, g).tout;
+                nrec = 0;
+                particle_pass<1>(g, cl, nullptr, fi, reach_f32(hs), 0, s_start[warp], s_pref[warp],
+                                 [&](bool valid, int j) {
+                                     float r2f = 0.0f;
+                                     bool keep = false;
+                                     if (valid && j != i) {
+                                         r2f = f_r2(fi, __ldg(&fpos[j]), g);
+                                         keep = r2f <= tout_s;
+                                     }
+                                     const unsigned m = __ballot_sync(kFull, keep);
+                                     if (keep) {
+                                         const int q = nrec + __popc(m & lt);
+                                         if (q < kRecW) rec[q] = make_int2(__float_as_int(r2f), j);
+                                     }
+                                     nrec += __popc(m);
+                                 });
+                __syncwarp();
+                if (nrec > kRecW) hs = -1.0;  // too many to keep: count by walking
+            }
+            if (h <= hs) {
+                for (int q0 = 0; q0 < nrec; q0 += 32) {
+                    const int q = q0 + lane;
+                    bool in = false, bd = false;
+                    int j = -1;
+                    if (q < nrec) {
+                        const int2 e = rec[q];
+                        const float r2f = __int_as_float(e.x);
+                        j = e.y;
+                        in = r2f < t.tin;
+                        bd = !in && r2f <= t.tout;
+                    }
+                    if (__any_sync(kFull, bd) && bd) {
+                        if (R2 < 0.0) R2 = __dmul_rn(R, R);
+                        in = exact_r2(pi, posh[j], g) < R2;
+                    }
+                    const unsigned m = __ballot_sync(kFull, in);
+                    if (in) {
+                        const int qq = c + __popc(m & lt);
+                        if (qq < kGSlab) slab[qq] = j;
+                    }
+                    c += __popc(m);
+                }
+            } else {
+                particle_pass<1>(g, cl, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
+                                 [&](bool valid, int j) {
+                                     bool in = false, bd = false;
+                                     if (valid && j != i) {
+                                         const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
+                                         in = r2f < t.tin;
+                                         bd = !in && r2f <= t.tout;
+                                     }
+                                     if (__any_sync(kFull, bd) && bd) {
+                                         if (R2 < 0.0) R2 = __dmul_rn(R, R);
+                                         in = exact_r2(pi, posh[j], g) < R2;
+                                     }
+                                     const unsigned m = __ballot_sync(kFull, in);
+                                     if (in) {
+                                         const int q = c + __popc(m & lt);
+                                         if (q < kGSlab) slab[q] = j;
+                                     }
+                                     c += __popc(m);
+                                 });
+            }
             cnt = c;
             if (cnt >= lowb && cnt <= highb) {
                 conv = true;
@@ -721,6 +783,7 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
                 h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
             }
         }
+        __syncwarp();  // the records are reused by this warp's next particle
         if (lane == 0) {
             posh[i].w = h;
             nnb[i] = cnt;
