@@ -46,6 +46,16 @@ __device__ __forceinline__ df add(df x, df y) {
 
 __device__ __forceinline__ df sub(df x, df y) { return add(x, neg(y)); }
 
+// x + y for operands of the same sign (no cancellation), left unnormalised:
+// the low part may reach ~1.5 ulp of the high one, which products, 1/sqrt,
+// 1/x and further same-sign sums accept at the same ~2^-46 relative error.
+// Not for running sums (the low parts would keep growing) nor for results
+// whose sign is tested.
+__device__ __forceinline__ df add_same(df x, df y) {
+    const df s = two_sum(x.hi, y.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+
 __device__ __forceinline__ df addf(df x, float b) {
     const df s = two_sum(x.hi, b);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
@@ -80,24 +90,37 @@ __device__ __forceinline__ df sqr(df x) {
 // exact scaling by a power of two (no overflow/underflow in use)
 __device__ __forceinline__ df scale2(df x, float p2) { return {__fmul_rn(x.hi, p2), __fmul_rn(x.lo, p2)}; }
 
-// 1/sqrt(x), x > 0: FP32 approximation, then one Newton step in double-float,
-// y1 = y0 + y0 (1 - x y0^2) / 2 (error ~2^-46 from the ~2^-23 seed).
+// 1/sqrt(x), x > 0: FP32 approximation y0, then one Newton step
+// y1 = y0 + y0 e / 2 with e = 1 - x y0^2 (error ~2^-46 from the ~2^-23 seed).
+// e is small (~2^-22), so the FMAs below give it to a few units of 2^-46
+// absolutely: y0^2 = p + pe exactly, then 1 - x_hi p, - x_hi pe, - x_lo p.
+// The correction y0 e / 2 is below 2^-22 y0 and joins y0 by Fast2Sum.
 __device__ __forceinline__ df rsqrt(df x) {
     float y0;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(x.hi));
-    const float hy = __fmul_rn(0.5f, y0);
     const float p = __fmul_rn(y0, y0);
-    const df y2 = {p, __fmaf_rn(y0, y0, -p)};
-    const df e = addf(neg(mul(x, y2)), 1.0f);  // 1 - x y0^2, small: computed exactly enough
-    return addf(mulf(e, hy), y0);
+    const float pe = __fmaf_rn(y0, y0, -p);
+    float e = __fmaf_rn(-x.hi, p, 1.0f);
+    e = __fmaf_rn(-x.hi, pe, e);
+    e = __fmaf_rn(-x.lo, p, e);
+    const float hy = __fmul_rn(0.5f, y0);
+    const float c = __fmul_rn(hy, e);
+    const float cl = __fmaf_rn(hy, e, -c);
+    const df r = fast_two_sum(y0, c);
+    return {r.hi, __fadd_rn(r.lo, cl)};
 }
 
-// 1/x, x > 0: FP32 approximation, one Newton step y1 = y0 + y0 (1 - x y0).
+// 1/x, x > 0: FP32 approximation y0, one Newton step y1 = y0 + y0 e with
+// e = 1 - x y0 (~2^-22), formed by FMAs as in rsqrt.
 __device__ __forceinline__ df rcp(df x) {
     float y0;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(x.hi));
-    const df e = addf(neg(mulf(x, y0)), 1.0f);
-    return addf(mulf(e, y0), y0);
+    float e = __fmaf_rn(-x.hi, y0, 1.0f);
+    e = __fmaf_rn(-x.lo, y0, e);
+    const float c = __fmul_rn(y0, e);
+    const float cl = __fmaf_rn(y0, e, -c);
+    const df r = fast_two_sum(y0, c);
+    return {r.hi, __fadd_rn(r.lo, cl)};
 }
 
 // Per-particle conversion to double-float with the FP64 pipe (exact to 2^-48).
