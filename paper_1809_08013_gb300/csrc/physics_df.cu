@@ -210,7 +210,7 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const df X = dfl::fx_sum(__fsub_rn(I0.x, J0.x), __fsub_rn(I1.x, J1.x), __fsub_rn(I2.x, J2.x));
         const df Y = dfl::fx_sum(__fsub_rn(I0.y, J0.y), __fsub_rn(I1.y, J1.y), __fsub_rn(I2.y, J2.y));
         const df Z = dfl::fx_sum(z2, z1, z0);
-        const df r2 = dfl::add_same(dfl::add_same(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
+        const df r2 = dfl::add(dfl::add_same(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
         df w = {1.0f, 0.0f};  // coincident particles: q = 0
         if (r2.hi > 0.0f) {
             const df q = dfl::mul(dfl::mul(r2, dfl::rsqrt(r2)), Hi);
@@ -330,29 +330,26 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const df X = dfl::fx_sum(__fsub_rn(I0.x, J0.x), __fsub_rn(I1.x, J1.x), __fsub_rn(I2.x, J2.x));
             const df Y = dfl::fx_sum(__fsub_rn(I0.y, J0.y), __fsub_rn(I1.y, J1.y), __fsub_rn(I2.y, J2.y));
             const df Z = dfl::fx_sum(z2, z1, z0);
-            const df r2 = dfl::add_same(dfl::add_same(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
+            const df r2 = dfl::add(dfl::add_same(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
             if (!(r2.hi > 0.0f)) continue;  // coincident particles exert no force
             const df rinv = dfl::rsqrt(r2);
             const df r = dfl::mul(r2, rinv);
             const df fa = dw_shape_k<KER>(dfl::mul(r, Hi), sn);
             const df fb = dw_shape_k<KER>(dfl::mul(r, df{b0.x, b0.y}), sn);
-            // f(q) <= 0 on the whole support for every kernel: a same-sign sum
-            const df Fb = dfl::mul(dfl::add_same(dfl::mul(Ki, fa), dfl::mul(df{b0.z, b0.w}, fb)),
+            const df Fb = dfl::mul(dfl::add(dfl::mul(Ki, fa), dfl::mul(df{b0.z, b0.w}, fb)),
                                    dfl::mul(rinv, c_half_pi));
             const df WX = dfl::sub(VXi, df{wa.x, wa.y}), WY = dfl::sub(VYi, df{wa.z, wa.w});
             const df WZ = dfl::sub(VZi, df{wb.x, wb.y});
             const df vr = dfl::add(dfl::add(dfl::mul(WX, X), dfl::mul(WY, Y)), dfl::mul(WZ, Z));
             df Pi = {0.f, 0.f};
             if (vr.hi < 0.0f) {
-                // h, rho, c > 0 and r^2 >= 0: same-sign sums
-                const df hb = dfl::add_same(hhi, df{b1.z, b1.w});
-                const df d1 = dfl::add_same(r2, dfl::mul(dfl::mul(eta2, hb), hb));
-                const df rb = dfl::add_same(rhi, df{b2.x, b2.y});
+                const df hb = dfl::add(hhi, df{b1.z, b1.w});
+                const df d1 = dfl::add(r2, dfl::mul(dfl::mul(eta2, hb), hb));
+                const df rb = dfl::add(rhi, df{b2.x, b2.y});
                 const df R = dfl::rcp(dfl::mul(d1, rb));
                 const df mu = dfl::mul(dfl::mul(dfl::mul(hb, vr), rb), R);
-                const df cb = dfl::add_same(cai, df{b2.z, b2.w});
-                // beta mu - alpha cb: mu < 0 here, so both terms are negative
-                const df t = dfl::add_same(dfl::mul(betad, mu), dfl::neg(cb));
+                const df cb = dfl::add(cai, df{b2.z, b2.w});
+                const df t = dfl::add(dfl::mul(betad, mu), dfl::neg(cb));
                 Pi = dfl::mul(dfl::mul(mu, t), dfl::mul(d1, R));
                 if (-mu.hi > mumx.hi) mumx = dfl::neg(mu);
             }
@@ -489,7 +486,7 @@ k_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const df X = dfl::fx_sum(__fsub_rn(I0.x, J0.x), __fsub_rn(I1.x, J1.x), __fsub_rn(I2.x, J2.x));
             const df Y = dfl::fx_sum(__fsub_rn(I0.y, J0.y), __fsub_rn(I1.y, J1.y), __fsub_rn(I2.y, J2.y));
             const df Z = dfl::fx_sum(z2, z1, z0);
-            const df r2 = dfl::add_same(dfl::add_same(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
+            const df r2 = dfl::add(dfl::add_same(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
             if (!(r2.hi > 0.0f)) continue;  // r = 0 adds nothing to tau
             const df q = dfl::mul(dfl::mul(r2, dfl::rsqrt(r2)), Hi);
             const df w = dfl::mul(df{vj.x, vj.y}, w_shape_k<KER>(q, sn));
@@ -584,7 +581,7 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const df X = dfl::fx_sum(__fsub_rn(I0.x, J0.x), __fsub_rn(I1.x, J1.x), __fsub_rn(I2.x, J2.x));
             const df Y = dfl::fx_sum(__fsub_rn(I0.y, J0.y), __fsub_rn(I1.y, J1.y), __fsub_rn(I2.y, J2.y));
             const df Z = dfl::fx_sum(z2, z1, z0);
-            const df r2 = dfl::add_same(dfl::add_same(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
+            const df r2 = dfl::add(dfl::add_same(dfl::sqr(X), dfl::sqr(Y)), dfl::sqr(Z));
             if (!(r2.hi > 0.0f)) continue;  // coincident particles exert no force
             const df r = dfl::mul(r2, dfl::rsqrt(r2));
             const df Hj = {b0.x, b0.y};
@@ -609,14 +606,13 @@ k_forces_iad_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const df vr = dfl::add(dfl::add(dfl::mul(WX, X), dfl::mul(WY, Y)), dfl::mul(WZ, Z));
             df Pi = {0.f, 0.f};
             if (vr.hi < 0.0f) {
-                // h, rho, c > 0 and r^2 >= 0: same-sign sums
-                const df hb = dfl::add_same(hhi, df{b1.z, b1.w});
-                const df d1 = dfl::add_same(r2, dfl::mul(dfl::mul(eta2, hb), hb));
-                const df rb = dfl::add_same(rhi, df{b2.x, b2.y});
+                const df hb = dfl::add(hhi, df{b1.z, b1.w});
+                const df d1 = dfl::add(r2, dfl::mul(dfl::mul(eta2, hb), hb));
+                const df rb = dfl::add(rhi, df{b2.x, b2.y});
                 const df Rr = dfl::rcp(dfl::mul(d1, rb));
                 const df mu = dfl::mul(dfl::mul(dfl::mul(hb, vr), rb), Rr);
-                const df cb = dfl::add_same(cai, df{b2.z, b2.w});
-                const df tt = dfl::add_same(dfl::mul(betad, mu), dfl::neg(cb));
+                const df cb = dfl::add(cai, df{b2.z, b2.w});
+                const df tt = dfl::add(dfl::mul(betad, mu), dfl::neg(cb));
                 Pi = dfl::mul(dfl::mul(mu, tt), dfl::mul(d1, Rr));
                 if (-mu.hi > mumx.hi) mumx = dfl::neg(mu);
             }
