@@ -558,12 +558,14 @@ VARIANTS = (("M4, kernel derivatives, FP64 pipe (precision 2)", 0, 0, 5, 2),
             ("M4, IAD gradients, FP64 pipe (precision 2)", 0, 1, 5, 2))
 
 
-def run_variants(args, B, dev, fp64_peak):
+def run_variants(args, B, dev, fp64_peak, fp32_peak):
     """The Table 1 variants on the benchmark workload: each a separate run of
     --variant-steps steps from the initial conditions (after one untimed
     step), with the pair kernels VARIANTS names. Roofline of the force phase
-    (the force kernel, with k_volume + k_iad for IAD and k_dt_finish) against
-    the FP64 FMA-chain probe, from the counted flops of variant_flops."""
+    (the force kernel, with k_volume + k_iad for IAD and k_dt_finish) from
+    the counted flops of variant_flops, against the FMA-chain probe of the
+    pipe the pair arithmetic runs on: FP32 for double-float (precision 0),
+    FP64 for precision 2."""
     import numpy as np
     import torch
     s, base = make_workload(args)
@@ -605,6 +607,7 @@ def run_variants(args, B, dev, fp64_peak):
         flops = nnz * (base_f + av_f * f_av) + ngather * iad_f
         forces_s = phase_ms["forces"] * 1e-3 / max(tsteps, 1)
         ach = flops / forces_s / 1e12
+        peak = (fp64_peak if prec == 2 else fp32_peak) / 1e12
         out.append({"variant": name, "kernel": kernel, "gradients": grads,
                     "sinc_n": sn if kernel == 2 else None,
                     "ms_per_step": ms / args.variant_steps,
@@ -613,12 +616,13 @@ def run_variants(args, B, dev, fp64_peak):
                     "status": B.STATUS_NAMES.get(st),
                     "precision": prec,
                     "roofline": {"bound": "alu", "kernel": kernel_names(kernel, grads, prec),
-                                 "achieved": ach, "peak": fp64_peak / 1e12,
-                                 "unit": "TFLOP/s", "frac": ach / (fp64_peak / 1e12),
+                                 "achieved": ach, "peak": peak,
+                                 "unit": "TFLOP/s", "frac": ach / peak,
                                  "flops_per_launch": flops,
                                  "counted": {"pair": base_f, "pair_av": av_f,
                                              "iad_pair": iad_f},
-                                 "peak_source": "FP64 FMA-chain probe, this run"}})
+                                 "peak_source": ("FP64" if prec == 2 else "FP32") +
+                                                " FMA-chain probe, this run"}})
     del ctx
     torch.cuda.empty_cache()
     return {"workload": workload_name(args).split(", FP64 accuracy")[0], "steps": args.variant_steps,
@@ -1045,7 +1049,8 @@ def run_native(args):
         for prec in ("fp64", "mixed"):
             ensembles[prec] = run_ensemble(args, B, dev, prec)
     serving = run_serving(args, B, dev) if solo and not args.no_serving else None
-    variants = run_variants(args, B, dev, fp64_peak) if solo and not args.no_variants else None
+    variants = (run_variants(args, B, dev, fp64_peak, fp32_peak)
+                if solo and not args.no_variants else None)
 
     clocks = sampler.summary(*main["wall"]) if sampler else None
 
