@@ -797,18 +797,25 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
     }
 }
 
-// Per-particle FP32 thresholds at the final h.
+// Per-particle FP32 thresholds at the final h, and (2h)^2 in the length unit
+// of the double-float pair kernels in the spare float of the position pack
+// (NaN where the periodic wrap could decide differently: exact test only).
 __global__ void __launch_bounds__(kThreads)
 k_finalize_h(int64_t n, Batch B, const double4_32a* __restrict__ posh,
-             float4* __restrict__ fpos, float* __restrict__ tin, int32_t* __restrict__ ocnt) {
+             float4* __restrict__ fpos, float* __restrict__ tin, int32_t* __restrict__ ocnt,
+             float4* __restrict__ xpk) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     ocnt[i] = 0;
     const int inst = slot_inst(B, i);
     if (!slot_real(B, inst, i)) return;
-    const Thr t = thresholds(2.0 * posh[i].w, B.grid + inst);
+    const Grid* g = B.grid + inst;
+    const double h = posh[i].w;
+    const Thr t = thresholds(2.0 * h, g);
     fpos[i].w = t.tout;
     tin[i] = t.tin;
+    const double R = 2.0 * h * p2d(-g->uL);
+    xpk[3 * i + 2].w = (g->periodic_z && 2.0 * h > 0.25 * g->lz) ? CUDART_NAN_F : (float)(R * R);
 }
 
 // Per-cell max h, and the instance's max (one atomic per block); blockIdx.y
@@ -906,9 +913,9 @@ k_outer(int64_t n, Batch B, const double4_32a* __restrict__ posh,
 __global__ void __launch_bounds__(kThreads)
 k_rowlen_sort(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __restrict__ ocnt,
               int32_t* __restrict__ rowlen, int32_t* __restrict__ rslab,
-              const unsigned* __restrict__ status) {
+              const unsigned* __restrict__ status, unsigned mask) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || (status[2] & IF_SLAB_OVF)) return;
+    if (i >= n || (status[2] & mask)) return;
     const int ng = ngather[i], no = ocnt[i];
     rowlen[i] = ng + no;
     int32_t* row = rslab + i * kRSlab + ng;
@@ -930,7 +937,7 @@ k_compose(int64_t n, const int32_t* __restrict__ rowlen, const int32_t* __restri
           unsigned* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (status[2] & IF_SLAB_OVF) return;  // the fallback wrote the CSR
+    if (status[2] & (IF_SLAB_OVF | IF_OUTER_OVF)) return;  // the fallback wrote the CSR
     if (offsets[n] > nnzcap) {
         if (i == 0 && lane == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
         return;
@@ -954,11 +961,11 @@ k_csr(int64_t n, Batch B, const double4_32a* __restrict__ posh,
       const int2* __restrict__ cells, const unsigned long long* __restrict__ cell_hmax,
       int32_t* __restrict__ rowlen, int32_t* __restrict__ ngather,
       const int64_t* __restrict__ offsets, int32_t* __restrict__ idx, int64_t nnzcap,
-      unsigned* __restrict__ status) {
+      unsigned* __restrict__ status, unsigned mask) {
     __shared__ int s_start[kThreads / 32][32], s_pref[kThreads / 32][32];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    if (!(status[2] & IF_SLAB_OVF)) return;  // the slab path built the list
+    if (!(status[2] & mask)) return;  // the slab path built the list
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (FILL && offsets[n] > nnzcap) {
         if (gw == 0 && lane == 0) atomicOr(&status[0], (unsigned)ST_CAPACITY);
@@ -1053,13 +1060,31 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
     k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(B, posh, c->fpos, c->cells, c->nnb,
                                                        c->ngather, c->rslab, c->hs_lo, c->hs_hi,
                                                        c->hs_it, c->wl, c->status);
-    k_finalize_h<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ocnt);
+    k_finalize_h<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ocnt, c->xpk);
     const unsigned gx = (unsigned)std::max(2, kReduceBlocks / c->ninst);
     k_cell_hmax<<<dim3(gx, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->grid, c->cells, posh,
                                                                   c->cell_hmax);
 }
 
-void launch_csr(sph_ctx* c, cudaStream_t s) {
+// The two-pass CSR build, for the rows flagged in status[2] & mask (launched
+// every step; without the flag its kernels return at once).
+static void csr_fallback(sph_ctx* c, cudaStream_t s, unsigned mask) {
+    const int64_t n = c->n;
+    double4_32a* posh = c->posh[c->cur];
+    const Batch B = batch_of(c);
+    c->launches += 5;  // two build passes and the three kernels of the scan
+    k_csr<false><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->cells,
+                                                        c->cell_hmax, c->rowlen, c->ngather,
+                                                        nullptr, nullptr, c->nnzcap, c->status,
+                                                        mask);
+    launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s);
+    k_csr<true><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->cells,
+                                                       c->cell_hmax, c->rowlen, c->ngather,
+                                                       c->offsets, c->idx, c->nnzcap, c->status,
+                                                       mask);
+}
+
+void launch_csr(sph_ctx* c, cudaStream_t s, bool outer_later) {
     const int64_t n = c->n;
     c->csr_ready = false;
     if (n == 0) {
@@ -1071,18 +1096,27 @@ void launch_csr(sph_ctx* c, cudaStream_t s) {
     const unsigned nbw = (unsigned)((n * 32 + kThreads - 1) / kThreads);
     double4_32a* posh = c->posh[c->cur];
     const Batch B = batch_of(c);
-    c->launches += 6;
-    k_outer<<<nbw, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ngather, c->rslab, c->ocnt,
-                                     c->status);
-    k_rowlen_sort<<<nb, kThreads, 0, s>>>(n, c->ngather, c->ocnt, c->rowlen, c->rslab, c->status);
+    if (!outer_later) {
+        c->launches += 2;
+        k_outer<<<nbw, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ngather, c->rslab,
+                                         c->ocnt, c->status);
+        k_rowlen_sort<<<nb, kThreads, 0, s>>>(n, c->ngather, c->ocnt, c->rowlen, c->rslab,
+                                              c->status, (unsigned)IF_SLAB_OVF);
+    }
     // fallback (a row did not fit its slab): the full two-pass build into the CSR
-    k_csr<false><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->cells,
-                                                        c->cell_hmax, c->rowlen, c->ngather,
-                                                        nullptr, nullptr, c->nnzcap, c->status);
-    launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s);
-    k_csr<true><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->cells,
-                                                       c->cell_hmax, c->rowlen, c->ngather,
-                                                       c->offsets, c->idx, c->nnzcap, c->status);
+    csr_fallback(c, s, (unsigned)IF_SLAB_OVF);
+}
+
+// After a density kernel that appended the outer parts: sort them, and build
+// the CSR instead if one of them overflowed its slab.
+void launch_rows_finish(sph_ctx* c, cudaStream_t s) {
+    const int64_t n = c->n;
+    if (n == 0) return;
+    const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    c->launches += 1;
+    k_rowlen_sort<<<nb, kThreads, 0, s>>>(n, c->ngather, c->ocnt, c->rowlen, c->rslab, c->status,
+                                          (unsigned)(IF_SLAB_OVF | IF_OUTER_OVF));
+    csr_fallback(c, s, (unsigned)IF_OUTER_OVF);
 }
 
 void launch_compose(sph_ctx* c, cudaStream_t s) {

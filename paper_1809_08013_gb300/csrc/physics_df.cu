@@ -173,13 +173,22 @@ __device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, d
 // ------------------------------------------------------------ density
 // T lanes per particle: lane s of particle i takes row entries s, s + T, ...
 // KER: the M4 spline, the Wendland C2 or the sinc kernel.
-template <bool FUSE, int T, int KER>
+// OUTER: the kernel also completes the rows of S_i. For each j of N_i it
+// decides whether i is in N_j -- r_ij^2 < (2 h_j)^2 by the defining FP64
+// test -- and, if not, appends i to the outer part of row j (atomic slot;
+// the parts are sorted afterwards). The pair's double-float r^2 is within
+// ~2^-45 of the defining FP64 value and (2 h_j)^2 is packed as a float
+// (within 2^-24), so r^2 below / above it by more than 2^-20 decides; the
+// band between takes the FP64 test itself. The sets are the exact ones, as
+// built by k_outer.
+template <bool FUSE, int T, int KER, bool OUTER>
 __global__ void __launch_bounds__(kThreads)
 k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const float4* __restrict__ xpk, const double* __restrict__ ue,
              Rows R, double4_32a* __restrict__ therm,
              double2* __restrict__ kern, float4* __restrict__ dpk, double* __restrict__ pint,
-             double* __restrict__ cint, unsigned* status) {
+             double* __restrict__ cint, unsigned* status, int32_t* __restrict__ rslab,
+             int32_t* __restrict__ ocnt) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
     const int sub = (int)(threadIdx.x % T);
     const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
@@ -200,6 +209,8 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     const float hlz = g.hlzc, L2 = g.lzc[0], L1 = g.lzc[1], L0 = g.lzc[2];
     const float4 I0 = xpk[3 * i], I1 = xpk[3 * i + 1], I2 = xpk[3 * i + 2];
     if (sub == 0) acc = df{I0.w, I1.w};  // self term m_i W(0, h_i): shape 1
+    // rows read from the CSR (a gather set overflowed) are complete already
+    const bool append = OUTER && !(R.status[2] & IF_SLAB_OVF);
     for (int e = sub; e < len; e += T) {
         const int j = __ldg(&ent[e]);
         const float4 J0 = __ldg(&xpk[3 * j]), J1 = __ldg(&xpk[3 * j + 1]);
@@ -217,6 +228,24 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             w = w_shape_k<KER>(q, sn);
         }
         acc = dfl::add(acc, dfl::mul(mj, w));
+        if (append) {
+            const float tj = J2.w;  // (2 h_j)^2 in the length unit (NaN: exact test only)
+            bool in_j;
+            if (r2.hi < tj * 0.99999905f) {
+                in_j = true;
+            } else if (r2.hi > tj * 1.00000095f) {
+                in_j = false;
+            } else {
+                const double4_32a pj = posh[j];
+                const double Rj = 2.0 * pj.w;
+                in_j = exact_r2_def(pi, pj, per, kp.lz) < __dmul_rn(Rj, Rj);
+            }
+            if (!in_j) {  // i joins the outer part of row j, after j's gather set
+                const int q = __ldg(&R.ngather[j]) + atomicAdd(&ocnt[j], 1);
+                if (q < kRSlab) rslab[(int64_t)j * kRSlab + q] = (int32_t)i;
+                else atomicOr(&status[2], (unsigned)IF_OUTER_OVF);
+            }
+        }
     }
     }
     if (T > 1) {
@@ -243,40 +272,38 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     }
 }
 
-template <bool FUSE, int T>
+template <bool FUSE, int T, bool OUTER>
 static void density_df_t(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
-    if (c->kern_kind == KER_WENDLAND)
-        k_density_df<FUSE, T, KER_WENDLAND><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
-            c->pint, c->cint, c->status);
-    else if (c->kern_kind == KER_SINC)
-        k_density_df<FUSE, T, KER_SINC><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
-            c->pint, c->cint, c->status);
-    else
-        k_density_df<FUSE, T, KER_M4><<<nb, kThreads, 0, s>>>(
-            n, batch_of(c), c->posh[b], c->xpk, c->ue[b], rows_of(c), c->therm, c->kern, c->dpk,
-            c->pint, c->cint, c->status);
+    const Rows R = OUTER ? rows_gather(c) : rows_of(c);
+    auto go = [&](auto kernel_fn) {
+        kernel_fn<<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->xpk, c->ue[b], R,
+                                          c->therm, c->kern, c->dpk, c->pint, c->cint, c->status,
+                                          c->rslab, c->ocnt);
+    };
+    if (c->kern_kind == KER_WENDLAND) go(k_density_df<FUSE, T, KER_WENDLAND, OUTER>);
+    else if (c->kern_kind == KER_SINC) go(k_density_df<FUSE, T, KER_SINC, OUTER>);
+    else go(k_density_df<FUSE, T, KER_M4, OUTER>);
 }
 
-template <bool FUSE>
+template <bool FUSE, bool OUTER>
 static void density_df_f(sph_ctx* c, cudaStream_t s) {
     switch (c->tpp) {
-        case 2: density_df_t<FUSE, 2>(c, s); break;
-        case 4: density_df_t<FUSE, 4>(c, s); break;
-        case 8: density_df_t<FUSE, 8>(c, s); break;
-        default: density_df_t<FUSE, 1>(c, s); break;
+        case 2: density_df_t<FUSE, 2, OUTER>(c, s); break;
+        case 4: density_df_t<FUSE, 4, OUTER>(c, s); break;
+        case 8: density_df_t<FUSE, 8, OUTER>(c, s); break;
+        default: density_df_t<FUSE, 1, OUTER>(c, s); break;
     }
 }
 
-void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
+void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s, bool outer) {
     if (c->n == 0) return;
     c->launches += 1;
-    if (fuse_eos) density_df_f<true>(c, s);
-    else density_df_f<false>(c, s);
+    if (fuse_eos && outer) density_df_f<true, true>(c, s);
+    else if (fuse_eos) density_df_f<true, false>(c, s);
+    else density_df_f<false, false>(c, s);
 }
 
 // ------------------------------------------------------------ forces + dt

@@ -299,10 +299,16 @@ void launch_step(sph_ctx* c, double* dt, double* time, cudaStream_t s) {
     mark(c, SPH_PHASE_CELLS, s);
     launch_h_search(c, s);
     mark(c, SPH_PHASE_HSEARCH, s);
-    launch_csr(c, s);
+    // at precision 0 the density kernel completes the rows (outer parts)
+    const bool fo = fused_outer(c);
+    launch_csr(c, s, fo);
     mark(c, SPH_PHASE_CSR, s);
-    launch_density(c, true, s);
+    launch_density(c, true, s, fo);
     mark(c, SPH_PHASE_DENSITY, s);
+    if (fo) {
+        launch_rows_finish(c, s);
+        mark(c, SPH_PHASE_CSR, s);
+    }
     launch_forces(c, dt, time, s);
     mark(c, SPH_PHASE_FORCES, s);
     launch_leapfrog(c, dt, s);

@@ -40,6 +40,8 @@ enum : unsigned {
 // internal flags (status[2], cleared at every build)
 enum : unsigned {
     IF_SLAB_OVF = 1u,   // a row did not fit the gather/outer slabs: full CSR kernels run
+    IF_OUTER_OVF = 2u,  // an outer part overflowed while the density kernel appended it:
+                        // the CSR kernels run after the density, before the forces
 };
 constexpr int kGSlab = 128;  // gather-set slots per particle (>= n_target + n_tol)
 constexpr int kRec = 256;    // h search: candidates recorded per lane in flight
@@ -274,11 +276,26 @@ struct Rows {
     const int32_t* ngather;  // |N_i|: the first ngather[i] entries of a row
     const unsigned* status;
     int64_t nnzcap;
+    unsigned mask;           // internal flags that send the reads to the CSR
 };
 
+// Rows of S_i once complete (either overflow flag selects the CSR).
 inline Rows rows_of(const sph_ctx* c) {
-    return Rows{c->rslab, c->idx, c->offsets, c->rowlen, c->ngather, c->status, c->nnzcap};
+    return Rows{c->rslab, c->idx, c->offsets, c->rowlen, c->ngather, c->status, c->nnzcap,
+                (unsigned)(IF_SLAB_OVF | IF_OUTER_OVF)};
 }
+
+// Gather parts only, for the density kernel that completes the outer parts
+// itself: an outer overflow raised while it runs must not switch its reads.
+inline Rows rows_gather(const sph_ctx* c) {
+    Rows r = rows_of(c);
+    r.mask = IF_SLAB_OVF;
+    return r;
+}
+
+// At precision 0 the step's density kernel also builds the outer parts of
+// the rows (k_density_df with OUTER); elsewhere k_outer does, before it.
+inline bool fused_outer(const sph_ctx* c) { return c->prec == PREC_FP64; }
 
 // The defining FP64 squared distance, operation by operation (minimum image
 // along z when periodic): (dx dx + dy dy) + dz dz, each operation rounded.
@@ -298,7 +315,7 @@ __device__ __forceinline__ double exact_r2_def(const double4_32a& a, const doubl
 // the rows cannot be read (a fallback CSR over capacity).
 __device__ __forceinline__ bool row_of(const Rows& R, int64_t n, int64_t i, bool gather_only,
                                        const int32_t*& ent, int& len) {
-    if (!(R.status[2] & IF_SLAB_OVF)) {
+    if (!(R.status[2] & R.mask)) {
         ent = R.rslab + i * kRSlab;
     } else {
         if (R.offsets[n] > R.nnzcap) return false;
@@ -322,16 +339,19 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s);
 
 // ---- neighbors.cu
 void launch_h_search(sph_ctx* c, cudaStream_t s);
-// the rows of S_i (slab form; the full two-pass CSR build if a row overflows)
-void launch_csr(sph_ctx* c, cudaStream_t s);
+// the rows of S_i (slab form; the full two-pass CSR build if a row overflows);
+// with outer_later the outer parts are left to the density kernel, and
+// launch_rows_finish completes the rows after it
+void launch_csr(sph_ctx* c, cudaStream_t s, bool outer_later = false);
+void launch_rows_finish(sph_ctx* c, cudaStream_t s);
 // the rows as a CSR in offsets / idx (a copy in slab form; nothing after a fallback)
 void launch_compose(sph_ctx* c, cudaStream_t s);
 
 // ---- physics.cu
 enum { GATHER_DENSITY = 1, GATHER_FORCES = 2 };
-void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s);
+void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s, bool outer = false);
 // ---- physics_df.cu (precision 0)
-void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s);
+void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s, bool outer = false);
 void launch_forces_df(sph_ctx* c, cudaStream_t s);
 void launch_forces_iad_df(sph_ctx* c, cudaStream_t s);  // IAD: volumes, matrices, forces
 // ---- physics_mixed.cu (precision 1)

@@ -389,3 +389,43 @@ def test_coincident_particles(B, orc, precision, var):
     ctx.sync()
     check({k: force_err(k, host(arr[k]), o[k], o, prm.periodic_z) for k in FORCES}, TOL_FP64)
     assert np.all(np.isfinite(host(arr["ax"])))
+
+
+def _dense_core():
+    """A 16^3 lattice with a dense core of 300 particles at its centre: the
+    lattice particles around the core count many core particles among their
+    neighbours, while the core particles (small h) count few of them, so some
+    rows of S_i are longer than the 224-entry row slab (225 here)."""
+    a, p = ics.square_patch(16, seed=3)
+    p.periodic_z = 0
+    rng = np.random.Generator(np.random.PCG64(1))
+    core = {k: np.zeros(300) for k in ics.FIELDS}
+    core["x"], core["y"], core["z"] = (rng.uniform(-0.01, 0.01, 300) for _ in range(3))
+    core["m"][:] = a["m"][0]
+    core["h"][:] = 0.002
+    s = {k: np.concatenate([a[k], core[k]]) for k in ics.FIELDS}
+    return ics.random_velocities(s, seed=4, scale=1.0), p
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_long_rows_from_the_step(B, orc, precision):
+    # at precision 0 the step's density kernel appends the outer parts itself;
+    # a row that overflows its slab must send the forces to the CSR built after it
+    s, prm = _dense_core()
+    prm.precision = precision
+    o = orc.pipeline(prm, s)
+    assert int(np.max(np.diff(o["off"]))) > 224  # the input does overflow a slab
+    st_o, ex = orc.step(prm, s, nsteps=1)
+    ctx = B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=1)
+    assert ctx.sync() == B.SPH_OK
+    assert np.array_equal(host(arr["h"]).view(np.int64), o["h"].view(np.int64))
+    off, idx, ng, order = ctx.neighbors_to_host()
+    assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
+    per = prm.periodic_z
+    err = {k: normwise(host(arr[k]), ex[k]) for k in ("rho", "p", "c")}
+    err.update({k: force_err(k, host(arr[k]), ex[k], o, per) for k in FORCES})
+    err.update({k: state_err(k, host(arr[k]), st_o[k], o, per, ex["dt"])
+                for k in ("x", "y", "z", "vx", "vy", "vz", "u")})
+    check(err, TOL_FP64)
