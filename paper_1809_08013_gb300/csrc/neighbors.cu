@@ -907,6 +907,31 @@ k_outer(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     }
 }
 
+// After the precision 0 density kernel (k_density_df with OUTER): i joins the
+// outer part of row j for every gather entry e of row i whose bit is set in
+// omask (i is not in N_j). One thread per row; the rows' gather parts are
+// only read and their outer parts only written, so nothing overlaps.
+__global__ void __launch_bounds__(kThreads)
+k_append_outer(int64_t n, Batch B, const unsigned long long* __restrict__ omask,
+               const int32_t* __restrict__ ngather, int32_t* __restrict__ rslab,
+               int32_t* __restrict__ ocnt, unsigned* __restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (status[2] & IF_SLAB_OVF)) return;  // the CSR holds the whole rows
+    const int inst = slot_inst(B, i);
+    if (!slot_real(B, inst, i)) return;
+    for (int w = 0; w < 2; ++w) {
+        unsigned long long m = omask[2 * i + w];
+        while (m) {
+            const int e = 64 * w + __ffsll((long long)m) - 1;
+            m &= m - 1ull;
+            const int32_t j = rslab[i * kRSlab + e];
+            const int q = __ldg(&ngather[j]) + atomicAdd(&ocnt[j], 1);
+            if (q < kRSlab) rslab[(int64_t)j * kRSlab + q] = (int32_t)i;
+            else atomicOr(&status[2], (unsigned)IF_OUTER_OVF);
+        }
+    }
+}
+
 // Row lengths, and the outer part of each row (appended in atomic order)
 // sorted by index in place, one thread per row (rows hold a few outer
 // entries): the rows, and every sum over them, become deterministic.
@@ -1107,13 +1132,15 @@ void launch_csr(sph_ctx* c, cudaStream_t s, bool outer_later) {
     csr_fallback(c, s, (unsigned)IF_SLAB_OVF);
 }
 
-// After a density kernel that appended the outer parts: sort them, and build
-// the CSR instead if one of them overflowed its slab.
+// After a density kernel that recorded the outer entries: append and sort
+// them, and build the CSR instead if one of them overflowed its slab.
 void launch_rows_finish(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     if (n == 0) return;
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
-    c->launches += 1;
+    c->launches += 2;
+    k_append_outer<<<nb, kThreads, 0, s>>>(n, batch_of(c), c->omask, c->ngather, c->rslab,
+                                           c->ocnt, c->status);
     k_rowlen_sort<<<nb, kThreads, 0, s>>>(n, c->ngather, c->ocnt, c->rowlen, c->rslab, c->status,
                                           (unsigned)(IF_SLAB_OVF | IF_OUTER_OVF));
     csr_fallback(c, s, (unsigned)IF_OUTER_OVF);

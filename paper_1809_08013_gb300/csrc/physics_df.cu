@@ -173,22 +173,22 @@ __device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, d
 // ------------------------------------------------------------ density
 // T lanes per particle: lane s of particle i takes row entries s, s + T, ...
 // KER: the M4 spline, the Wendland C2 or the sinc kernel.
-// OUTER: the kernel also completes the rows of S_i. For each j of N_i it
-// decides whether i is in N_j -- r_ij^2 < (2 h_j)^2 by the defining FP64
-// test -- and, if not, appends i to the outer part of row j (atomic slot;
-// the parts are sorted afterwards). The pair's double-float r^2 is within
-// ~2^-45 of the defining FP64 value and (2 h_j)^2 is packed as a float
-// (within 2^-24), so r^2 below / above it by more than 2^-20 decides; the
-// band between takes the FP64 test itself. The sets are the exact ones, as
-// built by k_outer.
+// OUTER: the kernel also decides, for each j of N_i, whether i is in N_j --
+// r_ij^2 < (2 h_j)^2 by the defining FP64 test -- and records the entries
+// where it is not as bits of omask (bit e for gather entry e of row i);
+// k_append_outer then appends those i to the outer parts of the rows j. The
+// pair's double-float r^2 is within ~2^-45 of the defining FP64 value and
+// (2 h_j)^2 is packed as a float (within 2^-24), so r^2 below / above it by
+// more than 2^-20 decides; the band between takes the FP64 test itself. The
+// sets are the exact ones, as built by k_outer.
 template <bool FUSE, int T, int KER, bool OUTER>
 __global__ void __launch_bounds__(kThreads)
 k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const float4* __restrict__ xpk, const double* __restrict__ ue,
              Rows R, double4_32a* __restrict__ therm,
              double2* __restrict__ kern, float4* __restrict__ dpk, double* __restrict__ pint,
-             double* __restrict__ cint, unsigned* status, int32_t* __restrict__ rslab,
-             int32_t* __restrict__ ocnt) {
+             double* __restrict__ cint, unsigned* status,
+             unsigned long long* __restrict__ omask) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
     const int sub = (int)(threadIdx.x % T);
     const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
@@ -199,6 +199,7 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     const KParams& kp = B.kp[inst];
     double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 1.0);
     df acc = {0.0f, 0.0f};
+    unsigned long long om0 = 0ull, om1 = 0ull;  // OUTER: bits of the gather entries
     if (act) {
     pi = posh[i];
     const Grid& g = B.grid[inst];
@@ -240,17 +241,28 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
                 const double Rj = 2.0 * pj.w;
                 in_j = exact_r2_def(pi, pj, per, kp.lz) < __dmul_rn(Rj, Rj);
             }
-            if (!in_j) {  // i joins the outer part of row j, after j's gather set
-                const int q = __ldg(&R.ngather[j]) + atomicAdd(&ocnt[j], 1);
-                if (q < kRSlab) rslab[(int64_t)j * kRSlab + q] = (int32_t)i;
-                else atomicOr(&status[2], (unsigned)IF_OUTER_OVF);
+            if (!in_j) {  // i belongs in the outer part of row j
+                if (e < 64) om0 |= 1ull << e;
+                else om1 |= 1ull << (e - 64);
             }
         }
     }
     }
     if (T > 1) {
         acc = dfl::lane_sum<T>(acc);
+        if (OUTER) {
+#pragma unroll
+            for (int o = 1; o < T; o <<= 1) {
+                om0 |= __shfl_xor_sync(0xffffffffu, om0, o);
+                om1 |= __shfl_xor_sync(0xffffffffu, om1, o);
+            }
+        }
         if (!act || sub != 0) return;
+    }
+    if (OUTER && !act) return;
+    if (OUTER) {
+        omask[2 * i] = om0;
+        omask[2 * i + 1] = om1;
     }
     const Grid& g = B.grid[inst];
     const double hinv = 1.0 / pi.w;
@@ -281,7 +293,7 @@ static void density_df_t(sph_ctx* c, cudaStream_t s) {
     auto go = [&](auto kernel_fn) {
         kernel_fn<<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->xpk, c->ue[b], R,
                                           c->therm, c->kern, c->dpk, c->pint, c->cint, c->status,
-                                          c->rslab, c->ocnt);
+                                          c->omask);
     };
     if (c->kern_kind == KER_WENDLAND) go(k_density_df<FUSE, T, KER_WENDLAND, OUTER>);
     else if (c->kern_kind == KER_SINC) go(k_density_df<FUSE, T, KER_SINC, OUTER>);

@@ -116,7 +116,7 @@ void free_all(sph_ctx* c) {
                     c->therm, c->kern, c->acc, c->pint, c->cint, c->dpk, c->mpk, c->mumax, c->fpos, c->tin, c->order[0],
                     c->order[1], c->keys[0], c->keys[1], c->vals[0], c->vals[1], c->hist,
                     c->hist_part, c->cells, c->cell_hmax, c->nnb, c->ngather, c->rowlen,
-                    c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
+                    c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->omask, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
                     c->tune_dt, c->roff, c->wctr, c->recs, c->iad_a, c->iad_b, c->vol, c->xpk, c->vpa, c->vpb,
                     c->stage, c->stage_nnb, c->vdf, c->cpk};
@@ -197,7 +197,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->ioff, (size_t)max_instances + 1) && al(&c->icnt, (size_t)max_instances) &&
          al(&c->coff, (size_t)max_instances + 1) && al(&c->kpi, (size_t)max_instances) &&
          al(&c->roff, (size_t)max_instances + 1) &&
-         al(&c->rslab, N * kRSlab) && al(&c->ocnt, N) &&
+         al(&c->rslab, N * kRSlab) && al(&c->ocnt, N) && al(&c->omask, 2 * N) &&
          al(&c->hs_lo, N) && al(&c->hs_hi, N) && al(&c->hs_it, N) && al(&c->wl, N) &&
          al(&c->scratch_scalar, 2) && al(&c->tune_dt, 2 * (size_t)max_instances) &&
          al(&c->wctr, 4) &&

@@ -219,6 +219,9 @@ struct sph_ctx {
                             // r < 2 h_j only, sorted); rowlen[i] = ngather[i] + ocnt[i]
     bool csr_ready;         // offsets / idx hold the rows as a CSR
     int32_t* ocnt;          // outer-set sizes
+    unsigned long long* omask;  // 2 per particle: bit e set when gather entry e of row i
+                                // is a j with i not in N_j (the density kernel's
+                                // record for the outer parts of precision 0)
     double *hs_lo, *hs_hi;  // bisection bracket of particles handed to the per-particle search
     int32_t* hs_it;         // counts already done for them
     int32_t* wl;            // their indices (count in status[3])
