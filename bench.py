@@ -87,7 +87,23 @@ FLOPS_PAIR_TABLE = 75
 # launch, and the share of cycles with an instruction issued. Each entry is
 # used only while the kernel's sources hash to the captured version (sha1 of
 # the files listed, in order); otherwise the bench reports null.
-NCU_EVIDENCE = {}
+NCU_EVIDENCE = {
+    # k_forces_df<2, M4>, the 1M patch, second step of the timed call
+    "df": {"sources": ("physics_df.cu", "df.cuh"), "sha1": "e063ee94a704ce3325525b197e19f8c797befef7",
+           "dram_bytes": (697.38 + 44.54) * 1e6, "warp_inst": 1751439991,
+           "issue_active": 71.65, "pairs": 100727656,
+           "profile": "profiles/forces_patch1m_evrard1m.md"},
+    # k_forces_mx<2>, the 1M Evrard sphere, mixed precision
+    "mixed": {"sources": ("physics_mixed.cu", "df.cuh"), "sha1": "62a1cff61fe2b67223df985bfc8f6152db92922e",
+              "dram_bytes": (650.83 + 38.13) * 1e6, "warp_inst": 583622306,
+              "issue_active": 47.52, "pairs": 105700202,
+              "profile": "profiles/forces_patch1m_evrard1m.md"},
+    # k_forces<M4>, the 1M patch, native FP64 pair sums
+    "fp64": {"sources": ("physics.cu",), "sha1": "e1c18ffb358bfc857d1d8256d7a10aee2bc36ffd",
+             "dram_bytes": (654.58 + 37.76) * 1e6, "warp_inst": 1248076044,
+             "issue_active": 7.48, "pairs": 100727656,
+             "profile": "profiles/forces_patch1m_evrard1m.md"},
+}
 
 
 def ncu_evidence(kind):
