@@ -182,7 +182,7 @@ k_density(int64_t n, Batch B, const double4_32a* __restrict__ posh,
 void launch_density(sph_ctx* c, bool fuse_eos, cudaStream_t s, bool outer) {
     if (c->prec == PREC_MIXED) {
         launch_pack_mx(c, false, s);
-        launch_density_mx(c, fuse_eos, s);
+        launch_density_mx(c, fuse_eos, s, outer);
         return;
     }
     if (!native_pairs(c)) {

@@ -172,12 +172,18 @@ k_pack_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
 }
 
 // T lanes per particle: lane s of particle i takes row entries s, s + T, ...
-template <bool FUSE, int T>
+// OUTER: as k_density_df, the kernel also records in omask the gather entries
+// j of row i with i not in N_j. The FP32 relative coordinates put r^2 within
+// ~2^-21 of the defining FP64 value and 1/h_j is packed as a float, so
+// r^2 / h_j^2 below / above 4 by more than 2^-18 decides; the band between,
+// and a periodic axis shorter than 8 h_j, take the FP64 test itself.
+template <bool FUSE, int T, bool OUTER>
 __global__ void __launch_bounds__(kThreads)
 k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
              const double* __restrict__ ue, float4* __restrict__ mpk,
              Rows R, double4_32a* __restrict__ therm,
-             double* __restrict__ pint, double* __restrict__ cint, unsigned* status) {
+             double* __restrict__ pint, double* __restrict__ cint, unsigned* status,
+             unsigned long long* __restrict__ omask) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
     const int sub = (int)(threadIdx.x % T);
     const int inst = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
@@ -187,11 +193,14 @@ k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     if (T == 1 && !act) return;
     const KParams& kp = B.kp[inst];
     df acc = {0.0f, 0.0f};
+    unsigned long long om0 = 0ull, om1 = 0ull;  // OUTER: bits of the gather entries
     if (act) {
     const float4 a0 = mpk[5 * i], a1 = mpk[5 * i + 1];
     const float hinv = a1.w;
     const ZWrap zw = make_zwrap(kp, B.grid[inst]);
     if (sub == 0) acc = df{a0.w, 0.0f};  // self term m_i W(0, h_i): shape 1
+    // rows read from the CSR (a gather set overflowed) are complete already
+    const bool append = OUTER && !(R.status[2] & IF_SLAB_OVF);
     for (int e = sub; e < len; e += T) {
         const int j = __ldg(&ent[e]);
         const float4 b0 = __ldg(&mpk[5 * j]), b1 = __ldg(&mpk[5 * j + 1]);
@@ -200,11 +209,39 @@ k_density_mx(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float q = r2 > 0.0f ? r2 * rsqrt_f(r2) * hinv : 0.0f;
         acc = dfl::addf(acc, b0.w * w_shape_f(q));
+        if (append) {
+            const float t = r2 * b1.w * b1.w;  // (r / h_j)^2
+            bool in_j;
+            if (!(zw.per && b1.w * zw.lzh < 8.0f) && t < 4.0f * 0.99999619f) {
+                in_j = true;
+            } else if (!(zw.per && b1.w * zw.lzh < 8.0f) && t > 4.0f * 1.00000381f) {
+                in_j = false;
+            } else {
+                const double4_32a pj = posh[j];
+                const double Rj = 2.0 * pj.w;
+                in_j = exact_r2_def(posh[i], pj, zw.per, kp.lz) < __dmul_rn(Rj, Rj);
+            }
+            if (!in_j) {  // i belongs in the outer part of row j
+                if (e < 64) om0 |= 1ull << e;
+                else om1 |= 1ull << (e - 64);
+            }
+        }
     }
     }
     if (T > 1) {
         acc = dfl::lane_sum<T>(acc);
+        if (OUTER) {
+#pragma unroll
+            for (int o = 1; o < T; o <<= 1) {
+                om0 |= __shfl_xor_sync(0xffffffffu, om0, o);
+                om1 |= __shfl_xor_sync(0xffffffffu, om1, o);
+            }
+        }
         if (!act || sub != 0) return;
+    }
+    if (OUTER) {
+        omask[2 * i] = om0;
+        omask[2 * i + 1] = om1;
     }
     const Grid& g = B.grid[inst];
     const double hd = posh[i].w;
@@ -333,31 +370,32 @@ void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s) {
                                                  c->mpk, c->status);
 }
 
-template <bool FUSE, int T>
+template <bool FUSE, int T, bool OUTER>
 static void density_mx_t(sph_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     const unsigned nb = (unsigned)((n * T + kThreads - 1) / kThreads);
     const int b = c->cur;
-    k_density_mx<FUSE, T><<<nb, kThreads, 0, s>>>(n, batch_of(c), c->posh[b], c->ue[b], c->mpk,
-                                                  rows_of(c),
-                                                  c->therm, c->pint, c->cint, c->status);
+    k_density_mx<FUSE, T, OUTER><<<nb, kThreads, 0, s>>>(
+        n, batch_of(c), c->posh[b], c->ue[b], c->mpk, OUTER ? rows_gather(c) : rows_of(c),
+        c->therm, c->pint, c->cint, c->status, c->omask);
 }
 
-template <bool FUSE>
+template <bool FUSE, bool OUTER>
 static void density_mx_f(sph_ctx* c, cudaStream_t s) {
     switch (c->tpp) {
-        case 2: density_mx_t<FUSE, 2>(c, s); break;
-        case 4: density_mx_t<FUSE, 4>(c, s); break;
-        case 8: density_mx_t<FUSE, 8>(c, s); break;
-        default: density_mx_t<FUSE, 1>(c, s); break;
+        case 2: density_mx_t<FUSE, 2, OUTER>(c, s); break;
+        case 4: density_mx_t<FUSE, 4, OUTER>(c, s); break;
+        case 8: density_mx_t<FUSE, 8, OUTER>(c, s); break;
+        default: density_mx_t<FUSE, 1, OUTER>(c, s); break;
     }
 }
 
-void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s) {
+void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s, bool outer) {
     if (c->n == 0) return;
     c->launches += 1;
-    if (fuse_eos) density_mx_f<true>(c, s);
-    else density_mx_f<false>(c, s);
+    if (fuse_eos && outer) density_mx_f<true, true>(c, s);
+    else if (fuse_eos) density_mx_f<true, false>(c, s);
+    else density_mx_f<false, false>(c, s);
 }
 
 template <int T>

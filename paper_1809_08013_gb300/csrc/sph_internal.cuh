@@ -45,7 +45,7 @@ enum : unsigned {
 };
 constexpr int kGSlab = 128;  // gather-set slots per particle (>= n_target + n_tol)
 constexpr int kRec = 256;    // h search: candidates recorded per lane in flight
-constexpr int kUnionBlocksPerSM = 2;  // resident blocks of the persistent h search
+constexpr int kUnionBlocksPerSM = 3;  // resident blocks of the persistent h search
 constexpr int kRSlab = 224;  // row slots per particle: gather set, then the outer set
                              // (outer sets: patch max ~40, Evrard ~64)
 
@@ -296,9 +296,10 @@ inline Rows rows_gather(const sph_ctx* c) {
     return r;
 }
 
-// At precision 0 the step's density kernel also builds the outer parts of
-// the rows (k_density_df with OUTER); elsewhere k_outer does, before it.
-inline bool fused_outer(const sph_ctx* c) { return c->prec == PREC_FP64; }
+// At precision 0 and 1 the step's density kernel also decides the outer parts
+// of the rows (k_density_df / k_density_mx with OUTER, then k_append_outer);
+// at precision 2 and outside a step, k_outer builds them before the density.
+inline bool fused_outer(const sph_ctx* c) { return c->prec == PREC_FP64 || c->prec == PREC_MIXED; }
 
 // The defining FP64 squared distance, operation by operation (minimum image
 // along z when periodic): (dx dx + dy dy) + dz dz, each operation rounded.
@@ -359,7 +360,7 @@ void launch_forces_df(sph_ctx* c, cudaStream_t s);
 void launch_forces_iad_df(sph_ctx* c, cudaStream_t s);  // IAD: volumes, matrices, forces
 // ---- physics_mixed.cu (precision 1)
 void launch_pack_mx(sph_ctx* c, bool thermo, cudaStream_t s);
-void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s);
+void launch_density_mx(sph_ctx* c, bool fuse_eos, cudaStream_t s, bool outer = false);
 void launch_forces_mx(sph_ctx* c, cudaStream_t s);
 void launch_eos_caller(const KParams& kp, const sph_particles* P, cudaStream_t s);
 // forces, then per instance dt[k] = cfl min_i (...) and time[k] += dt[k]
