@@ -919,14 +919,33 @@ k_append_outer(int64_t n, Batch B, const unsigned long long* __restrict__ omask,
     if (i >= n || (status[2] & IF_SLAB_OVF)) return;  // the CSR holds the whole rows
     const int inst = slot_inst(B, i);
     if (!slot_real(B, inst, i)) return;
-    for (int w = 0; w < 2; ++w) {
-        unsigned long long m = omask[2 * i + w];
-        while (m) {
-            const int e = 64 * w + __ffsll((long long)m) - 1;
-            m &= m - 1ull;
-            const int32_t j = rslab[i * kRSlab + e];
-            const int q = __ldg(&ngather[j]) + atomicAdd(&ocnt[j], 1);
-            if (q < kRSlab) rslab[(int64_t)j * kRSlab + q] = (int32_t)i;
+    // up to four appends in flight per thread: their loads, then their atomic
+    // slots, then their stores (each append is a chain of three memory steps)
+    constexpr int kBatch = 4;
+    const int32_t* row = rslab + i * kRSlab;
+    unsigned long long m0 = omask[2 * i], m1 = omask[2 * i + 1];
+    while (m0 | m1) {
+        int e[kBatch], j[kBatch], q[kBatch];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            e[b] = -1;
+            if (m0) {
+                e[b] = __ffsll((long long)m0) - 1;
+                m0 &= m0 - 1ull;
+            } else if (m1) {
+                e[b] = 64 + __ffsll((long long)m1) - 1;
+                m1 &= m1 - 1ull;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) j[b] = e[b] >= 0 ? row[e[b]] : 0;
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b)
+            q[b] = e[b] >= 0 ? __ldg(&ngather[j[b]]) + atomicAdd(&ocnt[j[b]], 1) : 0;
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            if (e[b] < 0) continue;
+            if (q[b] < kRSlab) rslab[(int64_t)j[b] * kRSlab + q[b]] = (int32_t)i;
             else atomicOr(&status[2], (unsigned)IF_OUTER_OVF);
         }
     }
@@ -1102,7 +1121,7 @@ static void csr_fallback(sph_ctx* c, cudaStream_t s, unsigned mask) {
                                                         c->cell_hmax, c->rowlen, c->ngather,
                                                         nullptr, nullptr, c->nnzcap, c->status,
                                                         mask);
-    launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s);
+    launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s, c->status + 2, mask);
     k_csr<true><<<kReduceBlocks * 4, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->cells,
                                                        c->cell_hmax, c->rowlen, c->ngather,
                                                        c->offsets, c->idx, c->nnzcap, c->status,
@@ -1151,7 +1170,9 @@ void launch_compose(sph_ctx* c, cudaStream_t s) {
     c->csr_ready = true;
     if (n == 0) return;
     const unsigned nbw = (unsigned)((n * 32 + kThreads - 1) / kThreads);
-    c->launches += 1;
+    c->launches += 4;
+    // row offsets of the slab rows (the steps scan them only for the fallback)
+    launch_scan_i32_i64(c->rowlen, n, c->offsets, c->row_part, s);
     k_compose<<<nbw, kThreads, 0, s>>>(n, c->rowlen, c->rslab, c->offsets, c->idx, c->nnzcap,
                                        c->status);
 }

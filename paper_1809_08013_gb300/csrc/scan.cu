@@ -37,9 +37,17 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total) {
     return r;
 }
 
+// gate / mask: when gate is given, the kernels do nothing unless *gate & mask
+// (a device flag decides whether the scan is needed; the launches stay fixed).
+__device__ __forceinline__ bool gated_off(const unsigned* gate, unsigned mask) {
+    return gate && !(*(volatile const unsigned*)gate & mask);
+}
+
 template <typename In, typename Acc>
 __global__ void __launch_bounds__(kThreads) k_scan_reduce(const In* __restrict__ in, int64_t n,
-                                                          Acc* __restrict__ part) {
+                                                          Acc* __restrict__ part,
+                                                          const unsigned* gate, unsigned mask) {
+    if (gated_off(gate, mask)) return;
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * 8;
     Acc s = 0;
 #pragma unroll
@@ -52,7 +60,9 @@ __global__ void __launch_bounds__(kThreads) k_scan_reduce(const In* __restrict__
 
 // Single block, exclusive scan in place over np partials.
 template <typename Acc>
-__global__ void __launch_bounds__(kThreads) k_scan_partials(Acc* part, int64_t np) {
+__global__ void __launch_bounds__(kThreads) k_scan_partials(Acc* part, int64_t np,
+                                                            const unsigned* gate, unsigned mask) {
+    if (gated_off(gate, mask)) return;
     const int64_t per = (np + kThreads - 1) / kThreads;
     const int64_t b = (int64_t)threadIdx.x * per;
     Acc s = 0;
@@ -71,7 +81,9 @@ __global__ void __launch_bounds__(kThreads) k_scan_partials(Acc* part, int64_t n
 template <typename In, typename Out>
 __global__ void __launch_bounds__(kThreads) k_scan_apply(const In* in, int64_t n,
                                                          const Out* __restrict__ part, Out* out,
-                                                         int write_total) {
+                                                         int write_total, const unsigned* gate,
+                                                         unsigned mask) {
+    if (gated_off(gate, mask)) return;
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * 8;
     Out v[8];
     Out s = 0;
@@ -93,23 +105,25 @@ __global__ void __launch_bounds__(kThreads) k_scan_apply(const In* in, int64_t n
 }
 
 void launch_scan_i32_i64(const int32_t* in, int64_t n, int64_t* out, int64_t* part,
-                         cudaStream_t s) {
+                         cudaStream_t s, const unsigned* gate, unsigned mask) {
     if (n <= 0) {
         cudaMemsetAsync(out, 0, sizeof(int64_t), s);
         return;
     }
     const int64_t np = scan_parts(n);
-    k_scan_reduce<int32_t, int64_t><<<(unsigned)np, kThreads, 0, s>>>(in, n, part);
-    k_scan_partials<int64_t><<<1, kThreads, 0, s>>>(part, np);
-    k_scan_apply<int32_t, int64_t><<<(unsigned)np, kThreads, 0, s>>>(in, n, part, out, 1);
+    k_scan_reduce<int32_t, int64_t><<<(unsigned)np, kThreads, 0, s>>>(in, n, part, gate, mask);
+    k_scan_partials<int64_t><<<1, kThreads, 0, s>>>(part, np, gate, mask);
+    k_scan_apply<int32_t, int64_t><<<(unsigned)np, kThreads, 0, s>>>(in, n, part, out, 1, gate,
+                                                                      mask);
 }
 
 void launch_scan_u32(uint32_t* data, int64_t n, uint32_t* part, cudaStream_t s) {
     if (n <= 0) return;
     const int64_t np = scan_parts(n);
-    k_scan_reduce<uint32_t, uint32_t><<<(unsigned)np, kThreads, 0, s>>>(data, n, part);
-    k_scan_partials<uint32_t><<<1, kThreads, 0, s>>>(part, np);
-    k_scan_apply<uint32_t, uint32_t><<<(unsigned)np, kThreads, 0, s>>>(data, n, part, data, 0);
+    k_scan_reduce<uint32_t, uint32_t><<<(unsigned)np, kThreads, 0, s>>>(data, n, part, nullptr, 0u);
+    k_scan_partials<uint32_t><<<1, kThreads, 0, s>>>(part, np, nullptr, 0u);
+    k_scan_apply<uint32_t, uint32_t><<<(unsigned)np, kThreads, 0, s>>>(data, n, part, data, 0,
+                                                                        nullptr, 0u);
 }
 
 }  // namespace sph

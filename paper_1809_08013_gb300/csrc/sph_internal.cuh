@@ -375,9 +375,10 @@ enum : unsigned {
 };
 
 // ---- scan.cu
-// exclusive scan of n int32 into n+1 int64 (out[n] = total)
+// exclusive scan of n int32 into n+1 int64 (out[n] = total); with gate, only
+// when *gate & mask is set on the device when the kernels run
 void launch_scan_i32_i64(const int32_t* in, int64_t n, int64_t* out, int64_t* part,
-                         cudaStream_t s);
+                         cudaStream_t s, const unsigned* gate = nullptr, unsigned mask = 0u);
 // exclusive scan in place over n uint32
 void launch_scan_u32(uint32_t* data, int64_t n, uint32_t* part, cudaStream_t s);
 int64_t scan_parts(int64_t n);
