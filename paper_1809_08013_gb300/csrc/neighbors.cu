@@ -402,164 +402,13 @@ __device__ int count_records(const int2* recb, int nrec, double hh, const Grid* 
     return c;
 }
 
-// min / max over the 8 lanes of a lane's group (lanes 8s .. 8s + 7)
-__device__ __forceinline__ float gmin8(float v) {
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-__device__ __forceinline__ float gmax8(float v) {
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-
-constexpr int kGroups = 4;          // groups of 8 lanes in the first counting pass
-constexpr int kGStride = 65;        // slots per group stream (64 + 1 against bank conflicts)
-
-// Shared memory of the first counting pass, per warp.
-struct GroupStage {
-    float4 st[kGroups][kGStride];   // staged candidates (float x, y, z) per group
-    int si[kGroups][kGStride];      // their particle indices
-    float4 ball[kGroups];           // group centre and squared radius
-};
-
-// The first counting pass of the h search (N_i at the current h) for the
-// warp's 32 lanes, taken as four groups of 8 Morton-consecutive lanes. Each
-// group has its own ball (centre of its active lanes' bounding box, radius =
-// largest distance of one of them from it + its reach + the slop), so a
-// candidate within reach of a lane is in its group's ball. One walk over the
-// cells of the warp's box loads each cell's particles once; every candidate
-// is appended to the stream of each group whose ball holds it (ballot
-// compaction, order kept). When a stream holds 32, all four streams are
-// tested in lock-step, each lane against its own group's 32 (union_chunk,
-// the same FP32 / exact FP64 decisions as every count), shorter streams
-// padded with far-away slots. A lane thus tests the candidates near its own
-// group (~half of those near the whole warp), and its gather set comes out in
-// the order of the walk, as in the single-cluster pass.
-__device__ __forceinline__ void grouped_first_pass(
-    const Grid* __restrict__ g, const int2* __restrict__ cells, const float4* __restrict__ fpos,
-    GroupStage& gs, const float4& fi, bool active, float Rq, const Thr& t, int64_t i, double h,
-    double& R2, const double4_32a* posh, int32_t* slab, int& c) {
-    const int lane = threadIdx.x & 31;
-    const int grp = lane >> 3;
-    const unsigned lt = (1u << lane) - 1u;
-    const bool per = g->periodic_z != 0;
-    // group balls
-    const float cx = 0.5f * (gmin8(active ? fi.x : CUDART_INF_F) + gmax8(active ? fi.x : -CUDART_INF_F));
-    const float cy = 0.5f * (gmin8(active ? fi.y : CUDART_INF_F) + gmax8(active ? fi.y : -CUDART_INF_F));
-    const float cz = 0.5f * (gmin8(active ? fi.z : CUDART_INF_F) + gmax8(active ? fi.z : -CUDART_INF_F));
-    float rl = 0.0f;
-    if (active) {
-        const float ex = fi.x - cx, ey = fi.y - cy, ez = fi.z - cz;
-        rl = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex))) + Rq;
-    }
-    const float rb = gmax8(rl) * 1.00001f + fmaxf(g->slop[0], fmaxf(g->slop[1], g->slop[2]));
-    if ((lane & 7) == 0) gs.ball[grp] = make_float4(cx, cy, cz, rb * rb);  // NaN: no active lane
-    // the warp's box: the cells the walk visits
-    const float lx = wmin(active ? fi.x - Rq : CUDART_INF_F), hx = wmax(active ? fi.x + Rq : -CUDART_INF_F);
-    const float ly = wmin(active ? fi.y - Rq : CUDART_INF_F), hy = wmax(active ? fi.y + Rq : -CUDART_INF_F);
-    const float lz = wmin(active ? fi.z - Rq : CUDART_INF_F), hz = wmax(active ? fi.z + Rq : -CUDART_INF_F);
-    const int a0 = __ffs(__ballot_sync(kFull, active)) - 1;
-    const float zc = __shfl_sync(kFull, fi.z, a0 < 0 ? 0 : a0);  // periodic image reference
-    __syncwarp();
-    if (!(lx <= hx)) return;  // no active lane
-    int x0, x1, y0, y1, z0, z1;
-    box_range(lx, hx, g, 0, x0, x1);
-    box_range(ly, hy, g, 1, y0, y1);
-    box_range(lz, hz, g, 2, z0, z1);
-    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-    const float Rq2 = Rq * Rq;
-    int fill[kGroups] = {0, 0, 0, 0};
-    int dummy = 0;
-    auto test_round = [&]() {  // all four streams: slots 0..31, then shift the rest down
-#pragma unroll
-        for (int s = 0; s < kGroups; ++s)
-            if (lane >= fill[s]) {
-                gs.st[s][lane] = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
-                gs.si[s][lane] = -1;
-            }
-        __syncwarp();
-        union_chunk(gs.st[grp], gs.si[grp], fi, t, active, false, -1.0f, i, h, R2, posh, g, slab,
-                    c, nullptr, dummy);
-        __syncwarp();
-#pragma unroll
-        for (int s = 0; s < kGroups; ++s) {
-            const bool mv = 32 + lane < fill[s];
-            float4 v;
-            int vi = 0;
-            if (mv) {
-                v = gs.st[s][32 + lane];
-                vi = gs.si[s][32 + lane];
-            }
-            __syncwarp();
-            if (mv) {
-                gs.st[s][lane] = v;
-                gs.si[s][lane] = vi;
-            }
-            fill[s] = fill[s] > 32 ? fill[s] - 32 : 0;
-        }
-        __syncwarp();
-    };
-    for (int kz = z0; kz <= z1; ++kz) {
-        const int czi = per ? wrapi(kz, nz) : kz;
-        const float gz = per ? 0.0f : axis_gap(fi.z, kz, g, 2);
-        for (int ky = y0; ky <= y1; ++ky) {
-            const long long row = ((long long)czi * ny + ky) * nx;
-            const float gy = axis_gap(fi.y, ky, g, 1);
-            for (int kx = x0; kx <= x1; ++kx) {
-                const int2 se = __ldg(&cells[row + kx]);
-                if (se.y <= se.x) continue;
-                const float gx = axis_gap(fi.x, kx, g, 0);
-                if (!__any_sync(kFull, active && fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < Rq2)) continue;
-                for (int s0 = se.x; s0 < se.y; s0 += 32) {
-                    const int j = s0 + lane;
-                    const bool ok = j < se.y;
-                    float4 f = make_float4(3.0e30f, 3.0e30f, 3.0e30f, 0.0f);
-                    if (ok) {
-                        f = __ldg(&fpos[j]);
-                        if (per) {
-                            const float d = f.z - zc;
-                            if (d > g->halflzf) f.z -= g->lzf;
-                            else if (d < -g->halflzf) f.z += g->lzf;
-                        }
-                    }
-                    int most = 0;
-#pragma unroll
-                    for (int s = 0; s < kGroups; ++s) {
-                        const float4 b = gs.ball[s];
-                        const float qx = f.x - b.x, qy = f.y - b.y, qz = f.z - b.z;
-                        const bool in = ok && fmaf(qz, qz, fmaf(qy, qy, qx * qx)) <= b.w;
-                        const unsigned m = __ballot_sync(kFull, in);
-                        if (in) {
-                            const int q = fill[s] + __popc(m & lt);
-                            gs.st[s][q] = f;
-                            gs.si[s][q] = j;
-                        }
-                        fill[s] += __popc(m);
-                        most = max(most, fill[s]);
-                    }
-                    if (most >= 32) {
-                        __syncwarp();
-                        test_round();
-                    }
-                }
-            }
-        }
-    }
-    while (max(max(fill[0], fill[1]), max(fill[2], fill[3])) > 0) {
-        __syncwarp();
-        test_round();
-    }
-}
-
 // The 32 particles i0 .. i0 + 31 (one per lane; all of one instance).
 __device__ __forceinline__ void union_group(
     int64_t i0, int64_t n, const Batch& B, double4_32a* posh, const float4* __restrict__ fpos,
     const int2* __restrict__ cells, int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
     int32_t* __restrict__ rslab, double* __restrict__ hs_lo, double* __restrict__ hs_hi,
     int32_t* __restrict__ hs_it, int32_t* __restrict__ wl, unsigned* __restrict__ status,
-    float4* st, int* sidx, int2* recb, GroupStage& gstage) {
+    float4* st, int* sidx, int2* recb) {
     const int lane = threadIdx.x & 31;
     const int64_t i = i0 + lane;
     const int inst = slot_inst(B, i0);
@@ -619,9 +468,7 @@ __device__ __forceinline__ void union_group(
         const int mcz = lane_cell(fi.z, g, 2);
         double R2 = -1.0;
         int c = 0, nrec = 0;
-        unsigned todo = rec ? am : 0u;
-        if (!rec)
-            grouped_first_pass(g, cells, fpos, gstage, fi, active, Rq, t, i, h, R2, posh, slab, c);
+        unsigned todo = am;
         while (todo) {
             const int a = __ffs(todo) - 1;
             const int ax = __shfl_sync(kFull, mcx, a), ay = __shfl_sync(kFull, mcy, a);
@@ -793,7 +640,6 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
           unsigned long long* __restrict__ wctr, int2* __restrict__ recs) {
     __shared__ float4 s_f[kThreads / 32][32];
     __shared__ int s_i[kThreads / 32][32];
-    __shared__ GroupStage s_g[kThreads / 32];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const long long ngroups = (n + 31) / 32;
@@ -804,8 +650,7 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
         if (gi >= ngroups) break;
         union_group(gi * 32, n, B, posh, fpos, cells, nnb, ngather, rslab, hs_lo, hs_hi, hs_it,
                     wl, status, s_f[warp], s_i[warp],
-                    recs + ((int64_t)(blockIdx.x * (kThreads / 32) + warp) * 32 + lane) * kRec,
-                    s_g[warp]);
+                    recs + ((int64_t)(blockIdx.x * (kThreads / 32) + warp) * 32 + lane) * kRec);
     }
 }
 
