@@ -156,11 +156,11 @@ __device__ __forceinline__ void wrap_fx(float& z2, float& z1, float& z0, float h
 
 __device__ __forceinline__ void eos_d(const KParams& kp, double rho, double u, double& p, double& c) {
     if (kp.eos == 0) {
-        const double x = rho / kp.rho0;
+        const double x = rho * kp.inv_rho0;  // within an ulp of rho / rho0
         const double x2 = x * x;
         const double x4 = x2 * x2;
         const double x7 = (x4 * x2) * x;
-        p = (kp.c0 * kp.c0 * kp.rho0 / 7.0) * (x7 - 1.0);
+        p = kp.tait_k * (x7 - 1.0);
         c = kp.c0 * (x2 * x);
     } else {
         p = (kp.gamma - 1.0) * rho * u;
@@ -272,9 +272,8 @@ k_density_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         double p, c;
         eos_d(kp, rho, ue[i], p, c);
         const double A = p / (rho * rho);
+        // (the FP64-pipe kernels' kern pack is not needed at this precision)
         therm[i] = make_double4_32a(0.5 * rho, A, 0.5 * kp.alpha * c, 0.5 * pi.w);
-        const double h2 = hinv * hinv;
-        kern[i] = make_double2(hinv, h2 * h2);
         dfl::write_pack(dpk, i, hinv, A, pi.w, rho, kp.alpha, c, dfl::pair_units(g.uL, g.uM, g.uV),
                         status, ST_RANGE);
         pint[i] = p;

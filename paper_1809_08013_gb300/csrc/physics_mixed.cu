@@ -106,11 +106,11 @@ __device__ __forceinline__ float dw_shape_f(float q) {
 
 __device__ __forceinline__ void eos_m(const KParams& kp, double rho, double u, double& p, double& c) {
     if (kp.eos == 0) {
-        const double x = rho / kp.rho0;
+        const double x = rho * kp.inv_rho0;  // within an ulp of rho / rho0
         const double x2 = x * x;
         const double x4 = x2 * x2;
         const double x7 = (x4 * x2) * x;
-        p = (kp.c0 * kp.c0 * kp.rho0 / 7.0) * (x7 - 1.0);
+        p = kp.tait_k * (x7 - 1.0);
         c = kp.c0 * (x2 * x);
     } else {
         p = (kp.gamma - 1.0) * rho * u;
@@ -130,7 +130,7 @@ __device__ __forceinline__ void pack_thermo(float4* __restrict__ mpk, int64_t k,
     const double Au = A * U.A;
     const double ru = 0.5 * rho * U.rho;
     const double cu = 0.5 * alpha * c * U.V;
-    if (!dfl::pack_in_range(hu, ru, Au, cu)) atomicOr(status, (unsigned)ST_RANGE);
+    if (!dfl::pack_in_range(hu, 2.0 * ru, Au, 2.0 * cu)) atomicOr(status, (unsigned)ST_RANGE);
     mpk[5 * k + 2].w = (float)(h2 * h2);
     mpk[5 * k + 3].w = (float)Au;
     mpk[5 * k + 4] = make_float4((float)(0.5 * h * U.L), (float)ru, (float)cu, 0.0f);

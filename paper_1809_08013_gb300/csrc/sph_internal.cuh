@@ -97,6 +97,7 @@ struct KParams {
     int kernel, gradients, sinc_n;
     double rho0, c0, gamma, alpha, beta, eta2, cfl, lz, cell_scale;
     double wnorm, dnorm;
+    double inv_rho0, tait_k;  // 1 / rho0 and c0^2 rho0 / 7, for the per-particle EOS
 };
 
 enum { KER_M4 = 0, KER_WENDLAND = 1, KER_SINC = 2 };
@@ -152,6 +153,8 @@ inline KParams kparams(const sph_params* p) {
     k.kernel = p->kernel;
     k.gradients = p->gradients;
     k.sinc_n = p->sinc_n;
+    k.inv_rho0 = p->rho0 != 0.0 ? 1.0 / p->rho0 : 0.0;
+    k.tait_k = p->c0 * p->c0 * p->rho0 / 7.0;
     if (p->kernel == KER_WENDLAND) {
         k.wnorm = 21.0 / (16.0 * kPi);
         k.dnorm = 105.0 / (16.0 * kPi);
