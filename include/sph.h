@@ -64,8 +64,8 @@ typedef enum {
  * change the results; in those units every quantity a pair term needs is
  * O(1). The step reports SPH_E_RANGE (through sph_sync) when, in them, some
  * particle has 1/h outside [2^-15, 2^15] (h more than 2^15 away from the
- * mean h of its instance), rho outside [2^-60, 2^60], or |p/rho^2| or alpha c
- * above 2^60, or when
+ * mean h of its instance), rho outside [2^-60, 2^60], alpha c above 2^60 or
+ * |p/rho^2| above 2^64, or when
  * the coordinates span more than about 2^120 smoothing lengths: input
  * outside what float-pair arithmetic can hold at FP64 accuracy. Use
  * precision 2 for such input. */

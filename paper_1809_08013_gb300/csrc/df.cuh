@@ -242,10 +242,11 @@ __host__ __device__ __forceinline__ PairUnits pair_units(int uL, int uM, int uV)
 // range with ample room (no product of pair terms overflows, and the low
 // parts of the terms that carry the sums stay normal): h within 2^15 of the
 // instance's mean h (so 1/h^4 stays within 2^+-60); rho in [2^-60, 2^60];
-// |p/rho^2| and alpha c below 2^60.
+// alpha c below 2^60; |p/rho^2| below 2^64 (a stiff equation of state far
+// from rho0 makes it the quantity with the widest range).
 __device__ __forceinline__ bool pack_in_range(double hinv_u, double rho_u, double A_u, double ac_u) {
     return hinv_u >= 0x1p-15 && hinv_u <= 0x1p15 && rho_u >= 0x1p-60 && rho_u <= 0x1p60 &&
-           fabs(A_u) <= 0x1p60 && ac_u <= 0x1p60;
+           fabs(A_u) <= 0x1p64 && ac_u <= 0x1p60;
 }
 
 // Per-particle pack of the double-float force kernel (48 B per particle), in
@@ -253,8 +254,8 @@ __device__ __forceinline__ bool pack_in_range(double hinv_u, double rho_u, doubl
 //   dpk[3k] = (1/h, 1/h^4), dpk[3k+1] = (p/rho^2, h/2), dpk[3k+2] = (rho/2, alpha c/2).
 // A particle outside pack_in_range sets `range_bit` in *status. The float
 // pairs are split with integer operations (from_double: within 2^-47 of each
-// value, no FP64 pipe); in range, every value lies in [2^-60, 2^60] or is
-// negligibly small (p/rho^2 near p = 0 may round to 0).
+// value, no FP64 pipe), which in range hold every value but p/rho^2; that one
+// is split on the FP64 pipe (from_double_fp64), which holds any float.
 __device__ __forceinline__ void write_pack(float4* __restrict__ dpk, int64_t k, double hinv,
                                            double A, double h, double rho, double alpha, double c,
                                            const PairUnits& U, unsigned* status,
@@ -266,7 +267,7 @@ __device__ __forceinline__ void write_pack(float4* __restrict__ dpk, int64_t k, 
     const double cu = (alpha * c) * (0.5 * U.V);
     if (!pack_in_range(hu, 2.0 * ru, Au, 2.0 * cu)) atomicOr(status, range_bit);
     const df a = from_double(hu), b = from_double(h2 * h2);
-    const df cA = from_double(Au), d = from_double(h * (0.5 * U.L));
+    const df cA = from_double_fp64(Au), d = from_double(h * (0.5 * U.L));
     const df e = from_double(ru), f = from_double(cu);
     dpk[3 * k + 0] = make_float4(a.hi, a.lo, b.hi, b.lo);
     dpk[3 * k + 1] = make_float4(cA.hi, cA.lo, d.hi, d.lo);
