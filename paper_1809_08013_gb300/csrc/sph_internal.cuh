@@ -45,7 +45,7 @@ enum : unsigned {
 };
 constexpr int kGSlab = 128;  // gather-set slots per particle (>= n_target + n_tol)
 constexpr int kRec = 256;    // h search: candidates recorded per lane in flight
-constexpr int kUnionBlocksPerSM = 3;  // resident blocks of the persistent h search
+constexpr int kUnionBlocksPerSM = 4;  // resident blocks of the persistent h search
 constexpr int kRSlab = 224;  // row slots per particle: gather set, then the outer set
                              // (outer sets: patch max ~40, Evrard ~64)
 
