@@ -226,12 +226,13 @@ sph_status sph_step(sph_ctx *ctx, const sph_params *prm, sph_particles *P, int n
                     void *stream);
 
 /* sph_step on HOST arrays: the same nsteps iterations, with every pointer of
- * P a host pointer (pinned memory lets the copies run asynchronously; any
- * host memory works). On the stream it copies x, y, z, vx, vy, vz, m, h, u
- * and *time to device staging buffers owned by the context, runs the steps,
- * and copies back x..u, *time, *dt and each of rho, p, c, ax, ay, az, du,
- * mumax, nnb that is not NULL (only the state fields and time, dt are
- * required). The staging (17 doubles and one int32 per particle of capacity)
+ * P a host pointer (any host memory works). The state x, y, z, vx, vy, vz, m,
+ * h, u is read at the start and written back at the end, with *time, *dt and
+ * each of rho, p, c, ax, ay, az, du, mumax, nnb that is not NULL (only the
+ * state fields and time, dt are required). An array in page-locked (pinned)
+ * or registered host memory is read and written in place by the call's first
+ * and last kernels, over the link to host memory; any other array is copied
+ * on the stream to device staging buffers owned by the context and back. The staging (17 doubles and one int32 per particle of capacity)
  * is allocated by the first call (SPH_E_NOMEM if that fails) and freed with
  * the context; sph_ctx_bytes does not include it. Asynchronous like
  * sph_step: the host arrays hold the results after sph_sync (or a stream

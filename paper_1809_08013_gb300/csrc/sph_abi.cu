@@ -670,6 +670,20 @@ sph_status sph_step(sph_ctx* c, const sph_params* prm, sph_particles* P, int nst
     return check_launch(c, "sph_step");
 }
 
+// The device address of a host array the GPU can reach in place (page-locked
+// or registered host memory, or managed memory), else NULL (pageable memory,
+// or nothing known about the pointer).
+static void* device_view(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged) ? a.devicePointer
+                                                                              : nullptr;
+}
+
 sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, int nsteps,
                          void* stream) {
     if (!c) return SPH_E_INVAL;
@@ -696,7 +710,10 @@ sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, in
             return SPH_E_NOMEM;
         }
     }
-    // device view: the state fields first (in/out), then the outputs
+    // device view: the state fields first (in/out), then the outputs. An array
+    // the GPU can reach in place (pinned host memory) is read by the first and
+    // written by the last kernel of the call directly, over the host link; any
+    // other is copied through the context's staging buffer.
     double* sg = c->stage;
     double** hf[17] = {&H->x, &H->y, &H->z, &H->vx, &H->vy, &H->vz, &H->m, &H->h, &H->u,
                        &H->rho, &H->p, &H->c, &H->ax, &H->ay, &H->az, &H->du, &H->mumax};
@@ -705,16 +722,22 @@ sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, in
     D.n = n;
     double** df[17] = {&D.x, &D.y, &D.z, &D.vx, &D.vy, &D.vz, &D.m, &D.h, &D.u,
                        &D.rho, &D.p, &D.c, &D.ax, &D.ay, &D.az, &D.du, &D.mumax};
-    for (int f = 0; f < 17; ++f) *df[f] = sg + (size_t)f * N;
+    bool direct[17];
+    for (int f = 0; f < 17; ++f) {
+        void* dv = n > 0 ? device_view(*hf[f]) : nullptr;
+        direct[f] = dv != nullptr;
+        *df[f] = direct[f] ? (double*)dv : sg + (size_t)f * N;
+    }
     if (!H->mumax) D.mumax = nullptr;
-    D.nnb = H->nnb ? c->stage_nnb : nullptr;
+    void* nnb_dv = n > 0 ? device_view(H->nnb) : nullptr;
+    D.nnb = H->nnb ? (nnb_dv ? (int32_t*)nnb_dv : c->stage_nnb) : nullptr;
     D.time = sg + 17 * N;
     D.dt = sg + 17 * N + 1;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = (size_t)n * sizeof(double);
     cudaError_t e = cudaSuccess;
     for (int f = 0; f < 9 && e == cudaSuccess && n > 0; ++f)
-        e = cudaMemcpyAsync(*df[f], *hf[f], bytes, cudaMemcpyHostToDevice, s);
+        if (!direct[f]) e = cudaMemcpyAsync(*df[f], *hf[f], bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.time, H->time, sizeof(double), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -724,8 +747,8 @@ sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, in
     launch_set_single(c, kparams(prm), n, s);
     run_steps(c, &D, nsteps, s);
     for (int f = 0; f < 17 && e == cudaSuccess && n > 0; ++f)
-        if (*hf[f]) e = cudaMemcpyAsync(*hf[f], *df[f], bytes, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && H->nnb && n > 0)
+        if (*hf[f] && !direct[f]) e = cudaMemcpyAsync(*hf[f], *df[f], bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && H->nnb && !nnb_dv && n > 0)
         e = cudaMemcpyAsync(H->nnb, D.nnb, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(H->time, D.time, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(H->dt, D.dt, sizeof(double), cudaMemcpyDeviceToHost, s);

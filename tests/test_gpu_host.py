@@ -107,3 +107,18 @@ def test_step_host_zero_steps_and_invalid(B):
     with pytest.raises(B.SphError) as e:
         ctx.step_host(prm, big, nsteps=1)
     assert e.value.status == B.SPH_E_INVAL
+
+
+def test_step_host_mixed_pinned_and_pageable(B):
+    # pinned arrays are read and written in place by the kernels, pageable ones
+    # go through the staging copies: any mix gives the bits of the device step
+    s, prm = _case("patch")
+    ref = _device_run(B, s, prm, 2)
+    ctx = B.Context(len(s["x"]))
+    h = _host_arrays(s, pinned=False)
+    for k in ("x", "vy", "h", "rho", "az"):
+        h[k] = torch.from_numpy(h[k].copy()).pin_memory()
+    ctx.step_host(prm, h, nsteps=2)
+    assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
+    for k in FIELDS + OUTS + ("nnb", "time", "dt"):
+        assert np.array_equal(_np(h[k]).view(np.uint8), ref[k].view(np.uint8)), k
