@@ -371,14 +371,16 @@ bool step_graph(sph_ctx* c, double* dt, double* time, cudaStream_t s) {
     return true;
 }
 
-// nsteps steps of the current batch: the caller's arrays are read into the
-// slot layout, and the final state is written back after the last step.
+// nsteps steps of the current batch: the caller's arrays (those of `in` when
+// given, else P's) are read into the slot layout, and the final state is
+// written back to P's after the last step.
 // Each step replays the step graph of its parity, unless per-phase timing is
 // on (events between the phases) or the stream is being captured already
 // (the caller is recording the launches into a graph of its own).
-void run_steps(sph_ctx* c, sph_particles* P, int nsteps, cudaStream_t s) {
+void run_steps(sph_ctx* c, sph_particles* P, int nsteps, cudaStream_t s,
+               const sph_particles* in = nullptr) {
     mark(c, -1, s);
-    launch_load_state(c, P, s);
+    launch_load_state(c, in ? in : P, s);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
         cudaGetLastError();
@@ -393,6 +395,56 @@ void run_steps(sph_ctx* c, sph_particles* P, int nsteps, cudaStream_t s) {
         mark(c, SPH_PHASE_UPDATE, s);
         if (c->timing) c->timed_steps += 1;
     }
+}
+
+// Device buffers out to host memory that the GPU reaches in place
+// (blockIdx.y = buffer). Every buffer is an array of doubles or int32: 16-byte
+// loads and stores where both ends are 16-byte aligned, else 4-byte words.
+// Four loads go out before their stores, so each thread keeps several
+// transfers over the host link in flight.
+constexpr int kHostCopyMax = 20;
+struct HostCopy {
+    const void* src[kHostCopyMax];
+    void* dst[kHostCopyMax];
+    int64_t bytes[kHostCopyMax];
+};
+
+template <typename T>
+__device__ __forceinline__ void copy_strided(const T* __restrict__ s, T* __restrict__ d, int64_t n,
+                                             int64_t t, int64_t st) {
+    int64_t i = t;
+    for (; i + 3 * st < n; i += 4 * st) {
+        const T a = s[i], b = s[i + st], e = s[i + 2 * st], f = s[i + 3 * st];
+        d[i] = a;
+        d[i + st] = b;
+        d[i + 2 * st] = e;
+        d[i + 3 * st] = f;
+    }
+    for (; i < n; i += st) d[i] = s[i];
+}
+
+__global__ void __launch_bounds__(kThreads) k_to_host(HostCopy C) {
+    const int f = blockIdx.y;
+    const char* s = (const char*)C.src[f];
+    char* d = (char*)C.dst[f];
+    const int64_t nb = C.bytes[f];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    int64_t done = 0;
+    if ((((uintptr_t)s | (uintptr_t)d) & 15) == 0) {
+        done = nb & ~(int64_t)15;
+        copy_strided((const int4*)s, (int4*)d, done >> 4, t, st);
+    }
+    copy_strided((const int32_t*)(s + done), (int32_t*)(d + done), (nb - done) >> 2, t, st);
+}
+
+void launch_to_host(sph_ctx* c, const HostCopy& C, int nbuf, int64_t maxbytes, cudaStream_t s) {
+    if (nbuf == 0) return;
+    const int64_t per_block = (int64_t)kThreads * 4 * 16;
+    const int64_t want = std::max<int64_t>(1, (maxbytes + per_block - 1) / per_block);
+    const int64_t cap = std::max(1, 16 * 152 / nbuf);
+    c->launches += 1;
+    k_to_host<<<dim3((unsigned)std::min(want, cap), (unsigned)nbuf), kThreads, 0, s>>>(C);
 }
 
 }  // namespace sph
@@ -710,10 +762,14 @@ sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, in
             return SPH_E_NOMEM;
         }
     }
-    // device view: the state fields first (in/out), then the outputs. An array
-    // the GPU can reach in place (pinned host memory) is read by the first and
-    // written by the last kernel of the call directly, over the host link; any
-    // other is copied through the context's staging buffer.
+    // Device view D: the staging buffer, the state fields first (in and out),
+    // then the outputs. The inputs I: a state array the GPU reaches in place
+    // (pinned host memory) is read by the call's first kernel directly, in the
+    // caller's order, over the host link; any other is copied to D's buffer
+    // first. The last step writes every output through the sort permutation
+    // into D (scattered 8-byte stores to host memory would waste most of each
+    // transfer); from there one copy kernel streams the pinned arrays out over
+    // the link, and the copy engines take the others.
     double* sg = c->stage;
     double** hf[17] = {&H->x, &H->y, &H->z, &H->vx, &H->vy, &H->vz, &H->m, &H->h, &H->u,
                        &H->rho, &H->p, &H->c, &H->ax, &H->ay, &H->az, &H->du, &H->mumax};
@@ -722,22 +778,25 @@ sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, in
     D.n = n;
     double** df[17] = {&D.x, &D.y, &D.z, &D.vx, &D.vy, &D.vz, &D.m, &D.h, &D.u,
                        &D.rho, &D.p, &D.c, &D.ax, &D.ay, &D.az, &D.du, &D.mumax};
-    bool direct[17];
+    void* view[17];
     for (int f = 0; f < 17; ++f) {
-        void* dv = n > 0 ? device_view(*hf[f]) : nullptr;
-        direct[f] = dv != nullptr;
-        *df[f] = direct[f] ? (double*)dv : sg + (size_t)f * N;
+        view[f] = n > 0 ? device_view(*hf[f]) : nullptr;
+        *df[f] = sg + (size_t)f * N;
     }
     if (!H->mumax) D.mumax = nullptr;
-    void* nnb_dv = n > 0 ? device_view(H->nnb) : nullptr;
-    D.nnb = H->nnb ? (nnb_dv ? (int32_t*)nnb_dv : c->stage_nnb) : nullptr;
+    D.nnb = H->nnb ? c->stage_nnb : nullptr;
+    void* nnb_view = n > 0 ? device_view(H->nnb) : nullptr;
     D.time = sg + 17 * N;
     D.dt = sg + 17 * N + 1;
+    sph_particles I = D;
+    double** in[9] = {&I.x, &I.y, &I.z, &I.vx, &I.vy, &I.vz, &I.m, &I.h, &I.u};
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = (size_t)n * sizeof(double);
     cudaError_t e = cudaSuccess;
-    for (int f = 0; f < 9 && e == cudaSuccess && n > 0; ++f)
-        if (!direct[f]) e = cudaMemcpyAsync(*df[f], *hf[f], bytes, cudaMemcpyHostToDevice, s);
+    for (int f = 0; f < 9 && e == cudaSuccess && n > 0; ++f) {
+        if (view[f]) *in[f] = (double*)view[f];
+        else e = cudaMemcpyAsync(*df[f], *hf[f], bytes, cudaMemcpyHostToDevice, s);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.time, H->time, sizeof(double), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -745,11 +804,29 @@ sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, in
         return SPH_E_CUDA;
     }
     launch_set_single(c, kparams(prm), n, s);
-    run_steps(c, &D, nsteps, s);
-    for (int f = 0; f < 17 && e == cudaSuccess && n > 0; ++f)
-        if (*hf[f] && !direct[f]) e = cudaMemcpyAsync(*hf[f], *df[f], bytes, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && H->nnb && !nnb_dv && n > 0)
-        e = cudaMemcpyAsync(H->nnb, D.nnb, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    run_steps(c, &D, nsteps, s, &I);
+    HostCopy hc;
+    int nhc = 0;
+    for (int f = 0; f < 17 && e == cudaSuccess && n > 0; ++f) {
+        if (!*hf[f]) continue;
+        if (view[f]) {
+            hc.src[nhc] = *df[f];
+            hc.dst[nhc] = view[f];
+            hc.bytes[nhc++] = (int64_t)bytes;
+        } else {
+            e = cudaMemcpyAsync(*hf[f], *df[f], bytes, cudaMemcpyDeviceToHost, s);
+        }
+    }
+    if (e == cudaSuccess && H->nnb && n > 0) {
+        if (nnb_view) {
+            hc.src[nhc] = D.nnb;
+            hc.dst[nhc] = nnb_view;
+            hc.bytes[nhc++] = n * (int64_t)sizeof(int32_t);
+        } else {
+            e = cudaMemcpyAsync(H->nnb, D.nnb, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        }
+    }
+    if (e == cudaSuccess) launch_to_host(c, hc, nhc, (int64_t)bytes, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(H->time, D.time, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(H->dt, D.dt, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) {

@@ -1,5 +1,6 @@
-"""sph_step_host: the step on HOST arrays through the C ABI (copies in, steps,
-copies back inside the call) gives the bits of sph_step on device arrays."""
+"""sph_step_host: the step on HOST arrays through the C ABI (pinned arrays
+read in place and written by a copy kernel, others copied through staging
+buffers, all inside the call) gives the bits of sph_step on device arrays."""
 import numpy as np
 import pytest
 
@@ -116,8 +117,13 @@ def test_step_host_mixed_pinned_and_pageable(B):
     ref = _device_run(B, s, prm, 2)
     ctx = B.Context(len(s["x"]))
     h = _host_arrays(s, pinned=False)
-    for k in ("x", "vy", "h", "rho", "az"):
+    for k in ("x", "vy", "h", "rho", "az", "nnb", "time"):
         h[k] = torch.from_numpy(h[k].copy()).pin_memory()
+    for k in ("u", "du"):  # views 8 bytes into pinned buffers: not 16-byte aligned
+        buf = torch.zeros(len(h[k]) + 1, dtype=torch.float64).pin_memory()
+        buf[1:] = torch.from_numpy(h[k])
+        h[k] = buf[1:]
+        assert h[k].data_ptr() % 16 == 8
     ctx.step_host(prm, h, nsteps=2)
     assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)
     for k in FIELDS + OUTS + ("nnb", "time", "dt"):
