@@ -48,10 +48,18 @@ typedef enum {
     SPH_E_HNOCONV = 5,   /* some particle's h search ended outside n_target +- n_tol;
                             results are still computed with its last h */
     SPH_E_TIMEOUT = 6,   /* reserved for bounded device waits */
-    SPH_E_RANGE = 7      /* precision 0 or 1: some per-particle quantity of the pair
+    SPH_E_RANGE = 7,     /* precision 0 or 1: some per-particle quantity of the pair
                             kernels lies outside the range they hold (see below); the
                             density and force outputs of the affected step are not
                             valid at their stated accuracy. Precision 2 never raises it */
+    SPH_E_NONFINITE = 8  /* a particle's state held a NaN or an infinity, or lay outside
+                            the geometry range of the neighbour search (|x|, |y|, |z| <=
+                            FLT_MAX, 0 <= h <= 2^100). The step still runs to its end
+                            without touching memory out of bounds: such a particle gets
+                            no neighbours of its own (a NaN or an infinite position also
+                            keeps it out of every other particle's sets) and is left out
+                            of the cell grid and the units; every output of its instance
+                            for that step is undefined */
 } sph_status;
 
 /* Range of the pair kernels at precision 0 (float pairs) and 1 (FP32).
@@ -344,8 +352,8 @@ sph_status sph_timing_read(sph_ctx *ctx, double *ms, int64_t *launches, int64_t 
 int64_t sph_launch_count(const sph_ctx *ctx);
 
 /* Wait for the stream, then return and clear the device status: SPH_OK, or
- * the most severe of SPH_E_CAPACITY, SPH_E_RANGE and SPH_E_HNOCONV (in that
- * order) raised since the last sph_sync. */
+ * the most severe of SPH_E_NONFINITE, SPH_E_CAPACITY, SPH_E_RANGE and
+ * SPH_E_HNOCONV (in that order) raised since the last sph_sync. */
 sph_status sph_sync(sph_ctx *ctx, void *stream);
 
 /* Number of particles whose h search did not converge since the last

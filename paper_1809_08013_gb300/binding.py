@@ -13,9 +13,10 @@ import re
 from . import build as _build
 
 (SPH_OK, SPH_E_INVAL, SPH_E_NOMEM, SPH_E_CUDA, SPH_E_CAPACITY, SPH_E_HNOCONV, SPH_E_TIMEOUT,
- SPH_E_RANGE) = range(8)
+ SPH_E_RANGE, SPH_E_NONFINITE) = range(9)
 STATUS_NAMES = {0: "SPH_OK", 1: "SPH_E_INVAL", 2: "SPH_E_NOMEM", 3: "SPH_E_CUDA",
-                4: "SPH_E_CAPACITY", 5: "SPH_E_HNOCONV", 6: "SPH_E_TIMEOUT", 7: "SPH_E_RANGE"}
+                4: "SPH_E_CAPACITY", 5: "SPH_E_HNOCONV", 6: "SPH_E_TIMEOUT", 7: "SPH_E_RANGE",
+                8: "SPH_E_NONFINITE"}
 
 PHASES = ("cells", "hsearch", "csr", "density", "forces", "update")
 STATE_FIELDS = ("x", "y", "z", "vx", "vy", "vz", "m", "h", "u")
@@ -304,9 +305,9 @@ class Context:
                                       _stream(stream)))
 
     def step_host(self, prm, arrays: dict, nsteps: int = 1, stream=None):
-        """sph_step_host: `arrays` are host arrays (see host_particles); the
-        library copies them in, steps, and copies the results back on the
-        stream (pinned memory makes the copies asynchronous)."""
+        """sph_step_host: `arrays` are host arrays (see host_particles). Pinned
+        arrays are read and written in place by the library's kernels; others
+        are copied through device staging buffers on the stream."""
         P = host_particles(arrays)
         self._check(self.lib.sph_step_host(self.h, C.byref(params(prm)), C.byref(P), int(nsteps),
                                            _stream(stream)))
@@ -352,8 +353,8 @@ class Context:
                 "trials": trials}
 
     def sync(self, stream=None) -> int:
-        """Wait for the stream; return the device status (SPH_OK, SPH_E_CAPACITY,
-        SPH_E_RANGE, SPH_E_HNOCONV) without raising."""
+        """Wait for the stream; return the device status (SPH_OK, SPH_E_NONFINITE,
+        SPH_E_CAPACITY, SPH_E_RANGE, SPH_E_HNOCONV) without raising."""
         return int(self.lib.sph_sync(self.h, _stream(stream)))
 
     def timing_enable(self, on: bool = True):

@@ -100,14 +100,22 @@ __device__ __forceinline__ int wrapi(int k, int n) {
 
 // Cell index range overlapping [v - R, v + R] along axis d (clamped); along the
 // periodic z axis an unclamped range (wrapped by the caller) or the whole axis.
+// A non-finite v or R (a particle outside the geometry range) gets no cells;
+// a periodic range far from the box (|index| >= 2^30) takes the whole axis,
+// so the callers' int loops never come near overflow.
 __device__ __forceinline__ void axis_range(float v, float R, const Grid* __restrict__ g, int d,
                                            int& k0, int& k1) {
     const float inv = g->invwf[d], s = g->slop[d];
     const int n = g->n[d];
+    if (!(fabsf(v) < CUDART_INF_F) || !(R < CUDART_INF_F)) {
+        k0 = 0;
+        k1 = -1;
+        return;
+    }
     if (d == 2 && g->periodic_z) {
         const float fa = floorf((v - R - s + g->halflzf) * inv);
         const float fb = floorf((v + R + s + g->halflzf) * inv);
-        if (!(fb - fa + 1.0f < (float)n)) {
+        if (!(fb - fa + 1.0f < (float)n) || !(fabsf(fa) < 1.0e9f && fabsf(fb) < 1.0e9f)) {
             k0 = 0;
             k1 = n - 1;
             return;
@@ -141,14 +149,20 @@ __device__ __forceinline__ float reach_f32(double h) {
 
 // Cell index range overlapping [a, b] along axis d (clamped); along the
 // periodic z axis an unclamped range (wrapped by the caller) or the whole axis.
+// Non-finite bounds and far periodic ranges as in axis_range.
 __device__ __forceinline__ void box_range(float a, float b, const Grid* __restrict__ g, int d,
                                           int& k0, int& k1) {
     const float inv = g->invwf[d], s = g->slop[d];
     const int n = g->n[d];
+    if (!(fabsf(a) < CUDART_INF_F) || !(fabsf(b) < CUDART_INF_F)) {
+        k0 = 0;
+        k1 = -1;
+        return;
+    }
     if (d == 2 && g->periodic_z) {
         const float fa = floorf((a - s + g->halflzf) * inv);
         const float fb = floorf((b + s + g->halflzf) * inv);
-        if (!(fb - fa + 1.0f < (float)n)) {
+        if (!(fb - fa + 1.0f < (float)n) || !(fabsf(fa) < 1.0e9f && fabsf(fb) < 1.0e9f)) {
             k0 = 0;
             k1 = n - 1;
             return;
@@ -175,48 +189,6 @@ __device__ __forceinline__ float wmax(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
     return v;
-}
-
-// One warp, 32 particles (one per lane): walk the cells of the union of the
-// active lanes' boxes [q - R, q + R] in warp-uniform loops, skipping a cell
-// no active lane wants (keep), staging each cell's particles 32 at a time in
-// shared memory; every lane then sees every staged candidate (visit). All
-// lanes must call this together.
-template <class Keep, class Visit>
-__device__ __forceinline__ void warp_walk(const Grid* __restrict__ g, const int2* __restrict__ cells,
-                                          const float4* __restrict__ fpos, float4* s_f,
-                                          const float4& q, float R, bool active, Keep&& keep,
-                                          Visit&& visit) {
-    const int lane = threadIdx.x & 31;
-    const float lx = wmin(active ? q.x - R : CUDART_INF_F), hx = wmax(active ? q.x + R : -CUDART_INF_F);
-    if (!(lx <= hx)) return;  // no active lane
-    const float ly = wmin(active ? q.y - R : CUDART_INF_F), hy = wmax(active ? q.y + R : -CUDART_INF_F);
-    const float lz = wmin(active ? q.z - R : CUDART_INF_F), hz = wmax(active ? q.z + R : -CUDART_INF_F);
-    int x0, x1, y0, y1, z0, z1;
-    box_range(lx, hx, g, 0, x0, x1);
-    box_range(ly, hy, g, 1, y0, y1);
-    box_range(lz, hz, g, 2, z0, z1);
-    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-    const bool per = g->periodic_z != 0;
-    for (int kz = z0; kz <= z1; ++kz) {
-        const int cz = per ? wrapi(kz, nz) : kz;
-        for (int ky = y0; ky <= y1; ++ky) {
-            const long long row = ((long long)cz * ny + ky) * nx;
-            for (int kx = x0; kx <= x1; ++kx) {
-                const int2 se = __ldg(&cells[row + kx]);
-                if (se.y <= se.x) continue;
-                if (!__any_sync(kFull, active && keep(kx, ky, kz))) continue;
-                for (int base = se.x; base < se.y; base += 32) {
-                    const int j = base + lane;
-                    if (j < se.y) s_f[lane] = __ldg(&fpos[j]);
-                    __syncwarp();
-                    const int cnt = min(32, se.y - base);
-                    for (int k = 0; k < cnt; ++k) visit(base + k, s_f[k]);
-                    __syncwarp();
-                }
-            }
-        }
-    }
 }
 
 // One warp, one particle: enumerate the candidates of every cell overlapping
@@ -423,11 +395,14 @@ __device__ __forceinline__ void union_group(
         h = posh[i].w;
         fi = fpos[i];
     }
+    // a particle outside the geometry range (reported by the bounding box)
+    // does not search: no neighbours, h unchanged
+    const bool geo = valid && isfinite(fi.x) && isfinite(fi.y) && isfinite(fi.z) && h_ok(h);
     const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
     const int max_it = kp.max_h_iter;
     const int defer = kp.defer_lanes;
     int cnt = 0, it = 0;
-    bool active = valid && max_it > 0, conv = false, deferred = false;
+    bool active = geo && max_it > 0, conv = false, deferred = false;
     int32_t* slab = rslab + (valid ? i : 0) * kRSlab;
     const bool per = g->periodic_z != 0;
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
@@ -834,7 +809,7 @@ k_cell_hmax(Batch B, Grid* gw, const int2* __restrict__ cells,
         long long m = 0;
         for (int k = se.x; k < se.y; ++k) {
             const long long b = __double_as_longlong(posh[k].w);
-            m = b > m ? b : m;
+            m = (b > m && b <= kHMaxBits) ? b : m;  // h outside the geometry range: not counted
         }
         cell_hmax[c] = (unsigned long long)m;
         bmax = m > bmax ? m : bmax;

@@ -190,7 +190,7 @@ __device__ __forceinline__ void box_warp_reduce(BoxPart& b) {
 __global__ void __launch_bounds__(kThreads)
 k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
        const double4_32a* __restrict__ velm, const double* __restrict__ ue,
-       double* __restrict__ part) {
+       double* __restrict__ part, unsigned* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (grp * kSlotAlign >= n) return;  // warp-uniform
@@ -198,11 +198,22 @@ k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     const int64_t end = __ldg(&B.ioff[inst]) + __ldg(&B.icnt[inst]);
     BoxPart b;
     box_init(b);
+    bool bad = false;
 #pragma unroll
     for (int q = 0; q < kSlotAlign / 32; ++q) {
         const int64_t k = grp * kSlotAlign + q * 32 + lane;
         if (k < end) {
+            // a particle outside the geometry range (NaN, infinity, beyond the
+            // FP32 range) is reported and kept out of the box and the means:
+            // the cells, the search and the units stay those of the others
             const double4_32a p = posh[k];
+            const double4_32a v = velm[k];
+            const double uk = ue[k];
+            const bool geo = coord_ok(p.x) && coord_ok(p.y) && coord_ok(p.z) && h_ok(p.w);
+            const bool fin = finite_bits(v.x) && finite_bits(v.y) && finite_bits(v.z) &&
+                             finite_bits(v.w) && finite_bits(uk);
+            bad |= !(geo && fin);
+            if (!(geo && fin)) continue;
             const long long kx = okey(p.x), ky = okey(p.y), kz = okey(p.z), kh = okey(p.w);
             b.mn[0] = kx < b.mn[0] ? kx : b.mn[0];
             b.mn[1] = ky < b.mn[1] ? ky : b.mn[1];
@@ -212,14 +223,14 @@ k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             b.mx[2] = kz > b.mx[2] ? kz : b.mx[2];
             b.mx[3] = kh > b.mx[3] ? kh : b.mx[3];
             b.hs += p.w;
-            const double4_32a v = velm[k];
-            const long long km = okey(v.w), ku = okey(ue[k]);
+            const long long km = okey(v.w), ku = okey(uk);
             const long long kv = okey(fmax(fabs(v.x), fmax(fabs(v.y), fabs(v.z))));
             b.mx[4] = km > b.mx[4] ? km : b.mx[4];
             b.mx[5] = kv > b.mx[5] ? kv : b.mx[5];
             b.mx[6] = ku > b.mx[6] ? ku : b.mx[6];
         }
     }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, (unsigned)ST_NONFINITE);
     box_warp_reduce(b);
     if (lane == 0) {
         double* o = part + grp * kBoxStride;
@@ -232,7 +243,7 @@ k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
 __device__ __forceinline__ int grid_count(double ext, double w, double* wout) {
     double c = floor(ext / w) + 1.0;
     if (c > (double)kMaxCellsPerAxis) c = (double)kMaxCellsPerAxis;
-    if (c < 1.0) c = 1.0;
+    if (!(c >= 1.0)) c = 1.0;  // also a NaN extent: never an empty axis
     double ww = w;
     if (c * ww <= ext) ww = ext / (c - 0.5);
     *wout = ww;
@@ -298,9 +309,8 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     const long long cellcap = g->cap;
     double mn[3] = {r[0], r[1], r[2]};
     double mx[3] = {-r[3], -r[4], -r[5]};
-    if (n == 0) {
-        for (int d = 0; d < 3; ++d) { mn[d] = 0.0; mx[d] = 0.0; }
-    }
+    for (int d = 0; d < 3; ++d)  // no particle, or none inside the geometry range
+        if (n == 0 || !(mn[d] <= mx[d])) { mn[d] = 0.0; mx[d] = 0.0; }
     if (inst == 0) {
         status[2] = 0u;
         status[3] = 0u;
@@ -414,8 +424,9 @@ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
 // any particle within reach of a query lies in a cell the query visits.
 __device__ __forceinline__ int cell_coord(double v, float lo, float inv, int n) {
     const float f = floorf((dfl::from_double(v).hi - lo) * inv);
+    const int top = n > 1 ? n - 1 : 0;
     if (!(f >= 0.0f)) return 0;  // also catches NaN
-    if (f > (float)(n - 1)) return n - 1;
+    if (f > (float)top) return top;
     return (int)f;
 }
 
@@ -580,7 +591,7 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
         c->launches += 1;
         const int64_t groups = (n + kSlotAlign - 1) / kSlotAlign;
         k_bbox<<<(unsigned)((groups * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            n, B, c->posh[c->cur], c->velm[c->cur], c->ue[c->cur], c->red_part);
+            n, B, c->posh[c->cur], c->velm[c->cur], c->ue[c->cur], c->red_part, c->status);
     }
     k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status, c->wctr);
     if (n == 0) return;

@@ -808,7 +808,7 @@ sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, in
     HostCopy hc;
     int nhc = 0;
     for (int f = 0; f < 17 && e == cudaSuccess && n > 0; ++f) {
-        if (!*hf[f]) continue;
+        if (!*hf[f] || f == 6) continue;  // m is read, never written
         if (view[f]) {
             hc.src[nhc] = *df[f];
             hc.dst[nhc] = view[f];
@@ -1013,6 +1013,11 @@ sph_status sph_sync(sph_ctx* c, void* stream) {
     }
     const unsigned bits = c->status_host[0];
     c->last_hnoconv = (int64_t)c->status_host[1];
+    if (bits & ST_NONFINITE) {
+        set_err(c, "a particle's state was non-finite or outside the geometry range "
+                   "(|x|, |y|, |z| <= FLT_MAX, 0 <= h <= 2^100)");
+        return SPH_E_NONFINITE;
+    }
     if (bits & ST_CAPACITY) {
         set_err(c, "neighbour list exceeded nnz capacity %lld", (long long)c->nnzcap);
         return SPH_E_CAPACITY;

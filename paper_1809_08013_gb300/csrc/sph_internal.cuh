@@ -36,7 +36,24 @@ enum : unsigned {
     ST_CAPACITY = 1u,   // neighbour list exceeded nnz capacity
     ST_HNOCONV = 2u,    // some h search did not converge
     ST_RANGE = 4u,      // a float-pair quantity left the range of the pair kernels
+    ST_NONFINITE = 8u,  // a particle's state was non-finite or outside the geometry range
 };
+
+// Geometry range of a particle (integer tests on the bits, no FP64 pipe): the
+// neighbour search works on FP32 coordinates and FP32 reaches, so |x|, |y|,
+// |z| <= FLT_MAX and 0 <= h <= 2^100 (false for NaN and infinities).
+constexpr long long kF32MaxBits = 0x47EFFFFFE0000000LL;  // FLT_MAX as a double
+constexpr long long kHMaxBits = 0x4630000000000000LL;    // 2^100
+__device__ __forceinline__ bool coord_ok(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) <= kF32MaxBits;
+}
+__device__ __forceinline__ bool h_ok(double h) {
+    const long long b = __double_as_longlong(h);
+    return b >= 0 && b <= kHMaxBits;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
 // internal flags (status[2], cleared at every build)
 enum : unsigned {
     IF_SLAB_OVF = 1u,   // a row did not fit the gather/outer slabs: full CSR kernels run

@@ -25,6 +25,18 @@ def test_library_exports_every_header_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_status_codes_match_header():
+    # the binding's status constants and names are the header's enum
+    import re
+    from pathlib import Path
+    hdr = (Path(__file__).resolve().parents[1] / "include" / "sph.h").read_text()
+    body = hdr[hdr.index("typedef enum {"):hdr.index("} sph_status;")]
+    enum = {int(v): k for k, v in re.findall(r"\b(SPH_[A-Z_]+)\s*=\s*(\d+)", body)}
+    assert enum == binding.STATUS_NAMES
+    for v, k in enum.items():
+        assert getattr(binding, k) == v
+
+
 def test_version_string(lib):
     assert b"sm_103a" in lib.sph_version()
 
