@@ -900,8 +900,9 @@ def measure_workload(args, B, dev, fp64_peak, fp32_peak, e2e=True, sampler=None)
 
     out["e2e"] = None
     if e2e:
-        # through the C ABI on HOST buffers (sph_step_host): every step copies
-        # the state in from pinned host memory, steps, and copies it back
+        # through the C ABI on HOST buffers (sph_step_host): every step reads
+        # the state from pinned host memory, steps, and writes it back (all
+        # but m, which the step only reads)
         ic_host = {k: torch.from_numpy(np.ascontiguousarray(s[k])) for k in B.STATE_FIELDS}
         host = {k: v.clone().pin_memory() for k, v in ic_host.items()}
         host["time"] = torch.zeros(1, dtype=torch.float64).pin_memory()
@@ -924,8 +925,9 @@ def measure_workload(args, B, dev, fp64_peak, fp32_peak, e2e=True, sampler=None)
         ctx.sync(stream)
         out["e2e"] = {"value": whole_job_rate(world, n, args.steps, ems), "unit": UNIT,
                       "h2d_bytes_per_step": 8 * len(B.STATE_FIELDS) * n + 8,
-                      "d2h_bytes_per_step": 8 * len(B.STATE_FIELDS) * n + 16,
-                      "api": "sph_step_host (C ABI, pinned host arrays; copies inside the call)"}
+                      "d2h_bytes_per_step": 8 * (len(B.STATE_FIELDS) - 1) * n + 16,
+                      "api": "sph_step_host (C ABI, pinned host arrays: read in place by the "
+                             "first kernel, results streamed back by a copy kernel)"}
     out["roofline"] = None
     if rank == 0:
         # the last step of the timed configuration again, for its neighbour list
