@@ -127,6 +127,18 @@ typedef struct {
                             G_ij = (W(r_ij, h_i) C_i + W(r_ij, h_j) C_j)(r_j - r_i) / 2
                             in place of Fbar_ij r_ij in the momentum and energy sums */
     int32_t sinc_n;      /* exponent n of the sinc kernel, 2..12 (read when kernel = 2) */
+    double list_skin;    /* h search: every particle keeps across steps the list of all
+                            particles within 2 h (1 + list_skin) of it at the last list
+                            build and counts its neighbours from that list while it still
+                            holds them all (no particle has moved far enough since); the
+                            instance rebuilds its lists when one no longer covers its
+                            particle's 2 h. 0 selects 0.15; a negative value turns the
+                            lists off (every count walks the cells); above 1:
+                            SPH_E_INVAL. Lists are kept per caller index: a batch
+                            instance whose caller range reaches past the context's
+                            capacity runs without them. A tuning knob: h and the
+                            neighbour sets do not depend on it (the order within a
+                            gather set does) */
 } sph_params;
 
 #define SPH_KERNEL_M4 0
@@ -347,6 +359,18 @@ sph_status sph_timing_enable(sph_ctx *ctx, int enable);
  * since the last read or enable; *steps receives the number of timed steps.
  * Any output pointer may be NULL. Clears the accumulators. */
 sph_status sph_timing_read(sph_ctx *ctx, double *ms, int64_t *launches, int64_t *steps);
+
+/* Forget the h search's candidate lists (sph_params.list_skin) of the
+ * particles [first, first + count) of the caller arrays, on the stream: the
+ * next step of their instance rebuilds its lists. h and the neighbour sets
+ * never depend on the lists; the order of the pair sums does, so a context
+ * carries, from one call to the next, lists that can change the last bits of
+ * the sums. Contexts with the same history of calls give the same bits, and
+ * an instance whose caller range (first, count) is new to the batch starts
+ * without lists. A caller that writes a new problem into a range the last
+ * batch already had, and wants the bits of a fresh context, calls this first.
+ * SPH_E_INVAL for a range outside [0, the context's capacity). */
+sph_status sph_lists_clear(sph_ctx *ctx, int64_t first, int64_t count, void *stream);
 
 /* Total kernel launches issued by this context since creation. */
 int64_t sph_launch_count(const sph_ctx *ctx);

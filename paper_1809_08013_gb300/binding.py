@@ -32,6 +32,7 @@ class SphParams(C.Structure):
         ("alpha", C.c_double), ("beta", C.c_double), ("eta2", C.c_double),
         ("cfl", C.c_double), ("lz", C.c_double), ("cell_scale", C.c_double),
         ("kernel", C.c_int32), ("gradients", C.c_int32), ("sinc_n", C.c_int32),
+        ("list_skin", C.c_double),
     ]
 
 
@@ -138,6 +139,8 @@ def load(rebuild: bool = True):
     L.sph_timing_enable.argtypes = [_DP, C.c_int]
     L.sph_timing_read.restype = C.c_int
     L.sph_timing_read.argtypes = [_DP, _DP, _DP, _DP]
+    L.sph_lists_clear.restype = C.c_int
+    L.sph_lists_clear.argtypes = [_DP, C.c_int64, C.c_int64, _DP]
     L.sph_launch_count.restype = C.c_int64
     L.sph_launch_count.argtypes = [_DP]
     L.sph_neighbor_rows.restype = C.c_int64
@@ -173,7 +176,8 @@ def params(p) -> SphParams:
                      float(p.rho0), float(p.c0), float(p.gamma),
                      float(p.alpha), float(p.beta), float(p.eta2), float(p.cfl), float(p.lz),
                      float(getattr(p, "cell_scale", 0.0)), int(getattr(p, "kernel", 0)),
-                     int(getattr(p, "gradients", 0)), int(getattr(p, "sinc_n", 5)))
+                     int(getattr(p, "gradients", 0)), int(getattr(p, "sinc_n", 5)),
+                     float(getattr(p, "list_skin", 0.0)))
 
 
 def _ptr(t):
@@ -369,6 +373,12 @@ class Context:
         self._check(self.lib.sph_timing_read(self.h, C.cast(ms, C.c_void_p), C.cast(ln, C.c_void_p),
                                              C.cast(C.pointer(st), C.c_void_p)))
         return dict(zip(PHASES, list(ms))), dict(zip(PHASES, list(ln))), int(st.value)
+
+    def lists_clear(self, first: int = 0, count: int | None = None, stream=None):
+        """sph_lists_clear: forget the candidate lists of [first, first + count)."""
+        if count is None:
+            count = self.n_capacity - first
+        self._check(self.lib.sph_lists_clear(self.h, int(first), int(count), _stream(stream)))
 
     def launch_count(self) -> int:
         return int(self.lib.sph_launch_count(self.h))

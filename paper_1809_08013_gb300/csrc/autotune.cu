@@ -46,6 +46,7 @@ float trial(sph_ctx* c, const sph_particles* P, const Knobs& k, int nsteps, cuda
     set_knobs(c, k, s);
     double* dt = c->tune_dt;
     double* tm = c->tune_dt + c->maxinst;
+    lists_clear(c, s);  // every trial starts without candidate lists
     launch_load_state(c, P, s);
     launch_step(c, dt, tm, s);
     cudaEventRecord(e0, s);
@@ -142,6 +143,7 @@ extern "C" sph_status sph_autotune(sph_ctx* c, sph_particles* P, int nsteps,
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    lists_clear(c, s);  // the caller's next steps start as they would untuned
     if (st == SPH_OK) {
         set_knobs(c, best, s);  // the batch keeps the chosen knobs
         out->cell_scale = best.cs;

@@ -27,29 +27,12 @@
 
 #include <algorithm>
 
+#include "df.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-// Lower and upper FP32 bounds of a positive double from its bit pattern
-// (truncation is rounding toward zero; integer operations only).
-__device__ __forceinline__ void f32_bounds(double x, float& lo, float& hi) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)(b >> 52) - 1023 + 127;
-    if (e <= 0) {
-        lo = 0.0f;
-        hi = 1.17549435e-38f;
-    } else if (e >= 255) {
-        lo = 3.40282347e+38f;
-        hi = CUDART_INF_F;
-    } else {
-        const unsigned lb = ((unsigned)e << 23) | ((unsigned)(b >> 29) & 0x7fffffu);
-        lo = __int_as_float((int)lb);
-        hi = (b & 0x1fffffffull) ? __int_as_float((int)(lb + 1)) : lo;
-    }
-}
 
 struct Thr {
     float tin, tout;
@@ -138,13 +121,6 @@ __device__ __forceinline__ float axis_gap(float v, int k, const Grid* __restrict
     const float a = g->lof[d] + (float)k * g->wf[d] - g->slop[d];
     const float b = g->lof[d] + (float)(k + 1) * g->wf[d] + g->slop[d];
     return fmaxf(0.0f, fmaxf(a - v, v - b));
-}
-
-// Upper FP32 bound of 2 x (a positive double), widened by 1e-4 relative.
-__device__ __forceinline__ float reach_f32(double h) {
-    float lo, hi;
-    f32_bounds(h, lo, hi);
-    return 2.0f * hi * 1.0001f;
 }
 
 // Cell index range overlapping [a, b] along axis d (clamped); along the
@@ -291,12 +267,18 @@ __device__ __forceinline__ int lane_cell(float v, const Grid* __restrict__ g, in
 // except those with r2 < tin_lo, certainly within 2 lo (lo the bisection's
 // lower bound, so within 2 h for every h still to be tried): those go to the
 // gather slab and the count c at once.
+// BL: also append to the lane's candidate list (caller indices, lrow, nl)
+// every staged candidate with r^2 <= tL. Padding slots (sidx -1) are never
+// counted, recorded or listed.
+template <bool BL>
 __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const int* __restrict__ sidx,
                                             const float4& fi, const Thr& t, bool active, bool rec,
                                             float tin_lo, int64_t i, double h, double& R2,
                                             const double4_32a* posh, const Grid* __restrict__ g,
-                                            int32_t* slab, int& c, int2* recb, int& nrec) {
-    unsigned in = 0u, bd = 0u;
+                                            int32_t* slab, int& c, int2* recb, int& nrec,
+                                            float tL, const int32_t* __restrict__ order,
+                                            int32_t* __restrict__ lrow, int& nl) {
+    unsigned in = 0u, bd = 0u, lb = 0u;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
         const float4 q = st[k];
@@ -304,14 +286,25 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         if (r2 < t.tin) in |= 1u << k;
         if (r2 <= t.tout) bd |= 1u << k;
+        if (BL && r2 <= tL) lb |= 1u << k;
     }
     if (!active) return;
+    if (BL) {
+        while (lb) {
+            const int k = __ffs(lb) - 1;
+            lb &= lb - 1u;
+            const int j = sidx[k];
+            if (j == i || j < 0) continue;
+            if (nl < kList) lrow[nl] = __ldg(&order[j]);
+            ++nl;
+        }
+    }
     if (rec) {
         while (bd) {
             const int k = __ffs(bd) - 1;
             bd &= bd - 1u;
             const int j = sidx[k];
-            if (j == i) continue;
+            if (j == i || j < 0) continue;
             const float4 q = st[k];
             const float dx = fi.x - q.x, dy = fi.y - q.y, dz = fi.z - q.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -330,7 +323,7 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
         const int k = __ffs(bd) - 1;
         bd &= bd - 1u;
         const int j = sidx[k];
-        if (j == i) continue;
+        if (j == i || j < 0) continue;
         if (R2 < 0.0) {
             const double R = 2.0 * h;
             R2 = __dmul_rn(R, R);
@@ -341,10 +334,52 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
         const int k = __ffs(in) - 1;
         in &= in - 1u;
         const int j = sidx[k];
-        if (j == i) continue;
+        if (j == i || j < 0) continue;
         if (c < kGSlab) slab[c] = j;
         ++c;
     }
+}
+
+// N_i(h) from a candidate list L (caller indices, ln entries; islot maps them
+// to slots): the same FP32 decisions with the exact FP64 band as a cell walk,
+// the members written to the slab in list order. The list must hold every j
+// within 2 h of i (the caller checks that it still does).
+__device__ __forceinline__ int list_count(const int32_t* __restrict__ L, int ln,
+                                          const int32_t* __restrict__ islot,
+                                          const float4* __restrict__ fpos, const float4& fi,
+                                          const Thr& t, int64_t i, double h,
+                                          const double4_32a* posh, const Grid* __restrict__ g,
+                                          int32_t* slab) {
+    int c = 0;
+    double R2 = -1.0;
+    for (int e0 = 0; e0 < ln; e0 += 4) {
+        const int4 q = __ldg(reinterpret_cast<const int4*>(L + e0));
+        const int id[4] = {q.x, q.y, q.z, q.w};
+        int j[4];
+        float4 f[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) j[k] = e0 + k < ln ? __ldg(&islot[id[k]]) : -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) f[k] = j[k] >= 0 ? __ldg(&fpos[j[k]]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (j[k] < 0) continue;
+            const float r2 = f_r2(fi, f[k], g);
+            bool in = r2 < t.tin;
+            if (!in && r2 <= t.tout) {
+                if (R2 < 0.0) {
+                    const double R = 2.0 * h;
+                    R2 = __dmul_rn(R, R);
+                }
+                in = exact_r2(posh[i], posh[j[k]], g) < R2;
+            }
+            if (in) {
+                if (c < kGSlab) slab[c] = j[k];
+                ++c;
+            }
+        }
+    }
+    return c;
 }
 
 // |N_i(hh)| from the c0 neighbours certainly within 2 lo <= 2 hh (already in
@@ -380,7 +415,8 @@ __device__ __forceinline__ void union_group(
     const int2* __restrict__ cells, int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
     int32_t* __restrict__ rslab, double* __restrict__ hs_lo, double* __restrict__ hs_hi,
     int32_t* __restrict__ hs_it, int32_t* __restrict__ wl, unsigned* __restrict__ status,
-    float4* st, int* sidx, int2* recb) {
+    float4* st, int* sidx, int2* recb, const int32_t* __restrict__ order,
+    const int32_t* __restrict__ islot, int32_t* __restrict__ lst, LMeta* __restrict__ lmeta) {
     const int lane = threadIdx.x & 31;
     const int64_t i = i0 + lane;
     const int inst = slot_inst(B, i0);
@@ -407,6 +443,24 @@ __device__ __forceinline__ void union_group(
     const bool per = g->periodic_z != 0;
     const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
     const unsigned lt = (1u << lane) - 1u;
+    // Candidate lists: a lane with a kept list was served by k_h_lists. A
+    // build step walks every lane, recording its list (every candidate within
+    // 2 h (1 + skin)) in the first walk.
+    const bool build = kp.list_skin > 0.0 && g->lbuild != 0;
+    const int32_t id = valid ? __ldg(&order[i]) : 0;
+    int32_t* lrow = lst + (int64_t)id * kList;
+    int nl = 0;
+    bool listed = false;
+    if (build && valid) {  // this build's record of the particle (its list comes with the walk)
+        const double4_32a p = posh[i];
+        reinterpret_cast<float4*>(lmeta)[2 * id] =
+            make_float4(dfl::from_double(p.x).hi, dfl::from_double(p.y).hi,
+                        dfl::from_double(p.z).hi, 0.0f);
+        reinterpret_cast<int4*>(lmeta)[2 * id + 1] = make_int4(g->lstamp, 0, 0, 0);
+    } else if (kp.list_skin > 0.0 && active && lmeta[id].cnt > 0) {
+        listed = true;
+        active = false;
+    }
     for (int pass = 0;; ++pass) {  // pass is warp-uniform; it (per lane) stops at convergence
         const unsigned am = __ballot_sync(kFull, active);
         if (!am) break;
@@ -418,7 +472,10 @@ __device__ __forceinline__ void union_group(
         const double hs = rec && !isinf(hi) ? hi : h;
         const Thr t = thresholds(2.0 * hs, g);
         const float tin_lo = rec && lo > 0.0 ? thresholds(2.0 * lo, g).tin : -1.0f;
-        const float Rq = reach_f32(hs);
+        const bool blist = build && pass == 0;  // list radius RL = 2 hs (1 + skin)
+        const double RL = blist ? 2.0 * hs * (1.0 + kp.list_skin) : 0.0;
+        const float tL = blist ? thresholds(RL, g).tout : 0.0f;
+        const float Rq = blist ? reach_f32(0.5 * RL) : reach_f32(hs);
         const float lzz = wmin(active ? fi.z - Rq : CUDART_INF_F), hzz = wmax(active ? fi.z + Rq : -CUDART_INF_F);
         // Periodic z: candidates are moved to the image nearest a reference lane's
         // z, which is each lane's minimum image while the warp spans < lz/4.
@@ -524,8 +581,14 @@ __device__ __forceinline__ void union_group(
                                 continue;
                             }
                             __syncwarp();
-                            union_chunk(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g,
-                                        slab, c, recb, nrec);
+                            if (blist)
+                                union_chunk<true>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2,
+                                                  posh, g, slab, c, recb, nrec, tL, order, lrow,
+                                                  nl);
+                            else
+                                union_chunk<false>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2,
+                                                   posh, g, slab, c, recb, nrec, tL, order, lrow,
+                                                   nl);
                             __syncwarp();
                             if (ok && r >= room) {
                                 st[r - room] = f;
@@ -542,10 +605,20 @@ __device__ __forceinline__ void union_group(
                     sidx[lane] = -1;
                 }
                 __syncwarp();
-                union_chunk(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g, slab, c, recb,
-                            nrec);
+                if (blist)
+                    union_chunk<true>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g, slab,
+                                      c, recb, nrec, tL, order, lrow, nl);
+                else
+                    union_chunk<false>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g, slab,
+                                       c, recb, nrec, tL, order, lrow, nl);
                 __syncwarp();
             }
+        }
+        if (blist && active) {  // the list of this walk, complete unless it overflowed
+            float lo_r, hi_r;
+            f32_bounds(RL, lo_r, hi_r);
+            lmeta[id].rad = lo_r * 0.999999f;
+            lmeta[id].cnt = nl <= kList ? nl : 0;
         }
         if (active && rec && nrec > kRec) {  // too many to record: one warp of its own
             deferred = true;
@@ -592,7 +665,75 @@ __device__ __forceinline__ void union_group(
         }
         return;
     }
-    if (deferred) return;
+    if (deferred || listed) return;
+    posh[i].w = h;
+    nnb[i] = cnt;
+    ngather[i] = cnt;
+    if (cnt > kGSlab) atomicOr(&status[2], (unsigned)IF_SLAB_OVF);
+    if (!conv) {
+        atomicOr(&status[0], (unsigned)ST_HNOCONV);
+        atomicAdd(&status[1], 1u);
+    }
+}
+
+// The h search of the particles with a kept candidate list (one thread per
+// slot; the others are left to k_h_union): the bisection of the cell walk,
+// each count from one scan of the list while the list still covers 2h (its
+// radius at the build minus twice the largest displacement since), the same
+// sequence of h and the same neighbour set. A particle whose next h the list
+// no longer covers is handed, with its bisection state, to k_h_iterate.
+__global__ void __launch_bounds__(kThreads)
+k_h_lists(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos,
+          int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ rslab,
+          double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
+          int32_t* __restrict__ wl, unsigned* __restrict__ status,
+          const int32_t* __restrict__ order, const int32_t* __restrict__ islot,
+          const int32_t* __restrict__ lst, const LMeta* __restrict__ lmeta) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int inst = slot_inst(B, i);
+    if (!slot_real(B, inst, i)) return;
+    const KParams& kp = B.kp[inst];
+    const Grid* __restrict__ g = B.grid + inst;
+    if (!(kp.list_skin > 0.0) || g->lbuild || kp.max_h_iter < 1) return;
+    const int32_t id = order[i];
+    const int ln = lmeta[id].cnt;
+    if (ln <= 0) return;
+    double h = posh[i].w;
+    const float4 fi = fpos[i];
+    if (!(isfinite(fi.x) && isfinite(fi.y) && isfinite(fi.z) && h_ok(h))) return;
+    const float lrad = lmeta[id].rad, dm2 = g->dm2;
+    const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
+    const int max_it = kp.max_h_iter;
+    const int32_t* L = lst + (int64_t)id * kList;
+    int32_t* slab = rslab + i * kRSlab;
+    double lo = 0.0, hi = CUDART_INF;
+    int cnt = 0, it = 0;
+    bool conv = false;
+    for (;;) {
+        if (!(reach_f32(h) + dm2 <= lrad)) {  // the list may miss a neighbour: walk
+            posh[i].w = h;
+            hs_lo[i] = lo;
+            hs_hi[i] = hi;
+            hs_it[i] = it;
+            wl[atomicAdd(&status[3], 1u)] = (int32_t)i;
+            return;
+        }
+        cnt = list_count(L, ln, islot, fpos, fi, thresholds(2.0 * h, g), i, h, posh, g, slab);
+        ++it;
+        if (cnt >= lowb && cnt <= highb) {
+            conv = true;
+            break;
+        }
+        if (it >= max_it) break;
+        if (cnt < lowb) {
+            lo = h;
+            h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+        } else {
+            hi = h;
+            h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
+        }
+    }
     posh[i].w = h;
     nnb[i] = cnt;
     ngather[i] = cnt;
@@ -612,7 +753,9 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
           int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ rslab,
           double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
           int32_t* __restrict__ wl, unsigned* __restrict__ status,
-          unsigned long long* __restrict__ wctr, int2* __restrict__ recs) {
+          unsigned long long* __restrict__ wctr, int2* __restrict__ recs,
+          const int32_t* __restrict__ order, const int32_t* __restrict__ islot,
+          int32_t* __restrict__ lst, LMeta* __restrict__ lmeta) {
     __shared__ float4 s_f[kThreads / 32][32];
     __shared__ int s_i[kThreads / 32][32];
     const int warp = threadIdx.x >> 5;
@@ -625,7 +768,8 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
         if (gi >= ngroups) break;
         union_group(gi * 32, n, B, posh, fpos, cells, nnb, ngather, rslab, hs_lo, hs_hi, hs_it,
                     wl, status, s_f[warp], s_i[warp],
-                    recs + ((int64_t)(blockIdx.x * (kThreads / 32) + warp) * 32 + lane) * kRec);
+                    recs + ((int64_t)(blockIdx.x * (kThreads / 32) + warp) * 32 + lane) * kRec,
+                    order, islot, lst, lmeta);
     }
 }
 
@@ -1071,11 +1215,15 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     double4_32a* posh = c->posh[c->cur];
     const Batch B = batch_of(c);
-    c->launches += 4;
+    c->launches += 5;
+    k_h_lists<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->nnb, c->ngather, c->rslab, c->hs_lo,
+                                      c->hs_hi, c->hs_it, c->wl, c->status, c->order[c->cur],
+                                      c->islot, c->lst, c->lmeta);
     const int64_t nbu = std::min<int64_t>((int64_t)c->nsm * kUnionBlocksPerSM, ((n + 31) / 32 + 7) / 8);
     k_h_union<<<(unsigned)nbu, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb,
                                                  c->ngather, c->rslab, c->hs_lo, c->hs_hi,
-                                                 c->hs_it, c->wl, c->status, c->wctr, c->recs);
+                                                 c->hs_it, c->wl, c->status, c->wctr, c->recs,
+                                                 c->order[c->cur], c->islot, c->lst, c->lmeta);
     k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(B, posh, c->fpos, c->cells, c->nnb,
                                                        c->ngather, c->rslab, c->hs_lo, c->hs_hi,
                                                        c->hs_it, c->wl, c->status);

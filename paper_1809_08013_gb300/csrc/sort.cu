@@ -156,8 +156,12 @@ constexpr long long kKeyMax = 0x7fffffffffffffffLL, kKeyMin = -kKeyMax - 1;
 // Bounding-box partials: min x, y, z and max x, y, z, h, m, |v| (largest
 // component), u (as keys) and the sum of h over the particles of each group
 // of kSlotAlign slots (one instance), one warp per group, reduced in a fixed
-// order. Stored as kBoxStride doubles per group: mn[3], mx[7], hs.
-constexpr int kBoxMax = 7;
+// order; with candidate lists also the largest displacement since the last
+// list build, the smallest list slack (list radius - 2h), and the largest and
+// smallest build stamp. Stored as kBoxStride doubles per group: mn[3],
+// mx[11], hs.
+constexpr int kBoxMax = 11;
+enum { BX_D = 7, BX_NSLACK = 8, BX_STAMP = 9, BX_NSTAMP = 10 };
 
 struct BoxPart {
     long long mn[3], mx[kBoxMax];
@@ -190,12 +194,17 @@ __device__ __forceinline__ void box_warp_reduce(BoxPart& b) {
 __global__ void __launch_bounds__(kThreads)
 k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
        const double4_32a* __restrict__ velm, const double* __restrict__ ue,
+       const int32_t* __restrict__ order, const LMeta* __restrict__ lmeta,
        double* __restrict__ part, unsigned* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (grp * kSlotAlign >= n) return;  // warp-uniform
     const int inst = slot_inst(B, grp * kSlotAlign);
     const int64_t end = __ldg(&B.ioff[inst]) + __ldg(&B.icnt[inst]);
+    const KParams& kp = B.kp[inst];
+    const bool lists = kp.list_skin > 0.0;
+    const bool per = kp.periodic_z != 0;
+    const float lzf = (float)kp.lz, hlzf = 0.5f * lzf;
     BoxPart b;
     box_init(b);
     bool bad = false;
@@ -212,6 +221,29 @@ k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const bool geo = coord_ok(p.x) && coord_ok(p.y) && coord_ok(p.z) && h_ok(p.w);
             const bool fin = finite_bits(v.x) && finite_bits(v.y) && finite_bits(v.z) &&
                              finite_bits(v.w) && finite_bits(uk);
+            if (lists && geo) {
+                // since the last list build: the displacement (truncated floats,
+                // the minimum image along a periodic z), the list's slack at the
+                // current h, the build stamp
+                const int32_t id = order[k];
+                const float4 m0 = __ldg(reinterpret_cast<const float4*>(lmeta) + 2 * id);
+                const int4 m1 = __ldg(reinterpret_cast<const int4*>(lmeta) + 2 * id + 1);
+                const float dx = dfl::from_double(p.x).hi - m0.x;
+                const float dy = dfl::from_double(p.y).hi - m0.y;
+                float dz = dfl::from_double(p.z).hi - m0.z;
+                if (per) {
+                    if (dz > hlzf) dz -= lzf;
+                    else if (dz < -hlzf) dz += lzf;
+                }
+                const long long kd = __float_as_int(sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))));
+                b.mx[BX_D] = kd > b.mx[BX_D] ? kd : b.mx[BX_D];  // NaN keys above +inf
+                if (m1.y > 0) {
+                    const long long ks = fkey(reach_f32(p.w) - m0.w);
+                    b.mx[BX_NSLACK] = ks > b.mx[BX_NSLACK] ? ks : b.mx[BX_NSLACK];
+                }
+                b.mx[BX_STAMP] = m1.x > b.mx[BX_STAMP] ? m1.x : b.mx[BX_STAMP];
+                b.mx[BX_NSTAMP] = -(long long)m1.x > b.mx[BX_NSTAMP] ? -(long long)m1.x : b.mx[BX_NSTAMP];
+            }
             bad |= !(geo && fin);
             if (!(geo && fin)) continue;
             const long long kx = okey(p.x), ky = okey(p.y), kz = okey(p.z), kh = okey(p.w);
@@ -259,7 +291,8 @@ constexpr int kGridThreads = 1024;
 
 __global__ void __launch_bounds__(kGridThreads)
 k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
-             unsigned* __restrict__ status, unsigned long long* __restrict__ wctr) {
+             unsigned* __restrict__ status, unsigned long long* __restrict__ wctr,
+             unsigned* __restrict__ lctr) {
     const int inst = blockIdx.x;
     const int64_t n = B.icnt[inst];
     const int64_t b0 = B.ioff[inst] / kSlotAlign;
@@ -281,6 +314,7 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     box_warp_reduce(v);
     __shared__ BoxPart sh[kGridThreads / 32];
     __shared__ double r[11];
+    __shared__ long long lk[4];  // list keys: displacement, -slack, stamp, -stamp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) sh[warp] = v;
     __syncthreads();
@@ -301,6 +335,7 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
         r[8] = okey_inv(a.mx[4]);   // max m
         r[9] = okey_inv(a.mx[5]);   // max |v| component
         r[10] = okey_inv(a.mx[6]);  // max u
+        for (int q = 0; q < 4; ++q) lk[q] = a.mx[BX_D + q];
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -396,6 +431,27 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     g->hlzc = (float)(0.5 * kp.lz * p2d(-g->uL));
     g->hmean = hmean;
     g->hmax_bits = 0ull;
+    // Candidate lists of the h search. The instance keeps its lists while
+    // every particle carries the same build stamp and twice the largest
+    // displacement since that build (bounded with the truncation errors of
+    // both positions) is below every list's slack at the current h: then any
+    // j within 2 h of i now was within the list radius at the build, and is
+    // listed. Otherwise this step rebuilds them under a new stamp.
+    g->lbuild = 0;
+    g->lstamp = 0;
+    g->dm2 = CUDART_INF_F;
+    if (kp.list_skin > 0.0 && n > 0) {
+        const long long smax = lk[2], smin = -lk[3];
+        const bool epoch = smax == smin && smin > 0;
+        const float D = lk[0] == kKeyMin ? 0.0f : __int_as_float((int)lk[0]);
+        const double Dm = (double)D * (1.0 + 0x1p-20) + 0x1p-20 * (X + (double)D);
+        const float dm2 = (float)(2.0 * Dm * (1.0 + 0x1p-20));
+        const float slack = lk[1] == kKeyMin ? CUDART_INF_F : -fkey_inv(lk[1]);
+        const bool keep = epoch && dm2 < slack;  // false for a NaN displacement
+        g->dm2 = dm2;
+        g->lbuild = keep ? 0 : 1;
+        g->lstamp = keep ? (int)smin : (int)((atomicAdd(lctr, 1u) & 0x3fffffffu) + 1u);
+    }
     g->ncells = (long long)cnt[0] * cnt[1] * cnt[2];
 }
 
@@ -532,7 +588,7 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
           const int32_t* __restrict__ order_in, double4_32a* __restrict__ posh_out,
           double4_32a* __restrict__ velm_out, double* __restrict__ u_out,
           int32_t* __restrict__ order_out, float4* __restrict__ fpos, float4* __restrict__ xpk,
-          float4* __restrict__ vpa, float2* __restrict__ vpb) {
+          float4* __restrict__ vpa, float2* __restrict__ vpb, int32_t* __restrict__ islot) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ntot) return;
     const int inst = (int)(keys[r] >> 24);
@@ -545,7 +601,9 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
     write_xpk(xpk, k, p, v.w, B.grid[inst]);
     if (B.kp[inst].precision == PREC_FP64) write_vpk(vpa, vpb, k, v, B.grid[inst]);
     u_out[k] = u_in[o];
-    order_out[k] = order_in[o];
+    const int32_t id = order_in[o];
+    order_out[k] = id;
+    if (B.kp[inst].list_skin > 0.0) islot[id] = (int32_t)k;  // (caller index < capacity)
     fpos[k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
 }
 
@@ -591,9 +649,11 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
         c->launches += 1;
         const int64_t groups = (n + kSlotAlign - 1) / kSlotAlign;
         k_bbox<<<(unsigned)((groups * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            n, B, c->posh[c->cur], c->velm[c->cur], c->ue[c->cur], c->red_part, c->status);
+            n, B, c->posh[c->cur], c->velm[c->cur], c->ue[c->cur], c->order[c->cur], c->lmeta,
+            c->red_part, c->status);
     }
-    k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status, c->wctr);
+    k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status, c->wctr,
+                                                    c->lctr);
     if (n == 0) return;
     const int64_t nt = c->ntot;
     if (nt == 0) return;
@@ -616,7 +676,8 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const int a = c->cur, b = 1 - c->cur;
     k_permute<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->vals[src], c->posh[a],
                                         c->velm[a], c->ue[a], c->order[a], c->posh[b], c->velm[b],
-                                        c->ue[b], c->order[b], c->fpos, c->xpk, c->vpa, c->vpb);
+                                        c->ue[b], c->order[b], c->fpos, c->xpk, c->vpa, c->vpb,
+                                        c->islot);
     c->cur = b;
     k_cells_clear<<<dim3(64, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->cells, c->cell_hmax);
     k_cells_mark<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->cells);

@@ -83,6 +83,7 @@ sph_status check_params(sph_ctx* c, const sph_params* p) {
         return SPH_E_INVAL;
     }
     if (p->periodic_z && !(p->lz > 0.0)) { set_err(c, "periodic_z needs lz > 0"); return SPH_E_INVAL; }
+    if (!(p->list_skin <= 1.0)) { set_err(c, "list_skin must be at most 1"); return SPH_E_INVAL; }
     if (!(p->cfl > 0.0)) { set_err(c, "cfl must be > 0"); return SPH_E_INVAL; }
     return SPH_OK;
 }
@@ -119,7 +120,7 @@ void free_all(sph_ctx* c) {
                     c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->omask, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
                     c->tune_dt, c->roff, c->wctr, c->recs, c->iad_a, c->iad_b, c->vol, c->xpk, c->vpa, c->vpb,
-                    c->stage, c->stage_nnb, c->vdf, c->cpk};
+                    c->stage, c->stage_nnb, c->vdf, c->cpk, c->lst, c->lmeta, c->islot, c->lctr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -201,7 +202,8 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->hs_lo, N) && al(&c->hs_hi, N) && al(&c->hs_it, N) && al(&c->wl, N) &&
          al(&c->scratch_scalar, 2) && al(&c->tune_dt, 2 * (size_t)max_instances) &&
          al(&c->wctr, 4) &&
-         al(&c->recs, (size_t)c->nsm * kUnionBlocksPerSM * kThreads * kRec);
+         al(&c->recs, (size_t)c->nsm * kUnionBlocksPerSM * kThreads * kRec) &&
+         al(&c->lst, N * kList) && al(&c->lmeta, N) && al(&c->islot, N) && al(&c->lctr, 1);
     return ok;
 }
 
@@ -276,7 +278,38 @@ k_set_single(KParams kp, int64_t n, long long cap, int64_t nblk, int32_t* __rest
     }
 }
 
+// The candidate lists of the h search and their records belong to an
+// instance's caller range: an instance whose range (first, count) was not one
+// of the previous batch's starts without them (its records are cleared, so
+// its next step builds its lists). A range kept from one call to the next
+// keeps its lists; whether they still hold is checked on the device.
+void lists_for_layout(sph_ctx* c, int ninst, const int64_t* first, const int64_t* cnt,
+                      cudaStream_t s) {
+    for (int k = 0; k < ninst; ++k) {
+        bool seen = false;
+        for (int q = 0; q < c->lay_n && !seen; ++q)
+            seen = c->lay_first[q] == first[k] && c->lay_cnt[q] == cnt[k];
+        if (!seen && cnt[k] > 0 && first[k] + cnt[k] <= c->ncap)
+            cudaMemsetAsync(c->lmeta + first[k], 0, (size_t)cnt[k] * sizeof(LMeta), s);
+    }
+    c->lay_n = ninst;
+    for (int k = 0; k < ninst; ++k) {
+        c->lay_first[k] = first[k];
+        c->lay_cnt[k] = cnt[k];
+    }
+}
+
+// Clear the list records of every instance of the current layout (their next
+// step builds).
+void lists_clear(sph_ctx* c, cudaStream_t s) {
+    for (int k = 0; k < c->lay_n; ++k)
+        if (c->lay_cnt[k] > 0 && c->lay_first[k] + c->lay_cnt[k] <= c->ncap)
+            cudaMemsetAsync(c->lmeta + c->lay_first[k], 0, (size_t)c->lay_cnt[k] * sizeof(LMeta), s);
+}
+
 void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s) {
+    const int64_t zero = 0;
+    lists_for_layout(c, 1, &zero, &n, s);
     c->n = n;
     c->ntot = n;
     c->cext = n;
@@ -455,6 +488,25 @@ int64_t sph_launch_count(const sph_ctx* c) { return c ? c->launches : 0; }
 
 int64_t sph_neighbor_rows(const sph_ctx* c) { return c ? c->n : 0; }
 
+sph_status sph_lists_clear(sph_ctx* c, int64_t first, int64_t count, void* stream) {
+    if (!c) return SPH_E_INVAL;
+    if (first < 0 || count < 0 || first + count > c->ncap) {
+        set_err(c, "sph_lists_clear: [%lld, %lld) outside [0, %lld)", (long long)first,
+                (long long)(first + count), (long long)c->ncap);
+        return SPH_E_INVAL;
+    }
+    if (count == 0) return SPH_OK;
+    DeviceGuard dg(c->device);
+    const cudaError_t e = cudaMemsetAsync(c->lmeta + first, 0, (size_t)count * sizeof(LMeta),
+                                          (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, "sph_lists_clear: %s", cudaGetErrorString(e));
+        return SPH_E_CUDA;
+    }
+    return SPH_OK;
+}
+
 sph_status sph_timing_enable(sph_ctx* c, int enable) {
     if (!c) return SPH_E_INVAL;
     DeviceGuard dg(c->device);
@@ -581,7 +633,9 @@ sph_status sph_ctx_create_batch(sph_ctx** out, int64_t ncap, int64_t nnzcap, int
     ok = ok && cudaMallocHost((void**)&c->status_host, 2 * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemset(c->status, 0, 4 * sizeof(unsigned)) == cudaSuccess &&
          cudaMemset(c->offsets, 0, sizeof(int64_t)) == cudaSuccess &&
-         cudaMemset(c->grid, 0, (size_t)max_instances * sizeof(Grid)) == cudaSuccess;
+         cudaMemset(c->grid, 0, (size_t)max_instances * sizeof(Grid)) == cudaSuccess &&
+         cudaMemset(c->lmeta, 0, (size_t)std::max<int64_t>(nslots, 1) * sizeof(LMeta)) == cudaSuccess &&
+         cudaMemset(c->lctr, 0, sizeof(unsigned)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -876,6 +930,8 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const
         slots += counts[k];
         if (k + 1 < ninst) slots = (slots + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
         kpi[k] = kparams(&params[k]);
+        // the candidate lists are stored by caller index, up to the capacity
+        if (coff[k] + counts[k] > c->ncap) kpi[k].list_skin = 0.0;
         memset(&grid[k], 0, sizeof(Grid));
         grid[k].cbase = cells;
         grid[k].cap = instance_cell_cap(counts[k]);
@@ -911,6 +967,7 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const
             blk[(size_t)b] = k;
     DeviceGuard dg(c->device);
     cudaStream_t s = (cudaStream_t)stream;
+    lists_for_layout(c, ninst, coff.data(), icnt.data(), s);
     cudaError_t e = cudaMemcpyAsync(c->ioff, ioff.data(), (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->coff, coff.data(), (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->icnt, icnt.data(), ninst * sizeof(int64_t), cudaMemcpyHostToDevice, s);

@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math_constants.h>
 #include <stdint.h>
 
 #include "../../include/sph.h"
@@ -29,7 +30,7 @@ constexpr int kRadixTile = kThreads * kRadixItems;  // 2048 keys per block
 constexpr int kScanTile = kThreads * 8;             // elements per block in scans
 constexpr int kReduceBlocks = 304;                  // 2 x 152 SMs
 constexpr int kMaxPairThreads = 8;                  // lanes per particle in the pair kernels
-constexpr int kBoxStride = 12;                      // doubles per bounding-box partial
+constexpr int kBoxStride = 16;                      // doubles per bounding-box partial
 
 // device status word
 enum : unsigned {
@@ -54,6 +55,42 @@ __device__ __forceinline__ bool h_ok(double h) {
 __device__ __forceinline__ bool finite_bits(double x) {
     return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
 }
+
+// Lower and upper FP32 bounds of a positive double from its bit pattern
+// (truncation is rounding toward zero; integer operations only).
+__device__ __forceinline__ void f32_bounds(double x, float& lo, float& hi) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)(b >> 52) - 1023 + 127;
+    if (e <= 0) {
+        lo = 0.0f;
+        hi = 1.17549435e-38f;
+    } else if (e >= 255) {
+        lo = 3.40282347e+38f;
+        hi = CUDART_INF_F;
+    } else {
+        const unsigned lb = ((unsigned)e << 23) | ((unsigned)(b >> 29) & 0x7fffffu);
+        lo = __int_as_float((int)lb);
+        hi = (b & 0x1fffffffull) ? __int_as_float((int)(lb + 1)) : lo;
+    }
+}
+
+// Upper FP32 bound of 2 x (a positive double), widened by 1e-4 relative.
+__device__ __forceinline__ float reach_f32(double h) {
+    float lo, hi;
+    f32_bounds(h, lo, hi);
+    return 2.0f * hi * 1.0001f;
+}
+
+// Order-preserving integer key of a float (and back): signed integer order of
+// the keys is the order of the values.
+__device__ __forceinline__ long long fkey(float f) {
+    const int b = __float_as_int(f);
+    return (long long)(b >= 0 ? b : (b ^ 0x7fffffff));
+}
+__device__ __forceinline__ float fkey_inv(long long k) {
+    const int b = (int)k;
+    return __int_as_float(b >= 0 ? b : (b ^ 0x7fffffff));
+}
 // internal flags (status[2], cleared at every build)
 enum : unsigned {
     IF_SLAB_OVF = 1u,   // a row did not fit the gather/outer slabs: full CSR kernels run
@@ -63,6 +100,18 @@ enum : unsigned {
 constexpr int kGSlab = 128;  // gather-set slots per particle (>= n_target + n_tol)
 constexpr int kRec = 256;    // h search: candidates recorded per lane in flight
 constexpr int kUnionBlocksPerSM = 4;  // resident blocks of the persistent h search
+// Candidate lists of the h search, kept across steps (neighbors.cu): per
+// particle (by caller index) the caller indices of every particle within the
+// list radius 2 h (1 + skin) at the instance's last list build.
+constexpr int kList = 192;                    // list entries per particle
+constexpr double kListSkinDefault = 0.15;     // sph_params.list_skin = 0 selects it
+struct LMeta {     // per caller index, written by the instance's last list build
+    float x, y, z;   // the particle's position then (truncated floats)
+    float rad;       // list radius (a lower bound): all j within it then are listed
+    int32_t stamp;   // that build (0: none; builds of one context are numbered)
+    int32_t cnt;     // list length (0: no usable list)
+    int32_t pad0, pad1;
+};
 constexpr int kRSlab = 224;  // row slots per particle: gather set, then the outer set
                              // (outer sets: patch max ~40, Evrard ~64)
 
@@ -96,6 +145,12 @@ struct Grid {
     // range, so in units where everything is already O(1) the results are
     // the same bits as without the rescaling.
     int uL, uM, uV;
+    // Candidate lists (set per step by the grid setup): lbuild = 1 when this
+    // step's h search rebuilds the instance's lists (stamped lstamp); else the
+    // lists of build lstamp hold, and dm2 bounds twice any particle's
+    // displacement since that build.
+    int lbuild, lstamp;
+    float dm2;
 };
 
 // 2^e as a double, exactly (e in [-1022, 1023]); integer operations only.
@@ -115,6 +170,7 @@ struct KParams {
     double rho0, c0, gamma, alpha, beta, eta2, cfl, lz, cell_scale;
     double wnorm, dnorm;
     double inv_rho0, tait_k;  // 1 / rho0 and c0^2 rho0 / 7, for the per-particle EOS
+    double list_skin;         // candidate lists' skin (0: no lists)
 };
 
 enum { KER_M4 = 0, KER_WENDLAND = 1, KER_SINC = 2 };
@@ -172,6 +228,7 @@ inline KParams kparams(const sph_params* p) {
     k.sinc_n = p->sinc_n;
     k.inv_rho0 = p->rho0 != 0.0 ? 1.0 / p->rho0 : 0.0;
     k.tait_k = p->c0 * p->c0 * p->rho0 / 7.0;
+    k.list_skin = p->list_skin < 0.0 ? 0.0 : (p->list_skin > 0.0 ? p->list_skin : kListSkinDefault);
     if (p->kernel == KER_WENDLAND) {
         k.wnorm = 21.0 / (16.0 * kPi);
         k.dnorm = 105.0 / (16.0 * kPi);
@@ -250,6 +307,12 @@ struct sph_ctx {
     sph::Grid* grid;        // per instance
     unsigned long long* wctr;  // work counters of persistent kernels (zeroed per build)
     int2* recs;             // h search records: kRec per lane of the persistent grid
+    int32_t* lst;           // candidate lists: kList per caller index
+    sph::LMeta* lmeta;      // their records, per caller index
+    int32_t* islot;         // slot of each caller index in the current order
+    unsigned* lctr;         // list builds so far (stamps)
+    int lay_n;              // instances of the last batch layout (first, count) ...
+    int64_t lay_first[sph::kMaxInstances], lay_cnt[sph::kMaxInstances];  // ... and theirs
     int nsm;                // streaming multiprocessors of the device
     unsigned* status;       // [0] bits, [1] non-converged count, [2] internal flags,
                             // [3] h-search worklist length
@@ -352,6 +415,9 @@ __device__ __forceinline__ bool row_of(const Rows& R, int64_t n, int64_t i, bool
 // ---- sph_abi.cu
 // Describe a single problem of n particles (a batch of one) on the stream.
 void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s);
+void lists_for_layout(sph_ctx* c, int ninst, const int64_t* first, const int64_t* cnt,
+                      cudaStream_t s);
+void lists_clear(sph_ctx* c, cudaStream_t s);
 // One step of the current batch on the context's state (dt, time: ninst each).
 void launch_step(sph_ctx* c, double* dt, double* time, cudaStream_t s);
 

@@ -178,6 +178,7 @@ class Server:
         torch = self.torch
         first = self.arena.take(req.n)
         assert first is not None
+        self.ctx.lists_clear(first, req.n, stream=self.stream)  # as on a fresh context
         for f in self.B.STATE_FIELDS:
             self.arr[f][first:first + req.n].copy_(torch.from_numpy(np.ascontiguousarray(state[f])),
                                                    non_blocking=True)
