@@ -372,6 +372,11 @@ sph_status sph_timing_read(sph_ctx *ctx, double *ms, int64_t *launches, int64_t 
  * SPH_E_INVAL for a range outside [0, the context's capacity). */
 sph_status sph_lists_clear(sph_ctx *ctx, int64_t first, int64_t count, void *stream);
 
+/* Number of candidate-list builds of this context so far (one per instance
+ * and rebuilding step), after the stream's work (synchronises the stream):
+ * a measure of how long the lists last for a given list_skin. */
+sph_status sph_list_builds(sph_ctx *ctx, int64_t *builds, void *stream);
+
 /* Total kernel launches issued by this context since creation. */
 int64_t sph_launch_count(const sph_ctx *ctx);
 

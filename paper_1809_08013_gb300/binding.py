@@ -141,6 +141,8 @@ def load(rebuild: bool = True):
     L.sph_timing_read.argtypes = [_DP, _DP, _DP, _DP]
     L.sph_lists_clear.restype = C.c_int
     L.sph_lists_clear.argtypes = [_DP, C.c_int64, C.c_int64, _DP]
+    L.sph_list_builds.restype = C.c_int
+    L.sph_list_builds.argtypes = [_DP, C.POINTER(C.c_int64), _DP]
     L.sph_launch_count.restype = C.c_int64
     L.sph_launch_count.argtypes = [_DP]
     L.sph_neighbor_rows.restype = C.c_int64
@@ -379,6 +381,12 @@ class Context:
         if count is None:
             count = self.n_capacity - first
         self._check(self.lib.sph_lists_clear(self.h, int(first), int(count), _stream(stream)))
+
+    def list_builds(self, stream=None) -> int:
+        """sph_list_builds: candidate-list builds so far (synchronises)."""
+        v = C.c_int64()
+        self._check(self.lib.sph_list_builds(self.h, C.byref(v), _stream(stream)))
+        return int(v.value)
 
     def launch_count(self) -> int:
         return int(self.lib.sph_launch_count(self.h))

@@ -507,6 +507,22 @@ sph_status sph_lists_clear(sph_ctx* c, int64_t first, int64_t count, void* strea
     return SPH_OK;
 }
 
+sph_status sph_list_builds(sph_ctx* c, int64_t* builds, void* stream) {
+    if (!c || !builds) return SPH_E_INVAL;
+    DeviceGuard dg(c->device);
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, c->lctr, sizeof v, cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, "sph_list_builds: %s", cudaGetErrorString(e));
+        return SPH_E_CUDA;
+    }
+    *builds = (int64_t)v;
+    return SPH_OK;
+}
+
 sph_status sph_timing_enable(sph_ctx* c, int enable) {
     if (!c) return SPH_E_INVAL;
     DeviceGuard dg(c->device);
