@@ -267,17 +267,16 @@ __device__ __forceinline__ int lane_cell(float v, const Grid* __restrict__ g, in
 // except those with r2 < tin_lo, certainly within 2 lo (lo the bisection's
 // lower bound, so within 2 h for every h still to be tried): those go to the
 // gather slab and the count c at once.
-// BL: also append to the lane's candidate list (caller indices, lrow, nl)
-// every staged candidate with r^2 <= tL. Padding slots (sidx -1) are never
-// counted, recorded or listed.
+// BL: also append to the lane's candidate list (slots, entries 32 apart from
+// lrow on; nl of them) every staged candidate with r^2 <= tL. Padding slots
+// (sidx -1) are never counted, recorded or listed.
 template <bool BL>
 __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const int* __restrict__ sidx,
                                             const float4& fi, const Thr& t, bool active, bool rec,
                                             float tin_lo, int64_t i, double h, double& R2,
                                             const double4_32a* posh, const Grid* __restrict__ g,
                                             int32_t* slab, int& c, int2* recb, int& nrec,
-                                            float tL, const int32_t* __restrict__ order,
-                                            int32_t* __restrict__ lrow, int& nl) {
+                                            float tL, int32_t* __restrict__ lrow, int& nl) {
     unsigned in = 0u, bd = 0u, lb = 0u;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
@@ -295,7 +294,7 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
             lb &= lb - 1u;
             const int j = sidx[k];
             if (j == i || j < 0) continue;
-            if (nl < kList) lrow[nl] = __ldg(&order[j]);
+            if (nl < kList) lrow[nl * 32] = j;
             ++nl;
         }
     }
@@ -340,12 +339,11 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
     }
 }
 
-// N_i(h) from a candidate list L (caller indices, ln entries; islot maps them
-// to slots): the same FP32 decisions with the exact FP64 band as a cell walk,
-// the members written to the slab in list order. The list must hold every j
-// within 2 h of i (the caller checks that it still does).
+// N_i(h) from a candidate list (slots, ln entries 32 apart from L on): the
+// same FP32 decisions with the exact FP64 band as a cell walk, the members
+// written to the slab in list order. The list must hold every j within 2 h of
+// i (the caller checks that it still does).
 __device__ __forceinline__ int list_count(const int32_t* __restrict__ L, int ln,
-                                          const int32_t* __restrict__ islot,
                                           const float4* __restrict__ fpos, const float4& fi,
                                           const Thr& t, int64_t i, double h,
                                           const double4_32a* posh, const Grid* __restrict__ g,
@@ -353,12 +351,10 @@ __device__ __forceinline__ int list_count(const int32_t* __restrict__ L, int ln,
     int c = 0;
     double R2 = -1.0;
     for (int e0 = 0; e0 < ln; e0 += 4) {
-        const int4 q = __ldg(reinterpret_cast<const int4*>(L + e0));
-        const int id[4] = {q.x, q.y, q.z, q.w};
         int j[4];
         float4 f[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) j[k] = e0 + k < ln ? __ldg(&islot[id[k]]) : -1;
+        for (int k = 0; k < 4; ++k) j[k] = e0 + k < ln ? __ldg(&L[(e0 + k) * 32]) : -1;
 #pragma unroll
         for (int k = 0; k < 4; ++k) f[k] = j[k] >= 0 ? __ldg(&fpos[j[k]]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -416,7 +412,7 @@ __device__ __forceinline__ void union_group(
     int32_t* __restrict__ rslab, double* __restrict__ hs_lo, double* __restrict__ hs_hi,
     int32_t* __restrict__ hs_it, int32_t* __restrict__ wl, unsigned* __restrict__ status,
     float4* st, int* sidx, int2* recb, const int32_t* __restrict__ order,
-    const int32_t* __restrict__ islot, int32_t* __restrict__ lst, LMeta* __restrict__ lmeta) {
+    int32_t* __restrict__ lst, LMeta* __restrict__ lmeta) {
     const int lane = threadIdx.x & 31;
     const int64_t i = i0 + lane;
     const int inst = slot_inst(B, i0);
@@ -448,7 +444,7 @@ __device__ __forceinline__ void union_group(
     // 2 h (1 + skin)) in the first walk.
     const bool build = kp.list_skin > 0.0 && g->lbuild != 0;
     const int32_t id = valid ? __ldg(&order[i]) : 0;
-    int32_t* lrow = lst + (int64_t)id * kList;
+    int32_t* lrow = lst + (i >> 5) * (int64_t)kList * 32 + (i & 31);
     int nl = 0;
     bool listed = false;
     if (build && valid) {  // this build's record of the particle (its list comes with the walk)
@@ -456,7 +452,8 @@ __device__ __forceinline__ void union_group(
         reinterpret_cast<float4*>(lmeta)[2 * id] =
             make_float4(dfl::from_double(p.x).hi, dfl::from_double(p.y).hi,
                         dfl::from_double(p.z).hi, 0.0f);
-        reinterpret_cast<int4*>(lmeta)[2 * id + 1] = make_int4(g->lstamp, 0, 0, 0);
+        lmeta[id].stamp = g->lstamp;  // (the cell code was recorded by the sort)
+        lmeta[id].cnt = 0;
     } else if (kp.list_skin > 0.0 && active && lmeta[id].cnt > 0) {
         listed = true;
         active = false;
@@ -583,12 +580,10 @@ __device__ __forceinline__ void union_group(
                             __syncwarp();
                             if (blist)
                                 union_chunk<true>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2,
-                                                  posh, g, slab, c, recb, nrec, tL, order, lrow,
-                                                  nl);
+                                                  posh, g, slab, c, recb, nrec, tL, lrow, nl);
                             else
                                 union_chunk<false>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2,
-                                                   posh, g, slab, c, recb, nrec, tL, order, lrow,
-                                                   nl);
+                                                   posh, g, slab, c, recb, nrec, tL, lrow, nl);
                             __syncwarp();
                             if (ok && r >= room) {
                                 st[r - room] = f;
@@ -607,10 +602,10 @@ __device__ __forceinline__ void union_group(
                 __syncwarp();
                 if (blist)
                     union_chunk<true>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g, slab,
-                                      c, recb, nrec, tL, order, lrow, nl);
+                                      c, recb, nrec, tL, lrow, nl);
                 else
                     union_chunk<false>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g, slab,
-                                       c, recb, nrec, tL, order, lrow, nl);
+                                       c, recb, nrec, tL, lrow, nl);
                 __syncwarp();
             }
         }
@@ -687,8 +682,8 @@ k_h_lists(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
           int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ rslab,
           double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
           int32_t* __restrict__ wl, unsigned* __restrict__ status,
-          const int32_t* __restrict__ order, const int32_t* __restrict__ islot,
-          const int32_t* __restrict__ lst, const LMeta* __restrict__ lmeta) {
+          const int32_t* __restrict__ order, const int32_t* __restrict__ lst,
+          const LMeta* __restrict__ lmeta) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int inst = slot_inst(B, i);
@@ -705,7 +700,7 @@ k_h_lists(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
     const float lrad = lmeta[id].rad, dm2 = g->dm2;
     const int lowb = kp.n_target - kp.n_tol, highb = kp.n_target + kp.n_tol;
     const int max_it = kp.max_h_iter;
-    const int32_t* L = lst + (int64_t)id * kList;
+    const int32_t* L = lst + (i >> 5) * (int64_t)kList * 32 + (i & 31);
     int32_t* slab = rslab + i * kRSlab;
     double lo = 0.0, hi = CUDART_INF;
     int cnt = 0, it = 0;
@@ -719,7 +714,7 @@ k_h_lists(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
             wl[atomicAdd(&status[3], 1u)] = (int32_t)i;
             return;
         }
-        cnt = list_count(L, ln, islot, fpos, fi, thresholds(2.0 * h, g), i, h, posh, g, slab);
+        cnt = list_count(L, ln, fpos, fi, thresholds(2.0 * h, g), i, h, posh, g, slab);
         ++it;
         if (cnt >= lowb && cnt <= highb) {
             conv = true;
@@ -754,8 +749,8 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
           double* __restrict__ hs_lo, double* __restrict__ hs_hi, int32_t* __restrict__ hs_it,
           int32_t* __restrict__ wl, unsigned* __restrict__ status,
           unsigned long long* __restrict__ wctr, int2* __restrict__ recs,
-          const int32_t* __restrict__ order, const int32_t* __restrict__ islot,
-          int32_t* __restrict__ lst, LMeta* __restrict__ lmeta) {
+          const int32_t* __restrict__ order, int32_t* __restrict__ lst,
+          LMeta* __restrict__ lmeta) {
     __shared__ float4 s_f[kThreads / 32][32];
     __shared__ int s_i[kThreads / 32][32];
     const int warp = threadIdx.x >> 5;
@@ -769,7 +764,7 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
         union_group(gi * 32, n, B, posh, fpos, cells, nnb, ngather, rslab, hs_lo, hs_hi, hs_it,
                     wl, status, s_f[warp], s_i[warp],
                     recs + ((int64_t)(blockIdx.x * (kThreads / 32) + warp) * 32 + lane) * kRec,
-                    order, islot, lst, lmeta);
+                    order, lst, lmeta);
     }
 }
 
@@ -1218,12 +1213,12 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
     c->launches += 5;
     k_h_lists<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->nnb, c->ngather, c->rslab, c->hs_lo,
                                       c->hs_hi, c->hs_it, c->wl, c->status, c->order[c->cur],
-                                      c->islot, c->lst, c->lmeta);
+                                      c->lst, c->lmeta);
     const int64_t nbu = std::min<int64_t>((int64_t)c->nsm * kUnionBlocksPerSM, ((n + 31) / 32 + 7) / 8);
     k_h_union<<<(unsigned)nbu, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb,
                                                  c->ngather, c->rslab, c->hs_lo, c->hs_hi,
                                                  c->hs_it, c->wl, c->status, c->wctr, c->recs,
-                                                 c->order[c->cur], c->islot, c->lst, c->lmeta);
+                                                 c->order[c->cur], c->lst, c->lmeta);
     k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(B, posh, c->fpos, c->cells, c->nnb,
                                                        c->ngather, c->rslab, c->hs_lo, c->hs_hi,
                                                        c->hs_it, c->wl, c->status);

@@ -237,7 +237,7 @@ k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
                 }
                 const long long kd = __float_as_int(sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))));
                 b.mx[BX_D] = kd > b.mx[BX_D] ? kd : b.mx[BX_D];  // NaN keys above +inf
-                if (m1.y > 0) {
+                if (m1.z > 0) {
                     const long long ks = fkey(reach_f32(p.w) - m0.w);
                     b.mx[BX_NSLACK] = ks > b.mx[BX_NSLACK] ? ks : b.mx[BX_NSLACK];
                 }
@@ -355,9 +355,36 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     double w = 2.0 * hmean * kp.cell_scale;
     if (!(w > 0.0) || !isfinite(w)) w = 1.0;
     const bool per = kp.periodic_z != 0;
+    double X = 0.0;
+    for (int d = 0; d < 3; ++d) X = fmax(X, fmax(fabs(mn[d]), fabs(mx[d])));
+    if (per) X = fmax(X, 0.5 * kp.lz);
+    // Candidate lists of the h search. The instance keeps its lists while
+    // every particle carries the same build stamp and twice the largest
+    // displacement since that build (bounded with the truncation errors of
+    // both positions) is below every list's slack at the current h: then any
+    // j within 2 h of i now was within the list radius at the build, and is
+    // listed. Otherwise this step rebuilds them under a new stamp. While they
+    // are kept, so are the build's cell geometry and (through the sort keys)
+    // its cells, whose walks then reach further by the displacement bound.
+    bool keep = false;
+    float dm2 = CUDART_INF_F;
+    if (kp.list_skin > 0.0 && n > 0) {
+        const long long smax = lk[2], smin = -lk[3];
+        const bool epoch = smax == smin && smin > 0;
+        const float D = lk[0] == kKeyMin ? 0.0f : __int_as_float((int)lk[0]);
+        const double Dm = (double)D * (1.0 + 0x1p-20) + 0x1p-20 * (X + (double)D);
+        dm2 = (float)(2.0 * Dm * (1.0 + 0x1p-20));
+        const float slack = lk[1] == kKeyMin ? CUDART_INF_F : -fkey_inv(lk[1]);
+        keep = epoch && g->gvalid && dm2 < slack;  // false for a NaN displacement
+        g->lstamp = keep ? (int)smin : (int)((atomicAdd(lctr, 1u) & 0x3fffffffu) + 1u);
+    } else {
+        g->lstamp = 0;
+    }
+    g->lbuild = kp.list_skin > 0.0 && n > 0 && !keep ? 1 : 0;
+    g->dm2 = dm2;
     int cnt[3];
     double ww[3], lo[3];
-    for (int tries = 0; tries < 200; ++tries) {
+    for (int tries = 0; tries < 200 && !keep; ++tries) {
         for (int d = 0; d < 3; ++d) {
             lo[d] = mn[d];
             cnt[d] = grid_count(mx[d] - mn[d], w, &ww[d]);
@@ -373,19 +400,21 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
         if ((long long)cnt[0] * cnt[1] * cnt[2] <= cellcap) break;
         w *= 1.25;
     }
-    double X = 0.0;
-    for (int d = 0; d < 3; ++d) X = fmax(X, fmax(fabs(mn[d]), fabs(mx[d])));
-    if (per) X = fmax(X, 0.5 * kp.lz);
-    for (int d = 0; d < 3; ++d) {
-        g->lo[d] = lo[d];
-        g->w[d] = ww[d];
-        g->inv_w[d] = 1.0 / ww[d];
-        g->n[d] = cnt[d];
-        g->lof[d] = (float)lo[d];
-        g->wf[d] = (float)ww[d];
-        g->invwf[d] = (float)(1.0 / ww[d]);
-        g->slop[d] = (float)(1e-3 * ww[d] + 1.2e-7 * X);
+    if (!keep) {
+        for (int d = 0; d < 3; ++d) {
+            g->lo[d] = lo[d];
+            g->w[d] = ww[d];
+            g->inv_w[d] = 1.0 / ww[d];
+            g->n[d] = cnt[d];
+            g->lof[d] = (float)lo[d];
+            g->wf[d] = (float)ww[d];
+            g->invwf[d] = (float)(1.0 / ww[d]);
+        }
+        g->ncells = (long long)cnt[0] * cnt[1] * cnt[2];
+        g->gvalid = 1;
     }
+    for (int d = 0; d < 3; ++d)
+        g->slop[d] = (float)(1e-3 * g->w[d] + 1.2e-7 * X + (keep ? 0.5 * 1.001 * dm2 : 0.0));
     g->periodic_z = per ? 1 : 0;
     g->lz = kp.lz;
     g->lzf = (float)kp.lz;
@@ -431,28 +460,6 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
     g->hlzc = (float)(0.5 * kp.lz * p2d(-g->uL));
     g->hmean = hmean;
     g->hmax_bits = 0ull;
-    // Candidate lists of the h search. The instance keeps its lists while
-    // every particle carries the same build stamp and twice the largest
-    // displacement since that build (bounded with the truncation errors of
-    // both positions) is below every list's slack at the current h: then any
-    // j within 2 h of i now was within the list radius at the build, and is
-    // listed. Otherwise this step rebuilds them under a new stamp.
-    g->lbuild = 0;
-    g->lstamp = 0;
-    g->dm2 = CUDART_INF_F;
-    if (kp.list_skin > 0.0 && n > 0) {
-        const long long smax = lk[2], smin = -lk[3];
-        const bool epoch = smax == smin && smin > 0;
-        const float D = lk[0] == kKeyMin ? 0.0f : __int_as_float((int)lk[0]);
-        const double Dm = (double)D * (1.0 + 0x1p-20) + 0x1p-20 * (X + (double)D);
-        const float dm2 = (float)(2.0 * Dm * (1.0 + 0x1p-20));
-        const float slack = lk[1] == kKeyMin ? CUDART_INF_F : -fkey_inv(lk[1]);
-        const bool keep = epoch && dm2 < slack;  // false for a NaN displacement
-        g->dm2 = dm2;
-        g->lbuild = keep ? 0 : 1;
-        g->lstamp = keep ? (int)smin : (int)((atomicAdd(lctr, 1u) & 0x3fffffffu) + 1u);
-    }
-    g->ncells = (long long)cnt[0] * cnt[1] * cnt[2];
 }
 
 // ----------------------------------------------------------- Morton keys
@@ -489,21 +496,32 @@ __device__ __forceinline__ int cell_coord(double v, float lo, float inv, int n) 
 // key = instance (top 8 bits) | 24-bit Morton code of the particle's cell in
 // its instance's grid, stored at the particle's rank roff[k] + (caller index
 // - coff[k]) with its current slot as the value.
+// While the instance keeps its candidate lists, the code is the particle's
+// code at the list build, so the sort gives every particle its slot of then;
+// a build step records the codes it sorts by.
 __global__ void __launch_bounds__(kThreads)
 k_keys(int64_t n, Batch B, const int64_t* __restrict__ coff, const int64_t* __restrict__ roff,
        const double4_32a* __restrict__ posh, const int32_t* __restrict__ order,
-       uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+       uint32_t* __restrict__ keys, int32_t* __restrict__ vals, LMeta* __restrict__ lmeta) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int inst = slot_inst(B, k);
     if (!slot_real(B, inst, k)) return;
     const Grid* g = B.grid + inst;
-    const double4_32a p = posh[k];
-    const int kx = cell_coord(p.x, g->lof[0], g->invwf[0], g->n[0]);
-    const int ky = cell_coord(p.y, g->lof[1], g->invwf[1], g->n[1]);
-    const int kz = cell_coord(p.z, g->lof[2], g->invwf[2], g->n[2]);
-    const uint32_t code = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
-    const int64_t q = __ldg(&roff[inst]) + ((int64_t)order[k] - __ldg(&coff[inst]));
+    const bool lists = B.kp[inst].list_skin > 0.0;
+    const int32_t id = order[k];
+    uint32_t code;
+    if (lists && !g->lbuild) {
+        code = lmeta[id].code;
+    } else {
+        const double4_32a p = posh[k];
+        const int kx = cell_coord(p.x, g->lof[0], g->invwf[0], g->n[0]);
+        const int ky = cell_coord(p.y, g->lof[1], g->invwf[1], g->n[1]);
+        const int kz = cell_coord(p.z, g->lof[2], g->invwf[2], g->n[2]);
+        code = spread3(kx) | (spread3(ky) << 1) | (spread3(kz) << 2);
+        if (lists) lmeta[id].code = code;
+    }
+    const int64_t q = __ldg(&roff[inst]) + ((int64_t)id - __ldg(&coff[inst]));
     keys[q] = ((uint32_t)inst << 24) | code;
     vals[q] = (int32_t)k;
 }
@@ -588,7 +606,7 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
           const int32_t* __restrict__ order_in, double4_32a* __restrict__ posh_out,
           double4_32a* __restrict__ velm_out, double* __restrict__ u_out,
           int32_t* __restrict__ order_out, float4* __restrict__ fpos, float4* __restrict__ xpk,
-          float4* __restrict__ vpa, float2* __restrict__ vpb, int32_t* __restrict__ islot) {
+          float4* __restrict__ vpa, float2* __restrict__ vpb) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ntot) return;
     const int inst = (int)(keys[r] >> 24);
@@ -601,9 +619,7 @@ k_permute(int64_t ntot, Batch B, const int64_t* __restrict__ roff,
     write_xpk(xpk, k, p, v.w, B.grid[inst]);
     if (B.kp[inst].precision == PREC_FP64) write_vpk(vpa, vpb, k, v, B.grid[inst]);
     u_out[k] = u_in[o];
-    const int32_t id = order_in[o];
-    order_out[k] = id;
-    if (B.kp[inst].list_skin > 0.0) islot[id] = (int32_t)k;  // (caller index < capacity)
+    order_out[k] = order_in[o];
     fpos[k] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
 }
 
@@ -661,7 +677,7 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const int passes = c->ninst > 1 ? 4 : 3;
     c->launches += 1 + passes * 5 + 3;
     k_keys<<<nb, kThreads, 0, s>>>(n, B, c->coff, c->roff, c->posh[c->cur], c->order[c->cur],
-                                   c->keys[0], c->vals[0]);
+                                   c->keys[0], c->vals[0], c->lmeta);
     const int nsb = (int)((nt + kRadixTile - 1) / kRadixTile);
     int src = 0;
     for (int pass = 0; pass < passes; ++pass) {
@@ -676,8 +692,7 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const int a = c->cur, b = 1 - c->cur;
     k_permute<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->vals[src], c->posh[a],
                                         c->velm[a], c->ue[a], c->order[a], c->posh[b], c->velm[b],
-                                        c->ue[b], c->order[b], c->fpos, c->xpk, c->vpa, c->vpb,
-                                        c->islot);
+                                        c->ue[b], c->order[b], c->fpos, c->xpk, c->vpa, c->vpb);
     c->cur = b;
     k_cells_clear<<<dim3(64, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->cells, c->cell_hmax);
     k_cells_mark<<<nbt, kThreads, 0, s>>>(nt, B, c->roff, c->keys[src], c->cells);

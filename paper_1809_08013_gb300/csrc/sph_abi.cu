@@ -120,7 +120,7 @@ void free_all(sph_ctx* c) {
                     c->offsets, c->row_part, c->idx, c->rslab, c->ocnt, c->omask, c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->red_part, c->dt_part, c->grid,
                     c->status, c->scratch_scalar, c->blk, c->ioff, c->icnt, c->coff, c->kpi,
                     c->tune_dt, c->roff, c->wctr, c->recs, c->iad_a, c->iad_b, c->vol, c->xpk, c->vpa, c->vpb,
-                    c->stage, c->stage_nnb, c->vdf, c->cpk, c->lst, c->lmeta, c->islot, c->lctr};
+                    c->stage, c->stage_nnb, c->vdf, c->cpk, c->lst, c->lmeta, c->lctr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -203,7 +203,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->scratch_scalar, 2) && al(&c->tune_dt, 2 * (size_t)max_instances) &&
          al(&c->wctr, 4) &&
          al(&c->recs, (size_t)c->nsm * kUnionBlocksPerSM * kThreads * kRec) &&
-         al(&c->lst, N * kList) && al(&c->lmeta, N) && al(&c->islot, N) && al(&c->lctr, 1);
+         al(&c->lst, (N + 31) / 32 * 32 * kList) && al(&c->lmeta, N) && al(&c->lctr, 1);
     return ok;
 }
 

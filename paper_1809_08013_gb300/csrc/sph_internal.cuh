@@ -100,17 +100,23 @@ enum : unsigned {
 constexpr int kGSlab = 128;  // gather-set slots per particle (>= n_target + n_tol)
 constexpr int kRec = 256;    // h search: candidates recorded per lane in flight
 constexpr int kUnionBlocksPerSM = 4;  // resident blocks of the persistent h search
-// Candidate lists of the h search, kept across steps (neighbors.cu): per
-// particle (by caller index) the caller indices of every particle within the
-// list radius 2 h (1 + skin) at the instance's last list build.
+// Candidate lists of the h search, kept across steps (neighbors.cu). While an
+// instance keeps its lists, its particles keep the slots of the list build:
+// the sort orders them by the cell codes of that build, not by their current
+// cells (the cell tables then hold the build's cells, and every cell walk
+// widens its reach by the largest displacement since). A list holds the slots
+// of every particle within 2 h (1 + skin) of its particle at the build; the
+// lists of the 32 slots of a warp are stored interleaved (entry e of slot i at
+// ((i / 32) kList + e) 32 + i % 32), so a warp reads 32 entries at once.
 constexpr int kList = 192;                    // list entries per particle
 constexpr double kListSkinDefault = 0.15;     // sph_params.list_skin = 0 selects it
 struct LMeta {     // per caller index, written by the instance's last list build
     float x, y, z;   // the particle's position then (truncated floats)
     float rad;       // list radius (a lower bound): all j within it then are listed
     int32_t stamp;   // that build (0: none; builds of one context are numbered)
+    uint32_t code;   // the particle's cell code (Morton) in the build's grid
     int32_t cnt;     // list length (0: no usable list)
-    int32_t pad0, pad1;
+    int32_t pad;
 };
 constexpr int kRSlab = 224;  // row slots per particle: gather set, then the outer set
                              // (outer sets: patch max ~40, Evrard ~64)
@@ -151,6 +157,7 @@ struct Grid {
     // displacement since that build.
     int lbuild, lstamp;
     float dm2;
+    int gvalid;  // the geometry above is that of a list build (kept while the lists are)
 };
 
 // 2^e as a double, exactly (e in [-1022, 1023]); integer operations only.
@@ -307,9 +314,8 @@ struct sph_ctx {
     sph::Grid* grid;        // per instance
     unsigned long long* wctr;  // work counters of persistent kernels (zeroed per build)
     int2* recs;             // h search records: kRec per lane of the persistent grid
-    int32_t* lst;           // candidate lists: kList per caller index
+    int32_t* lst;           // candidate lists: kList per slot (warp-interleaved)
     sph::LMeta* lmeta;      // their records, per caller index
-    int32_t* islot;         // slot of each caller index in the current order
     unsigned* lctr;         // list builds so far (stamps)
     int lay_n;              // instances of the last batch layout (first, count) ...
     int64_t lay_first[sph::kMaxInstances], lay_cnt[sph::kMaxInstances];  // ... and theirs
