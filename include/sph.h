@@ -127,18 +127,20 @@ typedef struct {
                             G_ij = (W(r_ij, h_i) C_i + W(r_ij, h_j) C_j)(r_j - r_i) / 2
                             in place of Fbar_ij r_ij in the momentum and energy sums */
     int32_t sinc_n;      /* exponent n of the sinc kernel, 2..12 (read when kernel = 2) */
-    double list_skin;    /* h search: every particle keeps across steps the list of all
-                            particles within 2 h (1 + list_skin) of it at the last list
-                            build and counts its neighbours from that list while it still
-                            holds them all (no particle has moved far enough since); the
-                            instance rebuilds its lists when one no longer covers its
-                            particle's 2 h. 0 selects 0.15; a negative value turns the
-                            lists off (every count walks the cells); above 1:
-                            SPH_E_INVAL. Lists are kept per caller index: a batch
-                            instance whose caller range reaches past the context's
-                            capacity runs without them. A tuning knob: h and the
-                            neighbour sets do not depend on it (the order within a
-                            gather set does) */
+    double list_skin;    /* h search with candidate lists (opt in; 0 or negative: off,
+                            every count walks the cells): every particle keeps across
+                            steps the list of all particles within 2 h (1 + list_skin)
+                            of it at the last list build and counts its neighbours from
+                            that list while it still holds them all (no particle has
+                            moved far enough since); the instance rebuilds its lists
+                            when one no longer covers its particle's 2 h. Above 1:
+                            SPH_E_INVAL. On GB300 the cell walk, which loads each
+                            candidate once for a warp of 32 particles, is the faster of
+                            the two for the benchmark workloads. Lists are kept per
+                            caller index: a batch instance whose caller range reaches
+                            past the context's capacity runs without them. A tuning
+                            knob: h and the neighbour sets do not depend on it (the
+                            order within a gather set does) */
 } sph_params;
 
 #define SPH_KERNEL_M4 0

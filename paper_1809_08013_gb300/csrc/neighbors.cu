@@ -350,15 +350,16 @@ __device__ __forceinline__ int list_count(const int32_t* __restrict__ L, int ln,
                                           int32_t* slab) {
     int c = 0;
     double R2 = -1.0;
-    for (int e0 = 0; e0 < ln; e0 += 4) {
-        int j[4];
-        float4 f[4];
+    constexpr int G = 4;  // entries in flight per group (loads first, then the tests)
+    for (int e0 = 0; e0 < ln; e0 += G) {
+        int j[G];
+        float4 f[G];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) j[k] = e0 + k < ln ? __ldg(&L[(e0 + k) * 32]) : -1;
+        for (int k = 0; k < G; ++k) j[k] = e0 + k < ln ? __ldg(&L[(e0 + k) * 32]) : -1;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) f[k] = j[k] >= 0 ? __ldg(&fpos[j[k]]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < G; ++k) f[k] = j[k] >= 0 ? __ldg(&fpos[j[k]]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < G; ++k) {
             if (j[k] < 0) continue;
             const float r2 = f_r2(fi, f[k], g);
             bool in = r2 < t.tin;
@@ -705,29 +706,31 @@ k_h_lists(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
     double lo = 0.0, hi = CUDART_INF;
     int cnt = 0, it = 0;
     bool conv = false;
-    for (;;) {
-        if (!(reach_f32(h) + dm2 <= lrad)) {  // the list may miss a neighbour: walk
-            posh[i].w = h;
-            hs_lo[i] = lo;
-            hs_hi[i] = hi;
-            hs_it[i] = it;
-            wl[atomicAdd(&status[3], 1u)] = (int32_t)i;
-            return;
-        }
+    // one count at the current h, from the list if it still covers 2h; a
+    // particle that has to go on bisecting (or whose list no longer covers
+    // 2h) continues in k_h_iterate, which records its candidates once
+    const bool covered = reach_f32(h) + dm2 <= lrad;
+    if (covered) {
         cnt = list_count(L, ln, fpos, fi, thresholds(2.0 * h, g), i, h, posh, g, slab);
-        ++it;
-        if (cnt >= lowb && cnt <= highb) {
-            conv = true;
-            break;
+        it = 1;
+        conv = cnt >= lowb && cnt <= highb;
+    }
+    if (!covered || (!conv && it < max_it)) {
+        if (covered) {
+            if (cnt < lowb) {
+                lo = h;
+                h = __dmul_rn(h, 1.25);  // no upper bound yet
+            } else {
+                hi = h;
+                h = __dmul_rn(h, 0.8);  // no lower bound yet
+            }
         }
-        if (it >= max_it) break;
-        if (cnt < lowb) {
-            lo = h;
-            h = isinf(hi) ? __dmul_rn(h, 1.25) : __dmul_rn(0.5, __dadd_rn(lo, hi));
-        } else {
-            hi = h;
-            h = (lo == 0.0) ? __dmul_rn(h, 0.8) : __dmul_rn(0.5, __dadd_rn(lo, hi));
-        }
+        posh[i].w = h;
+        hs_lo[i] = lo;
+        hs_hi[i] = hi;
+        hs_it[i] = it;
+        wl[atomicAdd(&status[3], 1u)] = (int32_t)i;
+        return;
     }
     posh[i].w = h;
     nnb[i] = cnt;
@@ -768,6 +771,19 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
     }
 }
 
+// The candidates of a list (ln entries 32 apart from L on), 32 at a time:
+// chunk(valid, j) is called by all lanes together, lane l receiving entry
+// e0 + l (valid = false past the end), as particle_pass hands out a walk's.
+template <class Chunk>
+__device__ __forceinline__ void list_pass(const int32_t* __restrict__ L, int ln, Chunk&& chunk) {
+    const int lane = threadIdx.x & 31;
+    for (int e0 = 0; e0 < ln; e0 += 32) {
+        const int e = e0 + lane;
+        const bool valid = e < ln;
+        chunk(valid, valid ? __ldg(&L[e * 32]) : -1);
+    }
+}
+
 // Phase 2: one warp per handed-over particle (persistent grid over the
 // worklist), continuing its bisection where phase 1 stopped. A walk over the
 // cells records, in shared memory and in walk order, every candidate that may
@@ -785,7 +801,9 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
             int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
             int32_t* __restrict__ rslab, const double* __restrict__ hs_lo,
             const double* __restrict__ hs_hi, const int32_t* __restrict__ hs_it,
-            const int32_t* __restrict__ wl, unsigned* __restrict__ status) {
+            const int32_t* __restrict__ wl, unsigned* __restrict__ status,
+            const int32_t* __restrict__ order, const int32_t* __restrict__ lst,
+            const LMeta* __restrict__ lmeta) {
     __shared__ int s_start[kThreads / 32][32], s_pref[kThreads / 32][32];
     __shared__ int2 s_rec[kThreads / 32][kRecW];  // (FP32 r^2 bits, j)
     const int warp = threadIdx.x >> 5;
@@ -810,6 +828,13 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
         int32_t* slab = rslab + i * kRSlab;
         double hs = -1.0;  // radius / 2 the records cover (none yet)
         int nrec = 0;
+        // the particle's kept candidate list, while it covers a radius 2 hq
+        // (then it replaces the cell walk: the same candidates within 2 hq)
+        const bool lists = kp.list_skin > 0.0 && !g->lbuild;
+        const int ln = lists ? lmeta[order[i]].cnt : 0;
+        const float lrad = ln > 0 ? lmeta[order[i]].rad : 0.0f;
+        const int32_t* L = lst + (i >> 5) * (int64_t)kList * 32 + (i & 31);
+        auto list_covers = [&](double hq) { return ln > 0 && reach_f32(hq) + g->dm2 <= lrad; };
         for (int it = hs_it[i]; it < max_it; ++it) {
             const double R = 2.0 * h;
             const Thr t = thresholds(R, g);
@@ -821,21 +846,23 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
                 hs = isinf(hi) ? __dmul_rn(h, 1.25) : hi;
                 const float tout_s = thresholds(2.0 * hs, g).tout;
                 nrec = 0;
-                particle_pass<1>(g, cl, nullptr, fi, reach_f32(hs), 0, s_start[warp], s_pref[warp],
-                                 [&](bool valid, int j) {
-                                     float r2f = 0.0f;
-                                     bool keep = false;
-                                     if (valid && j != i) {
-                                         r2f = f_r2(fi, __ldg(&fpos[j]), g);
-                                         keep = r2f <= tout_s;
-                                     }
-                                     const unsigned m = __ballot_sync(kFull, keep);
-                                     if (keep) {
-                                         const int q = nrec + __popc(m & lt);
-                                         if (q < kRecW) rec[q] = make_int2(__float_as_int(r2f), j);
-                                     }
-                                     nrec += __popc(m);
-                                 });
+                auto record = [&](bool valid, int j) {
+                    float r2f = 0.0f;
+                    bool keep = false;
+                    if (valid && j != i) {
+                        r2f = f_r2(fi, __ldg(&fpos[j]), g);
+                        keep = r2f <= tout_s;
+                    }
+                    const unsigned m = __ballot_sync(kFull, keep);
+                    if (keep) {
+                        const int q = nrec + __popc(m & lt);
+                        if (q < kRecW) rec[q] = make_int2(__float_as_int(r2f), j);
+                    }
+                    nrec += __popc(m);
+                };
+                if (list_covers(hs)) list_pass(L, ln, record);
+                else particle_pass<1>(g, cl, nullptr, fi, reach_f32(hs), 0, s_start[warp], s_pref[warp],
+                                      record);
                 __syncwarp();
                 if (nrec > kRecW) hs = -1.0;  // too many to keep: count by walking
             }
@@ -863,25 +890,27 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
                     c += __popc(m);
                 }
             } else {
-                particle_pass<1>(g, cl, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
-                                 [&](bool valid, int j) {
-                                     bool in = false, bd = false;
-                                     if (valid && j != i) {
-                                         const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
-                                         in = r2f < t.tin;
-                                         bd = !in && r2f <= t.tout;
-                                     }
-                                     if (__any_sync(kFull, bd) && bd) {
-                                         if (R2 < 0.0) R2 = __dmul_rn(R, R);
-                                         in = exact_r2(pi, posh[j], g) < R2;
-                                     }
-                                     const unsigned m = __ballot_sync(kFull, in);
-                                     if (in) {
-                                         const int q = c + __popc(m & lt);
-                                         if (q < kGSlab) slab[q] = j;
-                                     }
-                                     c += __popc(m);
-                                 });
+                auto count = [&](bool valid, int j) {
+                    bool in = false, bd = false;
+                    if (valid && j != i) {
+                        const float r2f = f_r2(fi, __ldg(&fpos[j]), g);
+                        in = r2f < t.tin;
+                        bd = !in && r2f <= t.tout;
+                    }
+                    if (__any_sync(kFull, bd) && bd) {
+                        if (R2 < 0.0) R2 = __dmul_rn(R, R);
+                        in = exact_r2(pi, posh[j], g) < R2;
+                    }
+                    const unsigned m = __ballot_sync(kFull, in);
+                    if (in) {
+                        const int q = c + __popc(m & lt);
+                        if (q < kGSlab) slab[q] = j;
+                    }
+                    c += __popc(m);
+                };
+                if (list_covers(h)) list_pass(L, ln, count);
+                else particle_pass<1>(g, cl, nullptr, fi, reach_f32(h), 0, s_start[warp], s_pref[warp],
+                                      count);
             }
             cnt = c;
             if (cnt >= lowb && cnt <= highb) {
@@ -1221,7 +1250,8 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
                                                  c->order[c->cur], c->lst, c->lmeta);
     k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(B, posh, c->fpos, c->cells, c->nnb,
                                                        c->ngather, c->rslab, c->hs_lo, c->hs_hi,
-                                                       c->hs_it, c->wl, c->status);
+                                                       c->hs_it, c->wl, c->status,
+                                                       c->order[c->cur], c->lst, c->lmeta);
     k_finalize_h<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ocnt, c->xpk);
     const unsigned gx = (unsigned)std::max(2, kReduceBlocks / c->ninst);
     k_cell_hmax<<<dim3(gx, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->grid, c->cells, posh,

@@ -109,7 +109,6 @@ constexpr int kUnionBlocksPerSM = 4;  // resident blocks of the persistent h sea
 // lists of the 32 slots of a warp are stored interleaved (entry e of slot i at
 // ((i / 32) kList + e) 32 + i % 32), so a warp reads 32 entries at once.
 constexpr int kList = 192;                    // list entries per particle
-constexpr double kListSkinDefault = 0.15;     // sph_params.list_skin = 0 selects it
 struct LMeta {     // per caller index, written by the instance's last list build
     float x, y, z;   // the particle's position then (truncated floats)
     float rad;       // list radius (a lower bound): all j within it then are listed
@@ -235,7 +234,7 @@ inline KParams kparams(const sph_params* p) {
     k.sinc_n = p->sinc_n;
     k.inv_rho0 = p->rho0 != 0.0 ? 1.0 / p->rho0 : 0.0;
     k.tait_k = p->c0 * p->c0 * p->rho0 / 7.0;
-    k.list_skin = p->list_skin < 0.0 ? 0.0 : (p->list_skin > 0.0 ? p->list_skin : kListSkinDefault);
+    k.list_skin = p->list_skin > 0.0 ? p->list_skin : 0.0;
     if (p->kernel == KER_WENDLAND) {
         k.wnorm = 21.0 / (16.0 * kPi);
         k.dnorm = 105.0 / (16.0 * kPi);

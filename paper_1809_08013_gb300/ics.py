@@ -79,8 +79,8 @@ class SphParams:
     kernel: int = KERNEL_M4      # 0 M4 cubic spline, 1 Wendland C2, 2 sinc
     gradients: int = GRAD_KERNEL # 0 kernel derivatives, 1 IAD
     sinc_n: int = 5              # exponent of the sinc kernel (2..12)
-    list_skin: float = 0.0       # h-search candidate lists' skin (0 = library default,
-                                 # < 0 = no lists; the oracle has none)
+    list_skin: float = 0.0       # h-search candidate lists' skin (> 0 turns them on;
+                                 # the oracle has none)
 
     def as_dict(self) -> dict:
         return dataclasses.asdict(self)

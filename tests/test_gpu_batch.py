@@ -180,7 +180,6 @@ def test_batch_step_replays_from_a_cuda_graph(B):
         for k in B.STATE_FIELDS:
             arr[k].copy_(ic[k])
         arr["time"].zero_()
-        ctx.lists_clear()  # each replay starts as the eager run did
         g.replay()
         torch.cuda.synchronize()
         assert ctx.sync() in (B.SPH_OK, B.SPH_E_HNOCONV)

@@ -41,7 +41,6 @@ def _case(side, seed, precision=0):
 
 def _run(B, ctx, s, prm, nsteps, timing, calls=1):
     arr = B.alloc_arrays(s)
-    ctx.lists_clear()  # every run starts as on a fresh context
     ctx.timing_enable(timing)
     for _ in range(calls):
         ctx.step(prm, arr, nsteps=nsteps)
@@ -105,7 +104,6 @@ def test_step_inside_a_callers_capture(B):
     ic = {k: arr[k].clone() for k in B.STATE_FIELDS}
     stream = torch.cuda.Stream()
     ctx.step(prm, arr, nsteps=1, stream=stream)  # first use outside the capture
-    ctx.lists_clear(stream=stream)  # the replay starts as a fresh context
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for k in B.STATE_FIELDS:

@@ -28,7 +28,7 @@ def B():
     return binding
 
 
-def _case(name, skin=0.0, precision=0):
+def _case(name, skin=0.15, precision=0):
     if name == "patch":  # periodic z, viscosity active; large enough that a warp's
         # search boxes at the list radius span less than a quarter of the period
         s, p = ics.square_patch(48, seed=51)

@@ -160,7 +160,6 @@ def test_split_run_equals_one_run(B, precision):
     one = B.alloc_arrays(s)
     ctx.step(prm, one, nsteps=5)
     two = B.alloc_arrays(s)
-    ctx.lists_clear()  # the second run starts as the first did
     ctx.step(prm, two, nsteps=2)
     ctx.step(prm, two, nsteps=3)
     ctx.sync()
