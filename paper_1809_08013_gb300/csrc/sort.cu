@@ -155,7 +155,7 @@ constexpr long long kKeyMax = 0x7fffffffffffffffLL, kKeyMin = -kKeyMax - 1;
 
 // Bounding-box partials: min x, y, z and max x, y, z, h, m, |v| (largest
 // component), u (as keys) and the sum of h over the particles of each group
-// of kSlotAlign slots (one instance), one warp per group, reduced in a fixed
+// of kBoxGroup slots (one instance), one warp per group, reduced in a fixed
 // order; with candidate lists also the largest displacement since the last
 // list build, the smallest list slack (list radius - 2h), and the largest and
 // smallest build stamp. Stored as kBoxStride doubles per group: mn[3],
@@ -191,6 +191,10 @@ __device__ __forceinline__ void box_warp_reduce(BoxPart& b) {
     }
 }
 
+static_assert(kSlotAlign % kBoxGroup == 0 && kBoxGroup % 32 == 0, "bbox groups");
+
+// LISTS: some instance keeps candidate lists (their statistics are gathered).
+template <bool LISTS>
 __global__ void __launch_bounds__(kThreads)
 k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
        const double4_32a* __restrict__ velm, const double* __restrict__ ue,
@@ -198,19 +202,19 @@ k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
        double* __restrict__ part, unsigned* __restrict__ status) {
     const int lane = threadIdx.x & 31;
     const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (grp * kSlotAlign >= n) return;  // warp-uniform
-    const int inst = slot_inst(B, grp * kSlotAlign);
+    if (grp * kBoxGroup >= n) return;  // warp-uniform
+    const int inst = slot_inst(B, grp * kBoxGroup);
     const int64_t end = __ldg(&B.ioff[inst]) + __ldg(&B.icnt[inst]);
     const KParams& kp = B.kp[inst];
-    const bool lists = kp.list_skin > 0.0;
+    const bool lists = LISTS && kp.list_skin > 0.0;
     const bool per = kp.periodic_z != 0;
     const float lzf = (float)kp.lz, hlzf = 0.5f * lzf;
     BoxPart b;
     box_init(b);
     bool bad = false;
 #pragma unroll
-    for (int q = 0; q < kSlotAlign / 32; ++q) {
-        const int64_t k = grp * kSlotAlign + q * 32 + lane;
+    for (int q = 0; q < kBoxGroup / 32; ++q) {
+        const int64_t k = grp * kBoxGroup + q * 32 + lane;
         if (k < end) {
             // a particle outside the geometry range (NaN, infinity, beyond the
             // FP32 range) is reported and kept out of the box and the means:
@@ -295,8 +299,8 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
              unsigned* __restrict__ lctr) {
     const int inst = blockIdx.x;
     const int64_t n = B.icnt[inst];
-    const int64_t b0 = B.ioff[inst] / kSlotAlign;
-    const int64_t nbk = (n + kSlotAlign - 1) / kSlotAlign;
+    const int64_t b0 = B.ioff[inst] / kBoxGroup;
+    const int64_t nbk = (n + kBoxGroup - 1) / kBoxGroup;
     BoxPart v;
     box_init(v);
     for (int64_t b = threadIdx.x; b < nbk; b += blockDim.x) {
@@ -661,12 +665,18 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const Batch B = batch_of(c);
     c->launches += 1;
-    if (nb > 0) {  // one warp per group of kSlotAlign slots
+    if (nb > 0) {  // one warp per group of kBoxGroup slots
         c->launches += 1;
-        const int64_t groups = (n + kSlotAlign - 1) / kSlotAlign;
-        k_bbox<<<(unsigned)((groups * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-            n, B, c->posh[c->cur], c->velm[c->cur], c->ue[c->cur], c->order[c->cur], c->lmeta,
-            c->red_part, c->status);
+        const int64_t groups = (n + kBoxGroup - 1) / kBoxGroup;
+        const unsigned gb = (unsigned)((groups * 32 + kThreads - 1) / kThreads);
+        if (c->any_lists)
+            k_bbox<true><<<gb, kThreads, 0, s>>>(n, B, c->posh[c->cur], c->velm[c->cur],
+                                                 c->ue[c->cur], c->order[c->cur], c->lmeta,
+                                                 c->red_part, c->status);
+        else
+            k_bbox<false><<<gb, kThreads, 0, s>>>(n, B, c->posh[c->cur], c->velm[c->cur],
+                                                  c->ue[c->cur], c->order[c->cur], c->lmeta,
+                                                  c->red_part, c->status);
     }
     k_grid_setup<<<c->ninst, kGridThreads, 0, s>>>(c->red_part, B, c->grid, c->status, c->wctr,
                                                     c->lctr);

@@ -192,7 +192,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->cells, (size_t)c->cellcap) && al(&c->cell_hmax, (size_t)c->cellcap) &&
          al(&c->nnb, N) && al(&c->ngather, N) && al(&c->rowlen, N) &&
          al(&c->offsets, N + 1) && al(&c->row_part, (size_t)scan_parts(N) + 1) &&
-         al(&c->idx, (size_t)nnzcap) && al(&c->red_part, nfb * kBoxStride) &&
+         al(&c->idx, (size_t)nnzcap) && al(&c->red_part, (N + kBoxGroup - 1) / kBoxGroup * kBoxStride) &&
          al(&c->dt_part, nfb * kMaxPairThreads) && al(&c->grid, (size_t)max_instances) &&
          al(&c->status, 4) && al(&c->blk, nfb) &&
          al(&c->ioff, (size_t)max_instances + 1) && al(&c->icnt, (size_t)max_instances) &&
@@ -310,6 +310,7 @@ void lists_clear(sph_ctx* c, cudaStream_t s) {
 void launch_set_single(sph_ctx* c, const KParams& kp, int64_t n, cudaStream_t s) {
     const int64_t zero = 0;
     lists_for_layout(c, 1, &zero, &n, s);
+    c->any_lists = kp.list_skin > 0.0;
     c->n = n;
     c->ntot = n;
     c->cext = n;
@@ -362,8 +363,8 @@ void drop_step_graphs(sph_ctx* c) {
 // them, so the results are the same bits.
 bool step_graph(sph_ctx* c, double* dt, double* time, cudaStream_t s) {
     const int par = c->cur;
-    const int64_t key[9] = {c->n, c->ntot, c->ninst, c->prec, c->tpp, c->kern_kind, c->grad_kind,
-                            (int64_t)(intptr_t)dt, (int64_t)(intptr_t)time};
+    const int64_t key[10] = {c->n, c->ntot, c->ninst, c->prec, c->tpp, c->kern_kind, c->grad_kind,
+                             (int64_t)(intptr_t)dt, (int64_t)(intptr_t)time, c->any_lists ? 1 : 0};
     sph_ctx::StepGraph& g = c->sg[par];
     if (!g.valid || memcmp(g.key, key, sizeof key) != 0) {
         if (g.valid) cudaGraphExecDestroy(g.exec);
@@ -984,6 +985,8 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const
     DeviceGuard dg(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     lists_for_layout(c, ninst, coff.data(), icnt.data(), s);
+    c->any_lists = false;
+    for (int k = 0; k < ninst; ++k) c->any_lists = c->any_lists || kpi[k].list_skin > 0.0;
     cudaError_t e = cudaMemcpyAsync(c->ioff, ioff.data(), (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->coff, coff.data(), (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->icnt, icnt.data(), ninst * sizeof(int64_t), cudaMemcpyHostToDevice, s);

@@ -31,6 +31,7 @@ constexpr int kScanTile = kThreads * 8;             // elements per block in sca
 constexpr int kReduceBlocks = 304;                  // 2 x 152 SMs
 constexpr int kMaxPairThreads = 8;                  // lanes per particle in the pair kernels
 constexpr int kBoxStride = 16;                      // doubles per bounding-box partial
+constexpr int kBoxGroup = 64;                       // slots per bounding-box partial (one warp)
 
 // device status word
 enum : unsigned {
@@ -308,7 +309,7 @@ struct sph_ctx {
     double *hs_lo, *hs_hi;  // bisection bracket of particles handed to the per-particle search
     int32_t* hs_it;         // counts already done for them
     int32_t* wl;            // their indices (count in status[3])
-    double* red_part;       // bbox partials: kBoxStride per group of kSlotAlign slots
+    double* red_part;       // bbox partials: kBoxStride per group of kBoxGroup slots
     double* dt_part;        // per force block (kMaxPairThreads per kThreads slots)
     sph::Grid* grid;        // per instance
     unsigned long long* wctr;  // work counters of persistent kernels (zeroed per build)
@@ -316,6 +317,7 @@ struct sph_ctx {
     int32_t* lst;           // candidate lists: kList per slot (warp-interleaved)
     sph::LMeta* lmeta;      // their records, per caller index
     unsigned* lctr;         // list builds so far (stamps)
+    bool any_lists;         // some instance of the current batch uses candidate lists
     int lay_n;              // instances of the last batch layout (first, count) ...
     int64_t lay_first[sph::kMaxInstances], lay_cnt[sph::kMaxInstances];  // ... and theirs
     int nsm;                // streaming multiprocessors of the device
@@ -341,7 +343,8 @@ struct sph_ctx {
     // sph_step / sph_batch_step instead of its ~35 separate launches.
     struct StepGraph {
         bool valid;
-        int64_t key[9];          // what the launches bake in (sizes, kinds, dt/time pointers)
+        int64_t key[10];         // what the launches bake in (sizes, kinds, dt/time pointers,
+                                 // the bounding-box variant)
         cudaGraphExec_t exec;
         int64_t launches;        // kernels of one step
     } sg[2];
