@@ -155,7 +155,8 @@ constexpr long long kKeyMax = 0x7fffffffffffffffLL, kKeyMin = -kKeyMax - 1;
 
 // Bounding-box partials: min x, y, z and max x, y, z, h, m, |v| (largest
 // component), u (as keys) and the sum of h over the particles of each group
-// of kBoxGroup slots (one instance), one warp per group, reduced in a fixed
+// of kSlotAlign slots (one instance), one block of kSlotAlign / kBoxWarpSlots
+// warps per group, reduced in a fixed
 // order; with candidate lists also the largest displacement since the last
 // list build, the smallest list slack (list radius - 2h), and the largest and
 // smallest build stamp. Stored as kBoxStride doubles per group: mn[3],
@@ -174,6 +175,8 @@ __device__ __forceinline__ void box_init(BoxPart& b) {
     b.hs = 0.0;
 }
 
+// Fixed-order warp reduction of the first NMAX maxima (the others untouched).
+template <int NMAX = kBoxMax>
 __device__ __forceinline__ void box_warp_reduce(BoxPart& b) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -183,7 +186,7 @@ __device__ __forceinline__ void box_warp_reduce(BoxPart& b) {
             b.mn[d] = v < b.mn[d] ? v : b.mn[d];
         }
 #pragma unroll
-        for (int d = 0; d < kBoxMax; ++d) {
+        for (int d = 0; d < NMAX; ++d) {
             const long long v = __shfl_xor_sync(0xffffffffu, b.mx[d], o);
             b.mx[d] = v > b.mx[d] ? v : b.mx[d];
         }
@@ -191,19 +194,20 @@ __device__ __forceinline__ void box_warp_reduce(BoxPart& b) {
     }
 }
 
-static_assert(kSlotAlign % kBoxGroup == 0 && kBoxGroup % 32 == 0, "bbox groups");
+static_assert(kSlotAlign % kBoxWarpSlots == 0 && kBoxWarpSlots % 32 == 0, "bbox groups");
+constexpr int kBoxThreads = kSlotAlign / kBoxWarpSlots * 32;  // one block per group
 
 // LISTS: some instance keeps candidate lists (their statistics are gathered).
 template <bool LISTS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kBoxThreads)
 k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
        const double4_32a* __restrict__ velm, const double* __restrict__ ue,
        const int32_t* __restrict__ order, const LMeta* __restrict__ lmeta,
        double* __restrict__ part, unsigned* __restrict__ status) {
-    const int lane = threadIdx.x & 31;
-    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (grp * kBoxGroup >= n) return;  // warp-uniform
-    const int inst = slot_inst(B, grp * kBoxGroup);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t grp = blockIdx.x;  // group of kSlotAlign slots (< n: one block per group)
+    const int64_t w0 = grp * kSlotAlign + (int64_t)warp * kBoxWarpSlots;
+    const int inst = slot_inst(B, grp * kSlotAlign);
     const int64_t end = __ldg(&B.ioff[inst]) + __ldg(&B.icnt[inst]);
     const KParams& kp = B.kp[inst];
     const bool lists = LISTS && kp.list_skin > 0.0;
@@ -213,8 +217,8 @@ k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
     box_init(b);
     bool bad = false;
 #pragma unroll
-    for (int q = 0; q < kBoxGroup / 32; ++q) {
-        const int64_t k = grp * kBoxGroup + q * 32 + lane;
+    for (int q = 0; q < kBoxWarpSlots / 32; ++q) {
+        const int64_t k = w0 + q * 32 + lane;
         if (k < end) {
             // a particle outside the geometry range (NaN, infinity, beyond the
             // FP32 range) is reported and kept out of the box and the means:
@@ -267,12 +271,23 @@ k_bbox(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, (unsigned)ST_NONFINITE);
-    box_warp_reduce(b);
-    if (lane == 0) {
+    // without lists the list fields are neither reduced nor written (nothing reads them)
+    constexpr int NMAX = LISTS ? kBoxMax : BX_D;
+    box_warp_reduce<NMAX>(b);
+    __shared__ BoxPart wb[kBoxThreads / 32];
+    if (lane == 0) wb[warp] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the block's warps in order: a fixed summation order
+        BoxPart a = wb[0];
+        for (int w = 1; w < kBoxThreads / 32; ++w) {
+            for (int d = 0; d < 3; ++d) a.mn[d] = wb[w].mn[d] < a.mn[d] ? wb[w].mn[d] : a.mn[d];
+            for (int d = 0; d < NMAX; ++d) a.mx[d] = wb[w].mx[d] > a.mx[d] ? wb[w].mx[d] : a.mx[d];
+            a.hs += wb[w].hs;
+        }
         double* o = part + grp * kBoxStride;
-        for (int d = 0; d < 3; ++d) o[d] = __longlong_as_double(b.mn[d]);
-        for (int d = 0; d < kBoxMax; ++d) o[3 + d] = __longlong_as_double(b.mx[d]);
-        o[3 + kBoxMax] = b.hs;
+        for (int d = 0; d < 3; ++d) o[d] = __longlong_as_double(a.mn[d]);
+        for (int d = 0; d < NMAX; ++d) o[3 + d] = __longlong_as_double(a.mx[d]);
+        o[3 + kBoxMax] = a.hs;
     }
 }
 
@@ -299,35 +314,47 @@ k_grid_setup(const double* __restrict__ part, Batch B, Grid* __restrict__ grid,
              unsigned* __restrict__ lctr) {
     const int inst = blockIdx.x;
     const int64_t n = B.icnt[inst];
-    const int64_t b0 = B.ioff[inst] / kBoxGroup;
-    const int64_t nbk = (n + kBoxGroup - 1) / kBoxGroup;
-    BoxPart v;
-    box_init(v);
-    for (int64_t b = threadIdx.x; b < nbk; b += blockDim.x) {
-        const double* o = part + (b0 + b) * kBoxStride;
-        for (int d = 0; d < 3; ++d) {
-            const long long k = __double_as_longlong(o[d]);
-            v.mn[d] = k < v.mn[d] ? k : v.mn[d];
-        }
-        for (int d = 0; d < kBoxMax; ++d) {
-            const long long k = __double_as_longlong(o[3 + d]);
-            v.mx[d] = k > v.mx[d] ? k : v.mx[d];
-        }
-        v.hs += o[3 + kBoxMax];
+    const int64_t b0 = B.ioff[inst] / kSlotAlign;
+    const int64_t nbk = (n + kSlotAlign - 1) / kSlotAlign;
+    // field f = t % 16 of every 64th partial from partial t / 16 on: each
+    // load instruction of a warp reads two whole partials. Fields 0-2 are
+    // minima, 3 .. 3 + kBoxMax - 1 maxima, 3 + kBoxMax the sum of h.
+    static_assert(kBoxStride == 16 && 3 + kBoxMax < kBoxStride, "bbox partial layout");
+    const int f = threadIdx.x & 15;
+    const bool fmin_ = f < 3, fsum = f == 3 + kBoxMax;
+    long long acc = fmin_ ? kKeyMax : kKeyMin;
+    double hsum = 0.0;
+    const double* base = part + b0 * kBoxStride + f;
+    for (int64_t b = threadIdx.x >> 4; b < nbk; b += kGridThreads / 16) {
+        const double v = base[b * kBoxStride];
+        const long long k = __double_as_longlong(v);
+        if (fmin_) acc = k < acc ? k : acc;
+        else acc = k > acc ? k : acc;
+        if (fsum) hsum += v;
     }
-    box_warp_reduce(v);
-    __shared__ BoxPart sh[kGridThreads / 32];
+    // lanes l and l + 16 hold the same field: combine, lower lane first (a
+    // fixed order), then the warps in order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {
+        const long long ok = __shfl_xor_sync(0xffffffffu, acc, 16);
+        const double oh = __shfl_xor_sync(0xffffffffu, hsum, 16);
+        acc = fmin_ ? (ok < acc ? ok : acc) : (ok > acc ? ok : acc);
+        hsum = lane < 16 ? hsum + oh : oh + hsum;
+    }
+    __shared__ long long wk[kGridThreads / 32][16];
+    __shared__ double wh[kGridThreads / 32];
+    if (lane < 16) wk[warp][lane] = acc;
+    if (lane == 3 + kBoxMax) wh[warp] = hsum;
+    __syncthreads();
     __shared__ double r[11];
     __shared__ long long lk[4];  // list keys: displacement, -slack, stamp, -stamp
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
     if (threadIdx.x == 0) {
-        BoxPart a = sh[0];
-        for (int w = 1; w < kGridThreads / 32; ++w) {
-            for (int d = 0; d < 3; ++d) a.mn[d] = sh[w].mn[d] < a.mn[d] ? sh[w].mn[d] : a.mn[d];
-            for (int d = 0; d < kBoxMax; ++d) a.mx[d] = sh[w].mx[d] > a.mx[d] ? sh[w].mx[d] : a.mx[d];
-            a.hs += sh[w].hs;
+        BoxPart a;
+        box_init(a);
+        for (int w = 0; w < kGridThreads / 32; ++w) {
+            for (int d = 0; d < 3; ++d) a.mn[d] = wk[w][d] < a.mn[d] ? wk[w][d] : a.mn[d];
+            for (int d = 0; d < kBoxMax; ++d) a.mx[d] = wk[w][3 + d] > a.mx[d] ? wk[w][3 + d] : a.mx[d];
+            a.hs += wh[w];
         }
         // the layout the grid derivation below reads: min x, y, z, -max x, y, z, -max h, sum h
         for (int d = 0; d < 3; ++d) {
@@ -665,16 +692,15 @@ void launch_build_cells(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     const Batch B = batch_of(c);
     c->launches += 1;
-    if (nb > 0) {  // one warp per group of kBoxGroup slots
+    if (nb > 0) {  // one block per group of kSlotAlign slots
         c->launches += 1;
-        const int64_t groups = (n + kBoxGroup - 1) / kBoxGroup;
-        const unsigned gb = (unsigned)((groups * 32 + kThreads - 1) / kThreads);
+        const unsigned gb = (unsigned)((n + kSlotAlign - 1) / kSlotAlign);
         if (c->any_lists)
-            k_bbox<true><<<gb, kThreads, 0, s>>>(n, B, c->posh[c->cur], c->velm[c->cur],
+            k_bbox<true><<<gb, kBoxThreads, 0, s>>>(n, B, c->posh[c->cur], c->velm[c->cur],
                                                  c->ue[c->cur], c->order[c->cur], c->lmeta,
                                                  c->red_part, c->status);
         else
-            k_bbox<false><<<gb, kThreads, 0, s>>>(n, B, c->posh[c->cur], c->velm[c->cur],
+            k_bbox<false><<<gb, kBoxThreads, 0, s>>>(n, B, c->posh[c->cur], c->velm[c->cur],
                                                   c->ue[c->cur], c->order[c->cur], c->lmeta,
                                                   c->red_part, c->status);
     }

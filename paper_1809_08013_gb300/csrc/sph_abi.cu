@@ -192,7 +192,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->cells, (size_t)c->cellcap) && al(&c->cell_hmax, (size_t)c->cellcap) &&
          al(&c->nnb, N) && al(&c->ngather, N) && al(&c->rowlen, N) &&
          al(&c->offsets, N + 1) && al(&c->row_part, (size_t)scan_parts(N) + 1) &&
-         al(&c->idx, (size_t)nnzcap) && al(&c->red_part, (N + kBoxGroup - 1) / kBoxGroup * kBoxStride) &&
+         al(&c->idx, (size_t)nnzcap) && al(&c->red_part, (N + kSlotAlign - 1) / kSlotAlign * kBoxStride) &&
          al(&c->dt_part, nfb * kMaxPairThreads) && al(&c->grid, (size_t)max_instances) &&
          al(&c->status, 4) && al(&c->blk, nfb) &&
          al(&c->ioff, (size_t)max_instances + 1) && al(&c->icnt, (size_t)max_instances) &&

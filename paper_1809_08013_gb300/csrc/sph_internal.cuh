@@ -31,7 +31,7 @@ constexpr int kScanTile = kThreads * 8;             // elements per block in sca
 constexpr int kReduceBlocks = 304;                  // 2 x 152 SMs
 constexpr int kMaxPairThreads = 8;                  // lanes per particle in the pair kernels
 constexpr int kBoxStride = 16;                      // doubles per bounding-box partial
-constexpr int kBoxGroup = 64;                       // slots per bounding-box partial (one warp)
+constexpr int kBoxWarpSlots = 64;                   // bounding box: slots per warp (4 per partial)
 
 // device status word
 enum : unsigned {
@@ -309,7 +309,7 @@ struct sph_ctx {
     double *hs_lo, *hs_hi;  // bisection bracket of particles handed to the per-particle search
     int32_t* hs_it;         // counts already done for them
     int32_t* wl;            // their indices (count in status[3])
-    double* red_part;       // bbox partials: kBoxStride per group of kBoxGroup slots
+    double* red_part;       // bbox partials: kBoxStride per group of kSlotAlign slots
     double* dt_part;        // per force block (kMaxPairThreads per kThreads slots)
     sph::Grid* grid;        // per instance
     unsigned long long* wctr;  // work counters of persistent kernels (zeroed per build)
