@@ -444,7 +444,7 @@ __device__ __forceinline__ void union_group(
     // build step walks every lane, recording its list (every candidate within
     // 2 h (1 + skin)) in the first walk.
     const bool build = kp.list_skin > 0.0 && g->lbuild != 0;
-    const int32_t id = valid ? __ldg(&order[i]) : 0;
+    const int32_t id = valid && kp.list_skin > 0.0 ? __ldg(&order[i]) : 0;
     int32_t* lrow = lst + (i >> 5) * (int64_t)kList * 32 + (i & 31);
     int nl = 0;
     bool listed = false;
@@ -1239,10 +1239,13 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
     double4_32a* posh = c->posh[c->cur];
     const Batch B = batch_of(c);
-    c->launches += 5;
-    k_h_lists<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->nnb, c->ngather, c->rslab, c->hs_lo,
-                                      c->hs_hi, c->hs_it, c->wl, c->status, c->order[c->cur],
-                                      c->lst, c->lmeta);
+    c->launches += 4;
+    if (c->any_lists) {
+        c->launches += 1;
+        k_h_lists<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->nnb, c->ngather, c->rslab,
+                                          c->hs_lo, c->hs_hi, c->hs_it, c->wl, c->status,
+                                          c->order[c->cur], c->lst, c->lmeta);
+    }
     const int64_t nbu = std::min<int64_t>((int64_t)c->nsm * kUnionBlocksPerSM, ((n + 31) / 32 + 7) / 8);
     k_h_union<<<(unsigned)nbu, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb,
                                                  c->ngather, c->rslab, c->hs_lo, c->hs_hi,
