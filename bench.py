@@ -89,18 +89,18 @@ FLOPS_PAIR_TABLE = 75
 # the files listed, in order); otherwise the bench reports null.
 NCU_EVIDENCE = {
     # k_forces_df<2, M4>, the 1M patch, second step of the timed call
-    "df": {"sources": ("physics_df.cu", "df.cuh"), "sha1": "e063ee94a704ce3325525b197e19f8c797befef7",
-           "dram_bytes": (697.38 + 44.54) * 1e6, "warp_inst": 1751439991,
-           "issue_active": 71.65, "pairs": 100727656,
+    "df": {"sources": ("physics_df.cu", "df.cuh"), "sha1": "7b55f361a012446c9ecf6a3dbf7b6ac7e10f3b34",
+           "dram_bytes": (697.76 + 44.33) * 1e6, "warp_inst": 1751314991,
+           "issue_active": 71.63, "pairs": 100727656,
            "profile": "profiles/forces_patch1m_evrard1m.md"},
     # k_forces_mx<2>, the 1M Evrard sphere, mixed precision
-    "mixed": {"sources": ("physics_mixed.cu", "df.cuh"), "sha1": "62a1cff61fe2b67223df985bfc8f6152db92922e",
-              "dram_bytes": (650.83 + 38.13) * 1e6, "warp_inst": 583622306,
-              "issue_active": 47.52, "pairs": 105700202,
+    "mixed": {"sources": ("physics_mixed.cu", "df.cuh"), "sha1": "342c531574d34f46723d3a8d907325d05aed3aee",
+              "dram_bytes": (650.91 + 37.92) * 1e6, "warp_inst": 583622306,
+              "issue_active": 47.63, "pairs": 105700202,
               "profile": "profiles/forces_patch1m_evrard1m.md"},
     # k_forces<M4>, the 1M patch, native FP64 pair sums
-    "fp64": {"sources": ("physics.cu",), "sha1": "e1c18ffb358bfc857d1d8256d7a10aee2bc36ffd",
-             "dram_bytes": (654.58 + 37.76) * 1e6, "warp_inst": 1248076044,
+    "fp64": {"sources": ("physics.cu",), "sha1": "6247f00dbf82cc04d06456dd9af9a433de9cf7fe",
+             "dram_bytes": (654.77 + 37.64) * 1e6, "warp_inst": 1248076044,
              "issue_active": 7.48, "pairs": 100727656,
              "profile": "profiles/forces_patch1m_evrard1m.md"},
 }
