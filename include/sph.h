@@ -136,7 +136,11 @@ typedef struct {
                             when one no longer covers its particle's 2 h. Above 1:
                             SPH_E_INVAL. On GB300 the cell walk, which loads each
                             candidate once for a warp of 32 particles, is the faster of
-                            the two for the benchmark workloads. Lists are kept per
+                            the two for the benchmark workloads. The first call that
+                            turns the lists on allocates their buffers (about 800 B per
+                            particle of capacity, not counted by sph_ctx_bytes; that call
+                            synchronises the device and is not capturable, SPH_E_NOMEM
+                            if the allocation fails). Lists are kept per
                             caller index: a batch instance whose caller range reaches
                             past the context's capacity runs without them. A tuning
                             knob: h and the neighbour sets do not depend on it (the

@@ -46,6 +46,8 @@ sph_status check_launch(sph_ctx* c, const char* where) {
     return SPH_OK;
 }
 
+sph_status ensure_lists(sph_ctx* c);
+
 sph_status check_params(sph_ctx* c, const sph_params* p) {
     if (!p) { set_err(c, "params is NULL"); return SPH_E_INVAL; }
     if (p->eos != 0 && p->eos != 1) { set_err(c, "eos must be 0 or 1"); return SPH_E_INVAL; }
@@ -85,6 +87,7 @@ sph_status check_params(sph_ctx* c, const sph_params* p) {
     if (p->periodic_z && !(p->lz > 0.0)) { set_err(c, "periodic_z needs lz > 0"); return SPH_E_INVAL; }
     if (!(p->list_skin <= 1.0)) { set_err(c, "list_skin must be at most 1"); return SPH_E_INVAL; }
     if (!(p->cfl > 0.0)) { set_err(c, "cfl must be > 0"); return SPH_E_INVAL; }
+    if (p->list_skin > 0.0) return ensure_lists(c);
     return SPH_OK;
 }
 
@@ -110,6 +113,32 @@ bool dalloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
     return cudaMalloc((void**)p, count * sizeof(T)) == cudaSuccess;
+}
+
+// The buffers of the h search's candidate lists, allocated (and cleared) by
+// the first call whose parameters turn the lists on: kList entries and a
+// 32-byte record per slot, ~800 B per particle of capacity.
+sph_status ensure_lists(sph_ctx* c) {
+    if (c->lmeta) return SPH_OK;
+    const size_t N = (size_t)std::max<int64_t>(c->nslots, 1);
+    DeviceGuard dg(c->device);
+    const bool ok = dalloc(&c->lst, (N + 31) / 32 * 32 * kList) && dalloc(&c->lmeta, N) &&
+                    dalloc(&c->lctr, 1) &&
+                    cudaMemset(c->lmeta, 0, N * sizeof(LMeta)) == cudaSuccess &&
+                    cudaMemset(c->lctr, 0, sizeof(unsigned)) == cudaSuccess &&
+                    cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (c->lst) cudaFree(c->lst);
+        if (c->lmeta) cudaFree(c->lmeta);
+        if (c->lctr) cudaFree(c->lctr);
+        c->lst = nullptr;
+        c->lmeta = nullptr;
+        c->lctr = nullptr;
+        set_err(c, "candidate lists: device allocation failed");
+        return SPH_E_NOMEM;
+    }
+    return SPH_OK;
 }
 
 void free_all(sph_ctx* c) {
@@ -202,8 +231,7 @@ bool allocate_all(sph_ctx* c, int64_t nslots, Allocator& al) {
          al(&c->hs_lo, N) && al(&c->hs_hi, N) && al(&c->hs_it, N) && al(&c->wl, N) &&
          al(&c->scratch_scalar, 2) && al(&c->tune_dt, 2 * (size_t)max_instances) &&
          al(&c->wctr, 4) &&
-         al(&c->recs, (size_t)c->nsm * kUnionBlocksPerSM * kThreads * kRec) &&
-         al(&c->lst, (N + 31) / 32 * 32 * kList) && al(&c->lmeta, N) && al(&c->lctr, 1);
+         al(&c->recs, (size_t)c->nsm * kUnionBlocksPerSM * kThreads * kRec);
     return ok;
 }
 
@@ -285,7 +313,7 @@ k_set_single(KParams kp, int64_t n, long long cap, int64_t nblk, int32_t* __rest
 // keeps its lists; whether they still hold is checked on the device.
 void lists_for_layout(sph_ctx* c, int ninst, const int64_t* first, const int64_t* cnt,
                       cudaStream_t s) {
-    for (int k = 0; k < ninst; ++k) {
+    for (int k = 0; k < ninst && c->lmeta; ++k) {
         bool seen = false;
         for (int q = 0; q < c->lay_n && !seen; ++q)
             seen = c->lay_first[q] == first[k] && c->lay_cnt[q] == cnt[k];
@@ -302,7 +330,7 @@ void lists_for_layout(sph_ctx* c, int ninst, const int64_t* first, const int64_t
 // Clear the list records of every instance of the current layout (their next
 // step builds).
 void lists_clear(sph_ctx* c, cudaStream_t s) {
-    for (int k = 0; k < c->lay_n; ++k)
+    for (int k = 0; k < c->lay_n && c->lmeta; ++k)
         if (c->lay_cnt[k] > 0 && c->lay_first[k] + c->lay_cnt[k] <= c->ncap)
             cudaMemsetAsync(c->lmeta + c->lay_first[k], 0, (size_t)c->lay_cnt[k] * sizeof(LMeta), s);
 }
@@ -496,7 +524,7 @@ sph_status sph_lists_clear(sph_ctx* c, int64_t first, int64_t count, void* strea
                 (long long)(first + count), (long long)c->ncap);
         return SPH_E_INVAL;
     }
-    if (count == 0) return SPH_OK;
+    if (count == 0 || !c->lmeta) return SPH_OK;  // no lists yet: nothing to forget
     DeviceGuard dg(c->device);
     const cudaError_t e = cudaMemsetAsync(c->lmeta + first, 0, (size_t)count * sizeof(LMeta),
                                           (cudaStream_t)stream);
@@ -510,6 +538,8 @@ sph_status sph_lists_clear(sph_ctx* c, int64_t first, int64_t count, void* strea
 
 sph_status sph_list_builds(sph_ctx* c, int64_t* builds, void* stream) {
     if (!c || !builds) return SPH_E_INVAL;
+    *builds = 0;
+    if (!c->lctr) return SPH_OK;  // lists never turned on
     DeviceGuard dg(c->device);
     unsigned v = 0;
     cudaError_t e = cudaMemcpyAsync(&v, c->lctr, sizeof v, cudaMemcpyDeviceToHost,
@@ -640,6 +670,7 @@ sph_status sph_ctx_create_batch(sph_ctx** out, int64_t ncap, int64_t nnzcap, int
     c->maxinst = max_instances;
     c->ninst = 1;
     c->cellcap = cell_capacity(ncap, max_instances);
+    c->nslots = nslots;
     if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         c->nsm < 1) {
         cudaGetLastError();
@@ -650,9 +681,7 @@ sph_status sph_ctx_create_batch(sph_ctx** out, int64_t ncap, int64_t nnzcap, int
     ok = ok && cudaMallocHost((void**)&c->status_host, 2 * sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemset(c->status, 0, 4 * sizeof(unsigned)) == cudaSuccess &&
          cudaMemset(c->offsets, 0, sizeof(int64_t)) == cudaSuccess &&
-         cudaMemset(c->grid, 0, (size_t)max_instances * sizeof(Grid)) == cudaSuccess &&
-         cudaMemset(c->lmeta, 0, (size_t)std::max<int64_t>(nslots, 1) * sizeof(LMeta)) == cudaSuccess &&
-         cudaMemset(c->lctr, 0, sizeof(unsigned)) == cudaSuccess;
+         cudaMemset(c->grid, 0, (size_t)max_instances * sizeof(Grid)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);

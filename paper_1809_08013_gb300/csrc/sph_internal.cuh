@@ -314,9 +314,10 @@ struct sph_ctx {
     sph::Grid* grid;        // per instance
     unsigned long long* wctr;  // work counters of persistent kernels (zeroed per build)
     int2* recs;             // h search records: kRec per lane of the persistent grid
-    int32_t* lst;           // candidate lists: kList per slot (warp-interleaved)
-    sph::LMeta* lmeta;      // their records, per caller index
-    unsigned* lctr;         // list builds so far (stamps)
+    int64_t nslots;         // slot capacity (particles plus the gaps between instances)
+    int32_t* lst;           // candidate lists: kList per slot (warp-interleaved); these
+    sph::LMeta* lmeta;      // three are allocated by the first call that turns lists on;
+    unsigned* lctr;         // their records per caller index; list builds so far
     bool any_lists;         // some instance of the current batch uses candidate lists
     int lay_n;              // instances of the last batch layout (first, count) ...
     int64_t lay_first[sph::kMaxInstances], lay_cnt[sph::kMaxInstances];  // ... and theirs
