@@ -268,12 +268,9 @@ __device__ __forceinline__ int lane_cell(float v, const Grid* __restrict__ g, in
 // lower bound, so within 2 h for every h still to be tried): those go to the
 // gather slab and the count c at once.
 // BL: also append to the lane's candidate list (slots, entries 32 apart from
-// lrow on; nl of them) every staged candidate with r^2 <= tL. WIDE: the
-// staged candidates keep their own z (a warp spanning more than a quarter of
-// a periodic box), and each lane takes its minimum image (one periodic shift,
-// as the FP32 error bound allows). Padding slots (sidx -1) are never
-// counted, recorded or listed.
-template <bool BL, bool WIDE>
+// lrow on; nl of them) every staged candidate with r^2 <= tL. Padding slots
+// (sidx -1) are never counted, recorded or listed.
+template <bool BL>
 __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const int* __restrict__ sidx,
                                             const float4& fi, const Thr& t, bool active, bool rec,
                                             float tin_lo, int64_t i, double h, double& R2,
@@ -281,18 +278,11 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
                                             int32_t* slab, int& c, int2* recb, int& nrec,
                                             float tL, int32_t* __restrict__ lrow, int& nl) {
     unsigned in = 0u, bd = 0u, lb = 0u;
-    auto r2of = [&](const float4& q) {
-        const float dx = fi.x - q.x, dy = fi.y - q.y;
-        float dz = fi.z - q.z;
-        if (WIDE) {
-            if (dz > g->halflzf) dz -= g->lzf;
-            else if (dz < -g->halflzf) dz += g->lzf;
-        }
-        return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    };
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        const float r2 = r2of(st[k]);
+        const float4 q = st[k];
+        const float dx = fi.x - q.x, dy = fi.y - q.y, dz = fi.z - q.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         if (r2 < t.tin) in |= 1u << k;
         if (r2 <= t.tout) bd |= 1u << k;
         if (BL && r2 <= tL) lb |= 1u << k;
@@ -314,7 +304,9 @@ __device__ __forceinline__ void union_chunk(const float4* __restrict__ st, const
             bd &= bd - 1u;
             const int j = sidx[k];
             if (j == i || j < 0) continue;
-            const float r2 = r2of(st[k]);
+            const float4 q = st[k];
+            const float dx = fi.x - q.x, dy = fi.y - q.y, dz = fi.z - q.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             if (r2 < tin_lo) {
                 if (c < kGSlab) slab[c] = j;
                 ++c;
@@ -484,10 +476,9 @@ __device__ __forceinline__ void union_group(
         const float Rq = blist ? reach_f32(0.5 * RL) : reach_f32(hs);
         const float lzz = wmin(active ? fi.z - Rq : CUDART_INF_F), hzz = wmax(active ? fi.z + Rq : -CUDART_INF_F);
         // Periodic z: candidates are moved to the image nearest a reference lane's
-        // z, which is each lane's minimum image while the warp spans < lz/4; a
-        // wider warp stages them unmoved and each lane takes its own image.
+        // z, which is each lane's minimum image while the warp spans < lz/4.
         const bool wide = per && (hzz - lzz > 0.25f * g->lzf);
-        if (pass > 0 && __popc(am) <= defer) {
+        if ((pass > 0 && __popc(am) <= defer) || wide) {
             if (active) {
                 deferred = true;
                 active = false;
@@ -527,23 +518,6 @@ __device__ __forceinline__ void union_group(
             box_range(sz0, sz1, g, 2, z0, z1);
             int fill = 0;  // staged candidates (warp-uniform)
             const float Rq2 = Rq * Rq;
-            auto chunk = [&]() {  // test the staged candidates (variant by list build and width)
-                if (blist) {
-                    if (wide)
-                        union_chunk<true, true>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g,
-                                                slab, c, recb, nrec, tL, lrow, nl);
-                    else
-                        union_chunk<true, false>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh,
-                                                 g, slab, c, recb, nrec, tL, lrow, nl);
-                } else {
-                    if (wide)
-                        union_chunk<false, true>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh,
-                                                 g, slab, c, recb, nrec, tL, lrow, nl);
-                    else
-                        union_chunk<false, false>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2,
-                                                  posh, g, slab, c, recb, nrec, tL, lrow, nl);
-                }
-            };
             // Query box of the cluster: a candidate within 2h_i (FP64) of one of its
             // lanes lies inside it. The slop (>= 1e-3 cell widths + 1.2e-7 X)
             // covers the FP32 rounding of both coordinates and of the periodic shift.
@@ -583,16 +557,14 @@ __device__ __forceinline__ void union_group(
                             float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
                             if (ok) {
                                 f = __ldg(&fpos[j]);
-                                if (per && !wide) {
+                                if (per) {
                                     const float d = f.z - zc;
                                     if (d > g->halflzf) f.z -= g->lzf;
                                     else if (d < -g->halflzf) f.z += g->lzf;
                                 }
-                                // (a wide cluster filters in x and y only)
-                                const float qx = f.x - ox, qy = f.y - oy;
-                                const float qz = wide ? 0.0f : f.z - oz;
+                                const float qx = f.x - ox, qy = f.y - oy, qz = f.z - oz;
                                 ok = f.x >= bx0 && f.x <= bx1 && f.y >= by0 && f.y <= by1 &&
-                                     (wide || (f.z >= bz0 && f.z <= bz1)) &&
+                                     f.z >= bz0 && f.z <= bz1 &&
                                      fmaf(qz, qz, fmaf(qy, qy, qx * qx)) <= rb2;
                             }
                             const unsigned m = __ballot_sync(kFull, ok);
@@ -607,7 +579,12 @@ __device__ __forceinline__ void union_group(
                                 continue;
                             }
                             __syncwarp();
-                            chunk();
+                            if (blist)
+                                union_chunk<true>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2,
+                                                  posh, g, slab, c, recb, nrec, tL, lrow, nl);
+                            else
+                                union_chunk<false>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2,
+                                                   posh, g, slab, c, recb, nrec, tL, lrow, nl);
                             __syncwarp();
                             if (ok && r >= room) {
                                 st[r - room] = f;
@@ -624,7 +601,12 @@ __device__ __forceinline__ void union_group(
                     sidx[lane] = -1;
                 }
                 __syncwarp();
-                chunk();
+                if (blist)
+                    union_chunk<true>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g, slab,
+                                      c, recb, nrec, tL, lrow, nl);
+                else
+                    union_chunk<false>(st, sidx, fi, t, mine, rec, tin_lo, i, h, R2, posh, g, slab,
+                                       c, recb, nrec, tL, lrow, nl);
                 __syncwarp();
             }
         }
