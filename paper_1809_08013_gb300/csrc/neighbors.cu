@@ -407,6 +407,9 @@ __device__ int count_records(const int2* recb, int nrec, double hh, const Grid* 
 }
 
 // The 32 particles i0 .. i0 + 31 (one per lane; all of one instance).
+// LISTS: the batch has instances with candidate lists (else their code is
+// compiled out).
+template <bool LISTS>
 __device__ __forceinline__ void union_group(
     int64_t i0, int64_t n, const Batch& B, double4_32a* posh, const float4* __restrict__ fpos,
     const int2* __restrict__ cells, int32_t* __restrict__ nnb, int32_t* __restrict__ ngather,
@@ -443,8 +446,8 @@ __device__ __forceinline__ void union_group(
     // Candidate lists: a lane with a kept list was served by k_h_lists. A
     // build step walks every lane, recording its list (every candidate within
     // 2 h (1 + skin)) in the first walk.
-    const bool build = kp.list_skin > 0.0 && g->lbuild != 0;
-    const int32_t id = valid && kp.list_skin > 0.0 ? __ldg(&order[i]) : 0;
+    const bool build = LISTS && kp.list_skin > 0.0 && g->lbuild != 0;
+    const int32_t id = LISTS && valid && kp.list_skin > 0.0 ? __ldg(&order[i]) : 0;
     int32_t* lrow = lst + (i >> 5) * (int64_t)kList * 32 + (i & 31);
     int nl = 0;
     bool listed = false;
@@ -455,7 +458,7 @@ __device__ __forceinline__ void union_group(
                         dfl::from_double(p.z).hi, 0.0f);
         lmeta[id].stamp = g->lstamp;  // (the cell code was recorded by the sort)
         lmeta[id].cnt = 0;
-    } else if (kp.list_skin > 0.0 && active && lmeta[id].cnt > 0) {
+    } else if (LISTS && kp.list_skin > 0.0 && active && lmeta[id].cnt > 0) {
         listed = true;
         active = false;
     }
@@ -745,6 +748,7 @@ k_h_lists(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
 // Persistent: warps take groups of 32 particles from a counter, so a group
 // whose particles straddle far-apart cells (a jump of the Morton curve: a
 // large query box, many candidates) delays one warp, not a whole wave.
+template <bool LISTS>
 __global__ void __launch_bounds__(kThreads, kUnionBlocksPerSM)
 k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos,
           const int2* __restrict__ cells,
@@ -764,7 +768,7 @@ k_h_union(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos
         if (lane == 0) gi = (long long)atomicAdd(wctr, 1ull);
         gi = __shfl_sync(kFull, gi, 0);
         if (gi >= ngroups) break;
-        union_group(gi * 32, n, B, posh, fpos, cells, nnb, ngather, rslab, hs_lo, hs_hi, hs_it,
+        union_group<LISTS>(gi * 32, n, B, posh, fpos, cells, nnb, ngather, rslab, hs_lo, hs_hi, hs_it,
                     wl, status, s_f[warp], s_i[warp],
                     recs + ((int64_t)(blockIdx.x * (kThreads / 32) + warp) * 32 + lane) * kRec,
                     order, lst, lmeta);
@@ -795,6 +799,7 @@ __device__ __forceinline__ void list_pass(const int32_t* __restrict__ L, int ln,
 // the record buffer holds) walks the cells again.
 constexpr int kRecW = 512;  // records per warp
 
+template <bool LISTS>
 __global__ void __launch_bounds__(kThreads)
 k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
             const int2* __restrict__ cells,
@@ -830,7 +835,7 @@ k_h_iterate(Batch B, double4_32a* posh, const float4* __restrict__ fpos,
         int nrec = 0;
         // the particle's kept candidate list, while it covers a radius 2 hq
         // (then it replaces the cell walk: the same candidates within 2 hq)
-        const bool lists = kp.list_skin > 0.0 && !g->lbuild;
+        const bool lists = LISTS && kp.list_skin > 0.0 && !g->lbuild;
         const int ln = lists ? lmeta[order[i]].cnt : 0;
         const float lrad = ln > 0 ? lmeta[order[i]].rad : 0.0f;
         const int32_t* L = lst + (i >> 5) * (int64_t)kList * 32 + (i & 31);
@@ -1247,14 +1252,21 @@ void launch_h_search(sph_ctx* c, cudaStream_t s) {
                                           c->order[c->cur], c->lst, c->lmeta);
     }
     const int64_t nbu = std::min<int64_t>((int64_t)c->nsm * kUnionBlocksPerSM, ((n + 31) / 32 + 7) / 8);
-    k_h_union<<<(unsigned)nbu, kThreads, 0, s>>>(n, B, posh, c->fpos, c->cells, c->nnb,
-                                                 c->ngather, c->rslab, c->hs_lo, c->hs_hi,
-                                                 c->hs_it, c->wl, c->status, c->wctr, c->recs,
-                                                 c->order[c->cur], c->lst, c->lmeta);
-    k_h_iterate<<<kReduceBlocks * 4, kThreads, 0, s>>>(B, posh, c->fpos, c->cells, c->nnb,
-                                                       c->ngather, c->rslab, c->hs_lo, c->hs_hi,
-                                                       c->hs_it, c->wl, c->status,
-                                                       c->order[c->cur], c->lst, c->lmeta);
+    if (c->any_lists) {
+        k_h_union<true><<<(unsigned)nbu, kThreads, 0, s>>>(
+            n, B, posh, c->fpos, c->cells, c->nnb, c->ngather, c->rslab, c->hs_lo, c->hs_hi,
+            c->hs_it, c->wl, c->status, c->wctr, c->recs, c->order[c->cur], c->lst, c->lmeta);
+        k_h_iterate<true><<<kReduceBlocks * 4, kThreads, 0, s>>>(
+            B, posh, c->fpos, c->cells, c->nnb, c->ngather, c->rslab, c->hs_lo, c->hs_hi,
+            c->hs_it, c->wl, c->status, c->order[c->cur], c->lst, c->lmeta);
+    } else {
+        k_h_union<false><<<(unsigned)nbu, kThreads, 0, s>>>(
+            n, B, posh, c->fpos, c->cells, c->nnb, c->ngather, c->rslab, c->hs_lo, c->hs_hi,
+            c->hs_it, c->wl, c->status, c->wctr, c->recs, c->order[c->cur], c->lst, c->lmeta);
+        k_h_iterate<false><<<kReduceBlocks * 4, kThreads, 0, s>>>(
+            B, posh, c->fpos, c->cells, c->nnb, c->ngather, c->rslab, c->hs_lo, c->hs_hi,
+            c->hs_it, c->wl, c->status, c->order[c->cur], c->lst, c->lmeta);
+    }
     k_finalize_h<<<nb, kThreads, 0, s>>>(n, B, posh, c->fpos, c->tin, c->ocnt, c->xpk);
     const unsigned gx = (unsigned)std::max(2, kReduceBlocks / c->ninst);
     k_cell_hmax<<<dim3(gx, (unsigned)c->ninst), kThreads, 0, s>>>(B, c->grid, c->cells, posh,
