@@ -1115,32 +1115,15 @@ k_rowlen_sort(int64_t n, const int32_t* __restrict__ ngather, const int32_t* __r
     if (i >= n || (status[2] & mask)) return;
     const int ng = ngather[i], no = ocnt[i];
     rowlen[i] = ng + no;
-    if (no < 2) return;
     int32_t* row = rslab + i * kRSlab + ng;
-    constexpr int kLocal = 32;  // outer parts are short: sorted in thread-local memory
-    if (no <= kLocal) {
-        int32_t v[kLocal];
-        for (int a = 0; a < no; ++a) v[a] = row[a];  // independent loads
-        for (int a = 1; a < no; ++a) {  // insertion sort
-            const int32_t x = v[a];
-            int b = a - 1;
-            while (b >= 0 && v[b] > x) {
-                v[b + 1] = v[b];
-                --b;
-            }
-            v[b + 1] = x;
-        }
-        for (int a = 0; a < no; ++a) row[a] = v[a];
-        return;
-    }
-    for (int a = 1; a < no; ++a) {  // a long outer part: insertion sort in place
-        const int32_t x = row[a];
+    for (int a = 1; a < no; ++a) {  // insertion sort
+        const int32_t v = row[a];
         int b = a - 1;
-        while (b >= 0 && row[b] > x) {
+        while (b >= 0 && row[b] > v) {
             row[b + 1] = row[b];
             --b;
         }
-        row[b + 1] = x;
+        row[b + 1] = v;
     }
 }
 
