@@ -28,12 +28,14 @@ using dfl::df;
 
 namespace {
 
-// pi h^3 W as a function of q >= 0 (cubic spline).
+// pi h^3 W as a function of q >= 0 (cubic spline). In the outer piece,
+// 1 <= q.hi <= 2, 2 - q.hi is exact (Sterbenz) and a multiple of ulp(q.hi),
+// so Fast2Sum with -q.lo gives 2 - q exactly, normalised.
 __device__ __forceinline__ df w_shape(df q) {
     const df q2 = dfl::sqr(q);
     const df a = dfl::addf(dfl::mulf(q, 0.75f), -1.5f);
     const df win = dfl::addf(dfl::mul(q2, a), 1.0f);  // 1 - 1.5 q^2 + 0.75 q^3
-    const df t = dfl::addf(dfl::neg(q), 2.0f);
+    const df t = dfl::fast_two_sum(__fsub_rn(2.0f, q.hi), -q.lo);
     const df wout = dfl::scale2(dfl::mul(dfl::sqr(t), t), 0.25f);  // (2 - q)^3 / 4
     const df zero = {0.0f, 0.0f};
     return q.hi < 1.0f ? win : (q.hi < 2.0f ? wout : zero);
@@ -43,11 +45,13 @@ __device__ __forceinline__ df w_shape(df q) {
 // (q + a)(b q + c) with the coefficients of q's piece:
 //   q < 1:      q (2.25 q - 3)                        (a, b, c) = (0, 2.25, -3)
 //   1 <= q < 2: (q - 2)(1.5 - 0.75 q) = -0.75 (2 - q)^2    (a, b, c) = (-2, -0.75, 1.5)
-// q + a is exact (TwoSum), and near q = 2 both factors are small with an
-// absolute error ~2^-47, so the product's absolute error stays ~2^-47 |2 - q|.
+// q + a is exact: for q < 1 it is q; for 1 <= q.hi <= 2, q.hi - 2 is exact
+// (Sterbenz) and a multiple of ulp(q.hi), so Fast2Sum with q.lo gives q - 2
+// exactly, normalised. Near q = 2 both factors are small with an absolute
+// error ~2^-47, so the product's absolute error stays ~2^-47 |2 - q|.
 __device__ __forceinline__ df dw_shape(df q) {
     const bool in = q.hi < 1.0f;
-    const df u = dfl::addf(q, in ? 0.0f : -2.0f);
+    const df u = in ? q : dfl::fast_two_sum(__fsub_rn(q.hi, 2.0f), q.lo);
     const df v = dfl::addf(dfl::mulf(q, in ? 2.25f : -0.75f), in ? -3.0f : 1.5f);
     const df f = dfl::mul(u, v);
     const df zero = {0.0f, 0.0f};
