@@ -451,7 +451,7 @@ __device__ __forceinline__ void union_group(
     int32_t* lrow = lst + (i >> 5) * (int64_t)kList * 32 + (i & 31);
     int nl = 0;
     bool listed = false;
-    if (build && valid) {  // this build's record of the particle (its list comes with the walk)
+    if (build && valid) {  // the list build's record of the particle (its list comes with the walk)
         const double4_32a p = posh[i];
         reinterpret_cast<float4*>(lmeta)[2 * id] =
             make_float4(dfl::from_double(p.x).hi, dfl::from_double(p.y).hi,
