@@ -311,13 +311,19 @@ k_set_single(KParams kp, int64_t n, long long cap, int64_t nblk, int32_t* __rest
 // of the previous batch's starts without them (its records are cleared, so
 // its next step builds its lists). A range kept from one call to the next
 // keeps its lists; whether they still hold is checked on the device.
+// [first, first + count) is a non-empty range within [0, the capacity)
+// (compared without forming first + count, which could overflow).
+static bool in_capacity(const sph_ctx* c, int64_t first, int64_t count) {
+    return count > 0 && first >= 0 && count <= c->ncap && first <= c->ncap - count;
+}
+
 void lists_for_layout(sph_ctx* c, int ninst, const int64_t* first, const int64_t* cnt,
                       cudaStream_t s) {
     for (int k = 0; k < ninst && c->lmeta; ++k) {
         bool seen = false;
         for (int q = 0; q < c->lay_n && !seen; ++q)
             seen = c->lay_first[q] == first[k] && c->lay_cnt[q] == cnt[k];
-        if (!seen && cnt[k] > 0 && first[k] + cnt[k] <= c->ncap)
+        if (!seen && in_capacity(c, first[k], cnt[k]))
             cudaMemsetAsync(c->lmeta + first[k], 0, (size_t)cnt[k] * sizeof(LMeta), s);
     }
     c->lay_n = ninst;
@@ -331,7 +337,7 @@ void lists_for_layout(sph_ctx* c, int ninst, const int64_t* first, const int64_t
 // step builds).
 void lists_clear(sph_ctx* c, cudaStream_t s) {
     for (int k = 0; k < c->lay_n && c->lmeta; ++k)
-        if (c->lay_cnt[k] > 0 && c->lay_first[k] + c->lay_cnt[k] <= c->ncap)
+        if (in_capacity(c, c->lay_first[k], c->lay_cnt[k]))
             cudaMemsetAsync(c->lmeta + c->lay_first[k], 0, (size_t)c->lay_cnt[k] * sizeof(LMeta), s);
 }
 
@@ -519,9 +525,9 @@ int64_t sph_neighbor_rows(const sph_ctx* c) { return c ? c->n : 0; }
 
 sph_status sph_lists_clear(sph_ctx* c, int64_t first, int64_t count, void* stream) {
     if (!c) return SPH_E_INVAL;
-    if (first < 0 || count < 0 || first + count > c->ncap) {
-        set_err(c, "sph_lists_clear: [%lld, %lld) outside [0, %lld)", (long long)first,
-                (long long)(first + count), (long long)c->ncap);
+    if (first < 0 || count < 0 || first > c->ncap || count > c->ncap - first) {
+        set_err(c, "sph_lists_clear: %lld entries from %lld outside [0, %lld)", (long long)count,
+                (long long)first, (long long)c->ncap);
         return SPH_E_INVAL;
     }
     if (count == 0 || !c->lmeta) return SPH_OK;  // no lists yet: nothing to forget
@@ -977,7 +983,8 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const
         if (k + 1 < ninst) slots = (slots + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
         kpi[k] = kparams(&params[k]);
         // the candidate lists are stored by caller index, up to the capacity
-        if (coff[k] + counts[k] > c->ncap) kpi[k].list_skin = 0.0;
+        // (compared without forming coff + count, which could overflow)
+        if (counts[k] > c->ncap || coff[k] > c->ncap - counts[k]) kpi[k].list_skin = 0.0;
         memset(&grid[k], 0, sizeof(Grid));
         grid[k].cbase = cells;
         grid[k].cap = instance_cell_cap(counts[k]);

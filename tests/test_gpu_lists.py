@@ -173,9 +173,10 @@ def test_lists_clear_gives_fresh_context_bits(B):
     fresh.sync()
     for f in STATE + OUTS + ("nnb", "dt", "time"):
         assert np.array_equal(host(again[f]).view(np.uint8), host(ref[f]).view(np.uint8)), f
-    with pytest.raises(B.SphError) as e:
-        ctx.lists_clear(n - 1, 2 + ctx.n_capacity)
-    assert e.value.status == B.SPH_E_INVAL
+    for first, count in ((n - 1, 2 + ctx.n_capacity), (1, 2 ** 63 - 1), (-1, 1), (2 ** 62, 1)):
+        with pytest.raises(B.SphError) as e:  # (first + count overflowing int64 too)
+            ctx.lists_clear(first, count)
+        assert e.value.status == B.SPH_E_INVAL
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
