@@ -276,7 +276,8 @@ sph_status sph_step_host(sph_ctx *ctx, const sph_params *prm, sph_particles *P, 
  * An instance's results are bit-identical to a single-problem sph_step of it
  * with the same parameters. Copies the descriptors to the device and waits
  * for the copy (synchronises `stream`). SPH_E_INVAL for ninst outside
- * [1, max_instances], a negative count, invalid params, or more particles
+ * [1, max_instances], a negative count or first, overlapping ranges, a range
+ * reaching past caller index 2^31 - 1, invalid params, or more particles
  * than the capacity. Any single-problem call replaces the batch. */
 sph_status sph_batch_set(sph_ctx *ctx, int32_t ninst, const int64_t *counts,
                          const int64_t *first, const sph_params *params, void *stream);

@@ -974,6 +974,12 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const
             set_err(c, "first[%d] < 0", k);
             return SPH_E_INVAL;
         }
+        // caller indices are held as int32: every instance ends below 2^31
+        // (compared without forming first + count, which could overflow)
+        if (counts[k] > (int64_t)INT32_MAX || (first && first[k] > (int64_t)INT32_MAX - counts[k])) {
+            set_err(c, "instance %d reaches past 2^31 - 1 caller entries", k);
+            return SPH_E_INVAL;
+        }
         ioff[k] = slots;
         roff[k] = tot;
         coff[k] = first ? first[k] : tot;

@@ -202,6 +202,14 @@ def test_batch_invalid_arguments(B):
     prms[2] = ics.SphParams(**{**prms[2].as_dict(), "precision": 1})
     with pytest.raises(B.SphError):  # mixed precisions in one batch
         ctx.batch_set(counts, prms)
+    ok = [p for _, p in insts]
+    for far in (2 ** 31 - 1, 2 ** 62, 2 ** 63 - 2):  # past caller index 2^31 - 1 (and
+        first = [0] * len(counts)                  # first + count overflowing int64)
+        first[1:] = [sum(counts[:k]) for k in range(1, len(counts))]
+        first[-1] = far
+        with pytest.raises(B.SphError) as e:
+            ctx.batch_set(counts, ok, first=first)
+        assert e.value.status == B.SPH_E_INVAL
     ctx.batch_set(counts, [p for _, p in insts])
     arr = B.alloc_arrays(concat([s for s, _ in insts[:-1]]), ninst=len(insts))
     with pytest.raises(B.SphError):  # arrays do not match the batch
