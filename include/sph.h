@@ -196,7 +196,10 @@ typedef struct {
  * S_i in a fixed slab of 224 entries (at most 128 of them the gather set);
  * the nnz_capacity-entry CSR is written for sph_build_neighbors and
  * sph_neighbors_to_host, and by a step only when some row does not fit its
- * slab (then SPH_E_CAPACITY if the CSR does not fit either). */
+ * slab (then SPH_E_CAPACITY if the CSR does not fit either). SPH_E_INVAL for
+ * a negative capacity, n_capacity (plus the batch gaps below) above
+ * 2^31 - 2 (slots are int32) or nnz_capacity above 2^40; SPH_E_CUDA for a
+ * device that does not exist. */
 sph_status sph_ctx_create(sph_ctx **out, int64_t n_capacity, int64_t nnz_capacity, int device);
 
 /* Largest number of instances of one batch (the instance id takes the top 8

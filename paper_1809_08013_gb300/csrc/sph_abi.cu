@@ -628,7 +628,9 @@ const char* sph_last_error(const sph_ctx* c) { return c ? c->err : "context is N
 int64_t sph_last_hnoconv(const sph_ctx* c) { return c ? c->last_hnoconv : 0; }
 
 int64_t sph_ctx_bytes(int64_t ncap, int64_t nnzcap, int32_t max_instances) {
-    if (ncap < 0 || nnzcap < 0 || max_instances < 1 || max_instances > SPH_MAX_INSTANCES) return -1;
+    if (ncap < 0 || ncap > (int64_t)INT32_MAX || nnzcap < 0 || max_instances < 1 ||
+        max_instances > SPH_MAX_INSTANCES)
+        return -1;
     sph_ctx c;
     memset(&c, 0, sizeof(c));
     c.ncap = ncap;
@@ -656,10 +658,11 @@ sph_status sph_ctx_create_batch(sph_ctx** out, int64_t ncap, int64_t nnzcap, int
     if (!out) return SPH_E_INVAL;
     *out = nullptr;
     if (max_instances < 1 || max_instances > SPH_MAX_INSTANCES) return SPH_E_INVAL;
+    if (ncap < 0 || ncap > (int64_t)INT32_MAX || nnzcap < 0 || nnzcap > ((int64_t)1 << 40))
+        return SPH_E_INVAL;
     // slots: the particles plus the gaps that start every instance on a block boundary
     const int64_t nslots = ncap + (int64_t)(kSlotAlign - 1) * (max_instances - 1);
-    if (ncap < 0 || nnzcap < 0 || nslots > (int64_t)INT32_MAX - 1 || nnzcap > ((int64_t)1 << 40))
-        return SPH_E_INVAL;
+    if (nslots > (int64_t)INT32_MAX - 1) return SPH_E_INVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();

@@ -63,6 +63,9 @@ def test_ctx_create_rejects_bad_sizes(lib):
     assert lib.sph_ctx_create(C.byref(h), -1, 10, 0) == binding.SPH_E_INVAL
     assert lib.sph_ctx_create(C.byref(h), 10, -5, 0) == binding.SPH_E_INVAL
     assert lib.sph_ctx_create(None, 10, 10, 0) == binding.SPH_E_INVAL
+    for ncap in (2 ** 31, 2 ** 63 - 1):  # slots are int32 (and ncap + gaps must not wrap)
+        assert lib.sph_ctx_create(C.byref(h), ncap, 10, 0) == binding.SPH_E_INVAL
+        assert lib.sph_ctx_bytes(ncap, 10, 1) == -1
     assert not h.value
 
 
