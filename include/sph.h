@@ -140,7 +140,7 @@ typedef struct {
                             turns the lists on allocates their buffers (about 800 B per
                             particle of capacity, not counted by sph_ctx_bytes; that call
                             synchronises the device and is not capturable, SPH_E_NOMEM
-                            if the allocation fails). Lists are kept per
+                            if the allocation fails). Their records are kept per
                             caller index: a batch instance whose caller range reaches
                             past the context's capacity runs without them. A tuning
                             knob: h and the neighbour sets do not depend on it (the

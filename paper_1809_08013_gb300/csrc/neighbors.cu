@@ -680,12 +680,14 @@ __device__ __forceinline__ void union_group(
     }
 }
 
-// The h search of the particles with a kept candidate list (one thread per
-// slot; the others are left to k_h_union): the bisection of the cell walk,
-// each count from one scan of the list while the list still covers 2h (its
-// radius at the build minus twice the largest displacement since), the same
-// sequence of h and the same neighbour set. A particle whose next h the list
-// no longer covers is handed, with its bisection state, to k_h_iterate.
+// The first count of the particles with a kept candidate list (one thread
+// per slot; the others are left to k_h_union): one scan of the list at the
+// current h, while the list still covers 2h (its radius at the build minus
+// twice the largest displacement since), with the cell walk's decisions. A
+// particle that converges is done; one that must go on bisecting (or whose
+// list does not cover 2h) is handed, with its bisection state, to
+// k_h_iterate, which takes its records from the list while it covers them:
+// the same sequence of h and the same neighbour set as the cell walk.
 __global__ void __launch_bounds__(kThreads)
 k_h_lists(int64_t n, Batch B, double4_32a* posh, const float4* __restrict__ fpos,
           int32_t* __restrict__ nnb, int32_t* __restrict__ ngather, int32_t* __restrict__ rslab,

@@ -991,7 +991,7 @@ sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const
         slots += counts[k];
         if (k + 1 < ninst) slots = (slots + kSlotAlign - 1) / kSlotAlign * kSlotAlign;
         kpi[k] = kparams(&params[k]);
-        // the candidate lists are stored by caller index, up to the capacity
+        // the candidate lists' records are kept by caller index, up to the capacity
         // (compared without forming coff + count, which could overflow)
         if (counts[k] > c->ncap || coff[k] > c->ncap - counts[k]) kpi[k].list_skin = 0.0;
         memset(&grid[k], 0, sizeof(Grid));
