@@ -324,7 +324,9 @@ void launch_density_df(sph_ctx* c, bool fuse_eos, cudaStream_t s, bool outer) {
 // ------------------------------------------------------------ forces + dt
 // Definitions as in physics.cu; algebra: Fbar = (0.5/pi)(f(q_i)/h_i^4 +
 // f(q_j)/h_j^4)/r, one shared reciprocal R = 1/((r^2 + eta2 hb^2) rhob) for the
-// viscosity, mu = hb v.r rhob R, 1/rhob = (r^2 + eta2 hb^2) R.
+// viscosity, mu = hb v.r rhob R, 1/rhob = (r^2 + eta2 hb^2) R. Every sum is
+// linear in Fbar, so its constant factor (0.5/pi, or dnorm/2) is applied once
+// per particle, in FP64, when the sums are written out.
 template <int T, int KER>
 __global__ void __launch_bounds__(kThreads, KER == KER_SINC ? 2 : 3)
 k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
@@ -356,7 +358,6 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         const bool per = kp.periodic_z != 0;
         const float hlz = gr.hlzc, L2 = gr.lzc[0], L1 = gr.lzc[1], L0 = gr.lzc[2];
         const int sn = kp.sinc_n;
-        const df c_half_pi = dfl::from_double_fp64(0.5 * (KER == KER_M4 ? kInvPi : kp.dnorm));
         const df eta2 = dfl::from_double_fp64(kp.eta2);
         const df betad = dfl::from_double_fp64(kp.beta);
         for (int e = sub; e < len; e += T) {
@@ -378,8 +379,7 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
             const df r = dfl::mul(r2, rinv);
             const df fa = dw_shape_k<KER>(dfl::mul(r, Hi), sn);
             const df fb = dw_shape_k<KER>(dfl::mul(r, df{b0.x, b0.y}), sn);
-            const df Fb = dfl::mul(dfl::add(dfl::mul(Ki, fa), dfl::mul(df{b0.z, b0.w}, fb)),
-                                   dfl::mul(rinv, c_half_pi));
+            const df Fb = dfl::mul(dfl::add(dfl::mul(Ki, fa), dfl::mul(df{b0.z, b0.w}, fb)), rinv);
             const df WX = dfl::sub(VXi, df{wa.x, wa.y}), WY = dfl::sub(VYi, df{wa.z, wa.w});
             const df WZ = dfl::sub(VZi, df{wb.x, wb.y});
             const df vr = dfl::add(dfl::add(dfl::mul(WX, X), dfl::mul(WY, Y)), dfl::mul(WZ, Z));
@@ -419,9 +419,12 @@ k_forces_df(int64_t n, Batch B, const double4_32a* __restrict__ posh,
         }
     }
     if (act && sub == 0) {
-        // back to the caller's units: a ~ V^2 / L, du ~ V^3 / L, mu ~ V
-        const Grid& gu = B.grid[slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T)];
-        const double sa = p2d(2 * gu.uV - gu.uL), su = p2d(3 * gu.uV - gu.uL);
+        // back to the caller's units: a ~ V^2 / L, du ~ V^3 / L, mu ~ V; and the
+        // constant factor of Fbar
+        const int ins = slot_inst(B, ((int64_t)blockIdx.x * blockDim.x) / T);
+        const Grid& gu = B.grid[ins];
+        const double cF = 0.5 * (KER == KER_M4 ? kInvPi : B.kp[ins].dnorm);
+        const double sa = p2d(2 * gu.uV - gu.uL) * cF, su = p2d(3 * gu.uV - gu.uL) * cF;
         const double Aid = (double)dpk[3 * i + 1].x + (double)dpk[3 * i + 1].y;
         acc[i] = make_double4_32a(-dfl::to_double(sx) * sa, -dfl::to_double(sy) * sa,
                                   -dfl::to_double(sz) * sa,
