@@ -89,9 +89,9 @@ FLOPS_PAIR_TABLE = 75
 # the files listed, in order); otherwise the bench reports null.
 NCU_EVIDENCE = {
     # k_forces_df<2, M4>, the 1M patch, second step of the timed call
-    "df": {"sources": ("physics_df.cu", "df.cuh"), "sha1": "7cb4ee095c6a4e1770cc73c1b05b8e9d23923f97",
-           "dram_bytes": (697.37 + 44.14) * 1e6, "warp_inst": 1721247545,
-           "issue_active": 73.96, "pairs": 100727656,
+    "df": {"sources": ("physics_df.cu", "df.cuh"), "sha1": "f8d02101d48d3d37cc808df61a0e0cc2ec302d17",
+           "dram_bytes": (697.33 + 44.48) * 1e6, "warp_inst": 1708627293,
+           "issue_active": 73.42, "pairs": 100727656,
            "profile": "profiles/forces_patch1m_evrard1m.md"},
     # k_forces_mx<2>, the 1M Evrard sphere, mixed precision
     "mixed": {"sources": ("physics_mixed.cu", "df.cuh"), "sha1": "342c531574d34f46723d3a8d907325d05aed3aee",
