@@ -348,6 +348,21 @@ sph_status sph_neighbors_to_host(sph_ctx *ctx, int64_t *offsets, int32_t *idx,
                                  int64_t idx_capacity, int32_t *ngather, int32_t *order,
                                  void *stream);
 
+/* The same neighbour list in CALLER order, on the host: row r belongs to
+ * the caller's particle r (r < ncaller, which must cover the caller arrays:
+ * n for a single problem, the batch's extent otherwise; rows of indices that
+ * hold no particle are empty) and lists caller indices: first its gather set
+ * N_r (ngather[r] entries), then the rest of S_r, each part in ascending
+ * caller index (so the rows do not depend on the library's internal order).
+ * offsets (ncaller + 1, required), idx (up to idx_capacity entries;
+ * SPH_E_INVAL if the list is longer) and ngather (ncaller) are host arrays;
+ * idx and ngather may be NULL. Permuted on the host after the copies of
+ * sph_neighbors_to_host (synchronises `stream`; host memory of about 4
+ * bytes per entry and 16 per particle). */
+sph_status sph_neighbors_to_host_caller(sph_ctx *ctx, int64_t ncaller, int64_t *offsets,
+                                        int32_t *idx, int64_t idx_capacity, int32_t *ngather,
+                                        void *stream);
+
 /* Phases of sph_step timed by sph_timing_read. */
 enum {
     SPH_PHASE_CELLS = 0,    /* load, bounding box, Morton keys, radix sort, permute, cell ranges */

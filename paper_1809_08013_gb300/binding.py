@@ -133,6 +133,8 @@ def load(rebuild: bool = True):
     L.sph_step_host.argtypes = [_DP, P(SphParams), P(SphParticles), C.c_int, _DP]
     L.sph_neighbors_to_host.restype = C.c_int
     L.sph_neighbors_to_host.argtypes = [_DP, _DP, _DP, C.c_int64, _DP, _DP, _DP]
+    L.sph_neighbors_to_host_caller.restype = C.c_int
+    L.sph_neighbors_to_host_caller.argtypes = [_DP, C.c_int64, _DP, _DP, C.c_int64, _DP, _DP]
     L.sph_sync.restype = C.c_int
     L.sph_sync.argtypes = [_DP, _DP]
     L.sph_timing_enable.restype = C.c_int
@@ -393,6 +395,22 @@ class Context:
 
     def last_hnoconv(self) -> int:
         return int(self.lib.sph_last_hnoconv(self.h))
+
+    def neighbors_caller(self, ncaller: int, stream=None):
+        """sph_neighbors_to_host_caller: the neighbour list in caller order
+        (offsets, idx, ngather) as host numpy arrays."""
+        import numpy as np
+        off = np.zeros(int(ncaller) + 1, dtype=np.int64)
+        I64, I32 = C.POINTER(C.c_int64), C.POINTER(C.c_int32)
+        self._check(self.lib.sph_neighbors_to_host_caller(
+            self.h, int(ncaller), off.ctypes.data_as(I64), None, 0, None, _stream(stream)))
+        nnz = int(off[-1])
+        idx = np.zeros(max(nnz, 1), dtype=np.int32)
+        ng = np.zeros(max(int(ncaller), 1), dtype=np.int32)
+        self._check(self.lib.sph_neighbors_to_host_caller(
+            self.h, int(ncaller), off.ctypes.data_as(I64), idx.ctypes.data_as(I32), len(idx),
+            ng.ctypes.data_as(I32), _stream(stream)))
+        return off, idx[:nnz], ng[:int(ncaller)]
 
     def neighbors_to_host(self, stream=None):
         """Neighbour list of the last build as host numpy arrays (offsets,

@@ -115,6 +115,26 @@ def test_batch_neighbour_lists_stay_in_their_instance(B, orc):
         assert same_sets((r[key], c[key], f[key]), canon_oracle(o["off"], o["idx"], o["ng"])), k
 
 
+def test_batch_caller_order_export(B, orc):
+    # caller rows of a batch: instance k's rows are its caller range, and
+    # each equals the oracle's row of that particle
+    insts = instances(0)
+    ctx, arr, counts, _ = run_batch(B, insts, nsteps=1)
+    off, idx, ng = ctx.neighbors_caller(sum(counts))
+    coff = np.concatenate([[0], np.cumsum(counts)])
+    for k, (s, p) in enumerate(insts):
+        o = orc.pipeline(p, s)
+        a, b = coff[k], coff[k + 1]
+        assert np.array_equal(off[a:b + 1] - off[a], o["off"]), k
+        assert np.array_equal(ng[a:b], o["ng"]), k
+        for r in range(b - a):
+            lo, g, hi = off[a + r], ng[a + r], off[a + r + 1]
+            oo, og = o["off"][r], o["ng"][r]
+            assert np.array_equal(idx[lo:lo + g] - a, np.sort(o["idx"][oo:oo + og])), (k, r)
+            assert np.array_equal(idx[lo + g:hi] - a,
+                                  np.sort(o["idx"][oo + og:o["off"][r + 1]])), (k, r)
+
+
 def test_batch_one_step_matches_oracle(B, orc):
     insts = instances(0)
     _, arr, counts, _ = run_batch(B, insts, nsteps=1)

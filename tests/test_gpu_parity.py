@@ -81,6 +81,28 @@ def test_neighbors_bit_exact(B, orc, name):
     assert same_sets(canon_gpu(off, idx, ng, order), canon_oracle(o["off"], o["idx"], o["ng"]))
 
 
+def _parts_sorted(off, idx, ng):
+    return all(np.all(np.diff(idx[off[r]:off[r] + ng[r]]) > 0) and
+               np.all(np.diff(idx[off[r] + ng[r]:off[r + 1]]) > 0) for r in range(len(off) - 1))
+
+
+@pytest.mark.parametrize("name", CASES[:2])
+def test_caller_order_export_equals_oracle(B, orc, name):
+    # rows of sph_neighbors_to_host_caller are the caller's particles: the row
+    # lengths and gather counts equal the oracle's entry by entry
+    s, prm, o, _ = oracle_of(orc, name)
+    ctx, arr, st = gpu_build(B, prm, s)
+    n = len(s["x"])
+    off, idx, ng = ctx.neighbors_caller(n)
+    assert np.array_equal(off, o["off"]) and np.array_equal(ng, o["ng"])
+    assert _parts_sorted(off, idx, ng)
+    ident = np.arange(n, dtype=np.int32)
+    assert same_sets(canon_gpu(off, idx, ng, ident), canon_oracle(o["off"], o["idx"], o["ng"]))
+    # and it is the internal export permuted
+    off2, idx2, ng2, order = ctx.neighbors_to_host()
+    assert same_sets(canon_gpu(off, idx, ng, ident), canon_gpu(off2, idx2, ng2, order))
+
+
 @pytest.mark.parametrize("name", CASES)
 def test_density_eos_forces_from_identical_inputs(B, orc, name):
     s, prm, o, _ = oracle_of(orc, name)
