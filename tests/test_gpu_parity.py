@@ -227,6 +227,47 @@ def test_full_size_one_step_1m(B, orc):
     assert abs(host(arr["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
 
 
+def test_full_size_twenty_steps_1m(B, orc):
+    # the benchmark's launch configuration: one sph_step(20) call on the 1M
+    # patch (the step graph replayed 20 times). Its last step is checked
+    # element by element against the oracle's step from the GPU's state after
+    # 19 steps (a split run gives the bits of one call), and the 20 steps
+    # against two conservation laws: central pair forces that are antisymmetric
+    # in i and j, with a kick-drift update, keep the linear momentum and the
+    # angular momentum about z exactly (the z image shift does not enter L_z).
+    s, prm = ics.square_patch(100, seed=2)
+    ctx = B.Context(len(s["x"]))
+    a20 = B.alloc_arrays(s)
+    ctx.step(prm, a20, nsteps=20)
+    a19 = B.alloc_arrays(s)
+    ctx.step(prm, a19, nsteps=19)
+    assert ctx.sync() == B.SPH_OK
+    s19 = {k: host(a19[k]).copy() for k in B.STATE_FIELDS}
+    o = orc.pipeline(prm, s19)
+    s1 = dict(s19)
+    s1["h"] = o["h"]
+    st_o = orc.leapfrog(prm, s1, o["dt"], o["ax"], o["ay"], o["az"], o["du"])
+    assert np.array_equal(host(a20["h"]).view(np.int64), o["h"].view(np.int64))
+    assert np.array_equal(host(a20["nnb"]), o["nnb"])
+    per = prm.periodic_z
+    err = {k: normwise(host(a20[k]), o[k]) for k in ("rho", "p", "c")}
+    err.update({k: force_err(k, host(a20[k]), o[k], o, per) for k in FORCES})
+    err.update({k: state_err(k, host(a20[k]), st_o[k], o, per, o["dt"])
+                for k in ("x", "y", "z", "vx", "vy", "vz", "u")})
+    check(err, TOL_FP64)
+    assert abs(host(a20["dt"])[0] - o["dt"]) <= TOL_FP64 * o["dt"]
+    # conservation over the 20 steps, against the magnitude of the summands
+    m = s["m"]
+    x, y, vx, vy, vz = (host(a20[k]) for k in ("x", "y", "vx", "vy", "vz"))
+    for v0, v in ((s["vx"], vx), (s["vy"], vy), (s["vz"], vz)):
+        assert abs(np.sum(m * v) - np.sum(m * v0)) <= 1e-12 * np.sum(m * np.abs(v))
+    lz0 = np.sum(m * (s["x"] * s["vy"] - s["y"] * s["vx"]))
+    lz = m * (x * vy - y * vx)
+    assert abs(np.sum(lz) - lz0) <= 1e-12 * np.sum(np.abs(lz))
+    # the time is the sum of the 20 steps' dt
+    assert host(a20["time"])[0] > host(a19["time"])[0] > 0.0
+
+
 # ---------------------------------------------------------------- edge cases
 def test_empty_input(B):
     s = {k: np.zeros(0) for k in ics.FIELDS}
