@@ -172,6 +172,30 @@ def test_three_steps_drift_is_small(B, orc):
     assert flips <= len(s["x"]) // 100
 
 
+def test_twenty_steps_drift_27k(B, orc, capsys):
+    # 20 steps of the 30^3 patch, each side from its own previous state:
+    # reported as drift, as trajectories may part at a bisection boundary (an
+    # ulp-level position difference can flip a count). Positions against the
+    # box size, velocities against the largest speed; the number of particles
+    # whose h bits differ after the 20 steps is reported beside them.
+    s, prm = _case("patch27k")
+    st_o, ex = orc.step(prm, s, nsteps=20)
+    ctx = B.Context(len(s["x"]))
+    arr = B.alloc_arrays(s)
+    ctx.step(prm, arr, nsteps=20)
+    assert ctx.sync() == B.SPH_OK
+    got = {k: host(arr[k]) for k in ("x", "y", "z", "vx", "vy", "vz", "h")}
+    vmax = float(np.max(np.sqrt(st_o["vx"] ** 2 + st_o["vy"] ** 2 + st_o["vz"] ** 2)))
+    drift = {k: float(np.max(np.abs(got[k] - st_o[k]))) for k in ("x", "y", "z")}
+    drift.update({k: float(np.max(np.abs(got[k] - st_o[k]))) / vmax for k in ("vx", "vy", "vz")})
+    flips = int(np.count_nonzero(got["h"] != st_o["h"]))
+    with capsys.disabled():
+        print(f"\n20-step drift, 30^3 patch: {drift}, h flips {flips} of {len(s['x'])}")
+    assert all(v <= 1e-9 for v in drift.values()), drift
+    assert flips <= len(s["x"]) // 100
+    assert abs(host(arr["time"])[0] - ex["time"]) <= 1e-9 * ex["time"]
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_split_run_equals_one_run(B, precision):
     # the internal order is a function of the positions only (keys are sorted
