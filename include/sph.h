@@ -358,7 +358,7 @@ sph_status sph_neighbors_to_host(sph_ctx *ctx, int64_t *offsets, int32_t *idx,
  * SPH_E_INVAL if the list is longer) and ngather (ncaller) are host arrays;
  * idx and ngather may be NULL. Permuted on the host after the copies of
  * sph_neighbors_to_host (synchronises `stream`; host memory of about 4
- * bytes per entry and 16 per particle). */
+ * bytes per entry and 16 per particle, SPH_E_NOMEM if it cannot be had). */
 sph_status sph_neighbors_to_host_caller(sph_ctx *ctx, int64_t ncaller, int64_t *offsets,
                                         int32_t *idx, int64_t idx_capacity, int32_t *ngather,
                                         void *stream);

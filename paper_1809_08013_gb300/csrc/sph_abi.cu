@@ -1127,44 +1127,52 @@ sph_status sph_neighbors_to_host_caller(sph_ctx* c, int64_t ncaller, int64_t* of
                    "arrays' extent %lld", (long long)ncaller, (long long)c->cext);
         return SPH_E_INVAL;
     }
-    // the internal rows on the host, then permuted to caller order there
-    const int64_t n = c->n;
-    std::vector<int64_t> off((size_t)n + 1);
-    std::vector<int32_t> ng((size_t)std::max<int64_t>(n, 1)), ord((size_t)std::max<int64_t>(n, 1));
-    sph_status st = sph_neighbors_to_host(c, off.data(), nullptr, 0, ng.data(), ord.data(), stream);
-    if (st != SPH_OK) return st;
-    const int64_t nnz = off[(size_t)n];
-    if (idx && nnz > idx_capacity) {
-        set_err(c, "neighbour list has %lld entries; buffer holds %lld", (long long)nnz,
-                (long long)idx_capacity);
-        return SPH_E_INVAL;
+    // the internal rows on the host, then permuted to caller order there (host
+    // memory in proportion to the list; an allocation failure is a status)
+    try {
+        const int64_t n = c->n;
+        std::vector<int64_t> off((size_t)n + 1);
+        std::vector<int32_t> ng((size_t)std::max<int64_t>(n, 1)), ord((size_t)std::max<int64_t>(n, 1));
+        sph_status st = sph_neighbors_to_host(c, off.data(), nullptr, 0, ng.data(), ord.data(), stream);
+        if (st != SPH_OK) return st;
+        const int64_t nnz = off[(size_t)n];
+        if (idx && nnz > idx_capacity) {
+            set_err(c, "neighbour list has %lld entries; buffer holds %lld", (long long)nnz,
+                    (long long)idx_capacity);
+            return SPH_E_INVAL;
+        }
+        std::vector<int32_t> in((size_t)std::max<int64_t>(idx ? nnz : 0, 1));
+        if (idx && (st = sph_neighbors_to_host(c, nullptr, in.data(), nnz, nullptr, nullptr,
+                                               stream)) != SPH_OK)
+            return st;
+        // row lengths by caller index (indices that hold no particle: empty rows),
+        // then their running sum
+        for (int64_t r = 0; r <= ncaller; ++r) offsets[r] = 0;
+        if (ngather)
+            for (int64_t r = 0; r < ncaller; ++r) ngather[r] = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            const int32_t o = ord[(size_t)k];
+            if (o < 0) continue;  // an empty slot between instances
+            offsets[o + 1] = off[(size_t)k + 1] - off[(size_t)k];
+            if (ngather) ngather[o] = ng[(size_t)k];
+        }
+        for (int64_t r = 0; r < ncaller; ++r) offsets[r + 1] += offsets[r];
+        if (!idx) return SPH_OK;
+        for (int64_t k = 0; k < n; ++k) {
+            const int32_t o = ord[(size_t)k];
+            if (o < 0) continue;
+            int32_t* dst = idx + offsets[o];
+            const int64_t a = off[(size_t)k], b = off[(size_t)k + 1];
+            for (int64_t e = a; e < b; ++e) dst[e - a] = ord[(size_t)in[(size_t)e]];
+            // each part in ascending caller index: independent of the internal order
+            std::sort(dst, dst + ng[(size_t)k]);
+            std::sort(dst + ng[(size_t)k], dst + (b - a));
+        }
+        return SPH_OK;
+    } catch (const std::bad_alloc&) {
+        set_err(c, "sph_neighbors_to_host_caller: host memory for the permutation");
+        return SPH_E_NOMEM;
     }
-    std::vector<int32_t> in((size_t)std::max<int64_t>(nnz, 1));
-    if (idx && (st = sph_neighbors_to_host(c, nullptr, in.data(), nnz, nullptr, nullptr, stream)) !=
-                   SPH_OK)
-        return st;
-    std::vector<int64_t> len((size_t)ncaller, 0);
-    std::vector<int64_t> row_of((size_t)ncaller, -1);  // internal row of each caller index
-    for (int64_t k = 0; k < n; ++k) {
-        const int32_t o = ord[(size_t)k];
-        if (o < 0) continue;  // an empty slot between instances
-        row_of[(size_t)o] = k;
-        len[(size_t)o] = off[(size_t)k + 1] - off[(size_t)k];
-    }
-    offsets[0] = 0;
-    for (int64_t r = 0; r < ncaller; ++r) offsets[r + 1] = offsets[r] + len[(size_t)r];
-    for (int64_t r = 0; r < ncaller; ++r) {
-        const int64_t k = row_of[(size_t)r];
-        if (ngather) ngather[r] = k >= 0 ? ng[(size_t)k] : 0;
-        if (!idx || k < 0) continue;
-        int32_t* dst = idx + offsets[r];
-        const int64_t a = off[(size_t)k], b = off[(size_t)k + 1];
-        for (int64_t e = a; e < b; ++e) dst[e - a] = ord[(size_t)in[(size_t)e]];
-        // each part in ascending caller index: independent of the internal order
-        std::sort(dst, dst + ng[(size_t)k]);
-        std::sort(dst + ng[(size_t)k], dst + (b - a));
-    }
-    return SPH_OK;
 }
 
 sph_status sph_sync(sph_ctx* c, void* stream) {

@@ -52,6 +52,8 @@ def test_null_context_is_rejected_without_launch(lib):
     assert lib.sph_step_host(None, C.byref(prm), C.byref(P), 1, None) == binding.SPH_E_INVAL
     assert lib.sph_sync(None, None) == binding.SPH_E_INVAL
     assert lib.sph_lists_clear(None, 0, 1, None) == binding.SPH_E_INVAL
+    off = (C.c_int64 * 2)()
+    assert lib.sph_neighbors_to_host_caller(None, 1, off, None, 0, None, None) == binding.SPH_E_INVAL
     v = C.c_int64(7)
     assert lib.sph_list_builds(None, C.byref(v), None) == binding.SPH_E_INVAL
     assert lib.sph_last_error(None) == b"context is NULL"
