@@ -946,9 +946,23 @@ sph_status sph_step_host(sph_ctx* c, const sph_params* prm, sph_particles* H, in
     return check_launch(c, "sph_step_host");
 }
 
+static sph_status batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const int64_t* first,
+                            const sph_params* params, void* stream);
+
+// (the host tables of a batch are std::vector: no exception leaves the ABI)
 sph_status sph_batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const int64_t* first,
                          const sph_params* params, void* stream) {
     if (!c) return SPH_E_INVAL;
+    try {
+        return batch_set(c, ninst, counts, first, params, stream);
+    } catch (const std::bad_alloc&) {
+        set_err(c, "sph_batch_set: host memory for the batch tables");
+        return SPH_E_NOMEM;
+    }
+}
+
+static sph_status batch_set(sph_ctx* c, int32_t ninst, const int64_t* counts, const int64_t* first,
+                            const sph_params* params, void* stream) {
     if (ninst < 1 || ninst > c->maxinst || !counts || !params) {
         set_err(c, "ninst = %d outside [1, %d] or NULL arrays", (int)ninst, c->maxinst);
         return SPH_E_INVAL;
