@@ -61,3 +61,15 @@ def test_summary_line_is_compact():
     assert len(txt) < 1500, len(txt)
     assert sm["serving"]["requests"] == 2000
     assert sm["evrard_mixed"]["roofline_frac"] == 0.0812
+
+
+def test_ncu_evidence_only_for_the_captured_sources(monkeypatch):
+    # the counters of a capture are reported only while the kernel's sources
+    # hash to the captured version
+    for kind in bench.NCU_EVIDENCE:
+        ref = bench.ncu_evidence(kind)
+        assert ref is None or ref["dram_bytes"] > 0
+    stale = {k: dict(v, sha1="0" * 40) for k, v in bench.NCU_EVIDENCE.items()}
+    monkeypatch.setattr(bench, "NCU_EVIDENCE", stale)
+    assert all(bench.ncu_evidence(k) is None for k in stale)
+    assert bench.ncu_evidence("no such kernel") is None
